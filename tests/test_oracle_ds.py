@@ -1,0 +1,125 @@
+"""Pins for the oracle's domain selection (Sec. III-B) and its generator."""
+
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import brute_force, ising, rng
+from oracle import domain_selection as ds
+
+
+def test_splitmix64_published_outputs():
+    # SplitMix64 started at 0: first three outputs
+    z = rng.splitmix64(0, np.arange(3))
+    assert [int(x) for x in z] == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4,
+                                   0x06C45D188009454F]
+
+
+def test_theta_init_relaxes_the_uniform_draw():
+    x0 = rng.uniform_pm1(11, 8, 50)
+    assert x0.min() >= -1.0 and x0.max() < 1.0
+    assert abs(x0.mean()) < 0.15
+    np.testing.assert_allclose(np.sin(rng.theta_init(11, 8, 50)), x0, atol=1e-15)
+
+
+def _setup(seed=0, n=24, B=5, conv="physics"):
+    inst = synth.random_sparse_instance(n, seed, p=0.3, kind="float", h="float",
+                                        convention=conv, j_scale=0.5)
+    cq, ch = ising.coefficients(inst.j_scale, inst.convention)
+    J = ising.coupling_matrix(inst)
+    h = ising.field(inst)
+    theta = np.random.default_rng(seed).uniform(-math.pi, math.pi, (n, B))
+    return inst, cq, ch, J, h, theta
+
+
+@pytest.mark.parametrize("conv", ["physics", "paper"])
+def test_gradient_matches_finite_difference(conv):
+    inst, cq, ch, J, h, theta = _setup(conv=conv)
+    p = ds.Params(mu=0.7)
+    s = ds.round_spins(theta)
+    r = ds.step(J, h, cq, ch, p, theta, np.zeros_like(theta), np.zeros_like(theta), 1)
+    d = 1e-6
+    for i in range(0, inst.n, 5):
+        tp = theta.copy()
+        tm = theta.copy()
+        tp[i] += d
+        tm[i] -= d
+        fd = (ds.loss(J, h, cq, ch, p.mu, tp, s) - ds.loss(J, h, cq, ch, p.mu, tm, s)) / (2 * d)
+        np.testing.assert_allclose(r.grad[i], fd, rtol=1e-6, atol=1e-7)
+
+
+def test_loss_at_the_corners_is_energy_minus_mu_d():
+    # with |sin theta| = 1 the loss of Eq. (loss function) is s^T (A - mu I) s + b^T s
+    inst, cq, ch, J, h, _ = _setup(n=18, B=4)
+    s = (2 * np.random.default_rng(3).integers(0, 2, (18, 4)) - 1).astype(float)
+    theta = s * (math.pi / 2)
+    mu = 1.3
+    L = ds.loss(J, h, cq, ch, mu, theta, ds.round_spins(theta))
+    np.testing.assert_allclose(L, ising.energy(inst, s) - mu * 18, rtol=1e-12)
+
+
+def test_adam_matches_torch_adam():
+    torch = pytest.importorskip("torch")
+    inst, cq, ch, J, h, theta = _setup(n=16, B=3)
+    p = ds.Params(lr=0.05, mu=0.2, beta1=0.8, beta2=0.99, eps=1e-6)
+    th = torch.tensor(theta, dtype=torch.float64, requires_grad=True)
+    opt = torch.optim.Adam([th], lr=p.lr, betas=(p.beta1, p.beta2), eps=p.eps)
+    m = np.zeros_like(theta)
+    v = np.zeros_like(theta)
+    cur = theta.copy()
+    for t in range(1, 6):
+        r = ds.step(J, h, cq, ch, p, cur, m, v, t)
+        # torch sees the same gradient of the frozen-spin loss at the same point
+        with torch.no_grad():
+            th.copy_(torch.tensor(cur))
+        s = torch.tensor(ds.round_spins(cur))
+        F = torch.tensor(r.F)
+        opt.zero_grad()
+        (torch.sin(th) * F).sum().backward()
+        np.testing.assert_allclose(th.grad.numpy(), r.grad, rtol=1e-13, atol=1e-13)
+        opt.step()
+        ref = th.detach().numpy()
+        diff = r.theta - ref
+        diff -= 2 * math.pi * np.rint(diff / (2 * math.pi))
+        assert np.max(np.abs(diff)) < 1e-12
+        assert s is not None
+        cur, m, v = r.theta, r.m, r.v
+
+
+def test_first_step_moves_each_angle_by_lr():
+    inst, cq, ch, J, h, theta = _setup(n=30, B=4)
+    p = ds.Params(lr=0.3, mu=0.1)
+    r = ds.step(J, h, cq, ch, p, theta, np.zeros_like(theta), np.zeros_like(theta), 1)
+    moved = r.theta - theta
+    moved -= 2 * math.pi * np.rint(moved / (2 * math.pi))
+    big = np.abs(r.grad) > 1e-3
+    np.testing.assert_allclose(np.abs(moved[big]), p.lr, rtol=1e-5)
+    assert np.all(np.sign(moved[big]) == -np.sign(r.grad[big]))
+    assert np.all(np.abs(r.theta) <= math.pi + 1e-12)
+
+
+def test_best_tracking_follows_the_trace():
+    inst = synth.sk_dense(40, 2, 1.0)
+    r = ds.select_domain(inst, ds.Params(restarts=6, steps=40, lr=0.3, seed=5), trace=True)
+    tr = r["trace"]
+    np.testing.assert_array_equal(r["restart_best_energy"], tr.min(axis=0))
+    np.testing.assert_array_equal(r["restart_best_step"], tr.argmin(axis=0) + 1)
+    # the stored best spins have the stored best energy
+    np.testing.assert_allclose(ising.energy(inst, r["restart_best_spins"]),
+                               r["restart_best_energy"], rtol=1e-12)
+    assert r["best_energy"] == tr.min()
+    assert r["best_restart"] == int(np.nonzero(tr.min(axis=0) == tr.min())[0][0])
+
+
+@pytest.mark.parametrize("n", [16, 20])
+def test_reaches_brute_force_ground_states(n):
+    hits = 0
+    for seed in range(4):
+        inst = synth.sk_dense(n, 100 + seed, 1.0)
+        e0, _ = brute_force.ground_state(inst)
+        r = ds.select_domain(inst, ds.Params(restarts=64, steps=150, lr=6.0, seed=seed))
+        assert r["best_energy"] >= e0 - 1e-9
+        hits += abs(r["best_energy"] - e0) < 1e-9
+    assert hits >= 3
