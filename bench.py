@@ -1,0 +1,379 @@
+#!/usr/bin/env python
+"""Benchmark of the pruning + domain-selection hot path on GB300.
+
+One bench step is one full solve through the C ABI on a synthetic max-cut
+instance shaped like the paper's benchmark problems: pruning, B restarts x T
+steps of the fused domain-selection step (Sec. III-B), best-of-restarts,
+reconstruction and the energy of the result on the full instance.
+
+Default workload: Erdos-Renyi N=2000, mean degree 10, weights +-1, J = -W/2
+(int8 dense), h = 0, 1024 restarts x 2000 steps, lr 6.0.
+
+Prints one JSON line (metric: relaxed spin-updates/s = N_reduced * B * T per
+second of device time). ``--impl reference`` times the FP64 CPU oracle on the
+same workload instead (bounded samples of the same solve).
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "relaxed spin-updates/s"
+UNIT = "spin-updates/s"
+WORKLOADS = {
+    # name: (instance, restarts, steps)
+    "er2000": ("er2000", 1024, 2000),
+    "er800": ("er800", 1024, 2000),
+    "sk100": ("sk100", 64, 1000),
+    "sk4096": ("sk4096", 4096, 5000),
+    "torus20k": ("torus20k", 512, 3000),
+    "er100k_pendant": ("er100k_pendant", 512, 3000),
+}
+L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
+
+
+def args_():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="er2000", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="auto")
+    ap.add_argument("--lr", type=float, default=6.0)
+    ap.add_argument("--mu", type=float, default=0.0)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-steps", type=int, default=200)
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------- clocks
+
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- helpers
+
+def device_instance(inst, torch):
+    import dataclasses
+    def t(x):
+        return None if x is None else torch.from_numpy(x).cuda()
+    return dataclasses.replace(inst, J=t(inst.J), indptr=t(inst.indptr),
+                               indices=t(inst.indices), data=t(inst.data), h=t(inst.h))
+
+
+def pinned_instance(inst, torch):
+    import dataclasses
+    def p(x):
+        if x is None:
+            return None
+        return torch.from_numpy(x).pin_memory().numpy()
+    return dataclasses.replace(inst, J=p(inst.J), indptr=p(inst.indptr),
+                               indices=p(inst.indices), data=p(inst.data), h=p(inst.h))
+
+
+def input_bytes(inst) -> int:
+    arrs = [inst.J, inst.indptr, inst.indices, inst.data, inst.h]
+    return int(sum(a.nbytes for a in arrs if a is not None))
+
+
+def peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        d["source"] = "measured"
+        return d
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0, "source": "fallback"}
+
+
+def traffic_for(kernel: str, src_file: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current source of the kernel."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    d = json.load(open(path)).get(kernel)
+    if not d:
+        return None
+    h = hashlib.sha256(open(os.path.join(ROOT, src_file), "rb").read()).hexdigest()[:16]
+    return d["bytes_per_launch"] if d.get("source_sha") == h else None
+
+
+def launches_per_solve(T: int, rounds: int, path: int) -> int:
+    # instance checks (2), pruning (3 + 7 per round incl. the final empty round + 3),
+    # session set-up (4), T steps x (step + track), finish (step + track + argmin),
+    # reconstruction (1), full-instance energy (check + 2)
+    return 2 + 3 + 7 * (rounds + 1) + 3 + 4 + 2 * T + 3 + 1 + 3
+
+
+# ----------------------------------------------------------------- reference arm
+
+def run_reference(a, rank, world):
+    """The FP64 CPU oracle on the same workload: each step is one bounded
+    sample of the solve (pruning, `sample` domain-selection steps over all
+    restarts, reconstruction, final energy)."""
+    if rank != 0:
+        return
+    import numpy as np
+    import synth
+    from oracle import domain_selection as ods
+    from oracle import ising, pruning
+    name, B, T = WORKLOADS[a.workload]
+    inst = synth.workload(name, 0)
+    sample = 3
+
+    def one():
+        res = pruning.prune(inst)
+        red = res.reduced
+        r = ods.select_domain(red, ods.Params(restarts=B, steps=sample, lr=a.lr, mu=a.mu, seed=0))
+        full = pruning.reconstruct(res, r["best_spins"])
+        ising.energy(inst, full.astype(np.float64))
+        return red.n * B * sample
+
+    for _ in range(a.warmup):
+        one()
+    t0 = time.perf_counter()
+    units = 0
+    for _ in range(a.steps):
+        units += one()
+    dt = time.perf_counter() - t0
+    value = units / dt
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * dt / a.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"{a.workload}: N={inst.n}, restarts={B}, steps={T}",
+                       "sample_steps_per_bench_step": sample, "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"per bench step: prune + {sample} of {T} steps x {B} "
+                                       "restarts + reconstruct + energy, numpy FP64"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------- CPU baseline
+
+def cpu_baseline(a, inst, B, seconds):
+    import numpy as np
+    from oracle import domain_selection as ods
+    from oracle import ising
+    cq, ch = ising.coefficients(inst.j_scale, inst.convention)
+    J = ising.coupling_matrix(inst)
+    h = ising.field(inst)
+    p = ods.Params(restarts=B, steps=1 << 30, lr=a.lr, mu=a.mu, seed=0)
+    from oracle import rng
+    th = rng.theta_init(0, B, inst.n)
+    m = np.zeros_like(th)
+    v = np.zeros_like(th)
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        r = ods.step(J, h, cq, ch, p, th, m, v, steps + 1)
+        th, m, v = r.theta, r.m, r.v
+        steps += 1
+        if time.perf_counter() - t0 >= seconds and steps >= 2:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": inst.n * B * steps / dt, "unit": UNIT, "cores": os.cpu_count(),
+            "kind": "oracle",
+            "sample": f"{steps} domain-selection steps x {B} restarts on the same instance "
+                      f"(numpy FP64, {dt:.1f} s)"}
+
+
+# ----------------------------------------------------------------- main
+
+def main():
+    a = args_()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    if a.impl == "reference":
+        run_reference(a, rank, world)
+        return
+    import numpy as np
+    import torch
+    import synth
+    from paper_2312_05837_gb300 import api
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    name, B, T = WORKLOADS[a.workload]
+    inst = synth.workload(name, seed=rank)
+    dinst = device_instance(inst, torch)
+    hinst = pinned_instance(inst, torch)
+    ctx = api.Context(local)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    kw = dict(lr=a.lr, mu=a.mu, precision=a.precision)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def solve(seed):
+        return api.solve(ctx, dinst, restarts=B, steps=T, seed=seed, **kw)
+
+    for w in range(a.warmup):
+        solve(1000 + w)
+    torch.cuda.synchronize()
+    pr = api.prune(ctx, inst)
+    n_red, rounds = pr.n_reduced, pr.rounds
+    pr.close()
+
+    clocks = Clocks(local)
+    clocks.start()
+    barrier()
+    total_ms = 0.0
+    last = None
+    for k in range(a.steps):
+        flush.fill_(float(k))  # L2 flush between timed solves (outside the timed region)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        last = solve(k)
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+    barrier()
+    clk = clocks.stop()
+    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    max_ms = float(t.item())
+    units = n_red * B * T
+    value = world * units * a.steps / (max_ms / 1e3)
+
+    # end to end: host (pinned) inputs, host outputs, copies inside the timed region
+    barrier()
+    w0 = time.perf_counter()
+    for k in range(a.steps):
+        out = api.solve(ctx, hinst, restarts=B, steps=T, seed=k, **kw)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - w0
+    te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = world * units * a.steps / float(te.item())
+
+    # dominant kernel: the fused step, timed launch by launch with events
+    prof = api.Session(ctx, dinst, restarts=B, steps=a.profile_steps, seed=7, profile=True, **kw)
+    prof.run(a.profile_steps)
+    st = prof.result()
+    prof.close()
+    avg_ms = st["kernel_ms"] / max(st["kernel_launches"], 1)
+    pk = peaks()
+    path = last["path"]
+    if path == 2:  # sparse: HBM bound, 24 B of theta/m/v traffic per update + spin bits
+        alg = n_red * ((B + 127) // 128 * 128) * (24 + 0.25)
+        roof = {"bound": "hbm", "achieved": alg / (avg_ms / 1e3) / 1e9, "peak": pk["hbm_gbs"],
+                "unit": "GB/s"}
+        kname, ksrc = "sparse_step_kernel", "paper_2312_05837_gb300/csrc/ds_sparse.cu"
+    elif path == 1:  # tensor cores: 2 N^2 B flop per step
+        alg = 2.0 * n_red * n_red * B
+        roof = {"bound": "tensor", "achieved": alg / (avg_ms / 1e3) / 1e12,
+                "peak": pk["bf16_tflops_sustained"], "unit": "TFLOP/s"}
+        kname, ksrc = "tc_step_kernel", "paper_2312_05837_gb300/csrc/ds_tc.cu"
+    else:  # plain FP32 FMA on the CUDA cores: 2 N^2 B flop per step
+        alg = 2.0 * n_red * n_red * B
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        fp32_peak = sms * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": alg / (avg_ms / 1e3) / 1e12, "peak": fp32_peak,
+                "unit": "TFLOP/s"}
+        kname, ksrc = "plain_step_kernel", "paper_2312_05837_gb300/csrc/ds_plain.cu"
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = traffic_for(kname, ksrc)
+    roof["kernel"] = kname
+    roof["peak_source"] = pk["source"]
+    roof["avg_launch_ms"] = avg_ms
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": max_ms / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {0: "f32", 1: "bf16", 2: "f32"}[path], "data": "synthetic",
+            "config": {"workload": f"{name}: N={inst.n} (N_reduced={n_red}), restarts={B}, "
+                                   f"steps={T}, lr={a.lr}, mu={a.mu}",
+                       "precision": a.precision, "path": {0: "plain", 1: "tc", 2: "sparse"}[path],
+                       "l2": "flushed (512 MB write) before each timed solve",
+                       "parallelism": f"replicas x{world}"},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": input_bytes(inst),
+                    "d2h_bytes_per_step": int(inst.n) + 8},
+            "gpu_launches": launches_per_solve(T, rounds, path) * a.steps,
+            "roofline": roof, "clocks": clk,
+            "best_energy": float(last["best_energy"].item())}
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(a, inst, B, a.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

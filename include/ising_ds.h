@@ -1,0 +1,255 @@
+/*
+ * ising_ds.h - C ABI of the GB300 pruning + domain-selection Ising solver.
+ *
+ * The solver follows Li, Dong and Pan, "Fast Numerical Solver of Ising
+ * Optimization Problems via Pruning and Domain Selection":
+ *   - the problem (Sec. II, Eq. primal): minimise E(s) over s in {-1,+1}^n,
+ *   - pruning (Sec. III-A, Algorithm 1): fix determined and semi-determined
+ *     spins and fold them into a smaller problem plus a constant,
+ *   - domain selection (Sec. III-B, Eq. loss function): relax each spin to
+ *     sin(theta_i), run Adam on many restarts at once, round, keep the best,
+ *   - reconstruction: recover the pruned spins from the record of pruning.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * An instance holds stored couplings J (symmetric, zero diagonal), an
+ * optional field h, a scale j_scale and a convention:
+ *   ISING_CONV_PHYSICS:  E(s) = -1/2 * j_scale * s^T J s - h^T s
+ *                        (max-cut with weights W is J = -W, j_scale = 1/2),
+ *   ISING_CONV_PAPER:    E(s) = j_scale * s^T J s + h^T s   (Sec. II form).
+ * Both reduce to E(s) = cQ s^T J s + cH h^T s, (cQ, cH) = (-j_scale/2, -1)
+ * or (j_scale, +1).
+ *
+ * Dense J is n*n row-major. CSR J stores both (i,j) and (j,i), columns
+ * strictly increasing inside a row, no diagonal entry; indptr has n+1
+ * entries. Spin vectors are int8 +1/-1. Restart-major arrays of B vectors of
+ * length n are [B][n] with the spin index contiguous.
+ *
+ * Memory: every pointer of an instance and every output pointer is host or
+ * device memory as the call's `mem` argument (or the instance's `mem` field)
+ * says; the library copies what it needs and never keeps a caller pointer
+ * past the call. Objects returned through `**out` are owned by the library
+ * and released by the matching *_destroy / *_free call.
+ *
+ * Errors: every call returns an ising_status. On error nothing is written to
+ * the outputs, and ising_last_error(ctx) describes the failure. A CUDA error
+ * is reported as ISING_ECUDA. No exception and no abort crosses the ABI.
+ * A context is not thread-safe: serialise calls on one context.
+ */
+#ifndef ISING_DS_H
+#define ISING_DS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum ising_status {
+  ISING_OK = 0,
+  ISING_EINVAL = 1,   /* bad argument: shape, dtype, asymmetric J, diagonal */
+  ISING_ENOMEM = 2,   /* device or host allocation failed */
+  ISING_ECUDA = 3,    /* a CUDA call failed */
+  ISING_ETIMEOUT = 4, /* a bounded device wait gave up */
+  ISING_EBUSY = 5,    /* server: request does not fit the memory budget now */
+  ISING_ENOTSUP = 6   /* combination not supported by this build */
+} ising_status;
+
+enum { ISING_LAYOUT_DENSE = 0, ISING_LAYOUT_CSR = 1 };
+enum { ISING_F64 = 0, ISING_F32 = 1, ISING_I8 = 2, ISING_I32 = 3 };
+enum { ISING_CONV_PHYSICS = 0, ISING_CONV_PAPER = 1 };
+enum { ISING_MEM_HOST = 0, ISING_MEM_DEVICE = 1 };
+
+/* Coupling product precision of the domain-selection step (Sec. III-B).
+ *  AUTO        dense -> TC, CSR -> sparse FP32/int kernel.
+ *  FP32_PLAIN  dense J in FP32 on the CUDA cores (SIMT FMA), the plain form.
+ *  TC          dense J on the tensor cores (tcgen05, FP32 accumulate), exact:
+ *              integer |J| <= 256 as one BF16 plane, other J as three BF16
+ *              planes hi + mid + lo (about 24 significant bits).
+ *  BF16        dense J rounded once to BF16 (lossy for non-integer J).
+ *  FP8         dense J as E4M3 with one FP32 scale per row; spins E4M3
+ *              (exact for integer |J| <= 16, lossy otherwise).
+ * Every candidate is rounded to +-1 and its energy re-evaluated exactly
+ * (integer J) or in FP64 (other J) by the final energy pass. */
+enum {
+  ISING_PREC_AUTO = 0,
+  ISING_PREC_FP32_PLAIN = 1,
+  ISING_PREC_TC = 2,
+  ISING_PREC_BF16 = 3,
+  ISING_PREC_FP8 = 4
+};
+
+/* Execution path actually used, reported in ising_ds_stats.path. */
+enum { ISING_PATH_PLAIN = 0, ISING_PATH_TC = 1, ISING_PATH_SPARSE = 2 };
+
+typedef struct ising_ctx ising_ctx;
+typedef struct ising_ds ising_ds;
+typedef struct ising_prune_result ising_prune_result;
+
+/* An Ising instance (Sec. II). Borrowed for the duration of a call. */
+typedef struct ising_instance {
+  int64_t n;              /* number of spins, >= 1 */
+  int32_t layout;         /* ISING_LAYOUT_* */
+  int32_t j_dtype;        /* ISING_F64/F32/I8/I32 */
+  const void* J;          /* dense: n*n; CSR: nnz values */
+  const int64_t* indptr;  /* CSR: n+1 row offsets, else NULL */
+  const int32_t* indices; /* CSR: nnz column indices, else NULL */
+  int64_t nnz;            /* CSR: number of stored entries */
+  int32_t h_dtype;        /* ISING_F64/F32/I32 (ignored when h is NULL) */
+  int32_t reserved0;
+  const void* h;          /* n fields, or NULL for h = 0 */
+  double j_scale;         /* effective coupling = j_scale * stored J */
+  int32_t convention;     /* ISING_CONV_* */
+  int32_t mem;            /* ISING_MEM_* for J, indptr, indices, h */
+} ising_instance;
+
+/* Domain-selection parameters (Sec. III-B, Sec. IV-B). */
+typedef struct ising_ds_params {
+  int64_t restarts; /* B >= 1 independent runs ("sweeps") */
+  int64_t steps;    /* T >= 0 Adam steps; energies at steps 1..T+1 */
+  double lr;        /* Adam learning rate (the paper uses 6.0) */
+  double mu;        /* penalty weight of Eq. (lagrange function), >= 0 */
+  double beta1;     /* Adam first-moment decay, in [0,1) (0.9) */
+  double beta2;     /* Adam second-moment decay, in [0,1) (0.999) */
+  double eps;       /* Adam epsilon, > 0 (1e-8) */
+  uint64_t seed;    /* theta_init = asin(x0), x0 from SplitMix64(seed) */
+  int32_t precision;/* ISING_PREC_* */
+  int32_t flags;    /* ISING_DS_PROFILE or 0 */
+} ising_ds_params;
+
+/* params.flags: time every step-kernel launch with CUDA events on the
+ * context's stream and report the sum in ising_ds_stats.kernel_ms. */
+#define ISING_DS_PROFILE 1
+
+typedef struct ising_ds_stats {
+  int64_t best_restart;     /* restart holding the overall best */
+  int64_t best_step;        /* step (1..T+1) at which it was reached */
+  double last_best_energy;  /* lowest energy of the final spins (step T+1) */
+  int64_t last_best_restart;
+  int64_t steps_done;
+  int32_t path;             /* ISING_PATH_* */
+  int32_t precision;        /* ISING_PREC_* actually used */
+  double device_ms;         /* device time of the steps (CUDA events) */
+  double kernel_ms;         /* step kernels only (with ISING_DS_PROFILE) */
+  int64_t kernel_launches;  /* step-kernel launches timed in kernel_ms */
+} ising_ds_stats;
+
+/* ------------------------------------------------------------------ context */
+
+/* Create a context on CUDA device `device`, issuing work on `stream`
+ * (a cudaStream_t, NULL = the legacy default stream). */
+int ising_create(ising_ctx** out, int device, void* stream);
+int ising_destroy(ising_ctx* ctx);
+/* Message of the last failed call on this context ("" if none). The string
+ * lives until the next call on the context. */
+const char* ising_last_error(const ising_ctx* ctx);
+int ising_set_stream(ising_ctx* ctx, void* stream);
+/* Wait for all work the context issued. */
+int ising_synchronize(ising_ctx* ctx);
+/* ABI version: major * 10000 + minor * 100 + patch. */
+int ising_version(void);
+
+/* ------------------------------------------------------------------ energy */
+
+/* E(s) (Sec. II) of `count` spin vectors spins[count][n] (int8, memory
+ * `mem`). Writes E_out[count] (float64) and, if Q_out / H_out are not NULL
+ * and the instance is integer, the exact parts Q = s^T J s and H = h^T s
+ * (int64, E = cQ Q + cH H). Integer couplings accumulate in integers and
+ * are exact; other couplings accumulate in FP64. Outputs are in memory
+ * `mem`. */
+int ising_energy(ising_ctx* ctx, const ising_instance* inst, const int8_t* spins,
+                 int64_t count, double* E_out, int64_t* Q_out, int64_t* H_out, int mem);
+
+/* ------------------------------------------------------------------ pruning */
+
+/* Algorithm 1 (Sec. III-A) on `inst`, rounds run until nothing changes:
+ * determined spins (strict rule, Eq. determined spin), then isolated spins
+ * with zero field if flags & 1 (ISING_PRUNE_ZERO_RULE, an extension), then
+ * semi-determined spins (Eq. semi determined spin) on what is left; fields
+ * fold in FP64 in row order, so decisions are reproducible bit for bit.
+ * The result (reduced instance, constant, record) lives on the device and
+ * is released by ising_prune_free. */
+#define ISING_PRUNE_ZERO_RULE 1
+int ising_prune(ising_ctx* ctx, const ising_instance* inst, int flags,
+                ising_prune_result** out);
+/* Sizes and scalars of a pruning result; any pointer may be NULL.
+ * constant: E(s) = E_reduced(s_G) + constant for the reconstructed s.
+ * eta: pruning rate 1 - n_reduced / n (Eq. pruning rate). */
+int ising_prune_info(const ising_prune_result* res, int64_t* n_reduced,
+                     int64_t* nnz_reduced, double* constant, double* eta,
+                     int32_t* rounds);
+/* The reduced instance: device pointers owned by `res` (valid until
+ * ising_prune_free), same layout, j_dtype, j_scale and convention as the
+ * input, h as float64. */
+int ising_prune_reduced(const ising_prune_result* res, ising_instance* out);
+/* Copies the reduced instance into caller buffers in memory `mem` (any may
+ * be NULL): J (dense n_reduced^2 or nnz_reduced values, input j_dtype),
+ * indptr (CSR, n_reduced + 1, int64), indices (CSR, nnz_reduced, int32),
+ * h (n_reduced, float64, in the input's convention). */
+int ising_prune_reduced_copy(const ising_prune_result* res, void* J, int64_t* indptr,
+                             int32_t* indices, double* h, int mem);
+/* The record of pruning, per original spin (arrays of n, memory `mem`, any
+ * may be NULL): kind 0 kept / 1 determined / 2 isolated-zero / 3 semi,
+ * round (0 if kept), value (+-1 for kinds 1 and 2), parent (kind 3),
+ * sign (kind 3: s = sign * s_parent), g_index (position in the reduced
+ * problem or -1). */
+int ising_prune_record(const ising_prune_result* res, int8_t* kind, int32_t* round,
+                       int8_t* value, int32_t* parent, int8_t* sign,
+                       int64_t* g_index, int mem);
+int ising_prune_free(ising_prune_result* res);
+/* Full spins (n) from the reduced problem's spins (n_reduced), both int8 in
+ * memory `mem`: kept spins copied, fixed spins set, semi-determined spins
+ * follow their parent chain. */
+int ising_reconstruct(ising_ctx* ctx, const ising_prune_result* res,
+                      const int8_t* reduced_spins, int8_t* full_spins, int mem);
+
+/* ------------------------------------------------------- domain selection */
+
+/* One-shot domain selection (Sec. III-B) on `inst`: B restarts x T steps,
+ * then the energy of the last rounded spins. Writes the best spins (n,
+ * int8) and energy over all steps and restarts (lowest energy, then lowest
+ * restart, then earliest step), in memory `mem`; stats may be NULL. */
+int ising_select_domain(ising_ctx* ctx, const ising_instance* inst,
+                        const ising_ds_params* p, int8_t* best_spins,
+                        double* best_energy, ising_ds_stats* stats, int mem);
+
+/* Full solve: pruning, domain selection on the reduced instance,
+ * reconstruction and the energy of the reconstructed spins on the full
+ * instance. prune_flags as ising_prune; best_spins has n entries. */
+int ising_solve(ising_ctx* ctx, const ising_instance* inst, const ising_ds_params* p,
+                int prune_flags, int8_t* best_spins, double* best_energy,
+                ising_ds_stats* stats, int mem);
+
+/* Session form of domain selection: create (uploads and converts J,
+ * initialises theta, m = v = 0, step 0), advance, inspect, destroy. */
+int ising_ds_create(ising_ctx* ctx, const ising_instance* inst,
+                    const ising_ds_params* p, ising_ds** out);
+/* Advance `steps` steps (stops at T). */
+int ising_ds_run(ising_ds* ds, int64_t steps);
+/* Evaluate the final spins (step T+1) and fill the result; idempotent. */
+int ising_ds_finish(ising_ds* ds);
+/* Current state, restart-major [B][n]: theta, m, v (float32), the spins
+ * s_{t+1} = sgn+(sin theta) the next step will use (int8), and t. Any pointer
+ * may be NULL. Memory `mem`. */
+int ising_ds_export_state(ising_ds* ds, float* theta, float* m, float* v,
+                          int8_t* spins, int64_t* t, int mem);
+/* Replace the state (theta, m, v restart-major, step counter t); the spins
+ * are re-derived from theta. Resets nothing else. */
+int ising_ds_import_state(ising_ds* ds, const float* theta, const float* m,
+                          const float* v, int64_t t, int mem);
+/* Energies E(s_t) of the spins consumed by the most recent step, [B]. */
+int ising_ds_last_energies(ising_ds* ds, double* E, int mem);
+/* Per-restart best so far: energy [B], step [B], spins [B][n] (any NULL). */
+int ising_ds_restart_best(ising_ds* ds, double* E, int64_t* step, int8_t* spins,
+                          int mem);
+/* Overall best (after ising_ds_finish, or the best so far). */
+int ising_ds_result(ising_ds* ds, int8_t* best_spins, double* best_energy,
+                    ising_ds_stats* stats, int mem);
+int ising_ds_destroy(ising_ds* ds);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ISING_DS_H */

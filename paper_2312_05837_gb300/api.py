@@ -1,0 +1,368 @@
+"""Python binding of the C ABI (include/ising_ds.h): argument marshalling only.
+
+Every function takes an instance object with the attributes ``n, layout, J,
+indptr, indices, data, h, j_scale, convention`` (numpy arrays for host memory,
+or torch CUDA tensors for device memory) and calls the matching ``ising_*``
+entry point. Nothing here computes any part of the method.
+"""
+
+from __future__ import annotations
+
+import ctypes
+from ctypes import byref, c_double, c_int32, c_int64, c_void_p
+
+import numpy as np
+
+from . import _lib as L
+
+_NP_DT = {np.dtype(np.float64): L.F64, np.dtype(np.float32): L.F32,
+          np.dtype(np.int8): L.I8, np.dtype(np.int32): L.I32}
+_PREC = {"auto": L.PREC_AUTO, "fp32": L.PREC_FP32_PLAIN, "plain": L.PREC_FP32_PLAIN,
+         "tc": L.PREC_TC, "bf16": L.PREC_BF16, "fp8": L.PREC_FP8}
+
+
+class IsingError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"ising error {code}: {msg}")
+        self.code = code
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _is_dev(x) -> bool:
+    return _is_torch(x) and x.is_cuda
+
+
+def _dtype_code(x) -> int:
+    if _is_torch(x):
+        t = _torch()
+        m = {t.float64: L.F64, t.float32: L.F32, t.int8: L.I8, t.int32: L.I32}
+        return m[x.dtype]
+    return _NP_DT[np.dtype(x.dtype)]
+
+
+def _ptr(x) -> int:
+    if x is None:
+        return 0
+    if _is_torch(x):
+        assert x.is_contiguous()
+        return x.data_ptr()
+    assert x.flags["C_CONTIGUOUS"]
+    return x.ctypes.data
+
+
+def _host(x, dtype=None):
+    if x is None:
+        return None
+    a = np.ascontiguousarray(x if dtype is None else np.asarray(x, dtype=dtype))
+    return a
+
+
+class Context:
+    """A library context on one CUDA device and stream (default: torch's
+    current stream on that device)."""
+
+    def __init__(self, device: int = 0, stream=None):
+        self.lib = L.load()
+        torch = _torch()
+        if stream is None:
+            stream = torch.cuda.current_stream(device).cuda_stream
+        elif hasattr(stream, "cuda_stream"):
+            stream = stream.cuda_stream
+        self.device = device
+        self.handle = c_void_p()
+        rc = self.lib.ising_create(byref(self.handle), device, c_void_p(stream))
+        if rc != L.OK:
+            raise IsingError(rc, "ising_create failed (no CUDA device?)")
+
+    def check(self, rc: int):
+        if rc != L.OK:
+            msg = self.lib.ising_last_error(self.handle)
+            raise IsingError(rc, msg.decode() if msg else "")
+
+    def synchronize(self):
+        self.check(self.lib.ising_synchronize(self.handle))
+
+    def close(self):
+        if self.handle:
+            self.lib.ising_destroy(self.handle)
+            self.handle = c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _conv(c) -> int:
+    return L.CONV_PAPER if c in ("paper", L.CONV_PAPER) else L.CONV_PHYSICS
+
+
+def make_instance(inst):
+    """ctypes ising_instance for `inst` plus the arrays it points into."""
+    keep = []
+    dense = inst.layout == "dense"
+    if dense:
+        J = inst.J
+    else:
+        J = inst.data
+    dev = _is_dev(J)
+    if not dev:
+        J = _host(J)
+    keep.append(J)
+    s = L.Instance()
+    s.n = int(inst.n)
+    s.layout = L.LAYOUT_DENSE if dense else L.LAYOUT_CSR
+    s.j_dtype = _dtype_code(J)
+    s.J = _ptr(J)
+    if not dense:
+        ip, ix = inst.indptr, inst.indices
+        if not dev:
+            ip = _host(ip, np.int64)
+            ix = _host(ix, np.int32)
+        keep += [ip, ix]
+        s.indptr = _ptr(ip)
+        s.indices = _ptr(ix)
+        s.nnz = int(ip[-1])
+    h = inst.h
+    if h is not None:
+        if not dev:
+            h = _host(h)
+            if h.dtype not in (np.float64, np.float32, np.int32):
+                h = h.astype(np.float64)
+        keep.append(h)
+        s.h_dtype = _dtype_code(h)
+        s.h = _ptr(h)
+    s.j_scale = float(inst.j_scale)
+    s.convention = _conv(inst.convention)
+    s.mem = L.MEM_DEVICE if dev else L.MEM_HOST
+    return s, keep
+
+
+def params(restarts, steps, lr=6.0, mu=0.0, beta1=0.9, beta2=0.999, eps=1e-8, seed=0,
+           precision="auto", profile=False) -> L.DSParams:
+    p = L.DSParams()
+    p.restarts = int(restarts)
+    p.steps = int(steps)
+    p.lr, p.mu, p.beta1, p.beta2, p.eps = float(lr), float(mu), float(beta1), float(beta2), float(eps)
+    p.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+    p.precision = _PREC[precision] if isinstance(precision, str) else int(precision)
+    p.flags = L.DS_PROFILE if profile else 0
+    return p
+
+
+def _stats_dict(st: L.DSStats) -> dict:
+    return {f: getattr(st, f) for f, _ in L.DSStats._fields_}
+
+
+def energy(ctx: Context, inst, spins, exact_parts: bool = False):
+    """E(s) for spins[count][n] (int8); returns float64 energies (and the
+    exact integer parts Q, H when asked)."""
+    s, keep = make_instance(inst)
+    dev = s.mem == L.MEM_DEVICE
+    if dev:
+        torch = _torch()
+        sp = spins.to(torch.int8).contiguous()
+        count = sp.shape[0] if sp.dim() == 2 else 1
+        E = torch.empty(count, dtype=torch.float64, device=sp.device)
+        Q = torch.empty(count, dtype=torch.int64, device=sp.device) if exact_parts else None
+        H = torch.empty(count, dtype=torch.int64, device=sp.device) if exact_parts else None
+    else:
+        sp = _host(spins, np.int8)
+        count = sp.shape[0] if sp.ndim == 2 else 1
+        E = np.empty(count, dtype=np.float64)
+        Q = np.empty(count, dtype=np.int64) if exact_parts else None
+        H = np.empty(count, dtype=np.int64) if exact_parts else None
+    ctx.check(ctx.lib.ising_energy(ctx.handle, byref(s), _ptr(sp), count, _ptr(E), _ptr(Q),
+                                   _ptr(H), L.MEM_DEVICE if dev else L.MEM_HOST))
+    return (E, Q, H) if exact_parts else E
+
+
+def _outputs(n, dev):
+    """Result buffers on the instance's side: (spins, energy, mem)."""
+    if dev:
+        torch = _torch()
+        return (torch.empty(n, dtype=torch.int8, device="cuda"),
+                torch.empty(1, dtype=torch.float64, device="cuda"), L.MEM_DEVICE)
+    return np.empty(n, dtype=np.int8), np.empty(1, dtype=np.float64), L.MEM_HOST
+
+
+def select_domain(ctx: Context, inst, restarts, steps, **kw):
+    """One-shot domain selection; returns best spins, energy and stats (on
+    the device when the instance is)."""
+    s, keep = make_instance(inst)
+    p = params(restarts, steps, **kw)
+    out, e, mem = _outputs(int(inst.n), s.mem == L.MEM_DEVICE)
+    st = L.DSStats()
+    ctx.check(ctx.lib.ising_select_domain(ctx.handle, byref(s), byref(p), _ptr(out),
+                                          ctypes.cast(_ptr(e), ctypes.POINTER(c_double)),
+                                          byref(st), mem))
+    return {"best_spins": out, "best_energy": e if mem == L.MEM_DEVICE else float(e[0]),
+            **_stats_dict(st)}
+
+
+def solve(ctx: Context, inst, restarts, steps, zero_rule=True, **kw):
+    """Pruning + domain selection + reconstruction + full-instance energy
+    (outputs on the device when the instance is)."""
+    s, keep = make_instance(inst)
+    p = params(restarts, steps, **kw)
+    out, e, mem = _outputs(int(inst.n), s.mem == L.MEM_DEVICE)
+    st = L.DSStats()
+    ctx.check(ctx.lib.ising_solve(ctx.handle, byref(s), byref(p),
+                                  L.PRUNE_ZERO_RULE if zero_rule else 0, _ptr(out),
+                                  ctypes.cast(_ptr(e), ctypes.POINTER(c_double)), byref(st), mem))
+    return {"best_spins": out, "best_energy": e if mem == L.MEM_DEVICE else float(e[0]),
+            **_stats_dict(st)}
+
+
+class Pruned:
+    """Result of ising_prune (owned by the library until close())."""
+
+    def __init__(self, ctx: Context, handle: c_void_p, src):
+        self.ctx = ctx
+        self.handle = handle
+        n_red, nnz_red, C, eta, rounds = c_int64(), c_int64(), c_double(), c_double(), c_int32()
+        ctx.check(ctx.lib.ising_prune_info(handle, byref(n_red), byref(nnz_red), byref(C),
+                                           byref(eta), byref(rounds)))
+        self.n = int(src.n)
+        self.n_reduced = n_red.value
+        self.nnz_reduced = nnz_red.value
+        self.constant = C.value
+        self.eta = eta.value
+        self.rounds = rounds.value
+        self._src = src
+
+    def record(self) -> dict:
+        n = self.n
+        kind = np.empty(n, np.int8)
+        rnd = np.empty(n, np.int32)
+        value = np.empty(n, np.int8)
+        parent = np.empty(n, np.int32)
+        sign = np.empty(n, np.int8)
+        gidx = np.empty(n, np.int64)
+        self.ctx.check(self.ctx.lib.ising_prune_record(self.handle, _ptr(kind), _ptr(rnd),
+                                                       _ptr(value), _ptr(parent), _ptr(sign),
+                                                       _ptr(gidx), L.MEM_HOST))
+        return dict(kind=kind, round=rnd, value=value, parent=parent, sign=sign, g_index=gidx)
+
+    def reduced(self):
+        """Reduced instance copied to host numpy arrays (same attributes as the input)."""
+        from types import SimpleNamespace
+        src = self._src
+        dense = src.layout == "dense"
+        jd = np.asarray(src.J if dense else src.data)
+        if _is_torch(jd):
+            jd = jd.cpu().numpy()
+        nr, nz = self.n_reduced, self.nnz_reduced
+        J = np.empty(nr * nr if dense else nz, dtype=jd.dtype)
+        ip = None if dense else np.empty(nr + 1, np.int64)
+        ix = None if dense else np.empty(nz, np.int32)
+        h = np.empty(nr, np.float64)
+        self.ctx.check(self.ctx.lib.ising_prune_reduced_copy(self.handle, _ptr(J), _ptr(ip),
+                                                             _ptr(ix), _ptr(h), L.MEM_HOST))
+        return SimpleNamespace(n=nr, layout=src.layout, J=J.reshape(nr, nr) if dense else None,
+                               indptr=ip, indices=ix, data=None if dense else J, h=h,
+                               j_scale=src.j_scale, convention=src.convention)
+
+    def reconstruct(self, reduced_spins) -> np.ndarray:
+        sg = _host(reduced_spins, np.int8)
+        out = np.empty(self.n, np.int8)
+        self.ctx.check(self.ctx.lib.ising_reconstruct(self.ctx.handle, self.handle, _ptr(sg),
+                                                      _ptr(out), L.MEM_HOST))
+        return out
+
+    def close(self):
+        if self.handle:
+            self.ctx.lib.ising_prune_free(self.handle)
+            self.handle = c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def prune(ctx: Context, inst, zero_rule: bool = True) -> Pruned:
+    s, keep = make_instance(inst)
+    h = c_void_p()
+    ctx.check(ctx.lib.ising_prune(ctx.handle, byref(s), L.PRUNE_ZERO_RULE if zero_rule else 0,
+                                  byref(h)))
+    return Pruned(ctx, h, inst)
+
+
+class Session:
+    """ising_ds_* session: create, run, inspect, finish."""
+
+    def __init__(self, ctx: Context, inst, restarts, steps, **kw):
+        self.ctx = ctx
+        s, keep = make_instance(inst)
+        self.p = params(restarts, steps, **kw)
+        self.n = int(inst.n)
+        self.B = int(restarts)
+        self.handle = c_void_p()
+        ctx.check(ctx.lib.ising_ds_create(ctx.handle, byref(s), byref(self.p), byref(self.handle)))
+
+    def run(self, steps: int):
+        self.ctx.check(self.ctx.lib.ising_ds_run(self.handle, int(steps)))
+
+    def finish(self):
+        self.ctx.check(self.ctx.lib.ising_ds_finish(self.handle))
+
+    def export_state(self):
+        B, n = self.B, self.n
+        th = np.empty((B, n), np.float32)
+        m = np.empty((B, n), np.float32)
+        v = np.empty((B, n), np.float32)
+        sp = np.empty((B, n), np.int8)
+        t = c_int64()
+        self.ctx.check(self.ctx.lib.ising_ds_export_state(self.handle, _ptr(th), _ptr(m), _ptr(v),
+                                                          _ptr(sp), byref(t), L.MEM_HOST))
+        return dict(theta=th, m=m, v=v, spins=sp, t=t.value)
+
+    def import_state(self, theta, m, v, t: int):
+        th = _host(theta, np.float32)
+        mm = _host(m, np.float32)
+        vv = _host(v, np.float32)
+        self.ctx.check(self.ctx.lib.ising_ds_import_state(self.handle, _ptr(th), _ptr(mm),
+                                                          _ptr(vv), int(t), L.MEM_HOST))
+
+    def last_energies(self) -> np.ndarray:
+        E = np.empty(self.B, np.float64)
+        self.ctx.check(self.ctx.lib.ising_ds_last_energies(self.handle, _ptr(E), L.MEM_HOST))
+        return E
+
+    def restart_best(self):
+        E = np.empty(self.B, np.float64)
+        st = np.empty(self.B, np.int64)
+        sp = np.empty((self.B, self.n), np.int8)
+        self.ctx.check(self.ctx.lib.ising_ds_restart_best(self.handle, _ptr(E), _ptr(st),
+                                                          _ptr(sp), L.MEM_HOST))
+        return E, st, sp
+
+    def result(self):
+        out = np.empty(self.n, np.int8)
+        e = c_double()
+        st = L.DSStats()
+        self.ctx.check(self.ctx.lib.ising_ds_result(self.handle, _ptr(out), byref(e), byref(st),
+                                                    L.MEM_HOST))
+        return {"best_spins": out, "best_energy": e.value, **_stats_dict(st)}
+
+    def close(self):
+        if self.handle:
+            self.ctx.lib.ising_ds_destroy(self.handle)
+            self.handle = c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

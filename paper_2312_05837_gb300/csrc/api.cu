@@ -1,0 +1,143 @@
+// Context management, the energy call (K3) and the full solve
+// (pruning -> domain selection -> reconstruction -> energy).
+#include "common.cuh"
+
+#include <algorithm>
+
+using namespace ising;
+
+extern "C" int ising_version(void) { return 10000; }
+
+extern "C" int ising_create(ising_ctx** out, int device, void* stream) {
+  if (!out) return ISING_EINVAL;
+  *out = nullptr;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+    cudaGetLastError();
+    return ISING_ECUDA;
+  }
+  if (cudaSetDevice(device) != cudaSuccess) return ISING_ECUDA;
+  auto ctx = new ising_ctx();
+  ctx->device = device;
+  ctx->stream = static_cast<cudaStream_t>(stream);
+  int sms = 0, optin = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+  ctx->sm_count = std::max(sms, 1);
+  ctx->smem_optin = (size_t)optin;
+  *out = ctx;
+  return ISING_OK;
+}
+
+extern "C" int ising_destroy(ising_ctx* ctx) {
+  if (!ctx) return ISING_OK;
+  cudaStreamSynchronize(ctx->stream);
+  delete ctx;
+  return ISING_OK;
+}
+
+extern "C" const char* ising_last_error(const ising_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : "null context";
+}
+
+extern "C" int ising_set_stream(ising_ctx* ctx, void* stream) {
+  if (!ctx) return ISING_EINVAL;
+  ctx->stream = static_cast<cudaStream_t>(stream);
+  return ISING_OK;
+}
+
+extern "C" int ising_synchronize(ising_ctx* ctx) {
+  if (!ctx) return ISING_EINVAL;
+  ISING_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return ISING_OK;
+}
+
+extern "C" int ising_energy(ising_ctx* ctx, const ising_instance* inst, const int8_t* spins,
+                            int64_t count, double* E_out, int64_t* Q_out, int64_t* H_out,
+                            int mem) {
+  if (!ctx) return ISING_EINVAL;
+  if (count < 0) return fail(ctx, ISING_EINVAL, "count must be >= 0");
+  if (count > 0 && (!spins || !E_out)) return fail(ctx, ISING_EINVAL, "spins and E_out are required");
+  if (mem != ISING_MEM_HOST && mem != ISING_MEM_DEVICE) return fail(ctx, ISING_EINVAL, "bad mem");
+  ISING_CUDA(ctx, cudaSetDevice(ctx->device));
+  DevInstance I;
+  ISING_TRY(upload_instance(ctx, inst, &I));
+  const bool exact = I.j_integer && I.j_absmax < 2147483648.0 && I.h_dyadic;
+  if ((Q_out || H_out) && !exact)
+    return fail(ctx, ISING_EINVAL, "Q/H outputs need an integer instance");
+  if (H_out && I.h_shift != 0) return fail(ctx, ISING_EINVAL, "H output needs an integer h");
+  if (count == 0) return ISING_OK;
+  cudaStream_t st = ctx->stream;
+  const int64_t n = I.n;
+  DevMem s, E, Q, H;
+  const int8_t* sp = spins;
+  if (mem == ISING_MEM_HOST) {
+    ISING_TRY(dev_alloc(ctx, s, (size_t)count * n));
+    ISING_CUDA(ctx, cudaMemcpyAsync(s.p, spins, (size_t)count * n, cudaMemcpyHostToDevice, st));
+    sp = s.as<int8_t>();
+  }
+  ISING_TRY(dev_alloc(ctx, E, count * 8));
+  ISING_TRY(dev_alloc(ctx, Q, count * 8));
+  ISING_TRY(dev_alloc(ctx, H, count * 8));
+  for (int64_t c0 = 0; c0 < count; c0 += 65535) {
+    int64_t c = std::min<int64_t>(65535, count - c0);
+    ISING_TRY(energy_device(ctx, I, sp + c0 * n, c, E.as<double>() + c0,
+                            exact ? Q.as<int64_t>() + c0 : nullptr,
+                            exact ? H.as<int64_t>() + c0 : nullptr));
+  }
+  cudaMemcpyKind k = mem == ISING_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  ISING_CUDA(ctx, cudaMemcpyAsync(E_out, E.p, count * 8, k, st));
+  if (Q_out) ISING_CUDA(ctx, cudaMemcpyAsync(Q_out, Q.p, count * 8, k, st));
+  if (H_out) ISING_CUDA(ctx, cudaMemcpyAsync(H_out, H.p, count * 8, k, st));
+  ISING_CUDA(ctx, cudaStreamSynchronize(st));
+  return ISING_OK;
+}
+
+extern "C" int ising_solve(ising_ctx* ctx, const ising_instance* inst, const ising_ds_params* p,
+                           int prune_flags, int8_t* best_spins, double* best_energy,
+                           ising_ds_stats* stats, int mem) {
+  if (!ctx) return ISING_EINVAL;
+  if (!inst) return fail(ctx, ISING_EINVAL, "instance is NULL");
+  if (mem != ISING_MEM_HOST && mem != ISING_MEM_DEVICE) return fail(ctx, ISING_EINVAL, "bad mem");
+  cudaStream_t st = ctx->stream;
+  ising_prune_result* pr = nullptr;
+  ISING_TRY(ising_prune(ctx, inst, prune_flags, &pr));
+  int64_t nG = 0;
+  ising_prune_info(pr, &nG, nullptr, nullptr, nullptr, nullptr);
+  const int64_t n = inst->n;
+  int rc = ISING_OK;
+  DevMem sG, full, E;
+  ising_ds_stats ds_stats{};
+  do {
+    if ((rc = dev_alloc(ctx, sG, std::max<int64_t>(nG, 1))) != ISING_OK) break;
+    if ((rc = dev_alloc(ctx, full, n)) != ISING_OK) break;
+    if ((rc = dev_alloc(ctx, E, 8)) != ISING_OK) break;
+    if (nG > 0) {
+      ising_instance red;
+      ising_prune_reduced(pr, &red);
+      double eg = 0.0;
+      rc = ising_select_domain(ctx, &red, p, sG.as<int8_t>(), &eg, &ds_stats, ISING_MEM_DEVICE);
+      if (rc != ISING_OK) break;
+    }
+    rc = ising_reconstruct(ctx, pr, sG.as<int8_t>(), full.as<int8_t>(), ISING_MEM_DEVICE);
+    if (rc != ISING_OK) break;
+    // the energy of the reconstructed spins on the full instance
+    ising_instance src = *inst;
+    rc = ising_energy(ctx, &src, full.as<int8_t>(), 1, E.as<double>(), nullptr, nullptr,
+                      ISING_MEM_DEVICE);
+    if (rc != ISING_OK) break;
+    cudaMemcpyKind k = mem == ISING_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    if (best_spins) {
+      cudaError_t e = cudaMemcpyAsync(best_spins, full.p, n, k, st);
+      if (e != cudaSuccess) { rc = fail(ctx, ISING_ECUDA, "copy of spins failed"); break; }
+    }
+    if (best_energy) {
+      cudaError_t e = cudaMemcpyAsync(best_energy, E.p, 8, k, st);
+      if (e != cudaSuccess) { rc = fail(ctx, ISING_ECUDA, "copy of energy failed"); break; }
+    }
+    cudaStreamSynchronize(st);
+    if (stats) *stats = ds_stats;
+  } while (0);
+  ising_prune_free(pr);
+  return rc;
+}

@@ -1,0 +1,762 @@
+// Domain selection (Sec. III-B): session management shared by every path,
+// initialisation theta = asin(x0), best tracking per restart (K4 part 1),
+// best-of-restarts reduction (K4 part 2) and the public C ABI calls.
+#include "ds_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <limits>
+
+using namespace ising;
+
+namespace ising {
+namespace {
+
+// theta_0 = asin(x0), x0 = SplitMix64(seed, (b << 32) | i) mapped to [-1, 1);
+// m = v = 0; S_1 = sgn+(x0). Dense state is [Bp][ld] restart-major, sparse
+// state [n][Bp].
+template <int KIND>
+__global__ void init_kernel(int64_t n, int64_t Bp, int64_t ld, bool spin_major, uint64_t seed,
+                            float* __restrict__ theta, float* __restrict__ m,
+                            float* __restrict__ v, void* __restrict__ spins) {
+  const int64_t total = spin_major ? n * Bp : Bp * ld;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t b, i;
+    if (spin_major) { i = e / Bp; b = e - i * Bp; } else { b = e / ld; i = e - b * ld; }
+    float th = 0.0f;
+    bool pos = true;
+    bool pad = i >= n;
+    if (!pad) {
+      uint64_t z = splitmix64(seed, ((uint64_t)b << 32) | (uint64_t)i);
+      double x0 = 2.0 * ((double)(z >> 11) * 0x1.0p-53) - 1.0;
+      th = (float)asin(x0);
+      pos = x0 >= 0.0;
+    }
+    theta[e] = th;
+    m[e] = 0.0f;
+    v[e] = 0.0f;
+    if (KIND == kSpinF32) {
+      static_cast<float*>(spins)[e] = pad ? 0.0f : (pos ? 1.0f : -1.0f);
+    } else if (KIND == kSpinBF16) {
+      static_cast<__nv_bfloat16*>(spins)[e] = __float2bfloat16(pad ? 0.0f : (pos ? 1.0f : -1.0f));
+    } else if (KIND == kSpinE4M3) {
+      // E4M3: +1 = 0x38, -1 = 0xB8, 0 = 0x00
+      static_cast<uint8_t*>(spins)[e] = pad ? 0 : (pos ? 0x38 : 0xB8);
+    }
+  }
+}
+
+// Bit-packed spins for the sparse path: word w of spin i holds restarts
+// 32w .. 32w+31, bit set = +1.
+__global__ void init_bits_kernel(int64_t n, int64_t Bp, uint64_t seed,
+                                 uint32_t* __restrict__ bits) {
+  const int64_t words = Bp / 32;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * words;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = e / words, w = e - i * words;
+    uint32_t word = 0;
+    for (int r = 0; r < 32; ++r) {
+      uint64_t b = (uint64_t)(w * 32 + r);
+      uint64_t z = splitmix64(seed, (b << 32) | (uint64_t)i);
+      double x0 = 2.0 * ((double)(z >> 11) * 0x1.0p-53) - 1.0;
+      if (x0 >= 0.0) word |= 1u << r;
+    }
+    bits[e] = word;
+  }
+}
+
+template <int KIND>
+__device__ __forceinline__ int8_t spin_at(const void* spins, int64_t n, int64_t Bp, int64_t ld,
+                                          int64_t b, int64_t i) {
+  if (KIND == kSpinF32) return static_cast<const float*>(spins)[b * ld + i] > 0.0f ? 1 : -1;
+  if (KIND == kSpinBF16)
+    return __bfloat162float(static_cast<const __nv_bfloat16*>(spins)[b * ld + i]) > 0.0f ? 1 : -1;
+  if (KIND == kSpinE4M3) return static_cast<const uint8_t*>(spins)[b * ld + i] == 0x38 ? 1 : -1;
+  const uint32_t w = static_cast<const uint32_t*>(spins)[i * (Bp / 32) + (b >> 5)];
+  return (w >> (b & 31)) & 1u ? 1 : -1;
+}
+
+// Best tracking for step t = counters[0] + 1: E_t(b) from the partials of
+// slot t % 2 (added in tile order), strict < against the best so far, copy
+// of S_t for improved restarts, then the last block advances the counter.
+template <int KIND>
+__global__ void __launch_bounds__(256) track_kernel(
+    int64_t n, int64_t B, int64_t Bp, int64_t ld, int mtiles, bool int_mode, double cq,
+    double chs, const long long* __restrict__ qpart, const long long* __restrict__ hpart,
+    const float* __restrict__ epart, const void* __restrict__ spins_t,
+    double* __restrict__ best_E, long long* __restrict__ best_t, int8_t* __restrict__ best_s,
+    double* __restrict__ last_E, long long* __restrict__ counters) {
+  __shared__ int improved;
+  const long long t = counters[0] + 1;
+  for (int64_t b = blockIdx.x; b < B; b += gridDim.x) {
+    if (threadIdx.x == 0) {
+      double E;
+      if (int_mode) {
+        long long q = 0, hs = 0;
+        for (int r = 0; r < mtiles; ++r) {
+          q += qpart[(int64_t)r * Bp + b];
+          hs += hpart[(int64_t)r * Bp + b];
+        }
+        E = cq * (double)q + chs * (double)hs;
+      } else {
+        double e = 0.0;
+        for (int r = 0; r < mtiles; ++r) e += (double)epart[(int64_t)r * Bp + b];
+        E = e;
+      }
+      last_E[b] = E;
+      improved = E < best_E[b];
+      if (improved) {
+        best_E[b] = E;
+        best_t[b] = t;
+      }
+    }
+    __syncthreads();
+    if (improved)
+      for (int64_t i = threadIdx.x; i < n; i += blockDim.x)
+        best_s[b * n + i] = spin_at<KIND>(spins_t, n, Bp, ld, b, i);
+    __syncthreads();
+  }
+  __shared__ bool last;
+  __threadfence();
+  if (threadIdx.x == 0) {
+    unsigned long long prev = atomicAdd(reinterpret_cast<unsigned long long*>(&counters[1]), 1ull);
+    last = prev == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    counters[0] = t;
+    counters[1] = 0;
+    __threadfence();
+  }
+}
+
+template <int KIND>
+__global__ void export_spins_kernel(int64_t n, int64_t B, int64_t Bp, int64_t ld,
+                                    const void* __restrict__ spins, int8_t* __restrict__ out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < B * n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t b = e / n, i = e - b * n;
+    out[e] = spin_at<KIND>(spins, n, Bp, ld, b, i);
+  }
+}
+
+// [n][Bp] <-> [B][n] transposes for the sparse path's state.
+__global__ void spin_major_to_restart_major(int64_t n, int64_t B, int64_t Bp,
+                                            const float* __restrict__ in, float* __restrict__ out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < B * n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t b = e / n, i = e - b * n;
+    out[e] = in[i * Bp + b];
+  }
+}
+
+__global__ void restart_major_to_spin_major(int64_t n, int64_t B, int64_t Bp,
+                                            const float* __restrict__ in, float* __restrict__ out,
+                                            bool wrap) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < B * n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t b = e / n, i = e - b * n;
+    float x = in[e];
+    out[i * Bp + b] = wrap ? wrap_angle(x) : x;
+  }
+}
+
+__global__ void wrap_rows_kernel(int64_t n, int64_t B, int64_t ld, float* __restrict__ th) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < B * n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t b = e / n, i = e - b * n;
+    th[b * ld + i] = wrap_angle(th[b * ld + i]);
+  }
+}
+
+// Spins from theta (restart-major dense state) into a spin slot.
+template <int KIND>
+__global__ void spins_from_theta_dense(int64_t n, int64_t Bp, int64_t ld,
+                                       const float* __restrict__ th, void* __restrict__ spins) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < Bp * ld;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = e % ld;
+    bool pad = i >= n;
+    bool pos = sin_nonneg(th[e]);
+    if (KIND == kSpinF32) static_cast<float*>(spins)[e] = pad ? 0.f : (pos ? 1.f : -1.f);
+    if (KIND == kSpinBF16)
+      static_cast<__nv_bfloat16*>(spins)[e] = __float2bfloat16(pad ? 0.f : (pos ? 1.f : -1.f));
+    if (KIND == kSpinE4M3) static_cast<uint8_t*>(spins)[e] = pad ? 0 : (pos ? 0x38 : 0xB8);
+  }
+}
+
+__global__ void spins_from_theta_bits(int64_t n, int64_t Bp, const float* __restrict__ th,
+                                      uint32_t* __restrict__ bits) {
+  const int64_t words = Bp / 32;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * words;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = e / words, w = e - i * words;
+    uint32_t word = 0;
+    for (int r = 0; r < 32; ++r)
+      if (sin_nonneg(th[i * Bp + w * 32 + r])) word |= 1u << r;
+    bits[e] = word;
+  }
+}
+
+__global__ void fill_double(double* p, int64_t count, double x) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count;
+       e += (int64_t)gridDim.x * blockDim.x)
+    p[e] = x;
+}
+
+// K4: lowest (energy, restart) over B restarts; one block, fixed reduction tree.
+__global__ void __launch_bounds__(1024) argmin_kernel(int64_t B, const double* __restrict__ E,
+                                                      long long* __restrict__ out) {
+  __shared__ double se[1024];
+  __shared__ long long sb[1024];
+  double be = INFINITY;
+  long long bb = -1;
+  for (int64_t b = threadIdx.x; b < B; b += blockDim.x) {
+    double e = E[b];
+    if (bb < 0 || e < be) { be = e; bb = b; }
+  }
+  se[threadIdx.x] = be;
+  sb[threadIdx.x] = bb;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      double e2 = se[threadIdx.x + s];
+      long long b2 = sb[threadIdx.x + s];
+      if (b2 >= 0 && (sb[threadIdx.x] < 0 || e2 < se[threadIdx.x] ||
+                      (e2 == se[threadIdx.x] && b2 < sb[threadIdx.x]))) {
+        se[threadIdx.x] = e2;
+        sb[threadIdx.x] = b2;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = sb[0];
+}
+
+int grid1d(ising_ctx* ctx, int64_t work) {
+  int64_t g = (work + 255) / 256;
+  int64_t cap = (int64_t)std::max(ctx->sm_count, 1) * 16;
+  return (int)std::max<int64_t>(1, std::min(g, cap));
+}
+
+int check_params(ising_ctx* ctx, const ising_ds_params* p) {
+  if (!p) return fail(ctx, ISING_EINVAL, "params is NULL");
+  if (p->restarts < 1 || p->restarts > (1 << 20))
+    return fail(ctx, ISING_EINVAL, "restarts must be in [1, 2^20]");
+  if (p->steps < 0) return fail(ctx, ISING_EINVAL, "steps must be >= 0");
+  if (!std::isfinite(p->lr) || p->lr < 0) return fail(ctx, ISING_EINVAL, "lr must be finite and >= 0");
+  if (!std::isfinite(p->mu) || p->mu < 0) return fail(ctx, ISING_EINVAL, "mu must be finite and >= 0");
+  if (!(p->beta1 >= 0 && p->beta1 < 1) || !(p->beta2 >= 0 && p->beta2 < 1))
+    return fail(ctx, ISING_EINVAL, "beta1 and beta2 must lie in [0, 1)");
+  if (!(p->eps > 0) || !std::isfinite(p->eps)) return fail(ctx, ISING_EINVAL, "eps must be > 0");
+  if (p->flags & ~ISING_DS_PROFILE) return fail(ctx, ISING_EINVAL, "unknown flags");
+  if (p->precision < ISING_PREC_AUTO || p->precision > ISING_PREC_FP8)
+    return fail(ctx, ISING_EINVAL, "unknown precision %d", p->precision);
+  return ISING_OK;
+}
+
+}  // namespace
+
+int track_step(ising_ds* ds) {
+  ising_ctx* ctx = ds->ctx;
+  const int slot = (int)((ds->t + 1) % 3);
+  const int pslot = (int)((ds->t + 1) % 2);
+  const double chs = ds->inst.ch * std::ldexp(1.0, -ds->h_shift);
+  int grid = (int)std::min<int64_t>(ds->B, (int64_t)ctx->sm_count * 4);
+#define ISING_TRACK(KIND)                                                                    \
+  track_kernel<KIND><<<grid, 256, 0, ctx->stream>>>(                                         \
+      ds->n, ds->B, ds->Bp, ds->ld, ds->mtiles, ds->int_energy, ds->inst.cq, chs,            \
+      ds->qpart[pslot].as<long long>(), ds->hpart[pslot].as<long long>(),                    \
+      ds->epart[pslot].as<float>(), ds->spins[slot].p, ds->best_E.as<double>(),              \
+      ds->best_t.as<long long>(), ds->best_s.as<int8_t>(), ds->last_E.as<double>(),          \
+      ds->counters.as<long long>())
+  switch (ds->spin_kind) {
+    case kSpinF32: ISING_TRACK(kSpinF32); break;
+    case kSpinBF16: ISING_TRACK(kSpinBF16); break;
+    case kSpinE4M3: ISING_TRACK(kSpinE4M3); break;
+    default: ISING_TRACK(kSpinBits); break;
+  }
+#undef ISING_TRACK
+  ISING_CUDA(ctx, cudaGetLastError());
+  return ISING_OK;
+}
+
+int export_spins_int8(ising_ds* ds, int slot, int8_t* out) {
+  ising_ctx* ctx = ds->ctx;
+  int g = grid1d(ctx, ds->B * ds->n);
+  const void* sp = ds->spins[slot].p;
+  switch (ds->spin_kind) {
+    case kSpinF32: export_spins_kernel<kSpinF32><<<g, 256, 0, ctx->stream>>>(ds->n, ds->B, ds->Bp, ds->ld, sp, out); break;
+    case kSpinBF16: export_spins_kernel<kSpinBF16><<<g, 256, 0, ctx->stream>>>(ds->n, ds->B, ds->Bp, ds->ld, sp, out); break;
+    case kSpinE4M3: export_spins_kernel<kSpinE4M3><<<g, 256, 0, ctx->stream>>>(ds->n, ds->B, ds->Bp, ds->ld, sp, out); break;
+    default: export_spins_kernel<kSpinBits><<<g, 256, 0, ctx->stream>>>(ds->n, ds->B, ds->Bp, ds->ld, sp, out); break;
+  }
+  ISING_CUDA(ctx, cudaGetLastError());
+  return ISING_OK;
+}
+
+namespace {
+
+int init_state(ising_ds* ds) {
+  ising_ctx* ctx = ds->ctx;
+  const bool spin_major = ds->path == ISING_PATH_SPARSE;
+  const int64_t elems = spin_major ? ds->n * ds->Bp : ds->Bp * ds->ld;
+  ISING_TRY(dev_alloc(ctx, ds->theta, elems * 4));
+  ISING_TRY(dev_alloc(ctx, ds->m, elems * 4));
+  ISING_TRY(dev_alloc(ctx, ds->v, elems * 4));
+  size_t spin_bytes;
+  switch (ds->spin_kind) {
+    case kSpinF32: spin_bytes = elems * 4; break;
+    case kSpinBF16: spin_bytes = elems * 2; break;
+    case kSpinE4M3: spin_bytes = elems; break;
+    default: spin_bytes = ds->n * (ds->Bp / 32) * 4; break;
+  }
+  for (auto& s : ds->spins) {
+    ISING_TRY(dev_alloc(ctx, s, spin_bytes));
+    ISING_CUDA(ctx, cudaMemsetAsync(s.p, 0, spin_bytes, ctx->stream));
+  }
+  const int slot1 = 1;  // S_1 lives in spins[1 % 3]
+  int g = grid1d(ctx, elems);
+  float* th = ds->theta.as<float>();
+  float* mm = ds->m.as<float>();
+  float* vv = ds->v.as<float>();
+  void* s1 = ds->spins[slot1].p;
+  uint64_t seed = ds->p.seed;
+  switch (ds->spin_kind) {
+    case kSpinF32: init_kernel<kSpinF32><<<g, 256, 0, ctx->stream>>>(ds->n, ds->Bp, ds->ld, false, seed, th, mm, vv, s1); break;
+    case kSpinBF16: init_kernel<kSpinBF16><<<g, 256, 0, ctx->stream>>>(ds->n, ds->Bp, ds->ld, false, seed, th, mm, vv, s1); break;
+    case kSpinE4M3: init_kernel<kSpinE4M3><<<g, 256, 0, ctx->stream>>>(ds->n, ds->Bp, ds->ld, false, seed, th, mm, vv, s1); break;
+    default:
+      init_kernel<kSpinBits><<<g, 256, 0, ctx->stream>>>(ds->n, ds->Bp, ds->ld, true, seed, th, mm, vv, nullptr);
+      init_bits_kernel<<<grid1d(ctx, ds->n * ds->Bp / 32), 256, 0, ctx->stream>>>(
+          ds->n, ds->Bp, seed, ds->spins[slot1].as<uint32_t>());
+      break;
+  }
+  ISING_CUDA(ctx, cudaGetLastError());
+  return ISING_OK;
+}
+
+int common_alloc(ising_ds* ds) {
+  ising_ctx* ctx = ds->ctx;
+  const int64_t B = ds->B, n = ds->n;
+  for (int s = 0; s < 2; ++s) {
+    ISING_TRY(dev_alloc(ctx, ds->qpart[s], (size_t)ds->mtiles * ds->Bp * 8));
+    ISING_TRY(dev_alloc(ctx, ds->hpart[s], (size_t)ds->mtiles * ds->Bp * 8));
+    ISING_TRY(dev_alloc(ctx, ds->epart[s], (size_t)ds->mtiles * ds->Bp * 4));
+    ISING_CUDA(ctx, cudaMemsetAsync(ds->hpart[s].p, 0, ds->hpart[s].bytes, ctx->stream));
+  }
+  ISING_TRY(dev_alloc(ctx, ds->best_E, B * 8));
+  ISING_TRY(dev_alloc(ctx, ds->best_t, B * 8));
+  ISING_TRY(dev_alloc(ctx, ds->best_s, (size_t)B * n));
+  ISING_TRY(dev_alloc(ctx, ds->last_E, B * 8));
+  ISING_TRY(dev_alloc(ctx, ds->counters, 16));
+  ISING_TRY(dev_alloc(ctx, ds->scratch, 64));
+  fill_double<<<grid1d(ctx, B), 256, 0, ctx->stream>>>(ds->best_E.as<double>(), B, INFINITY);
+  fill_double<<<grid1d(ctx, B), 256, 0, ctx->stream>>>(ds->last_E.as<double>(), B, INFINITY);
+  ISING_CUDA(ctx, cudaGetLastError());
+  ISING_CUDA(ctx, cudaMemsetAsync(ds->best_t.p, 0, B * 8, ctx->stream));
+  ISING_CUDA(ctx, cudaMemsetAsync(ds->best_s.p, 0, (size_t)B * n, ctx->stream));
+  ISING_CUDA(ctx, cudaMemsetAsync(ds->counters.p, 0, 16, ctx->stream));
+  // Adam bias corrections for t = 0 .. T + 1 (entry 0 unused)
+  std::vector<float> bias((size_t)(ds->T + 2) * 2);
+  for (int64_t t = 1; t <= ds->T + 1; ++t) {
+    bias[2 * t] = (float)(1.0 / (1.0 - std::pow(ds->p.beta1, (double)t)));
+    bias[2 * t + 1] = (float)(1.0 / (1.0 - std::pow(ds->p.beta2, (double)t)));
+  }
+  bias[0] = bias[1] = 1.0f;
+  ISING_TRY(dev_alloc(ctx, ds->bias, bias.size() * 4));
+  ISING_CUDA(ctx, cudaMemcpyAsync(ds->bias.p, bias.data(), bias.size() * 4,
+                                  cudaMemcpyHostToDevice, ctx->stream));
+  ISING_CUDA(ctx, cudaStreamSynchronize(ctx->stream));  // `bias` is a host temporary
+  return ISING_OK;
+}
+
+int setup_field(ising_ds* ds) {
+  ising_ctx* ctx = ds->ctx;
+  const int64_t n = ds->n;
+  ISING_TRY(dev_alloc(ctx, ds->hf, n * 4));
+  ISING_TRY(dev_alloc(ctx, ds->hint, n * 4));
+  ISING_CUDA(ctx, cudaMemsetAsync(ds->hf.p, 0, n * 4, ctx->stream));
+  ISING_CUDA(ctx, cudaMemsetAsync(ds->hint.p, 0, n * 4, ctx->stream));
+  if (!ds->inst.has_h) return ISING_OK;
+  std::vector<double> h(n);
+  size_t es = dtype_size(ds->inst.h_dtype);
+  std::vector<unsigned char> raw(n * es);
+  ISING_CUDA(ctx, cudaMemcpyAsync(raw.data(), ds->inst.h.p, n * es, cudaMemcpyDeviceToHost, ctx->stream));
+  ISING_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  for (int64_t i = 0; i < n; ++i) {
+    switch (ds->inst.h_dtype) {
+      case ISING_F64: h[i] = reinterpret_cast<double*>(raw.data())[i]; break;
+      case ISING_F32: h[i] = reinterpret_cast<float*>(raw.data())[i]; break;
+      default: h[i] = reinterpret_cast<int32_t*>(raw.data())[i]; break;
+    }
+  }
+  std::vector<float> hf(n);
+  std::vector<int32_t> hi(n);
+  for (int64_t i = 0; i < n; ++i) {
+    hf[i] = (float)h[i];
+    hi[i] = ds->int_energy ? (int32_t)std::llrint(std::ldexp(h[i], ds->h_shift)) : 0;
+  }
+  ISING_CUDA(ctx, cudaMemcpyAsync(ds->hf.p, hf.data(), n * 4, cudaMemcpyHostToDevice, ctx->stream));
+  ISING_CUDA(ctx, cudaMemcpyAsync(ds->hint.p, hi.data(), n * 4, cudaMemcpyHostToDevice, ctx->stream));
+  ISING_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return ISING_OK;
+}
+
+int path_step_raw(ising_ds* ds, bool update) {
+  switch (ds->path) {
+    case ISING_PATH_PLAIN: return plain_step(ds, update);
+    case ISING_PATH_SPARSE: return sparse_step(ds, update);
+    default: return tc_step(ds, update);
+  }
+}
+
+// One step kernel; with ISING_DS_PROFILE its device time is measured by a
+// pair of events on the launching stream.
+int path_step(ising_ds* ds, bool update) {
+  if (!(ds->p.flags & ISING_DS_PROFILE)) return path_step_raw(ds, update);
+  ising_ctx* ctx = ds->ctx;
+  if (!ds->kev[0]) {
+    ISING_CUDA(ctx, cudaEventCreate(&ds->kev[0]));
+    ISING_CUDA(ctx, cudaEventCreate(&ds->kev[1]));
+  }
+  ISING_CUDA(ctx, cudaEventRecord(ds->kev[0], ctx->stream));
+  ISING_TRY(path_step_raw(ds, update));
+  ISING_CUDA(ctx, cudaEventRecord(ds->kev[1], ctx->stream));
+  ISING_CUDA(ctx, cudaEventSynchronize(ds->kev[1]));
+  float ms = 0.f;
+  ISING_CUDA(ctx, cudaEventElapsedTime(&ms, ds->kev[0], ds->kev[1]));
+  ds->kernel_ms += ms;
+  ds->kernel_launches += 1;
+  return ISING_OK;
+}
+
+int copy_out(ising_ctx* ctx, void* dst, const void* src, size_t bytes, int mem) {
+  if (bytes == 0) return ISING_OK;
+  ISING_CUDA(ctx, cudaMemcpyAsync(dst, src, bytes,
+                                  mem == ISING_MEM_HOST ? cudaMemcpyDeviceToHost
+                                                        : cudaMemcpyDeviceToDevice,
+                                  ctx->stream));
+  return ISING_OK;
+}
+
+// Overall best: K4 on the per-restart bests. With non-integer energies the
+// tracked values are FP32-accurate, so every restart within a margin of the
+// minimum is re-evaluated in FP64 (K3) and the lowest (energy, restart) of
+// those re-evaluated values wins.
+int select_best(ising_ds* ds) {
+  ising_ctx* ctx = ds->ctx;
+  argmin_kernel<<<1, 1024, 0, ctx->stream>>>(ds->B, ds->best_E.as<double>(),
+                                             ds->scratch.as<long long>());
+  ISING_CUDA(ctx, cudaGetLastError());
+  long long bidx = -1;
+  ISING_CUDA(ctx, cudaMemcpyAsync(&bidx, ds->scratch.p, 8, cudaMemcpyDeviceToHost, ctx->stream));
+  std::vector<double> bestE(ds->B), lastE(ds->B);
+  ISING_CUDA(ctx, cudaMemcpyAsync(bestE.data(), ds->best_E.p, ds->B * 8, cudaMemcpyDeviceToHost, ctx->stream));
+  ISING_CUDA(ctx, cudaMemcpyAsync(lastE.data(), ds->last_E.p, ds->B * 8, cudaMemcpyDeviceToHost, ctx->stream));
+  ISING_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (bidx < 0) return fail(ctx, ISING_ECUDA, "best-of-restarts reduction found no restart");
+  // the paper's literal output: best of the final spins
+  ds->last_best_restart = 0;
+  for (int64_t b = 1; b < ds->B; ++b)
+    if (lastE[b] < lastE[ds->last_best_restart]) ds->last_best_restart = b;
+  ds->last_best_energy = lastE[ds->last_best_restart];
+  if (ds->int_energy) {
+    ds->best_restart = bidx;
+    ds->best_energy = bestE[bidx];
+    return ISING_OK;
+  }
+  const double emin = bestE[bidx];
+  const double margin = 1e-4 * std::fabs(emin) + 1e-9;
+  std::vector<int64_t> cand;
+  for (int64_t b = 0; b < ds->B; ++b)
+    if (bestE[b] <= emin + margin) cand.push_back(b);
+  std::sort(cand.begin(), cand.end(), [&](int64_t a, int64_t b) {
+    return bestE[a] < bestE[b] || (bestE[a] == bestE[b] && a < b);
+  });
+  if (cand.size() > 64) cand.resize(64);
+  DevMem rows, E;
+  ISING_TRY(dev_alloc(ctx, rows, cand.size() * ds->n));
+  ISING_TRY(dev_alloc(ctx, E, cand.size() * 8));
+  for (size_t c = 0; c < cand.size(); ++c)
+    ISING_CUDA(ctx, cudaMemcpyAsync(rows.as<int8_t>() + c * ds->n, ds->best_s.as<int8_t>() + cand[c] * ds->n,
+                                    ds->n, cudaMemcpyDeviceToDevice, ctx->stream));
+  ISING_TRY(energy_device(ctx, ds->inst, rows.as<int8_t>(), (int64_t)cand.size(), E.as<double>(),
+                          nullptr, nullptr));
+  std::vector<double> ex(cand.size());
+  ISING_CUDA(ctx, cudaMemcpyAsync(ex.data(), E.p, cand.size() * 8, cudaMemcpyDeviceToHost, ctx->stream));
+  ISING_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  size_t w = 0;
+  for (size_t c = 1; c < cand.size(); ++c)
+    if (ex[c] < ex[w] || (ex[c] == ex[w] && cand[c] < cand[w])) w = c;
+  ds->best_restart = cand[w];
+  ds->best_energy = ex[w];
+  return ISING_OK;
+}
+
+}  // namespace
+}  // namespace ising
+
+// ------------------------------------------------------------------ C ABI
+
+extern "C" int ising_ds_create(ising_ctx* ctx, const ising_instance* inst,
+                               const ising_ds_params* p, ising_ds** out) {
+  if (!ctx) return ISING_EINVAL;
+  if (!out) return fail(ctx, ISING_EINVAL, "out is NULL");
+  *out = nullptr;
+  ISING_TRY(check_params(ctx, p));
+  ISING_CUDA(ctx, cudaSetDevice(ctx->device));
+  auto ds = new ising_ds();
+  ds->ctx = ctx;
+  ds->p = *p;
+  int rc = [&]() -> int {
+    ISING_TRY(upload_instance(ctx, inst, &ds->inst));
+    ds->n = ds->inst.n;
+    ds->B = p->restarts;
+    ds->T = p->steps;
+    const DevInstance& I = ds->inst;
+    // exact integer energies when every G = J s fits a float exactly
+    ds->int_energy = I.j_integer && I.j_absmax * (double)ds->n < 4194304.0 && I.h_dyadic;
+    ds->h_shift = I.h_shift;
+    ds->k = StepConsts{(float)I.cq, (float)I.ch, (float)p->mu, (float)p->lr,
+                       (float)p->beta1, (float)p->beta2, (float)p->eps};
+    int prec = p->precision;
+    if (I.layout == ISING_LAYOUT_CSR) {
+      if (prec != ISING_PREC_AUTO && prec != ISING_PREC_FP32_PLAIN)
+        return fail(ctx, ISING_ENOTSUP, "CSR instances run the sparse FP32/int path only");
+      ds->path = ISING_PATH_SPARSE;
+      ds->prec = ISING_PREC_FP32_PLAIN;
+    } else if (prec == ISING_PREC_FP32_PLAIN) {
+      ds->path = ISING_PATH_PLAIN;
+      ds->prec = prec;
+    } else {
+      ds->path = ISING_PATH_TC;
+      ds->prec = prec == ISING_PREC_AUTO ? ISING_PREC_TC : prec;
+    }
+    switch (ds->path) {
+      case ISING_PATH_PLAIN: ISING_TRY(plain_setup(ds)); break;
+      case ISING_PATH_SPARSE: ISING_TRY(sparse_setup(ds)); break;
+      default: ISING_TRY(tc_setup(ds)); break;
+    }
+    ISING_TRY(setup_field(ds));
+    ISING_TRY(common_alloc(ds));
+    ISING_TRY(init_state(ds));
+    ISING_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return ISING_OK;
+  }();
+  if (rc != ISING_OK) {
+    ising_ds_destroy(ds);
+    return rc;
+  }
+  *out = ds;
+  return ISING_OK;
+}
+
+extern "C" int ising_ds_run(ising_ds* ds, int64_t steps) {
+  if (!ds) return ISING_EINVAL;
+  ising_ctx* ctx = ds->ctx;
+  if (steps < 0) return fail(ctx, ISING_EINVAL, "steps must be >= 0");
+  if (ds->finished) return fail(ctx, ISING_EINVAL, "session already finished");
+  int64_t todo = std::min(steps, ds->T - ds->t);
+  if (todo <= 0) return ISING_OK;
+  cudaEvent_t e0, e1;
+  ISING_CUDA(ctx, cudaEventCreate(&e0));
+  ISING_CUDA(ctx, cudaEventCreate(&e1));
+  ISING_CUDA(ctx, cudaEventRecord(e0, ctx->stream));
+  for (int64_t s = 0; s < todo; ++s) {
+    int rc = path_step(ds, true);
+    if (rc == ISING_OK) rc = track_step(ds);
+    if (rc != ISING_OK) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return rc;
+    }
+    ds->t += 1;
+  }
+  ISING_CUDA(ctx, cudaEventRecord(e1, ctx->stream));
+  ISING_CUDA(ctx, cudaEventSynchronize(e1));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  ds->device_ms += ms;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ISING_CUDA(ctx, cudaGetLastError());
+  return ISING_OK;
+}
+
+extern "C" int ising_ds_finish(ising_ds* ds) {
+  if (!ds) return ISING_EINVAL;
+  if (ds->finished) return ISING_OK;
+  ising_ctx* ctx = ds->ctx;
+  ISING_TRY(ising_ds_run(ds, ds->T - ds->t));
+  // energy of S_{T+1}: the step kernels in energy-only mode, then tracking
+  ISING_TRY(path_step(ds, false));
+  ISING_TRY(track_step(ds));
+  ISING_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  ISING_TRY(select_best(ds));
+  ds->finished = true;
+  return ISING_OK;
+}
+
+extern "C" int ising_ds_export_state(ising_ds* ds, float* theta, float* m, float* v,
+                                     int8_t* spins, int64_t* t, int mem) {
+  if (!ds) return ISING_EINVAL;
+  ising_ctx* ctx = ds->ctx;
+  if (mem != ISING_MEM_HOST && mem != ISING_MEM_DEVICE) return fail(ctx, ISING_EINVAL, "bad mem");
+  const int64_t n = ds->n, B = ds->B;
+  cudaMemcpyKind kind = mem == ISING_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  float* outs[3] = {theta, m, v};
+  const DevMem* srcs[3] = {&ds->theta, &ds->m, &ds->v};
+  DevMem tmp;
+  for (int a = 0; a < 3; ++a) {
+    if (!outs[a]) continue;
+    if (ds->path == ISING_PATH_SPARSE) {
+      if (!tmp.p) ISING_TRY(dev_alloc(ctx, tmp, (size_t)B * n * 4));
+      spin_major_to_restart_major<<<grid1d(ctx, B * n), 256, 0, ctx->stream>>>(
+          n, B, ds->Bp, srcs[a]->as<float>(), tmp.as<float>());
+      ISING_CUDA(ctx, cudaGetLastError());
+      ISING_CUDA(ctx, cudaMemcpyAsync(outs[a], tmp.p, (size_t)B * n * 4, kind, ctx->stream));
+      ISING_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    } else {
+      ISING_CUDA(ctx, cudaMemcpy2DAsync(outs[a], n * 4, srcs[a]->p, ds->ld * 4, n * 4, B, kind,
+                                        ctx->stream));
+    }
+  }
+  if (spins) {
+    DevMem s8;
+    ISING_TRY(dev_alloc(ctx, s8, (size_t)B * n));
+    ISING_TRY(export_spins_int8(ds, (int)((ds->t + 1) % 3), s8.as<int8_t>()));
+    ISING_CUDA(ctx, cudaMemcpyAsync(spins, s8.p, (size_t)B * n,
+                                    mem == ISING_MEM_HOST ? cudaMemcpyDeviceToHost
+                                                          : cudaMemcpyDeviceToDevice,
+                                    ctx->stream));
+    ISING_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  }
+  if (t) *t = ds->t;
+  ISING_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return ISING_OK;
+}
+
+extern "C" int ising_ds_import_state(ising_ds* ds, const float* theta, const float* m,
+                                     const float* v, int64_t t, int mem) {
+  if (!ds) return ISING_EINVAL;
+  ising_ctx* ctx = ds->ctx;
+  if (!theta || !m || !v) return fail(ctx, ISING_EINVAL, "theta, m and v are required");
+  if (mem != ISING_MEM_HOST && mem != ISING_MEM_DEVICE) return fail(ctx, ISING_EINVAL, "bad mem");
+  if (t < 0 || t > ds->T) return fail(ctx, ISING_EINVAL, "t must lie in [0, T]");
+  if (ds->finished) return fail(ctx, ISING_EINVAL, "session already finished");
+  const int64_t n = ds->n, B = ds->B;
+  cudaMemcpyKind kind = mem == ISING_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  const float* ins[3] = {theta, m, v};
+  DevMem* dsts[3] = {&ds->theta, &ds->m, &ds->v};
+  DevMem tmp;
+  for (int a = 0; a < 3; ++a) {
+    if (ds->path == ISING_PATH_SPARSE) {
+      if (!tmp.p) ISING_TRY(dev_alloc(ctx, tmp, (size_t)B * n * 4));
+      ISING_CUDA(ctx, cudaMemcpyAsync(tmp.p, ins[a], (size_t)B * n * 4, kind, ctx->stream));
+      restart_major_to_spin_major<<<grid1d(ctx, B * n), 256, 0, ctx->stream>>>(
+          n, B, ds->Bp, tmp.as<float>(), dsts[a]->as<float>(), a == 0);
+      ISING_CUDA(ctx, cudaGetLastError());
+      ISING_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    } else {
+      ISING_CUDA(ctx, cudaMemcpy2DAsync(dsts[a]->p, ds->ld * 4, ins[a], n * 4, n * 4, B, kind,
+                                        ctx->stream));
+      if (a == 0) {
+        wrap_rows_kernel<<<grid1d(ctx, B * n), 256, 0, ctx->stream>>>(n, B, ds->ld,
+                                                                      ds->theta.as<float>());
+        ISING_CUDA(ctx, cudaGetLastError());
+      }
+    }
+  }
+  ds->t = t;
+  long long cnt[2] = {(long long)t, 0};
+  ISING_CUDA(ctx, cudaMemcpyAsync(ds->counters.p, cnt, 16, cudaMemcpyHostToDevice, ctx->stream));
+  const int slot = (int)((t + 1) % 3);
+  if (ds->path == ISING_PATH_SPARSE) {
+    spins_from_theta_bits<<<grid1d(ctx, n * ds->Bp / 32), 256, 0, ctx->stream>>>(
+        n, ds->Bp, ds->theta.as<float>(), ds->spins[slot].as<uint32_t>());
+  } else {
+    int g = grid1d(ctx, ds->Bp * ds->ld);
+    switch (ds->spin_kind) {
+      case kSpinF32: spins_from_theta_dense<kSpinF32><<<g, 256, 0, ctx->stream>>>(n, ds->Bp, ds->ld, ds->theta.as<float>(), ds->spins[slot].p); break;
+      case kSpinBF16: spins_from_theta_dense<kSpinBF16><<<g, 256, 0, ctx->stream>>>(n, ds->Bp, ds->ld, ds->theta.as<float>(), ds->spins[slot].p); break;
+      default: spins_from_theta_dense<kSpinE4M3><<<g, 256, 0, ctx->stream>>>(n, ds->Bp, ds->ld, ds->theta.as<float>(), ds->spins[slot].p); break;
+    }
+  }
+  ISING_CUDA(ctx, cudaGetLastError());
+  ISING_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return ISING_OK;
+}
+
+extern "C" int ising_ds_last_energies(ising_ds* ds, double* E, int mem) {
+  if (!ds) return ISING_EINVAL;
+  if (!E) return fail(ds->ctx, ISING_EINVAL, "E is NULL");
+  ISING_TRY(copy_out(ds->ctx, E, ds->last_E.p, ds->B * 8, mem));
+  ISING_CUDA(ds->ctx, cudaStreamSynchronize(ds->ctx->stream));
+  return ISING_OK;
+}
+
+extern "C" int ising_ds_restart_best(ising_ds* ds, double* E, int64_t* step, int8_t* spins,
+                                     int mem) {
+  if (!ds) return ISING_EINVAL;
+  if (E) ISING_TRY(copy_out(ds->ctx, E, ds->best_E.p, ds->B * 8, mem));
+  if (step) ISING_TRY(copy_out(ds->ctx, step, ds->best_t.p, ds->B * 8, mem));
+  if (spins) ISING_TRY(copy_out(ds->ctx, spins, ds->best_s.p, (size_t)ds->B * ds->n, mem));
+  ISING_CUDA(ds->ctx, cudaStreamSynchronize(ds->ctx->stream));
+  return ISING_OK;
+}
+
+extern "C" int ising_ds_result(ising_ds* ds, int8_t* best_spins, double* best_energy,
+                               ising_ds_stats* stats, int mem) {
+  if (!ds) return ISING_EINVAL;
+  ising_ctx* ctx = ds->ctx;
+  if (!ds->finished) ISING_TRY(select_best(ds));
+  const int64_t b = ds->best_restart;
+  if (best_spins)
+    ISING_TRY(copy_out(ctx, best_spins, ds->best_s.as<int8_t>() + b * ds->n, ds->n, mem));
+  if (best_energy) {
+    if (mem == ISING_MEM_HOST) *best_energy = ds->best_energy;
+    else ISING_CUDA(ctx, cudaMemcpyAsync(best_energy, &ds->best_energy, 8, cudaMemcpyHostToDevice, ctx->stream));
+  }
+  if (stats) {
+    long long st = 0;
+    ISING_CUDA(ctx, cudaMemcpyAsync(&st, ds->best_t.as<long long>() + b, 8, cudaMemcpyDeviceToHost, ctx->stream));
+    ISING_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    stats->best_restart = b;
+    stats->best_step = st;
+    stats->last_best_energy = ds->last_best_energy;
+    stats->last_best_restart = ds->last_best_restart;
+    stats->steps_done = ds->t;
+    stats->path = ds->path;
+    stats->precision = ds->prec;
+    stats->device_ms = ds->device_ms;
+    stats->kernel_ms = ds->kernel_ms;
+    stats->kernel_launches = ds->kernel_launches;
+  }
+  ISING_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return ISING_OK;
+}
+
+extern "C" int ising_ds_destroy(ising_ds* ds) {
+  if (!ds) return ISING_OK;
+  if (ds->ctx) cudaStreamSynchronize(ds->ctx->stream);
+  for (auto& e : ds->kev)
+    if (e) cudaEventDestroy(e);
+  tc_release(ds);
+  delete ds;
+  return ISING_OK;
+}
+
+extern "C" int ising_select_domain(ising_ctx* ctx, const ising_instance* inst,
+                                   const ising_ds_params* p, int8_t* best_spins,
+                                   double* best_energy, ising_ds_stats* stats, int mem) {
+  if (!ctx) return ISING_EINVAL;
+  if (mem != ISING_MEM_HOST && mem != ISING_MEM_DEVICE) return fail(ctx, ISING_EINVAL, "bad mem");
+  ising_ds* ds = nullptr;
+  ISING_TRY(ising_ds_create(ctx, inst, p, &ds));
+  int rc = ising_ds_finish(ds);
+  if (rc == ISING_OK) rc = ising_ds_result(ds, best_spins, best_energy, stats, mem);
+  ising_ds_destroy(ds);
+  return rc;
+}

@@ -1,0 +1,114 @@
+// Domain-selection session (Sec. III-B) shared by the step kernels.
+#pragma once
+
+#include "common.cuh"
+
+namespace ising {
+
+// Per-step constants of the update. Adam bias corrections come from a device
+// table indexed by the step counter, so launches stay identical across steps
+// and can be replayed from a CUDA graph.
+struct StepConsts {
+  float cq, ch, mu, lr, b1, b2, eps;
+};
+
+// theta - 2 pi rint(theta / 2 pi) with 2 pi split in two floats, so that the
+// result lies in [-pi, pi] up to one rounding (projection of Sec. III-B
+// reading: sin and cos are unchanged).
+__device__ __forceinline__ float wrap_angle(float th) {
+  const float kInv2Pi = 0.15915494309189535f;
+  const float k2PiHi = __int_as_float(0x40C90FDB);  // 2 pi rounded up to float
+  const float k2PiLo = -1.7484555314695172e-07f;    // 2 pi - k2PiHi
+  float k = rintf(th * kInv2Pi);
+  th = fmaf(-k, k2PiHi, th);
+  th = fmaf(-k, k2PiLo, th);
+  return th;
+}
+
+// sgn+(sin theta) for float theta with |theta| < 2 pi, by comparisons: sin is
+// >= 0 exactly on [0, pi] and [-2 pi, -pi]; pi and 2 pi are not floats, so the
+// bounds are the floats on the correct side of them.
+__device__ __forceinline__ bool sin_nonneg(float th) {
+  const float kPiDn = __int_as_float(0x40490FDA);     // largest float < pi
+  const float kPiUp = __int_as_float(0x40490FDB);     // smallest float > pi
+  const float k2PiDn = __int_as_float(0x40C90FDA);    // largest float < 2 pi
+  return (th >= 0.0f && th <= kPiDn) || (th <= -kPiUp && th >= -k2PiDn);
+}
+
+// Adam on one coordinate; returns the projected new angle.
+__device__ __forceinline__ float adam_update(const StepConsts& k, float c1, float c2, float g,
+                                             float th, float& m, float& v) {
+  m = fmaf(k.b1, m, (1.0f - k.b1) * g);
+  v = fmaf(k.b2, v, (1.0f - k.b2) * (g * g));
+  const float mhat = m * c1;
+  const float vhat = v * c2;
+  th = th - k.lr * mhat / (sqrtf(vhat) + k.eps);
+  return wrap_angle(th);
+}
+
+enum SpinKind { kSpinF32 = 0, kSpinBF16 = 1, kSpinBits = 2, kSpinE4M3 = 3 };
+
+}  // namespace ising
+
+struct ising_ds {
+  ising_ctx* ctx = nullptr;
+  ising::DevInstance inst;
+  ising_ds_params p{};
+  int64_t n = 0, B = 0, T = 0;
+  int64_t t = 0;          // steps done (host mirror of the device counter)
+  int path = ISING_PATH_PLAIN;
+  int prec = ISING_PREC_FP32_PLAIN;
+  bool int_energy = false; // energies accumulate exactly in integers
+  int h_shift = 0;         // integer field = h * 2^h_shift
+  ising::StepConsts k{};
+  // state layout: dense paths [Bp][ld] restart-major; sparse path [n][Bp]
+  int64_t ld = 0;          // leading dimension of restart-major arrays
+  int64_t Bp = 0;          // padded restart count (sparse: multiple of 128)
+  int spin_kind = ising::kSpinF32;
+  ising::DevMem theta, m, v;
+  ising::DevMem spins[3];  // S_t lives in spins[t % 3]
+  int mtiles = 0;          // number of energy partial rows
+  ising::DevMem qpart[2], hpart[2], epart[2];  // [mtiles][Bp], slot t % 2
+  ising::DevMem hf;        // float32 field (n)
+  ising::DevMem hint;      // int32 field * 2^h_shift (n)
+  ising::DevMem best_E, best_t, best_s, last_E;
+  ising::DevMem counters;  // int64 [0] = steps done, [1] = done-block counter
+  ising::DevMem bias;      // float2 [T + 2]: 1/(1-b1^t), 1/(1-b2^t)
+  // dense operands
+  ising::DevMem Jf;        // plain path: float n x n
+  ising::DevMem Jop[3];    // tensor path: planes (bf16 or e4m3), [n][ld]
+  int planes = 1;
+  ising::DevMem rowscale;  // fp8 path: float per row
+  void* tc = nullptr;      // tensor-core path state (tensor maps etc.)
+  // sparse operands
+  ising::DevMem sp_val;    // int8 or float values
+  bool sp_int8 = false;
+  // results
+  bool finished = false;
+  int64_t best_restart = -1;
+  double best_energy = 0.0;
+  double device_ms = 0.0;
+  double kernel_ms = 0.0;
+  int64_t kernel_launches = 0;
+  cudaEvent_t kev[2] = {nullptr, nullptr};
+  double last_best_energy = 0.0;
+  int64_t last_best_restart = -1;
+  ising::DevMem scratch;   // small per-session scratch (argmin etc.)
+};
+
+namespace ising {
+
+// Path-specific hooks, implemented in ds_plain.cu, ds_sparse.cu, ds_tc.cu.
+int plain_setup(ising_ds* ds);
+int plain_step(ising_ds* ds, bool update);
+int sparse_setup(ising_ds* ds);
+int sparse_step(ising_ds* ds, bool update);
+int tc_setup(ising_ds* ds);
+int tc_step(ising_ds* ds, bool update);
+void tc_release(ising_ds* ds);
+
+// Shared session services (ds.cu).
+int track_step(ising_ds* ds);  // reduce partials of step t+1, best tracking, t += 1
+int export_spins_int8(ising_ds* ds, int slot, int8_t* out);  // spins[slot] -> int8 [B][n]
+
+}  // namespace ising

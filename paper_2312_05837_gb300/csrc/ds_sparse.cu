@@ -1,0 +1,219 @@
+// K2s: fused domain-selection step (Sec. III-B) for CSR couplings.
+//
+// Layout: state theta, m, v is [n][Bp] (restarts contiguous, Bp a multiple of
+// 128); spins are bit-packed [n][Bp/32] words (bit set = +1), so a whole
+// neighbour's spins for 512 restarts are 64 bytes. A warp owns one row at a
+// time; lane l owns restarts 128 q + 4 l + {0..3}, so every state access is a
+// coalesced float4 and a neighbour's spins are one broadcast word per lane
+// group. The per-row epilogue is the same as the dense paths: F = cQ G +
+// cH h - mu s, g = cos(theta) F, Adam, projection, new spin bit; energy
+// partials of the input spins are summed per block in warp order.
+#include "ds_internal.cuh"
+
+#include <algorithm>
+
+namespace ising {
+namespace {
+
+template <int Q, bool UPDATE, bool INT_E, bool VAL_I8>
+__global__ void __launch_bounds__(256) sparse_step_kernel(
+    int64_t n, int64_t Bp, int64_t rows_per_block, const int32_t* __restrict__ rowptr,
+    const int32_t* __restrict__ col, const void* __restrict__ val,
+    const uint32_t* __restrict__ bits_in, uint32_t* __restrict__ bits_out,
+    float* __restrict__ theta, float* __restrict__ m, float* __restrict__ v,
+    const float* __restrict__ hf, const int32_t* __restrict__ hint, StepConsts k,
+    const float2* __restrict__ bias, const long long* __restrict__ counters,
+    long long* __restrict__ qpart, long long* __restrict__ hpart, float* __restrict__ epart) {
+  constexpr int W = 8;  // warps per block
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t words = Bp / 32;
+  const int64_t cb = (int64_t)blockIdx.y * (128 * Q);  // first restart of this chunk
+  const int64_t wofs = cb / 32 + (lane >> 3);
+  const int nshift = 4 * (lane & 7);
+  const int64_t r0 = (int64_t)blockIdx.x * rows_per_block;
+  const int64_t r1 = r0 + rows_per_block < n ? r0 + rows_per_block : n;
+  const float2 bc = bias[counters[0] + 1];
+
+  int eq[Q][4], eh[Q][4];
+  float ee[Q][4];
+#pragma unroll
+  for (int q = 0; q < Q; ++q)
+#pragma unroll
+    for (int r = 0; r < 4; ++r) { eq[q][r] = 0; eh[q][r] = 0; ee[q][r] = 0.f; }
+
+  for (int64_t i = r0 + warp; i < r1; i += W) {
+    float G[Q][4];
+#pragma unroll
+    for (int q = 0; q < Q; ++q)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) G[q][r] = 0.f;
+    const int e1 = rowptr[i + 1];
+    for (int e = rowptr[i]; e < e1; ++e) {
+      const int64_t j = col[e];
+      const float Jv = VAL_I8 ? (float)static_cast<const int8_t*>(val)[e]
+                              : static_cast<const float*>(val)[e];
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        const uint32_t nib = (__ldg(&bits_in[j * words + wofs + 4 * q]) >> nshift) & 0xFu;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) G[q][r] += ((nib >> r) & 1u) ? Jv : -Jv;
+      }
+    }
+    const float h = hf[i];
+    const int hi = hint[i];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const uint32_t own = (bits_in[i * words + wofs + 4 * q] >> nshift) & 0xFu;
+      const int64_t base = i * Bp + cb + 128 * q + 4 * lane;
+      float4 th4, m4, v4;
+      if (UPDATE) {
+        th4 = *reinterpret_cast<const float4*>(theta + base);
+        m4 = *reinterpret_cast<const float4*>(m + base);
+        v4 = *reinterpret_cast<const float4*>(v + base);
+      }
+      float* thp = &th4.x;
+      float* mp = &m4.x;
+      float* vp = &v4.x;
+      uint32_t newnib = 0;
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const float s = ((own >> r) & 1u) ? 1.f : -1.f;
+        if (INT_E) {
+          eq[q][r] += (int)s * __float2int_rn(G[q][r]);
+          eh[q][r] += (int)s * hi;
+        } else {
+          ee[q][r] += s * fmaf(k.cq, G[q][r], k.ch * h);
+        }
+        if (UPDATE) {
+          const float F = fmaf(k.cq, G[q][r], fmaf(k.ch, h, -k.mu * s));
+          const float g = cosf(thp[r]) * F;
+          thp[r] = adam_update(k, bc.x, bc.y, g, thp[r], mp[r], vp[r]);
+          if (sin_nonneg(thp[r])) newnib |= 1u << r;
+        }
+      }
+      if (UPDATE) {
+        *reinterpret_cast<float4*>(theta + base) = th4;
+        *reinterpret_cast<float4*>(m + base) = m4;
+        *reinterpret_cast<float4*>(v + base) = v4;
+        uint32_t word = newnib << nshift;
+        word |= __shfl_xor_sync(0xffffffffu, word, 1);
+        word |= __shfl_xor_sync(0xffffffffu, word, 2);
+        word |= __shfl_xor_sync(0xffffffffu, word, 4);
+        if ((lane & 7) == 0) bits_out[i * words + wofs + 4 * q] = word;
+      }
+    }
+  }
+
+  // energy partials: per restart, sum over this block's rows in warp order
+  __shared__ float red_f[INT_E ? 1 : W][INT_E ? 1 : 128 * Q];
+  __shared__ int red_q[INT_E ? W : 1][INT_E ? 128 * Q : 1];
+  __shared__ int red_h[INT_E ? W : 1][INT_E ? 128 * Q : 1];
+#pragma unroll
+  for (int q = 0; q < Q; ++q)
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int c = 128 * q + 4 * lane + r;
+      if (INT_E) {
+        red_q[warp][c] = eq[q][r];
+        red_h[warp][c] = eh[q][r];
+      } else {
+        red_f[warp][c] = ee[q][r];
+      }
+    }
+  __syncthreads();
+  for (int c = threadIdx.x; c < 128 * Q; c += blockDim.x) {
+    const int64_t o = (int64_t)blockIdx.x * Bp + cb + c;
+    if (INT_E) {
+      long long a = 0, b = 0;
+#pragma unroll
+      for (int w = 0; w < W; ++w) { a += red_q[w][c]; b += red_h[w][c]; }
+      qpart[o] = a;
+      hpart[o] = b;
+    } else {
+      float a = 0.f;
+#pragma unroll
+      for (int w = 0; w < W; ++w) a += red_f[w][c];
+      epart[o] = a;
+    }
+  }
+}
+
+__global__ void csr_values_kernel(const void* J, int dt, int64_t nnz, bool to_i8, void* out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    double x = load_as_double(J, dt, e);
+    if (to_i8) static_cast<int8_t*>(out)[e] = (int8_t)x;
+    else static_cast<float*>(out)[e] = (float)x;
+  }
+}
+
+int chunk_q(int64_t Bp) {
+  int64_t c = Bp / 128;
+  if (c % 4 == 0) return 4;
+  if (c % 2 == 0) return 2;
+  return 1;
+}
+
+int64_t sparse_rows_per_block(ising_ds* ds) {
+  const int64_t target = (int64_t)ds->ctx->sm_count * 4;
+  int64_t nb = std::min<int64_t>((ds->n + 63) / 64, std::max<int64_t>(target, 1));
+  return (ds->n + nb - 1) / nb;
+}
+
+}  // namespace
+
+int sparse_setup(ising_ds* ds) {
+  ising_ctx* ctx = ds->ctx;
+  ds->Bp = (ds->B + 127) / 128 * 128;
+  ds->ld = ds->n;
+  ds->spin_kind = kSpinBits;
+  const int64_t rpb = sparse_rows_per_block(ds);
+  ds->mtiles = (int)((ds->n + rpb - 1) / rpb);
+  ds->sp_int8 = ds->inst.j_integer && ds->inst.j_absmax <= 127.0;
+  const int64_t nnz = ds->inst.nnz;
+  ISING_TRY(dev_alloc(ctx, ds->sp_val, (size_t)nnz * (ds->sp_int8 ? 1 : 4)));
+  if (nnz) {
+    int g = (int)std::min<int64_t>((nnz + 255) / 256, (int64_t)ctx->sm_count * 16);
+    csr_values_kernel<<<g, 256, 0, ctx->stream>>>(ds->inst.J.p, ds->inst.j_dtype, nnz,
+                                                  ds->sp_int8, ds->sp_val.p);
+    ISING_CUDA(ctx, cudaGetLastError());
+  }
+  return ISING_OK;
+}
+
+int sparse_step(ising_ds* ds, bool update) {
+  ising_ctx* ctx = ds->ctx;
+  const int64_t t = ds->t + 1;
+  const uint32_t* in = ds->spins[t % 3].as<uint32_t>();
+  uint32_t* out = ds->spins[(t + 1) % 3].as<uint32_t>();
+  const int ps = (int)(t % 2);
+  const int64_t rpb = sparse_rows_per_block(ds);
+  const int Q = chunk_q(ds->Bp);
+  dim3 grid((unsigned)ds->mtiles, (unsigned)(ds->Bp / (128 * Q)));
+#define ISING_SP(QQ, U, I, V)                                                                 \
+  sparse_step_kernel<QQ, U, I, V><<<grid, 256, 0, ctx->stream>>>(                             \
+      ds->n, ds->Bp, rpb, ds->inst.rowptr.as<int32_t>(), ds->inst.indices.as<int32_t>(),      \
+      ds->sp_val.p, in, out, ds->theta.as<float>(), ds->m.as<float>(), ds->v.as<float>(),     \
+      ds->hf.as<float>(), ds->hint.as<int32_t>(), ds->k, ds->bias.as<float2>(),               \
+      ds->counters.as<long long>(), ds->qpart[ps].as<long long>(),                            \
+      ds->hpart[ps].as<long long>(), ds->epart[ps].as<float>())
+#define ISING_SP_V(QQ, U, I) \
+  do { if (ds->sp_int8) ISING_SP(QQ, U, I, true); else ISING_SP(QQ, U, I, false); } while (0)
+#define ISING_SP_I(QQ, U) \
+  do { if (ds->int_energy) ISING_SP_V(QQ, U, true); else ISING_SP_V(QQ, U, false); } while (0)
+#define ISING_SP_U(QQ) \
+  do { if (update) ISING_SP_I(QQ, true); else ISING_SP_I(QQ, false); } while (0)
+  switch (Q) {
+    case 4: ISING_SP_U(4); break;
+    case 2: ISING_SP_U(2); break;
+    default: ISING_SP_U(1); break;
+  }
+#undef ISING_SP_U
+#undef ISING_SP_I
+#undef ISING_SP_V
+#undef ISING_SP
+  ISING_CUDA(ctx, cudaGetLastError());
+  return ISING_OK;
+}
+
+}  // namespace ising

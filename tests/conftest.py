@@ -26,3 +26,11 @@ def pytest_collection_modifyitems(config, items):
     for item in items:
         if "gpu" in item.keywords:
             item.add_marker(skip)
+
+
+@pytest.fixture(scope="session")
+def gpu_ctx():
+    from paper_2312_05837_gb300 import api
+    ctx = api.Context(0)
+    yield ctx
+    ctx.close()

@@ -1,0 +1,69 @@
+"""Shared checks for the GPU parity tests: the CUDA path's state, exported
+through the C ABI, against one oracle step from the same state."""
+
+import math
+
+import numpy as np
+
+from oracle import domain_selection as ods
+from oracle import ising
+
+TOL = 1e-5  # per-element bound on FP32 gradient error, relative to the row scale
+
+
+def row_scale(inst, mu):
+    """|cQ| sum_j |J_ij| + |cH h_i| + mu: the largest the loss field can be."""
+    cq, ch = ising.coefficients(inst.j_scale, inst.convention)
+    J = ising.coupling_matrix(inst)
+    a = np.asarray(abs(J).sum(axis=1)).ravel()
+    return abs(cq) * a + abs(ch) * np.abs(ising.field(inst)) + mu
+
+
+def oracle_step(inst, st, t, p):
+    """One oracle step from an exported state (restart-major arrays)."""
+    cq, ch = ising.coefficients(inst.j_scale, inst.convention)
+    J = ising.coupling_matrix(inst)
+    h = ising.field(inst)
+    th = st["theta"].T.astype(np.float64)
+    m = st["m"].T.astype(np.float64)
+    v = st["v"].T.astype(np.float64)
+    return ods.step(J, h, cq, ch, p, th, m, v, t)
+
+
+def wrapped_diff(a, b):
+    d = a - b
+    return d - 2 * math.pi * np.rint(d / (2 * math.pi))
+
+
+def check_step(inst, st0, st1, last_E, p, exact_energy):
+    """st0: state before step t = st0['t'] + 1, st1: after it."""
+    t = st0["t"] + 1
+    r = oracle_step(inst, st0, t, p)
+    # spins consumed by the step are the oracle's rounding of the same theta
+    np.testing.assert_array_equal(st0["spins"].T, r.spins.astype(np.int8))
+    if exact_energy:
+        np.testing.assert_array_equal(last_E, r.energy)
+    else:
+        cq, ch = ising.coefficients(inst.j_scale, inst.convention)
+        bound = TOL * (np.sum(np.abs(r.spins * r.G), axis=0) * abs(cq) +
+                       np.abs(ising.field(inst)) @ np.ones_like(r.spins) + 1.0)
+        assert np.all(np.abs(last_E - r.energy) <= bound)
+    sc = row_scale(inst, p.mu)[:, None]
+    m0 = st0["m"].T.astype(np.float64)
+    v0 = st0["v"].T.astype(np.float64)
+    # gradient recovered from the first moment: g = (m1 - b1 m0) / (1 - b1)
+    m1 = st1["m"].T.astype(np.float64)
+    v1 = st1["v"].T.astype(np.float64)
+    assert np.all(np.abs(m1 - r.m) <= TOL * (np.abs(m0) + (1 - p.beta1) * sc) + 1e-30)
+    assert np.all(np.abs(v1 - r.v) <= TOL * (v0 + 2 * (1 - p.beta2) * sc * sc) + 1e-30)
+    if np.all(m0 == 0):
+        g = m1 / (1 - p.beta1)
+        assert np.max(np.abs(g - r.grad) / sc) <= TOL
+    th1 = st1["theta"].T.astype(np.float64)
+    assert np.max(np.abs(wrapped_diff(th1, r.theta))) <= TOL * (1 + p.lr)
+    # next spins: identical wherever the rounding is not within the tolerance
+    clear = np.abs(np.sin(r.theta)) > 10 * TOL * (1 + p.lr)
+    nxt = st1["spins"].T
+    assert np.array_equal(nxt[clear], ods.round_spins(r.theta)[clear].astype(np.int8))
+    assert clear.mean() > 0.99
+    return r
