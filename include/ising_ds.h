@@ -140,6 +140,8 @@ typedef struct ising_ds_stats {
 /* Create a context on CUDA device `device`, issuing work on `stream`
  * (a cudaStream_t, NULL = the legacy default stream). */
 int ising_create(ising_ctx** out, int device, void* stream);
+/* Destroy a context. Every session and pruning result created on it must be
+ * destroyed first (they refer to the context). */
 int ising_destroy(ising_ctx* ctx);
 /* Message of the last failed call on this context ("" if none). The string
  * lives until the next call on the context. */
@@ -238,6 +240,11 @@ int ising_ds_export_state(ising_ds* ds, float* theta, float* m, float* v,
  * are re-derived from theta. Resets nothing else. */
 int ising_ds_import_state(ising_ds* ds, const float* theta, const float* m,
                           const float* v, int64_t t, int mem);
+/* The coupling product G = J s (Sec. III-B, the term inside the loss field)
+ * of the spins the next step will use, computed by the session's own step
+ * kernel and precision (tensor cores, CUDA cores or sparse); restart-major
+ * [B][n] float32 in memory `mem`. Does not advance the session. */
+int ising_ds_coupling(ising_ds* ds, float* G_out, int mem);
 /* Energies E(s_t) of the spins consumed by the most recent step, [B]. */
 int ising_ds_last_energies(ising_ds* ds, double* E, int mem);
 /* Per-restart best so far: energy [B], step [B], spins [B][n] (any NULL). */

@@ -9,6 +9,7 @@ entry point. Nothing here computes any part of the method.
 from __future__ import annotations
 
 import ctypes
+import weakref
 from ctypes import byref, c_double, c_int32, c_int64, c_void_p
 
 import numpy as np
@@ -78,6 +79,7 @@ class Context:
             stream = stream.cuda_stream
         self.device = device
         self.handle = c_void_p()
+        self._children = weakref.WeakSet()  # sessions / pruning results using this context
         rc = self.lib.ising_create(byref(self.handle), device, c_void_p(stream))
         if rc != L.OK:
             raise IsingError(rc, "ising_create failed (no CUDA device?)")
@@ -91,7 +93,11 @@ class Context:
         self.check(self.lib.ising_synchronize(self.handle))
 
     def close(self):
+        """Releases the context after every session / pruning result made on
+        it (the library requires those to go first)."""
         if self.handle:
+            for child in list(self._children):
+                child.close()
             self.lib.ising_destroy(self.handle)
             self.handle = c_void_p()
 
@@ -229,6 +235,7 @@ class Pruned:
     def __init__(self, ctx: Context, handle: c_void_p, src):
         self.ctx = ctx
         self.handle = handle
+        ctx._children.add(self)
         n_red, nnz_red, C, eta, rounds = c_int64(), c_int64(), c_double(), c_double(), c_int32()
         ctx.check(ctx.lib.ising_prune_info(handle, byref(n_red), byref(nnz_red), byref(C),
                                            byref(eta), byref(rounds)))
@@ -309,6 +316,7 @@ class Session:
         self.n = int(inst.n)
         self.B = int(restarts)
         self.handle = c_void_p()
+        ctx._children.add(self)
         ctx.check(ctx.lib.ising_ds_create(ctx.handle, byref(s), byref(self.p), byref(self.handle)))
 
     def run(self, steps: int):
@@ -334,6 +342,12 @@ class Session:
         vv = _host(v, np.float32)
         self.ctx.check(self.ctx.lib.ising_ds_import_state(self.handle, _ptr(th), _ptr(mm),
                                                           _ptr(vv), int(t), L.MEM_HOST))
+
+    def coupling(self) -> np.ndarray:
+        """G = J s of the next step's spins, [B][n] float32."""
+        G = np.empty((self.B, self.n), np.float32)
+        self.ctx.check(self.ctx.lib.ising_ds_coupling(self.handle, _ptr(G), L.MEM_HOST))
+        return G
 
     def last_energies(self) -> np.ndarray:
         E = np.empty(self.B, np.float64)

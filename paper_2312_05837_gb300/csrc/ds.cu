@@ -405,10 +405,11 @@ int setup_field(ising_ds* ds) {
 }
 
 int path_step_raw(ising_ds* ds, bool update) {
+  const int mode = update ? kModeUpdate : kModeEnergy;
   switch (ds->path) {
-    case ISING_PATH_PLAIN: return plain_step(ds, update);
-    case ISING_PATH_SPARSE: return sparse_step(ds, update);
-    default: return tc_step(ds, update);
+    case ISING_PATH_PLAIN: return plain_step(ds, mode, nullptr);
+    case ISING_PATH_SPARSE: return sparse_step(ds, mode, nullptr);
+    default: return tc_step(ds, mode, nullptr);
   }
 }
 
@@ -520,7 +521,8 @@ extern "C" int ising_ds_create(ising_ctx* ctx, const ising_instance* inst,
     ds->int_energy = I.j_integer && I.j_absmax * (double)ds->n < 4194304.0 && I.h_dyadic;
     ds->h_shift = I.h_shift;
     ds->k = StepConsts{(float)I.cq, (float)I.ch, (float)p->mu, (float)p->lr,
-                       (float)p->beta1, (float)p->beta2, (float)p->eps};
+                       (float)p->beta1, (float)p->beta2, (float)p->eps,
+                       (float)(1.0 - p->beta1), (float)(1.0 - p->beta2)};
     int prec = p->precision;
     if (I.layout == ISING_LAYOUT_CSR) {
       if (prec != ISING_PREC_AUTO && prec != ISING_PREC_FP32_PLAIN)
@@ -582,6 +584,7 @@ extern "C" int ising_ds_run(ising_ds* ds, int64_t steps) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   ISING_CUDA(ctx, cudaGetLastError());
+  if (ds->path == ISING_PATH_TC) ISING_TRY(tc_error(ds));
   return ISING_OK;
 }
 
@@ -594,6 +597,7 @@ extern "C" int ising_ds_finish(ising_ds* ds) {
   ISING_TRY(path_step(ds, false));
   ISING_TRY(track_step(ds));
   ISING_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (ds->path == ISING_PATH_TC) ISING_TRY(tc_error(ds));
   ISING_TRY(select_best(ds));
   ds->finished = true;
   return ISING_OK;
@@ -686,6 +690,36 @@ extern "C" int ising_ds_import_state(ising_ds* ds, const float* theta, const flo
   }
   ISING_CUDA(ctx, cudaGetLastError());
   ISING_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return ISING_OK;
+}
+
+extern "C" int ising_ds_coupling(ising_ds* ds, float* G_out, int mem) {
+  if (!ds) return ISING_EINVAL;
+  ising_ctx* ctx = ds->ctx;
+  if (!G_out) return fail(ctx, ISING_EINVAL, "G_out is NULL");
+  if (mem != ISING_MEM_HOST && mem != ISING_MEM_DEVICE) return fail(ctx, ISING_EINVAL, "bad mem");
+  if (ds->finished) return fail(ctx, ISING_EINVAL, "session already finished");
+  const int64_t n = ds->n, B = ds->B;
+  cudaMemcpyKind kind = mem == ISING_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  DevMem G;
+  if (ds->path == ISING_PATH_SPARSE) {
+    DevMem Gt;
+    ISING_TRY(dev_alloc(ctx, Gt, (size_t)n * ds->Bp * 4));
+    ISING_TRY(dev_alloc(ctx, G, (size_t)B * n * 4));
+    ISING_TRY(sparse_step(ds, kModeCoupling, Gt.as<float>()));
+    spin_major_to_restart_major<<<grid1d(ctx, B * n), 256, 0, ctx->stream>>>(
+        n, B, ds->Bp, Gt.as<float>(), G.as<float>());
+    ISING_CUDA(ctx, cudaGetLastError());
+    ISING_CUDA(ctx, cudaMemcpyAsync(G_out, G.p, (size_t)B * n * 4, kind, ctx->stream));
+    ISING_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  } else {
+    ISING_TRY(dev_alloc(ctx, G, (size_t)ds->Bp * ds->ld * 4));
+    if (ds->path == ISING_PATH_PLAIN) ISING_TRY(plain_step(ds, kModeCoupling, G.as<float>()));
+    else ISING_TRY(tc_step(ds, kModeCoupling, G.as<float>()));
+    ISING_CUDA(ctx, cudaMemcpy2DAsync(G_out, n * 4, G.p, ds->ld * 4, n * 4, B, kind, ctx->stream));
+    ISING_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (ds->path == ISING_PATH_TC) ISING_TRY(tc_error(ds));
+  }
   return ISING_OK;
 }
 

@@ -10,6 +10,7 @@ namespace ising {
 // and can be replayed from a CUDA graph.
 struct StepConsts {
   float cq, ch, mu, lr, b1, b2, eps;
+  float omb1, omb2;  // 1 - b1 and 1 - b2 formed in FP64, then rounded
 };
 
 // theta - 2 pi rint(theta / 2 pi) with 2 pi split in two floats, so that the
@@ -38,8 +39,8 @@ __device__ __forceinline__ bool sin_nonneg(float th) {
 // Adam on one coordinate; returns the projected new angle.
 __device__ __forceinline__ float adam_update(const StepConsts& k, float c1, float c2, float g,
                                              float th, float& m, float& v) {
-  m = fmaf(k.b1, m, (1.0f - k.b1) * g);
-  v = fmaf(k.b2, v, (1.0f - k.b2) * (g * g));
+  m = fmaf(k.b1, m, k.omb1 * g);
+  v = fmaf(k.b2, v, k.omb2 * (g * g));
   const float mhat = m * c1;
   const float vhat = v * c2;
   th = th - k.lr * mhat / (sqrtf(vhat) + k.eps);
@@ -47,6 +48,10 @@ __device__ __forceinline__ float adam_update(const StepConsts& k, float c1, floa
 }
 
 enum SpinKind { kSpinF32 = 0, kSpinBF16 = 1, kSpinBits = 2, kSpinE4M3 = 3 };
+
+// What a step launch does: the full update, only the energies of the input
+// spins (the final evaluation), or only the coupling product G = J s.
+enum StepMode { kModeUpdate = 0, kModeEnergy = 1, kModeCoupling = 2 };
 
 }  // namespace ising
 
@@ -99,12 +104,15 @@ struct ising_ds {
 namespace ising {
 
 // Path-specific hooks, implemented in ds_plain.cu, ds_sparse.cu, ds_tc.cu.
+// A step launch reads S_t from spins[(t) % 3] with t = ds->t + 1; in coupling
+// mode it writes G to Gout (dense: [B][ld], sparse: [n][Bp]) and nothing else.
 int plain_setup(ising_ds* ds);
-int plain_step(ising_ds* ds, bool update);
+int plain_step(ising_ds* ds, int mode, float* Gout);
 int sparse_setup(ising_ds* ds);
-int sparse_step(ising_ds* ds, bool update);
+int sparse_step(ising_ds* ds, int mode, float* Gout);
 int tc_setup(ising_ds* ds);
-int tc_step(ising_ds* ds, bool update);
+int tc_step(ising_ds* ds, int mode, float* Gout);
+int tc_error(ising_ds* ds);  // ISING_ETIMEOUT if a bounded wait gave up
 void tc_release(ising_ds* ds);
 
 // Shared session services (ds.cu).

@@ -17,13 +17,15 @@ __global__ void to_float_kernel(const void* J, int dt, int64_t count, float* out
     out[e] = (float)load_as_double(J, dt, e);
 }
 
-template <bool UPDATE, bool INT_E>
+template <int MODE, bool INT_E>
 __global__ void __launch_bounds__(256) plain_step_kernel(
     const float* __restrict__ J, int64_t n, int64_t B, const float* __restrict__ S,
     float* __restrict__ Snext, float* __restrict__ theta, float* __restrict__ m,
     float* __restrict__ v, const float* __restrict__ hf, const int32_t* __restrict__ hint,
     StepConsts k, const float2* __restrict__ bias, const long long* __restrict__ counters,
-    long long* __restrict__ qpart, long long* __restrict__ hpart, float* __restrict__ epart) {
+    long long* __restrict__ qpart, long long* __restrict__ hpart, float* __restrict__ epart,
+    float* __restrict__ Gout) {
+  constexpr bool UPDATE = MODE == kModeUpdate;
   __shared__ float As[BK][BM + 4];
   __shared__ float Bs[BK][BN + 4];
   const int tid = threadIdx.x;
@@ -74,6 +76,10 @@ __global__ void __launch_bounds__(256) plain_step_kernel(
       if (i < n && b < B) {
         const int64_t idx = b * n + i;
         const float G = acc[r][c];
+        if (MODE == kModeCoupling) {
+          Gout[idx] = G;
+          continue;
+        }
         const float s = S[idx];
         const float h = hf[i];
         if (INT_E) {
@@ -105,7 +111,7 @@ __global__ void __launch_bounds__(256) plain_step_kernel(
         es += __shfl_xor_sync(0xffffffffu, es, o);
       }
     }
-    if (tx == 0 && b < B) {
+    if (MODE != kModeCoupling && tx == 0 && b < B) {
       const int64_t o = (int64_t)blockIdx.x * B + b;
       if (INT_E) {
         qpart[o] = qs;
@@ -133,7 +139,7 @@ int plain_setup(ising_ds* ds) {
   return ISING_OK;
 }
 
-int plain_step(ising_ds* ds, bool update) {
+int plain_step(ising_ds* ds, int mode, float* Gout) {
   ising_ctx* ctx = ds->ctx;
   const int64_t t = ds->t + 1;
   const float* S = ds->spins[t % 3].as<float>();
@@ -145,11 +151,13 @@ int plain_step(ising_ds* ds, bool update) {
       ds->Jf.as<float>(), ds->n, ds->B, S, Sn, ds->theta.as<float>(), ds->m.as<float>(),      \
       ds->v.as<float>(), ds->hf.as<float>(), ds->hint.as<int32_t>(), ds->k,                   \
       ds->bias.as<float2>(), ds->counters.as<long long>(), ds->qpart[ps].as<long long>(),     \
-      ds->hpart[ps].as<long long>(), ds->epart[ps].as<float>())
-  if (update) {
-    if (ds->int_energy) ISING_PLAIN(true, true); else ISING_PLAIN(true, false);
+      ds->hpart[ps].as<long long>(), ds->epart[ps].as<float>(), Gout)
+  if (mode == kModeUpdate) {
+    if (ds->int_energy) ISING_PLAIN(kModeUpdate, true); else ISING_PLAIN(kModeUpdate, false);
+  } else if (mode == kModeEnergy) {
+    if (ds->int_energy) ISING_PLAIN(kModeEnergy, true); else ISING_PLAIN(kModeEnergy, false);
   } else {
-    if (ds->int_energy) ISING_PLAIN(false, true); else ISING_PLAIN(false, false);
+    ISING_PLAIN(kModeCoupling, true);
   }
 #undef ISING_PLAIN
   ISING_CUDA(ctx, cudaGetLastError());

@@ -15,7 +15,7 @@
 namespace ising {
 namespace {
 
-template <int Q, bool UPDATE, bool INT_E, bool VAL_I8>
+template <int Q, int MODE, bool INT_E, bool VAL_I8>
 __global__ void __launch_bounds__(256) sparse_step_kernel(
     int64_t n, int64_t Bp, int64_t rows_per_block, const int32_t* __restrict__ rowptr,
     const int32_t* __restrict__ col, const void* __restrict__ val,
@@ -23,7 +23,9 @@ __global__ void __launch_bounds__(256) sparse_step_kernel(
     float* __restrict__ theta, float* __restrict__ m, float* __restrict__ v,
     const float* __restrict__ hf, const int32_t* __restrict__ hint, StepConsts k,
     const float2* __restrict__ bias, const long long* __restrict__ counters,
-    long long* __restrict__ qpart, long long* __restrict__ hpart, float* __restrict__ epart) {
+    long long* __restrict__ qpart, long long* __restrict__ hpart, float* __restrict__ epart,
+    float* __restrict__ Gout) {
+  constexpr bool UPDATE = MODE == kModeUpdate;
   constexpr int W = 8;  // warps per block
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t words = Bp / 32;
@@ -58,6 +60,13 @@ __global__ void __launch_bounds__(256) sparse_step_kernel(
 #pragma unroll
         for (int r = 0; r < 4; ++r) G[q][r] += ((nib >> r) & 1u) ? Jv : -Jv;
       }
+    }
+    if (MODE == kModeCoupling) {
+#pragma unroll
+      for (int q = 0; q < Q; ++q)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) Gout[i * Bp + cb + 128 * q + 4 * lane + r] = G[q][r];
+      continue;
     }
     const float h = hf[i];
     const int hi = hint[i];
@@ -105,6 +114,7 @@ __global__ void __launch_bounds__(256) sparse_step_kernel(
   }
 
   // energy partials: per restart, sum over this block's rows in warp order
+  if (MODE == kModeCoupling) return;
   __shared__ float red_f[INT_E ? 1 : W][INT_E ? 1 : 128 * Q];
   __shared__ int red_q[INT_E ? W : 1][INT_E ? 128 * Q : 1];
   __shared__ int red_h[INT_E ? W : 1][INT_E ? 128 * Q : 1];
@@ -181,7 +191,7 @@ int sparse_setup(ising_ds* ds) {
   return ISING_OK;
 }
 
-int sparse_step(ising_ds* ds, bool update) {
+int sparse_step(ising_ds* ds, int mode, float* Gout) {
   ising_ctx* ctx = ds->ctx;
   const int64_t t = ds->t + 1;
   const uint32_t* in = ds->spins[t % 3].as<uint32_t>();
@@ -196,13 +206,17 @@ int sparse_step(ising_ds* ds, bool update) {
       ds->sp_val.p, in, out, ds->theta.as<float>(), ds->m.as<float>(), ds->v.as<float>(),     \
       ds->hf.as<float>(), ds->hint.as<int32_t>(), ds->k, ds->bias.as<float2>(),               \
       ds->counters.as<long long>(), ds->qpart[ps].as<long long>(),                            \
-      ds->hpart[ps].as<long long>(), ds->epart[ps].as<float>())
+      ds->hpart[ps].as<long long>(), ds->epart[ps].as<float>(), Gout)
 #define ISING_SP_V(QQ, U, I) \
   do { if (ds->sp_int8) ISING_SP(QQ, U, I, true); else ISING_SP(QQ, U, I, false); } while (0)
 #define ISING_SP_I(QQ, U) \
   do { if (ds->int_energy) ISING_SP_V(QQ, U, true); else ISING_SP_V(QQ, U, false); } while (0)
-#define ISING_SP_U(QQ) \
-  do { if (update) ISING_SP_I(QQ, true); else ISING_SP_I(QQ, false); } while (0)
+#define ISING_SP_U(QQ)                                                \
+  do {                                                                \
+    if (mode == kModeUpdate) ISING_SP_I(QQ, kModeUpdate);             \
+    else if (mode == kModeEnergy) ISING_SP_I(QQ, kModeEnergy);        \
+    else ISING_SP_V(QQ, kModeCoupling, true);                         \
+  } while (0)
   switch (Q) {
     case 4: ISING_SP_U(4); break;
     case 2: ISING_SP_U(2); break;

@@ -1,13 +1,496 @@
-// K2: tensor-core form of the fused domain-selection step (placeholder until
-// the tcgen05 kernel lands).
+// K2: the fused domain-selection step (Sec. III-B) for dense J on the
+// tcgen05 tensor cores.
+//
+// G = J S is a GEMM with M = spins (J rows, 128 per tile), N = restarts (BN
+// per tile) and K = spins. J is stored as BF16 planes [n][ld] (one plane when
+// every J is an integer of magnitude <= 256, which BF16 holds exactly; three
+// planes hi + mid + lo otherwise, giving about 24 significant bits), the spins
+// S_t as BF16 +-1 [B][ld] (restart-major, K contiguous). Both operands are
+// K-major, so one TMA box of 64 elements x rows fills a 128-byte swizzled
+// shared-memory tile that tcgen05.mma reads directly.
+//
+// One persistent CTA per SM, warp-specialised:
+//   warp 0     TMA producer: STAGES-deep ring of (J tile, S tile) per k-block,
+//   warp 1     allocates tensor memory and issues the MMAs (one thread) into
+//              one of two accumulator buffers (2 x BN columns of 128 lanes),
+//   warps 4-7  epilogue: each thread owns one spin i (its TMEM lane) and walks
+//              the tile's restarts 16 columns at a time: loss field
+//              F = cQ G + cH h - mu s, gradient cos(theta) F, Adam, projection,
+//              new spin into S_{t+1}, and the energy of the input spins, summed
+//              over the tile's 128 spins by a butterfly across lanes and a
+//              fixed-order sum across the 4 warps.
+// While the epilogue drains one accumulator the MMA fills the other. Every
+// mbarrier wait is bounded; a timeout sets an error word and the CTA drains
+// its in-flight copies and MMAs, frees tensor memory and returns.
 #include "ds_internal.cuh"
+#include "tcgen05.cuh"
+
+#include <cudaTypedefs.h>
+
+#include <algorithm>
 
 namespace ising {
+namespace {
+
+constexpr int kBM = 128;
+constexpr int kBK = 64;  // BF16 elements in one 128-byte swizzled row
+constexpr int kThreads = 256;
+constexpr long long kWaitCycles = 4000000000ll;  // about 2 s
+
+struct TcArgs {
+  int64_t n, B, ld;
+  int nk;      // k-blocks per plane
+  int planes;  // 1 or 3
+  int mtiles, ntiles;
+  StepConsts k;
+  const float2* bias;
+  const long long* counters;
+  const __nv_bfloat16* S;  // S_t, [B][ld]
+  __nv_bfloat16* Snext;    // S_{t+1}
+  float* theta;
+  float* m;
+  float* v;
+  const float* hf;
+  const int32_t* hint;
+  long long* qpart;
+  long long* hpart;
+  float* epart;
+  float* Gout;  // coupling mode: [B][ld]
+  int* err;
+  int has_h;
+};
+
+template <int BN>
+struct TcLayout {
+  static constexpr uint32_t kA = kBM * kBK * 2;
+  static constexpr uint32_t kB = BN * kBK * 2;
+  static constexpr uint32_t kStage = kA + kB;
+  static constexpr int kStages = (200 * 1024) / kStage;
+  static constexpr uint32_t kBars = kStages * kStage;  // barrier block
+  static constexpr uint32_t kBytes = kBars + 256 + 1024;  // + alignment slack
+};
+
+// Sum over the 32 lanes of each of 16 columns; afterwards lanes l and l^1
+// hold the total of column 8 b4 + 4 b3 + 2 b2 + b1 (bits of l).
+template <typename T>
+__device__ __forceinline__ T column_sums16(T (&x)[16], int lane) {
+#pragma unroll
+  for (int o = 16, len = 8; o >= 2; o >>= 1, len >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int j = 0; j < len; ++j) {
+      T send = up ? x[j] : x[j + len];
+      T keep = up ? x[j + len] : x[j];
+      x[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  return x[0] + __shfl_xor_sync(0xffffffffu, x[0], 1);
+}
+
+__device__ __forceinline__ int column_of_lane(int lane) {
+  return ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
+}
+
+template <int BN, int MODE, bool INT_E>
+__global__ void __launch_bounds__(kThreads, 1)
+    tc_step_kernel(const __grid_constant__ CUtensorMap tmA0,
+                   const __grid_constant__ CUtensorMap tmA1,
+                   const __grid_constant__ CUtensorMap tmA2,
+                   const __grid_constant__ CUtensorMap tmB, const TcArgs P) {
+  using Lay = TcLayout<BN>;
+  constexpr int STAGES = Lay::kStages;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + Lay::kBars);
+  uint64_t* empty = full + STAGES;
+  uint64_t* acc_full = empty + STAGES;
+  uint64_t* acc_empty = acc_full + 2;
+  uint64_t* drain = acc_empty + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&acc_full[b], 1);
+      tc::mbar_init(&acc_empty[b], 4);
+    }
+    tc::mbar_init(drain, 1);
+    *abort_flag = 0;
+    tc::fence_barrier_init();
+  }
+  if (warp == 1) {
+    tc::tmem_alloc(tmem_slot, 2 * BN);
+    tc::fence_before_sync();
+  }
+  if (warp == 0 && lane == 0) {
+    tc::prefetch_map(&tmA0);
+    tc::prefetch_map(&tmB);
+  }
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem_base = *tmem_slot;
+  const int total = P.mtiles * P.ntiles;
+  const int nkt = P.nk * P.planes;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ------------------------------------------------ TMA producer
+      uint32_t stage = 0, phase = 0;
+      int issued = 0;
+      bool ok = true;
+      for (int tl = blockIdx.x; tl < total && ok; tl += gridDim.x) {
+        const int m0 = (tl % P.mtiles) * kBM;
+        const int n0 = (tl / P.mtiles) * BN;
+        for (int kt = 0; kt < nkt; ++kt) {
+          if (!tc::mbar_wait(&empty[stage], phase ^ 1, abort_flag, kWaitCycles)) {
+            ok = false;
+            break;
+          }
+          uint8_t* sa = smem + stage * Lay::kStage;
+          tc::mbar_expect_tx(&full[stage], Lay::kStage);
+          const int plane = kt / P.nk, kb = kt - plane * P.nk;
+          const CUtensorMap* ma = plane == 0 ? &tmA0 : (plane == 1 ? &tmA1 : &tmA2);
+          tc::tma_load_2d(sa, ma, &full[stage], kb * kBK, m0);
+          tc::tma_load_2d(sa + Lay::kA, &tmB, &full[stage], kb * kBK, n0);
+          ++issued;
+          if (++stage == STAGES) { stage = 0; phase ^= 1; }
+        }
+      }
+      if (!ok) {
+        // let the copies already issued land before the CTA exits
+        int back = issued < STAGES ? issued : STAGES;
+        uint32_t s = stage, ph = phase;
+        for (int q = 0; q < back; ++q) {
+          if (s == 0) { s = STAGES - 1; ph ^= 1; } else { --s; }
+          tc::mbar_wait(&full[s], ph, nullptr, kWaitCycles / 8);
+        }
+        atomicExch(P.err, 1);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ------------------------------------------------ MMA issuer
+      constexpr uint32_t idesc = tc::idesc_make(kBM, BN, 1u);
+      uint32_t stage = 0, phase = 0;
+      int it = 0;
+      bool ok = true;
+      for (int tl = blockIdx.x; tl < total && ok; tl += gridDim.x, ++it) {
+        const int buf = it & 1;
+        const uint32_t use = (uint32_t)(it >> 1);
+        if (!tc::mbar_wait(&acc_empty[buf], (use & 1) ^ 1, abort_flag, kWaitCycles)) {
+          ok = false;
+          break;
+        }
+        tc::fence_after_sync();
+        const uint32_t d = tmem_base + (uint32_t)(buf * BN);
+        for (int kt = 0; kt < nkt; ++kt) {
+          if (!tc::mbar_wait(&full[stage], phase, abort_flag, kWaitCycles)) {
+            ok = false;
+            break;
+          }
+          tc::fence_after_sync();
+          const uint32_t a0 = tc::smem_u32(smem + stage * Lay::kStage);
+          const uint32_t b0 = a0 + Lay::kA;
+#pragma unroll
+          for (int k = 0; k < kBK / 16; ++k) {
+            tc::mma_f16(d, tc::desc_k_sw128(a0 + 32 * k), tc::desc_k_sw128(b0 + 32 * k), idesc,
+                        (kt > 0 || k > 0) ? 1u : 0u);
+          }
+          tc::mma_commit(&empty[stage]);
+          if (++stage == STAGES) { stage = 0; phase ^= 1; }
+        }
+        if (ok) tc::mma_commit(&acc_full[buf]);
+      }
+      if (!ok) {
+        tc::mma_commit(drain);
+        tc::mbar_wait(drain, 0, nullptr, kWaitCycles / 8);
+        atomicExch(P.err, 2);
+      }
+    }
+  } else if (warp >= 4) {
+    // ------------------------------------------------ epilogue
+    const int q = warp - 4;
+    const long long t = P.counters[0] + 1;
+    const float2 bc = P.bias[t];
+    int it = 0;
+    for (int tl = blockIdx.x; tl < total; tl += gridDim.x, ++it) {
+      const int buf = it & 1;
+      const uint32_t use = (uint32_t)(it >> 1);
+      const int mt = tl % P.mtiles;
+      const int64_t m0 = (int64_t)mt * kBM;
+      const int64_t n0 = (int64_t)(tl / P.mtiles) * BN;
+      if (!tc::mbar_wait(&acc_full[buf], use & 1, abort_flag, kWaitCycles)) {
+        atomicExch(P.err, 3);
+        break;
+      }
+      tc::fence_after_sync();
+      const int64_t i = m0 + 32 * q + lane;
+      const bool row_ok = i < P.n;
+      const float h = row_ok ? P.hf[i] : 0.f;
+      const int hi = row_ok ? P.hint[i] : 0;
+      const uint32_t tbase = tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * BN);
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN; c0 += 16) {
+        uint32_t r[16];
+        tc::tmem_ld16(tbase + c0, r);
+        tc::tmem_wait_ld();
+        if (c0 + 16 == BN) {
+          tc::fence_before_sync();
+          __syncwarp();
+          if (lane == 0) tc::mbar_arrive(&acc_empty[buf]);
+        }
+        float ef[16];
+        int eq[16], eh[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          ef[j] = 0.f;
+          eq[j] = 0;
+          eh[j] = 0;
+          const int64_t b = n0 + c0 + j;
+          if (!row_ok || b >= P.B) continue;
+          const int64_t idx = b * P.ld + i;
+          const float G = __uint_as_float(r[j]);
+          if (MODE == kModeCoupling) {
+            P.Gout[idx] = G;
+            continue;
+          }
+          const float s = __bfloat162float(P.S[idx]);
+          if (INT_E) {
+            eq[j] = (int)s * __float2int_rn(G);
+            eh[j] = (int)s * hi;
+          } else {
+            ef[j] = s * fmaf(P.k.cq, G, P.k.ch * h);
+          }
+          if (MODE == kModeUpdate) {
+            const float F = fmaf(P.k.cq, G, fmaf(P.k.ch, h, -P.k.mu * s));
+            float th = P.theta[idx];
+            float mm = P.m[idx], vv = P.v[idx];
+            const float g = cosf(th) * F;
+            th = adam_update(P.k, bc.x, bc.y, g, th, mm, vv);
+            P.theta[idx] = th;
+            P.m[idx] = mm;
+            P.v[idx] = vv;
+            P.Snext[idx] = __float2bfloat16(sin_nonneg(th) ? 1.f : -1.f);
+          }
+        }
+        if (MODE != kModeCoupling) {
+          // this warp's 32 spins summed per restart; partial row 4 mt + q
+          const int64_t b = n0 + c0 + column_of_lane(lane);
+          const int64_t o = ((int64_t)mt * 4 + q) * P.B + b;
+          if (INT_E) {
+            const int tq = column_sums16(eq, lane);
+            const int th = P.has_h ? column_sums16(eh, lane) : 0;
+            if ((lane & 1) == 0 && b < P.B) {
+              P.qpart[o] = tq;
+              P.hpart[o] = th;
+            }
+          } else {
+            const float te = column_sums16(ef, lane);
+            if ((lane & 1) == 0 && b < P.B) P.epart[o] = te;
+          }
+        }
+      }
+    }
+  }
+  __syncwarp();
+  __syncthreads();
+  if (warp == 1) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem_base, 2 * BN);
+  }
+}
+
+__global__ void to_planes_kernel(const void* J, int dt, int64_t n, int64_t ld, int planes,
+                                 __nv_bfloat16* p0, __nv_bfloat16* p1, __nv_bfloat16* p2) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * ld;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / ld, k = e - i * ld;
+    const double x = k < n ? load_as_double(J, dt, i * n + k) : 0.0;
+    const __nv_bfloat16 hi = __double2bfloat16(x);
+    p0[e] = hi;
+    if (planes == 3) {
+      const double r1 = x - (double)__bfloat162float(hi);
+      const __nv_bfloat16 mid = __double2bfloat16(r1);
+      const double r2 = r1 - (double)__bfloat162float(mid);
+      p1[e] = mid;
+      p2[e] = __double2bfloat16(r2);
+    }
+  }
+}
+
+struct TcState {
+  CUtensorMap A[3];
+  CUtensorMap B[3];  // one per spin slot
+  int BN = 128;
+  size_t smem = 0;
+  int grid = 1;
+  bool maps_ready = false;
+  DevMem err;
+};
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// 2D BF16 map over rows x cols (cols contiguous, row pitch ld elements), box
+// of box_cols x box_rows with the 128-byte swizzle; out-of-range reads are 0.
+int make_map(ising_ctx* ctx, CUtensorMap* map, const void* base, int64_t cols, int64_t rows,
+             int64_t ld, int box_cols, int box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return fail(ctx, ISING_ECUDA, "cuTensorMapEncodeTiled is unavailable");
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
+  cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims,
+                  strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(ctx, ISING_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return ISING_OK;
+}
+
+template <int BN, int MODE, bool INT_E>
+int launch_bn(ising_ds* ds, TcState* st, const TcArgs& a, int slot) {
+  auto kern = tc_step_kernel<BN, MODE, INT_E>;
+  const size_t smem = TcLayout<BN>::kBytes;
+  static bool attr_set = false;  // per instantiation
+  if (!attr_set) {
+    ISING_CUDA(ds->ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem));
+    attr_set = true;
+  }
+  kern<<<st->grid, kThreads, smem, ds->ctx->stream>>>(st->A[0], st->A[1], st->A[2], st->B[slot], a);
+  ISING_CUDA(ds->ctx, cudaGetLastError());
+  return ISING_OK;
+}
+
+template <int MODE, bool INT_E>
+int launch_mode(ising_ds* ds, TcState* st, const TcArgs& a, int slot) {
+  switch (st->BN) {
+    case 256: return launch_bn<256, MODE, INT_E>(ds, st, a, slot);
+    case 64: return launch_bn<64, MODE, INT_E>(ds, st, a, slot);
+    default: return launch_bn<128, MODE, INT_E>(ds, st, a, slot);
+  }
+}
+
+}  // namespace
 
 int tc_setup(ising_ds* ds) {
-  return fail(ds->ctx, ISING_ENOTSUP, "tensor-core path not built yet");
+  ising_ctx* ctx = ds->ctx;
+  const DevInstance& I = ds->inst;
+  if (ds->prec == ISING_PREC_FP8) return fail(ctx, ISING_ENOTSUP, "FP8 path not built yet");
+  if (ctx->smem_optin < TcLayout<256>::kBytes)
+    return fail(ctx, ISING_ENOTSUP, "device lacks the shared memory the tensor-core step needs");
+  auto st = new TcState();
+  ds->tc = st;
+  ds->ld = (ds->n + 7) / 8 * 8;
+  ds->Bp = ds->B;
+  ds->spin_kind = kSpinBF16;
+  ds->mtiles = 4 * ceil_div_i(ds->n, kBM);  // one energy-partial row per epilogue warp
+  const bool exact = I.j_integer && I.j_absmax <= 256.0;
+  ds->planes = (exact || ds->prec == ISING_PREC_BF16) ? 1 : 3;
+  st->BN = ds->B <= 64 ? 64 : (ds->B >= 2048 ? 256 : 128);
+  const int64_t plane_elems = ds->n * ds->ld;
+  for (int p = 0; p < ds->planes; ++p) ISING_TRY(dev_alloc(ctx, ds->Jop[p], plane_elems * 2));
+  int g = (int)std::min<int64_t>((plane_elems + 255) / 256, (int64_t)ctx->sm_count * 16);
+  to_planes_kernel<<<g, 256, 0, ctx->stream>>>(
+      I.J.p, I.j_dtype, ds->n, ds->ld, ds->planes, ds->Jop[0].as<__nv_bfloat16>(),
+      ds->Jop[ds->planes == 3 ? 1 : 0].as<__nv_bfloat16>(),
+      ds->Jop[ds->planes == 3 ? 2 : 0].as<__nv_bfloat16>());
+  ISING_CUDA(ctx, cudaGetLastError());
+  for (int p = 0; p < 3; ++p) {
+    const void* base = ds->Jop[p < ds->planes ? p : 0].p;
+    ISING_TRY(make_map(ctx, &st->A[p], base, ds->n, ds->n, ds->ld, kBK, kBM));
+  }
+  ISING_TRY(dev_alloc(ctx, st->err, 16));
+  ISING_CUDA(ctx, cudaMemsetAsync(st->err.p, 0, 16, ctx->stream));
+  const int tiles = ceil_div_i(ds->n, kBM) * ceil_div_i(ds->B, st->BN);
+  st->grid = std::max(1, std::min(tiles, ctx->sm_count));
+  return ISING_OK;
 }
-int tc_step(ising_ds* ds, bool) { return fail(ds->ctx, ISING_ENOTSUP, "tensor-core path not built yet"); }
-void tc_release(ising_ds*) {}
+
+// The B-operand maps point at the spin buffers, which exist only after the
+// common allocation; they are built on first use.
+static int tc_maps(ising_ds* ds, TcState* st) {
+  static_assert(sizeof(CUtensorMap) == 128, "CUtensorMap size");
+  for (int s = 0; s < 3; ++s)
+    ISING_TRY(make_map(ds->ctx, &st->B[s], ds->spins[s].p, ds->n, ds->B, ds->ld, kBK, st->BN));
+  return ISING_OK;
+}
+
+int tc_run(ising_ds* ds, int mode, float* Gout) {
+  auto st = static_cast<TcState*>(ds->tc);
+  if (!st->maps_ready) {
+    ISING_TRY(tc_maps(ds, st));
+    st->maps_ready = true;
+  }
+  const int64_t t = ds->t + 1;
+  const int ps = (int)(t % 2);
+  TcArgs a;
+  a.n = ds->n;
+  a.B = ds->B;
+  a.ld = ds->ld;
+  a.nk = ceil_div_i(ds->n, kBK);
+  a.planes = ds->planes;
+  a.mtiles = ceil_div_i(ds->n, kBM);
+  a.ntiles = ceil_div_i(ds->B, st->BN);
+  a.k = ds->k;
+  a.bias = ds->bias.as<float2>();
+  a.counters = ds->counters.as<long long>();
+  a.S = ds->spins[t % 3].as<__nv_bfloat16>();
+  a.Snext = ds->spins[(t + 1) % 3].as<__nv_bfloat16>();
+  a.theta = ds->theta.as<float>();
+  a.m = ds->m.as<float>();
+  a.v = ds->v.as<float>();
+  a.hf = ds->hf.as<float>();
+  a.hint = ds->hint.as<int32_t>();
+  a.qpart = ds->qpart[ps].as<long long>();
+  a.hpart = ds->hpart[ps].as<long long>();
+  a.epart = ds->epart[ps].as<float>();
+  a.Gout = Gout;
+  a.err = st->err.as<int>();
+  a.has_h = ds->inst.has_h ? 1 : 0;
+  const int slot = (int)(t % 3);
+  const bool ie = ds->int_energy;
+  switch (mode) {
+    case kModeUpdate: return ie ? launch_mode<kModeUpdate, true>(ds, st, a, slot)
+                                : launch_mode<kModeUpdate, false>(ds, st, a, slot);
+    case kModeEnergy: return ie ? launch_mode<kModeEnergy, true>(ds, st, a, slot)
+                                : launch_mode<kModeEnergy, false>(ds, st, a, slot);
+    default: return launch_mode<kModeCoupling, true>(ds, st, a, slot);
+  }
+}
+
+int tc_step(ising_ds* ds, int mode, float* Gout) { return tc_run(ds, mode, Gout); }
+
+int tc_error(ising_ds* ds) {
+  auto st = static_cast<TcState*>(ds->tc);
+  if (!st) return ISING_OK;
+  int e = 0;
+  ISING_CUDA(ds->ctx, cudaMemcpyAsync(&e, st->err.p, 4, cudaMemcpyDeviceToHost, ds->ctx->stream));
+  ISING_CUDA(ds->ctx, cudaStreamSynchronize(ds->ctx->stream));
+  if (e) return fail(ds->ctx, ISING_ETIMEOUT, "tensor-core step: a bounded wait gave up (role %d)", e);
+  return ISING_OK;
+}
+
+void tc_release(ising_ds* ds) {
+  delete static_cast<TcState*>(ds->tc);
+  ds->tc = nullptr;
+}
 
 }  // namespace ising

@@ -35,7 +35,8 @@ INSTANCES = _instances()
 # (instance, precision) pairs exercised by the parity tests
 CASES = [("er_int", "fp32"), ("sk_float", "fp32"), ("sk_float_h", "fp32"),
          ("rand_int_h_paper", "fp32"), ("torus_small", "auto"), ("er_pendant_h", "auto"),
-         ("csr_float_h", "auto")]
+         ("csr_float_h", "auto"), ("er_int", "tc"), ("sk_float", "tc"), ("sk_float_h", "tc"),
+         ("rand_int_h_paper", "tc")]
 
 
 def _exact(inst):
@@ -115,7 +116,7 @@ def test_best_tracking_and_result(gpu_ctx, name, prec):
     s.close()
 
 
-@pytest.mark.parametrize("prec", ["fp32", "auto"])
+@pytest.mark.parametrize("prec", ["fp32", "auto", "tc"])
 def test_reaches_brute_force_ground_states(gpu_ctx, prec):
     hits = 0
     for seed in range(4):
@@ -130,7 +131,7 @@ def test_reaches_brute_force_ground_states(gpu_ctx, prec):
     assert hits >= 3
 
 
-@pytest.mark.parametrize("prec,layout", [("fp32", "dense"), ("auto", "csr")])
+@pytest.mark.parametrize("prec,layout", [("fp32", "dense"), ("auto", "csr"), ("tc", "dense")])
 @pytest.mark.parametrize("n,B,T", [(1, 1, 3), (1, 5, 0), (2, 1, 4), (129, 130, 3), (257, 3, 2)])
 def test_edge_sizes(gpu_ctx, prec, layout, n, B, T):
     inst = synth.random_sparse_instance(n, n + B, p=0.2, kind="int", h="int", layout=layout)
