@@ -77,9 +77,11 @@ __device__ __forceinline__ int8_t spin_at(const void* spins, int64_t n, int64_t 
   return (w >> (b & 31)) & 1u ? 1 : -1;
 }
 
-// Best tracking for step t = counters[0] + 1: E_t(b) from the partials of
-// slot t % 2 (added in tile order), strict < against the best so far, copy
-// of S_t for improved restarts, then the last block advances the counter.
+// Best tracking for step t = counters[0] + 1, one warp per restart: E_t(b)
+// from the partials of slot t % 2 (lane l adds rows l, l+32, ... in order,
+// then a fixed xor tree across lanes, so the sum is deterministic), strict <
+// against the best so far, copy of S_t for improved restarts; the last block
+// advances the step counter.
 template <int KIND>
 __global__ void __launch_bounds__(256) track_kernel(
     int64_t n, int64_t B, int64_t Bp, int64_t ld, int mtiles, bool int_mode, double cq,
@@ -87,37 +89,44 @@ __global__ void __launch_bounds__(256) track_kernel(
     const float* __restrict__ epart, const void* __restrict__ spins_t,
     double* __restrict__ best_E, long long* __restrict__ best_t, int8_t* __restrict__ best_s,
     double* __restrict__ last_E, long long* __restrict__ counters) {
-  __shared__ int improved;
   const long long t = counters[0] + 1;
-  for (int64_t b = blockIdx.x; b < B; b += gridDim.x) {
-    if (threadIdx.x == 0) {
-      double E;
-      if (int_mode) {
-        long long q = 0, hs = 0;
-        for (int r = 0; r < mtiles; ++r) {
-          q += qpart[(int64_t)r * Bp + b];
-          hs += hpart[(int64_t)r * Bp + b];
-        }
-        E = cq * (double)q + chs * (double)hs;
-      } else {
-        double e = 0.0;
-        for (int r = 0; r < mtiles; ++r) e += (double)epart[(int64_t)r * Bp + b];
-        E = e;
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t b = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); b < B;
+       b += warps) {
+    double E;
+    if (int_mode) {
+      long long q = 0, hs = 0;
+      for (int r = lane; r < mtiles; r += 32) {
+        q += qpart[(int64_t)r * Bp + b];
+        hs += hpart[(int64_t)r * Bp + b];
       }
+      for (int o = 16; o; o >>= 1) {
+        q += __shfl_xor_sync(0xffffffffu, q, o);
+        hs += __shfl_xor_sync(0xffffffffu, hs, o);
+      }
+      E = cq * (double)q + chs * (double)hs;
+    } else {
+      double e = 0.0;
+      for (int r = lane; r < mtiles; r += 32) e += (double)epart[(int64_t)r * Bp + b];
+      for (int o = 16; o; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+      E = e;
+    }
+    // every lane holds the same E (the xor tree is symmetric)
+    const bool improved = E < best_E[b];
+    __syncwarp();
+    if (lane == 0) {
       last_E[b] = E;
-      improved = E < best_E[b];
       if (improved) {
         best_E[b] = E;
         best_t[b] = t;
       }
     }
-    __syncthreads();
     if (improved)
-      for (int64_t i = threadIdx.x; i < n; i += blockDim.x)
-        best_s[b * n + i] = spin_at<KIND>(spins_t, n, Bp, ld, b, i);
-    __syncthreads();
+      for (int64_t i = lane; i < n; i += 32) best_s[b * n + i] = spin_at<KIND>(spins_t, n, Bp, ld, b, i);
   }
   __shared__ bool last;
+  __syncthreads();
   __threadfence();
   if (threadIdx.x == 0) {
     unsigned long long prev = atomicAdd(reinterpret_cast<unsigned long long*>(&counters[1]), 1ull);
@@ -263,7 +272,7 @@ int track_step(ising_ds* ds) {
   const int slot = (int)((ds->t + 1) % 3);
   const int pslot = (int)((ds->t + 1) % 2);
   const double chs = ds->inst.ch * std::ldexp(1.0, -ds->h_shift);
-  int grid = (int)std::min<int64_t>(ds->B, (int64_t)ctx->sm_count * 4);
+  int grid = (int)std::min<int64_t>((ds->B + 7) / 8, (int64_t)ctx->sm_count * 4);
 #define ISING_TRACK(KIND)                                                                    \
   track_kernel<KIND><<<grid, 256, 0, ctx->stream>>>(                                         \
       ds->n, ds->B, ds->Bp, ds->ld, ds->mtiles, ds->int_energy, ds->inst.cq, chs,            \
