@@ -564,6 +564,65 @@ extern "C" int ising_ds_create(ising_ctx* ctx, const ising_instance* inst,
   return ISING_OK;
 }
 
+namespace ising {
+namespace {
+
+constexpr int64_t kGraphSteps = 48;  // a multiple of the launch period 6
+
+// Captures kGraphSteps steps (step kernel + tracking) into a graph on a
+// private stream; the host step counter is restored afterwards because
+// capture does not execute anything.
+int build_graph(ising_ds* ds) {
+  ising_ctx* ctx = ds->ctx;
+  ISING_CUDA(ctx, cudaStreamCreateWithFlags(&ds->gstream, cudaStreamNonBlocking));
+  ISING_CUDA(ctx, cudaEventCreateWithFlags(&ds->gev[0], cudaEventDisableTiming));
+  ISING_CUDA(ctx, cudaEventCreateWithFlags(&ds->gev[1], cudaEventDisableTiming));
+  cudaStream_t saved = ctx->stream;
+  const int64_t t0 = ds->t;
+  ctx->stream = ds->gstream;
+  cudaGraph_t g = nullptr;
+  int rc = ISING_OK;
+  cudaError_t e = cudaStreamBeginCapture(ds->gstream, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    for (int64_t s = 0; s < kGraphSteps && rc == ISING_OK; ++s) {
+      rc = path_step_raw(ds, true);
+      if (rc == ISING_OK) rc = track_step(ds);
+      ds->t += 1;
+    }
+    e = cudaStreamEndCapture(ds->gstream, &g);
+  }
+  ds->t = t0;
+  ctx->stream = saved;
+  if (rc != ISING_OK) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) return fail(ctx, ISING_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&ds->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    ds->graph = nullptr;
+    return fail(ctx, ISING_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+  }
+  return ISING_OK;
+}
+
+// kGraphSteps steps by one graph launch, ordered after prior work on the
+// context's stream and before later work on it.
+int replay_graph(ising_ds* ds) {
+  ising_ctx* ctx = ds->ctx;
+  ISING_CUDA(ctx, cudaEventRecord(ds->gev[0], ctx->stream));
+  ISING_CUDA(ctx, cudaStreamWaitEvent(ds->gstream, ds->gev[0], 0));
+  ISING_CUDA(ctx, cudaGraphLaunch(ds->graph, ds->gstream));
+  ISING_CUDA(ctx, cudaEventRecord(ds->gev[1], ds->gstream));
+  ISING_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ds->gev[1], 0));
+  ds->t += kGraphSteps;
+  return ISING_OK;
+}
+
+}  // namespace
+}  // namespace ising
+
 extern "C" int ising_ds_run(ising_ds* ds, int64_t steps) {
   if (!ds) return ISING_EINVAL;
   ising_ctx* ctx = ds->ctx;
@@ -575,15 +634,25 @@ extern "C" int ising_ds_run(ising_ds* ds, int64_t steps) {
   ISING_CUDA(ctx, cudaEventCreate(&e0));
   ISING_CUDA(ctx, cudaEventCreate(&e1));
   ISING_CUDA(ctx, cudaEventRecord(e0, ctx->stream));
-  for (int64_t s = 0; s < todo; ++s) {
-    int rc = path_step(ds, true);
-    if (rc == ISING_OK) rc = track_step(ds);
+  const bool use_graph = !(ds->p.flags & ISING_DS_PROFILE) && todo >= 2 * kGraphSteps;
+  for (int64_t s = 0; s < todo;) {
+    int rc = ISING_OK;
+    // (t > 0: the kernels have run once outside capture, which sets their attributes)
+    if (use_graph && ds->t > 0 && ds->t % 6 == 0 && todo - s >= kGraphSteps) {
+      if (!ds->graph) rc = build_graph(ds);
+      if (rc == ISING_OK) rc = replay_graph(ds);
+      s += kGraphSteps;
+    } else {
+      rc = path_step(ds, true);
+      if (rc == ISING_OK) rc = track_step(ds);
+      ds->t += 1;
+      s += 1;
+    }
     if (rc != ISING_OK) {
       cudaEventDestroy(e0);
       cudaEventDestroy(e1);
       return rc;
     }
-    ds->t += 1;
   }
   ISING_CUDA(ctx, cudaEventRecord(e1, ctx->stream));
   ISING_CUDA(ctx, cudaEventSynchronize(e1));
@@ -785,6 +854,13 @@ extern "C" int ising_ds_destroy(ising_ds* ds) {
   if (!ds) return ISING_OK;
   if (ds->ctx) cudaStreamSynchronize(ds->ctx->stream);
   for (auto& e : ds->kev)
+    if (e) cudaEventDestroy(e);
+  if (ds->graph) cudaGraphExecDestroy(ds->graph);
+  if (ds->gstream) {
+    cudaStreamSynchronize(ds->gstream);
+    cudaStreamDestroy(ds->gstream);
+  }
+  for (auto& e : ds->gev)
     if (e) cudaEventDestroy(e);
   tc_release(ds);
   delete ds;

@@ -99,6 +99,11 @@ struct ising_ds {
   double last_best_energy = 0.0;
   int64_t last_best_restart = -1;
   ising::DevMem scratch;   // small per-session scratch (argmin etc.)
+  // CUDA graph of kGraphSteps consecutive steps starting at t % 6 == 0 (the
+  // launches repeat with period 6: spins rotate over 3 slots, partials over 2)
+  cudaGraphExec_t graph = nullptr;
+  cudaStream_t gstream = nullptr;  // private stream for capture and replay
+  cudaEvent_t gev[2] = {nullptr, nullptr};
 };
 
 namespace ising {

@@ -13,12 +13,13 @@
 //   warp 0     TMA producer: STAGES-deep ring of (J tile, S tile) per k-block,
 //   warp 1     allocates tensor memory and issues the MMAs (one thread) into
 //              one of two accumulator buffers (2 x BN columns of 128 lanes),
-//   warps 4-7  epilogue: each thread owns one spin i (its TMEM lane) and walks
-//              the tile's restarts 16 columns at a time: loss field
+//   warps 4-11 epilogue: each thread owns one spin i (its TMEM lane) and walks
+//              half of the tile's restarts 16 columns at a time (the chunk's
+//              state is loaded into registers while the TMEM read lands): loss field
 //              F = cQ G + cH h - mu s, gradient cos(theta) F, Adam, projection,
 //              new spin into S_{t+1}, and the energy of the input spins, summed
-//              over the tile's 128 spins by a butterfly across lanes and a
-//              fixed-order sum across the 4 warps.
+//              over each warp's 32 spins by a butterfly across lanes into
+//              one partial row per warp (summed in fixed order afterwards).
 // While the epilogue drains one accumulator the MMA fills the other. Every
 // mbarrier wait is bounded; a timeout sets an error word and the CTA drains
 // its in-flight copies and MMAs, frees tensor memory and returns.
@@ -34,7 +35,8 @@ namespace {
 
 constexpr int kBM = 128;
 constexpr int kBK = 64;  // BF16 elements in one 128-byte swizzled row
-constexpr int kThreads = 256;
+constexpr int kEpiWarps = 8;  // two per TMEM lane quarter, each owning half the tile's columns
+constexpr int kThreads = 128 + 32 * kEpiWarps;
 constexpr long long kWaitCycles = 4000000000ll;  // about 2 s
 
 struct TcArgs {
@@ -118,7 +120,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     for (int b = 0; b < 2; ++b) {
       tc::mbar_init(&acc_full[b], 1);
-      tc::mbar_init(&acc_empty[b], 4);
+      tc::mbar_init(&acc_empty[b], kEpiWarps);
     }
     tc::mbar_init(drain, 1);
     *abort_flag = 0;
@@ -215,16 +217,23 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else if (warp >= 4) {
     // ------------------------------------------------ epilogue
-    const int q = warp - 4;
+    const int q = warp & 3;             // TMEM lane quarter of this warp
+    const int half = (warp - 4) >> 2;   // which half of the tile's columns
+    constexpr int kCols = BN / 2;
     const long long t = P.counters[0] + 1;
     const float2 bc = P.bias[t];
+    float* __restrict__ theta = P.theta;
+    float* __restrict__ mvec = P.m;
+    float* __restrict__ vvec = P.v;
+    const __nv_bfloat16* __restrict__ Sin = P.S;
+    __nv_bfloat16* __restrict__ Sout = P.Snext;
     int it = 0;
     for (int tl = blockIdx.x; tl < total; tl += gridDim.x, ++it) {
       const int buf = it & 1;
       const uint32_t use = (uint32_t)(it >> 1);
       const int mt = tl % P.mtiles;
       const int64_t m0 = (int64_t)mt * kBM;
-      const int64_t n0 = (int64_t)(tl / P.mtiles) * BN;
+      const int64_t n0 = (int64_t)(tl / P.mtiles) * BN + half * kCols;
       if (!tc::mbar_wait(&acc_full[buf], use & 1, abort_flag, kWaitCycles)) {
         atomicExch(P.err, 3);
         break;
@@ -234,13 +243,34 @@ __global__ void __launch_bounds__(kThreads, 1)
       const bool row_ok = i < P.n;
       const float h = row_ok ? P.hf[i] : 0.f;
       const int hi = row_ok ? P.hint[i] : 0;
-      const uint32_t tbase = tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * BN);
+      const uint32_t tbase = tmem_base + ((uint32_t)(32 * q) << 16) +
+                             (uint32_t)(buf * BN + half * kCols);
 #pragma unroll 1
-      for (int c0 = 0; c0 < BN; c0 += 16) {
+      for (int c0 = 0; c0 < kCols; c0 += 16) {
         uint32_t r[16];
         tc::tmem_ld16(tbase + c0, r);
+        // state of the 16 restarts of this chunk, loaded while the TMEM read lands
+        float th[16], mm[16], vv[16], sv[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int64_t b = n0 + c0 + j;
+          const bool ok = row_ok && b < P.B;
+          const int64_t idx = b * P.ld + i;
+          th[j] = 0.f;
+          mm[j] = 0.f;
+          vv[j] = 0.f;
+          sv[j] = 0.f;
+          if (ok && MODE != kModeCoupling) {
+            sv[j] = __bfloat162float(Sin[idx]);
+            if (MODE == kModeUpdate) {
+              th[j] = theta[idx];
+              mm[j] = mvec[idx];
+              vv[j] = vvec[idx];
+            }
+          }
+        }
         tc::tmem_wait_ld();
-        if (c0 + 16 == BN) {
+        if (c0 + 16 == kCols) {
           tc::fence_before_sync();
           __syncwarp();
           if (lane == 0) tc::mbar_arrive(&acc_empty[buf]);
@@ -249,34 +279,41 @@ __global__ void __launch_bounds__(kThreads, 1)
         int eq[16], eh[16];
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
+          const int64_t b = n0 + c0 + j;
+          const bool ok = row_ok && b < P.B;
+          const int64_t idx = b * P.ld + i;
+          const float G = __uint_as_float(r[j]);
           ef[j] = 0.f;
           eq[j] = 0;
           eh[j] = 0;
-          const int64_t b = n0 + c0 + j;
-          if (!row_ok || b >= P.B) continue;
-          const int64_t idx = b * P.ld + i;
-          const float G = __uint_as_float(r[j]);
+          if (!ok) continue;
           if (MODE == kModeCoupling) {
             P.Gout[idx] = G;
             continue;
           }
-          const float s = __bfloat162float(P.S[idx]);
+          const float sj = sv[j];
           if (INT_E) {
-            eq[j] = (int)s * __float2int_rn(G);
-            eh[j] = (int)s * hi;
+            eq[j] = (int)sj * __float2int_rn(G);
+            eh[j] = (int)sj * hi;
           } else {
-            ef[j] = s * fmaf(P.k.cq, G, P.k.ch * h);
+            ef[j] = sj * fmaf(P.k.cq, G, P.k.ch * h);
           }
           if (MODE == kModeUpdate) {
-            const float F = fmaf(P.k.cq, G, fmaf(P.k.ch, h, -P.k.mu * s));
-            float th = P.theta[idx];
-            float mm = P.m[idx], vv = P.v[idx];
-            const float g = cosf(th) * F;
-            th = adam_update(P.k, bc.x, bc.y, g, th, mm, vv);
-            P.theta[idx] = th;
-            P.m[idx] = mm;
-            P.v[idx] = vv;
-            P.Snext[idx] = __float2bfloat16(sin_nonneg(th) ? 1.f : -1.f);
+            const float F = fmaf(P.k.cq, G, fmaf(P.k.ch, h, -P.k.mu * sj));
+            const float g = cosf(th[j]) * F;
+            th[j] = adam_update(P.k, bc.x, bc.y, g, th[j], mm[j], vv[j]);
+          }
+        }
+        if (MODE == kModeUpdate) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int64_t b = n0 + c0 + j;
+            if (!row_ok || b >= P.B) continue;
+            const int64_t idx = b * P.ld + i;
+            theta[idx] = th[j];
+            mvec[idx] = mm[j];
+            vvec[idx] = vv[j];
+            Sout[idx] = __float2bfloat16(sin_nonneg(th[j]) ? 1.f : -1.f);
           }
         }
         if (MODE != kModeCoupling) {
@@ -285,10 +322,10 @@ __global__ void __launch_bounds__(kThreads, 1)
           const int64_t o = ((int64_t)mt * 4 + q) * P.B + b;
           if (INT_E) {
             const int tq = column_sums16(eq, lane);
-            const int th = P.has_h ? column_sums16(eh, lane) : 0;
+            const int th2 = P.has_h ? column_sums16(eh, lane) : 0;
             if ((lane & 1) == 0 && b < P.B) {
               P.qpart[o] = tq;
-              P.hpart[o] = th;
+              P.hpart[o] = th2;
             }
           } else {
             const float te = column_sums16(ef, lane);
