@@ -245,6 +245,13 @@ int ising_ds_import_state(ising_ds* ds, const float* theta, const float* m,
  * kernel and precision (tensor cores, CUDA cores or sparse); restart-major
  * [B][n] float32 in memory `mem`. Does not advance the session. */
 int ising_ds_coupling(ising_ds* ds, float* G_out, int mem);
+/* Role timeline of the most recent step launch of a session created with
+ * ISING_DS_PROFILE (tensor-core path): 8 globaltimer stamps (ns) per CTA -
+ * start, first / last TMA issue, first MMA issue, last MMA commit, first
+ * accumulator seen by the epilogue, epilogue done, end. Copies
+ * min(cap, 8 * CTAs) values to host `out`; *count receives 8 * CTAs (0 when
+ * the path keeps no timeline). */
+int ising_ds_trace(ising_ds* ds, uint64_t* out, int64_t cap, int64_t* count);
 /* Energies E(s_t) of the spins consumed by the most recent step, [B]. */
 int ising_ds_last_energies(ising_ds* ds, double* E, int mem);
 /* Per-restart best so far: energy [B], step [B], spins [B][n] (any NULL). */

@@ -75,6 +75,7 @@ _PROTOS = {
                                       POINTER(c_int64), c_int]),
     "ising_ds_import_state": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_int]),
     "ising_ds_coupling": (c_int, [c_void_p, c_void_p, c_int]),
+    "ising_ds_trace": (c_int, [c_void_p, c_void_p, c_int64, POINTER(c_int64)]),
     "ising_ds_last_energies": (c_int, [c_void_p, c_void_p, c_int]),
     "ising_ds_restart_best": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int]),
     "ising_ds_result": (c_int, [c_void_p, c_void_p, POINTER(c_double), POINTER(DSStats), c_int]),

@@ -349,6 +349,16 @@ class Session:
         self.ctx.check(self.ctx.lib.ising_ds_coupling(self.handle, _ptr(G), L.MEM_HOST))
         return G
 
+    def trace(self) -> np.ndarray:
+        """Per-CTA role timeline of the last profiled step launch, (CTAs, 8) ns."""
+        cnt = c_int64()
+        self.ctx.check(self.ctx.lib.ising_ds_trace(self.handle, None, 0, byref(cnt)))
+        out = np.zeros(max(cnt.value, 0), np.uint64)
+        if cnt.value:
+            self.ctx.check(self.ctx.lib.ising_ds_trace(self.handle, _ptr(out), cnt.value,
+                                                       byref(cnt)))
+        return out.reshape(-1, 8)
+
     def last_energies(self) -> np.ndarray:
         E = np.empty(self.B, np.float64)
         self.ctx.check(self.ctx.lib.ising_ds_last_energies(self.handle, _ptr(E), L.MEM_HOST))

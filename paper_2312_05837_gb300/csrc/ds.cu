@@ -801,6 +801,14 @@ extern "C" int ising_ds_coupling(ising_ds* ds, float* G_out, int mem) {
   return ISING_OK;
 }
 
+extern "C" int ising_ds_trace(ising_ds* ds, uint64_t* out, int64_t cap, int64_t* count) {
+  if (!ds || !count) return ISING_EINVAL;
+  if (cap > 0 && !out) return fail(ds->ctx, ISING_EINVAL, "out is NULL");
+  *count = 0;
+  if (ds->path != ISING_PATH_TC) return ISING_OK;
+  return tc_trace(ds, out, cap, count);
+}
+
 extern "C" int ising_ds_last_energies(ising_ds* ds, double* E, int mem) {
   if (!ds) return ISING_EINVAL;
   if (!E) return fail(ds->ctx, ISING_EINVAL, "E is NULL");

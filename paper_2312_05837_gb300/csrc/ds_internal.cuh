@@ -118,6 +118,7 @@ int sparse_step(ising_ds* ds, int mode, float* Gout);
 int tc_setup(ising_ds* ds);
 int tc_step(ising_ds* ds, int mode, float* Gout);
 int tc_error(ising_ds* ds);  // ISING_ETIMEOUT if a bounded wait gave up
+int tc_trace(ising_ds* ds, uint64_t* out, int64_t cap, int64_t* count);
 void tc_release(ising_ds* ds);
 
 // Shared session services (ds.cu).

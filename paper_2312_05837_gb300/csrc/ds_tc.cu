@@ -60,7 +60,22 @@ struct TcArgs {
   float* Gout;  // coupling mode: [B][ld]
   int* err;
   int has_h;
+  unsigned long long* trace;  // per-CTA role timeline (profiling), or null
 };
+
+__device__ __forceinline__ unsigned long long now_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Trace slots per CTA (globaltimer, ns): 0 start, 1 first TMA issued, 2 last
+// TMA issued, 3 first MMA issued, 4 last MMA committed, 5 epilogue has its
+// first accumulator, 6 epilogue done (warp 4), 7 end.
+#define ISING_TRACE(slot)                                                            \
+  do {                                                                               \
+    if (P.trace) P.trace[(size_t)blockIdx.x * 8 + (slot)] = now_ns();                \
+  } while (0)
 
 template <int BN>
 struct TcLayout {
@@ -136,6 +151,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   __syncthreads();
   tc::fence_after_sync();
+  if (threadIdx.x == 0) ISING_TRACE(0);
   const uint32_t tmem_base = *tmem_slot;
   const int total = P.mtiles * P.ntiles;
   const int nkt = P.nk * P.planes;
@@ -160,10 +176,12 @@ __global__ void __launch_bounds__(kThreads, 1)
           const CUtensorMap* ma = plane == 0 ? &tmA0 : (plane == 1 ? &tmA1 : &tmA2);
           tc::tma_load_2d(sa, ma, &full[stage], kb * kBK, m0);
           tc::tma_load_2d(sa + Lay::kA, &tmB, &full[stage], kb * kBK, n0);
+          if (issued == 0) ISING_TRACE(1);
           ++issued;
           if (++stage == STAGES) { stage = 0; phase ^= 1; }
         }
       }
+      ISING_TRACE(2);
       if (!ok) {
         // let the copies already issued land before the CTA exits
         int back = issued < STAGES ? issued : STAGES;
@@ -197,6 +215,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             break;
           }
           tc::fence_after_sync();
+          if (it == 0 && kt == 0) ISING_TRACE(3);
           const uint32_t a0 = tc::smem_u32(smem + stage * Lay::kStage);
           const uint32_t b0 = a0 + Lay::kA;
 #pragma unroll
@@ -209,6 +228,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         if (ok) tc::mma_commit(&acc_full[buf]);
       }
+      ISING_TRACE(4);
       if (!ok) {
         tc::mma_commit(drain);
         tc::mbar_wait(drain, 0, nullptr, kWaitCycles / 8);
@@ -239,6 +259,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         break;
       }
       tc::fence_after_sync();
+      if (it == 0 && warp == 4 && lane == 0) ISING_TRACE(5);
       const int64_t i = m0 + 32 * q + lane;
       const bool row_ok = i < P.n;
       const float h = row_ok ? P.hf[i] : 0.f;
@@ -335,8 +356,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
   }
+  if (warp == 4 && lane == 0) ISING_TRACE(6);
   __syncwarp();
   __syncthreads();
+  if (threadIdx.x == 0) ISING_TRACE(7);
   if (warp == 1) {
     tc::fence_after_sync();
     tc::tmem_dealloc(tmem_base, 2 * BN);
@@ -369,6 +392,7 @@ struct TcState {
   int grid = 1;
   bool maps_ready = false;
   DevMem err;
+  DevMem trace;  // grid x 8 timestamps of the last profiled launch
 };
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -502,6 +526,11 @@ int tc_run(ising_ds* ds, int mode, float* Gout) {
   a.Gout = Gout;
   a.err = st->err.as<int>();
   a.has_h = ds->inst.has_h ? 1 : 0;
+  a.trace = nullptr;
+  if (ds->p.flags & ISING_DS_PROFILE) {
+    if (!st->trace.p) ISING_TRY(dev_alloc(ds->ctx, st->trace, (size_t)st->grid * 8 * 8));
+    a.trace = st->trace.as<unsigned long long>();
+  }
   const int slot = (int)(t % 3);
   const bool ie = ds->int_energy;
   switch (mode) {
@@ -522,6 +551,18 @@ int tc_error(ising_ds* ds) {
   ISING_CUDA(ds->ctx, cudaMemcpyAsync(&e, st->err.p, 4, cudaMemcpyDeviceToHost, ds->ctx->stream));
   ISING_CUDA(ds->ctx, cudaStreamSynchronize(ds->ctx->stream));
   if (e) return fail(ds->ctx, ISING_ETIMEOUT, "tensor-core step: a bounded wait gave up (role %d)", e);
+  return ISING_OK;
+}
+
+int tc_trace(ising_ds* ds, uint64_t* out, int64_t cap, int64_t* count) {
+  auto st = static_cast<TcState*>(ds->tc);
+  *count = 0;
+  if (!st || !st->trace.p) return ISING_OK;
+  const int64_t n = std::min<int64_t>(cap, (int64_t)st->grid * 8);
+  if (n > 0)
+    ISING_CUDA(ds->ctx, cudaMemcpyAsync(out, st->trace.p, n * 8, cudaMemcpyDeviceToHost, ds->ctx->stream));
+  ISING_CUDA(ds->ctx, cudaStreamSynchronize(ds->ctx->stream));
+  *count = (int64_t)st->grid * 8;
   return ISING_OK;
 }
 

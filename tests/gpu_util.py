@@ -58,7 +58,7 @@ def check_step(inst, st0, st1, last_E, p, exact_energy):
     assert np.all(np.abs(v1 - r.v) <= TOL * (v0 + 2 * (1 - p.beta2) * sc * sc) + 1e-30)
     if np.all(m0 == 0):
         g = m1 / (1 - p.beta1)
-        assert np.max(np.abs(g - r.grad) / sc) <= TOL
+        assert np.all(np.abs(g - r.grad) <= TOL * sc)
     th1 = st1["theta"].T.astype(np.float64)
     # Adam divides by sqrt(v): a gradient error dg moves theta by sens * dg,
     # sens = lr * d(mhat / (sqrt(vhat) + eps)) / dg, evaluated at the oracle's values

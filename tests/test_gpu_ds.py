@@ -154,3 +154,25 @@ def test_invalid_parameters(gpu_ctx):
     with pytest.raises(api.IsingError) as e:
         api.select_domain(gpu_ctx, INSTANCES["torus_small"], restarts=4, steps=2, precision="bf16")
     assert e.value.code == 6
+
+
+@pytest.mark.parametrize("name,prec", [("er_int", "tc"), ("sk_float_h", "tc"), ("er_int", "fp32"),
+                                       ("torus_small", "auto")])
+def test_graph_replay_equals_step_by_step(gpu_ctx, name, prec):
+    """Long runs replay a captured CUDA graph of the step loop; the state and
+    the bests must be bit-identical to launching the steps one by one."""
+    inst = INSTANCES[name]
+    T = 230
+    a = api.Session(gpu_ctx, inst, restarts=70, steps=T, seed=2, precision=prec)
+    b = api.Session(gpu_ctx, inst, restarts=70, steps=T, seed=2, precision=prec)
+    a.run(T)
+    for _ in range(T):
+        b.run(1)
+    sa, sb = a.export_state(), b.export_state()
+    for k in ["theta", "m", "v", "spins"]:
+        np.testing.assert_array_equal(sa[k], sb[k])
+    assert sa["t"] == sb["t"] == T
+    for x, y in zip(a.restart_best(), b.restart_best()):
+        np.testing.assert_array_equal(x, y)
+    a.close()
+    b.close()
