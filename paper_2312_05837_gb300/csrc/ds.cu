@@ -543,7 +543,7 @@ extern "C" int ising_ds_create(ising_ctx* ctx, const ising_instance* inst,
       ds->prec = prec;
     } else {
       ds->path = ISING_PATH_TC;
-      ds->prec = prec == ISING_PREC_AUTO ? ISING_PREC_TC : prec;
+      ds->prec = prec;  // AUTO is resolved by the tensor-core set-up
     }
     switch (ds->path) {
       case ISING_PATH_PLAIN: ISING_TRY(plain_setup(ds)); break;

@@ -13,8 +13,8 @@
 //   warp 0     TMA producer: STAGES-deep ring of (J tile, S tile) per k-block,
 //   warp 1     allocates tensor memory and issues the MMAs (one thread) into
 //              one of two accumulator buffers (2 x BN columns of 128 lanes),
-//   warps 4-11 epilogue: each thread owns one spin i (its TMEM lane) and walks
-//              half of the tile's restarts 16 columns at a time (the chunk's
+//   warps 4-19 epilogue: each thread owns one spin i (its TMEM lane) and walks
+//              a quarter of the tile's restarts 8 columns at a time (the chunk's
 //              state is loaded into registers while the TMEM read lands): loss field
 //              F = cQ G + cH h - mu s, gradient cos(theta) F, Adam, projection,
 //              new spin into S_{t+1}, and the energy of the input spins, summed
@@ -26,6 +26,7 @@
 #include "ds_internal.cuh"
 #include "tcgen05.cuh"
 
+#include <cuda_fp8.h>
 #include <cudaTypedefs.h>
 
 #include <algorithm>
@@ -34,8 +35,9 @@ namespace ising {
 namespace {
 
 constexpr int kBM = 128;
-constexpr int kBK = 64;  // BF16 elements in one 128-byte swizzled row
-constexpr int kEpiWarps = 8;  // two per TMEM lane quarter, each owning half the tile's columns
+constexpr int kRowBytes = 128;  // one 128-byte swizzled row per operand row and k-block
+constexpr int kEpiWarps = 16;  // four per TMEM lane quarter, each owning a quarter of the columns
+constexpr int kChunk = 8;      // columns per TMEM read
 constexpr int kThreads = 128 + 32 * kEpiWarps;
 constexpr long long kWaitCycles = 4000000000ll;  // about 2 s
 
@@ -47,8 +49,9 @@ struct TcArgs {
   StepConsts k;
   const float2* bias;
   const long long* counters;
-  const __nv_bfloat16* S;  // S_t, [B][ld]
-  __nv_bfloat16* Snext;    // S_{t+1}
+  const void* S;           // S_t, [B][ld] (BF16 or E4M3)
+  void* Snext;             // S_{t+1}
+  const float* rowscale;   // FP8 path with scaled rows, else null
   float* theta;
   float* m;
   float* v;
@@ -65,7 +68,7 @@ struct TcArgs {
 
 __device__ __forceinline__ unsigned long long now_ns() {
   unsigned long long t;
-  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t)::"memory");
   return t;
 }
 
@@ -79,20 +82,20 @@ __device__ __forceinline__ unsigned long long now_ns() {
 
 template <int BN>
 struct TcLayout {
-  static constexpr uint32_t kA = kBM * kBK * 2;
-  static constexpr uint32_t kB = BN * kBK * 2;
+  static constexpr uint32_t kA = kBM * kRowBytes;
+  static constexpr uint32_t kB = BN * kRowBytes;
   static constexpr uint32_t kStage = kA + kB;
   static constexpr int kStages = (200 * 1024) / kStage;
   static constexpr uint32_t kBars = kStages * kStage;  // barrier block
   static constexpr uint32_t kBytes = kBars + 256 + 1024;  // + alignment slack
 };
 
-// Sum over the 32 lanes of each of 16 columns; afterwards lanes l and l^1
-// hold the total of column 8 b4 + 4 b3 + 2 b2 + b1 (bits of l).
+// Sum over the 32 lanes of each of 8 columns; afterwards lanes l, l^1, l^2,
+// l^3 hold the total of column 4 b4 + 2 b3 + b2 (bits of l).
 template <typename T>
-__device__ __forceinline__ T column_sums16(T (&x)[16], int lane) {
+__device__ __forceinline__ T column_sums8(T (&x)[8], int lane) {
 #pragma unroll
-  for (int o = 16, len = 8; o >= 2; o >>= 1, len >>= 1) {
+  for (int o = 16, len = 4; o >= 4; o >>= 1, len >>= 1) {
     const bool up = (lane & o) != 0;
 #pragma unroll
     for (int j = 0; j < len; ++j) {
@@ -101,14 +104,15 @@ __device__ __forceinline__ T column_sums16(T (&x)[16], int lane) {
       x[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
     }
   }
-  return x[0] + __shfl_xor_sync(0xffffffffu, x[0], 1);
+  T y = x[0] + __shfl_xor_sync(0xffffffffu, x[0], 2);
+  return y + __shfl_xor_sync(0xffffffffu, y, 1);
 }
 
 __device__ __forceinline__ int column_of_lane(int lane) {
-  return ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
+  return ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
 }
 
-template <int BN, int MODE, bool INT_E>
+template <int BN, int MODE, bool INT_E, bool FP8>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_step_kernel(const __grid_constant__ CUtensorMap tmA0,
                    const __grid_constant__ CUtensorMap tmA1,
@@ -116,6 +120,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                    const __grid_constant__ CUtensorMap tmB, const TcArgs P) {
   using Lay = TcLayout<BN>;
   constexpr int STAGES = Lay::kStages;
+  constexpr int kBK = FP8 ? 128 : 64;  // elements per 128-byte row
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -196,7 +201,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp == 1) {
     if (lane == 0) {
       // ------------------------------------------------ MMA issuer
-      constexpr uint32_t idesc = tc::idesc_make(kBM, BN, 1u);
+      constexpr uint32_t idesc = tc::idesc_make(kBM, BN, FP8 ? 0u : 1u);
       uint32_t stage = 0, phase = 0;
       int it = 0;
       bool ok = true;
@@ -219,9 +224,13 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint32_t a0 = tc::smem_u32(smem + stage * Lay::kStage);
           const uint32_t b0 = a0 + Lay::kA;
 #pragma unroll
-          for (int k = 0; k < kBK / 16; ++k) {
-            tc::mma_f16(d, tc::desc_k_sw128(a0 + 32 * k), tc::desc_k_sw128(b0 + 32 * k), idesc,
-                        (kt > 0 || k > 0) ? 1u : 0u);
+          for (int k = 0; k < 4; ++k) {  // 32 bytes of K per MMA (16 BF16 or 32 E4M3)
+            if (FP8)
+              tc::mma_f8(d, tc::desc_k_sw128(a0 + 32 * k), tc::desc_k_sw128(b0 + 32 * k), idesc,
+                         (kt > 0 || k > 0) ? 1u : 0u);
+            else
+              tc::mma_f16(d, tc::desc_k_sw128(a0 + 32 * k), tc::desc_k_sw128(b0 + 32 * k), idesc,
+                          (kt > 0 || k > 0) ? 1u : 0u);
           }
           tc::mma_commit(&empty[stage]);
           if (++stage == STAGES) { stage = 0; phase ^= 1; }
@@ -238,22 +247,24 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp >= 4) {
     // ------------------------------------------------ epilogue
     const int q = warp & 3;             // TMEM lane quarter of this warp
-    const int half = (warp - 4) >> 2;   // which half of the tile's columns
-    constexpr int kCols = BN / 2;
+    const int part = (warp - 4) >> 2;   // which quarter of the tile's columns
+    constexpr int kCols = BN / 4;
     const long long t = P.counters[0] + 1;
     const float2 bc = P.bias[t];
     float* __restrict__ theta = P.theta;
     float* __restrict__ mvec = P.m;
     float* __restrict__ vvec = P.v;
-    const __nv_bfloat16* __restrict__ Sin = P.S;
-    __nv_bfloat16* __restrict__ Sout = P.Snext;
+    const __nv_bfloat16* __restrict__ Sin = static_cast<const __nv_bfloat16*>(P.S);
+    __nv_bfloat16* __restrict__ Sout = static_cast<__nv_bfloat16*>(P.Snext);
+    const uint8_t* __restrict__ Sin8 = static_cast<const uint8_t*>(P.S);
+    uint8_t* __restrict__ Sout8 = static_cast<uint8_t*>(P.Snext);
     int it = 0;
     for (int tl = blockIdx.x; tl < total; tl += gridDim.x, ++it) {
       const int buf = it & 1;
       const uint32_t use = (uint32_t)(it >> 1);
       const int mt = tl % P.mtiles;
       const int64_t m0 = (int64_t)mt * kBM;
-      const int64_t n0 = (int64_t)(tl / P.mtiles) * BN + half * kCols;
+      const int64_t n0 = (int64_t)(tl / P.mtiles) * BN + part * kCols;
       if (!tc::mbar_wait(&acc_full[buf], use & 1, abort_flag, kWaitCycles)) {
         atomicExch(P.err, 3);
         break;
@@ -264,16 +275,17 @@ __global__ void __launch_bounds__(kThreads, 1)
       const bool row_ok = i < P.n;
       const float h = row_ok ? P.hf[i] : 0.f;
       const int hi = row_ok ? P.hint[i] : 0;
+      const float rs = (P.rowscale && row_ok) ? P.rowscale[i] : 1.f;
       const uint32_t tbase = tmem_base + ((uint32_t)(32 * q) << 16) +
-                             (uint32_t)(buf * BN + half * kCols);
+                             (uint32_t)(buf * BN + part * kCols);
 #pragma unroll 1
-      for (int c0 = 0; c0 < kCols; c0 += 16) {
-        uint32_t r[16];
-        tc::tmem_ld16(tbase + c0, r);
-        // state of the 16 restarts of this chunk, loaded while the TMEM read lands
-        float th[16], mm[16], vv[16], sv[16];
+      for (int c0 = 0; c0 < kCols; c0 += kChunk) {
+        uint32_t r[kChunk];
+        tc::tmem_ld8(tbase + c0, r);
+        // state of this chunk's restarts, loaded while the TMEM read lands
+        float th[kChunk], mm[kChunk], vv[kChunk], sv[kChunk];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
+        for (int j = 0; j < kChunk; ++j) {
           const int64_t b = n0 + c0 + j;
           const bool ok = row_ok && b < P.B;
           const int64_t idx = b * P.ld + i;
@@ -282,7 +294,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           vv[j] = 0.f;
           sv[j] = 0.f;
           if (ok && MODE != kModeCoupling) {
-            sv[j] = __bfloat162float(Sin[idx]);
+            sv[j] = FP8 ? (Sin8[idx] == 0x38 ? 1.f : -1.f) : __bfloat162float(Sin[idx]);
             if (MODE == kModeUpdate) {
               th[j] = theta[idx];
               mm[j] = mvec[idx];
@@ -291,19 +303,19 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
         tc::tmem_wait_ld();
-        if (c0 + 16 == kCols) {
+        if (c0 + kChunk == kCols) {
           tc::fence_before_sync();
           __syncwarp();
           if (lane == 0) tc::mbar_arrive(&acc_empty[buf]);
         }
-        float ef[16];
-        int eq[16], eh[16];
+        float ef[kChunk];
+        int eq[kChunk], eh[kChunk];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
+        for (int j = 0; j < kChunk; ++j) {
           const int64_t b = n0 + c0 + j;
           const bool ok = row_ok && b < P.B;
           const int64_t idx = b * P.ld + i;
-          const float G = __uint_as_float(r[j]);
+          const float G = __uint_as_float(r[j]) * rs;
           ef[j] = 0.f;
           eq[j] = 0;
           eh[j] = 0;
@@ -327,14 +339,15 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         if (MODE == kModeUpdate) {
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
+          for (int j = 0; j < kChunk; ++j) {
             const int64_t b = n0 + c0 + j;
             if (!row_ok || b >= P.B) continue;
             const int64_t idx = b * P.ld + i;
             theta[idx] = th[j];
             mvec[idx] = mm[j];
             vvec[idx] = vv[j];
-            Sout[idx] = __float2bfloat16(sin_nonneg(th[j]) ? 1.f : -1.f);
+            if (FP8) Sout8[idx] = sin_nonneg(th[j]) ? 0x38 : 0xB8;
+            else Sout[idx] = __float2bfloat16(sin_nonneg(th[j]) ? 1.f : -1.f);
           }
         }
         if (MODE != kModeCoupling) {
@@ -342,15 +355,15 @@ __global__ void __launch_bounds__(kThreads, 1)
           const int64_t b = n0 + c0 + column_of_lane(lane);
           const int64_t o = ((int64_t)mt * 4 + q) * P.B + b;
           if (INT_E) {
-            const int tq = column_sums16(eq, lane);
-            const int th2 = P.has_h ? column_sums16(eh, lane) : 0;
-            if ((lane & 1) == 0 && b < P.B) {
+            const int tq = column_sums8(eq, lane);
+            const int th2 = P.has_h ? column_sums8(eh, lane) : 0;
+            if ((lane & 3) == 0 && b < P.B) {
               P.qpart[o] = tq;
               P.hpart[o] = th2;
             }
           } else {
-            const float te = column_sums16(ef, lane);
-            if ((lane & 1) == 0 && b < P.B) P.epart[o] = te;
+            const float te = column_sums8(ef, lane);
+            if ((lane & 3) == 0 && b < P.B) P.epart[o] = te;
           }
         }
       }
@@ -384,6 +397,35 @@ __global__ void to_planes_kernel(const void* J, int dt, int64_t n, int64_t ld, i
   }
 }
 
+// E4M3 plane: exact when rowscale is null (integers |J| <= 16), otherwise
+// J_ij / scale_i rounded to E4M3 with scale_i = max_j |J_ij| / 448.
+__global__ void to_fp8_kernel(const void* J, int dt, int64_t n, int64_t ld, const float* rowscale,
+                              uint8_t* out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * ld;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / ld, k = e - i * ld;
+    double x = k < n ? load_as_double(J, dt, i * n + k) : 0.0;
+    if (rowscale) x = rowscale[i] > 0.f ? x / (double)rowscale[i] : 0.0;
+    out[e] = (uint8_t)__nv_cvt_float_to_fp8((float)x, __NV_SATFINITE, __NV_E4M3);
+  }
+}
+
+__global__ void row_absmax_kernel(const void* J, int dt, int64_t n, float* scale) {
+  for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
+    double mx = 0.0;
+    for (int64_t k = threadIdx.x; k < n; k += blockDim.x) mx = fmax(mx, fabs(load_as_double(J, dt, i * n + k)));
+    for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    __shared__ double sm[32];
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mx = fmax(mx, sm[w]);
+      scale[i] = (float)(sm[0] > mx ? sm[0] : mx) / 448.f;
+    }
+    __syncthreads();
+  }
+}
+
 struct TcState {
   CUtensorMap A[3];
   CUtensorMap B[3];  // one per spin slot
@@ -391,6 +433,7 @@ struct TcState {
   size_t smem = 0;
   int grid = 1;
   bool maps_ready = false;
+  bool fp8 = false;
   DevMem err;
   DevMem trace;  // grid x 8 timestamps of the last profiled launch
 };
@@ -411,23 +454,24 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 // 2D BF16 map over rows x cols (cols contiguous, row pitch ld elements), box
 // of box_cols x box_rows with the 128-byte swizzle; out-of-range reads are 0.
 int make_map(ising_ctx* ctx, CUtensorMap* map, const void* base, int64_t cols, int64_t rows,
-             int64_t ld, int box_cols, int box_rows) {
+             int64_t ld, int box_cols, int box_rows, bool fp8) {
   auto fn = encode_fn();
   if (!fn) return fail(ctx, ISING_ECUDA, "cuTensorMapEncodeTiled is unavailable");
   cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld * (fp8 ? 1 : 2))};
   cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
   cuuint32_t es[2] = {1, 1};
-  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims,
+  CUresult r = fn(map, fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                  const_cast<void*>(base), dims,
                   strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail(ctx, ISING_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
   return ISING_OK;
 }
 
-template <int BN, int MODE, bool INT_E>
+template <int BN, int MODE, bool INT_E, bool FP8>
 int launch_bn(ising_ds* ds, TcState* st, const TcArgs& a, int slot) {
-  auto kern = tc_step_kernel<BN, MODE, INT_E>;
+  auto kern = tc_step_kernel<BN, MODE, INT_E, FP8>;
   const size_t smem = TcLayout<BN>::kBytes;
   static bool attr_set = false;  // per instantiation
   if (!attr_set) {
@@ -440,13 +484,19 @@ int launch_bn(ising_ds* ds, TcState* st, const TcArgs& a, int slot) {
   return ISING_OK;
 }
 
+template <int MODE, bool INT_E, bool FP8>
+int launch_bn_sel(ising_ds* ds, TcState* st, const TcArgs& a, int slot) {
+  switch (st->BN) {
+    case 256: return launch_bn<256, MODE, INT_E, FP8>(ds, st, a, slot);
+    case 64: return launch_bn<64, MODE, INT_E, FP8>(ds, st, a, slot);
+    default: return launch_bn<128, MODE, INT_E, FP8>(ds, st, a, slot);
+  }
+}
+
 template <int MODE, bool INT_E>
 int launch_mode(ising_ds* ds, TcState* st, const TcArgs& a, int slot) {
-  switch (st->BN) {
-    case 256: return launch_bn<256, MODE, INT_E>(ds, st, a, slot);
-    case 64: return launch_bn<64, MODE, INT_E>(ds, st, a, slot);
-    default: return launch_bn<128, MODE, INT_E>(ds, st, a, slot);
-  }
+  return st->fp8 ? launch_bn_sel<MODE, INT_E, true>(ds, st, a, slot)
+                 : launch_bn_sel<MODE, INT_E, false>(ds, st, a, slot);
 }
 
 }  // namespace
@@ -454,29 +504,49 @@ int launch_mode(ising_ds* ds, TcState* st, const TcArgs& a, int slot) {
 int tc_setup(ising_ds* ds) {
   ising_ctx* ctx = ds->ctx;
   const DevInstance& I = ds->inst;
-  if (ds->prec == ISING_PREC_FP8) return fail(ctx, ISING_ENOTSUP, "FP8 path not built yet");
   if (ctx->smem_optin < TcLayout<256>::kBytes)
     return fail(ctx, ISING_ENOTSUP, "device lacks the shared memory the tensor-core step needs");
   auto st = new TcState();
   ds->tc = st;
-  ds->ld = (ds->n + 7) / 8 * 8;
+  const bool exact16 = I.j_integer && I.j_absmax <= 16.0;
+  const bool exact256 = I.j_integer && I.j_absmax <= 256.0;
+  // AUTO: E4M3 when it holds J exactly, else the exact BF16 form
+  if (ds->prec == ISING_PREC_AUTO) ds->prec = exact16 ? ISING_PREC_FP8 : ISING_PREC_TC;
+  st->fp8 = ds->prec == ISING_PREC_FP8;
+  ds->ld = st->fp8 ? (ds->n + 15) / 16 * 16 : (ds->n + 7) / 8 * 8;
   ds->Bp = ds->B;
-  ds->spin_kind = kSpinBF16;
-  ds->mtiles = 4 * ceil_div_i(ds->n, kBM);  // one energy-partial row per epilogue warp
-  const bool exact = I.j_integer && I.j_absmax <= 256.0;
-  ds->planes = (exact || ds->prec == ISING_PREC_BF16) ? 1 : 3;
+  ds->spin_kind = st->fp8 ? kSpinE4M3 : kSpinBF16;
+  ds->mtiles = 4 * ceil_div_i(ds->n, kBM);  // one energy-partial row per epilogue lane quarter
   st->BN = ds->B <= 64 ? 64 : (ds->B >= 2048 ? 256 : 128);
   const int64_t plane_elems = ds->n * ds->ld;
-  for (int p = 0; p < ds->planes; ++p) ISING_TRY(dev_alloc(ctx, ds->Jop[p], plane_elems * 2));
   int g = (int)std::min<int64_t>((plane_elems + 255) / 256, (int64_t)ctx->sm_count * 16);
-  to_planes_kernel<<<g, 256, 0, ctx->stream>>>(
-      I.J.p, I.j_dtype, ds->n, ds->ld, ds->planes, ds->Jop[0].as<__nv_bfloat16>(),
-      ds->Jop[ds->planes == 3 ? 1 : 0].as<__nv_bfloat16>(),
-      ds->Jop[ds->planes == 3 ? 2 : 0].as<__nv_bfloat16>());
-  ISING_CUDA(ctx, cudaGetLastError());
-  for (int p = 0; p < 3; ++p) {
-    const void* base = ds->Jop[p < ds->planes ? p : 0].p;
-    ISING_TRY(make_map(ctx, &st->A[p], base, ds->n, ds->n, ds->ld, kBK, kBM));
+  if (st->fp8) {
+    ds->planes = 1;
+    ISING_TRY(dev_alloc(ctx, ds->Jop[0], plane_elems));
+    const float* rs = nullptr;
+    if (!exact16) {
+      ISING_TRY(dev_alloc(ctx, ds->rowscale, ds->n * 4));
+      row_absmax_kernel<<<(int)std::min<int64_t>(ds->n, 65535), 256, 0, ctx->stream>>>(
+          I.J.p, I.j_dtype, ds->n, ds->rowscale.as<float>());
+      rs = ds->rowscale.as<float>();
+    }
+    to_fp8_kernel<<<g, 256, 0, ctx->stream>>>(I.J.p, I.j_dtype, ds->n, ds->ld, rs,
+                                              ds->Jop[0].as<uint8_t>());
+    ISING_CUDA(ctx, cudaGetLastError());
+    for (int p = 0; p < 3; ++p)
+      ISING_TRY(make_map(ctx, &st->A[p], ds->Jop[0].p, ds->n, ds->n, ds->ld, 128, kBM, true));
+  } else {
+    ds->planes = (exact256 || ds->prec == ISING_PREC_BF16) ? 1 : 3;
+    for (int p = 0; p < ds->planes; ++p) ISING_TRY(dev_alloc(ctx, ds->Jop[p], plane_elems * 2));
+    to_planes_kernel<<<g, 256, 0, ctx->stream>>>(
+        I.J.p, I.j_dtype, ds->n, ds->ld, ds->planes, ds->Jop[0].as<__nv_bfloat16>(),
+        ds->Jop[ds->planes == 3 ? 1 : 0].as<__nv_bfloat16>(),
+        ds->Jop[ds->planes == 3 ? 2 : 0].as<__nv_bfloat16>());
+    ISING_CUDA(ctx, cudaGetLastError());
+    for (int p = 0; p < 3; ++p) {
+      const void* base = ds->Jop[p < ds->planes ? p : 0].p;
+      ISING_TRY(make_map(ctx, &st->A[p], base, ds->n, ds->n, ds->ld, 64, kBM, false));
+    }
   }
   ISING_TRY(dev_alloc(ctx, st->err, 16));
   ISING_CUDA(ctx, cudaMemsetAsync(st->err.p, 0, 16, ctx->stream));
@@ -490,7 +560,8 @@ int tc_setup(ising_ds* ds) {
 static int tc_maps(ising_ds* ds, TcState* st) {
   static_assert(sizeof(CUtensorMap) == 128, "CUtensorMap size");
   for (int s = 0; s < 3; ++s)
-    ISING_TRY(make_map(ds->ctx, &st->B[s], ds->spins[s].p, ds->n, ds->B, ds->ld, kBK, st->BN));
+    ISING_TRY(make_map(ds->ctx, &st->B[s], ds->spins[s].p, ds->n, ds->B, ds->ld,
+                       st->fp8 ? 128 : 64, st->BN, st->fp8));
   return ISING_OK;
 }
 
@@ -506,15 +577,16 @@ int tc_run(ising_ds* ds, int mode, float* Gout) {
   a.n = ds->n;
   a.B = ds->B;
   a.ld = ds->ld;
-  a.nk = ceil_div_i(ds->n, kBK);
+  a.nk = ceil_div_i(ds->n, st->fp8 ? 128 : 64);
   a.planes = ds->planes;
   a.mtiles = ceil_div_i(ds->n, kBM);
   a.ntiles = ceil_div_i(ds->B, st->BN);
   a.k = ds->k;
   a.bias = ds->bias.as<float2>();
   a.counters = ds->counters.as<long long>();
-  a.S = ds->spins[t % 3].as<__nv_bfloat16>();
-  a.Snext = ds->spins[(t + 1) % 3].as<__nv_bfloat16>();
+  a.S = ds->spins[t % 3].p;
+  a.Snext = ds->spins[(t + 1) % 3].p;
+  a.rowscale = ds->rowscale.p ? ds->rowscale.as<float>() : nullptr;
   a.theta = ds->theta.as<float>();
   a.m = ds->m.as<float>();
   a.v = ds->v.as<float>();

@@ -38,7 +38,7 @@ def test_tc_single_tile(gpu_ctx):
     _check(gpu_ctx, synth.er_dense(128, 0, p=0.2, weights="pm1"), 128, "tc", True)
 
 
-@pytest.mark.parametrize("prec", ["tc", "fp32"])
+@pytest.mark.parametrize("prec", ["tc", "fp32", "fp8", "auto"])
 @pytest.mark.parametrize("n,B", [(200, 130), (64, 1), (1, 3), (300, 512), (129, 257)])
 def test_dense_integer_exact(gpu_ctx, prec, n, B):
     inst = synth.random_sparse_instance(n, n + B, p=0.3, kind="int", h="int", layout="dense",
@@ -77,3 +77,22 @@ def test_sparse(gpu_ctx, name, B):
 
 def test_bench_size_tc(gpu_ctx):
     _check(gpu_ctx, synth.workload("er2000", 0), 1024, "tc", True)
+
+
+def test_fp8_row_scaled_error_is_e4m3_sized(gpu_ctx):
+    """Non-integer J in E4M3 with one scale per row: each coupling is rounded
+    to 3 mantissa bits (relative error <= 2^-4), so |dG_i| <= 2^-4 sum_j |J_ij|."""
+    inst = synth.sk_dense(300, 8, 1 / math.sqrt(300), np.float32)
+    s = api.Session(gpu_ctx, inst, restarts=96, steps=1, seed=1, precision="fp8")
+    st = s.export_state()
+    G = s.coupling()
+    J = ising.coupling_matrix(inst)
+    ref = (J @ st["spins"].T.astype(np.float64)).T
+    scale = np.abs(J).sum(axis=1)[None, :]
+    err = np.max(np.abs(G - ref) / scale)
+    assert 1e-4 < err <= 2.0 ** -4
+    s.close()
+
+
+def test_bench_size_fp8(gpu_ctx):
+    _check(gpu_ctx, synth.workload("er2000", 0), 1024, "fp8", True)

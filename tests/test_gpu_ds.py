@@ -36,7 +36,7 @@ INSTANCES = _instances()
 CASES = [("er_int", "fp32"), ("sk_float", "fp32"), ("sk_float_h", "fp32"),
          ("rand_int_h_paper", "fp32"), ("torus_small", "auto"), ("er_pendant_h", "auto"),
          ("csr_float_h", "auto"), ("er_int", "tc"), ("sk_float", "tc"), ("sk_float_h", "tc"),
-         ("rand_int_h_paper", "tc")]
+         ("rand_int_h_paper", "tc"), ("er_int", "fp8"), ("rand_int_h_paper", "auto")]
 
 
 def _exact(inst):
@@ -131,7 +131,8 @@ def test_reaches_brute_force_ground_states(gpu_ctx, prec):
     assert hits >= 3
 
 
-@pytest.mark.parametrize("prec,layout", [("fp32", "dense"), ("auto", "csr"), ("tc", "dense")])
+@pytest.mark.parametrize("prec,layout", [("fp32", "dense"), ("auto", "csr"), ("tc", "dense"),
+                                         ("fp8", "dense")])
 @pytest.mark.parametrize("n,B,T", [(1, 1, 3), (1, 5, 0), (2, 1, 4), (129, 130, 3), (257, 3, 2)])
 def test_edge_sizes(gpu_ctx, prec, layout, n, B, T):
     inst = synth.random_sparse_instance(n, n + B, p=0.2, kind="int", h="int", layout=layout)
@@ -157,7 +158,7 @@ def test_invalid_parameters(gpu_ctx):
 
 
 @pytest.mark.parametrize("name,prec", [("er_int", "tc"), ("sk_float_h", "tc"), ("er_int", "fp32"),
-                                       ("torus_small", "auto")])
+                                       ("torus_small", "auto"), ("er_int", "fp8")])
 def test_graph_replay_equals_step_by_step(gpu_ctx, name, prec):
     """Long runs replay a captured CUDA graph of the step loop; the state and
     the bests must be bit-identical to launching the steps one by one."""
