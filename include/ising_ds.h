@@ -163,6 +163,31 @@ int ising_version(void);
 int ising_energy(ising_ctx* ctx, const ising_instance* inst, const int8_t* spins,
                  int64_t count, double* E_out, int64_t* Q_out, int64_t* H_out, int mem);
 
+/* E(s) of `count` spin vectors like ising_energy, but allocating nothing, for
+ * callers that cannot allocate device memory (they own fixed buffers, or
+ * they run where cudaMalloc is not allowed). The paper has no counterpart:
+ * this is a deployment convenience.
+ *   - Every pointer (the instance's, spins[count][n] int8, E_out[count]
+ *     float64) must be device memory; inst->mem must be ISING_MEM_DEVICE.
+ *     No context is needed and the instance is not validated (J must be
+ *     symmetric with zero diagonal, CSR columns sorted).
+ *   - Work is queued on `stream` (a cudaStream_t, NULL = legacy default
+ *     stream) and is not waited for; E_out is ready when the stream is.
+ *   - Partial sums live in one 2 MiB static device array per device (held
+ *     until the process exits); a call needs count * ceil(n / 64) * 16
+ *     bytes of it and larger calls return ISING_EINVAL. Every call reuses the
+ *     same array: calls whose work overlaps on the GPU (two streams, or two
+ *     threads) race and give wrong results. Nothing in it has to start at
+ *     zero (each call writes every slot it reads).
+ *   - The first call made with a device current looks up the array's device
+ *     address; make that first call before any stream capture.
+ * Integer J and h (I8/I32) accumulate exactly in int64; others in FP64.
+ * Errors return a status; ising_energy_noalloc_error() describes the last
+ * one on the calling thread. */
+int ising_energy_noalloc(const ising_instance* inst, const int8_t* spins, int64_t count,
+                         double* E_out, void* stream);
+const char* ising_energy_noalloc_error(void);
+
 /* ------------------------------------------------------------------ pruning */
 
 /* Algorithm 1 (Sec. III-A) on `inst`, rounds run until nothing changes:

@@ -54,6 +54,8 @@ _PROTOS = {
     "ising_synchronize": (c_int, [c_void_p]),
     "ising_energy": (c_int, [c_void_p, POINTER(Instance), c_void_p, c_int64, c_void_p,
                              c_void_p, c_void_p, c_int]),
+    "ising_energy_noalloc": (c_int, [POINTER(Instance), c_void_p, c_int64, c_void_p, c_void_p]),
+    "ising_energy_noalloc_error": (c_char_p, []),
     "ising_prune": (c_int, [c_void_p, POINTER(Instance), c_int, POINTER(c_void_p)]),
     "ising_prune_info": (c_int, [c_void_p, POINTER(c_int64), POINTER(c_int64),
                                  POINTER(c_double), POINTER(c_double), POINTER(c_int32)]),

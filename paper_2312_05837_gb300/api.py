@@ -192,6 +192,26 @@ def energy(ctx: Context, inst, spins, exact_parts: bool = False):
     return (E, Q, H) if exact_parts else E
 
 
+def energy_noalloc(inst, spins, E_out, stream=None):
+    """ising_energy_noalloc: energies of spins[count][n] into the caller's
+    E_out[count] (all torch CUDA tensors); queues the work on `stream`
+    (default: torch's current stream) without allocating anything."""
+    lib = L.load()
+    s, keep = make_instance(inst)
+    if s.mem != L.MEM_DEVICE:
+        raise ValueError("energy_noalloc takes a device-memory instance")
+    if stream is None:
+        stream = _torch().cuda.current_stream().cuda_stream
+    elif hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    count = spins.shape[0] if spins.dim() == 2 else 1
+    rc = lib.ising_energy_noalloc(byref(s), _ptr(spins), count, _ptr(E_out), c_void_p(stream))
+    if rc != L.OK:
+        msg = lib.ising_energy_noalloc_error()
+        raise IsingError(rc, msg.decode() if msg else "")
+    return E_out
+
+
 def _outputs(n, dev):
     """Result buffers on the instance's side: (spins, energy, mem)."""
     if dev:

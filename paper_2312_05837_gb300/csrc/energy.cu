@@ -115,3 +115,150 @@ int energy_device(ising_ctx* ctx, const DevInstance& inst, const int8_t* spins, 
 }
 
 }  // namespace ising
+
+// ---------------------------------------------------------------------------
+// Energy with no allocation at all, for callers that cannot allocate device
+// memory (a host that hands the library fixed buffers, or code running where
+// cudaMalloc is not allowed, such as inside a stream being captured into a
+// CUDA graph by someone else). The per-block partial sums live in one
+// file-scope device array instead of a cudaMalloc'd buffer.
+
+namespace ising {
+namespace {
+
+// Scratch for the no-allocation energy: 2 MiB per device, held by every GPU
+// that loads this library until the process exits. One call needs
+// count * ceil(n / 64) * 16 bytes of it.
+constexpr size_t kNoAllocScratchBytes = size_t(2) << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+// Device address of g_noalloc_scratch per device, looked up by the first call
+// made with that device current (the array's host-side name is not a device
+// address).
+constexpr int kMaxDevices = 64;
+void* g_noalloc_ptr[kMaxDevices] = {};
+thread_local char g_noalloc_err[256] = "";
+
+int noalloc_fail(int code, const char* msg) {
+  snprintf(g_noalloc_err, sizeof g_noalloc_err, "%s", msg);
+  return code;
+}
+
+// The rows kernel of ising_energy with the caller's int64 CSR offsets.
+template <bool INT>
+__global__ void __launch_bounds__(256) energy_rows_i64(int64_t n, int layout, int j_dtype,
+                                                       const void* J, const int64_t* indptr,
+                                                       const int32_t* indices, const void* h,
+                                                       int h_dtype, const int8_t* __restrict__ spins,
+                                                       int64_t nchunks, void* __restrict__ qpart,
+                                                       void* __restrict__ hpart) {
+  using Acc = typename std::conditional<INT, long long, double>::type;
+  const int64_t vec = blockIdx.y;
+  const int8_t* s = spins + vec * n;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __shared__ Acc sq[8], sh[8];
+  Acc q_acc = 0, h_acc = 0;
+  for (int r = 0; r < kRowsPerBlock / 8; ++r) {
+    int64_t i = (int64_t)blockIdx.x * kRowsPerBlock + warp * (kRowsPerBlock / 8) + r;
+    if (i >= n) break;
+    Acc dot = 0;
+    if (layout == ISING_LAYOUT_DENSE) {
+      for (int64_t j = lane; j < n; j += 32) {
+        if (INT) dot += (Acc)load_as_int(J, j_dtype, i * n + j) * s[j];
+        else dot += load_as_double(J, j_dtype, i * n + j) * (double)s[j];
+      }
+    } else {
+      for (int64_t k = indptr[i] + lane; k < indptr[i + 1]; k += 32) {
+        int32_t j = indices[k];
+        if (INT) dot += (Acc)load_as_int(J, j_dtype, k) * s[j];
+        else dot += load_as_double(J, j_dtype, k) * (double)s[j];
+      }
+    }
+    for (int o = 16; o; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+    if (lane == 0) {
+      q_acc += dot * (Acc)s[i];
+      if (h) {
+        if (INT) h_acc += (Acc)load_as_int(h, h_dtype, i) * s[i];
+        else h_acc += load_as_double(h, h_dtype, i) * (double)s[i];
+      }
+    }
+  }
+  if (lane == 0) {
+    sq[warp] = q_acc;
+    sh[warp] = h_acc;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    Acc a = 0, b = 0;
+    for (int w = 0; w < 8; ++w) { a += sq[w]; b += sh[w]; }
+    static_cast<Acc*>(qpart)[vec * nchunks + blockIdx.x] = a;
+    static_cast<Acc*>(hpart)[vec * nchunks + blockIdx.x] = b;
+  }
+}
+
+}  // namespace
+}  // namespace ising
+
+extern "C" const char* ising_energy_noalloc_error(void) { return ising::g_noalloc_err; }
+
+extern "C" int ising_energy_noalloc(const ising_instance* inst, const int8_t* spins,
+                                    int64_t count, double* E_out, void* stream) {
+  using namespace ising;
+  if (!inst || !spins || !E_out) return noalloc_fail(ISING_EINVAL, "inst, spins and E_out are required");
+  if (inst->mem != ISING_MEM_DEVICE)
+    return noalloc_fail(ISING_EINVAL, "the instance must be in device memory");
+  if (inst->n < 1) return noalloc_fail(ISING_EINVAL, "n must be >= 1");
+  if (inst->layout != ISING_LAYOUT_DENSE && inst->layout != ISING_LAYOUT_CSR)
+    return noalloc_fail(ISING_EINVAL, "unknown layout");
+  if (dtype_size(inst->j_dtype) == 0 || !inst->J) return noalloc_fail(ISING_EINVAL, "bad J");
+  if (inst->layout == ISING_LAYOUT_CSR && (!inst->indptr || (!inst->indices && inst->nnz > 0)))
+    return noalloc_fail(ISING_EINVAL, "CSR needs indptr and indices");
+  if (inst->h && (dtype_size(inst->h_dtype) == 0 || inst->h_dtype == ISING_I8))
+    return noalloc_fail(ISING_EINVAL, "h_dtype must be F64, F32 or I32");
+  if (count < 0 || count > 65535) return noalloc_fail(ISING_EINVAL, "count must lie in [0, 65535]");
+  if (count == 0) return ISING_OK;
+  const int64_t nchunks = (inst->n + kRowsPerBlock - 1) / kRowsPerBlock;
+  const size_t need = (size_t)count * (size_t)nchunks * 16;
+  if (need > kNoAllocScratchBytes)
+    return noalloc_fail(ISING_EINVAL,
+                        "count * ceil(n / 64) * 16 bytes exceeds the 2 MiB no-allocation scratch");
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    cudaGetLastError();
+    return noalloc_fail(ISING_ECUDA, "no current CUDA device");
+  }
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      cudaGetLastError();
+      return noalloc_fail(ISING_ECUDA, "cudaGetSymbolAddress of the scratch array failed");
+    }
+    g_noalloc_ptr[dev] = p;
+  }
+  unsigned char* scratch = static_cast<unsigned char*>(g_noalloc_ptr[dev]);
+  void* qp = scratch;
+  void* hp = scratch + (size_t)count * nchunks * 8;
+  const bool exact = (inst->j_dtype == ISING_I8 || inst->j_dtype == ISING_I32) &&
+                     (!inst->h || inst->h_dtype == ISING_I32);
+  double cq, ch;
+  coefficients(inst, &cq, &ch);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  dim3 grid((unsigned)nchunks, (unsigned)count);
+  if (exact) {
+    energy_rows_i64<true><<<grid, 256, 0, st>>>(inst->n, inst->layout, inst->j_dtype, inst->J,
+                                                inst->indptr, inst->indices, inst->h,
+                                                inst->h_dtype, spins, nchunks, qp, hp);
+    energy_finish<true><<<(unsigned)((count + 127) / 128), 128, 0, st>>>(
+        count, nchunks, qp, hp, cq, ch, 0, E_out, nullptr, nullptr);
+  } else {
+    energy_rows_i64<false><<<grid, 256, 0, st>>>(inst->n, inst->layout, inst->j_dtype, inst->J,
+                                                 inst->indptr, inst->indices, inst->h,
+                                                 inst->h_dtype, spins, nchunks, qp, hp);
+    energy_finish<false><<<(unsigned)((count + 127) / 128), 128, 0, st>>>(
+        count, nchunks, qp, hp, cq, ch, 0, E_out, nullptr, nullptr);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return noalloc_fail(ISING_ECUDA, cudaGetErrorString(e));
+  return ISING_OK;
+}
