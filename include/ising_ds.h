@@ -119,8 +119,15 @@ typedef struct ising_ds_params {
 } ising_ds_params;
 
 /* params.flags: time every step-kernel launch with CUDA events on the
- * context's stream and report the sum in ising_ds_stats.kernel_ms. */
+ * context's stream and report the sum in ising_ds_stats.kernel_ms (for the
+ * resident tensor-core form, one launch runs many steps: kernel_ms / kernel_launches
+ * is then the time per step). */
 #define ISING_DS_PROFILE 1
+/* params.flags: keep the tensor-core path's state in device memory between
+ * steps (one launch per step) even when the resident form would fit. The
+ * resident form, used when every 128 x BN tile gets its own SM, keeps theta,
+ * m and v in tensor memory across a whole run (one cooperative launch). */
+#define ISING_DS_STREAMING 2
 
 typedef struct ising_ds_stats {
   int64_t best_restart;     /* restart holding the overall best */

@@ -22,6 +22,7 @@ PREC_AUTO, PREC_FP32_PLAIN, PREC_TC, PREC_BF16, PREC_FP8 = range(5)
 PATH_PLAIN, PATH_TC, PATH_SPARSE = range(3)
 PRUNE_ZERO_RULE = 1
 DS_PROFILE = 1
+DS_STREAMING = 2
 
 
 class Instance(ctypes.Structure):

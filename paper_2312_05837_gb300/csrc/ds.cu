@@ -259,7 +259,8 @@ int check_params(ising_ctx* ctx, const ising_ds_params* p) {
   if (!(p->beta1 >= 0 && p->beta1 < 1) || !(p->beta2 >= 0 && p->beta2 < 1))
     return fail(ctx, ISING_EINVAL, "beta1 and beta2 must lie in [0, 1)");
   if (!(p->eps > 0) || !std::isfinite(p->eps)) return fail(ctx, ISING_EINVAL, "eps must be > 0");
-  if (p->flags & ~ISING_DS_PROFILE) return fail(ctx, ISING_EINVAL, "unknown flags");
+  if (p->flags & ~(ISING_DS_PROFILE | ISING_DS_STREAMING))
+    return fail(ctx, ISING_EINVAL, "unknown flags");
   if (p->precision < ISING_PREC_AUTO || p->precision > ISING_PREC_FP8)
     return fail(ctx, ISING_EINVAL, "unknown precision %d", p->precision);
   return ISING_OK;
@@ -634,6 +635,18 @@ extern "C" int ising_ds_run(ising_ds* ds, int64_t steps) {
   ISING_CUDA(ctx, cudaEventCreate(&e0));
   ISING_CUDA(ctx, cudaEventCreate(&e1));
   ISING_CUDA(ctx, cudaEventRecord(e0, ctx->stream));
+  if (ds->path == ISING_PATH_TC && tc_is_resident(ds)) {
+    // all steps in one cooperative launch, state resident in tensor memory
+    int rc = tc_run_resident(ds, todo);
+    if (rc != ISING_OK) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return rc;
+    }
+    ds->t += todo;
+    if (ds->p.flags & ISING_DS_PROFILE) ds->kernel_launches += todo;
+    todo = 0;
+  }
   const bool use_graph = !(ds->p.flags & ISING_DS_PROFILE) && todo >= 2 * kGraphSteps;
   for (int64_t s = 0; s < todo;) {
     int rc = ISING_OK;
@@ -659,6 +672,8 @@ extern "C" int ising_ds_run(ising_ds* ds, int64_t steps) {
   float ms = 0.f;
   cudaEventElapsedTime(&ms, e0, e1);
   ds->device_ms += ms;
+  if (ds->path == ISING_PATH_TC && tc_is_resident(ds) && (ds->p.flags & ISING_DS_PROFILE))
+    ds->kernel_ms += ms;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   ISING_CUDA(ctx, cudaGetLastError());

@@ -426,6 +426,393 @@ __global__ void row_absmax_kernel(const void* J, int dt, int64_t n, float* scale
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// Resident form: when every tile of the problem fits one CTA per SM, each CTA
+// keeps its tile of theta, m, v in tensor memory for a whole run of steps
+// (TMEM columns [0, BN) accumulator, [BN, 2BN) theta, [2BN, 3BN) m,
+// [3BN, 4BN) v), so a step moves only the J / S tiles (TMA) and the new
+// spins and energy partials (global stores). Steps are separated by a grid
+// barrier (cooperative launch, so all CTAs are co-resident; the wait is
+// bounded). The epilogue warps track the best of step t-1 for this CTA's
+// slice of restarts while the tensor cores work on step t. The spins of the
+// current step are re-derived from theta (sgn+(sin theta), as they were
+// written), so the epilogue reads no state from global memory.
+
+struct TcResArgs {
+  TcArgs P;
+  int64_t steps;
+  void* spins[3];
+  long long* qpart[2];
+  long long* hpart[2];
+  float* epart[2];
+  unsigned int* gbar;  // grid barrier arrivals (zeroed before the launch)
+  int* gabort;         // raised by any CTA that gives up
+  double* best_E;
+  long long* best_t;
+  int8_t* best_s;
+  double* last_E;
+  double cq, chs;      // E = cq * Q + chs * H (integer mode)
+  int rows;            // energy-partial rows (4 per m-tile)
+  int slice;           // restarts tracked per CTA
+};
+
+template <bool FP8>
+__device__ __forceinline__ int8_t stored_spin(const void* S, int64_t idx) {
+  if (FP8) return static_cast<const uint8_t*>(S)[idx] == 0x38 ? 1 : -1;
+  return __bfloat162float(static_cast<const __nv_bfloat16*>(S)[idx]) > 0.f ? 1 : -1;
+}
+
+// Best tracking of step t for restarts [b0, b1), one warp per restart
+// (same arithmetic and order as track_kernel).
+template <bool INT_E, bool FP8>
+__device__ __forceinline__ void track_slice(const TcResArgs& R, long long t, int64_t b0, int64_t b1,
+                                            int wid, int nw, int lane) {
+  const TcArgs& P = R.P;
+  const int ps = (int)(t % 2);
+  const void* St = R.spins[t % 3];
+  for (int64_t b = b0 + wid; b < b1; b += nw) {
+    double E;
+    if (INT_E) {
+      long long q = 0, hs = 0;
+      for (int r = lane; r < R.rows; r += 32) {
+        q += R.qpart[ps][(int64_t)r * P.B + b];
+        hs += R.hpart[ps][(int64_t)r * P.B + b];
+      }
+      for (int o = 16; o; o >>= 1) {
+        q += __shfl_xor_sync(0xffffffffu, q, o);
+        hs += __shfl_xor_sync(0xffffffffu, hs, o);
+      }
+      E = R.cq * (double)q + R.chs * (double)hs;
+    } else {
+      double e = 0.0;
+      for (int r = lane; r < R.rows; r += 32) e += (double)R.epart[ps][(int64_t)r * P.B + b];
+      for (int o = 16; o; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+      E = e;
+    }
+    const bool improved = E < R.best_E[b];
+    __syncwarp();
+    if (lane == 0) {
+      R.last_E[b] = E;
+      if (improved) {
+        R.best_E[b] = E;
+        R.best_t[b] = t;
+      }
+    }
+    if (improved)
+      for (int64_t i = lane; i < P.n; i += 32) R.best_s[b * P.n + i] = stored_spin<FP8>(St, b * P.ld + i);
+  }
+}
+
+template <int BN, bool INT_E, bool FP8>
+__global__ void __launch_bounds__(kThreads, 1)
+    tc_resident_kernel(const __grid_constant__ CUtensorMap tmA0,
+                       const __grid_constant__ CUtensorMap tmA1,
+                       const __grid_constant__ CUtensorMap tmA2,
+                       const __grid_constant__ CUtensorMap tmB0,
+                       const __grid_constant__ CUtensorMap tmB1,
+                       const __grid_constant__ CUtensorMap tmB2, const TcResArgs R) {
+  const TcArgs& P = R.P;
+  using Lay = TcLayout<BN>;
+  constexpr int STAGES = Lay::kStages;
+  constexpr int kBK = FP8 ? 128 : 64;
+  constexpr uint32_t kTmemCols = 4 * BN;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + Lay::kBars);
+  uint64_t* empty = full + STAGES;
+  uint64_t* acc_full = empty + STAGES;
+  uint64_t* acc_empty = acc_full + 1;
+  uint64_t* step_done = acc_empty + 1;
+  uint64_t* go = step_done + 1;
+  uint64_t* drain = go + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&empty[s], 1);
+    }
+    tc::mbar_init(acc_full, 1);
+    tc::mbar_init(acc_empty, kEpiWarps);
+    tc::mbar_init(step_done, kEpiWarps);
+    tc::mbar_init(go, 1);
+    tc::mbar_init(drain, 1);
+    *abort_flag = 0;
+    tc::fence_barrier_init();
+  }
+  if (warp == 1) {
+    tc::tmem_alloc(tmem_slot, kTmemCols);
+    tc::fence_before_sync();
+  }
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem_base = *tmem_slot;
+  const long long t0 = P.counters[0];
+  const int64_t K = R.steps;
+  const int mt = blockIdx.x % P.mtiles;
+  const int64_t m0 = (int64_t)mt * kBM;
+  const int64_t n0 = (int64_t)(blockIdx.x / P.mtiles) * BN;
+  const int nkt = P.nk * P.planes;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ------------------------------------------------ TMA producer
+      uint32_t stage = 0, phase = 0;
+      int issued = 0;
+      bool ok = true;
+      for (int64_t s = 0; s < K && ok; ++s) {
+        if (s > 0) {
+          if (!tc::mbar_wait(go, (uint32_t)((s - 1) & 1), abort_flag, kWaitCycles)) {
+            ok = false;
+            break;
+          }
+          tc::fence_proxy_async_global();
+        }
+        const long long t = t0 + s + 1;
+        const int slot = (int)(t % 3);
+        const CUtensorMap* mb = slot == 0 ? &tmB0 : (slot == 1 ? &tmB1 : &tmB2);
+        for (int kt = 0; kt < nkt; ++kt) {
+          if (!tc::mbar_wait(&empty[stage], phase ^ 1, abort_flag, kWaitCycles)) {
+            ok = false;
+            break;
+          }
+          uint8_t* sa = smem + stage * Lay::kStage;
+          tc::mbar_expect_tx(&full[stage], Lay::kStage);
+          const int plane = kt / P.nk, kb = kt - plane * P.nk;
+          const CUtensorMap* ma = plane == 0 ? &tmA0 : (plane == 1 ? &tmA1 : &tmA2);
+          tc::tma_load_2d(sa, ma, &full[stage], kb * kBK, (int)m0);
+          tc::tma_load_2d(sa + Lay::kA, mb, &full[stage], kb * kBK, (int)n0);
+          ++issued;
+          if (++stage == STAGES) { stage = 0; phase ^= 1; }
+        }
+      }
+      if (!ok) {
+        int back = issued < STAGES ? issued : STAGES;
+        uint32_t s2 = stage, ph = phase;
+        for (int q = 0; q < back; ++q) {
+          if (s2 == 0) { s2 = STAGES - 1; ph ^= 1; } else { --s2; }
+          tc::mbar_wait(&full[s2], ph, nullptr, kWaitCycles / 8);
+        }
+        atomicExch(P.err, 1);
+        atomicExch(R.gabort, 1);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ------------------------------------------------ MMA issuer
+      constexpr uint32_t idesc = tc::idesc_make(kBM, BN, FP8 ? 0u : 1u);
+      uint32_t stage = 0, phase = 0;
+      bool ok = true;
+      for (int64_t s = 0; s < K && ok; ++s) {
+        if (!tc::mbar_wait(acc_empty, (uint32_t)((s & 1) ^ 1), abort_flag, kWaitCycles)) {
+          ok = false;
+          break;
+        }
+        tc::fence_after_sync();
+        for (int kt = 0; kt < nkt; ++kt) {
+          if (!tc::mbar_wait(&full[stage], phase, abort_flag, kWaitCycles)) {
+            ok = false;
+            break;
+          }
+          tc::fence_after_sync();
+          const uint32_t a0 = tc::smem_u32(smem + stage * Lay::kStage);
+          const uint32_t b0 = a0 + Lay::kA;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            if (FP8)
+              tc::mma_f8(tmem_base, tc::desc_k_sw128(a0 + 32 * k), tc::desc_k_sw128(b0 + 32 * k),
+                         idesc, (kt > 0 || k > 0) ? 1u : 0u);
+            else
+              tc::mma_f16(tmem_base, tc::desc_k_sw128(a0 + 32 * k), tc::desc_k_sw128(b0 + 32 * k),
+                          idesc, (kt > 0 || k > 0) ? 1u : 0u);
+          }
+          tc::mma_commit(&empty[stage]);
+          if (++stage == STAGES) { stage = 0; phase ^= 1; }
+        }
+        if (ok) tc::mma_commit(acc_full);
+      }
+      if (!ok) {
+        tc::mma_commit(drain);
+        tc::mbar_wait(drain, 0, nullptr, kWaitCycles / 8);
+        atomicExch(P.err, 2);
+        atomicExch(R.gabort, 1);
+      }
+    }
+  } else if (warp == 2) {
+    if (lane == 0) {
+      // ------------------------------------------------ grid-barrier controller
+      const unsigned int nblk = gridDim.x;
+      for (int64_t s = 0; s < K; ++s) {
+        if (!tc::mbar_wait(step_done, (uint32_t)(s & 1), abort_flag, kWaitCycles)) break;
+        __threadfence();
+        atomicAdd(R.gbar, 1u);
+        const unsigned int target = (unsigned int)(s + 1) * nblk;
+        const long long c0 = clock64();
+        bool ok = true;
+        while (tc::ld_acquire_gpu(R.gbar) < target) {
+          if (*reinterpret_cast<volatile int*>(R.gabort)) { ok = false; break; }
+          if (clock64() - c0 > kWaitCycles) {
+            atomicExch(R.gabort, 1);
+            atomicExch(P.err, 4);
+            ok = false;
+            break;
+          }
+        }
+        if (!ok) {
+          *abort_flag = 1;
+          break;
+        }
+        __threadfence();
+        tc::mbar_arrive(go);
+      }
+    }
+  } else if (warp >= 4) {
+    // ------------------------------------------------ epilogue (+ tracking)
+    const int q = warp & 3;
+    const int part = (warp - 4) >> 2;
+    constexpr int kCols = BN / 4;
+    const int64_t i = m0 + 32 * q + lane;
+    const bool row_ok = i < P.n;
+    const float h = row_ok ? P.hf[i] : 0.f;
+    const int hi = row_ok ? P.hint[i] : 0;
+    const float rs = (P.rowscale && row_ok) ? P.rowscale[i] : 1.f;
+    const int64_t nb0 = n0 + part * kCols;  // first restart of this warp's columns
+    const uint32_t lane_off = (uint32_t)(32 * q) << 16;
+    const uint32_t t_acc = tmem_base + lane_off + (uint32_t)(part * kCols);
+    const uint32_t t_th = t_acc + BN, t_m = t_acc + 2 * BN, t_v = t_acc + 3 * BN;
+    // tracked restarts of this CTA
+    const int64_t tb0 = (int64_t)blockIdx.x * R.slice;
+    const int64_t tb1 = tb0 + R.slice < P.B ? tb0 + R.slice : P.B;
+    // state of this warp's columns into tensor memory
+#pragma unroll 1
+    for (int c0 = 0; c0 < kCols; c0 += kChunk) {
+      uint32_t a[kChunk], bm[kChunk], c[kChunk];
+#pragma unroll
+      for (int j = 0; j < kChunk; ++j) {
+        const int64_t b = nb0 + c0 + j;
+        const bool ok = row_ok && b < P.B;
+        const int64_t idx = b * P.ld + i;
+        a[j] = __float_as_uint(ok ? P.theta[idx] : 0.f);
+        bm[j] = __float_as_uint(ok ? P.m[idx] : 0.f);
+        c[j] = __float_as_uint(ok ? P.v[idx] : 0.f);
+      }
+      tc::tmem_st8(t_th + c0, a);
+      tc::tmem_st8(t_m + c0, bm);
+      tc::tmem_st8(t_v + c0, c);
+    }
+    tc::tmem_wait_st();
+    bool ok = true;
+    for (int64_t s = 0; s < K && ok; ++s) {
+      const long long t = t0 + s + 1;
+      if (s > 0) {
+        if (!tc::mbar_wait(go, (uint32_t)((s - 1) & 1), abort_flag, kWaitCycles)) { ok = false; break; }
+        track_slice<INT_E, FP8>(R, t - 1, tb0, tb1, warp - 4, kEpiWarps, lane);
+      }
+      if (!tc::mbar_wait(acc_full, (uint32_t)(s & 1), abort_flag, kWaitCycles)) {
+        atomicExch(P.err, 3);
+        atomicExch(R.gabort, 1);
+        ok = false;
+        break;
+      }
+      tc::fence_after_sync();
+      const bool last = s + 1 == K;
+      const float2 bc = P.bias[t];
+      void* Sout = R.spins[(t + 1) % 3];
+      const int ps = (int)(t % 2);
+#pragma unroll 1
+      for (int c0 = 0; c0 < kCols; c0 += kChunk) {
+        uint32_t r[kChunk], th[kChunk], mm[kChunk], vv[kChunk];
+        tc::tmem_ld8(t_acc + c0, r);
+        tc::tmem_ld8(t_th + c0, th);
+        tc::tmem_ld8(t_m + c0, mm);
+        tc::tmem_ld8(t_v + c0, vv);
+        tc::tmem_wait_ld();
+        if (c0 + kChunk == kCols) {
+          tc::fence_before_sync();
+          __syncwarp();
+          if (lane == 0) tc::mbar_arrive(acc_empty);
+        }
+        float ef[kChunk];
+        int eq[kChunk], eh[kChunk];
+#pragma unroll
+        for (int j = 0; j < kChunk; ++j) {
+          const int64_t b = nb0 + c0 + j;
+          const bool okj = row_ok && b < P.B;
+          float tj = __uint_as_float(th[j]), mj = __uint_as_float(mm[j]), vj = __uint_as_float(vv[j]);
+          const float G = __uint_as_float(r[j]) * rs;
+          const float sj = sin_nonneg(tj) ? 1.f : -1.f;  // the spin this step consumed
+          ef[j] = 0.f;
+          eq[j] = 0;
+          eh[j] = 0;
+          if (okj) {
+            if (INT_E) {
+              eq[j] = (int)sj * __float2int_rn(G);
+              eh[j] = (int)sj * hi;
+            } else {
+              ef[j] = sj * fmaf(P.k.cq, G, P.k.ch * h);
+            }
+            const float F = fmaf(P.k.cq, G, fmaf(P.k.ch, h, -P.k.mu * sj));
+            const float g = cosf(tj) * F;
+            tj = adam_update(P.k, bc.x, bc.y, g, tj, mj, vj);
+            const int64_t idx = b * P.ld + i;
+            if (FP8) static_cast<uint8_t*>(Sout)[idx] = sin_nonneg(tj) ? 0x38 : 0xB8;
+            else static_cast<__nv_bfloat16*>(Sout)[idx] = __float2bfloat16(sin_nonneg(tj) ? 1.f : -1.f);
+            if (last) {
+              P.theta[idx] = tj;
+              P.m[idx] = mj;
+              P.v[idx] = vj;
+            }
+          }
+          th[j] = __float_as_uint(tj);
+          mm[j] = __float_as_uint(mj);
+          vv[j] = __float_as_uint(vj);
+        }
+        if (!last) {
+          tc::tmem_st8(t_th + c0, th);
+          tc::tmem_st8(t_m + c0, mm);
+          tc::tmem_st8(t_v + c0, vv);
+        }
+        const int64_t b = nb0 + c0 + column_of_lane(lane);
+        const int64_t o = ((int64_t)mt * 4 + q) * P.B + b;
+        if (INT_E) {
+          const int tq = column_sums8(eq, lane);
+          const int th2 = P.has_h ? column_sums8(eh, lane) : 0;
+          if ((lane & 3) == 0 && b < P.B) {
+            R.qpart[ps][o] = tq;
+            R.hpart[ps][o] = th2;
+          }
+        } else {
+          const float te = column_sums8(ef, lane);
+          if ((lane & 3) == 0 && b < P.B) R.epart[ps][o] = te;
+        }
+      }
+      tc::tmem_wait_st();
+      tc::fence_proxy_async_global();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(step_done);
+    }
+    if (ok && K > 0) {
+      // the last step's bests, once every CTA has written its partials
+      if (tc::mbar_wait(go, (uint32_t)((K - 1) & 1), abort_flag, kWaitCycles))
+        track_slice<INT_E, FP8>(R, t0 + K, tb0, tb1, warp - 4, kEpiWarps, lane);
+    }
+  }
+  __syncwarp();
+  __syncthreads();
+  if (threadIdx.x == 0 && blockIdx.x == 0 && !*abort_flag) {
+    long long* cnt = const_cast<long long*>(P.counters);
+    cnt[0] = t0 + K;
+  }
+  if (warp == 1) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem_base, kTmemCols);
+  }
+}
+
 struct TcState {
   CUtensorMap A[3];
   CUtensorMap B[3];  // one per spin slot
@@ -434,6 +821,8 @@ struct TcState {
   int grid = 1;
   bool maps_ready = false;
   bool fp8 = false;
+  bool resident = false;  // one tile per CTA, state kept in tensor memory
+  DevMem gsync;           // grid barrier counter + abort word
   DevMem err;
   DevMem trace;  // grid x 8 timestamps of the last profiled launch
 };
@@ -501,6 +890,38 @@ int launch_mode(ising_ds* ds, TcState* st, const TcArgs& a, int slot) {
 
 }  // namespace
 
+template <int BN, bool INT_E, bool FP8>
+int resident_attr(ising_ctx* ctx, int* blocks_per_sm) {
+  auto kern = tc_resident_kernel<BN, INT_E, FP8>;
+  const size_t smem = TcLayout<BN>::kBytes;
+  ISING_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  ISING_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kern, kThreads, smem));
+  return ISING_OK;
+}
+
+template <int BN, bool INT_E, bool FP8>
+int resident_launch(ising_ds* ds, TcState* st, const TcResArgs& ra) {
+  auto kern = tc_resident_kernel<BN, INT_E, FP8>;
+  void* args[] = {&st->A[0], &st->A[1], &st->A[2], &st->B[0], &st->B[1], &st->B[2],
+                  const_cast<TcResArgs*>(&ra)};
+  ISING_CUDA(ds->ctx, cudaLaunchCooperativeKernel((const void*)kern, dim3(st->grid), dim3(kThreads),
+                                                  args, TcLayout<BN>::kBytes, ds->ctx->stream));
+  return ISING_OK;
+}
+
+template <int BN>
+int resident_attr_bn(ising_ds* ds, bool fp8, int* nb) {
+  if (ds->int_energy) return fp8 ? resident_attr<BN, true, true>(ds->ctx, nb) : resident_attr<BN, true, false>(ds->ctx, nb);
+  return fp8 ? resident_attr<BN, false, true>(ds->ctx, nb) : resident_attr<BN, false, false>(ds->ctx, nb);
+}
+
+template <int BN>
+int resident_launch_bn(ising_ds* ds, TcState* st, const TcResArgs& ra) {
+  if (ds->int_energy)
+    return st->fp8 ? resident_launch<BN, true, true>(ds, st, ra) : resident_launch<BN, true, false>(ds, st, ra);
+  return st->fp8 ? resident_launch<BN, false, true>(ds, st, ra) : resident_launch<BN, false, false>(ds, st, ra);
+}
+
 int tc_setup(ising_ds* ds) {
   ising_ctx* ctx = ds->ctx;
   const DevInstance& I = ds->inst;
@@ -550,8 +971,27 @@ int tc_setup(ising_ds* ds) {
   }
   ISING_TRY(dev_alloc(ctx, st->err, 16));
   ISING_CUDA(ctx, cudaMemsetAsync(st->err.p, 0, 16, ctx->stream));
-  const int tiles = ceil_div_i(ds->n, kBM) * ceil_div_i(ds->B, st->BN);
-  st->grid = std::max(1, std::min(tiles, ctx->sm_count));
+  // resident form when every (128 x BN) tile gets its own co-resident CTA
+  if (!(ds->p.flags & ISING_DS_STREAMING)) {
+    const int mtn = ceil_div_i(ds->n, kBM);
+    for (int bn : {128, 64}) {
+      const int tiles = mtn * ceil_div_i(ds->B, bn);
+      int nb = 0;
+      ISING_TRY(bn == 128 ? resident_attr_bn<128>(ds, st->fp8, &nb) : resident_attr_bn<64>(ds, st->fp8, &nb));
+      if (nb >= 1 && tiles <= nb * ctx->sm_count) {
+        st->resident = true;
+        st->BN = bn;
+        st->grid = tiles;
+        break;
+      }
+    }
+  }
+  if (st->resident) {
+    ISING_TRY(dev_alloc(ctx, st->gsync, 16));
+  } else {
+    const int tiles = ceil_div_i(ds->n, kBM) * ceil_div_i(ds->B, st->BN);
+    st->grid = std::max(1, std::min(tiles, ctx->sm_count));
+  }
   return ISING_OK;
 }
 
@@ -614,7 +1054,70 @@ int tc_run(ising_ds* ds, int mode, float* Gout) {
   }
 }
 
-int tc_step(ising_ds* ds, int mode, float* Gout) { return tc_run(ds, mode, Gout); }
+int tc_step(ising_ds* ds, int mode, float* Gout) {
+  auto st = static_cast<TcState*>(ds->tc);
+  if (!st->resident) return tc_run(ds, mode, Gout);
+  // the streaming kernel with the resident tile shape: one CTA per tile
+  return tc_run(ds, mode, Gout);
+}
+
+bool tc_is_resident(ising_ds* ds) {
+  auto st = static_cast<TcState*>(ds->tc);
+  return st && st->resident;
+}
+
+int tc_run_resident(ising_ds* ds, int64_t steps) {
+  auto st = static_cast<TcState*>(ds->tc);
+  if (!st->maps_ready) {
+    ISING_TRY(tc_maps(ds, st));
+    st->maps_ready = true;
+  }
+  ISING_CUDA(ds->ctx, cudaMemsetAsync(st->gsync.p, 0, 16, ds->ctx->stream));
+  TcResArgs r;
+  TcArgs& a = r.P;
+  a.n = ds->n;
+  a.B = ds->B;
+  a.ld = ds->ld;
+  a.nk = ceil_div_i(ds->n, st->fp8 ? 128 : 64);
+  a.planes = ds->planes;
+  a.mtiles = ceil_div_i(ds->n, kBM);
+  a.ntiles = ceil_div_i(ds->B, st->BN);
+  a.k = ds->k;
+  a.bias = ds->bias.as<float2>();
+  a.counters = ds->counters.as<long long>();
+  a.S = nullptr;
+  a.Snext = nullptr;
+  a.rowscale = ds->rowscale.p ? ds->rowscale.as<float>() : nullptr;
+  a.theta = ds->theta.as<float>();
+  a.m = ds->m.as<float>();
+  a.v = ds->v.as<float>();
+  a.hf = ds->hf.as<float>();
+  a.hint = ds->hint.as<int32_t>();
+  a.qpart = a.hpart = nullptr;
+  a.epart = nullptr;
+  a.Gout = nullptr;
+  a.err = st->err.as<int>();
+  a.has_h = ds->inst.has_h ? 1 : 0;
+  a.trace = nullptr;
+  r.steps = steps;
+  for (int k = 0; k < 3; ++k) r.spins[k] = ds->spins[k].p;
+  for (int k = 0; k < 2; ++k) {
+    r.qpart[k] = ds->qpart[k].as<long long>();
+    r.hpart[k] = ds->hpart[k].as<long long>();
+    r.epart[k] = ds->epart[k].as<float>();
+  }
+  r.gbar = st->gsync.as<unsigned int>();
+  r.gabort = st->gsync.as<int>() + 1;
+  r.best_E = ds->best_E.as<double>();
+  r.best_t = ds->best_t.as<long long>();
+  r.best_s = ds->best_s.as<int8_t>();
+  r.last_E = ds->last_E.as<double>();
+  r.cq = ds->inst.cq;
+  r.chs = ds->inst.ch * std::ldexp(1.0, -ds->h_shift);
+  r.rows = ds->mtiles;
+  r.slice = (int)((ds->B + st->grid - 1) / st->grid);
+  return st->BN == 128 ? resident_launch_bn<128>(ds, st, r) : resident_launch_bn<64>(ds, st, r);
+}
 
 int tc_error(ising_ds* ds) {
   auto st = static_cast<TcState*>(ds->tc);

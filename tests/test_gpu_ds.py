@@ -36,17 +36,26 @@ INSTANCES = _instances()
 CASES = [("er_int", "fp32"), ("sk_float", "fp32"), ("sk_float_h", "fp32"),
          ("rand_int_h_paper", "fp32"), ("torus_small", "auto"), ("er_pendant_h", "auto"),
          ("csr_float_h", "auto"), ("er_int", "tc"), ("sk_float", "tc"), ("sk_float_h", "tc"),
-         ("rand_int_h_paper", "tc"), ("er_int", "fp8"), ("rand_int_h_paper", "auto")]
+         ("rand_int_h_paper", "tc"), ("er_int", "fp8"), ("rand_int_h_paper", "auto"),
+         ("er_int", "fp8-stream"), ("sk_float_h", "tc-stream"), ("rand_int_h_paper", "tc-stream")]
 
 
 def _exact(inst):
     return bool(inst.integer)
 
 
+def _kw(prec):
+    """'tc-stream' / 'fp8-stream' force the tensor-core path's streaming form
+    (state in device memory between steps) instead of the resident one."""
+    if prec.endswith("-stream"):
+        return dict(precision=prec[: -len("-stream")], streaming=True)
+    return dict(precision=prec)
+
+
 @pytest.mark.parametrize("name,prec", CASES)
 def test_initial_state_is_the_oracle_draw(gpu_ctx, name, prec):
     inst = INSTANCES[name]
-    s = api.Session(gpu_ctx, inst, restarts=37, steps=5, seed=9, precision=prec)
+    s = api.Session(gpu_ctx, inst, restarts=37, steps=5, seed=9, **_kw(prec))
     st = s.export_state()
     th0 = rng.theta_init(9, 37, inst.n).T
     np.testing.assert_allclose(st["theta"], th0, rtol=0, atol=4e-7)
@@ -60,7 +69,7 @@ def test_initial_state_is_the_oracle_draw(gpu_ctx, name, prec):
 def test_one_step_parity_along_a_run(gpu_ctx, name, prec, lr, mu):
     inst = INSTANCES[name]
     p = ods.Params(restarts=40, steps=12, lr=lr, mu=mu, seed=3)
-    s = api.Session(gpu_ctx, inst, restarts=40, steps=12, lr=lr, mu=mu, seed=3, precision=prec)
+    s = api.Session(gpu_ctx, inst, restarts=40, steps=12, lr=lr, mu=mu, seed=3, **_kw(prec))
     st = s.export_state()
     for _ in range(12):
         s.run(1)
@@ -79,7 +88,7 @@ def test_one_step_parity_from_an_imported_state(gpu_ctx, name, prec):
     m = (r.standard_normal((B, n)) * 0.3).astype(np.float32)
     v = (r.random((B, n)) * 0.5).astype(np.float32)
     p = ods.Params(restarts=B, steps=20, lr=0.5, mu=0.2, seed=1)
-    s = api.Session(gpu_ctx, inst, restarts=B, steps=20, lr=0.5, mu=0.2, seed=1, precision=prec)
+    s = api.Session(gpu_ctx, inst, restarts=B, steps=20, lr=0.5, mu=0.2, seed=1, **_kw(prec))
     s.import_state(th, m, v, 7)
     st0 = s.export_state()
     assert st0["t"] == 7
@@ -93,7 +102,7 @@ def test_one_step_parity_from_an_imported_state(gpu_ctx, name, prec):
 def test_best_tracking_and_result(gpu_ctx, name, prec):
     inst = INSTANCES[name]
     B, T = 24, 30
-    s = api.Session(gpu_ctx, inst, restarts=B, steps=T, lr=6.0, seed=5, precision=prec)
+    s = api.Session(gpu_ctx, inst, restarts=B, steps=T, lr=6.0, seed=5, **_kw(prec))
     trace = np.full((T + 1, B), np.inf)
     for t in range(T):
         s.run(1)
@@ -158,14 +167,15 @@ def test_invalid_parameters(gpu_ctx):
 
 
 @pytest.mark.parametrize("name,prec", [("er_int", "tc"), ("sk_float_h", "tc"), ("er_int", "fp32"),
-                                       ("torus_small", "auto"), ("er_int", "fp8")])
+                                       ("torus_small", "auto"), ("er_int", "fp8"),
+                                       ("er_int", "fp8-stream"), ("sk_float_h", "tc-stream")])
 def test_graph_replay_equals_step_by_step(gpu_ctx, name, prec):
     """Long runs replay a captured CUDA graph of the step loop; the state and
     the bests must be bit-identical to launching the steps one by one."""
     inst = INSTANCES[name]
     T = 230
-    a = api.Session(gpu_ctx, inst, restarts=70, steps=T, seed=2, precision=prec)
-    b = api.Session(gpu_ctx, inst, restarts=70, steps=T, seed=2, precision=prec)
+    a = api.Session(gpu_ctx, inst, restarts=70, steps=T, seed=2, **_kw(prec))
+    b = api.Session(gpu_ctx, inst, restarts=70, steps=T, seed=2, **_kw(prec))
     a.run(T)
     for _ in range(T):
         b.run(1)
@@ -175,5 +185,34 @@ def test_graph_replay_equals_step_by_step(gpu_ctx, name, prec):
     assert sa["t"] == sb["t"] == T
     for x, y in zip(a.restart_best(), b.restart_best()):
         np.testing.assert_array_equal(x, y)
+    a.close()
+    b.close()
+
+
+
+@pytest.mark.parametrize("name,prec,B", [("er_int", "fp8", 300), ("sk_float_h", "tc", 200),
+                                         ("rand_int_h_paper", "tc", 1)])
+def test_resident_equals_streaming(gpu_ctx, name, prec, B):
+    """The resident tensor-core form (state in tensor memory, one cooperative
+    launch for the whole run, tracking inside) gives the same state and bests
+    bit for bit as the streaming form (one launch per step)."""
+    inst = INSTANCES[name]
+    T = 57
+    a = api.Session(gpu_ctx, inst, restarts=B, steps=T, seed=4, precision=prec)
+    b = api.Session(gpu_ctx, inst, restarts=B, steps=T, seed=4, precision=prec, streaming=True)
+    a.run(20)
+    a.run(T - 20)
+    b.run(T)
+    sa, sb = a.export_state(), b.export_state()
+    for k in ["theta", "m", "v", "spins"]:
+        np.testing.assert_array_equal(sa[k], sb[k])
+    for x, y in zip(a.restart_best(), b.restart_best()):
+        np.testing.assert_array_equal(x, y)
+    np.testing.assert_array_equal(a.last_energies(), b.last_energies())
+    a.finish()
+    b.finish()
+    ra, rb = a.result(), b.result()
+    assert ra["best_energy"] == rb["best_energy"]
+    np.testing.assert_array_equal(ra["best_spins"], rb["best_spins"])
     a.close()
     b.close()
