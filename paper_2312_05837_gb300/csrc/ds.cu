@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(256) track_kernel(
     double chs, const long long* __restrict__ qpart, const long long* __restrict__ hpart,
     const float* __restrict__ epart, const void* __restrict__ spins_t,
     double* __restrict__ best_E, long long* __restrict__ best_t, int8_t* __restrict__ best_s,
-    double* __restrict__ last_E, long long* __restrict__ counters) {
+    double* __restrict__ last_E, long long* __restrict__ counters, int64_t bs_ld) {
   const long long t = counters[0] + 1;
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -122,8 +122,12 @@ __global__ void __launch_bounds__(256) track_kernel(
         best_t[b] = t;
       }
     }
-    if (improved)
-      for (int64_t i = lane; i < n; i += 32) best_s[b * n + i] = spin_at<KIND>(spins_t, n, Bp, ld, b, i);
+    if (improved) {
+      if (KIND == kSpinBits)
+        for (int64_t i = lane; i < n; i += 32) best_s[b * bs_ld + i] = spin_at<KIND>(spins_t, n, Bp, ld, b, i);
+      else
+        copy_spin_row_dense<KIND>(best_s + b * bs_ld, spins_t, n, ld, b, lane);
+    }
   }
   __shared__ bool last;
   __syncthreads();
@@ -280,7 +284,7 @@ int track_step(ising_ds* ds) {
       ds->qpart[pslot].as<long long>(), ds->hpart[pslot].as<long long>(),                    \
       ds->epart[pslot].as<float>(), ds->spins[slot].p, ds->best_E.as<double>(),              \
       ds->best_t.as<long long>(), ds->best_s.as<int8_t>(), ds->last_E.as<double>(),          \
-      ds->counters.as<long long>())
+      ds->counters.as<long long>(), ds->bs_ld)
   switch (ds->spin_kind) {
     case kSpinF32: ISING_TRACK(kSpinF32); break;
     case kSpinBF16: ISING_TRACK(kSpinBF16); break;
@@ -358,7 +362,8 @@ int common_alloc(ising_ds* ds) {
   }
   ISING_TRY(dev_alloc(ctx, ds->best_E, B * 8));
   ISING_TRY(dev_alloc(ctx, ds->best_t, B * 8));
-  ISING_TRY(dev_alloc(ctx, ds->best_s, (size_t)B * n));
+  ds->bs_ld = (n + 15) / 16 * 16;
+  ISING_TRY(dev_alloc(ctx, ds->best_s, (size_t)B * ds->bs_ld));
   ISING_TRY(dev_alloc(ctx, ds->last_E, B * 8));
   ISING_TRY(dev_alloc(ctx, ds->counters, 16));
   ISING_TRY(dev_alloc(ctx, ds->scratch, 64));
@@ -366,7 +371,7 @@ int common_alloc(ising_ds* ds) {
   fill_double<<<grid1d(ctx, B), 256, 0, ctx->stream>>>(ds->last_E.as<double>(), B, INFINITY);
   ISING_CUDA(ctx, cudaGetLastError());
   ISING_CUDA(ctx, cudaMemsetAsync(ds->best_t.p, 0, B * 8, ctx->stream));
-  ISING_CUDA(ctx, cudaMemsetAsync(ds->best_s.p, 0, (size_t)B * n, ctx->stream));
+  ISING_CUDA(ctx, cudaMemsetAsync(ds->best_s.p, 0, (size_t)B * ds->bs_ld, ctx->stream));
   ISING_CUDA(ctx, cudaMemsetAsync(ds->counters.p, 0, 16, ctx->stream));
   // Adam bias corrections for t = 0 .. T + 1 (entry 0 unused)
   std::vector<float> bias((size_t)(ds->T + 2) * 2);
@@ -491,7 +496,7 @@ int select_best(ising_ds* ds) {
   ISING_TRY(dev_alloc(ctx, rows, cand.size() * ds->n));
   ISING_TRY(dev_alloc(ctx, E, cand.size() * 8));
   for (size_t c = 0; c < cand.size(); ++c)
-    ISING_CUDA(ctx, cudaMemcpyAsync(rows.as<int8_t>() + c * ds->n, ds->best_s.as<int8_t>() + cand[c] * ds->n,
+    ISING_CUDA(ctx, cudaMemcpyAsync(rows.as<int8_t>() + c * ds->n, ds->best_s.as<int8_t>() + cand[c] * ds->bs_ld,
                                     ds->n, cudaMemcpyDeviceToDevice, ctx->stream));
   ISING_TRY(energy_device(ctx, ds->inst, rows.as<int8_t>(), (int64_t)cand.size(), E.as<double>(),
                           nullptr, nullptr));
@@ -837,7 +842,11 @@ extern "C" int ising_ds_restart_best(ising_ds* ds, double* E, int64_t* step, int
   if (!ds) return ISING_EINVAL;
   if (E) ISING_TRY(copy_out(ds->ctx, E, ds->best_E.p, ds->B * 8, mem));
   if (step) ISING_TRY(copy_out(ds->ctx, step, ds->best_t.p, ds->B * 8, mem));
-  if (spins) ISING_TRY(copy_out(ds->ctx, spins, ds->best_s.p, (size_t)ds->B * ds->n, mem));
+  if (spins)
+    ISING_CUDA(ds->ctx, cudaMemcpy2DAsync(spins, ds->n, ds->best_s.p, ds->bs_ld, ds->n, ds->B,
+                                          mem == ISING_MEM_HOST ? cudaMemcpyDeviceToHost
+                                                                : cudaMemcpyDeviceToDevice,
+                                          ds->ctx->stream));
   ISING_CUDA(ds->ctx, cudaStreamSynchronize(ds->ctx->stream));
   return ISING_OK;
 }
@@ -849,7 +858,7 @@ extern "C" int ising_ds_result(ising_ds* ds, int8_t* best_spins, double* best_en
   if (!ds->finished) ISING_TRY(select_best(ds));
   const int64_t b = ds->best_restart;
   if (best_spins)
-    ISING_TRY(copy_out(ctx, best_spins, ds->best_s.as<int8_t>() + b * ds->n, ds->n, mem));
+    ISING_TRY(copy_out(ctx, best_spins, ds->best_s.as<int8_t>() + b * ds->bs_ld, ds->n, mem));
   if (best_energy) {
     if (mem == ISING_MEM_HOST) *best_energy = ds->best_energy;
     else ISING_CUDA(ctx, cudaMemcpyAsync(best_energy, &ds->best_energy, 8, cudaMemcpyHostToDevice, ctx->stream));

@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(256) plain_step_kernel(
         if (UPDATE) {
           const float F = fmaf(k.cq, G, fmaf(k.ch, h, -k.mu * s));
           float th = theta[idx];
-          const float g = cosf(th) * F;
+          const float g = cos_proj(th) * F;
           float mm = m[idx], vv = v[idx];
           th = adam_update(k, bc.x, bc.y, g, th, mm, vv);
           theta[idx] = th;

@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(256) sparse_step_kernel(
         }
         if (UPDATE) {
           const float F = fmaf(k.cq, G[q][r], fmaf(k.ch, h, -k.mu * s));
-          const float g = cosf(thp[r]) * F;
+          const float g = cos_proj(thp[r]) * F;
           thp[r] = adam_update(k, bc.x, bc.y, g, thp[r], mp[r], vp[r]);
           if (sin_nonneg(thp[r])) newnib |= 1u << r;
         }

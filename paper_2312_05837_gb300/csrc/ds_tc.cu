@@ -333,7 +333,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           if (MODE == kModeUpdate) {
             const float F = fmaf(P.k.cq, G, fmaf(P.k.ch, h, -P.k.mu * sj));
-            const float g = cosf(th[j]) * F;
+            const float g = cos_proj(th[j]) * F;
             th[j] = adam_update(P.k, bc.x, bc.y, g, th[j], mm[j], vv[j]);
           }
         }
@@ -452,16 +452,11 @@ struct TcResArgs {
   long long* best_t;
   int8_t* best_s;
   double* last_E;
+  int64_t bs_ld;       // row pitch of best_s
   double cq, chs;      // E = cq * Q + chs * H (integer mode)
   int rows;            // energy-partial rows (4 per m-tile)
   int slice;           // restarts tracked per CTA
 };
-
-template <bool FP8>
-__device__ __forceinline__ int8_t stored_spin(const void* S, int64_t idx) {
-  if (FP8) return static_cast<const uint8_t*>(S)[idx] == 0x38 ? 1 : -1;
-  return __bfloat162float(static_cast<const __nv_bfloat16*>(S)[idx]) > 0.f ? 1 : -1;
-}
 
 // Best tracking of step t for restarts [b0, b1), one warp per restart
 // (same arithmetic and order as track_kernel).
@@ -500,7 +495,7 @@ __device__ __forceinline__ void track_slice(const TcResArgs& R, long long t, int
       }
     }
     if (improved)
-      for (int64_t i = lane; i < P.n; i += 32) R.best_s[b * P.n + i] = stored_spin<FP8>(St, b * P.ld + i);
+      copy_spin_row_dense<FP8 ? kSpinE4M3 : kSpinBF16>(R.best_s + b * R.bs_ld, St, P.n, P.ld, b, lane);
   }
 }
 
@@ -557,6 +552,15 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int64_t m0 = (int64_t)mt * kBM;
   const int64_t n0 = (int64_t)(blockIdx.x / P.mtiles) * BN;
   const int nkt = P.nk * P.planes;
+  // role timeline of one step (profiling): 0 producer starts the step, 1 last
+  // TMA issued, 2 last MMA committed, 3 epilogue finished tracking, 4 epilogue
+  // has the accumulator, 5 epilogue done, 6 controller saw the CTA done,
+  // 7 grid barrier passed
+  const int64_t rec = K >= 2 ? K - 2 : 0;
+#define ISING_RTRACE(slot, s)                                                     \
+  do {                                                                            \
+    if (P.trace && (s) == rec) P.trace[(size_t)blockIdx.x * 8 + (slot)] = now_ns(); \
+  } while (0)
 
   if (warp == 0) {
     if (lane == 0) {
@@ -572,6 +576,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           tc::fence_proxy_async_global();
         }
+        ISING_RTRACE(0, s);
         const long long t = t0 + s + 1;
         const int slot = (int)(t % 3);
         const CUtensorMap* mb = slot == 0 ? &tmB0 : (slot == 1 ? &tmB1 : &tmB2);
@@ -589,6 +594,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           ++issued;
           if (++stage == STAGES) { stage = 0; phase ^= 1; }
         }
+        ISING_RTRACE(1, s);
       }
       if (!ok) {
         int back = issued < STAGES ? issued : STAGES;
@@ -634,6 +640,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (++stage == STAGES) { stage = 0; phase ^= 1; }
         }
         if (ok) tc::mma_commit(acc_full);
+        ISING_RTRACE(2, s);
       }
       if (!ok) {
         tc::mma_commit(drain);
@@ -648,6 +655,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const unsigned int nblk = gridDim.x;
       for (int64_t s = 0; s < K; ++s) {
         if (!tc::mbar_wait(step_done, (uint32_t)(s & 1), abort_flag, kWaitCycles)) break;
+        ISING_RTRACE(6, s);
         __threadfence();
         atomicAdd(R.gbar, 1u);
         const unsigned int target = (unsigned int)(s + 1) * nblk;
@@ -667,6 +675,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           break;
         }
         __threadfence();
+        ISING_RTRACE(7, s);
         tc::mbar_arrive(go);
       }
     }
@@ -712,6 +721,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (!tc::mbar_wait(go, (uint32_t)((s - 1) & 1), abort_flag, kWaitCycles)) { ok = false; break; }
         track_slice<INT_E, FP8>(R, t - 1, tb0, tb1, warp - 4, kEpiWarps, lane);
       }
+      if (warp == 4 && lane == 0) ISING_RTRACE(3, s);
       if (!tc::mbar_wait(acc_full, (uint32_t)(s & 1), abort_flag, kWaitCycles)) {
         atomicExch(P.err, 3);
         atomicExch(R.gabort, 1);
@@ -719,6 +729,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         break;
       }
       tc::fence_after_sync();
+      if (warp == 4 && lane == 0) ISING_RTRACE(4, s);
       const bool last = s + 1 == K;
       const float2 bc = P.bias[t];
       void* Sout = R.spins[(t + 1) % 3];
@@ -756,7 +767,7 @@ __global__ void __launch_bounds__(kThreads, 1)
               ef[j] = sj * fmaf(P.k.cq, G, P.k.ch * h);
             }
             const float F = fmaf(P.k.cq, G, fmaf(P.k.ch, h, -P.k.mu * sj));
-            const float g = cosf(tj) * F;
+            const float g = cos_proj(tj) * F;
             tj = adam_update(P.k, bc.x, bc.y, g, tj, mj, vj);
             const int64_t idx = b * P.ld + i;
             if (FP8) static_cast<uint8_t*>(Sout)[idx] = sin_nonneg(tj) ? 0x38 : 0xB8;
@@ -793,6 +804,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc::tmem_wait_st();
       tc::fence_proxy_async_global();
       __syncwarp();
+      if (warp == 4 && lane == 0) ISING_RTRACE(5, s);
       if (lane == 0) tc::mbar_arrive(step_done);
     }
     if (ok && K > 0) {
@@ -1099,6 +1111,10 @@ int tc_run_resident(ising_ds* ds, int64_t steps) {
   a.err = st->err.as<int>();
   a.has_h = ds->inst.has_h ? 1 : 0;
   a.trace = nullptr;
+  if (ds->p.flags & ISING_DS_PROFILE) {
+    if (!st->trace.p) ISING_TRY(dev_alloc(ds->ctx, st->trace, (size_t)st->grid * 8 * 8));
+    a.trace = st->trace.as<unsigned long long>();
+  }
   r.steps = steps;
   for (int k = 0; k < 3; ++k) r.spins[k] = ds->spins[k].p;
   for (int k = 0; k < 2; ++k) {
@@ -1111,6 +1127,7 @@ int tc_run_resident(ising_ds* ds, int64_t steps) {
   r.best_E = ds->best_E.as<double>();
   r.best_t = ds->best_t.as<long long>();
   r.best_s = ds->best_s.as<int8_t>();
+  r.bs_ld = ds->bs_ld;
   r.last_E = ds->last_E.as<double>();
   r.cq = ds->inst.cq;
   r.chs = ds->inst.ch * std::ldexp(1.0, -ds->h_shift);

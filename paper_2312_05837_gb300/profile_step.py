@@ -23,6 +23,8 @@ def main() -> None:
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--precision", default="auto")
     ap.add_argument("--trace", action="store_true", help="print the per-CTA role timeline")
+    ap.add_argument("--resident-trace", action="store_true",
+                    help="label the timeline with the resident form's slots")
     a = ap.parse_args()
     import numpy as np
     import synth
@@ -39,8 +41,10 @@ def main() -> None:
         tr = s.trace().astype(np.int64)
         if tr.size:
             rel = (tr - tr[:, 0].min()) / 1e3
-            names = ["start", "tma_first", "tma_last", "mma_first", "mma_last", "epi_acc",
-                     "epi_done", "end"]
+            names = (["step_start", "tma_last", "mma_last", "tracked", "epi_acc", "epi_done",
+                      "ctl_done", "barrier"] if a.resident_trace else
+                     ["start", "tma_first", "tma_last", "mma_first", "mma_last", "epi_acc",
+                      "epi_done", "end"])
             for k, nm in enumerate(names):
                 print(f"  {nm:10s} median {np.median(rel[:, k]):8.2f} us  max {rel[:, k].max():8.2f} us")
     s.close()

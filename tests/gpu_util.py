@@ -71,8 +71,9 @@ def check_step(inst, st0, st1, last_E, p, exact_energy):
                        np.abs(mhat) * (1 - p.beta2) * c2 * np.abs(r.grad) /
                        np.maximum(rv * (rv + p.eps) ** 2, 1e-300))
     # gradient error: for integer instances F is exact and only cos(theta) is
-    # rounded (relative 2^-22 or better); otherwise the FP32 product bounds it
-    dg = np.abs(r.grad) * 1e-6 if exact_energy else TOL * sc
+    # approximated (absolute error <= 2^-21.41 < 4e-7 on [-pi, pi]); otherwise
+    # the FP32 product bounds it
+    dg = np.abs(r.F) * 4e-7 if exact_energy else TOL * sc
     tol_th = TOL * (1 + p.lr) * (1 + np.abs(mhat) / (rv + p.eps)) + sens * dg
     assert np.all(np.abs(wrapped_diff(th1, r.theta)) <= tol_th)
     # next spins: identical wherever the rounding is not within the tolerance
