@@ -27,24 +27,26 @@ __device__ __forceinline__ float wrap_angle(float th) {
 }
 
 // sgn+(sin theta) for float theta with |theta| < 2 pi, by comparisons: sin is
-// >= 0 exactly on [0, pi] and [-2 pi, -pi]; pi and 2 pi are not floats, so the
-// bounds are the floats on the correct side of them.
+// >= 0 exactly on [0, pi] and (-2 pi, -pi], i.e. when (theta >= 0) differs
+// from (|theta| > pi); pi is not a float, and |theta| > pi holds exactly when
+// |theta| exceeds the largest float below pi.
 __device__ __forceinline__ bool sin_nonneg(float th) {
-  const float kPiDn = __int_as_float(0x40490FDA);     // largest float < pi
-  const float kPiUp = __int_as_float(0x40490FDB);     // smallest float > pi
-  const float k2PiDn = __int_as_float(0x40C90FDA);    // largest float < 2 pi
-  return (th >= 0.0f && th <= kPiDn) || (th <= -kPiUp && th >= -k2PiDn);
+  const float kPiDn = __int_as_float(0x40490FDA);  // largest float < pi
+  return (th >= 0.0f) != (fabsf(th) > kPiDn);
 }
 
-// Adam on one coordinate; returns the projected new angle. The division uses
-// the fast reciprocal (at most 2 ulp), far inside the 1e-5 step tolerance.
+// Adam on one coordinate; returns the projected new angle. The square root and
+// the division use the hardware approximations (a few ulp), far inside the
+// 1e-5 step tolerance.
 __device__ __forceinline__ float adam_update(const StepConsts& k, float c1, float c2, float g,
                                              float th, float& m, float& v) {
   m = fmaf(k.b1, m, k.omb1 * g);
   v = fmaf(k.b2, v, k.omb2 * (g * g));
   const float mhat = m * c1;
   const float vhat = v * c2;
-  th = th - __fdividef(k.lr * mhat, sqrtf(vhat) + k.eps);
+  float rt;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(rt) : "f"(vhat));  // relative error ~2^-23
+  th = th - __fdividef(k.lr * mhat, rt + k.eps);
   return wrap_angle(th);
 }
 

@@ -569,18 +569,44 @@ __global__ void __launch_bounds__(kThreads, 1)
       int issued = 0;
       bool ok = true;
       for (int64_t s = 0; s < K && ok; ++s) {
+        const long long t = t0 + s + 1;
+        const int slot = (int)(t % 3);
+        const CUtensorMap* mb = slot == 0 ? &tmB0 : (slot == 1 ? &tmB1 : &tmB2);
+        // J does not change between steps: the J tiles of the first k-blocks
+        // are requested before the grid barrier, their S tiles after it
+        const int pre = s > 0 ? (nkt < STAGES ? nkt : STAGES) : 0;
+        const uint32_t st0 = stage;
+        for (int kt = 0; kt < pre; ++kt) {
+          if (!tc::mbar_wait(&empty[stage], phase ^ 1, abort_flag, kWaitCycles)) {
+            ok = false;
+            break;
+          }
+          uint8_t* sa = smem + stage * Lay::kStage;
+          tc::mbar_expect_tx(&full[stage], Lay::kStage);
+          const int plane = kt / P.nk, kb = kt - plane * P.nk;
+          const CUtensorMap* ma = plane == 0 ? &tmA0 : (plane == 1 ? &tmA1 : &tmA2);
+          tc::tma_load_2d(sa, ma, &full[stage], kb * kBK, (int)m0);
+          ++issued;
+          if (++stage == STAGES) { stage = 0; phase ^= 1; }
+        }
+        if (!ok) break;
         if (s > 0) {
           if (!tc::mbar_wait(go, (uint32_t)((s - 1) & 1), abort_flag, kWaitCycles)) {
+            // the prefetched J copies are counted in `issued` and drained below
             ok = false;
             break;
           }
           tc::fence_proxy_async_global();
         }
         ISING_RTRACE(0, s);
-        const long long t = t0 + s + 1;
-        const int slot = (int)(t % 3);
-        const CUtensorMap* mb = slot == 0 ? &tmB0 : (slot == 1 ? &tmB1 : &tmB2);
-        for (int kt = 0; kt < nkt; ++kt) {
+        uint32_t sp = st0;
+        for (int kt = 0; kt < pre; ++kt) {
+          const int plane = kt / P.nk, kb = kt - plane * P.nk;
+          (void)plane;
+          tc::tma_load_2d(smem + sp * Lay::kStage + Lay::kA, mb, &full[sp], kb * kBK, (int)n0);
+          if (++sp == STAGES) sp = 0;
+        }
+        for (int kt = pre; kt < nkt; ++kt) {
           if (!tc::mbar_wait(&empty[stage], phase ^ 1, abort_flag, kWaitCycles)) {
             ok = false;
             break;
@@ -749,27 +775,28 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         float ef[kChunk];
         int eq[kChunk], eh[kChunk];
+        // columns of this chunk that exist (all of them except in a ragged last tile)
+        const int nvalid = row_ok ? (int)max((int64_t)0, min((int64_t)kChunk, P.B - (nb0 + c0))) : 0;
+        const int64_t base = (nb0 + c0) * P.ld + i;
 #pragma unroll
         for (int j = 0; j < kChunk; ++j) {
-          const int64_t b = nb0 + c0 + j;
-          const bool okj = row_ok && b < P.B;
+          const bool okj = j < nvalid;
           float tj = __uint_as_float(th[j]), mj = __uint_as_float(mm[j]), vj = __uint_as_float(vv[j]);
           const float G = __uint_as_float(r[j]) * rs;
-          const float sj = sin_nonneg(tj) ? 1.f : -1.f;  // the spin this step consumed
-          ef[j] = 0.f;
-          eq[j] = 0;
-          eh[j] = 0;
+          const bool pos = sin_nonneg(tj);  // the spin this step consumed
+          const float sj = pos ? 1.f : -1.f;
+          if (INT_E) {
+            const int gi = __float2int_rn(G);
+            eq[j] = okj ? (pos ? gi : -gi) : 0;
+            eh[j] = okj ? (pos ? hi : -hi) : 0;
+          } else {
+            ef[j] = okj ? sj * fmaf(P.k.cq, G, P.k.ch * h) : 0.f;
+          }
+          const float F = fmaf(P.k.cq, G, fmaf(P.k.ch, h, -P.k.mu * sj));
+          const float g = cos_proj(tj) * F;
+          tj = adam_update(P.k, bc.x, bc.y, g, tj, mj, vj);
           if (okj) {
-            if (INT_E) {
-              eq[j] = (int)sj * __float2int_rn(G);
-              eh[j] = (int)sj * hi;
-            } else {
-              ef[j] = sj * fmaf(P.k.cq, G, P.k.ch * h);
-            }
-            const float F = fmaf(P.k.cq, G, fmaf(P.k.ch, h, -P.k.mu * sj));
-            const float g = cos_proj(tj) * F;
-            tj = adam_update(P.k, bc.x, bc.y, g, tj, mj, vj);
-            const int64_t idx = b * P.ld + i;
+            const int64_t idx = base + (int64_t)j * P.ld;
             if (FP8) static_cast<uint8_t*>(Sout)[idx] = sin_nonneg(tj) ? 0x38 : 0xB8;
             else static_cast<__nv_bfloat16*>(Sout)[idx] = __float2bfloat16(sin_nonneg(tj) ? 1.f : -1.f);
             if (last) {
