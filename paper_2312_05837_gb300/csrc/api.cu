@@ -25,6 +25,13 @@ extern "C" int ising_create(ising_ctx** out, int device, void* stream) {
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
   ctx->sm_count = std::max(sms, 1);
   ctx->smem_optin = (size_t)optin;
+  // keep freed pool memory cached for the next solve instead of returning it
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  cudaGetLastError();
   *out = ctx;
   return ISING_OK;
 }
@@ -93,15 +100,29 @@ extern "C" int ising_energy(ising_ctx* ctx, const ising_instance* inst, const in
   return ISING_OK;
 }
 
+namespace ising {
+int prune_device(ising_ctx* ctx, const DevInstance& I, int flags, ising_prune_result** out);
+int ds_create_impl(ising_ctx* ctx, const ising_instance* inst, const ising_ds_params* p,
+                   ising_ds** out, bool validate);
+}
+
+// The instance is uploaded and validated once; domain selection runs on the
+// reduced instance the library derived from it, and the final energy is taken
+// on the uploaded copy.
 extern "C" int ising_solve(ising_ctx* ctx, const ising_instance* inst, const ising_ds_params* p,
                            int prune_flags, int8_t* best_spins, double* best_energy,
                            ising_ds_stats* stats, int mem) {
   if (!ctx) return ISING_EINVAL;
   if (!inst) return fail(ctx, ISING_EINVAL, "instance is NULL");
   if (mem != ISING_MEM_HOST && mem != ISING_MEM_DEVICE) return fail(ctx, ISING_EINVAL, "bad mem");
+  if (prune_flags & ~ISING_PRUNE_ZERO_RULE) return fail(ctx, ISING_EINVAL, "unknown prune flags");
+  if (!p) return fail(ctx, ISING_EINVAL, "params is NULL");
+  ISING_CUDA(ctx, cudaSetDevice(ctx->device));
   cudaStream_t st = ctx->stream;
+  DevInstance I;
+  ISING_TRY(upload_instance(ctx, inst, &I));
   ising_prune_result* pr = nullptr;
-  ISING_TRY(ising_prune(ctx, inst, prune_flags, &pr));
+  ISING_TRY(prune_device(ctx, I, prune_flags, &pr));
   int64_t nG = 0;
   ising_prune_info(pr, &nG, nullptr, nullptr, nullptr, nullptr);
   const int64_t n = inst->n;
@@ -116,15 +137,17 @@ extern "C" int ising_solve(ising_ctx* ctx, const ising_instance* inst, const isi
       ising_instance red;
       ising_prune_reduced(pr, &red);
       double eg = 0.0;
-      rc = ising_select_domain(ctx, &red, p, sG.as<int8_t>(), &eg, &ds_stats, ISING_MEM_DEVICE);
+      ising_ds* ds = nullptr;
+      rc = ds_create_impl(ctx, &red, p, &ds, false);
+      if (rc == ISING_OK) rc = ising_ds_finish(ds);
+      if (rc == ISING_OK) rc = ising_ds_result(ds, sG.as<int8_t>(), &eg, &ds_stats, ISING_MEM_DEVICE);
+      ising_ds_destroy(ds);
       if (rc != ISING_OK) break;
     }
     rc = ising_reconstruct(ctx, pr, sG.as<int8_t>(), full.as<int8_t>(), ISING_MEM_DEVICE);
     if (rc != ISING_OK) break;
     // the energy of the reconstructed spins on the full instance
-    ising_instance src = *inst;
-    rc = ising_energy(ctx, &src, full.as<int8_t>(), 1, E.as<double>(), nullptr, nullptr,
-                      ISING_MEM_DEVICE);
+    rc = energy_device(ctx, I, full.as<int8_t>(), 1, E.as<double>(), nullptr, nullptr);
     if (rc != ISING_OK) break;
     cudaMemcpyKind k = mem == ISING_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
     if (best_spins) {

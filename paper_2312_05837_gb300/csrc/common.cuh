@@ -51,21 +51,31 @@ inline int fail(ising_ctx* ctx, int code, const char* fmt, ...) {
     if (r_ != ISING_OK) return r_; \
   } while (0)
 
-// Owning device allocation (cudaFree on destruction).
+// Owning device allocation from the stream-ordered pool: allocated and freed
+// on the stream the work using it is issued on, so releasing a buffer never
+// synchronises the device and repeated solves reuse pooled memory.
 struct DevMem {
   void* p = nullptr;
   size_t bytes = 0;
+  cudaStream_t stream = nullptr;
   DevMem() = default;
   DevMem(const DevMem&) = delete;
   DevMem& operator=(const DevMem&) = delete;
-  DevMem(DevMem&& o) noexcept : p(o.p), bytes(o.bytes) { o.p = nullptr; o.bytes = 0; }
+  DevMem(DevMem&& o) noexcept : p(o.p), bytes(o.bytes), stream(o.stream) { o.p = nullptr; o.bytes = 0; }
   DevMem& operator=(DevMem&& o) noexcept {
-    if (this != &o) { release(); p = o.p; bytes = o.bytes; o.p = nullptr; o.bytes = 0; }
+    if (this != &o) {
+      release();
+      p = o.p;
+      bytes = o.bytes;
+      stream = o.stream;
+      o.p = nullptr;
+      o.bytes = 0;
+    }
     return *this;
   }
   ~DevMem() { release(); }
   void release() {
-    if (p) cudaFree(p);
+    if (p) cudaFreeAsync(p, stream);
     p = nullptr;
     bytes = 0;
   }
@@ -75,11 +85,12 @@ struct DevMem {
 inline int dev_alloc(ising_ctx* ctx, DevMem& m, size_t bytes) {
   m.release();
   if (bytes == 0) bytes = 16;
-  cudaError_t e = cudaMalloc(&m.p, bytes);
+  m.stream = ctx->stream;
+  cudaError_t e = cudaMallocAsync(&m.p, bytes, m.stream);
   if (e != cudaSuccess) {
     m.p = nullptr;
     cudaGetLastError();
-    return fail(ctx, ISING_ENOMEM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    return fail(ctx, ISING_ENOMEM, "cudaMallocAsync(%zu) failed: %s", bytes, cudaGetErrorString(e));
   }
   m.bytes = bytes;
   return ISING_OK;
@@ -140,8 +151,11 @@ struct DevInstance {
 };
 
 // Uploads / copies `in` to the device and validates it (symmetry, zero
-// diagonal, CSR structure). Defined in instance.cu.
-int upload_instance(ising_ctx* ctx, const ising_instance* in, DevInstance* out);
+// diagonal, CSR structure; skipped when `validate` is false, for instances the
+// library derived itself). Value facts are always gathered. Defined in
+// instance.cu.
+int upload_instance(ising_ctx* ctx, const ising_instance* in, DevInstance* out,
+                    bool validate = true);
 
 // Device view of an instance for kernels.
 struct InstView {

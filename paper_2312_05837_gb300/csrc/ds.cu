@@ -516,8 +516,18 @@ int select_best(ising_ds* ds) {
 
 // ------------------------------------------------------------------ C ABI
 
+namespace ising {
+int ds_create_impl(ising_ctx* ctx, const ising_instance* inst, const ising_ds_params* p,
+                   ising_ds** out, bool validate);
+}
+
 extern "C" int ising_ds_create(ising_ctx* ctx, const ising_instance* inst,
                                const ising_ds_params* p, ising_ds** out) {
+  return ising::ds_create_impl(ctx, inst, p, out, true);
+}
+
+int ising::ds_create_impl(ising_ctx* ctx, const ising_instance* inst, const ising_ds_params* p,
+                          ising_ds** out, bool validate) {
   if (!ctx) return ISING_EINVAL;
   if (!out) return fail(ctx, ISING_EINVAL, "out is NULL");
   *out = nullptr;
@@ -527,7 +537,7 @@ extern "C" int ising_ds_create(ising_ctx* ctx, const ising_instance* inst,
   ds->ctx = ctx;
   ds->p = *p;
   int rc = [&]() -> int {
-    ISING_TRY(upload_instance(ctx, inst, &ds->inst));
+    ISING_TRY(upload_instance(ctx, inst, &ds->inst, validate));
     ds->n = ds->inst.n;
     ds->B = p->restarts;
     ds->T = p->steps;

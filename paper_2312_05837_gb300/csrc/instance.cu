@@ -16,31 +16,54 @@ struct ValFlags {
   unsigned long long h_absmax;
 };
 
-__device__ __forceinline__ void note_abs(unsigned long long* slot, double x) {
-  atomicMax(slot, (unsigned long long)__double_as_longlong(fabs(x)));
-}
-
-__device__ __forceinline__ void note_value(ValFlags* f, double x) {
-  if (!isfinite(x)) atomicOr(&f->bad, 16u);
-  if (x != rint(x)) atomicOr(&f->j_nonint, 1u);
-  note_abs(&f->j_absmax, x);
-}
-
-// Dense: J[i][j] == J[j][i] exactly, J[i][i] == 0, plus value facts.
-__global__ void check_dense(const void* J, int dt, int64_t n, ValFlags* f) {
-  int64_t total = n * n;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    int64_t i = e / n, j = e - i * n;
-    double x = load_as_double(J, dt, e);
-    note_value(f, x);
-    if (i == j) {
-      if (x != 0.0) atomicOr(&f->bad, 2u);
-    } else if (j > i) {
-      double y = load_as_double(J, dt, j * n + i);
-      if (!(x == y)) atomicOr(&f->bad, 1u);
+// Facts gathered per thread and merged once per warp (a same-address atomic
+// per element would serialise millions of updates).
+struct LocalFacts {
+  unsigned int bad = 0, nonint = 0;
+  double absmax = 0.0;
+  __device__ void note(double x) {
+    if (!isfinite(x)) bad |= 16u;
+    if (x != rint(x)) nonint = 1u;
+    absmax = fmax(absmax, fabs(x));
+  }
+  __device__ void flush(ValFlags* f) {
+    for (int o = 16; o; o >>= 1) {
+      bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+      nonint |= __shfl_xor_sync(0xffffffffu, nonint, o);
+      absmax = fmax(absmax, __shfl_xor_sync(0xffffffffu, absmax, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+      if (bad) atomicOr(&f->bad, bad);
+      if (nonint) atomicOr(&f->j_nonint, nonint);
+      atomicMax(&f->j_absmax, (unsigned long long)__double_as_longlong(absmax));
     }
   }
+};
+
+// Dense: J[i][j] == J[j][i] exactly, J[i][i] == 0, plus value facts. Every
+// thread runs the same number of loop trips so the warp-level merge at the
+// end sees all 32 lanes.
+__global__ void check_dense(const void* J, int dt, int64_t n, ValFlags* f, bool structure) {
+  const int64_t total = n * n;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  LocalFacts lf;
+  const int64_t e0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t trips = (total + stride - 1) / stride;
+  for (int64_t k = 0; k < trips; ++k) {
+    const int64_t e = e0 + k * stride;
+    if (e >= total) continue;
+    const int64_t i = e / n, j = e - i * n;
+    const double x = load_as_double(J, dt, e);
+    lf.note(x);
+    if (!structure) continue;
+    if (i == j) {
+      if (x != 0.0) lf.bad |= 2u;
+    } else if (j > i) {
+      const double y = load_as_double(J, dt, j * n + i);
+      if (!(x == y)) lf.bad |= 1u;
+    }
+  }
+  lf.flush(f);
 }
 
 __global__ void check_indptr(const int64_t* indptr, int64_t n, int64_t nnz, int32_t* rowptr,
@@ -58,22 +81,28 @@ __global__ void check_indptr(const int64_t* indptr, int64_t n, int64_t nnz, int3
 // CSR rows: columns in range, strictly increasing, no diagonal; each (i,j,v)
 // has a partner (j,i,v) found by binary search in row j.
 __global__ void check_csr(const int64_t* indptr, const int32_t* idx, const void* vals, int dt,
-                          int64_t n, ValFlags* f) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
+                          int64_t n, ValFlags* f, bool structure) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t trips = (n + stride - 1) / stride;
+  LocalFacts lf;
+  for (int64_t tr = 0; tr < trips; ++tr) {
+    const int64_t i = i0 + tr * stride;
+    if (i >= n) continue;
     int64_t a = indptr[i], b = indptr[i + 1];
     int32_t prev = -1;
     for (int64_t k = a; k < b; ++k) {
       int32_t j = idx[k];
       double x = load_as_double(vals, dt, k);
-      note_value(f, x);
+      lf.note(x);
+      if (!structure) continue;
       if (j < 0 || j >= n || j <= prev) {
-        atomicOr(&f->bad, 4u);
+        lf.bad |= 4u;
         break;
       }
       prev = j;
       if (j == i) {
-        atomicOr(&f->bad, 2u);
+        lf.bad |= 2u;
         continue;
       }
       int64_t lo = indptr[j], hi = indptr[j + 1] - 1;
@@ -87,23 +116,40 @@ __global__ void check_csr(const int64_t* indptr, const int32_t* idx, const void*
         }
         if (c < (int32_t)i) lo = mid + 1; else hi = mid - 1;
       }
-      if (!found) atomicOr(&f->bad, 1u);
+      if (!found) lf.bad |= 1u;
     }
   }
+  lf.flush(f);
 }
 
 __global__ void check_h(const void* h, int dt, int64_t n, ValFlags* f) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t trips = (n + stride - 1) / stride;
+  unsigned int bad = 0, mask_all = 0x1FFu;
+  double amax = 0.0;
+  for (int64_t tr = 0; tr < trips; ++tr) {
+    const int64_t i = i0 + tr * stride;
+    if (i >= n) continue;
     double x = load_as_double(h, dt, i);
-    if (!isfinite(x)) atomicOr(&f->bad, 16u);
-    atomicMax(&f->h_absmax, (unsigned long long)__double_as_longlong(fabs(x)));
+    if (!isfinite(x)) bad |= 16u;
+    amax = fmax(amax, fabs(x));
     unsigned int mask = 0;
     for (int k = 0; k <= 8; ++k) {
       double y = ldexp(x, k);
       if (y == rint(y) && fabs(y) < 1073741824.0) mask |= 1u << k;
     }
-    atomicAnd(&f->h_mask, mask);
+    mask_all &= mask;
+  }
+  for (int o = 16; o; o >>= 1) {
+    bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+    mask_all &= __shfl_xor_sync(0xffffffffu, mask_all, o);
+    amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (bad) atomicOr(&f->bad, bad);
+    atomicAnd(&f->h_mask, mask_all);
+    atomicMax(&f->h_absmax, (unsigned long long)__double_as_longlong(amax));
   }
 }
 
@@ -117,7 +163,7 @@ int grid_for(ising_ctx* ctx, int64_t work) {
 
 }  // namespace
 
-int upload_instance(ising_ctx* ctx, const ising_instance* in, DevInstance* out) {
+int upload_instance(ising_ctx* ctx, const ising_instance* in, DevInstance* out, bool validate) {
   if (!in) return fail(ctx, ISING_EINVAL, "instance is NULL");
   if (in->n < 1) return fail(ctx, ISING_EINVAL, "n must be >= 1 (got %lld)", (long long)in->n);
   if (in->n > (int64_t)INT32_MAX - 1) return fail(ctx, ISING_EINVAL, "n too large");
@@ -156,7 +202,7 @@ int upload_instance(ising_ctx* ctx, const ising_instance* in, DevInstance* out) 
     ISING_TRY(dev_alloc(ctx, out->J, bytes));
     ISING_CUDA(ctx, cudaMemcpyAsync(out->J.p, in->J, bytes, kind, st));
     out->nnz = n * n;
-    check_dense<<<grid_for(ctx, n * n), 256, 0, st>>>(out->J.p, in->j_dtype, n, fd);
+    check_dense<<<grid_for(ctx, n * n), 256, 0, st>>>(out->J.p, in->j_dtype, n, fd, validate);
     ISING_CUDA(ctx, cudaGetLastError());
   } else {
     if (!in->indptr || (!in->indices && in->nnz > 0))
@@ -182,7 +228,7 @@ int upload_instance(ising_ctx* ctx, const ising_instance* in, DevInstance* out) 
     if (fh.bad & 8u) return fail(ctx, ISING_EINVAL, "CSR indptr is not a valid offset array");
     check_csr<<<grid_for(ctx, n), 256, 0, st>>>(out->indptr.as<int64_t>(),
                                                 out->indices.as<int32_t>(), out->J.p,
-                                                in->j_dtype, n, fd);
+                                                in->j_dtype, n, fd, validate);
     ISING_CUDA(ctx, cudaGetLastError());
   }
   out->has_h = in->h != nullptr;

@@ -330,6 +330,10 @@ struct ising_prune_result {
   DevMem Jr, indptr_r, indices_r, h_r;
 };
 
+namespace ising {
+int prune_device(ising_ctx* ctx, const DevInstance& I, int flags, ising_prune_result** out);
+}
+
 extern "C" int ising_prune(ising_ctx* ctx, const ising_instance* inst, int flags,
                            ising_prune_result** out) {
   if (!ctx) return ISING_EINVAL;
@@ -337,9 +341,16 @@ extern "C" int ising_prune(ising_ctx* ctx, const ising_instance* inst, int flags
   if (flags & ~ISING_PRUNE_ZERO_RULE) return fail(ctx, ISING_EINVAL, "unknown prune flags");
   *out = nullptr;
   ISING_CUDA(ctx, cudaSetDevice(ctx->device));
-  cudaStream_t st = ctx->stream;
   DevInstance I;
   ISING_TRY(upload_instance(ctx, inst, &I));
+  return ising::prune_device(ctx, I, flags, out);
+}
+
+// Algorithm 1 on an uploaded, validated instance.
+int ising::prune_device(ising_ctx* ctx, const DevInstance& I, int flags,
+                        ising_prune_result** out) {
+  *out = nullptr;
+  cudaStream_t st = ctx->stream;
   const int64_t n = I.n;
   // CSR view with double values
   DevMem rowptr, col, val;
