@@ -159,11 +159,15 @@ def traffic_for(kernel: str, src_file: str):
     return d["bytes_per_launch"] if d.get("source_sha") == h else None
 
 
-def launches_per_solve(T: int, rounds: int, path: int) -> int:
-    # instance checks (2), pruning (3 + 7 per round incl. the final empty round + 3),
-    # session set-up (4), T steps x (step + track), finish (step + track + argmin),
-    # reconstruction (1), full-instance energy (check + 2)
-    return 2 + 3 + 7 * (rounds + 1) + 3 + 4 + 2 * T + 3 + 1 + 3
+def launches_per_solve(T: int, rounds: int, path: int, resident: bool) -> int:
+    """Kernels of one solve: instance check (1), pruning (dense->CSR 2, init 1,
+    7 per round incl. the final empty one, sum + reduced field + reduced J 3),
+    session set-up (facts 1, operand 1, fills 2, init 1), the steps (one
+    cooperative launch when resident, else step + track per step), finish
+    (energy-only step + track + argmin), reconstruction (1), full-instance
+    energy (2)."""
+    steps = 1 if resident else 2 * T
+    return 1 + 3 + 7 * (rounds + 1) + 3 + 5 + steps + 3 + 1 + 2
 
 
 # ----------------------------------------------------------------- reference arm
@@ -369,7 +373,7 @@ def main():
                        "parallelism": f"replicas x{world}"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": input_bytes(inst),
                     "d2h_bytes_per_step": int(inst.n) + 8},
-            "gpu_launches": launches_per_solve(T, rounds, path) * a.steps,
+            "gpu_launches": launches_per_solve(T, rounds, path, bool(last["resident"])) * a.steps,
             "roofline": roof, "clocks": clk,
             "best_energy": float(last["best_energy"].item())}
     if rank == 0 and world == 1 and not a.no_cpu_baseline:

@@ -140,6 +140,8 @@ typedef struct ising_ds_stats {
   double device_ms;         /* device time of the steps (CUDA events) */
   double kernel_ms;         /* step kernels only (with ISING_DS_PROFILE) */
   int64_t kernel_launches;  /* step-kernel launches timed in kernel_ms */
+  int32_t resident;         /* 1 if the tensor-core path kept the state in tensor memory */
+  int32_t reserved0;
 } ising_ds_stats;
 
 /* ------------------------------------------------------------------ context */
