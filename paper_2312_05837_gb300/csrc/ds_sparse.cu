@@ -16,7 +16,7 @@ namespace ising {
 namespace {
 
 template <int Q, int MODE, bool INT_E, bool VAL_I8>
-__global__ void __launch_bounds__(256) sparse_step_kernel(
+__global__ void __launch_bounds__(256, 2) sparse_step_kernel(
     int64_t n, int64_t Bp, int64_t rows_per_block, const int32_t* __restrict__ rowptr,
     const int32_t* __restrict__ col, const void* __restrict__ val,
     const uint32_t* __restrict__ bits_in, uint32_t* __restrict__ bits_out,
@@ -44,6 +44,20 @@ __global__ void __launch_bounds__(256) sparse_step_kernel(
     for (int r = 0; r < 4; ++r) { eq[q][r] = 0; eh[q][r] = 0; ee[q][r] = 0.f; }
 
   for (int64_t i = r0 + warp; i < r1; i += W) {
+    // state and own spins first (streamed once per step, evict-first), so
+    // their latency overlaps the neighbour gather below
+    float4 th4[Q], m4[Q], v4[Q];
+    uint32_t own[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const int64_t base = i * Bp + cb + 128 * q + 4 * lane;
+      if (UPDATE) {
+        th4[q] = __ldcs(reinterpret_cast<const float4*>(theta + base));
+        m4[q] = __ldcs(reinterpret_cast<const float4*>(m + base));
+        v4[q] = __ldcs(reinterpret_cast<const float4*>(v + base));
+      }
+      own[q] = (bits_in[i * words + wofs + 4 * q] >> nshift) & 0xFu;
+    }
     float G[Q][4];
 #pragma unroll
     for (int q = 0; q < Q; ++q)
@@ -72,21 +86,14 @@ __global__ void __launch_bounds__(256) sparse_step_kernel(
     const int hi = hint[i];
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
-      const uint32_t own = (bits_in[i * words + wofs + 4 * q] >> nshift) & 0xFu;
       const int64_t base = i * Bp + cb + 128 * q + 4 * lane;
-      float4 th4, m4, v4;
-      if (UPDATE) {
-        th4 = *reinterpret_cast<const float4*>(theta + base);
-        m4 = *reinterpret_cast<const float4*>(m + base);
-        v4 = *reinterpret_cast<const float4*>(v + base);
-      }
-      float* thp = &th4.x;
-      float* mp = &m4.x;
-      float* vp = &v4.x;
+      float* thp = &th4[q].x;
+      float* mp = &m4[q].x;
+      float* vp = &v4[q].x;
       uint32_t newnib = 0;
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
-        const float s = ((own >> r) & 1u) ? 1.f : -1.f;
+        const float s = ((own[q] >> r) & 1u) ? 1.f : -1.f;
         if (INT_E) {
           eq[q][r] += (int)s * __float2int_rn(G[q][r]);
           eh[q][r] += (int)s * hi;
@@ -101,9 +108,9 @@ __global__ void __launch_bounds__(256) sparse_step_kernel(
         }
       }
       if (UPDATE) {
-        *reinterpret_cast<float4*>(theta + base) = th4;
-        *reinterpret_cast<float4*>(m + base) = m4;
-        *reinterpret_cast<float4*>(v + base) = v4;
+        __stcs(reinterpret_cast<float4*>(theta + base), th4[q]);
+        __stcs(reinterpret_cast<float4*>(m + base), m4[q]);
+        __stcs(reinterpret_cast<float4*>(v + base), v4[q]);
         uint32_t word = newnib << nshift;
         word |= __shfl_xor_sync(0xffffffffu, word, 1);
         word |= __shfl_xor_sync(0xffffffffu, word, 2);
@@ -157,11 +164,10 @@ __global__ void csr_values_kernel(const void* J, int dt, int64_t nnz, bool to_i8
   }
 }
 
+// Restarts per warp pass = 128 * Q. Q = 2 keeps the registers low enough for
+// two 256-thread blocks per SM (16 warps, about 48 KB of state loads in flight).
 int chunk_q(int64_t Bp) {
-  int64_t c = Bp / 128;
-  if (c % 4 == 0) return 4;
-  if (c % 2 == 0) return 2;
-  return 1;
+  return (Bp / 128) % 2 == 0 ? 2 : 1;
 }
 
 int64_t sparse_rows_per_block(ising_ds* ds) {
@@ -218,7 +224,6 @@ int sparse_step(ising_ds* ds, int mode, float* Gout) {
     else ISING_SP_V(QQ, kModeCoupling, true);                         \
   } while (0)
   switch (Q) {
-    case 4: ISING_SP_U(4); break;
     case 2: ISING_SP_U(2); break;
     default: ISING_SP_U(1); break;
   }
