@@ -128,6 +128,12 @@ typedef struct ising_ds_params {
  * resident form, used when every 128 x BN tile gets its own SM, keeps theta,
  * m and v in tensor memory across a whole run (one cooperative launch). */
 #define ISING_DS_STREAMING 2
+/* params.flags: skip the launch-shape autotuner and use the default shape.
+ * The autotuner (sparse path) times the first steps of a run once per
+ * problem shape with each candidate shape and keeps the fastest; results do
+ * not depend on the shape. Choices are cached per process and, when the
+ * environment variable ISING_TUNE_CACHE names a file, across processes. */
+#define ISING_DS_NO_AUTOTUNE 4
 
 typedef struct ising_ds_stats {
   int64_t best_restart;     /* restart holding the overall best */

@@ -23,6 +23,7 @@ PATH_PLAIN, PATH_TC, PATH_SPARSE = range(3)
 PRUNE_ZERO_RULE = 1
 DS_PROFILE = 1
 DS_STREAMING = 2
+DS_NO_AUTOTUNE = 4
 
 
 class Instance(ctypes.Structure):

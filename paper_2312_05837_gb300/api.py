@@ -154,14 +154,15 @@ def make_instance(inst):
 
 
 def params(restarts, steps, lr=6.0, mu=0.0, beta1=0.9, beta2=0.999, eps=1e-8, seed=0,
-           precision="auto", profile=False, streaming=False) -> L.DSParams:
+           precision="auto", profile=False, streaming=False, autotune=True) -> L.DSParams:
     p = L.DSParams()
     p.restarts = int(restarts)
     p.steps = int(steps)
     p.lr, p.mu, p.beta1, p.beta2, p.eps = float(lr), float(mu), float(beta1), float(beta2), float(eps)
     p.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
     p.precision = _PREC[precision] if isinstance(precision, str) else int(precision)
-    p.flags = (L.DS_PROFILE if profile else 0) | (L.DS_STREAMING if streaming else 0)
+    p.flags = ((L.DS_PROFILE if profile else 0) | (L.DS_STREAMING if streaming else 0) |
+               (0 if autotune else L.DS_NO_AUTOTUNE))
     return p
 
 

@@ -5,7 +5,13 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
+#include <fstream>
 #include <limits>
+#include <map>
+#include <mutex>
+#include <sstream>
+#include <string>
 
 using namespace ising;
 
@@ -263,7 +269,7 @@ int check_params(ising_ctx* ctx, const ising_ds_params* p) {
   if (!(p->beta1 >= 0 && p->beta1 < 1) || !(p->beta2 >= 0 && p->beta2 < 1))
     return fail(ctx, ISING_EINVAL, "beta1 and beta2 must lie in [0, 1)");
   if (!(p->eps > 0) || !std::isfinite(p->eps)) return fail(ctx, ISING_EINVAL, "eps must be > 0");
-  if (p->flags & ~(ISING_DS_PROFILE | ISING_DS_STREAMING))
+  if (p->flags & ~(ISING_DS_PROFILE | ISING_DS_STREAMING | ISING_DS_NO_AUTOTUNE))
     return fail(ctx, ISING_EINVAL, "unknown flags");
   if (p->precision < ISING_PREC_AUTO || p->precision > ISING_PREC_FP8)
     return fail(ctx, ISING_EINVAL, "unknown precision %d", p->precision);
@@ -639,6 +645,90 @@ int replay_graph(ising_ds* ds) {
 }  // namespace
 }  // namespace ising
 
+namespace ising {
+namespace {
+
+// Launch-shape autotuner: the chosen sparse slice width per problem shape,
+// kept for the process and optionally in the file named by ISING_TUNE_CACHE.
+std::mutex g_tune_mu;
+std::map<std::string, int> g_tune;
+bool g_tune_loaded = false;
+
+std::string tune_key(const ising_ds* ds) {
+  std::ostringstream k;
+  k << "sparse n=" << ds->n << " nnz=" << ds->inst.nnz << " Bp=" << ds->Bp
+    << " i8=" << ds->sp_int8 << " ie=" << ds->int_energy;
+  return k.str();
+}
+
+void tune_load_locked() {
+  if (g_tune_loaded) return;
+  g_tune_loaded = true;
+  const char* path = std::getenv("ISING_TUNE_CACHE");
+  if (!path) return;
+  std::ifstream f(path);
+  std::string line;
+  while (std::getline(f, line)) {
+    const size_t bar = line.rfind('|');
+    if (bar == std::string::npos) continue;
+    g_tune[line.substr(0, bar)] = std::atoi(line.c_str() + bar + 1);
+  }
+}
+
+void tune_store_locked(const std::string& key, int v) {
+  g_tune[key] = v;
+  const char* path = std::getenv("ISING_TUNE_CACHE");
+  if (!path) return;
+  std::ofstream f(path, std::ios::app);
+  f << key << "|" << v << "\n";
+}
+
+// Times one real step with each candidate shape (twice, alternating) and keeps
+// the fastest; returns the number of steps it ran.
+int autotune_sparse(ising_ds* ds, int64_t budget, int64_t* done) {
+  *done = 0;
+  ds->tuned = true;
+  if ((ds->p.flags & ISING_DS_NO_AUTOTUNE) || (ds->Bp / 128) % 2 != 0) return ISING_OK;
+  const std::string key = tune_key(ds);
+  {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    tune_load_locked();
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      ds->sp_q = it->second;
+      return ISING_OK;
+    }
+  }
+  if (budget < 4) return ISING_OK;
+  ising_ctx* ctx = ds->ctx;
+  cudaEvent_t ev[5];
+  for (auto& e : ev) ISING_CUDA(ctx, cudaEventCreate(&e));
+  const int order[4] = {1, 2, 1, 2};
+  int rc = ISING_OK;
+  ISING_CUDA(ctx, cudaEventRecord(ev[0], ctx->stream));
+  for (int k = 0; k < 4 && rc == ISING_OK; ++k) {
+    ds->sp_q = order[k];
+    rc = sparse_step(ds, kModeUpdate, nullptr);
+    if (rc == ISING_OK) rc = track_step(ds);
+    ds->t += 1;
+    *done += 1;
+    cudaEventRecord(ev[k + 1], ctx->stream);
+  }
+  float t[4] = {0, 0, 0, 0};
+  if (rc == ISING_OK) {
+    cudaEventSynchronize(ev[4]);
+    for (int k = 0; k < 4; ++k) cudaEventElapsedTime(&t[k], ev[k], ev[k + 1]);
+    ds->sp_q = (t[0] + t[2] <= t[1] + t[3]) ? 1 : 2;
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    tune_store_locked(key, ds->sp_q);
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  return rc;
+}
+
+}  // namespace
+}  // namespace ising
+
 extern "C" int ising_ds_run(ising_ds* ds, int64_t steps) {
   if (!ds) return ISING_EINVAL;
   ising_ctx* ctx = ds->ctx;
@@ -662,8 +752,17 @@ extern "C" int ising_ds_run(ising_ds* ds, int64_t steps) {
     if (ds->p.flags & ISING_DS_PROFILE) ds->kernel_launches += todo;
     todo = 0;
   }
+  int64_t s0 = 0;
+  if (ds->path == ISING_PATH_SPARSE && !ds->tuned) {
+    int rc = autotune_sparse(ds, todo, &s0);
+    if (rc != ISING_OK) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return rc;
+    }
+  }
   const bool use_graph = !(ds->p.flags & ISING_DS_PROFILE) && todo >= 2 * kGraphSteps;
-  for (int64_t s = 0; s < todo;) {
+  for (int64_t s = s0; s < todo;) {
     int rc = ISING_OK;
     // (t > 0: the kernels have run once outside capture, which sets their attributes)
     if (use_graph && ds->t > 0 && ds->t % 6 == 0 && todo - s >= kGraphSteps) {

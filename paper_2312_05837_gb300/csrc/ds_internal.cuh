@@ -141,6 +141,8 @@ struct ising_ds {
   // sparse operands
   ising::DevMem sp_val;    // int8 or float values
   bool sp_int8 = false;
+  int sp_q = 1;            // sparse slice width (x 128 restarts), chosen by the autotuner
+  bool tuned = false;
   // results
   bool finished = false;
   int64_t best_restart = -1;

@@ -15,8 +15,12 @@
 namespace ising {
 namespace {
 
-template <int MODE, bool INT_E, bool VAL_I8>
-__global__ void __launch_bounds__(256, 3) sparse_step_kernel(
+// Q = restarts per warp pass / 128. Q = 1 keeps about 70 registers (three
+// blocks per SM); Q = 2 gathers each neighbour's spins once for 256 restarts
+// (two blocks per SM). Both visit rows, lanes and partials in the same order,
+// so their results are identical bit for bit.
+template <int Q, int MODE, bool INT_E, bool VAL_I8>
+__global__ void __launch_bounds__(256, Q == 1 ? 3 : 2) sparse_step_kernel(
     int64_t n, int64_t Bp, int64_t rows_per_block, const int32_t* __restrict__ rowptr,
     const int32_t* __restrict__ col, const void* __restrict__ val,
     const uint32_t* __restrict__ bits_in, uint32_t* __restrict__ bits_out,
@@ -29,102 +33,130 @@ __global__ void __launch_bounds__(256, 3) sparse_step_kernel(
   constexpr int W = 8;  // warps per block
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t words = Bp / 32;
-  const int64_t cb = (int64_t)blockIdx.y * 128;  // first restart of this slice
+  const int64_t cb = (int64_t)blockIdx.y * (128 * Q);  // first restart of this slice
   const int64_t wofs = cb / 32 + (lane >> 3);
   const int nshift = 4 * (lane & 7);
   const int64_t r0 = (int64_t)blockIdx.x * rows_per_block;
   const int64_t r1 = r0 + rows_per_block < n ? r0 + rows_per_block : n;
   const float2 bc = bias[counters[0] + 1];
 
-  int eq[4] = {0, 0, 0, 0}, eh[4] = {0, 0, 0, 0};
-  float ee[4] = {0.f, 0.f, 0.f, 0.f};
+  int eq[Q][4], eh[Q][4];
+  float ee[Q][4];
+#pragma unroll
+  for (int q = 0; q < Q; ++q)
+#pragma unroll
+    for (int r = 0; r < 4; ++r) { eq[q][r] = 0; eh[q][r] = 0; ee[q][r] = 0.f; }
 
   // rows of this warp: r0 + warp, r0 + warp + W, ...; the state of the next
   // row is requested before the current row's neighbour gather (streamed once
   // per step, evict-first), so HBM latency overlaps the dependent gather
-  float4 th_n = {}, m_n = {}, v_n = {};
-  uint32_t own_n = 0;
+  float4 th_n[Q], m_n[Q], v_n[Q];
+  uint32_t own_n[Q];
   auto fetch = [&](int64_t row) {
-    const int64_t base = row * Bp + cb + 4 * lane;
-    if (UPDATE) {
-      th_n = __ldcs(reinterpret_cast<const float4*>(theta + base));
-      m_n = __ldcs(reinterpret_cast<const float4*>(m + base));
-      v_n = __ldcs(reinterpret_cast<const float4*>(v + base));
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const int64_t base = row * Bp + cb + 128 * q + 4 * lane;
+      if (UPDATE) {
+        th_n[q] = __ldcs(reinterpret_cast<const float4*>(theta + base));
+        m_n[q] = __ldcs(reinterpret_cast<const float4*>(m + base));
+        v_n[q] = __ldcs(reinterpret_cast<const float4*>(v + base));
+      }
+      own_n[q] = (bits_in[row * words + wofs + 4 * q] >> nshift) & 0xFu;
     }
-    own_n = (bits_in[row * words + wofs] >> nshift) & 0xFu;
   };
   if (r0 + warp < r1) fetch(r0 + warp);
   for (int64_t i = r0 + warp; i < r1; i += W) {
-    float4 th4 = th_n, m4 = m_n, v4 = v_n;
-    const uint32_t own = own_n;
+    float4 th4[Q], m4[Q], v4[Q];
+    uint32_t own[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      th4[q] = th_n[q];
+      m4[q] = m_n[q];
+      v4[q] = v_n[q];
+      own[q] = own_n[q];
+    }
     if (i + W < r1) fetch(i + W);
-    float G[4] = {0.f, 0.f, 0.f, 0.f};
+    float G[Q][4];
+#pragma unroll
+    for (int q = 0; q < Q; ++q)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) G[q][r] = 0.f;
     const int e1 = rowptr[i + 1];
     for (int e = rowptr[i]; e < e1; ++e) {
       const int64_t j = col[e];
       const float Jv = VAL_I8 ? (float)static_cast<const int8_t*>(val)[e]
                               : static_cast<const float*>(val)[e];
-      const uint32_t nib = (__ldg(&bits_in[j * words + wofs]) >> nshift) & 0xFu;
 #pragma unroll
-      for (int r = 0; r < 4; ++r) G[r] += ((nib >> r) & 1u) ? Jv : -Jv;
+      for (int q = 0; q < Q; ++q) {
+        const uint32_t nib = (__ldg(&bits_in[j * words + wofs + 4 * q]) >> nshift) & 0xFu;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) G[q][r] += ((nib >> r) & 1u) ? Jv : -Jv;
+      }
     }
-    const int64_t base = i * Bp + cb + 4 * lane;
     if (MODE == kModeCoupling) {
 #pragma unroll
-      for (int r = 0; r < 4; ++r) Gout[base + r] = G[r];
+      for (int q = 0; q < Q; ++q)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) Gout[i * Bp + cb + 128 * q + 4 * lane + r] = G[q][r];
       continue;
     }
     const float h = hf[i];
     const int hi = hint[i];
-    float* thp = &th4.x;
-    float* mp = &m4.x;
-    float* vp = &v4.x;
-    uint32_t newnib = 0;
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      const float s = ((own >> r) & 1u) ? 1.f : -1.f;
-      if (INT_E) {
-        eq[r] += (int)s * __float2int_rn(G[r]);
-        eh[r] += (int)s * hi;
-      } else {
-        ee[r] += s * fmaf(k.cq, G[r], k.ch * h);
+    for (int q = 0; q < Q; ++q) {
+      const int64_t base = i * Bp + cb + 128 * q + 4 * lane;
+      float* thp = &th4[q].x;
+      float* mp = &m4[q].x;
+      float* vp = &v4[q].x;
+      uint32_t newnib = 0;
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const float s = ((own[q] >> r) & 1u) ? 1.f : -1.f;
+        if (INT_E) {
+          eq[q][r] += (int)s * __float2int_rn(G[q][r]);
+          eh[q][r] += (int)s * hi;
+        } else {
+          ee[q][r] += s * fmaf(k.cq, G[q][r], k.ch * h);
+        }
+        if (UPDATE) {
+          const float F = fmaf(k.cq, G[q][r], fmaf(k.ch, h, -k.mu * s));
+          const float g = cos_proj(thp[r]) * F;
+          thp[r] = adam_update(k, bc.x, bc.y, g, thp[r], mp[r], vp[r]);
+          if (sin_nonneg(thp[r])) newnib |= 1u << r;
+        }
       }
       if (UPDATE) {
-        const float F = fmaf(k.cq, G[r], fmaf(k.ch, h, -k.mu * s));
-        const float g = cos_proj(thp[r]) * F;
-        thp[r] = adam_update(k, bc.x, bc.y, g, thp[r], mp[r], vp[r]);
-        if (sin_nonneg(thp[r])) newnib |= 1u << r;
+        __stcs(reinterpret_cast<float4*>(theta + base), th4[q]);
+        __stcs(reinterpret_cast<float4*>(m + base), m4[q]);
+        __stcs(reinterpret_cast<float4*>(v + base), v4[q]);
+        uint32_t word = newnib << nshift;
+        word |= __shfl_xor_sync(0xffffffffu, word, 1);
+        word |= __shfl_xor_sync(0xffffffffu, word, 2);
+        word |= __shfl_xor_sync(0xffffffffu, word, 4);
+        if ((lane & 7) == 0) bits_out[i * words + wofs + 4 * q] = word;
       }
-    }
-    if (UPDATE) {
-      __stcs(reinterpret_cast<float4*>(theta + base), th4);
-      __stcs(reinterpret_cast<float4*>(m + base), m4);
-      __stcs(reinterpret_cast<float4*>(v + base), v4);
-      uint32_t word = newnib << nshift;
-      word |= __shfl_xor_sync(0xffffffffu, word, 1);
-      word |= __shfl_xor_sync(0xffffffffu, word, 2);
-      word |= __shfl_xor_sync(0xffffffffu, word, 4);
-      if ((lane & 7) == 0) bits_out[i * words + wofs] = word;
     }
   }
 
   // energy partials: per restart, sum over this block's rows in warp order
   if (MODE == kModeCoupling) return;
-  __shared__ float red_f[INT_E ? 1 : W][INT_E ? 1 : 128];
-  __shared__ int red_q[INT_E ? W : 1][INT_E ? 128 : 1];
-  __shared__ int red_h[INT_E ? W : 1][INT_E ? 128 : 1];
+  __shared__ float red_f[INT_E ? 1 : W][INT_E ? 1 : 128 * Q];
+  __shared__ int red_q[INT_E ? W : 1][INT_E ? 128 * Q : 1];
+  __shared__ int red_h[INT_E ? W : 1][INT_E ? 128 * Q : 1];
 #pragma unroll
-  for (int r = 0; r < 4; ++r) {
-    const int c = 4 * lane + r;
-    if (INT_E) {
-      red_q[warp][c] = eq[r];
-      red_h[warp][c] = eh[r];
-    } else {
-      red_f[warp][c] = ee[r];
+  for (int q = 0; q < Q; ++q)
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int c = 128 * q + 4 * lane + r;
+      if (INT_E) {
+        red_q[warp][c] = eq[q][r];
+        red_h[warp][c] = eh[q][r];
+      } else {
+        red_f[warp][c] = ee[q][r];
+      }
     }
-  }
   __syncthreads();
-  for (int c = threadIdx.x; c < 128; c += blockDim.x) {
+  for (int c = threadIdx.x; c < 128 * Q; c += blockDim.x) {
     const int64_t o = (int64_t)blockIdx.x * Bp + cb + c;
     if (INT_E) {
       long long a = 0, b = 0;
@@ -184,14 +216,21 @@ int sparse_step(ising_ds* ds, int mode, float* Gout) {
   uint32_t* out = ds->spins[(t + 1) % 3].as<uint32_t>();
   const int ps = (int)(t % 2);
   const int64_t rpb = sparse_rows_per_block(ds);
-  dim3 grid((unsigned)ds->mtiles, (unsigned)(ds->Bp / 128));
+  const int Q = (ds->sp_q == 2 && (ds->Bp / 128) % 2 == 0) ? 2 : 1;
+  dim3 grid((unsigned)ds->mtiles, (unsigned)(ds->Bp / (128 * Q)));
 #define ISING_SP(U, I, V)                                                                     \
-  sparse_step_kernel<U, I, V><<<grid, 256, 0, ctx->stream>>>(                                 \
+  do {                                                                                        \
+    if (Q == 2)                                                                               \
+      sparse_step_kernel<2, U, I, V><<<grid, 256, 0, ctx->stream>>>(ISING_SP_ARGS);           \
+    else                                                                                      \
+      sparse_step_kernel<1, U, I, V><<<grid, 256, 0, ctx->stream>>>(ISING_SP_ARGS);           \
+  } while (0)
+#define ISING_SP_ARGS                                                                         \
       ds->n, ds->Bp, rpb, ds->inst.rowptr.as<int32_t>(), ds->inst.indices.as<int32_t>(),      \
       ds->sp_val.p, in, out, ds->theta.as<float>(), ds->m.as<float>(), ds->v.as<float>(),     \
       ds->hf.as<float>(), ds->hint.as<int32_t>(), ds->k, ds->bias.as<float2>(),               \
       ds->counters.as<long long>(), ds->qpart[ps].as<long long>(),                            \
-      ds->hpart[ps].as<long long>(), ds->epart[ps].as<float>(), Gout)
+      ds->hpart[ps].as<long long>(), ds->epart[ps].as<float>(), Gout
 #define ISING_SP_V(U, I) \
   do { if (ds->sp_int8) ISING_SP(U, I, true); else ISING_SP(U, I, false); } while (0)
 #define ISING_SP_I(U) \
@@ -201,6 +240,7 @@ int sparse_step(ising_ds* ds, int mode, float* Gout) {
   else ISING_SP_V(kModeCoupling, true);
 #undef ISING_SP_I
 #undef ISING_SP_V
+#undef ISING_SP_ARGS
 #undef ISING_SP
   ISING_CUDA(ctx, cudaGetLastError());
   return ISING_OK;

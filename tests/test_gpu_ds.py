@@ -216,3 +216,57 @@ def test_resident_equals_streaming(gpu_ctx, name, prec, B):
     np.testing.assert_array_equal(ra["best_spins"], rb["best_spins"])
     a.close()
     b.close()
+
+
+def test_autotuned_sparse_equals_fixed_shape(gpu_ctx):
+    """The autotuner only changes the launch shape: state and bests match a
+    run with the default shape bit for bit."""
+    inst = INSTANCES["er_pendant_h"]
+    a = api.Session(gpu_ctx, inst, restarts=256, steps=30, seed=6)
+    b = api.Session(gpu_ctx, inst, restarts=256, steps=30, seed=6, autotune=False)
+    a.run(30)
+    b.run(30)
+    sa, sb = a.export_state(), b.export_state()
+    for k in ["theta", "m", "v", "spins"]:
+        np.testing.assert_array_equal(sa[k], sb[k])
+    for x, y in zip(a.restart_best(), b.restart_best()):
+        np.testing.assert_array_equal(x, y)
+    a.close()
+    b.close()
+
+
+_FORCED_SHAPE = r"""
+import sys, numpy as np
+sys.path.insert(0, {root!r})
+import synth
+from paper_2312_05837_gb300 import api
+inst = synth.random_sparse_instance(300, 9, p=0.02, kind="float", h="float")
+ctx = api.Context(0)
+a = api.Session(ctx, inst, restarts=256, steps=12, seed=3)            # shape from the cache file
+b = api.Session(ctx, inst, restarts=256, steps=12, seed=3, autotune=False)
+a.run(12); b.run(12)
+sa, sb = a.export_state(), b.export_state()
+ok = all(np.array_equal(sa[k], sb[k]) for k in ["theta", "m", "v", "spins"])
+ok = ok and all(np.array_equal(x, y) for x, y in zip(a.restart_best(), b.restart_best()))
+a.close(); b.close(); ctx.close()
+print("EQUAL" if ok else "DIFFERENT")
+"""
+
+
+def test_two_slice_shape_equals_one_slice_shape(tmp_path):
+    """Forces the 256-restart slice shape through the tuning cache file in a
+    fresh process and compares it with the default 128-restart shape."""
+    import os
+    import subprocess
+    import sys
+    import synth as S
+    inst = S.random_sparse_instance(300, 9, p=0.02, kind="float", h="float")
+    key = f"sparse n=300 nnz={int(inst.indptr[-1])} Bp=256 i8=0 ie=0"
+    cache = tmp_path / "tune.txt"
+    cache.write_text(key + "|2\n")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, ISING_TUNE_CACHE=str(cache))
+    out = subprocess.run([sys.executable, "-c", _FORCED_SHAPE.format(root=root)], env=env,
+                         capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0, out.stderr[-2000:]
+    assert out.stdout.strip().endswith("EQUAL"), out.stdout[-500:]
