@@ -302,6 +302,60 @@ int ising_ds_result(ising_ds* ds, int8_t* best_spins, double* best_energy,
                     ising_ds_stats* stats, int mem);
 int ising_ds_destroy(ising_ds* ds);
 
+/* ------------------------------------------------------------------ serving */
+
+/* A request server: callers submit instances as they arrive; a worker thread
+ * admits queued requests while their estimated device footprint fits the
+ * memory budget and a slot is free, advances every admitted request by
+ * `chunk_steps` steps per round on its own stream (the kernels of different
+ * requests overlap on the device, and requests that arrive meanwhile join at
+ * the next round), and posts each result when its steps are done. A request
+ * is solved exactly as ising_solve would solve it alone (pruning, domain
+ * selection with the state kept in device memory between steps, best of
+ * restarts, reconstruction, energy), so its result does not depend on what
+ * else is being served. The paper has no counterpart. */
+typedef struct ising_server ising_server;
+
+typedef struct ising_server_cfg {
+  uint64_t budget_bytes; /* device memory the admitted requests may use */
+  int32_t max_active;    /* requests on the GPU at once (streams), >= 1 */
+  int32_t chunk_steps;   /* steps per request per scheduling round, >= 1 */
+  int32_t flags;         /* reserved, 0 */
+  int32_t reserved;
+} ising_server_cfg;
+
+typedef struct ising_result {
+  int32_t status;        /* ISING_OK, or the error the request failed with */
+  int32_t done;          /* 1 once the result is final */
+  int64_t n;
+  double best_energy;    /* energy of the returned spins on the full instance */
+  int64_t best_restart;
+  int64_t best_step;
+  int64_t footprint;     /* estimated device bytes while admitted */
+  double t_submit_ms;    /* host clock, ms since the server was created */
+  double t_admit_ms;
+  double t_done_ms;
+} ising_result;
+
+/* Creates the server on the context's device; the context must outlive it. */
+int ising_server_create(ising_ctx* ctx, const ising_server_cfg* cfg, ising_server** out);
+/* Copies the instance (host or device memory) and queues it with its
+ * parameters and prune flags; *req_id identifies it. ISING_EBUSY when its
+ * estimated footprint exceeds the whole budget (it could never be admitted). */
+int ising_server_submit(ising_server* srv, const ising_instance* inst, const ising_ds_params* p,
+                        int prune_flags, uint64_t* req_id);
+/* Non-blocking: fills *res (res->done tells whether it is final) and, once
+ * done, copies the n best spins to host `spins` if not NULL. ISING_EINVAL for
+ * an unknown id. */
+int ising_server_poll(ising_server* srv, uint64_t req_id, ising_result* res, int8_t* spins);
+/* Blocks until the request is done or `timeout_s` passes (ISING_ETIMEOUT). */
+int ising_server_wait(ising_server* srv, uint64_t req_id, double timeout_s, ising_result* res,
+                      int8_t* spins);
+/* Drops a finished request's stored result. */
+int ising_server_release(ising_server* srv, uint64_t req_id);
+/* Finishes the queued and active requests, stops the worker, frees all. */
+int ising_server_destroy(ising_server* srv);
+
 #ifdef __cplusplus
 }
 #endif

@@ -47,6 +47,18 @@ class DSStats(ctypes.Structure):
                 ("kernel_launches", c_int64), ("resident", c_int32), ("reserved0", c_int32)]
 
 
+class ServerCfg(ctypes.Structure):
+    _fields_ = [("budget_bytes", c_uint64), ("max_active", c_int32), ("chunk_steps", c_int32),
+                ("flags", c_int32), ("reserved", c_int32)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", c_int32), ("done", c_int32), ("n", c_int64),
+                ("best_energy", c_double), ("best_restart", c_int64), ("best_step", c_int64),
+                ("footprint", c_int64), ("t_submit_ms", c_double), ("t_admit_ms", c_double),
+                ("t_done_ms", c_double)]
+
+
 _PROTOS = {
     "ising_version": (c_int, []),
     "ising_create": (c_int, [POINTER(c_void_p), c_int, c_void_p]),
@@ -84,6 +96,13 @@ _PROTOS = {
     "ising_ds_restart_best": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int]),
     "ising_ds_result": (c_int, [c_void_p, c_void_p, POINTER(c_double), POINTER(DSStats), c_int]),
     "ising_ds_destroy": (c_int, [c_void_p]),
+    "ising_server_create": (c_int, [c_void_p, POINTER(ServerCfg), POINTER(c_void_p)]),
+    "ising_server_submit": (c_int, [c_void_p, POINTER(Instance), POINTER(DSParams), c_int,
+                                    POINTER(c_uint64)]),
+    "ising_server_poll": (c_int, [c_void_p, c_uint64, POINTER(Result), c_void_p]),
+    "ising_server_wait": (c_int, [c_void_p, c_uint64, c_double, POINTER(Result), c_void_p]),
+    "ising_server_release": (c_int, [c_void_p, c_uint64]),
+    "ising_server_destroy": (c_int, [c_void_p]),
 }
 
 _lib = None

@@ -193,6 +193,68 @@ def energy(ctx: Context, inst, spins, exact_parts: bool = False):
     return (E, Q, H) if exact_parts else E
 
 
+class Server:
+    """ising_server_*: continuous batching of independent solves (see the
+    header). Requests are copied at submit; results hold the best spins, their
+    energy on the full instance and submit / admit / done times (ms)."""
+
+    def __init__(self, ctx: Context, budget_bytes: int, max_active: int = 8,
+                 chunk_steps: int = 250):
+        self.ctx = ctx
+        cfg = L.ServerCfg()
+        cfg.budget_bytes = int(budget_bytes)
+        cfg.max_active = int(max_active)
+        cfg.chunk_steps = int(chunk_steps)
+        cfg.flags = 0
+        cfg.reserved = 0
+        self.handle = c_void_p()
+        ctx._children.add(self)
+        ctx.check(ctx.lib.ising_server_create(ctx.handle, byref(cfg), byref(self.handle)))
+        self._n = {}
+
+    def submit(self, inst, restarts, steps, zero_rule=True, **kw) -> int:
+        s, keep = make_instance(inst)
+        p = params(restarts, steps, **kw)
+        rid = ctypes.c_uint64()
+        self.ctx.check(self.ctx.lib.ising_server_submit(
+            self.handle, byref(s), byref(p), L.PRUNE_ZERO_RULE if zero_rule else 0, byref(rid)))
+        self._n[rid.value] = int(inst.n)
+        return rid.value
+
+    def _result(self, res, spins):
+        d = {f: getattr(res, f) for f, _ in L.Result._fields_}
+        d["best_spins"] = spins if res.done else None
+        return d
+
+    def poll(self, rid: int):
+        res = L.Result()
+        spins = np.empty(self._n.get(rid, 1), np.int8)
+        self.ctx.check(self.ctx.lib.ising_server_poll(self.handle, rid, byref(res), _ptr(spins)))
+        return self._result(res, spins)
+
+    def wait(self, rid: int, timeout: float = 600.0):
+        res = L.Result()
+        spins = np.empty(self._n[rid], np.int8)
+        self.ctx.check(self.ctx.lib.ising_server_wait(self.handle, rid, float(timeout), byref(res),
+                                                      _ptr(spins)))
+        return self._result(res, spins)
+
+    def release(self, rid: int):
+        self.ctx.check(self.ctx.lib.ising_server_release(self.handle, rid))
+        self._n.pop(rid, None)
+
+    def close(self):
+        if self.handle:
+            self.ctx.lib.ising_server_destroy(self.handle)
+            self.handle = c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def energy_noalloc(inst, spins, E_out, stream=None):
     """ising_energy_noalloc: energies of spins[count][n] into the caller's
     E_out[count] (all torch CUDA tensors); queues the work on `stream`

@@ -730,6 +730,35 @@ int autotune_sparse(ising_ds* ds, int64_t budget, int64_t* done) {
 }  // namespace
 }  // namespace ising
 
+// Queues up to `todo` steps on the session's stream without waiting for them:
+// one cooperative launch in the resident form, otherwise the autotuner's
+// first steps, then graph replays of kGraphSteps steps and single steps.
+int ising::ds_advance(ising_ds* ds, int64_t todo) {
+  if (ds->path == ISING_PATH_TC && tc_is_resident(ds)) {
+    ISING_TRY(tc_run_resident(ds, todo));
+    ds->t += todo;
+    if (ds->p.flags & ISING_DS_PROFILE) ds->kernel_launches += todo;
+    return ISING_OK;
+  }
+  int64_t s0 = 0;
+  if (ds->path == ISING_PATH_SPARSE && !ds->tuned) ISING_TRY(autotune_sparse(ds, todo, &s0));
+  const bool use_graph = !(ds->p.flags & ISING_DS_PROFILE) && todo >= 2 * kGraphSteps;
+  for (int64_t s = s0; s < todo;) {
+    // (t > 0: the kernels have run once outside capture, which sets their attributes)
+    if (use_graph && ds->t > 0 && ds->t % 6 == 0 && todo - s >= kGraphSteps) {
+      if (!ds->graph) ISING_TRY(build_graph(ds));
+      ISING_TRY(replay_graph(ds));
+      s += kGraphSteps;
+    } else {
+      ISING_TRY(path_step(ds, true));
+      ISING_TRY(track_step(ds));
+      ds->t += 1;
+      s += 1;
+    }
+  }
+  return ISING_OK;
+}
+
 extern "C" int ising_ds_run(ising_ds* ds, int64_t steps) {
   if (!ds) return ISING_EINVAL;
   ising_ctx* ctx = ds->ctx;
@@ -741,46 +770,11 @@ extern "C" int ising_ds_run(ising_ds* ds, int64_t steps) {
   ISING_CUDA(ctx, cudaEventCreate(&e0));
   ISING_CUDA(ctx, cudaEventCreate(&e1));
   ISING_CUDA(ctx, cudaEventRecord(e0, ctx->stream));
-  if (ds->path == ISING_PATH_TC && tc_is_resident(ds)) {
-    // all steps in one cooperative launch, state resident in tensor memory
-    int rc = tc_run_resident(ds, todo);
-    if (rc != ISING_OK) {
-      cudaEventDestroy(e0);
-      cudaEventDestroy(e1);
-      return rc;
-    }
-    ds->t += todo;
-    if (ds->p.flags & ISING_DS_PROFILE) ds->kernel_launches += todo;
-    todo = 0;
-  }
-  int64_t s0 = 0;
-  if (ds->path == ISING_PATH_SPARSE && !ds->tuned) {
-    int rc = autotune_sparse(ds, todo, &s0);
-    if (rc != ISING_OK) {
-      cudaEventDestroy(e0);
-      cudaEventDestroy(e1);
-      return rc;
-    }
-  }
-  const bool use_graph = !(ds->p.flags & ISING_DS_PROFILE) && todo >= 2 * kGraphSteps;
-  for (int64_t s = s0; s < todo;) {
-    int rc = ISING_OK;
-    // (t > 0: the kernels have run once outside capture, which sets their attributes)
-    if (use_graph && ds->t > 0 && ds->t % 6 == 0 && todo - s >= kGraphSteps) {
-      if (!ds->graph) rc = build_graph(ds);
-      if (rc == ISING_OK) rc = replay_graph(ds);
-      s += kGraphSteps;
-    } else {
-      rc = path_step(ds, true);
-      if (rc == ISING_OK) rc = track_step(ds);
-      ds->t += 1;
-      s += 1;
-    }
-    if (rc != ISING_OK) {
-      cudaEventDestroy(e0);
-      cudaEventDestroy(e1);
-      return rc;
-    }
+  int rc = ds_advance(ds, todo);
+  if (rc != ISING_OK) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
   }
   ISING_CUDA(ctx, cudaEventRecord(e1, ctx->stream));
   ISING_CUDA(ctx, cudaEventSynchronize(e1));

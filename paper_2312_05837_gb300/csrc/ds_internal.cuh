@@ -179,6 +179,9 @@ int tc_trace(ising_ds* ds, uint64_t* out, int64_t cap, int64_t* count);
 void tc_release(ising_ds* ds);
 
 // Shared session services (ds.cu).
+int ds_advance(ising_ds* ds, int64_t todo);  // queue steps without waiting
+int ds_create_impl(ising_ctx* ctx, const ising_instance* inst, const ising_ds_params* p,
+                   ising_ds** out, bool validate);
 int track_step(ising_ds* ds);  // reduce partials of step t+1, best tracking, t += 1
 int export_spins_int8(ising_ds* ds, int slot, int8_t* out);  // spins[slot] -> int8 [B][n]
 

@@ -44,7 +44,8 @@ def test_struct_layouts_match_the_header(tmp_path):
     if cc is None:
         pytest.skip("no C compiler")
     structs = {"ising_instance": L.Instance, "ising_ds_params": L.DSParams,
-               "ising_ds_stats": L.DSStats}
+               "ising_ds_stats": L.DSStats, "ising_server_cfg": L.ServerCfg,
+               "ising_result": L.Result}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "ising_ds.h"',
              'int main(void) {']
     for cname, cls in structs.items():

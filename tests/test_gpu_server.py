@@ -1,0 +1,72 @@
+"""The request server (continuous batching of independent solves): each
+result equals the same request solved alone, admission follows the memory
+budget, and oversized requests are refused."""
+
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import ising
+from paper_2312_05837_gb300 import api
+
+pytestmark = pytest.mark.gpu
+
+
+def _mix():
+    return [
+        (synth.er_dense(300, 1, p=0.05, weights="pm1"), dict(restarts=256, steps=300)),
+        (synth.sk_dense(200, 2, 1 / math.sqrt(200), np.float32, h_std=0.3),
+         dict(restarts=200, steps=260, precision="tc")),
+        (synth.torus_csr(20, 30, 3), dict(restarts=256, steps=333)),
+        (synth.er_pendant_csr(400, 3.0, 100, 3, 4, h_mode="int2"), dict(restarts=128, steps=280)),
+        (synth.er_dense(520, 5, mean_degree=8, weights="pm1"), dict(restarts=300, steps=250)),
+        (synth.random_sparse_instance(90, 6, p=0.1, kind="int", h="int", layout="dense"),
+         dict(restarts=64, steps=500, precision="fp32")),
+    ]
+
+
+def test_results_in_the_mix_equal_results_alone(gpu_ctx):
+    mix = _mix()
+    alone = [api.solve(gpu_ctx, inst, seed=11 + k, **kw) for k, (inst, kw) in enumerate(mix)]
+    srv = api.Server(gpu_ctx, budget_bytes=8 << 30, max_active=4, chunk_steps=64)
+    ids = [srv.submit(inst, seed=11 + k, **kw) for k, (inst, kw) in enumerate(mix)]
+    for k, rid in enumerate(ids):
+        res = srv.wait(rid, timeout=300)
+        assert res["status"] == 0 and res["done"] == 1
+        np.testing.assert_array_equal(res["best_spins"], alone[k]["best_spins"])
+        assert res["best_energy"] == alone[k]["best_energy"]
+        e = ising.energy(mix[k][0], res["best_spins"].astype(np.float64))
+        assert res["best_energy"] == pytest.approx(float(e), rel=1e-12, abs=1e-9)
+        assert res["t_submit_ms"] <= res["t_admit_ms"] <= res["t_done_ms"]
+    srv.close()
+
+
+def test_admission_follows_the_budget(gpu_ctx):
+    mix = _mix()[:4]
+    srv = api.Server(gpu_ctx, budget_bytes=8 << 30, max_active=4, chunk_steps=100)
+    fps = []
+    for inst, kw in mix:
+        rid = srv.submit(inst, **kw)
+        fps.append(srv.wait(rid)["footprint"])
+    srv.close()
+    # a budget that holds any one request but no two: requests run one at a time
+    budget = max(fps) + min(fps) // 2
+    srv = api.Server(gpu_ctx, budget_bytes=budget, max_active=4, chunk_steps=100)
+    ids = [srv.submit(inst, **kw) for inst, kw in mix]
+    res = [srv.wait(r, timeout=300) for r in ids]
+    for a, b in zip(res, res[1:]):
+        assert b["t_admit_ms"] >= a["t_done_ms"] - 1e-6
+    assert all(r["status"] == 0 for r in res)
+    srv.close()
+
+
+def test_oversized_request_is_refused_and_unknown_ids_are_errors(gpu_ctx):
+    srv = api.Server(gpu_ctx, budget_bytes=1 << 20, max_active=2, chunk_steps=10)
+    with pytest.raises(api.IsingError) as e:
+        srv.submit(synth.er_dense(300, 1, p=0.05), restarts=256, steps=10)
+    assert e.value.code == 5
+    with pytest.raises(api.IsingError):
+        srv.poll(12345)
+    srv.close()
