@@ -56,6 +56,8 @@ def args_():
     ap.add_argument("--mu", type=float, default=0.0)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the time-to-target and serving legs")
     ap.add_argument("--profile-steps", type=int, default=200)
     return ap.parse_args()
 
@@ -246,6 +248,94 @@ def cpu_baseline(a, inst, B, seconds):
                       f"(numpy FP64, {dt:.1f} s)"}
 
 
+# ----------------------------------------------------------------- time to target
+
+def time_to_target(ctx, dinst, B, T, seed, chunk=50):
+    """Device time until the best-so-far energy reaches E*, the final best of
+    the plain FP32 form on the same instance and seed, for the plain form and
+    the default (tensor-core) form; both advance in chunks of `chunk` steps and
+    are checked after each chunk."""
+    import numpy as np
+    from paper_2312_05837_gb300 import api
+
+    def trace(prec):
+        s = api.Session(ctx, dinst, restarts=B, steps=T, seed=seed, precision=prec)
+        hist = []
+        done = 0
+        while done < T:
+            k = min(chunk, T - done)
+            s.run(k)
+            done += k
+            hist.append((s.result()["device_ms"], float(np.min(s.restart_best()[0]))))
+        s.finish()
+        r = s.result()
+        s.close()
+        return hist, r
+
+    hist_p, rp = trace("fp32")
+    target = rp["best_energy"]
+    hist_f, rf = trace("auto")
+
+    def first(hist):
+        for ms, e in hist:
+            if e <= target:
+                return ms
+        return None
+
+    tp, tf = first(hist_p), first(hist_f)
+    return {"target_energy": target, "plain_fp32_ms": tp, "fast_ms": tf,
+            "fast_precision": {1: "fp32", 2: "tc-bf16", 3: "bf16", 4: "e4m3"}.get(rf["precision"]),
+            "speedup": (tp / tf) if (tp and tf) else None, "chunk_steps": chunk,
+            "fast_best_energy": rf["best_energy"]}
+
+
+# ----------------------------------------------------------------- serving
+
+def serving(ctx, count=40, rate=200.0, n_max=2048, B=256, T=2000, seed=5):
+    """A Poisson stream of mixed requests (half dense Gaussian SK, half sparse
+    ER, N log-uniform in [64, n_max]) through the request server, against the
+    plain per-request FP32 form processing the same stream one request at a
+    time in arrival order. Latency = done - arrival."""
+    import numpy as np
+    import synth
+    from paper_2312_05837_gb300 import api
+    reqs = synth.serving_stream(count, seed, rate=rate, n_max=n_max)
+    srv = api.Server(ctx, budget_bytes=120 << 30, max_active=8, chunk_steps=250)
+    t0 = time.perf_counter()
+    ids = []
+    for k, (ta, inst) in enumerate(reqs):
+        wait = t0 + ta - time.perf_counter()
+        if wait > 0:
+            time.sleep(wait)
+        ids.append(srv.submit(inst, restarts=B, steps=T, seed=k))
+    res = [srv.wait(r, timeout=1200) for r in ids]
+    srv.close()
+    lat = np.array([r["t_done_ms"] - r["t_submit_ms"] for r in res])
+    span = (max(r["t_done_ms"] for r in res) - min(r["t_submit_ms"] for r in res)) / 1e3
+    # plain per-request FP32: measured service time of each request alone,
+    # served first come first served from the same arrival times
+    service = []
+    for k, (ta, inst) in enumerate(reqs):
+        w0 = time.perf_counter()
+        api.solve(ctx, inst, restarts=B, steps=T, seed=k, precision="fp32")
+        service.append(time.perf_counter() - w0)
+    done = 0.0
+    lat_p = []
+    for (ta, _), sv in zip(reqs, service):
+        start = max(ta, done)
+        done = start + sv
+        lat_p.append(1e3 * (done - ta))
+    lat_p = np.array(lat_p)
+    return {"requests": count, "rate_per_s": rate, "n_range": [64, n_max], "restarts": B,
+            "steps": T, "mix": "50% dense SK J~N(0,1/N) h~N(0,0.1), 50% sparse ER deg 8 +-1",
+            "served": {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                       "instances_per_s": count / span, "max_active": 8, "chunk_steps": 250},
+            "plain_fp32_per_request": {"p50_ms": float(np.percentile(lat_p, 50)),
+                                       "p99_ms": float(np.percentile(lat_p, 99)),
+                                       "instances_per_s": count / (done - reqs[0][0])},
+            "all_ok": all(r["status"] == 0 for r in res)}
+
+
 # ----------------------------------------------------------------- main
 
 def main():
@@ -376,6 +466,9 @@ def main():
             "gpu_launches": launches_per_solve(T, rounds, path, bool(last["resident"])) * a.steps,
             "roofline": roof, "clocks": clk,
             "best_energy": float(last["best_energy"].item())}
+    if rank == 0 and not a.no_extras:
+        line["time_to_target"] = time_to_target(ctx, dinst, B, T, seed=3)
+        line["serving"] = serving(ctx)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(a, inst, B, a.cpu_seconds)
     if rank == 0:

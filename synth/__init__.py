@@ -23,4 +23,5 @@ from .instances import (  # noqa: F401
     table1_instance,
     random_sparse_instance,
     workload,
+    serving_stream,
 )

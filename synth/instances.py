@@ -378,3 +378,29 @@ def workload(name: str, seed: int = 0) -> Instance:
         return er_pendant_csr(100000, 4.0, 20000, 3, seed, h_mode="int2",
                               name="er100k_pendant_h")
     raise KeyError(name)
+
+
+def serving_stream(count: int, seed: int, rate: float = 200.0, n_min: int = 64,
+                   n_max: int = 8192, dense_fraction: float = 0.5, sparse_degree: float = 8.0):
+    """Request stream shaped like the serving workload: Poisson arrivals at
+    `rate` per second, N log-uniform in [n_min, n_max], a `dense_fraction` of
+    dense Gaussian SK instances (J ~ N(0, 1/N), h ~ N(0, 0.1)) and the rest
+    sparse ER graphs of the given mean degree with couplings +-1. Returns a
+    list of (arrival time in seconds, Instance)."""
+    rng = _rng(seed, 10)
+    t = 0.0
+    out = []
+    for k in range(count):
+        t += float(rng.exponential(1.0 / rate))
+        n = int(round(math.exp(rng.uniform(math.log(n_min), math.log(n_max)))))
+        if rng.random() < dense_fraction:
+            inst = sk_dense(n, seed * 100003 + k, math.sqrt(1.0 / n), np.float32,
+                            h_std=math.sqrt(0.1), name=f"req{k}-sk{n}")
+        else:
+            e = er_graph_edges(n, seed * 100003 + k, mean_degree=min(sparse_degree, n - 1))
+            w = _pm1(_rng(seed * 100003 + k, 11), e.shape[0])
+            indptr, indices, data = csr_from_edges(n, e, w)
+            inst = Instance(n=n, layout="csr", indptr=indptr, indices=indices, data=data,
+                            j_scale=1.0, convention="physics", name=f"req{k}-er{n}")
+        out.append((t, inst))
+    return out
