@@ -18,6 +18,22 @@ using namespace ising;
 namespace ising {
 namespace {
 
+// asin(x) to FP32 accuracy from a double x: directly for |x| <= 1/2, else by
+// asin(x) = pi/2 - 2 asin(sqrt((1 - |x|) / 2)) with 1 - |x| formed exactly in
+// FP64 (the direct form loses accuracy near |x| = 1 where its slope blows up).
+// The sign of x is kept (x0 is 0 or at least 2^-52 in magnitude).
+__device__ __forceinline__ float asin_of(double x) {
+  const double ax = fabs(x);
+  float r;
+  if (ax <= 0.5) {
+    r = asinf((float)ax);
+  } else {
+    const float y = (float)((1.0 - ax) * 0.5);
+    r = 1.57079632679489662f - 2.0f * asinf(sqrtf(y));
+  }
+  return x < 0.0 ? -r : r;
+}
+
 // theta_0 = asin(x0), x0 = SplitMix64(seed, (b << 32) | i) mapped to [-1, 1);
 // m = v = 0; S_1 = sgn+(x0). Dense state is [Bp][ld] restart-major, sparse
 // state [n][Bp].
@@ -36,7 +52,7 @@ __global__ void init_kernel(int64_t n, int64_t Bp, int64_t ld, bool spin_major, 
     if (!pad) {
       uint64_t z = splitmix64(seed, ((uint64_t)b << 32) | (uint64_t)i);
       double x0 = 2.0 * ((double)(z >> 11) * 0x1.0p-53) - 1.0;
-      th = (float)asin(x0);
+      th = asin_of(x0);
       pos = x0 >= 0.0;
     }
     theta[e] = th;
@@ -137,6 +153,85 @@ __global__ void __launch_bounds__(256) track_kernel(
   }
   __shared__ bool last;
   __syncthreads();
+  __threadfence();
+  if (threadIdx.x == 0) {
+    unsigned long long prev = atomicAdd(reinterpret_cast<unsigned long long*>(&counters[1]), 1ull);
+    last = prev == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    counters[0] = t;
+    counters[1] = 0;
+    __threadfence();
+  }
+}
+
+// Best tracking for the bit-packed spins of the sparse path: a block owns 32
+// consecutive restarts (one spin word column). Energies and bests as in
+// track_kernel (one warp per restart, same order); the spins of the improved
+// restarts are then copied by 32 x 32 bit transposes: a lane loads the word of
+// spin i0 + lane, and one ballot per restart gives its 32 spins.
+__global__ void __launch_bounds__(256) track_bits_kernel(
+    int64_t n, int64_t B, int64_t Bp, int mtiles, bool int_mode, double cq, double chs,
+    const long long* __restrict__ qpart, const long long* __restrict__ hpart,
+    const float* __restrict__ epart, const uint32_t* __restrict__ bits,
+    double* __restrict__ best_E, long long* __restrict__ best_t, int8_t* __restrict__ best_s,
+    double* __restrict__ last_E, long long* __restrict__ counters, int64_t bs_ld) {
+  __shared__ unsigned int improved_mask;
+  const long long t = counters[0] + 1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t words = Bp / 32;
+  for (int64_t w = blockIdx.x; w < words; w += gridDim.x) {
+    if (threadIdx.x == 0) improved_mask = 0u;
+    __syncthreads();
+    for (int r = warp; r < 32; r += 8) {
+      const int64_t b = w * 32 + r;
+      if (b >= B) continue;
+      double E;
+      if (int_mode) {
+        long long q = 0, hs = 0;
+        for (int k = lane; k < mtiles; k += 32) {
+          q += qpart[(int64_t)k * Bp + b];
+          hs += hpart[(int64_t)k * Bp + b];
+        }
+        for (int o = 16; o; o >>= 1) {
+          q += __shfl_xor_sync(0xffffffffu, q, o);
+          hs += __shfl_xor_sync(0xffffffffu, hs, o);
+        }
+        E = cq * (double)q + chs * (double)hs;
+      } else {
+        double e = 0.0;
+        for (int k = lane; k < mtiles; k += 32) e += (double)epart[(int64_t)k * Bp + b];
+        for (int o = 16; o; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+        E = e;
+      }
+      const bool improved = E < best_E[b];
+      __syncwarp();
+      if (lane == 0) {
+        last_E[b] = E;
+        if (improved) {
+          best_E[b] = E;
+          best_t[b] = t;
+          atomicOr(&improved_mask, 1u << r);
+        }
+      }
+    }
+    __syncthreads();
+    const unsigned int mask = improved_mask;
+    if (mask) {
+      for (int64_t i0 = (int64_t)warp * 32; i0 < n; i0 += 8 * 32) {
+        const int64_t i = i0 + lane;
+        const uint32_t word = i < n ? bits[i * words + w] : 0u;
+        for (int r = 0; r < 32; ++r) {
+          if (!((mask >> r) & 1u)) continue;
+          const uint32_t col = __ballot_sync(0xffffffffu, (word >> r) & 1u);
+          if (i < n) best_s[(w * 32 + r) * bs_ld + i] = ((col >> lane) & 1u) ? 1 : -1;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  __shared__ bool last;
   __threadfence();
   if (threadIdx.x == 0) {
     unsigned long long prev = atomicAdd(reinterpret_cast<unsigned long long*>(&counters[1]), 1ull);
@@ -295,7 +390,15 @@ int track_step(ising_ds* ds) {
     case kSpinF32: ISING_TRACK(kSpinF32); break;
     case kSpinBF16: ISING_TRACK(kSpinBF16); break;
     case kSpinE4M3: ISING_TRACK(kSpinE4M3); break;
-    default: ISING_TRACK(kSpinBits); break;
+    default:
+      track_bits_kernel<<<(int)std::min<int64_t>(ds->Bp / 32, (int64_t)ctx->sm_count * 4), 256, 0,
+                          ctx->stream>>>(
+          ds->n, ds->B, ds->Bp, ds->mtiles, ds->int_energy, ds->inst.cq, chs,
+          ds->qpart[pslot].as<long long>(), ds->hpart[pslot].as<long long>(),
+          ds->epart[pslot].as<float>(), ds->spins[slot].as<uint32_t>(), ds->best_E.as<double>(),
+          ds->best_t.as<long long>(), ds->best_s.as<int8_t>(), ds->last_E.as<double>(),
+          ds->counters.as<long long>(), ds->bs_ld);
+      break;
   }
 #undef ISING_TRACK
   ISING_CUDA(ctx, cudaGetLastError());

@@ -207,24 +207,37 @@ __global__ void k_values_double(const void* J, int dt, int64_t count, double* ou
     out[e] = load_as_double(J, dt, e);
 }
 
-// Dense -> CSR (non-zero entries, increasing column), used by pruning only.
+// Dense -> CSR (non-zero entries, increasing column), used by pruning only:
+// a warp per row, 32 columns per ballot, positions from the ballot prefix.
 __global__ void k_dense_count(const void* J, int dt, int64_t n, int32_t* cnt) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t i = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
     int c = 0;
-    for (int64_t j = 0; j < n; ++j) c += load_as_double(J, dt, i * n + j) != 0.0;
-    cnt[i] = c;
+    for (int64_t j0 = 0; j0 < n; j0 += 32) {
+      const int64_t j = j0 + lane;
+      c += __popc(__ballot_sync(0xffffffffu, j < n && load_as_double(J, dt, i * n + j) != 0.0));
+    }
+    if (lane == 0) cnt[i] = c;
   }
 }
 
 __global__ void k_dense_fill(const void* J, int dt, int64_t n, const int32_t* rowptr,
                              int32_t* col, double* val) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t i = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
     int o = rowptr[i];
-    for (int64_t j = 0; j < n; ++j) {
-      double x = load_as_double(J, dt, i * n + j);
-      if (x != 0.0) { col[o] = (int32_t)j; val[o] = x; ++o; }
+    for (int64_t j0 = 0; j0 < n; j0 += 32) {
+      const int64_t j = j0 + lane;
+      const double x = j < n ? load_as_double(J, dt, i * n + j) : 0.0;
+      const unsigned int m = __ballot_sync(0xffffffffu, x != 0.0);
+      if (x != 0.0) {
+        const int pos = o + __popc(m & ((1u << lane) - 1u));
+        col[pos] = (int32_t)j;
+        val[pos] = x;
+      }
+      o += __popc(m);
     }
   }
 }
@@ -362,7 +375,7 @@ int ising::prune_device(ising_ctx* ctx, const DevInstance& I, int flags,
   } else {
     DevMem cnt;
     ISING_TRY(dev_alloc(ctx, cnt, n * 4));
-    k_dense_count<<<grid_n(ctx, n), 256, 0, st>>>(I.J.p, I.j_dtype, n, cnt.as<int32_t>());
+    k_dense_count<<<grid_n(ctx, n * 32), 256, 0, st>>>(I.J.p, I.j_dtype, n, cnt.as<int32_t>());
     std::vector<int32_t> c(n), rp(n + 1);
     ISING_CUDA(ctx, cudaMemcpyAsync(c.data(), cnt.p, n * 4, cudaMemcpyDeviceToHost, st));
     ISING_CUDA(ctx, cudaStreamSynchronize(st));
@@ -373,7 +386,7 @@ int ising::prune_device(ising_ctx* ctx, const DevInstance& I, int flags,
     ISING_TRY(dev_alloc(ctx, col, nnz * 4));
     ISING_TRY(dev_alloc(ctx, val, nnz * 8));
     ISING_CUDA(ctx, cudaMemcpyAsync(rowptr.p, rp.data(), (n + 1) * 4, cudaMemcpyHostToDevice, st));
-    k_dense_fill<<<grid_n(ctx, n), 256, 0, st>>>(I.J.p, I.j_dtype, n, rowptr.as<int32_t>(),
+    k_dense_fill<<<grid_n(ctx, n * 32), 256, 0, st>>>(I.J.p, I.j_dtype, n, rowptr.as<int32_t>(),
                                                  col.as<int32_t>(), val.as<double>());
     ISING_CUDA(ctx, cudaStreamSynchronize(st));
   }
