@@ -165,14 +165,28 @@ def launches_per_solve(T: int, rounds: int, path: int, resident: bool) -> int:
     """Kernels of one solve: instance check (1), pruning (dense->CSR 2, init 1,
     7 per round incl. the final empty one, sum + reduced field + reduced J 3),
     session set-up (facts 1, operand 1, fills 2, init 1), the steps (one
-    cooperative launch when resident, else step + track per step), finish
-    (energy-only step + track + argmin), reconstruction (1), full-instance
-    energy (2)."""
-    steps = 1 if resident else 2 * T
-    return 1 + 3 + 7 * (rounds + 1) + 3 + 5 + steps + 3 + 1 + 2
+    cooperative launch when resident, else step + track per step, plus the
+    copy of improved bit-packed spins on the sparse path), finish
+    (energy-only step + track (+ copy) + argmin), reconstruction (1),
+    full-instance energy (2)."""
+    per_step = 3 if path == 2 else 2
+    steps = 1 if resident else per_step * T
+    return 1 + 3 + 7 * (rounds + 1) + 3 + 5 + steps + per_step + 1 + 1 + 2
 
 
 # ----------------------------------------------------------------- reference arm
+
+def over_ranks(dist, x: float, op: str, device) -> float:
+    """The max or the sum of a per-rank number over all ranks (the number
+    itself without a process group); `device` is where the collective's
+    tensor lives ("cuda" for NCCL, "cpu" for gloo)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
 
 def run_reference(a, rank, world):
     """The FP64 CPU oracle on the same workload: each step is one bounded
@@ -396,12 +410,12 @@ def main():
         total_ms += e0.elapsed_time(e1)
     barrier()
     clk = clocks.stop()
-    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    max_ms = float(t.item())
+    max_ms = over_ranks(dist, total_ms, "max", "cuda")
     units = n_red * B * T
-    value = world * units * a.steps / (max_ms / 1e3)
+    # each rank solves its own instance (seeded by its rank), so the reduced
+    # sizes differ: the job's units are the sum over ranks
+    job_units = over_ranks(dist, float(units), "sum", "cuda")
+    value = job_units * a.steps / (max_ms / 1e3)
 
     # end to end: host (pinned) inputs, host outputs, copies inside the timed region
     barrier()
@@ -410,10 +424,7 @@ def main():
         out = api.solve(ctx, hinst, restarts=B, steps=T, seed=k, **kw)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - w0
-    te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = world * units * a.steps / float(te.item())
+    e2e_value = job_units * a.steps / over_ranks(dist, e2e_s, "max", "cuda")
 
     # dominant kernel: the fused step, timed launch by launch with events
     prof = api.Session(ctx, dinst, restarts=B, steps=a.profile_steps, seed=7, profile=True, **kw)

@@ -102,15 +102,17 @@ __device__ __forceinline__ int8_t spin_at(const void* spins, int64_t n, int64_t 
 // Best tracking for step t = counters[0] + 1, one warp per restart: E_t(b)
 // from the partials of slot t % 2 (lane l adds rows l, l+32, ... in order,
 // then a fixed xor tree across lanes, so the sum is deterministic), strict <
-// against the best so far, copy of S_t for improved restarts; the last block
-// advances the step counter.
+// against the best so far, copy of S_t for improved restarts (for bit-packed
+// spins a per-restart flag instead, which track_bits_copy_kernel reads); the
+// last block advances the step counter.
 template <int KIND>
 __global__ void __launch_bounds__(256) track_kernel(
     int64_t n, int64_t B, int64_t Bp, int64_t ld, int mtiles, bool int_mode, double cq,
     double chs, const long long* __restrict__ qpart, const long long* __restrict__ hpart,
     const float* __restrict__ epart, const void* __restrict__ spins_t,
     double* __restrict__ best_E, long long* __restrict__ best_t, int8_t* __restrict__ best_s,
-    double* __restrict__ last_E, long long* __restrict__ counters, int64_t bs_ld) {
+    double* __restrict__ last_E, long long* __restrict__ counters, int64_t bs_ld,
+    uint8_t* __restrict__ improved_out) {
   const long long t = counters[0] + 1;
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -119,6 +121,7 @@ __global__ void __launch_bounds__(256) track_kernel(
     double E;
     if (int_mode) {
       long long q = 0, hs = 0;
+#pragma unroll 4
       for (int r = lane; r < mtiles; r += 32) {
         q += qpart[(int64_t)r * Bp + b];
         hs += hpart[(int64_t)r * Bp + b];
@@ -130,6 +133,7 @@ __global__ void __launch_bounds__(256) track_kernel(
       E = cq * (double)q + chs * (double)hs;
     } else {
       double e = 0.0;
+#pragma unroll 4
       for (int r = lane; r < mtiles; r += 32) e += (double)epart[(int64_t)r * Bp + b];
       for (int o = 16; o; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
       E = e;
@@ -144,11 +148,11 @@ __global__ void __launch_bounds__(256) track_kernel(
         best_t[b] = t;
       }
     }
-    if (improved) {
-      if (KIND == kSpinBits)
-        for (int64_t i = lane; i < n; i += 32) best_s[b * bs_ld + i] = spin_at<KIND>(spins_t, n, Bp, ld, b, i);
-      else
-        copy_spin_row_dense<KIND>(best_s + b * bs_ld, spins_t, n, ld, b, lane);
+    if (KIND == kSpinBits) {
+      // bit-packed spins are copied by track_bits_copy_kernel
+      if (lane == 0) improved_out[b] = improved ? 1 : 0;
+    } else if (improved) {
+      copy_spin_row_dense<KIND>(best_s + b * bs_ld, spins_t, n, ld, b, lane);
     }
   }
   __shared__ bool last;
@@ -166,82 +170,32 @@ __global__ void __launch_bounds__(256) track_kernel(
   }
 }
 
-// Best tracking for the bit-packed spins of the sparse path: a block owns 32
-// consecutive restarts (one spin word column). Energies and bests as in
-// track_kernel (one warp per restart, same order); the spins of the improved
-// restarts are then copied by 32 x 32 bit transposes: a lane loads the word of
-// spin i0 + lane, and one ballot per restart gives its 32 spins.
-__global__ void __launch_bounds__(256) track_bits_kernel(
-    int64_t n, int64_t B, int64_t Bp, int mtiles, bool int_mode, double cq, double chs,
-    const long long* __restrict__ qpart, const long long* __restrict__ hpart,
-    const float* __restrict__ epart, const uint32_t* __restrict__ bits,
-    double* __restrict__ best_E, long long* __restrict__ best_t, int8_t* __restrict__ best_s,
-    double* __restrict__ last_E, long long* __restrict__ counters, int64_t bs_ld) {
-  __shared__ unsigned int improved_mask;
-  const long long t = counters[0] + 1;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t words = Bp / 32;
-  for (int64_t w = blockIdx.x; w < words; w += gridDim.x) {
-    if (threadIdx.x == 0) improved_mask = 0u;
-    __syncthreads();
-    for (int r = warp; r < 32; r += 8) {
-      const int64_t b = w * 32 + r;
-      if (b >= B) continue;
-      double E;
-      if (int_mode) {
-        long long q = 0, hs = 0;
-        for (int k = lane; k < mtiles; k += 32) {
-          q += qpart[(int64_t)k * Bp + b];
-          hs += hpart[(int64_t)k * Bp + b];
-        }
-        for (int o = 16; o; o >>= 1) {
-          q += __shfl_xor_sync(0xffffffffu, q, o);
-          hs += __shfl_xor_sync(0xffffffffu, hs, o);
-        }
-        E = cq * (double)q + chs * (double)hs;
-      } else {
-        double e = 0.0;
-        for (int k = lane; k < mtiles; k += 32) e += (double)epart[(int64_t)k * Bp + b];
-        for (int o = 16; o; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
-        E = e;
-      }
-      const bool improved = E < best_E[b];
-      __syncwarp();
-      if (lane == 0) {
-        last_E[b] = E;
-        if (improved) {
-          best_E[b] = E;
-          best_t[b] = t;
-          atomicOr(&improved_mask, 1u << r);
-        }
-      }
+// Copy of S_t into best_s for the restarts that improved at step t, for the
+// bit-packed spins of the sparse path (the flags come from track_kernel). A
+// warp task is one spin word column w (restarts 32w .. 32w + 31) over 32
+// consecutive spins: a lane loads the word of its spin and writes bit r of it
+// to row 32w + r of best_s for every improved r, so each store of the warp
+// covers 32 consecutive bytes of one row.
+__global__ void __launch_bounds__(256) track_bits_copy_kernel(
+    int64_t n, int64_t B, int64_t words, const uint32_t* __restrict__ bits,
+    const uint8_t* __restrict__ improved, int8_t* __restrict__ best_s, int64_t bs_ld) {
+  const int lane = threadIdx.x & 31;
+  const int64_t chunks = (n + 31) / 32;
+  const int64_t tasks = chunks * words;
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t task = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); task < tasks;
+       task += nwarps) {
+    const int64_t w = task / chunks;
+    const int64_t i = (task - w * chunks) * 32 + lane;
+    const int64_t b = w * 32 + lane;
+    const unsigned int mask = __ballot_sync(0xffffffffu, b < B && improved[b] != 0);
+    if (!mask) continue;
+    if (i >= n) continue;
+    const uint32_t word = bits[i * words + w];
+    for (unsigned int m = mask; m; m &= m - 1) {
+      const int r = __ffs(m) - 1;
+      best_s[(w * 32 + r) * bs_ld + i] = ((word >> r) & 1u) ? 1 : -1;
     }
-    __syncthreads();
-    const unsigned int mask = improved_mask;
-    if (mask) {
-      for (int64_t i0 = (int64_t)warp * 32; i0 < n; i0 += 8 * 32) {
-        const int64_t i = i0 + lane;
-        const uint32_t word = i < n ? bits[i * words + w] : 0u;
-        for (int r = 0; r < 32; ++r) {
-          if (!((mask >> r) & 1u)) continue;
-          const uint32_t col = __ballot_sync(0xffffffffu, (word >> r) & 1u);
-          if (i < n) best_s[(w * 32 + r) * bs_ld + i] = ((col >> lane) & 1u) ? 1 : -1;
-        }
-      }
-    }
-    __syncthreads();
-  }
-  __shared__ bool last;
-  __threadfence();
-  if (threadIdx.x == 0) {
-    unsigned long long prev = atomicAdd(reinterpret_cast<unsigned long long*>(&counters[1]), 1ull);
-    last = prev == gridDim.x - 1;
-  }
-  __syncthreads();
-  if (last && threadIdx.x == 0) {
-    counters[0] = t;
-    counters[1] = 0;
-    __threadfence();
   }
 }
 
@@ -385,20 +339,22 @@ int track_step(ising_ds* ds) {
       ds->qpart[pslot].as<long long>(), ds->hpart[pslot].as<long long>(),                    \
       ds->epart[pslot].as<float>(), ds->spins[slot].p, ds->best_E.as<double>(),              \
       ds->best_t.as<long long>(), ds->best_s.as<int8_t>(), ds->last_E.as<double>(),          \
-      ds->counters.as<long long>(), ds->bs_ld)
+      ds->counters.as<long long>(), ds->bs_ld, ds->improved.as<uint8_t>())
   switch (ds->spin_kind) {
     case kSpinF32: ISING_TRACK(kSpinF32); break;
     case kSpinBF16: ISING_TRACK(kSpinBF16); break;
     case kSpinE4M3: ISING_TRACK(kSpinE4M3); break;
-    default:
-      track_bits_kernel<<<(int)std::min<int64_t>(ds->Bp / 32, (int64_t)ctx->sm_count * 4), 256, 0,
-                          ctx->stream>>>(
-          ds->n, ds->B, ds->Bp, ds->mtiles, ds->int_energy, ds->inst.cq, chs,
-          ds->qpart[pslot].as<long long>(), ds->hpart[pslot].as<long long>(),
-          ds->epart[pslot].as<float>(), ds->spins[slot].as<uint32_t>(), ds->best_E.as<double>(),
-          ds->best_t.as<long long>(), ds->best_s.as<int8_t>(), ds->last_E.as<double>(),
-          ds->counters.as<long long>(), ds->bs_ld);
+    default: {
+      ISING_TRACK(kSpinBits);
+      const int64_t words = ds->Bp / 32;
+      const int64_t tasks = (ds->n + 31) / 32 * words;
+      const int cgrid = (int)std::max<int64_t>(
+          1, std::min<int64_t>((tasks + 7) / 8, (int64_t)ctx->sm_count * 8));
+      track_bits_copy_kernel<<<cgrid, 256, 0, ctx->stream>>>(
+          ds->n, ds->B, words, ds->spins[slot].as<uint32_t>(), ds->improved.as<uint8_t>(),
+          ds->best_s.as<int8_t>(), ds->bs_ld);
       break;
+    }
   }
 #undef ISING_TRACK
   ISING_CUDA(ctx, cudaGetLastError());
@@ -474,6 +430,7 @@ int common_alloc(ising_ds* ds) {
   ds->bs_ld = (n + 15) / 16 * 16;
   ISING_TRY(dev_alloc(ctx, ds->best_s, (size_t)B * ds->bs_ld));
   ISING_TRY(dev_alloc(ctx, ds->last_E, B * 8));
+  ISING_TRY(dev_alloc(ctx, ds->improved, B));
   ISING_TRY(dev_alloc(ctx, ds->counters, 16));
   ISING_TRY(dev_alloc(ctx, ds->scratch, 64));
   fill_double<<<grid1d(ctx, B), 256, 0, ctx->stream>>>(ds->best_E.as<double>(), B, INFINITY);

@@ -129,6 +129,7 @@ struct ising_ds {
   ising::DevMem hf;        // float32 field (n)
   ising::DevMem hint;      // int32 field * 2^h_shift (n)
   ising::DevMem best_E, best_t, best_s, last_E;
+  ising::DevMem improved;  // per restart: improved at the last tracked step (bit-packed path)
   int64_t bs_ld = 0;       // row pitch of best_s (n rounded up to 16)
   ising::DevMem counters;  // int64 [0] = steps done, [1] = done-block counter
   ising::DevMem bias;      // float2 [T + 2]: 1/(1-b1^t), 1/(1-b2^t)

@@ -63,6 +63,7 @@ struct TcArgs {
   float* Gout;  // coupling mode: [B][ld]
   int* err;
   int has_h;
+  int gmagic;  // integer G with |G| < 2^22 (resident epilogue's FP32-to-int trick)
   unsigned long long* trace;  // per-CTA role timeline (profiling), or null
 };
 
@@ -432,10 +433,13 @@ __global__ void row_absmax_kernel(const void* J, int dt, int64_t n, float* scale
 // keeps its tile of theta, m, v in tensor memory for a whole run of steps
 // (TMEM columns [0, BN) accumulator, [BN, 2BN) theta, [2BN, 3BN) m,
 // [3BN, 4BN) v), so a step moves only the J / S tiles (TMA) and the new
-// spins and energy partials (global stores). Steps are separated by a grid
-// barrier (cooperative launch, so all CTAs are co-resident; the wait is
-// bounded). The epilogue warps track the best of step t-1 for this CTA's
-// slice of restarts while the tensor cores work on step t. The spins of the
+// spins and energy partials (global stores). Step t + 1 of a restart needs
+// S_t of all rows, i.e. the output of every m-tile of the same restart
+// column, so the CTAs of one column pass a barrier between steps (an
+// arrival counter per column; the cooperative launch keeps all CTAs
+// co-resident, and the wait is bounded); columns run independently. The
+// epilogue warps track the best of step t-1 for this CTA's slice of its
+// column's restarts while the tensor cores work on step t. The spins of the
 // current step are re-derived from theta (sgn+(sin theta), as they were
 // written), so the epilogue reads no state from global memory.
 
@@ -446,7 +450,7 @@ struct TcResArgs {
   long long* qpart[2];
   long long* hpart[2];
   float* epart[2];
-  unsigned int* gbar;  // grid barrier arrivals (zeroed before the launch)
+  unsigned int* gbar;  // per restart-column barrier arrivals, 32 words apart (zeroed before the launch)
   int* gabort;         // raised by any CTA that gives up
   double* best_E;
   long long* best_t;
@@ -455,47 +459,193 @@ struct TcResArgs {
   int64_t bs_ld;       // row pitch of best_s
   double cq, chs;      // E = cq * Q + chs * H (integer mode)
   int rows;            // energy-partial rows (4 per m-tile)
-  int slice;           // restarts tracked per CTA
+  int slice;           // restarts tracked per CTA within its column of tiles
 };
 
-// Best tracking of step t for restarts [b0, b1), one warp per restart
-// (same arithmetic and order as track_kernel).
+// Best tracking of step t for restarts [b0, b1): one warp per restart (same
+// arithmetic and order as track_kernel), up to four restarts per warp at a
+// time so that their loads are in flight together.
 template <bool INT_E, bool FP8>
 __device__ __forceinline__ void track_slice(const TcResArgs& R, long long t, int64_t b0, int64_t b1,
                                             int wid, int nw, int lane) {
   const TcArgs& P = R.P;
   const int ps = (int)(t % 2);
   const void* St = R.spins[t % 3];
-  for (int64_t b = b0 + wid; b < b1; b += nw) {
-    double E;
+  constexpr int U = 4;
+  for (int64_t bb = b0 + wid; bb < b1; bb += (int64_t)U * nw) {
+    double E[U], best[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t b = bb + (int64_t)u * nw;
+      const bool ok = b < b1;
+      best[u] = ok ? R.best_E[b] : 0.0;
+      if (INT_E) {
+        long long q = 0, hs = 0;
+        if (ok)
+          for (int r = lane; r < R.rows; r += 32) {
+            q += R.qpart[ps][(int64_t)r * P.B + b];
+            hs += R.hpart[ps][(int64_t)r * P.B + b];
+          }
+        for (int o = 16; o; o >>= 1) {
+          q += __shfl_xor_sync(0xffffffffu, q, o);
+          hs += __shfl_xor_sync(0xffffffffu, hs, o);
+        }
+        E[u] = R.cq * (double)q + R.chs * (double)hs;
+      } else {
+        double e = 0.0;
+        if (ok)
+          for (int r = lane; r < R.rows; r += 32) e += (double)R.epart[ps][(int64_t)r * P.B + b];
+        for (int o = 16; o; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+        E[u] = e;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t b = bb + (int64_t)u * nw;
+      if (b >= b1) break;
+      const bool improved = E[u] < best[u];
+      if (lane == 0) {
+        R.last_E[b] = E[u];
+        if (improved) {
+          R.best_E[b] = E[u];
+          R.best_t[b] = t;
+        }
+      }
+      if (improved)
+        copy_spin_row_dense<FP8 ? kSpinE4M3 : kSpinBF16>(R.best_s + b * R.bs_ld, St, P.n, P.ld, b, lane);
+    }
+  }
+}
+
+// Per-lane constants of the resident epilogue: the lane owns row i of the
+// tile and the warp's BN / 4 columns starting at restart nb0.
+struct EpiLane {
+  int64_t i, nb0, orow;
+  bool row_ok;
+  int hi, ncols, lane;
+  float rs, chh, hm_pos, hm_neg;
+  uint32_t t_acc;
+};
+
+// One step of the resident epilogue over the warp's columns, in chunks of 8:
+// the step's energy partials, the Adam update of theta / m / v (kept in
+// tensor memory), and the next spins. Rows past n and columns past B hold
+// G = 0 (the TMA fills out-of-range operand rows with zeros), so their
+// energy terms vanish or are never stored; only stores are guarded.
+// MAGIC (integer G with |G| < 2^22): s_i G_i is turned into an integer by
+// adding 1.5 * 2^23 in FP32, whose bit pattern is then 0x4B400000 + s_i G_i,
+// so the warp sums the raw patterns (redux.sync, wrapping) and removes 32
+// times the offset once per column.
+template <int BN, bool INT_E, bool FP8, bool MAGIC>
+__device__ __forceinline__ void resident_chunks(const TcResArgs& R, const EpiLane& E, long long t,
+                                                float2 bc, bool last, uint64_t* acc_empty) {
+  const TcArgs& P = R.P;
+  constexpr int kCols = BN / 4;
+  const uint32_t t_th = E.t_acc + BN, t_m = E.t_acc + 2 * BN, t_v = E.t_acc + 3 * BN;
+  void* Sout = R.spins[(t + 1) % 3];
+  const int ps = (int)(t % 2);
+  const int lane = E.lane;
+#pragma unroll 1
+  for (int c0 = 0; c0 < kCols; c0 += kChunk) {
+    uint32_t r[kChunk], th[kChunk], mm[kChunk], vv[kChunk];
+    tc::tmem_ld8(E.t_acc + c0, r);
+    tc::tmem_ld8(t_th + c0, th);
+    tc::tmem_ld8(t_m + c0, mm);
+    tc::tmem_ld8(t_v + c0, vv);
+    tc::tmem_wait_ld();
+    if (c0 + kChunk == kCols) {
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(acc_empty);
+    }
+    uint32_t pos_bits = 0, new_bits = 0;
+    int eq[kChunk];
+    float ef[kChunk];
+#pragma unroll
+    for (int j = 0; j < kChunk; ++j) {
+      float tj = __uint_as_float(th[j]), mj = __uint_as_float(mm[j]), vj = __uint_as_float(vv[j]);
+      const float G = INT_E ? __uint_as_float(r[j]) : __uint_as_float(r[j]) * E.rs;
+      const bool pos = sin_nonneg(tj);  // the spin this step consumed
+      pos_bits |= (pos ? 1u : 0u) << j;
+      if (INT_E) {
+        if (MAGIC) {
+          eq[j] = __float_as_int(__fadd_rn(pos ? G : -G, 12582912.0f));
+        } else {
+          const int gi = __float2int_rn(G);
+          eq[j] = pos ? gi : -gi;
+        }
+      } else {
+        ef[j] = (pos ? 1.f : -1.f) * fmaf(P.k.cq, G, E.chh);
+      }
+      const float F = fmaf(P.k.cq, G, pos ? E.hm_pos : E.hm_neg);
+      const float g = cos_proj(tj) * F;
+      tj = adam_update(P.k, bc.x, bc.y, g, tj, mj, vj);
+      new_bits |= (sin_nonneg(tj) ? 1u : 0u) << j;
+      th[j] = __float_as_uint(tj);
+      mm[j] = __float_as_uint(mj);
+      vv[j] = __float_as_uint(vj);
+    }
+    if (!last) {
+      tc::tmem_st8(t_th + c0, th);
+      tc::tmem_st8(t_m + c0, mm);
+      tc::tmem_st8(t_v + c0, vv);
+    }
+    if (E.row_ok) {
+      const int nv = E.ncols - c0;  // columns of this chunk below B
+      const int64_t base = (E.nb0 + c0) * P.ld + E.i;
+      if (nv >= kChunk) {
+#pragma unroll
+        for (int j = 0; j < kChunk; ++j) {
+          const bool sp = (new_bits >> j) & 1u;
+          if (FP8) static_cast<uint8_t*>(Sout)[base + j * P.ld] = sp ? 0x38 : 0xB8;
+          else static_cast<__nv_bfloat16*>(Sout)[base + j * P.ld] = __float2bfloat16(sp ? 1.f : -1.f);
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < kChunk; ++j) {
+          if (j >= nv) break;
+          const bool sp = (new_bits >> j) & 1u;
+          if (FP8) static_cast<uint8_t*>(Sout)[base + j * P.ld] = sp ? 0x38 : 0xB8;
+          else static_cast<__nv_bfloat16*>(Sout)[base + j * P.ld] = __float2bfloat16(sp ? 1.f : -1.f);
+        }
+      }
+      if (last) {
+#pragma unroll
+        for (int j = 0; j < kChunk; ++j) {
+          if (j >= nv) break;
+          const int64_t idx = base + (int64_t)j * P.ld;
+          P.theta[idx] = __uint_as_float(th[j]);
+          P.m[idx] = __uint_as_float(mm[j]);
+          P.v[idx] = __uint_as_float(vv[j]);
+        }
+      }
+    }
     if (INT_E) {
-      long long q = 0, hs = 0;
-      for (int r = lane; r < R.rows; r += 32) {
-        q += R.qpart[ps][(int64_t)r * P.B + b];
-        hs += R.hpart[ps][(int64_t)r * P.B + b];
+      // lane j < 8 ends up with the sums of column c0 + j over the warp's 32 rows
+      int q = 0, hs = 0;
+#pragma unroll
+      for (int j = 0; j < kChunk; ++j) {
+        const unsigned int sum = __reduce_add_sync(0xffffffffu, (unsigned int)eq[j]);
+        if (lane == j) q = (int)(MAGIC ? sum - 32u * 0x4B400000u : sum);
       }
-      for (int o = 16; o; o >>= 1) {
-        q += __shfl_xor_sync(0xffffffffu, q, o);
-        hs += __shfl_xor_sync(0xffffffffu, hs, o);
+      if (P.has_h) {
+#pragma unroll
+        for (int j = 0; j < kChunk; ++j) {
+          const int hv = ((pos_bits >> j) & 1u) ? E.hi : -E.hi;
+          const int sum = __reduce_add_sync(0xffffffffu, hv);
+          if (lane == j) hs = sum;
+        }
       }
-      E = R.cq * (double)q + R.chs * (double)hs;
+      const int64_t b = E.nb0 + c0 + lane;
+      if (lane < kChunk && b < P.B) {
+        R.qpart[ps][E.orow + b] = q;
+        R.hpart[ps][E.orow + b] = hs;
+      }
     } else {
-      double e = 0.0;
-      for (int r = lane; r < R.rows; r += 32) e += (double)R.epart[ps][(int64_t)r * P.B + b];
-      for (int o = 16; o; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
-      E = e;
+      const float te = column_sums8(ef, lane);
+      const int64_t b = E.nb0 + c0 + column_of_lane(lane);
+      if ((lane & 3) == 0 && b < P.B) R.epart[ps][E.orow + b] = te;
     }
-    const bool improved = E < R.best_E[b];
-    __syncwarp();
-    if (lane == 0) {
-      R.last_E[b] = E;
-      if (improved) {
-        R.best_E[b] = E;
-        R.best_t[b] = t;
-      }
-    }
-    if (improved)
-      copy_spin_row_dense<FP8 ? kSpinE4M3 : kSpinBF16>(R.best_s + b * R.bs_ld, St, P.n, P.ld, b, lane);
   }
 }
 
@@ -555,7 +705,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   // role timeline of one step (profiling): 0 producer starts the step, 1 last
   // TMA issued, 2 last MMA committed, 3 epilogue finished tracking, 4 epilogue
   // has the accumulator, 5 epilogue done, 6 controller saw the CTA done,
-  // 7 grid barrier passed
+  // 7 column barrier passed
   const int64_t rec = K >= 2 ? K - 2 : 0;
 #define ISING_RTRACE(slot, s)                                                     \
   do {                                                                            \
@@ -573,7 +723,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int slot = (int)(t % 3);
         const CUtensorMap* mb = slot == 0 ? &tmB0 : (slot == 1 ? &tmB1 : &tmB2);
         // J does not change between steps: the J tiles of the first k-blocks
-        // are requested before the grid barrier, their S tiles after it
+        // are requested before the column barrier, their S tiles after it
         const int pre = s > 0 ? (nkt < STAGES ? nkt : STAGES) : 0;
         const uint32_t st0 = stage;
         for (int kt = 0; kt < pre; ++kt) {
@@ -678,16 +828,18 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp == 2) {
     if (lane == 0) {
       // ------------------------------------------------ grid-barrier controller
-      const unsigned int nblk = gridDim.x;
+      // the CTAs of one restart column (all m-tiles of the same restarts)
+      // exchange spins; columns are independent and never wait on each other
+      unsigned int* colbar = R.gbar + 32 * (blockIdx.x / P.mtiles);
       for (int64_t s = 0; s < K; ++s) {
         if (!tc::mbar_wait(step_done, (uint32_t)(s & 1), abort_flag, kWaitCycles)) break;
         ISING_RTRACE(6, s);
         __threadfence();
-        atomicAdd(R.gbar, 1u);
-        const unsigned int target = (unsigned int)(s + 1) * nblk;
+        atomicAdd(colbar, 1u);
+        const unsigned int target = (unsigned int)(s + 1) * (unsigned int)P.mtiles;
         const long long c0 = clock64();
         bool ok = true;
-        while (tc::ld_acquire_gpu(R.gbar) < target) {
+        while (tc::ld_acquire_gpu(colbar) < target) {
           if (*reinterpret_cast<volatile int*>(R.gabort)) { ok = false; break; }
           if (clock64() - c0 > kWaitCycles) {
             atomicExch(R.gabort, 1);
@@ -719,9 +871,23 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t lane_off = (uint32_t)(32 * q) << 16;
     const uint32_t t_acc = tmem_base + lane_off + (uint32_t)(part * kCols);
     const uint32_t t_th = t_acc + BN, t_m = t_acc + 2 * BN, t_v = t_acc + 3 * BN;
+    EpiLane E;
+    E.i = i;
+    E.row_ok = row_ok;
+    E.hi = hi;
+    E.rs = rs;
+    E.chh = P.k.ch * h;
+    E.hm_pos = fmaf(P.k.ch, h, -P.k.mu);  // = fmaf(ch, h, -mu s) for s = +1
+    E.hm_neg = fmaf(P.k.ch, h, P.k.mu);   // ... and for s = -1
+    E.nb0 = nb0;
+    E.ncols = (int)max((int64_t)0, min((int64_t)kCols, P.B - nb0));
+    E.orow = ((int64_t)mt * 4 + q) * P.B;
+    E.t_acc = t_acc;
+    E.lane = lane;
     // tracked restarts of this CTA
-    const int64_t tb0 = (int64_t)blockIdx.x * R.slice;
-    const int64_t tb1 = tb0 + R.slice < P.B ? tb0 + R.slice : P.B;
+    const int64_t col_end = n0 + BN < P.B ? n0 + BN : P.B;
+    const int64_t tb0 = n0 + (int64_t)mt * R.slice;
+    const int64_t tb1 = tb0 + R.slice < col_end ? tb0 + R.slice : col_end;
     // state of this warp's columns into tensor memory
 #pragma unroll 1
     for (int c0 = 0; c0 < kCols; c0 += kChunk) {
@@ -743,6 +909,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     bool ok = true;
     for (int64_t s = 0; s < K && ok; ++s) {
       const long long t = t0 + s + 1;
+      const float2 bc = P.bias[t];  // loaded ahead of the waits, off the critical path
       if (s > 0) {
         if (!tc::mbar_wait(go, (uint32_t)((s - 1) & 1), abort_flag, kWaitCycles)) { ok = false; break; }
         track_slice<INT_E, FP8>(R, t - 1, tb0, tb1, warp - 4, kEpiWarps, lane);
@@ -757,76 +924,11 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc::fence_after_sync();
       if (warp == 4 && lane == 0) ISING_RTRACE(4, s);
       const bool last = s + 1 == K;
-      const float2 bc = P.bias[t];
-      void* Sout = R.spins[(t + 1) % 3];
-      const int ps = (int)(t % 2);
-#pragma unroll 1
-      for (int c0 = 0; c0 < kCols; c0 += kChunk) {
-        uint32_t r[kChunk], th[kChunk], mm[kChunk], vv[kChunk];
-        tc::tmem_ld8(t_acc + c0, r);
-        tc::tmem_ld8(t_th + c0, th);
-        tc::tmem_ld8(t_m + c0, mm);
-        tc::tmem_ld8(t_v + c0, vv);
-        tc::tmem_wait_ld();
-        if (c0 + kChunk == kCols) {
-          tc::fence_before_sync();
-          __syncwarp();
-          if (lane == 0) tc::mbar_arrive(acc_empty);
-        }
-        float ef[kChunk];
-        int eq[kChunk], eh[kChunk];
-        // columns of this chunk that exist (all of them except in a ragged last tile)
-        const int nvalid = row_ok ? (int)max((int64_t)0, min((int64_t)kChunk, P.B - (nb0 + c0))) : 0;
-        const int64_t base = (nb0 + c0) * P.ld + i;
-#pragma unroll
-        for (int j = 0; j < kChunk; ++j) {
-          const bool okj = j < nvalid;
-          float tj = __uint_as_float(th[j]), mj = __uint_as_float(mm[j]), vj = __uint_as_float(vv[j]);
-          const float G = __uint_as_float(r[j]) * rs;
-          const bool pos = sin_nonneg(tj);  // the spin this step consumed
-          const float sj = pos ? 1.f : -1.f;
-          if (INT_E) {
-            const int gi = __float2int_rn(G);
-            eq[j] = okj ? (pos ? gi : -gi) : 0;
-            eh[j] = okj ? (pos ? hi : -hi) : 0;
-          } else {
-            ef[j] = okj ? sj * fmaf(P.k.cq, G, P.k.ch * h) : 0.f;
-          }
-          const float F = fmaf(P.k.cq, G, fmaf(P.k.ch, h, -P.k.mu * sj));
-          const float g = cos_proj(tj) * F;
-          tj = adam_update(P.k, bc.x, bc.y, g, tj, mj, vj);
-          if (okj) {
-            const int64_t idx = base + (int64_t)j * P.ld;
-            if (FP8) static_cast<uint8_t*>(Sout)[idx] = sin_nonneg(tj) ? 0x38 : 0xB8;
-            else static_cast<__nv_bfloat16*>(Sout)[idx] = __float2bfloat16(sin_nonneg(tj) ? 1.f : -1.f);
-            if (last) {
-              P.theta[idx] = tj;
-              P.m[idx] = mj;
-              P.v[idx] = vj;
-            }
-          }
-          th[j] = __float_as_uint(tj);
-          mm[j] = __float_as_uint(mj);
-          vv[j] = __float_as_uint(vj);
-        }
-        if (!last) {
-          tc::tmem_st8(t_th + c0, th);
-          tc::tmem_st8(t_m + c0, mm);
-          tc::tmem_st8(t_v + c0, vv);
-        }
-        const int64_t b = nb0 + c0 + column_of_lane(lane);
-        const int64_t o = ((int64_t)mt * 4 + q) * P.B + b;
-        if (INT_E) {
-          const int tq = column_sums8(eq, lane);
-          const int th2 = P.has_h ? column_sums8(eh, lane) : 0;
-          if ((lane & 3) == 0 && b < P.B) {
-            R.qpart[ps][o] = tq;
-            R.hpart[ps][o] = th2;
-          }
-        } else {
-          const float te = column_sums8(ef, lane);
-          if ((lane & 3) == 0 && b < P.B) R.epart[ps][o] = te;
-        }
+      if constexpr (INT_E) {
+        if (P.gmagic) resident_chunks<BN, true, FP8, true>(R, E, t, bc, last, acc_empty);
+        else resident_chunks<BN, true, FP8, false>(R, E, t, bc, last, acc_empty);
+      } else {
+        resident_chunks<BN, false, FP8, false>(R, E, t, bc, last, acc_empty);
       }
       tc::tmem_wait_st();
       tc::fence_proxy_async_global();
@@ -861,7 +963,7 @@ struct TcState {
   bool maps_ready = false;
   bool fp8 = false;
   bool resident = false;  // one tile per CTA, state kept in tensor memory
-  DevMem gsync;           // grid barrier counter + abort word
+  DevMem gsync;           // abort word + per-column barrier counters
   DevMem err;
   DevMem trace;  // grid x 8 timestamps of the last profiled launch
 };
@@ -961,6 +1063,11 @@ int resident_launch_bn(ising_ds* ds, TcState* st, const TcResArgs& ra) {
   return st->fp8 ? resident_launch<BN, false, true>(ds, st, ra) : resident_launch<BN, false, false>(ds, st, ra);
 }
 
+// Abort word, then one arrival counter per restart column, 128 bytes apart.
+static size_t gsync_bytes(const ising_ds* ds, const TcState* st) {
+  return (size_t)(1 + ceil_div_i(ds->B, st->BN)) * 128;
+}
+
 int tc_setup(ising_ds* ds) {
   ising_ctx* ctx = ds->ctx;
   const DevInstance& I = ds->inst;
@@ -1026,7 +1133,7 @@ int tc_setup(ising_ds* ds) {
     }
   }
   if (st->resident) {
-    ISING_TRY(dev_alloc(ctx, st->gsync, 16));
+    ISING_TRY(dev_alloc(ctx, st->gsync, gsync_bytes(ds, st)));
   } else {
     const int tiles = ceil_div_i(ds->n, kBM) * ceil_div_i(ds->B, st->BN);
     st->grid = std::max(1, std::min(tiles, ctx->sm_count));
@@ -1077,6 +1184,8 @@ int tc_run(ising_ds* ds, int mode, float* Gout) {
   a.Gout = Gout;
   a.err = st->err.as<int>();
   a.has_h = ds->inst.has_h ? 1 : 0;
+  // |G_i| <= max |J_ij| * n in stored units
+  a.gmagic = (ds->int_energy && ds->inst.j_absmax * (double)ds->n < 4194304.0) ? 1 : 0;
   a.trace = nullptr;
   if (ds->p.flags & ISING_DS_PROFILE) {
     if (!st->trace.p) ISING_TRY(dev_alloc(ds->ctx, st->trace, (size_t)st->grid * 8 * 8));
@@ -1111,7 +1220,7 @@ int tc_run_resident(ising_ds* ds, int64_t steps) {
     ISING_TRY(tc_maps(ds, st));
     st->maps_ready = true;
   }
-  ISING_CUDA(ds->ctx, cudaMemsetAsync(st->gsync.p, 0, 16, ds->ctx->stream));
+  ISING_CUDA(ds->ctx, cudaMemsetAsync(st->gsync.p, 0, gsync_bytes(ds, st), ds->ctx->stream));
   TcResArgs r;
   TcArgs& a = r.P;
   a.n = ds->n;
@@ -1137,6 +1246,8 @@ int tc_run_resident(ising_ds* ds, int64_t steps) {
   a.Gout = nullptr;
   a.err = st->err.as<int>();
   a.has_h = ds->inst.has_h ? 1 : 0;
+  // |G_i| <= max |J_ij| * n in stored units
+  a.gmagic = (ds->int_energy && ds->inst.j_absmax * (double)ds->n < 4194304.0) ? 1 : 0;
   a.trace = nullptr;
   if (ds->p.flags & ISING_DS_PROFILE) {
     if (!st->trace.p) ISING_TRY(dev_alloc(ds->ctx, st->trace, (size_t)st->grid * 8 * 8));
@@ -1149,8 +1260,8 @@ int tc_run_resident(ising_ds* ds, int64_t steps) {
     r.hpart[k] = ds->hpart[k].as<long long>();
     r.epart[k] = ds->epart[k].as<float>();
   }
-  r.gbar = st->gsync.as<unsigned int>();
-  r.gabort = st->gsync.as<int>() + 1;
+  r.gabort = st->gsync.as<int>();
+  r.gbar = st->gsync.as<unsigned int>() + 32;
   r.best_E = ds->best_E.as<double>();
   r.best_t = ds->best_t.as<long long>();
   r.best_s = ds->best_s.as<int8_t>();
@@ -1159,7 +1270,7 @@ int tc_run_resident(ising_ds* ds, int64_t steps) {
   r.cq = ds->inst.cq;
   r.chs = ds->inst.ch * std::ldexp(1.0, -ds->h_shift);
   r.rows = ds->mtiles;
-  r.slice = (int)((ds->B + st->grid - 1) / st->grid);
+  r.slice = ceil_div_i(st->BN, ceil_div_i(ds->n, kBM));
   return st->BN == 128 ? resident_launch_bn<128>(ds, st, r) : resident_launch_bn<64>(ds, st, r);
 }
 
