@@ -63,7 +63,7 @@ struct TcArgs {
   float* Gout;  // coupling mode: [B][ld]
   int* err;
   int has_h;
-  int gmagic;  // integer G with |G| < 2^22 (resident epilogue's FP32-to-int trick)
+  int gmagic;  // resident epilogue's integer energy mode (EMODE of resident_chunks)
   unsigned long long* trace;  // per-CTA role timeline (profiling), or null
 };
 
@@ -411,6 +411,18 @@ __global__ void to_fp8_kernel(const void* J, int dt, int64_t n, int64_t ld, cons
   }
 }
 
+// max_i sum_j |J_ij| of an integer-valued dense J (exact in FP64), one warp per row.
+__global__ void row_abssum_max_kernel(const void* J, int dt, int64_t n, unsigned long long* out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t i = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
+    double a = 0.0;
+    for (int64_t k = lane; k < n; k += 32) a += fabs(load_as_double(J, dt, i * n + k));
+    for (int o = 16; o; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (lane == 0) atomicMax(out, (unsigned long long)a);
+  }
+}
+
 __global__ void row_absmax_kernel(const void* J, int dt, int64_t n, float* scale) {
   for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
     double mx = 0.0;
@@ -532,11 +544,14 @@ struct EpiLane {
 // tensor memory), and the next spins. Rows past n and columns past B hold
 // G = 0 (the TMA fills out-of-range operand rows with zeros), so their
 // energy terms vanish or are never stored; only stores are guarded.
-// MAGIC (integer G with |G| < 2^22): s_i G_i is turned into an integer by
+// EMODE 1 (integer G with |G| < 2^22): s_i G_i is turned into an integer by
 // adding 1.5 * 2^23 in FP32, whose bit pattern is then 0x4B400000 + s_i G_i,
 // so the warp sums the raw patterns (redux.sync, wrapping) and removes 32
-// times the offset once per column.
-template <int BN, bool INT_E, bool FP8, bool MAGIC>
+// times the offset once per column. EMODE 2 (also 32 max_i sum_j |J_ij| <
+// 2^15): two columns share one reduction, packed as a + 2^16 b; the low half
+// of the sum is then sum a exactly and the high half sum b. EMODE 0 converts
+// with F2I.
+template <int BN, bool INT_E, bool FP8, int EMODE>
 __device__ __forceinline__ void resident_chunks(const TcResArgs& R, const EpiLane& E, long long t,
                                                 float2 bc, bool last, uint64_t* acc_empty) {
   const TcArgs& P = R.P;
@@ -568,7 +583,7 @@ __device__ __forceinline__ void resident_chunks(const TcResArgs& R, const EpiLan
       const bool pos = sin_nonneg(tj);  // the spin this step consumed
       pos_bits |= (pos ? 1u : 0u) << j;
       if (INT_E) {
-        if (MAGIC) {
+        if (EMODE > 0) {
           eq[j] = __float_as_int(__fadd_rn(pos ? G : -G, 12582912.0f));
         } else {
           const int gi = __float2int_rn(G);
@@ -623,10 +638,23 @@ __device__ __forceinline__ void resident_chunks(const TcResArgs& R, const EpiLan
     if (INT_E) {
       // lane j < 8 ends up with the sums of column c0 + j over the warp's 32 rows
       int q = 0, hs = 0;
+      if (EMODE == 2) {
 #pragma unroll
-      for (int j = 0; j < kChunk; ++j) {
-        const unsigned int sum = __reduce_add_sync(0xffffffffu, (unsigned int)eq[j]);
-        if (lane == j) q = (int)(MAGIC ? sum - 32u * 0x4B400000u : sum);
+        for (int jp = 0; jp < kChunk / 2; ++jp) {
+          // 0x4B400000 << 16 wraps to 0: only the low column carries the offset
+          const unsigned int v = (unsigned int)eq[2 * jp] + ((unsigned int)eq[2 * jp + 1] << 16);
+          const unsigned int sum = __reduce_add_sync(0xffffffffu, v) - 32u * 0x4B400000u;
+          const int lo = (int)(short)(sum & 0xFFFFu);
+          const int hi = (int)(sum - (unsigned int)lo) >> 16;
+          if (lane == 2 * jp) q = lo;
+          if (lane == 2 * jp + 1) q = hi;
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < kChunk; ++j) {
+          const unsigned int sum = __reduce_add_sync(0xffffffffu, (unsigned int)eq[j]);
+          if (lane == j) q = (int)(EMODE == 1 ? sum - 32u * 0x4B400000u : sum);
+        }
       }
       if (P.has_h) {
 #pragma unroll
@@ -834,8 +862,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int64_t s = 0; s < K; ++s) {
         if (!tc::mbar_wait(step_done, (uint32_t)(s & 1), abort_flag, kWaitCycles)) break;
         ISING_RTRACE(6, s);
-        __threadfence();
-        atomicAdd(colbar, 1u);
+        // release at GPU scope: the spins and partials this CTA's epilogue
+        // wrote (ordered before step_done) are visible before the arrival
+        tc::red_release_gpu(colbar, 1u);
         const unsigned int target = (unsigned int)(s + 1) * (unsigned int)P.mtiles;
         const long long c0 = clock64();
         bool ok = true;
@@ -852,7 +881,6 @@ __global__ void __launch_bounds__(kThreads, 1)
           *abort_flag = 1;
           break;
         }
-        __threadfence();
         ISING_RTRACE(7, s);
         tc::mbar_arrive(go);
       }
@@ -925,10 +953,11 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (warp == 4 && lane == 0) ISING_RTRACE(4, s);
       const bool last = s + 1 == K;
       if constexpr (INT_E) {
-        if (P.gmagic) resident_chunks<BN, true, FP8, true>(R, E, t, bc, last, acc_empty);
-        else resident_chunks<BN, true, FP8, false>(R, E, t, bc, last, acc_empty);
+        if (P.gmagic == 2) resident_chunks<BN, true, FP8, 2>(R, E, t, bc, last, acc_empty);
+        else if (P.gmagic == 1) resident_chunks<BN, true, FP8, 1>(R, E, t, bc, last, acc_empty);
+        else resident_chunks<BN, true, FP8, 0>(R, E, t, bc, last, acc_empty);
       } else {
-        resident_chunks<BN, false, FP8, false>(R, E, t, bc, last, acc_empty);
+        resident_chunks<BN, false, FP8, 0>(R, E, t, bc, last, acc_empty);
       }
       tc::tmem_wait_st();
       tc::fence_proxy_async_global();
@@ -964,6 +993,7 @@ struct TcState {
   bool fp8 = false;
   bool resident = false;  // one tile per CTA, state kept in tensor memory
   DevMem gsync;           // abort word + per-column barrier counters
+  int emode = 0;          // resident epilogue's integer energy mode (0 F2I, 1 offset, 2 packed)
   DevMem err;
   DevMem trace;  // grid x 8 timestamps of the last profiled launch
 };
@@ -1117,6 +1147,23 @@ int tc_setup(ising_ds* ds) {
   }
   ISING_TRY(dev_alloc(ctx, st->err, 16));
   ISING_CUDA(ctx, cudaMemsetAsync(st->err.p, 0, 16, ctx->stream));
+  if (ds->int_energy) {
+    // |G_i| < 2^22 holds for integer energies; pairs of column sums fit one
+    // 32-bit reduction when 32 max_i sum_j |J_ij| < 2^15
+    st->emode = 1;
+    if (I.layout == ISING_LAYOUT_DENSE) {
+      DevMem mx;
+      ISING_TRY(dev_alloc(ctx, mx, 8));
+      ISING_CUDA(ctx, cudaMemsetAsync(mx.p, 0, 8, ctx->stream));
+      const int rg = (int)std::max<int64_t>(1, std::min<int64_t>((ds->n + 7) / 8, (int64_t)ctx->sm_count * 16));
+      row_abssum_max_kernel<<<rg, 256, 0, ctx->stream>>>(I.J.p, I.j_dtype, ds->n, mx.as<unsigned long long>());
+      ISING_CUDA(ctx, cudaGetLastError());
+      unsigned long long r = 0;
+      ISING_CUDA(ctx, cudaMemcpyAsync(&r, mx.p, 8, cudaMemcpyDeviceToHost, ctx->stream));
+      ISING_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+      if (32ull * r < 32768ull) st->emode = 2;
+    }
+  }
   // resident form when every (128 x BN) tile gets its own co-resident CTA
   if (!(ds->p.flags & ISING_DS_STREAMING)) {
     const int mtn = ceil_div_i(ds->n, kBM);
@@ -1185,7 +1232,7 @@ int tc_run(ising_ds* ds, int mode, float* Gout) {
   a.err = st->err.as<int>();
   a.has_h = ds->inst.has_h ? 1 : 0;
   // |G_i| <= max |J_ij| * n in stored units
-  a.gmagic = (ds->int_energy && ds->inst.j_absmax * (double)ds->n < 4194304.0) ? 1 : 0;
+  a.gmagic = st->emode;
   a.trace = nullptr;
   if (ds->p.flags & ISING_DS_PROFILE) {
     if (!st->trace.p) ISING_TRY(dev_alloc(ds->ctx, st->trace, (size_t)st->grid * 8 * 8));
@@ -1247,7 +1294,7 @@ int tc_run_resident(ising_ds* ds, int64_t steps) {
   a.err = st->err.as<int>();
   a.has_h = ds->inst.has_h ? 1 : 0;
   // |G_i| <= max |J_ij| * n in stored units
-  a.gmagic = (ds->int_energy && ds->inst.j_absmax * (double)ds->n < 4194304.0) ? 1 : 0;
+  a.gmagic = st->emode;
   a.trace = nullptr;
   if (ds->p.flags & ISING_DS_PROFILE) {
     if (!st->trace.p) ISING_TRY(dev_alloc(ds->ctx, st->trace, (size_t)st->grid * 8 * 8));
