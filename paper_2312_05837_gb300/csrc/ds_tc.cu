@@ -91,6 +91,19 @@ struct TcLayout {
   static constexpr uint32_t kBytes = kBars + 256 + 1024;  // + alignment slack
 };
 
+// Resident form: shared memory holds the first `jres` J tiles of the CTA's
+// rows for the whole run (J does not change between steps), then `nst`
+// stages of a J tile and the S tile of one restart group (GN); the later J
+// tiles stream through the stages. Sizes are chosen at launch (TcResArgs).
+template <int GN>
+struct ResLayout {
+  static constexpr int kKps = 2;  // k-blocks per stage: [J tiles][S tiles]
+  static constexpr uint32_t kA = kBM * kRowBytes;
+  static constexpr uint32_t kB = GN * kRowBytes;
+  static constexpr uint32_t kStage = kKps * (kA + kB);
+  static constexpr int kMaxStages = 8;
+};
+
 // Sum over the 32 lanes of each of 8 columns; afterwards lanes l, l^1, l^2,
 // l^3 hold the total of column 4 b4 + 2 b3 + b2 (bits of l).
 template <typename T>
@@ -442,18 +455,23 @@ __global__ void row_absmax_kernel(const void* J, int dt, int64_t n, float* scale
 
 // ---------------------------------------------------------------------------
 // Resident form: when every tile of the problem fits one CTA per SM, each CTA
-// keeps its tile of theta, m, v in tensor memory for a whole run of steps
-// (TMEM columns [0, BN) accumulator, [BN, 2BN) theta, [2BN, 3BN) m,
-// [3BN, 4BN) v), so a step moves only the J / S tiles (TMA) and the new
-// spins and energy partials (global stores). Step t + 1 of a restart needs
-// S_t of all rows, i.e. the output of every m-tile of the same restart
-// column, so the CTAs of one column pass a barrier between steps (an
-// arrival counter per column; the cooperative launch keeps all CTAs
-// co-resident, and the wait is bounded); columns run independently. The
-// epilogue warps track the best of step t-1 for this CTA's slice of its
-// column's restarts while the tensor cores work on step t. The spins of the
-// current step are re-derived from theta (sgn+(sin theta), as they were
-// written), so the epilogue reads no state from global memory.
+// keeps its tile of theta, m, v in tensor memory for a whole run of steps, so
+// a step moves only the J / S tiles (TMA) and the new spins and energy
+// partials (global stores). A CTA holds two groups of GN restarts, each with
+// its own tensor-memory block (accumulator, theta, m, v: columns
+// [4 GN g, 4 GN (g + 1))), and the tensor cores alternate between them: while
+// the epilogue warps update group 0 from its accumulator, the MMAs of group 1
+// run, and the other way round, so the operand stream (bound by what one SM
+// can take in) and the epilogue (bound by instruction issue) overlap. Step
+// t + 1 of a group needs S_t of all rows, i.e. the output of every m-tile of
+// the same restarts, so the CTAs of one group's column pass a barrier
+// between steps (an arrival counter per group and column; the cooperative
+// launch keeps all CTAs co-resident, and the waits are bounded); groups and
+// columns run independently. The epilogue warps track the best of step
+// t - 1 of a group for their CTA's slice of its restarts before its step t
+// epilogue. The spins of the current step are re-derived from theta
+// (sgn+(sin theta), as they were written), so the epilogue reads no state
+// from global memory.
 
 struct TcResArgs {
   TcArgs P;
@@ -471,60 +489,63 @@ struct TcResArgs {
   int64_t bs_ld;       // row pitch of best_s
   double cq, chs;      // E = cq * Q + chs * H (integer mode)
   int rows;            // energy-partial rows (4 per m-tile)
-  int slice;           // restarts tracked per CTA within its column of tiles
+  int jres;            // J tiles (k-blocks) kept in shared memory for the whole run
+  int nst;             // pipeline stages after them
+  uint32_t bars;       // shared-memory offset of the barrier block
+  int slice;           // restarts of a group tracked per CTA of its column
 };
 
-// Best tracking of step t for restarts [b0, b1): one warp per restart (same
-// arithmetic and order as track_kernel), up to four restarts per warp at a
-// time so that their loads are in flight together.
+// Best tracking of step t for restarts [b0, b1) by one warp, a lane per
+// restart, with the same sums as track_kernel (whose lane l adds rows l,
+// l + 32, ... starting from 0, then combines the lanes by an xor tree over
+// lane bits 4, 3, 2, 1, 0): here one lane forms the 32 lane sums and adds
+// them in that tree's order. The spins of the improved restarts are then
+// copied one restart at a time by the whole warp.
 template <bool INT_E, bool FP8>
-__device__ __forceinline__ void track_slice(const TcResArgs& R, long long t, int64_t b0, int64_t b1,
-                                            int wid, int nw, int lane) {
+__device__ __forceinline__ void track_warp(const TcResArgs& R, long long t, int64_t b0, int64_t b1,
+                                           int lane) {
   const TcArgs& P = R.P;
   const int ps = (int)(t % 2);
   const void* St = R.spins[t % 3];
-  constexpr int U = 4;
-  for (int64_t bb = b0 + wid; bb < b1; bb += (int64_t)U * nw) {
-    double E[U], best[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int64_t b = bb + (int64_t)u * nw;
-      const bool ok = b < b1;
-      best[u] = ok ? R.best_E[b] : 0.0;
+  for (int64_t bb = b0; bb < b1; bb += 32) {
+    const int64_t b = bb + lane;
+    const bool ok = b < b1;
+    bool improved = false;
+    if (ok) {
+      const double best = R.best_E[b];
+      double E;
       if (INT_E) {
         long long q = 0, hs = 0;
-        if (ok)
-          for (int r = lane; r < R.rows; r += 32) {
-            q += R.qpart[ps][(int64_t)r * P.B + b];
-            hs += R.hpart[ps][(int64_t)r * P.B + b];
-          }
-        for (int o = 16; o; o >>= 1) {
-          q += __shfl_xor_sync(0xffffffffu, q, o);
-          hs += __shfl_xor_sync(0xffffffffu, hs, o);
+        for (int r = 0; r < R.rows; ++r) {
+          q += R.qpart[ps][(int64_t)r * P.B + b];
+          hs += R.hpart[ps][(int64_t)r * P.B + b];
         }
-        E[u] = R.cq * (double)q + R.chs * (double)hs;
+        E = R.cq * (double)q + R.chs * (double)hs;
       } else {
-        double e = 0.0;
-        if (ok)
-          for (int r = lane; r < R.rows; r += 32) e += (double)R.epart[ps][(int64_t)r * P.B + b];
-        for (int o = 16; o; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
-        E[u] = e;
+        double y[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          double lo = 0.0, hi = 0.0;  // the sums of lanes j and j + 16
+          for (int r = j; r < R.rows; r += 32) lo += (double)R.epart[ps][(int64_t)r * P.B + b];
+          for (int r = j + 16; r < R.rows; r += 32) hi += (double)R.epart[ps][(int64_t)r * P.B + b];
+          y[j] = lo + hi;
+        }
+#pragma unroll
+        for (int w = 8; w >= 1; w >>= 1)
+#pragma unroll
+          for (int j = 0; j < w; ++j) y[j] = y[j] + y[j + w];
+        E = y[0];
+      }
+      improved = E < best;
+      R.last_E[b] = E;
+      if (improved) {
+        R.best_E[b] = E;
+        R.best_t[b] = t;
       }
     }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int64_t b = bb + (int64_t)u * nw;
-      if (b >= b1) break;
-      const bool improved = E[u] < best[u];
-      if (lane == 0) {
-        R.last_E[b] = E[u];
-        if (improved) {
-          R.best_E[b] = E[u];
-          R.best_t[b] = t;
-        }
-      }
-      if (improved)
-        copy_spin_row_dense<FP8 ? kSpinE4M3 : kSpinBF16>(R.best_s + b * R.bs_ld, St, P.n, P.ld, b, lane);
+    for (unsigned int m = __ballot_sync(0xffffffffu, improved); m; m &= m - 1) {
+      const int64_t br = bb + __ffs(m) - 1;
+      copy_spin_row_dense<FP8 ? kSpinE4M3 : kSpinBF16>(R.best_s + br * R.bs_ld, St, P.n, P.ld, br, lane);
     }
   }
 }
@@ -532,10 +553,17 @@ __device__ __forceinline__ void track_slice(const TcResArgs& R, long long t, int
 // Per-lane constants of the resident epilogue: the lane owns row i of the
 // tile and the warp's BN / 4 columns starting at restart nb0.
 struct EpiLane {
-  int64_t i, nb0, orow;
+  int64_t i, orow;
   bool row_ok;
-  int hi, ncols, lane;
+  int hi, lane;
   float rs, chh, hm_pos, hm_neg;
+};
+
+// The warp's columns within one restart group: first restart, how many of
+// them lie below B, tensor-memory column of their accumulator.
+struct EpiGroup {
+  int64_t nb0;
+  int ncols;
   uint32_t t_acc;
 };
 
@@ -551,19 +579,20 @@ struct EpiLane {
 // 2^15): two columns share one reduction, packed as a + 2^16 b; the low half
 // of the sum is then sum a exactly and the high half sum b. EMODE 0 converts
 // with F2I.
-template <int BN, bool INT_E, bool FP8, int EMODE>
-__device__ __forceinline__ void resident_chunks(const TcResArgs& R, const EpiLane& E, long long t,
-                                                float2 bc, bool last, uint64_t* acc_empty) {
+template <int GN, bool INT_E, bool FP8, int EMODE>
+__device__ __forceinline__ void resident_chunks(const TcResArgs& R, const EpiLane& E,
+                                                const EpiGroup& Gr, long long t, float2 bc,
+                                                bool last, uint64_t* acc_empty) {
   const TcArgs& P = R.P;
-  constexpr int kCols = BN / 4;
-  const uint32_t t_th = E.t_acc + BN, t_m = E.t_acc + 2 * BN, t_v = E.t_acc + 3 * BN;
+  constexpr int kCols = GN / 4;
+  const uint32_t t_th = Gr.t_acc + GN, t_m = Gr.t_acc + 2 * GN, t_v = Gr.t_acc + 3 * GN;
   void* Sout = R.spins[(t + 1) % 3];
   const int ps = (int)(t % 2);
   const int lane = E.lane;
 #pragma unroll 1
   for (int c0 = 0; c0 < kCols; c0 += kChunk) {
     uint32_t r[kChunk], th[kChunk], mm[kChunk], vv[kChunk];
-    tc::tmem_ld8(E.t_acc + c0, r);
+    tc::tmem_ld8(Gr.t_acc + c0, r);
     tc::tmem_ld8(t_th + c0, th);
     tc::tmem_ld8(t_m + c0, mm);
     tc::tmem_ld8(t_v + c0, vv);
@@ -606,8 +635,8 @@ __device__ __forceinline__ void resident_chunks(const TcResArgs& R, const EpiLan
       tc::tmem_st8(t_v + c0, vv);
     }
     if (E.row_ok) {
-      const int nv = E.ncols - c0;  // columns of this chunk below B
-      const int64_t base = (E.nb0 + c0) * P.ld + E.i;
+      const int nv = Gr.ncols - c0;  // columns of this chunk below B
+      const int64_t base = (Gr.nb0 + c0) * P.ld + E.i;
       if (nv >= kChunk) {
 #pragma unroll
         for (int j = 0; j < kChunk; ++j) {
@@ -664,20 +693,20 @@ __device__ __forceinline__ void resident_chunks(const TcResArgs& R, const EpiLan
           if (lane == j) hs = sum;
         }
       }
-      const int64_t b = E.nb0 + c0 + lane;
+      const int64_t b = Gr.nb0 + c0 + lane;
       if (lane < kChunk && b < P.B) {
         R.qpart[ps][E.orow + b] = q;
         R.hpart[ps][E.orow + b] = hs;
       }
     } else {
       const float te = column_sums8(ef, lane);
-      const int64_t b = E.nb0 + c0 + column_of_lane(lane);
+      const int64_t b = Gr.nb0 + c0 + column_of_lane(lane);
       if ((lane & 3) == 0 && b < P.B) R.epart[ps][E.orow + b] = te;
     }
   }
 }
 
-template <int BN, bool INT_E, bool FP8>
+template <int GN, bool INT_E, bool FP8>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_resident_kernel(const __grid_constant__ CUtensorMap tmA0,
                        const __grid_constant__ CUtensorMap tmA1,
@@ -686,20 +715,24 @@ __global__ void __launch_bounds__(kThreads, 1)
                        const __grid_constant__ CUtensorMap tmB1,
                        const __grid_constant__ CUtensorMap tmB2, const TcResArgs R) {
   const TcArgs& P = R.P;
-  using Lay = TcLayout<BN>;
-  constexpr int STAGES = Lay::kStages;
+  using Lay = ResLayout<GN>;
+  const int STAGES = R.nst;
+  const int jres = R.jres;
   constexpr int kBK = FP8 ? 128 : 64;
-  constexpr uint32_t kTmemCols = 4 * BN;
+  constexpr uint32_t kTmemCols = 8 * GN;  // per group: accumulator, theta, m, v
+  constexpr int kCols = GN / 4;           // columns of a group per epilogue warp
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + Lay::kBars);
-  uint64_t* empty = full + STAGES;
-  uint64_t* acc_full = empty + STAGES;
-  uint64_t* acc_empty = acc_full + 1;
-  uint64_t* step_done = acc_empty + 1;
-  uint64_t* go = step_done + 1;
-  uint64_t* drain = go + 1;
+  uint8_t* stages = smem + (size_t)jres * Lay::kA;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + R.bars);
+  uint64_t* empty = full + Lay::kMaxStages;
+  uint64_t* jfull = empty + Lay::kMaxStages;  // the resident J tiles have landed
+  uint64_t* acc_full = jfull + 1;       // [2], one per restart group
+  uint64_t* acc_empty = acc_full + 2;   // [2]
+  uint64_t* step_done = acc_empty + 2;  // [2]
+  uint64_t* go = step_done + 2;         // [2]
+  uint64_t* drain = go + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
@@ -709,11 +742,14 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc::mbar_init(&full[s], 1);
       tc::mbar_init(&empty[s], 1);
     }
-    tc::mbar_init(acc_full, 1);
-    tc::mbar_init(acc_empty, kEpiWarps);
-    tc::mbar_init(step_done, kEpiWarps);
-    tc::mbar_init(go, 1);
+    for (int g = 0; g < 2; ++g) {
+      tc::mbar_init(&acc_full[g], 1);
+      tc::mbar_init(&acc_empty[g], kEpiWarps);
+      tc::mbar_init(&step_done[g], kEpiWarps);
+      tc::mbar_init(&go[g], 1);
+    }
     tc::mbar_init(drain, 1);
+    tc::mbar_init(jfull, 1);
     *abort_flag = 0;
     tc::fence_barrier_init();
   }
@@ -726,79 +762,81 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t tmem_base = *tmem_slot;
   const long long t0 = P.counters[0];
   const int64_t K = R.steps;
+  const int64_t NP = 2 * K;  // phases: step s of group g is phase 2 s + g
   const int mt = blockIdx.x % P.mtiles;
   const int64_t m0 = (int64_t)mt * kBM;
-  const int64_t n0 = (int64_t)(blockIdx.x / P.mtiles) * BN;
+  const int64_t n0 = (int64_t)(blockIdx.x / P.mtiles) * (2 * GN);  // first restart of the CTA
   const int nkt = P.nk * P.planes;
-  // role timeline of one step (profiling): 0 producer starts the step, 1 last
-  // TMA issued, 2 last MMA committed, 3 epilogue finished tracking, 4 epilogue
-  // has the accumulator, 5 epilogue done, 6 controller saw the CTA done,
-  // 7 column barrier passed
+  // role timeline of one step of group 0 (profiling): 0 producer starts the
+  // step, 1 last TMA issued, 2 last MMA committed, 3 controller finished
+  // tracking the step, 4 epilogue has the accumulator, 5 epilogue done,
+  // 6 controller saw the CTA done, 7 column barrier passed
   const int64_t rec = K >= 2 ? K - 2 : 0;
-#define ISING_RTRACE(slot, s)                                                     \
-  do {                                                                            \
-    if (P.trace && (s) == rec) P.trace[(size_t)blockIdx.x * 8 + (slot)] = now_ns(); \
+#define ISING_RTRACE(slot, s, g)                                                   \
+  do {                                                                             \
+    if (P.trace && (s) == rec && (g) == 0)                                         \
+      P.trace[(size_t)blockIdx.x * 8 + (slot)] = now_ns();                          \
   } while (0)
 
   if (warp == 0) {
     if (lane == 0) {
       // ------------------------------------------------ TMA producer
+      // the resident J tiles, once
+      if (jres > 0) {
+        tc::mbar_expect_tx(jfull, (uint32_t)jres * Lay::kA);
+        for (int kt = 0; kt < jres; ++kt) {
+          const int plane = kt / P.nk, kb = kt - plane * P.nk;
+          const CUtensorMap* ma = plane == 0 ? &tmA0 : (plane == 1 ? &tmA1 : &tmA2);
+          tc::tma_load_2d(smem + (size_t)kt * Lay::kA, ma, jfull, kb * kBK, (int)m0);
+        }
+      }
       uint32_t stage = 0, phase = 0;
       int issued = 0;
       bool ok = true;
-      for (int64_t s = 0; s < K && ok; ++s) {
+      for (int64_t p = 0; p < NP && ok; ++p) {
+        const int64_t s = p >> 1;
+        const int g = (int)(p & 1);
         const long long t = t0 + s + 1;
         const int slot = (int)(t % 3);
         const CUtensorMap* mb = slot == 0 ? &tmB0 : (slot == 1 ? &tmB1 : &tmB2);
-        // J does not change between steps: the J tiles of the first k-blocks
-        // are requested before the column barrier, their S tiles after it
-        const int pre = s > 0 ? (nkt < STAGES ? nkt : STAGES) : 0;
-        const uint32_t st0 = stage;
-        for (int kt = 0; kt < pre; ++kt) {
-          if (!tc::mbar_wait(&empty[stage], phase ^ 1, abort_flag, kWaitCycles)) {
-            ok = false;
-            break;
-          }
-          uint8_t* sa = smem + stage * Lay::kStage;
-          tc::mbar_expect_tx(&full[stage], Lay::kStage);
-          const int plane = kt / P.nk, kb = kt - plane * P.nk;
-          const CUtensorMap* ma = plane == 0 ? &tmA0 : (plane == 1 ? &tmA1 : &tmA2);
-          tc::tma_load_2d(sa, ma, &full[stage], kb * kBK, (int)m0);
-          ++issued;
-          if (++stage == STAGES) { stage = 0; phase ^= 1; }
-        }
-        if (!ok) break;
+        const int nb = (int)(n0 + g * GN);
         if (s > 0) {
-          if (!tc::mbar_wait(go, (uint32_t)((s - 1) & 1), abort_flag, kWaitCycles)) {
-            // the prefetched J copies are counted in `issued` and drained below
+          // S_t of the group exists once every CTA of its column is through step t - 1
+          if (!tc::mbar_wait(&go[g], (uint32_t)((s - 1) & 1), abort_flag, kWaitCycles)) {
             ok = false;
             break;
           }
           tc::fence_proxy_async_global();
         }
-        ISING_RTRACE(0, s);
-        uint32_t sp = st0;
-        for (int kt = 0; kt < pre; ++kt) {
-          const int plane = kt / P.nk, kb = kt - plane * P.nk;
-          (void)plane;
-          tc::tma_load_2d(smem + sp * Lay::kStage + Lay::kA, mb, &full[sp], kb * kBK, (int)n0);
-          if (++sp == STAGES) sp = 0;
-        }
-        for (int kt = pre; kt < nkt; ++kt) {
+        ISING_RTRACE(0, s, g);
+        for (int kt0 = 0; kt0 < nkt; kt0 += Lay::kKps) {
           if (!tc::mbar_wait(&empty[stage], phase ^ 1, abort_flag, kWaitCycles)) {
             ok = false;
             break;
           }
-          uint8_t* sa = smem + stage * Lay::kStage;
-          tc::mbar_expect_tx(&full[stage], Lay::kStage);
-          const int plane = kt / P.nk, kb = kt - plane * P.nk;
-          const CUtensorMap* ma = plane == 0 ? &tmA0 : (plane == 1 ? &tmA1 : &tmA2);
-          tc::tma_load_2d(sa, ma, &full[stage], kb * kBK, (int)m0);
-          tc::tma_load_2d(sa + Lay::kA, mb, &full[stage], kb * kBK, (int)n0);
+          uint8_t* sa = stages + (size_t)stage * Lay::kStage;
+          uint32_t bytes = 0;
+#pragma unroll
+          for (int u = 0; u < Lay::kKps; ++u) {
+            const int kt = kt0 + u;
+            if (kt < nkt) bytes += kt < jres ? Lay::kB : Lay::kA + Lay::kB;
+          }
+          tc::mbar_expect_tx(&full[stage], bytes);
+#pragma unroll
+          for (int u = 0; u < Lay::kKps; ++u) {
+            const int kt = kt0 + u;
+            if (kt >= nkt) break;
+            const int plane = kt / P.nk, kb = kt - plane * P.nk;
+            if (kt >= jres) {
+              const CUtensorMap* ma = plane == 0 ? &tmA0 : (plane == 1 ? &tmA1 : &tmA2);
+              tc::tma_load_2d(sa + u * Lay::kA, ma, &full[stage], kb * kBK, (int)m0);
+            }
+            tc::tma_load_2d(sa + Lay::kKps * Lay::kA + u * Lay::kB, mb, &full[stage], kb * kBK, nb);
+          }
           ++issued;
-          if (++stage == STAGES) { stage = 0; phase ^= 1; }
+          if (++stage == (uint32_t)STAGES) { stage = 0; phase ^= 1; }
         }
-        ISING_RTRACE(1, s);
+        ISING_RTRACE(1, s, g);
       }
       if (!ok) {
         int back = issued < STAGES ? issued : STAGES;
@@ -807,6 +845,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (s2 == 0) { s2 = STAGES - 1; ph ^= 1; } else { --s2; }
           tc::mbar_wait(&full[s2], ph, nullptr, kWaitCycles / 8);
         }
+        if (jres > 0) tc::mbar_wait(jfull, 0, nullptr, kWaitCycles / 8);
         atomicExch(P.err, 1);
         atomicExch(R.gabort, 1);
       }
@@ -814,37 +853,46 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp == 1) {
     if (lane == 0) {
       // ------------------------------------------------ MMA issuer
-      constexpr uint32_t idesc = tc::idesc_make(kBM, BN, FP8 ? 0u : 1u);
+      constexpr uint32_t idesc = tc::idesc_make(kBM, GN, FP8 ? 0u : 1u);
       uint32_t stage = 0, phase = 0;
-      bool ok = true;
-      for (int64_t s = 0; s < K && ok; ++s) {
-        if (!tc::mbar_wait(acc_empty, (uint32_t)((s & 1) ^ 1), abort_flag, kWaitCycles)) {
+      bool ok = jres == 0 || tc::mbar_wait(jfull, 0, abort_flag, kWaitCycles);
+      for (int64_t p = 0; p < NP && ok; ++p) {
+        const int64_t s = p >> 1;
+        const int g = (int)(p & 1);
+        const uint32_t d = tmem_base + (uint32_t)(g * 4 * GN);
+        if (!tc::mbar_wait(&acc_empty[g], (uint32_t)((s & 1) ^ 1), abort_flag, kWaitCycles)) {
           ok = false;
           break;
         }
         tc::fence_after_sync();
-        for (int kt = 0; kt < nkt; ++kt) {
+        for (int kt0 = 0; kt0 < nkt; kt0 += Lay::kKps) {
           if (!tc::mbar_wait(&full[stage], phase, abort_flag, kWaitCycles)) {
             ok = false;
             break;
           }
           tc::fence_after_sync();
-          const uint32_t a0 = tc::smem_u32(smem + stage * Lay::kStage);
-          const uint32_t b0 = a0 + Lay::kA;
+          const uint32_t sb = tc::smem_u32(stages + (size_t)stage * Lay::kStage);
 #pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            if (FP8)
-              tc::mma_f8(tmem_base, tc::desc_k_sw128(a0 + 32 * k), tc::desc_k_sw128(b0 + 32 * k),
-                         idesc, (kt > 0 || k > 0) ? 1u : 0u);
-            else
-              tc::mma_f16(tmem_base, tc::desc_k_sw128(a0 + 32 * k), tc::desc_k_sw128(b0 + 32 * k),
-                          idesc, (kt > 0 || k > 0) ? 1u : 0u);
+          for (int u = 0; u < Lay::kKps; ++u) {
+            const int kt = kt0 + u;
+            if (kt >= nkt) break;
+            const uint32_t a0 = kt < jres ? tc::smem_u32(smem + (size_t)kt * Lay::kA) : sb + u * Lay::kA;
+            const uint32_t b0 = sb + Lay::kKps * Lay::kA + u * Lay::kB;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              if (FP8)
+                tc::mma_f8(d, tc::desc_k_sw128(a0 + 32 * k), tc::desc_k_sw128(b0 + 32 * k), idesc,
+                           (kt > 0 || k > 0) ? 1u : 0u);
+              else
+                tc::mma_f16(d, tc::desc_k_sw128(a0 + 32 * k), tc::desc_k_sw128(b0 + 32 * k), idesc,
+                            (kt > 0 || k > 0) ? 1u : 0u);
+            }
           }
           tc::mma_commit(&empty[stage]);
-          if (++stage == STAGES) { stage = 0; phase ^= 1; }
+          if (++stage == (uint32_t)STAGES) { stage = 0; phase ^= 1; }
         }
-        if (ok) tc::mma_commit(acc_full);
-        ISING_RTRACE(2, s);
+        if (ok) tc::mma_commit(&acc_full[g]);
+        ISING_RTRACE(2, s, g);
       }
       if (!ok) {
         tc::mma_commit(drain);
@@ -853,124 +901,130 @@ __global__ void __launch_bounds__(kThreads, 1)
         atomicExch(R.gabort, 1);
       }
     }
-  } else if (warp == 2) {
-    if (lane == 0) {
-      // ------------------------------------------------ grid-barrier controller
-      // the CTAs of one restart column (all m-tiles of the same restarts)
-      // exchange spins; columns are independent and never wait on each other
-      unsigned int* colbar = R.gbar + 32 * (blockIdx.x / P.mtiles);
-      for (int64_t s = 0; s < K; ++s) {
-        if (!tc::mbar_wait(step_done, (uint32_t)(s & 1), abort_flag, kWaitCycles)) break;
-        ISING_RTRACE(6, s);
+  } else if (warp == 2 || warp == 3) {
+    // ------------------------------------------------ column-barrier controller
+    // of group g = warp - 2, and its best tracking: the CTAs of one restart
+    // group's column (all m-tiles of the same restarts) exchange spins;
+    // groups and columns are independent and never wait on each other. Step
+    // s of the group is tracked after its barrier, before this CTA arrives at
+    // the barrier of step s + 1, which any overwrite of the step's partials
+    // and spins (at step s + 2) has to wait for.
+    const int g = warp - 2;
+    unsigned int* colbar = R.gbar + 32 * (2 * (blockIdx.x / P.mtiles) + g);
+    const int64_t gs = n0 + g * GN;
+    const int64_t ge = gs + GN < P.B ? gs + GN : P.B;
+    const int64_t tb0 = gs + (int64_t)mt * R.slice;
+    const int64_t tb1 = tb0 + R.slice < ge ? tb0 + R.slice : ge;
+    for (int64_t s = 0; s < K; ++s) {
+      int ok = 1;
+      if (lane == 0) ok = tc::mbar_wait(&step_done[g], (uint32_t)(s & 1), abort_flag, kWaitCycles) ? 1 : 0;
+      if (lane == 0 && ok) {
+        ISING_RTRACE(6, s, g);
         // release at GPU scope: the spins and partials this CTA's epilogue
         // wrote (ordered before step_done) are visible before the arrival
         tc::red_release_gpu(colbar, 1u);
         const unsigned int target = (unsigned int)(s + 1) * (unsigned int)P.mtiles;
         const long long c0 = clock64();
-        bool ok = true;
         while (tc::ld_acquire_gpu(colbar) < target) {
-          if (*reinterpret_cast<volatile int*>(R.gabort)) { ok = false; break; }
+          if (*reinterpret_cast<volatile int*>(R.gabort)) { ok = 0; break; }
           if (clock64() - c0 > kWaitCycles) {
             atomicExch(R.gabort, 1);
             atomicExch(P.err, 4);
-            ok = false;
+            ok = 0;
             break;
           }
         }
-        if (!ok) {
-          *abort_flag = 1;
-          break;
+        if (!ok) *abort_flag = 1;
+        else {
+          ISING_RTRACE(7, s, g);
+          tc::mbar_arrive(&go[g]);
         }
-        ISING_RTRACE(7, s);
-        tc::mbar_arrive(go);
       }
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) break;
+      // acquire side of the barrier for the whole warp (lane 0's acquire
+      // load is ordered before the shuffle)
+      __threadfence();
+      track_warp<INT_E, FP8>(R, t0 + s + 1, tb0, tb1, lane);
+      if (lane == 0) ISING_RTRACE(3, s, g);
     }
-  } else if (warp >= 4) {
-    // ------------------------------------------------ epilogue (+ tracking)
+  } else {
+    // ------------------------------------------------ epilogue
     const int q = warp & 3;
-    const int part = (warp - 4) >> 2;
-    constexpr int kCols = BN / 4;
+    const int part = (warp - 4) >> 2;  // which quarter of a group's columns
     const int64_t i = m0 + 32 * q + lane;
     const bool row_ok = i < P.n;
     const float h = row_ok ? P.hf[i] : 0.f;
-    const int hi = row_ok ? P.hint[i] : 0;
-    const float rs = (P.rowscale && row_ok) ? P.rowscale[i] : 1.f;
-    const int64_t nb0 = n0 + part * kCols;  // first restart of this warp's columns
-    const uint32_t lane_off = (uint32_t)(32 * q) << 16;
-    const uint32_t t_acc = tmem_base + lane_off + (uint32_t)(part * kCols);
-    const uint32_t t_th = t_acc + BN, t_m = t_acc + 2 * BN, t_v = t_acc + 3 * BN;
     EpiLane E;
     E.i = i;
     E.row_ok = row_ok;
-    E.hi = hi;
-    E.rs = rs;
+    E.hi = row_ok ? P.hint[i] : 0;
+    E.rs = (P.rowscale && row_ok) ? P.rowscale[i] : 1.f;
     E.chh = P.k.ch * h;
     E.hm_pos = fmaf(P.k.ch, h, -P.k.mu);  // = fmaf(ch, h, -mu s) for s = +1
     E.hm_neg = fmaf(P.k.ch, h, P.k.mu);   // ... and for s = -1
-    E.nb0 = nb0;
-    E.ncols = (int)max((int64_t)0, min((int64_t)kCols, P.B - nb0));
     E.orow = ((int64_t)mt * 4 + q) * P.B;
-    E.t_acc = t_acc;
     E.lane = lane;
-    // tracked restarts of this CTA
-    const int64_t col_end = n0 + BN < P.B ? n0 + BN : P.B;
-    const int64_t tb0 = n0 + (int64_t)mt * R.slice;
-    const int64_t tb1 = tb0 + R.slice < col_end ? tb0 + R.slice : col_end;
+    const uint32_t lane_off = (uint32_t)(32 * q) << 16;
+    auto group = [&](int g) {
+      EpiGroup Gr;
+      Gr.nb0 = n0 + g * GN + part * kCols;
+      Gr.ncols = (int)max((int64_t)0, min((int64_t)kCols, P.B - Gr.nb0));
+      Gr.t_acc = tmem_base + lane_off + (uint32_t)(g * 4 * GN + part * kCols);
+      return Gr;
+    };
     // state of this warp's columns into tensor memory
+    for (int g = 0; g < 2; ++g) {
+      const EpiGroup Gr = group(g);
 #pragma unroll 1
-    for (int c0 = 0; c0 < kCols; c0 += kChunk) {
-      uint32_t a[kChunk], bm[kChunk], c[kChunk];
+      for (int c0 = 0; c0 < kCols; c0 += kChunk) {
+        uint32_t a[kChunk], bm[kChunk], c[kChunk];
 #pragma unroll
-      for (int j = 0; j < kChunk; ++j) {
-        const int64_t b = nb0 + c0 + j;
-        const bool ok = row_ok && b < P.B;
-        const int64_t idx = b * P.ld + i;
-        a[j] = __float_as_uint(ok ? P.theta[idx] : 0.f);
-        bm[j] = __float_as_uint(ok ? P.m[idx] : 0.f);
-        c[j] = __float_as_uint(ok ? P.v[idx] : 0.f);
+        for (int j = 0; j < kChunk; ++j) {
+          const int64_t b = Gr.nb0 + c0 + j;
+          const bool ok = row_ok && b < P.B;
+          const int64_t idx = b * P.ld + i;
+          a[j] = __float_as_uint(ok ? P.theta[idx] : 0.f);
+          bm[j] = __float_as_uint(ok ? P.m[idx] : 0.f);
+          c[j] = __float_as_uint(ok ? P.v[idx] : 0.f);
+        }
+        tc::tmem_st8(Gr.t_acc + GN + c0, a);
+        tc::tmem_st8(Gr.t_acc + 2 * GN + c0, bm);
+        tc::tmem_st8(Gr.t_acc + 3 * GN + c0, c);
       }
-      tc::tmem_st8(t_th + c0, a);
-      tc::tmem_st8(t_m + c0, bm);
-      tc::tmem_st8(t_v + c0, c);
     }
     tc::tmem_wait_st();
     bool ok = true;
-    for (int64_t s = 0; s < K && ok; ++s) {
+    for (int64_t p = 0; p < NP && ok; ++p) {
+      const int64_t s = p >> 1;
+      const int g = (int)(p & 1);
       const long long t = t0 + s + 1;
-      const float2 bc = P.bias[t];  // loaded ahead of the waits, off the critical path
-      if (s > 0) {
-        if (!tc::mbar_wait(go, (uint32_t)((s - 1) & 1), abort_flag, kWaitCycles)) { ok = false; break; }
-        track_slice<INT_E, FP8>(R, t - 1, tb0, tb1, warp - 4, kEpiWarps, lane);
-      }
-      if (warp == 4 && lane == 0) ISING_RTRACE(3, s);
-      if (!tc::mbar_wait(acc_full, (uint32_t)(s & 1), abort_flag, kWaitCycles)) {
+      const float2 bc = P.bias[t];  // loaded ahead of the wait, off the critical path
+      if (!tc::mbar_wait(&acc_full[g], (uint32_t)(s & 1), abort_flag, kWaitCycles)) {
         atomicExch(P.err, 3);
         atomicExch(R.gabort, 1);
         ok = false;
         break;
       }
       tc::fence_after_sync();
-      if (warp == 4 && lane == 0) ISING_RTRACE(4, s);
+      if (warp == 4 && lane == 0) ISING_RTRACE(4, s, g);
       const bool last = s + 1 == K;
+      const EpiGroup Gr = group(g);
       if constexpr (INT_E) {
-        if (P.gmagic == 2) resident_chunks<BN, true, FP8, 2>(R, E, t, bc, last, acc_empty);
-        else if (P.gmagic == 1) resident_chunks<BN, true, FP8, 1>(R, E, t, bc, last, acc_empty);
-        else resident_chunks<BN, true, FP8, 0>(R, E, t, bc, last, acc_empty);
+        if (P.gmagic == 2) resident_chunks<GN, true, FP8, 2>(R, E, Gr, t, bc, last, &acc_empty[g]);
+        else if (P.gmagic == 1) resident_chunks<GN, true, FP8, 1>(R, E, Gr, t, bc, last, &acc_empty[g]);
+        else resident_chunks<GN, true, FP8, 0>(R, E, Gr, t, bc, last, &acc_empty[g]);
       } else {
-        resident_chunks<BN, false, FP8, 0>(R, E, t, bc, last, acc_empty);
+        resident_chunks<GN, false, FP8, 0>(R, E, Gr, t, bc, last, &acc_empty[g]);
       }
       tc::tmem_wait_st();
       tc::fence_proxy_async_global();
       __syncwarp();
-      if (warp == 4 && lane == 0) ISING_RTRACE(5, s);
-      if (lane == 0) tc::mbar_arrive(step_done);
-    }
-    if (ok && K > 0) {
-      // the last step's bests, once every CTA has written its partials
-      if (tc::mbar_wait(go, (uint32_t)((K - 1) & 1), abort_flag, kWaitCycles))
-        track_slice<INT_E, FP8>(R, t0 + K, tb0, tb1, warp - 4, kEpiWarps, lane);
+      if (warp == 4 && lane == 0) ISING_RTRACE(5, s, g);
+      if (lane == 0) tc::mbar_arrive(&step_done[g]);
     }
   }
+#undef ISING_RTRACE
   __syncwarp();
   __syncthreads();
   if (threadIdx.x == 0 && blockIdx.x == 0 && !*abort_flag) {
@@ -985,7 +1039,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 struct TcState {
   CUtensorMap A[3];
-  CUtensorMap B[3];  // one per spin slot
+  CUtensorMap B[3];   // one per spin slot, boxes of BN restarts (streaming kernel)
+  CUtensorMap Bg[3];  // one per spin slot, boxes of one restart group (resident kernel)
   int BN = 128;
   size_t smem = 0;
   int grid = 1;
@@ -994,6 +1049,10 @@ struct TcState {
   bool resident = false;  // one tile per CTA, state kept in tensor memory
   DevMem gsync;           // abort word + per-column barrier counters
   int emode = 0;          // resident epilogue's integer energy mode (0 F2I, 1 offset, 2 packed)
+  int gn = 64;            // resident form: restarts per group (a CTA holds two groups)
+  int jres = 0, nst = 0;  // resident form: J tiles kept in shared memory, stages
+  uint32_t bars = 0;      // resident form: offset of the barrier block
+  size_t res_bytes = 0;   // resident form: dynamic shared memory
   DevMem err;
   DevMem trace;  // grid x 8 timestamps of the last profiled launch
 };
@@ -1061,29 +1120,29 @@ int launch_mode(ising_ds* ds, TcState* st, const TcArgs& a, int slot) {
 
 }  // namespace
 
-template <int BN, bool INT_E, bool FP8>
-int resident_attr(ising_ctx* ctx, int* blocks_per_sm) {
-  auto kern = tc_resident_kernel<BN, INT_E, FP8>;
-  const size_t smem = TcLayout<BN>::kBytes;
+template <int GN, bool INT_E, bool FP8>
+int resident_attr(ising_ctx* ctx, size_t smem, int* blocks_per_sm) {
+  auto kern = tc_resident_kernel<GN, INT_E, FP8>;
   ISING_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   ISING_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kern, kThreads, smem));
   return ISING_OK;
 }
 
-template <int BN, bool INT_E, bool FP8>
+template <int GN, bool INT_E, bool FP8>
 int resident_launch(ising_ds* ds, TcState* st, const TcResArgs& ra) {
-  auto kern = tc_resident_kernel<BN, INT_E, FP8>;
-  void* args[] = {&st->A[0], &st->A[1], &st->A[2], &st->B[0], &st->B[1], &st->B[2],
+  auto kern = tc_resident_kernel<GN, INT_E, FP8>;
+  void* args[] = {&st->A[0], &st->A[1], &st->A[2], &st->Bg[0], &st->Bg[1], &st->Bg[2],
                   const_cast<TcResArgs*>(&ra)};
   ISING_CUDA(ds->ctx, cudaLaunchCooperativeKernel((const void*)kern, dim3(st->grid), dim3(kThreads),
-                                                  args, TcLayout<BN>::kBytes, ds->ctx->stream));
+                                                  args, st->res_bytes, ds->ctx->stream));
   return ISING_OK;
 }
 
-template <int BN>
-int resident_attr_bn(ising_ds* ds, bool fp8, int* nb) {
-  if (ds->int_energy) return fp8 ? resident_attr<BN, true, true>(ds->ctx, nb) : resident_attr<BN, true, false>(ds->ctx, nb);
-  return fp8 ? resident_attr<BN, false, true>(ds->ctx, nb) : resident_attr<BN, false, false>(ds->ctx, nb);
+template <int GN>
+int resident_attr_bn(ising_ds* ds, bool fp8, size_t smem, int* nb) {
+  if (ds->int_energy)
+    return fp8 ? resident_attr<GN, true, true>(ds->ctx, smem, nb) : resident_attr<GN, true, false>(ds->ctx, smem, nb);
+  return fp8 ? resident_attr<GN, false, true>(ds->ctx, smem, nb) : resident_attr<GN, false, false>(ds->ctx, smem, nb);
 }
 
 template <int BN>
@@ -1093,9 +1152,10 @@ int resident_launch_bn(ising_ds* ds, TcState* st, const TcResArgs& ra) {
   return st->fp8 ? resident_launch<BN, false, true>(ds, st, ra) : resident_launch<BN, false, false>(ds, st, ra);
 }
 
-// Abort word, then one arrival counter per restart column, 128 bytes apart.
+// Abort word, then one arrival counter per restart group of each column, 128
+// bytes apart.
 static size_t gsync_bytes(const ising_ds* ds, const TcState* st) {
-  return (size_t)(1 + ceil_div_i(ds->B, st->BN)) * 128;
+  return (size_t)(1 + 2 * ceil_div_i(ds->B, st->BN)) * 128;
 }
 
 int tc_setup(ising_ds* ds) {
@@ -1164,18 +1224,33 @@ int tc_setup(ising_ds* ds) {
       if (32ull * r < 32768ull) st->emode = 2;
     }
   }
-  // resident form when every (128 x BN) tile gets its own co-resident CTA
+  // resident form when every (128 x 2 GN) tile gets its own co-resident CTA
+  // (a tensor-memory kernel holds its SM alone): two groups of GN restarts
+  // per CTA, 64 each, or 32 when B <= 64
   if (!(ds->p.flags & ISING_DS_STREAMING)) {
-    const int mtn = ceil_div_i(ds->n, kBM);
-    for (int bn : {128, 64}) {
-      const int tiles = mtn * ceil_div_i(ds->B, bn);
-      int nb = 0;
-      ISING_TRY(bn == 128 ? resident_attr_bn<128>(ds, st->fp8, &nb) : resident_attr_bn<64>(ds, st->fp8, &nb));
+    const int gn = ds->B > 64 ? 64 : 32;
+    const int tiles = ceil_div_i(ds->n, kBM) * ceil_div_i(ds->B, 2 * gn);
+    // shared memory: resident J tiles (as many as leave room for 4 stages of 2 k-blocks),
+    // then the stages, then the barrier block
+    const int64_t kA = (int64_t)kBM * kRowBytes, kStage = 2 * (kA + (int64_t)gn * kRowBytes);
+    const int64_t region = ((int64_t)ctx->smem_optin - 1024 - 512) / 1024 * 1024;
+    const int nkt = ceil_div_i(ds->n, st->fp8 ? 128 : 64) * ds->planes;
+    const int jres = (int)std::min<int64_t>(nkt, std::max<int64_t>(0, (region - 4 * kStage) / kA));
+    const int nst = (int)std::min<int64_t>(8, (region - jres * kA) / kStage);
+    int nb = 0;
+    if (nst >= 2) {
+      const size_t bytes = (size_t)region + 512 + 1024;
+      ISING_TRY(gn == 64 ? resident_attr_bn<64>(ds, st->fp8, bytes, &nb)
+                         : resident_attr_bn<32>(ds, st->fp8, bytes, &nb));
       if (nb >= 1 && tiles <= nb * ctx->sm_count) {
         st->resident = true;
-        st->BN = bn;
+        st->BN = 2 * gn;
+        st->gn = gn;
         st->grid = tiles;
-        break;
+        st->jres = jres;
+        st->nst = nst;
+        st->bars = (uint32_t)region;
+        st->res_bytes = bytes;
       }
     }
   }
@@ -1192,9 +1267,13 @@ int tc_setup(ising_ds* ds) {
 // common allocation; they are built on first use.
 static int tc_maps(ising_ds* ds, TcState* st) {
   static_assert(sizeof(CUtensorMap) == 128, "CUtensorMap size");
-  for (int s = 0; s < 3; ++s)
+  for (int s = 0; s < 3; ++s) {
     ISING_TRY(make_map(ds->ctx, &st->B[s], ds->spins[s].p, ds->n, ds->B, ds->ld,
                        st->fp8 ? 128 : 64, st->BN, st->fp8));
+    if (st->resident)
+      ISING_TRY(make_map(ds->ctx, &st->Bg[s], ds->spins[s].p, ds->n, ds->B, ds->ld,
+                         st->fp8 ? 128 : 64, st->gn, st->fp8));
+  }
   return ISING_OK;
 }
 
@@ -1317,8 +1396,11 @@ int tc_run_resident(ising_ds* ds, int64_t steps) {
   r.cq = ds->inst.cq;
   r.chs = ds->inst.ch * std::ldexp(1.0, -ds->h_shift);
   r.rows = ds->mtiles;
-  r.slice = ceil_div_i(st->BN, ceil_div_i(ds->n, kBM));
-  return st->BN == 128 ? resident_launch_bn<128>(ds, st, r) : resident_launch_bn<64>(ds, st, r);
+  r.slice = ceil_div_i(st->gn, ceil_div_i(ds->n, kBM));
+  r.jres = st->jres;
+  r.nst = st->nst;
+  r.bars = st->bars;
+  return st->gn == 64 ? resident_launch_bn<64>(ds, st, r) : resident_launch_bn<32>(ds, st, r);
 }
 
 int tc_error(ising_ds* ds) {
