@@ -448,7 +448,12 @@ def main():
                 "unit": "TFLOP/s",
                 "peak_note": ("FP8 = 2 x measured BF16 sustained" if fp8
                               else "measured BF16 sustained")}
-        kname, ksrc = "tc_resident_kernel", "paper_2312_05837_gb300/csrc/ds_tc.cu"
+        if st["precision"] == 2 and not inst.integer:
+            # float J as three BF16 planes: the tensor cores execute 3 x the
+            # algorithmic flops counted here
+            roof["operand_planes"] = 3
+        kname = "tc_resident_kernel" if st["resident"] else "tc_step_kernel"
+        ksrc = "paper_2312_05837_gb300/csrc/ds_tc.cu"
     else:  # plain FP32 FMA on the CUDA cores: 2 N^2 B flop per step
         alg = 2.0 * n_red * n_red * B
         sms = torch.cuda.get_device_properties(local).multi_processor_count
