@@ -40,6 +40,9 @@ WORKLOADS = {
     "sk4096": ("sk4096", 4096, 5000),
     "torus20k": ("torus20k", 512, 3000),
     "er100k_pendant": ("er100k_pendant", 512, 3000),
+    # complete 1000-spin graphs of the solver comparison (Sec. IV-C)
+    "table2_uniform": ("table2_uniform", 1024, 1000),
+    "table2_gaussian": ("table2_gaussian", 1024, 1000),
 }
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 
@@ -161,17 +164,39 @@ def traffic_for(kernel: str, src_file: str):
     return d["bytes_per_launch"] if d.get("source_sha") == h else None
 
 
+def paper_metrics(inst, E: float, seconds: float) -> dict:
+    """Sec. IV-C's figures for one solve: chi_hat = 1/2 - E / (2 (sqrt(d)
+    ||A||_F + ||b||_1)) in the paper's form E = s^T A s + b^T s, the estimated
+    time-to-solution T log(1 - 0.99) / log(1 - e^chi_hat / d) and the speed
+    v = chi_hat / T, with T the solve's device time."""
+    import math
+    import numpy as np
+    if inst.convention == "paper":
+        cq, ch = inst.j_scale, 1.0
+    else:
+        cq, ch = -0.5 * inst.j_scale, -1.0
+    J = np.asarray(inst.dense(), dtype=np.float64)
+    h = np.zeros(inst.n) if inst.h is None else np.asarray(inst.h, dtype=np.float64)
+    scale = math.sqrt(inst.n) * abs(cq) * float(np.linalg.norm(J)) + abs(ch) * float(np.abs(h).sum())
+    chi = 0.5 - E / (2.0 * scale)
+    p = math.exp(chi) / inst.n
+    tts = seconds * math.log(1.0 - 0.99) / math.log(1.0 - p) if 0.0 < p < 1.0 else None
+    return {"chi_hat": chi, "T_s": seconds, "tts_s": tts, "v_per_s": chi / seconds}
+
+
 def launches_per_solve(T: int, rounds: int, path: int, resident: bool) -> int:
-    """Kernels of one solve: instance check (1), pruning (dense->CSR 2, init 1,
-    7 per round incl. the final empty one, sum + reduced field + reduced J 3),
-    session set-up (facts 1, operand 1, fills 2, init 1), the steps (one
-    cooperative launch when resident, else step + track per step, plus the
-    copy of improved bit-packed spins on the sparse path), finish
-    (energy-only step + track (+ copy) + argmin), reconstruction (1),
-    full-instance energy (2)."""
+    """Kernels of one solve, as the ncu launch list of a solve shows them:
+    instance checks (couplings twice, field once), pruning (dense->CSR 2,
+    init 1, 7 per round incl. the final empty one, sum + reduced J + reduced
+    field 3), session set-up (fills 2, init 1, operand 1, plus the row-sum
+    bound of the integer tensor-core path), the steps (one cooperative launch
+    when resident, else step + track per step, plus the copy of improved
+    bit-packed spins on the sparse path), finish (energy-only step + track
+    (+ copy) + argmin), reconstruction (1), full-instance energy (2)."""
     per_step = 3 if path == 2 else 2
     steps = 1 if resident else per_step * T
-    return 1 + 3 + 7 * (rounds + 1) + 3 + 5 + steps + per_step + 1 + 1 + 2
+    setup = 4 + (1 if path == 1 else 0)
+    return 3 + 3 + 7 * (rounds + 1) + 3 + setup + steps + per_step + 1 + 1 + 2
 
 
 # ----------------------------------------------------------------- reference arm
@@ -482,6 +507,8 @@ def main():
             "gpu_launches": launches_per_solve(T, rounds, path, bool(last["resident"])) * a.steps,
             "roofline": roof, "clocks": clk,
             "best_energy": float(last["best_energy"].item())}
+    if name.startswith("table2"):
+        line["paper_metrics"] = paper_metrics(inst, line["best_energy"], max_ms / a.steps / 1e3)
     if rank == 0 and not a.no_extras:
         line["time_to_target"] = time_to_target(ctx, dinst, B, T, seed=3)
         line["serving"] = serving(ctx)

@@ -21,6 +21,7 @@ from .instances import (  # noqa: F401
     torus_csr,
     regular_instance,
     table1_instance,
+    table2_instance,
     random_sparse_instance,
     workload,
     serving_stream,

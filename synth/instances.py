@@ -331,6 +331,28 @@ def table1_instance(dist: str, seed: int, n: int = 1000, k: int = 6) -> Instance
     return regular_instance(n, k, seed, jv, hv, name=f"table1-{dist}")
 
 
+def table2_instance(dist: str, seed: int, n: int = 1000) -> Instance:
+    """The complete-graph family of the solver comparison (Sec. IV-C), paper
+    convention E = sum_{i>j} J_hat_ij s_i s_j + sum_i h_i s_i:
+    uniform  J_hat_ij, h_i ~ U(-1000, 1000);
+    gaussian J_hat_ij, h_i ~ N(0, alpha^2) with alpha ~ U(0, 1000) drawn once
+    per instance. Dense FP32."""
+    rng = _rng(seed, 10)
+    if dist == "uniform":
+        g = rng.uniform(-1000.0, 1000.0, (n, n))
+        hv = rng.uniform(-1000.0, 1000.0, n)
+    elif dist == "gaussian":
+        alpha = rng.uniform(0.0, 1000.0)
+        g = rng.standard_normal((n, n)) * alpha
+        hv = rng.standard_normal(n) * alpha
+    else:
+        raise ValueError(dist)
+    J = np.triu(g, k=1)
+    J = (J + J.T).astype(np.float32)
+    return Instance(n=n, layout="dense", J=J, h=hv.astype(np.float32), j_scale=0.5,
+                    convention="paper", name=f"table2-{dist}")
+
+
 def random_sparse_instance(n: int, seed: int, p: float = 0.3, kind: str = "int",
                            h: str = "int", convention: str = "physics",
                            j_scale: float = 1.0, layout: str = "csr",
@@ -367,6 +389,10 @@ def workload(name: str, seed: int = 0) -> Instance:
         return er_dense(800, seed, p=0.06, weights="one", name="er800")
     if name == "er2000":
         return er_dense(2000, seed, mean_degree=10.0, weights="pm1", name="er2000")
+    if name == "table2_uniform":
+        return table2_instance("uniform", seed)
+    if name == "table2_gaussian":
+        return table2_instance("gaussian", seed)
     if name == "sk4096":
         return sk_dense(4096, seed, math.sqrt(1.0 / 4096), np.float32,
                         h_std=math.sqrt(0.1), name="sk4096")

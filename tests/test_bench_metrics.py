@@ -1,0 +1,41 @@
+"""bench.py's Sec. IV-C figures (chi_hat, estimated TTS, speed) against the
+oracle's metrics module, on both conventions and layouts."""
+
+import os
+import sys
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import domain_selection as ods
+from oracle import metrics
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+@pytest.mark.parametrize("inst", [synth.table2_instance("uniform", 0, n=60),
+                                  synth.table2_instance("gaussian", 1, n=40),
+                                  synth.table1_instance("gaussian", 2, n=50),
+                                  synth.er_dense(70, 3, p=0.1, weights="pm1")])
+def test_paper_metrics_match_the_oracle(inst):
+    import bench
+    r = ods.select_domain(inst, ods.Params(restarts=8, steps=30, seed=1))
+    E = float(r["best_energy"])
+    got = bench.paper_metrics(inst, E, 0.25)
+    chi = metrics.chi_hat(inst, E)
+    assert got["chi_hat"] == pytest.approx(chi, rel=1e-12)
+    assert got["tts_s"] == pytest.approx(metrics.tts(0.25, chi, inst.n), rel=1e-9)
+    assert got["v_per_s"] == pytest.approx(metrics.speed(0.25, chi), rel=1e-12)
+    assert got["chi_hat"] > 0.5  # E < 0 for a found optimum of a random instance
+
+
+def test_table2_family_shapes():
+    u = synth.table2_instance("uniform", 5, n=200)
+    assert u.convention == "paper" and u.j_scale == 0.5 and u.J.dtype == np.float32
+    assert np.array_equal(u.J, u.J.T) and not np.diag(u.J).any()
+    assert np.abs(u.J).max() <= 1000 and np.abs(u.h).max() <= 1000
+    g = synth.table2_instance("gaussian", 5, n=200)
+    assert np.array_equal(g.J, g.J.T)

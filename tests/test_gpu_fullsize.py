@@ -1,7 +1,8 @@
 """Parity at the full workload sizes the benchmark times, in the same launch
 configuration (precision AUTO, so the resident FP8 tensor-core form for the
 N=2000 max-cut, the sparse kernel for the torus and the pruned ER graph, the
-streaming three-plane BF16 form for N=4096 SK): after a run of steps, one
+streaming three-plane BF16 form for N=4096 SK, the resident three-plane form
+for the complete 1000-spin graphs of Sec. IV-C): after a run of steps, one
 step of a sample of restarts is checked against the oracle element by
 element (Sec. III-B), and the reduced-precision operand forms are held to the
 plain FP32 path's best energy (Sec. IV)."""
@@ -31,6 +32,7 @@ def _sample(st, idx):
     ("torus20k", 512, 200, 2, 1),
     ("sk4096", 4096, 40, 1, 2),
     ("er100k_pendant", 512, 60, 2, 1),
+    ("table2_uniform", 1024, 100, 1, 2),
 ])
 def test_bench_workload_sampled_one_step_parity(gpu_ctx, name, B, warm, path, prec):
     inst = synth.workload(name, 0)
@@ -50,7 +52,7 @@ def test_bench_workload_sampled_one_step_parity(gpu_ctx, name, B, warm, path, pr
     s.finish()
     res = s.result()
     assert (res["path"], res["precision"]) == (path, prec)
-    if name == "er2000":
+    if name in ("er2000", "table2_uniform"):
         assert res["resident"] == 1
     e = ising.energy(inst, res["best_spins"].astype(np.float64))
     assert res["best_energy"] == pytest.approx(float(e), rel=1e-12, abs=1e-9)
