@@ -164,26 +164,6 @@ def traffic_for(kernel: str, src_file: str):
     return d["bytes_per_launch"] if d.get("source_sha") == h else None
 
 
-def paper_metrics(inst, E: float, seconds: float) -> dict:
-    """Sec. IV-C's figures for one solve: chi_hat = 1/2 - E / (2 (sqrt(d)
-    ||A||_F + ||b||_1)) in the paper's form E = s^T A s + b^T s, the estimated
-    time-to-solution T log(1 - 0.99) / log(1 - e^chi_hat / d) and the speed
-    v = chi_hat / T, with T the solve's device time."""
-    import math
-    import numpy as np
-    if inst.convention == "paper":
-        cq, ch = inst.j_scale, 1.0
-    else:
-        cq, ch = -0.5 * inst.j_scale, -1.0
-    J = np.asarray(inst.dense(), dtype=np.float64)
-    h = np.zeros(inst.n) if inst.h is None else np.asarray(inst.h, dtype=np.float64)
-    scale = math.sqrt(inst.n) * abs(cq) * float(np.linalg.norm(J)) + abs(ch) * float(np.abs(h).sum())
-    chi = 0.5 - E / (2.0 * scale)
-    p = math.exp(chi) / inst.n
-    tts = seconds * math.log(1.0 - 0.99) / math.log(1.0 - p) if 0.0 < p < 1.0 else None
-    return {"chi_hat": chi, "T_s": seconds, "tts_s": tts, "v_per_s": chi / seconds}
-
-
 def launches_per_solve(T: int, rounds: int, path: int, resident: bool) -> int:
     """Kernels of one solve, as the ncu launch list of a solve shows them:
     instance checks (couplings twice, field once), pruning (dense->CSR 2,
@@ -508,6 +488,7 @@ def main():
             "roofline": roof, "clocks": clk,
             "best_energy": float(last["best_energy"].item())}
     if name.startswith("table2"):
+        from paper_2312_05837_gb300.metrics import paper_metrics
         line["paper_metrics"] = paper_metrics(inst, line["best_energy"], max_ms / a.steps / 1e3)
     if rank == 0 and not a.no_extras:
         line["time_to_target"] = time_to_target(ctx, dinst, B, T, seed=3)

@@ -1,5 +1,6 @@
-"""bench.py's Sec. IV-C figures (chi_hat, estimated TTS, speed) against the
-oracle's metrics module, on both conventions and layouts."""
+"""The library's Sec. IV-C figures (chi_hat, estimated TTS, speed), which
+bench.py and the experiments report, against the oracle's metrics module,
+on both conventions and layouts."""
 
 import os
 import sys
@@ -21,10 +22,10 @@ if ROOT not in sys.path:
                                   synth.table1_instance("gaussian", 2, n=50),
                                   synth.er_dense(70, 3, p=0.1, weights="pm1")])
 def test_paper_metrics_match_the_oracle(inst):
-    import bench
+    from paper_2312_05837_gb300.metrics import paper_metrics
     r = ods.select_domain(inst, ods.Params(restarts=8, steps=30, seed=1))
     E = float(r["best_energy"])
-    got = bench.paper_metrics(inst, E, 0.25)
+    got = paper_metrics(inst, E, 0.25)
     chi = metrics.chi_hat(inst, E)
     assert got["chi_hat"] == pytest.approx(chi, rel=1e-12)
     assert got["tts_s"] == pytest.approx(metrics.tts(0.25, chi, inst.n), rel=1e-9)

@@ -1,0 +1,37 @@
+"""The pruning experiment of Sec. IV-B (Table 1) on the GPU path, a few
+trials per family: the GPU pruning rate equals the oracle's on every
+instance (the binary family prunes nothing, as the table says), both solves
+return spins whose oracle energy is the reported energy, and the aggregate
+carries every column of the table."""
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import ising, pruning
+from paper_2312_05837_gb300 import api, experiments
+from paper_2312_05837_gb300.metrics import chi_hat
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("dist", ["uniform", "gaussian", "binary", "binary_int"])
+def test_trials_match_the_oracle(gpu_ctx, dist):
+    for k in range(3):
+        inst = synth.table1_instance(dist, 100 + k)
+        r = experiments.table1_trial(gpu_ctx, inst, restarts=4, steps=60, seed=k)
+        assert r["eta"] == pruning.prune(inst).eta
+        if dist.startswith("binary"):
+            assert r["eta"] == 0.0
+        for tag in ["pds", "ds"]:
+            e = float(ising.energy(inst, r["spins_" + tag].astype(np.float64)))
+            assert r["E_" + tag] == pytest.approx(e, rel=1e-12, abs=1e-9)
+            assert r["chi_" + tag] == pytest.approx(chi_hat(inst, e), rel=1e-12)
+
+
+def test_aggregate_has_every_column(gpu_ctx):
+    out = experiments.table1(gpu_ctx, "uniform", trials=4, restarts=1, steps=50)
+    for key in ["eta", "T_ds", "chi_ds", "T_pds", "chi_pds", "d_chi"]:
+        mean, std = out[key]
+        assert np.isfinite(mean) and std >= 0
+    assert 0.5 < out["eta"][0] <= 1.0
