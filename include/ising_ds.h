@@ -134,6 +134,16 @@ typedef struct ising_ds_params {
  * not depend on the shape. Choices are cached per process and, when the
  * environment variable ISING_TUNE_CACHE names a file, across processes. */
 #define ISING_DS_NO_AUTOTUNE 4
+/* params.flags: the convergence rule of Sec. IV-B, read on the energy of the
+ * rounded spins: restart b stops at the first step t >= 5 where
+ * max - min of E_{t-4..t}(b) <= 0.005 |E_t(b) - E_1(b)| (at convergence
+ * sin(theta) -> s and the paper's loss equals E - mu d). A stopped restart's
+ * best and last energy are those of steps 1..t; the run ends once every
+ * restart has stopped (checked every 48 steps, so up to 47 more steps may run,
+ * which change nothing) and ising_ds_stats.steps_done tells how far it went;
+ * the final evaluation (step T+1) applies to restarts still running after T.
+ * Per-restart stopping steps: ising_ds_convergence. */
+#define ISING_DS_CONVERGE 8
 
 typedef struct ising_ds_stats {
   int64_t best_restart;     /* restart holding the overall best */
@@ -295,6 +305,9 @@ int ising_ds_trace(ising_ds* ds, uint64_t* out, int64_t cap, int64_t* count);
 /* Energies E(s_t) of the spins consumed by the most recent step, [B]. */
 int ising_ds_last_energies(ising_ds* ds, double* E, int mem);
 /* Per-restart best so far: energy [B], step [B], spins [B][n] (any NULL). */
+/* With ISING_DS_CONVERGE: the step at which each restart stopped (0 while it
+ * runs), [B] int64 in memory `mem`. Without the flag all zeros. */
+int ising_ds_convergence(ising_ds* ds, int64_t* step, int mem);
 int ising_ds_restart_best(ising_ds* ds, double* E, int64_t* step, int8_t* spins,
                           int mem);
 /* Overall best (after ising_ds_finish, or the best so far). */

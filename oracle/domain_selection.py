@@ -92,10 +92,25 @@ def step(J, h, cq, ch, p: Params, theta, m, v, t: int) -> StepResult:
     return StepResult(s, G, E, F, g, th, m, v)
 
 
-def select_domain(inst, p: Params, trace: bool = False, theta0=None):
+# Convergence rule of Sec. IV-B: a restart has converged at step t when the
+# spread (max - min) of its last CONV_WINDOW values is at most CONV_TOL times
+# the change since the first step. Read on the energy of the rounded spins
+# (at convergence sin(theta) -> s and the loss equals E - mu d).
+CONV_WINDOW = 5
+CONV_TOL = 0.005
+
+
+def select_domain(inst, p: Params, trace: bool = False, theta0=None, converge: bool = False):
     """Run T steps on all restarts; return a dict with the overall best
     (energy, spins, restart, step), per-restart bests, the last-step energies
-    E_{T+1} and, when ``trace``, the (T+1, B) energy trace."""
+    E_{T+1} and, when ``trace``, the (T+1, B) energy trace.
+
+    With ``converge``, each restart stops at the first step t >= CONV_WINDOW
+    where max - min of E_{t-4..t} <= CONV_TOL |E_t - E_1| (Sec. IV-B): its best
+    and last energy are those of steps 1..t, ``conv_step`` holds t (0 if it
+    never stops), and the run ends once every restart has stopped
+    (``steps_done``); the final evaluation E_{T+1} applies to the restarts
+    still running after step T."""
     cq, ch = ising.coefficients(inst.j_scale, inst.convention)
     J = ising.coupling_matrix(inst)
     h = ising.field(inst)
@@ -108,21 +123,44 @@ def select_domain(inst, p: Params, trace: bool = False, theta0=None):
     best_s = np.zeros((n, B))
     tr = np.zeros((p.steps + 1, B)) if trace else None
 
+    conv_step = np.zeros(B, dtype=np.int64)
+    ring = np.zeros((CONV_WINDOW, B))
+    E_init = np.zeros(B)
+    E_stop = np.zeros(B)
+
     def keep(E, s, t):
-        better = E < best_e
+        better = (E < best_e) & (conv_step == 0)
         best_e[better] = E[better]
         best_t[better] = t
         best_s[:, better] = s[:, better]
 
+    steps_done = p.steps
     for t in range(1, p.steps + 1):
         r = step(J, h, cq, ch, p, theta, m, v, t)
         keep(r.energy, r.spins, t)
         if trace:
             tr[t - 1] = r.energy
         theta, m, v = r.theta, r.m, r.v
+        if converge:
+            active = conv_step == 0
+            ring[(t - 1) % CONV_WINDOW, active] = r.energy[active]
+            if t == 1:
+                E_init[:] = r.energy
+            E_stop[active] = r.energy[active]
+            if t >= CONV_WINDOW:
+                spread = ring.max(axis=0) - ring.min(axis=0)
+                hit = active & (spread <= CONV_TOL * np.abs(r.energy - E_init))
+                conv_step[hit] = t
+            if (conv_step > 0).all():
+                steps_done = t
+                break
     s_last = round_spins(theta)
     E_last = cq * np.sum(s_last * (J @ s_last), axis=0) + ch * (h @ s_last)
-    keep(E_last, s_last, p.steps + 1)
+    if steps_done == p.steps:
+        keep(E_last, s_last, p.steps + 1)
+    if converge:
+        stopped = conv_step > 0
+        E_last = np.where(stopped, E_stop, E_last)
     if trace:
         tr[p.steps] = E_last
     b = int(np.lexsort((np.arange(B), best_e))[0])
@@ -131,4 +169,4 @@ def select_domain(inst, p: Params, trace: bool = False, theta0=None):
                 restart_best_energy=best_e, restart_best_step=best_t,
                 restart_best_spins=best_s.astype(np.int8),
                 last_energy=E_last, last_spins=s_last.astype(np.int8),
-                theta=theta, m=m, v=v, trace=tr)
+                theta=theta, m=m, v=v, trace=tr, conv_step=conv_step, steps_done=steps_done)

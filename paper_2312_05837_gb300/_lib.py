@@ -24,6 +24,7 @@ PRUNE_ZERO_RULE = 1
 DS_PROFILE = 1
 DS_STREAMING = 2
 DS_NO_AUTOTUNE = 4
+DS_CONVERGE = 8
 
 
 class Instance(ctypes.Structure):
@@ -94,6 +95,7 @@ _PROTOS = {
     "ising_ds_trace": (c_int, [c_void_p, c_void_p, c_int64, POINTER(c_int64)]),
     "ising_ds_last_energies": (c_int, [c_void_p, c_void_p, c_int]),
     "ising_ds_restart_best": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int]),
+    "ising_ds_convergence": (c_int, [c_void_p, c_void_p, c_int]),
     "ising_ds_result": (c_int, [c_void_p, c_void_p, POINTER(c_double), POINTER(DSStats), c_int]),
     "ising_ds_destroy": (c_int, [c_void_p]),
     "ising_server_create": (c_int, [c_void_p, POINTER(ServerCfg), POINTER(c_void_p)]),

@@ -154,7 +154,8 @@ def make_instance(inst):
 
 
 def params(restarts, steps, lr=6.0, mu=0.0, beta1=0.9, beta2=0.999, eps=1e-8, seed=0,
-           precision="auto", profile=False, streaming=False, autotune=True) -> L.DSParams:
+           precision="auto", profile=False, streaming=False, autotune=True,
+           converge=False) -> L.DSParams:
     p = L.DSParams()
     p.restarts = int(restarts)
     p.steps = int(steps)
@@ -162,7 +163,7 @@ def params(restarts, steps, lr=6.0, mu=0.0, beta1=0.9, beta2=0.999, eps=1e-8, se
     p.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
     p.precision = _PREC[precision] if isinstance(precision, str) else int(precision)
     p.flags = ((L.DS_PROFILE if profile else 0) | (L.DS_STREAMING if streaming else 0) |
-               (0 if autotune else L.DS_NO_AUTOTUNE))
+               (0 if autotune else L.DS_NO_AUTOTUNE) | (L.DS_CONVERGE if converge else 0))
     return p
 
 
@@ -446,6 +447,13 @@ class Session:
         E = np.empty(self.B, np.float64)
         self.ctx.check(self.ctx.lib.ising_ds_last_energies(self.handle, _ptr(E), L.MEM_HOST))
         return E
+
+    def convergence(self) -> np.ndarray:
+        """Step at which each restart stopped under the convergence rule (0
+        while it runs)."""
+        out = np.empty(self.B, np.int64)
+        self.ctx.check(self.ctx.lib.ising_ds_convergence(self.handle, _ptr(out), L.MEM_HOST))
+        return out
 
     def restart_best(self):
         E = np.empty(self.B, np.float64)

@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <cstdlib>
 #include <fstream>
 #include <limits>
@@ -104,7 +105,8 @@ __device__ __forceinline__ int8_t spin_at(const void* spins, int64_t n, int64_t 
 // then a fixed xor tree across lanes, so the sum is deterministic), strict <
 // against the best so far, copy of S_t for improved restarts (for bit-packed
 // spins a per-restart flag instead, which track_bits_copy_kernel reads); the
-// last block advances the step counter.
+// last block advances the step counter. With the convergence rule (conv_step
+// non-null) a stopped restart is left alone, and steps t <= T feed the rule.
 template <int KIND>
 __global__ void __launch_bounds__(256) track_kernel(
     int64_t n, int64_t B, int64_t Bp, int64_t ld, int mtiles, bool int_mode, double cq,
@@ -112,7 +114,9 @@ __global__ void __launch_bounds__(256) track_kernel(
     const float* __restrict__ epart, const void* __restrict__ spins_t,
     double* __restrict__ best_E, long long* __restrict__ best_t, int8_t* __restrict__ best_s,
     double* __restrict__ last_E, long long* __restrict__ counters, int64_t bs_ld,
-    uint8_t* __restrict__ improved_out) {
+    uint8_t* __restrict__ improved_out, int64_t T, double* __restrict__ conv_ring,
+    double* __restrict__ conv_init, long long* __restrict__ conv_step,
+    unsigned long long* __restrict__ conv_count) {
   const long long t = counters[0] + 1;
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -139,14 +143,16 @@ __global__ void __launch_bounds__(256) track_kernel(
       E = e;
     }
     // every lane holds the same E (the xor tree is symmetric)
-    const bool improved = E < best_E[b];
+    const bool active = conv_step == nullptr || conv_step[b] == 0;
+    const bool improved = active && E < best_E[b];
     __syncwarp();
-    if (lane == 0) {
+    if (lane == 0 && active) {
       last_E[b] = E;
       if (improved) {
         best_E[b] = E;
         best_t[b] = t;
       }
+      if (conv_step && t <= T) conv_update(conv_ring, conv_init, conv_step, conv_count, B, b, t, E);
     }
     if (KIND == kSpinBits) {
       // bit-packed spins are copied by track_bits_copy_kernel
@@ -318,7 +324,7 @@ int check_params(ising_ctx* ctx, const ising_ds_params* p) {
   if (!(p->beta1 >= 0 && p->beta1 < 1) || !(p->beta2 >= 0 && p->beta2 < 1))
     return fail(ctx, ISING_EINVAL, "beta1 and beta2 must lie in [0, 1)");
   if (!(p->eps > 0) || !std::isfinite(p->eps)) return fail(ctx, ISING_EINVAL, "eps must be > 0");
-  if (p->flags & ~(ISING_DS_PROFILE | ISING_DS_STREAMING | ISING_DS_NO_AUTOTUNE))
+  if (p->flags & ~(ISING_DS_PROFILE | ISING_DS_STREAMING | ISING_DS_NO_AUTOTUNE | ISING_DS_CONVERGE))
     return fail(ctx, ISING_EINVAL, "unknown flags");
   if (p->precision < ISING_PREC_AUTO || p->precision > ISING_PREC_FP8)
     return fail(ctx, ISING_EINVAL, "unknown precision %d", p->precision);
@@ -333,13 +339,16 @@ int track_step(ising_ds* ds) {
   const int pslot = (int)((ds->t + 1) % 2);
   const double chs = ds->inst.ch * std::ldexp(1.0, -ds->h_shift);
   int grid = (int)std::min<int64_t>((ds->B + 7) / 8, (int64_t)ctx->sm_count * 4);
+  const bool conv = ds->conv.p != nullptr;
 #define ISING_TRACK(KIND)                                                                    \
   track_kernel<KIND><<<grid, 256, 0, ctx->stream>>>(                                         \
       ds->n, ds->B, ds->Bp, ds->ld, ds->mtiles, ds->int_energy, ds->inst.cq, chs,            \
       ds->qpart[pslot].as<long long>(), ds->hpart[pslot].as<long long>(),                    \
       ds->epart[pslot].as<float>(), ds->spins[slot].p, ds->best_E.as<double>(),              \
       ds->best_t.as<long long>(), ds->best_s.as<int8_t>(), ds->last_E.as<double>(),          \
-      ds->counters.as<long long>(), ds->bs_ld, ds->improved.as<uint8_t>())
+      ds->counters.as<long long>(), ds->bs_ld, ds->improved.as<uint8_t>(), ds->T,             \
+      conv ? ds->conv_ring() : nullptr, conv ? ds->conv_init() : nullptr,                   \
+      conv ? ds->conv_step() : nullptr, conv ? ds->conv_count() : nullptr)
   switch (ds->spin_kind) {
     case kSpinF32: ISING_TRACK(kSpinF32); break;
     case kSpinBF16: ISING_TRACK(kSpinBF16); break;
@@ -431,6 +440,10 @@ int common_alloc(ising_ds* ds) {
   ISING_TRY(dev_alloc(ctx, ds->best_s, (size_t)B * ds->bs_ld));
   ISING_TRY(dev_alloc(ctx, ds->last_E, B * 8));
   ISING_TRY(dev_alloc(ctx, ds->improved, B));
+  if (ds->p.flags & ISING_DS_CONVERGE) {
+    ISING_TRY(dev_alloc(ctx, ds->conv, (size_t)(7 * B + 1) * 8));
+    ISING_CUDA(ctx, cudaMemsetAsync(ds->conv.p, 0, ds->conv.bytes, ctx->stream));
+  }
   ISING_TRY(dev_alloc(ctx, ds->counters, 16));
   ISING_TRY(dev_alloc(ctx, ds->scratch, 64));
   fill_double<<<grid1d(ctx, B), 256, 0, ctx->stream>>>(ds->best_E.as<double>(), B, INFINITY);
@@ -819,18 +832,46 @@ int ising::ds_advance(ising_ds* ds, int64_t todo) {
   return ISING_OK;
 }
 
+// With the convergence rule: whether every restart has stopped (reads the
+// device count; synchronises the stream).
+int ising::ds_conv_check(ising_ds* ds) {
+  if (!ds->conv.p || ds->conv_all) return ISING_OK;
+  unsigned long long c = 0;
+  ISING_CUDA(ds->ctx, cudaMemcpyAsync(&c, ds->conv_count(), 8, cudaMemcpyDeviceToHost, ds->ctx->stream));
+  ISING_CUDA(ds->ctx, cudaStreamSynchronize(ds->ctx->stream));
+  if ((int64_t)c >= ds->B) ds->conv_all = true;
+  return ISING_OK;
+}
+
+namespace {
+constexpr int64_t kConvChunk = 48;  // steps between checks of the convergence count
+
+// ds_advance, in chunks with a check of the convergence count after each
+// when the rule is on; stops once every restart has stopped.
+int advance_checked(ising_ds* ds, int64_t todo) {
+  if (!ds->conv.p) return ds_advance(ds, todo);
+  while (todo > 0 && !ds->conv_all) {
+    const int64_t k = std::min(todo, kConvChunk);
+    ISING_TRY(ds_advance(ds, k));
+    todo -= k;
+    ISING_TRY(ds_conv_check(ds));
+  }
+  return ISING_OK;
+}
+}  // namespace
+
 extern "C" int ising_ds_run(ising_ds* ds, int64_t steps) {
   if (!ds) return ISING_EINVAL;
   ising_ctx* ctx = ds->ctx;
   if (steps < 0) return fail(ctx, ISING_EINVAL, "steps must be >= 0");
   if (ds->finished) return fail(ctx, ISING_EINVAL, "session already finished");
   int64_t todo = std::min(steps, ds->T - ds->t);
-  if (todo <= 0) return ISING_OK;
+  if (todo <= 0 || ds->conv_all) return ISING_OK;
   cudaEvent_t e0, e1;
   ISING_CUDA(ctx, cudaEventCreate(&e0));
   ISING_CUDA(ctx, cudaEventCreate(&e1));
   ISING_CUDA(ctx, cudaEventRecord(e0, ctx->stream));
-  int rc = ds_advance(ds, todo);
+  int rc = advance_checked(ds, todo);
   if (rc != ISING_OK) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -856,8 +897,11 @@ extern "C" int ising_ds_finish(ising_ds* ds) {
   ising_ctx* ctx = ds->ctx;
   ISING_TRY(ising_ds_run(ds, ds->T - ds->t));
   // energy of S_{T+1}: the step kernels in energy-only mode, then tracking
-  ISING_TRY(path_step(ds, false));
-  ISING_TRY(track_step(ds));
+  // (nothing to evaluate once every restart has stopped)
+  if (!ds->conv_all) {
+    ISING_TRY(path_step(ds, false));
+    ISING_TRY(track_step(ds));
+  }
   ISING_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   if (ds->path == ISING_PATH_TC) ISING_TRY(tc_error(ds));
   ISING_TRY(select_best(ds));
@@ -998,6 +1042,24 @@ extern "C" int ising_ds_last_energies(ising_ds* ds, double* E, int mem) {
   if (!E) return fail(ds->ctx, ISING_EINVAL, "E is NULL");
   ISING_TRY(copy_out(ds->ctx, E, ds->last_E.p, ds->B * 8, mem));
   ISING_CUDA(ds->ctx, cudaStreamSynchronize(ds->ctx->stream));
+  return ISING_OK;
+}
+
+extern "C" int ising_ds_convergence(ising_ds* ds, int64_t* step, int mem) {
+  if (!ds) return ISING_EINVAL;
+  ising_ctx* ctx = ds->ctx;
+  if (mem != ISING_MEM_HOST && mem != ISING_MEM_DEVICE) return fail(ctx, ISING_EINVAL, "bad mem");
+  if (!step) return fail(ctx, ISING_EINVAL, "step is NULL");
+  const cudaMemcpyKind kind = mem == ISING_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  if (ds->conv.p) {
+    ISING_CUDA(ctx, cudaMemcpyAsync(step, ds->conv_step(), ds->B * 8, kind, ctx->stream));
+  } else if (mem == ISING_MEM_HOST) {
+    ISING_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    std::memset(step, 0, ds->B * 8);
+  } else {
+    ISING_CUDA(ctx, cudaMemsetAsync(step, 0, ds->B * 8, ctx->stream));
+  }
+  ISING_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   return ISING_OK;
 }
 

@@ -55,6 +55,32 @@ __device__ __forceinline__ float adam_update(const StepConsts& k, float c1, floa
 // the gradient cos(theta) F is within 4e-7 |F| of the exact one.
 __device__ __forceinline__ float cos_proj(float th) { return __cosf(th); }
 
+// Convergence rule of Sec. IV-B on the energies of restart b (window 5,
+// tolerance 0.005; see ISING_DS_CONVERGE): records E_t, and at t >= 5
+// stops the restart when the window's spread is within the tolerance.
+// Returns true when the restart stops at this step.
+constexpr double kConvTol = 0.005;
+__device__ __forceinline__ bool conv_update(double* ring, double* init, long long* step,
+                                            unsigned long long* count, int64_t B, int64_t b,
+                                            long long t, double E) {
+  ring[((t - 1) % 5) * B + b] = E;
+  if (t == 1) init[b] = E;
+  if (t < 5) return false;
+  double mx = ring[b], mn = ring[b];
+#pragma unroll
+  for (int k = 1; k < 5; ++k) {
+    const double x = ring[k * B + b];
+    mx = fmax(mx, x);
+    mn = fmin(mn, x);
+  }
+  if (mx - mn <= kConvTol * fabs(E - init[b])) {
+    step[b] = t;
+    atomicAdd(count, 1ull);
+    return true;
+  }
+  return false;
+}
+
 enum SpinKind { kSpinF32 = 0, kSpinBF16 = 1, kSpinBits = 2, kSpinE4M3 = 3 };
 
 // Sign bit of each byte of four E4M3 spins -> four int8 +1 / -1.
@@ -130,6 +156,14 @@ struct ising_ds {
   ising::DevMem hint;      // int32 field * 2^h_shift (n)
   ising::DevMem best_E, best_t, best_s, last_E;
   ising::DevMem improved;  // per restart: improved at the last tracked step (bit-packed path)
+  // convergence rule (ISING_DS_CONVERGE): [5][B] ring of energies, [B] E_1,
+  // [B] stopping step, and the count of stopped restarts
+  ising::DevMem conv;
+  bool conv_all = false;   // every restart has stopped
+  double* conv_ring() const { return conv.as<double>(); }
+  double* conv_init() const { return conv.as<double>() + 5 * B; }
+  long long* conv_step() const { return reinterpret_cast<long long*>(conv.as<double>() + 6 * B); }
+  unsigned long long* conv_count() const { return reinterpret_cast<unsigned long long*>(conv.as<double>() + 7 * B); }
   int64_t bs_ld = 0;       // row pitch of best_s (n rounded up to 16)
   ising::DevMem counters;  // int64 [0] = steps done, [1] = done-block counter
   ising::DevMem bias;      // float2 [T + 2]: 1/(1-b1^t), 1/(1-b2^t)
@@ -180,6 +214,7 @@ int tc_trace(ising_ds* ds, uint64_t* out, int64_t cap, int64_t* count);
 void tc_release(ising_ds* ds);
 
 // Shared session services (ds.cu).
+int ds_conv_check(ising_ds* ds);
 int ds_advance(ising_ds* ds, int64_t todo);  // queue steps without waiting
 int ds_create_impl(ising_ctx* ctx, const ising_instance* inst, const ising_ds_params* p,
                    ising_ds** out, bool validate);

@@ -489,6 +489,11 @@ struct TcResArgs {
   int64_t bs_ld;       // row pitch of best_s
   double cq, chs;      // E = cq * Q + chs * H (integer mode)
   int rows;            // energy-partial rows (4 per m-tile)
+  int64_t T;           // steps of the run (convergence rule: steps <= T feed it)
+  double* conv_ring;   // convergence rule state, or null (see conv_update)
+  double* conv_init;
+  long long* conv_step;
+  unsigned long long* conv_count;
   int jres;            // J tiles (k-blocks) kept in shared memory for the whole run
   int nst;             // pipeline stages after them
   uint32_t bars;       // shared-memory offset of the barrier block
@@ -500,7 +505,8 @@ struct TcResArgs {
 // l + 32, ... starting from 0, then combines the lanes by an xor tree over
 // lane bits 4, 3, 2, 1, 0): here one lane forms the 32 lane sums and adds
 // them in that tree's order. The spins of the improved restarts are then
-// copied one restart at a time by the whole warp.
+// copied one restart at a time by the whole warp. With the convergence rule a
+// stopped restart is left alone, and steps t <= T feed the rule.
 template <bool INT_E, bool FP8>
 __device__ __forceinline__ void track_warp(const TcResArgs& R, long long t, int64_t b0, int64_t b1,
                                            int lane) {
@@ -511,7 +517,8 @@ __device__ __forceinline__ void track_warp(const TcResArgs& R, long long t, int6
     const int64_t b = bb + lane;
     const bool ok = b < b1;
     bool improved = false;
-    if (ok) {
+    const bool active = ok && (R.conv_step == nullptr || R.conv_step[b] == 0);
+    if (active) {
       const double best = R.best_E[b];
       double E;
       if (INT_E) {
@@ -542,6 +549,8 @@ __device__ __forceinline__ void track_warp(const TcResArgs& R, long long t, int6
         R.best_E[b] = E;
         R.best_t[b] = t;
       }
+      if (R.conv_step && t <= R.T)
+        conv_update(R.conv_ring, R.conv_init, R.conv_step, R.conv_count, P.B, b, t, E);
     }
     for (unsigned int m = __ballot_sync(0xffffffffu, improved); m; m &= m - 1) {
       const int64_t br = bb + __ffs(m) - 1;
@@ -1398,6 +1407,12 @@ int tc_run_resident(ising_ds* ds, int64_t steps) {
   r.rows = ds->mtiles;
   r.slice = ceil_div_i(st->gn, ceil_div_i(ds->n, kBM));
   r.jres = st->jres;
+  r.T = ds->T;
+  const bool conv = ds->conv.p != nullptr;
+  r.conv_ring = conv ? ds->conv_ring() : nullptr;
+  r.conv_init = conv ? ds->conv_init() : nullptr;
+  r.conv_step = conv ? ds->conv_step() : nullptr;
+  r.conv_count = conv ? ds->conv_count() : nullptr;
   r.nst = st->nst;
   r.bars = st->bars;
   return st->gn == 64 ? resident_launch_bn<64>(ds, st, r) : resident_launch_bn<32>(ds, st, r);

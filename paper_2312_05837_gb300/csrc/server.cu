@@ -197,11 +197,18 @@ void worker_loop(ising_server* srv) {
       }
     }
     // 3. wait for the round
-    for (Request* r : act) cudaStreamSynchronize(srv->slots[r->slot]->stream);
+    for (Request* r : act) {
+      cudaStreamSynchronize(srv->slots[r->slot]->stream);
+      if (r->status == ISING_OK && r->ds) {
+        int rc = ds_conv_check(r->ds);  // convergence rule: have all restarts stopped?
+        if (rc != ISING_OK) r->status = rc;
+      }
+    }
     // 4. finish what is done
     std::vector<Request*> finished;
     for (Request* r : act) {
-      const bool steps_done = r->status != ISING_OK || !r->ds || r->ds->t >= r->ds->T;
+      const bool steps_done =
+          r->status != ISING_OK || !r->ds || r->ds->t >= r->ds->T || r->ds->conv_all;
       if (!steps_done) continue;
       if (r->status == ISING_OK) {
         int rc = finish_request(srv, r);

@@ -8,6 +8,7 @@ import pytest
 import synth
 from oracle import brute_force, ising, rng
 from oracle import domain_selection as ds
+from oracle import domain_selection as ods
 
 
 def test_splitmix64_published_outputs():
@@ -123,3 +124,45 @@ def test_reaches_brute_force_ground_states(n):
         assert r["best_energy"] >= e0 - 1e-9
         hits += abs(r["best_energy"] - e0) < 1e-9
     assert hits >= 3
+
+
+def test_convergence_rule_closed_form_without_motion():
+    """lr = 0 leaves theta where it starts: every restart's energy is the same
+    at every step, the spread is 0 <= 0.005 |E_t - E_1| = 0, so all restarts
+    stop at the fifth step and the run ends there (Sec. IV-B rule)."""
+    inst = synth.er_dense(40, 2, p=0.2, weights="pm1")
+    r = ods.select_domain(inst, ods.Params(restarts=6, steps=50, lr=0.0, seed=3), converge=True,
+                          trace=True)
+    assert (r["conv_step"] == ods.CONV_WINDOW).all() and r["steps_done"] == ods.CONV_WINDOW
+    np.testing.assert_array_equal(r["restart_best_step"], 1)
+    np.testing.assert_array_equal(r["restart_best_energy"], r["trace"][0])
+
+
+@pytest.mark.parametrize("lr,h", [(0.05, None), (6.0, "int")])
+def test_convergence_steps_follow_the_energy_trace(lr, h):
+    """Against the trace of the same run without the rule (the dynamics do not
+    depend on it): each restart stops at the first step where the window
+    spread is within the tolerance, its best is the trace minimum up to
+    there, and restarts that never stop keep the plain run's best."""
+    inst = synth.random_sparse_instance(30, 5, p=0.3, kind="int", h=h or "none", layout="dense")
+    p = ods.Params(restarts=12, steps=120, lr=lr, seed=7)
+    plain = ods.select_domain(inst, p, trace=True)
+    conv = ods.select_domain(inst, p, converge=True)
+    tr = plain["trace"][:-1]  # E_1 .. E_T
+    stops = 0
+    for b in range(p.restarts):
+        t_star = 0
+        for t in range(ods.CONV_WINDOW, p.steps + 1):
+            w = tr[t - ods.CONV_WINDOW:t, b]
+            if w.max() - w.min() <= ods.CONV_TOL * abs(tr[t - 1, b] - tr[0, b]):
+                t_star = t
+                break
+        assert conv["conv_step"][b] == t_star
+        if t_star:
+            stops += 1
+            assert conv["restart_best_energy"][b] == tr[:t_star, b].min()
+            assert conv["restart_best_step"][b] == int(np.argmin(tr[:t_star, b])) + 1
+            assert conv["last_energy"][b] == tr[t_star - 1, b]
+        else:
+            assert conv["restart_best_energy"][b] == plain["restart_best_energy"][b]
+    assert stops > 0
