@@ -439,13 +439,15 @@ def main():
     avg_ms = st["kernel_ms"] / max(st["kernel_launches"], 1)
     pk = peaks()
     path = last["path"]
+    # the profiled session runs the full instance (no pruning): its size counts
+    n_prof = inst.n
     if path == 2:  # sparse: HBM bound, 24 B of theta/m/v traffic per update + spin bits
-        alg = n_red * ((B + 127) // 128 * 128) * (24 + 0.25)
+        alg = n_prof * ((B + 127) // 128 * 128) * (24 + 0.25)
         roof = {"bound": "hbm", "achieved": alg / (avg_ms / 1e3) / 1e9, "peak": pk["hbm_gbs"],
                 "unit": "GB/s"}
         kname, ksrc = "sparse_step_kernel", "paper_2312_05837_gb300/csrc/ds_sparse.cu"
     elif path == 1:  # tensor cores: 2 N^2 B flop per step
-        alg = 2.0 * n_red * n_red * B
+        alg = 2.0 * n_prof * n_prof * B
         fp8 = st["precision"] == 4
         # E4M3 operands: the measured BF16 rate times the nominal FP8/BF16 ratio (2)
         peak = pk["bf16_tflops_sustained"] * (2.0 if fp8 else 1.0)
@@ -460,7 +462,7 @@ def main():
         kname = "tc_resident_kernel" if st["resident"] else "tc_step_kernel"
         ksrc = "paper_2312_05837_gb300/csrc/ds_tc.cu"
     else:  # plain FP32 FMA on the CUDA cores: 2 N^2 B flop per step
-        alg = 2.0 * n_red * n_red * B
+        alg = 2.0 * n_prof * n_prof * B
         sms = torch.cuda.get_device_properties(local).multi_processor_count
         fp32_peak = sms * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
         roof = {"bound": "alu", "achieved": alg / (avg_ms / 1e3) / 1e12, "peak": fp32_peak,

@@ -15,12 +15,12 @@
 namespace ising {
 namespace {
 
-// Q = restarts per warp pass / 128. Q = 1 keeps about 70 registers (three
-// blocks per SM); Q = 2 gathers each neighbour's spins once for 256 restarts
-// (two blocks per SM). Both visit rows, lanes and partials in the same order,
+// Q = restarts per warp pass / 128. Q = 1 fits 64 registers (four blocks
+// per SM); Q = 2 gathers each neighbour's spins once for 256 restarts (two
+// blocks per SM). Both visit rows, lanes and partials in the same order,
 // so their results are identical bit for bit.
 template <int Q, int MODE, bool INT_E, bool VAL_I8>
-__global__ void __launch_bounds__(256, Q == 1 ? 3 : 2) sparse_step_kernel(
+__global__ void __launch_bounds__(256, Q == 1 ? 4 : 2) sparse_step_kernel(
     int64_t n, int64_t Bp, int64_t rows_per_block, const int32_t* __restrict__ rowptr,
     const int32_t* __restrict__ col, const void* __restrict__ val,
     const uint32_t* __restrict__ bits_in, uint32_t* __restrict__ bits_out,
@@ -182,9 +182,13 @@ __global__ void csr_values_kernel(const void* J, int dt, int64_t nnz, bool to_i8
   }
 }
 
+// Row blocks: one wave of the Q = 1 kernel (four blocks per SM over the
+// 128-restart slices), at least 64 rows each; a warp then streams its rows
+// back to back with the next row's state in flight.
 int64_t sparse_rows_per_block(ising_ds* ds) {
-  const int64_t target = (int64_t)ds->ctx->sm_count * 4;
-  int64_t nb = std::min<int64_t>((ds->n + 63) / 64, std::max<int64_t>(target, 1));
+  const int64_t slices = std::max<int64_t>(ds->Bp / 128, 1);
+  const int64_t target = std::max<int64_t>((int64_t)ds->ctx->sm_count * 4 / slices, 1);
+  const int64_t nb = std::min<int64_t>((ds->n + 63) / 64, target);
   return (ds->n + nb - 1) / nb;
 }
 
