@@ -144,6 +144,15 @@ typedef struct ising_ds_params {
  * the final evaluation (step T+1) applies to restarts still running after T.
  * Per-restart stopping steps: ising_ds_convergence. */
 #define ISING_DS_CONVERGE 8
+/* params.flags: the relaxed coupling product G = J sin(theta) in the update
+ * (the loss field F = cQ G + cH h - mu s and the gradient cos(theta) F keep
+ * their form; s and the energies stay those of the rounded spins), instead
+ * of the paper's G = J s of the local optimum s (Sec. III-B). Dense paths
+ * evaluate the energies with a second product on s each step; the tensor
+ * cores take x in BF16 (so G is within 2^-8 sum_j |J_ij| of the exact
+ * product; E4M3 operands and the resident form are not used), the CUDA-core
+ * and sparse paths in FP32. */
+#define ISING_DS_RELAXED 16
 
 typedef struct ising_ds_stats {
   int64_t best_restart;     /* restart holding the overall best */

@@ -45,6 +45,10 @@ class Params:
     beta2: float = 0.999
     eps: float = 1e-8
     seed: int = 0
+    # "rounded": G = J s (the paper's loss field on the local optimum s of the
+    # domain); "relaxed": G = J sin(theta), the coupling product on the
+    # relaxed spins, with the same F = cQ G + cH h - mu s and g = cos(theta) F
+    grad_mode: str = "rounded"
 
 
 def round_spins(theta: np.ndarray) -> np.ndarray:
@@ -82,6 +86,12 @@ def step(J, h, cq, ch, p: Params, theta, m, v, t: int) -> StepResult:
     s = round_spins(theta)
     F, G = loss_field(J, h, cq, ch, p.mu, s)
     E = cq * np.sum(s * G, axis=0) + ch * (h @ s)
+    if p.grad_mode == "relaxed":
+        # the product on the relaxed spins drives the update; E stays that of s
+        G = J @ np.sin(theta)
+        F = cq * G + ch * h[:, None] - p.mu * s
+    elif p.grad_mode != "rounded":
+        raise ValueError(p.grad_mode)
     g = np.cos(theta) * F
     m = p.beta1 * m + (1.0 - p.beta1) * g
     v = p.beta2 * v + (1.0 - p.beta2) * g * g

@@ -25,6 +25,7 @@ DS_PROFILE = 1
 DS_STREAMING = 2
 DS_NO_AUTOTUNE = 4
 DS_CONVERGE = 8
+DS_RELAXED = 16
 
 
 class Instance(ctypes.Structure):

@@ -155,7 +155,7 @@ def make_instance(inst):
 
 def params(restarts, steps, lr=6.0, mu=0.0, beta1=0.9, beta2=0.999, eps=1e-8, seed=0,
            precision="auto", profile=False, streaming=False, autotune=True,
-           converge=False) -> L.DSParams:
+           converge=False, relaxed=False) -> L.DSParams:
     p = L.DSParams()
     p.restarts = int(restarts)
     p.steps = int(steps)
@@ -163,7 +163,8 @@ def params(restarts, steps, lr=6.0, mu=0.0, beta1=0.9, beta2=0.999, eps=1e-8, se
     p.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
     p.precision = _PREC[precision] if isinstance(precision, str) else int(precision)
     p.flags = ((L.DS_PROFILE if profile else 0) | (L.DS_STREAMING if streaming else 0) |
-               (0 if autotune else L.DS_NO_AUTOTUNE) | (L.DS_CONVERGE if converge else 0))
+               (0 if autotune else L.DS_NO_AUTOTUNE) | (L.DS_CONVERGE if converge else 0) |
+               (L.DS_RELAXED if relaxed else 0))
     return p
 
 

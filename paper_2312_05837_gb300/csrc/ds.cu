@@ -260,6 +260,20 @@ __global__ void spins_from_theta_dense(int64_t n, int64_t Bp, int64_t ld,
   }
 }
 
+// Relaxed spins x = sin(theta) of the state (any layout; `ld` > 0 marks the
+// restart-major dense layout, whose padding columns i >= n stay 0) as FP32
+// or BF16.
+__global__ void x_from_theta(int64_t count, int64_t n, int64_t ld, bool bf16,
+                             const float* __restrict__ th, void* __restrict__ x) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const bool pad = ld > 0 && e % ld >= n;
+    const float v = pad ? 0.f : sin_proj(th[e]);
+    if (bf16) static_cast<__nv_bfloat16*>(x)[e] = __float2bfloat16(v);
+    else static_cast<float*>(x)[e] = v;
+  }
+}
+
 __global__ void spins_from_theta_bits(int64_t n, int64_t Bp, const float* __restrict__ th,
                                       uint32_t* __restrict__ bits) {
   const int64_t words = Bp / 32;
@@ -324,7 +338,8 @@ int check_params(ising_ctx* ctx, const ising_ds_params* p) {
   if (!(p->beta1 >= 0 && p->beta1 < 1) || !(p->beta2 >= 0 && p->beta2 < 1))
     return fail(ctx, ISING_EINVAL, "beta1 and beta2 must lie in [0, 1)");
   if (!(p->eps > 0) || !std::isfinite(p->eps)) return fail(ctx, ISING_EINVAL, "eps must be > 0");
-  if (p->flags & ~(ISING_DS_PROFILE | ISING_DS_STREAMING | ISING_DS_NO_AUTOTUNE | ISING_DS_CONVERGE))
+  if (p->flags & ~(ISING_DS_PROFILE | ISING_DS_STREAMING | ISING_DS_NO_AUTOTUNE |
+                   ISING_DS_CONVERGE | ISING_DS_RELAXED))
     return fail(ctx, ISING_EINVAL, "unknown flags");
   if (p->precision < ISING_PREC_AUTO || p->precision > ISING_PREC_FP8)
     return fail(ctx, ISING_EINVAL, "unknown precision %d", p->precision);
@@ -386,6 +401,18 @@ int export_spins_int8(ising_ds* ds, int slot, int8_t* out) {
 
 namespace {
 
+// x = sin(theta) of the current state into relaxed slot `slot`.
+int derive_x(ising_ds* ds, int slot) {
+  ising_ctx* ctx = ds->ctx;
+  const bool dense = ds->path != ISING_PATH_SPARSE;
+  const int64_t count = dense ? ds->Bp * ds->ld : ds->n * ds->Bp;
+  x_from_theta<<<grid1d(ctx, count), 256, 0, ctx->stream>>>(
+      count, ds->n, dense ? ds->ld : 0, ds->path == ISING_PATH_TC, ds->theta.as<float>(),
+      ds->xbuf[slot].p);
+  ISING_CUDA(ctx, cudaGetLastError());
+  return ISING_OK;
+}
+
 int init_state(ising_ds* ds) {
   ising_ctx* ctx = ds->ctx;
   const bool spin_major = ds->path == ISING_PATH_SPARSE;
@@ -422,6 +449,14 @@ int init_state(ising_ds* ds) {
       break;
   }
   ISING_CUDA(ctx, cudaGetLastError());
+  if (ds->relaxed()) {
+    const size_t xb = (size_t)elems * (ds->path == ISING_PATH_TC ? 2 : 4);
+    for (auto& x : ds->xbuf) {
+      ISING_TRY(dev_alloc(ctx, x, xb));
+      ISING_CUDA(ctx, cudaMemsetAsync(x.p, 0, xb, ctx->stream));
+    }
+    ISING_TRY(derive_x(ds, 1));  // x_1 = sin(theta_0)
+  }
   return ISING_OK;
 }
 
@@ -499,6 +534,19 @@ int setup_field(ising_ds* ds) {
 }
 
 int path_step_raw(ising_ds* ds, bool update) {
+  if (update && ds->relaxed()) {
+    // relaxed product: the sparse kernel gathers both spin forms at once; the
+    // dense paths take the energies of the rounded spins in a pass of their own
+    switch (ds->path) {
+      case ISING_PATH_SPARSE: return sparse_step(ds, kModeRelaxed, nullptr);
+      case ISING_PATH_PLAIN:
+        ISING_TRY(plain_step(ds, kModeEnergy, nullptr));
+        return plain_step(ds, kModeRelaxed, nullptr);
+      default:
+        ISING_TRY(tc_step(ds, kModeEnergy, nullptr));
+        return tc_step(ds, kModeRelaxed, nullptr);
+    }
+  }
   const int mode = update ? kModeUpdate : kModeEnergy;
   switch (ds->path) {
     case ISING_PATH_PLAIN: return plain_step(ds, mode, nullptr);
@@ -995,6 +1043,7 @@ extern "C" int ising_ds_import_state(ising_ds* ds, const float* theta, const flo
     }
   }
   ISING_CUDA(ctx, cudaGetLastError());
+  if (ds->relaxed()) ISING_TRY(derive_x(ds, (int)((t + 1) % 2)));
   ISING_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   return ISING_OK;
 }

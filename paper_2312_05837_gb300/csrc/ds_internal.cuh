@@ -50,6 +50,10 @@ __device__ __forceinline__ float adam_update(const StepConsts& k, float c1, floa
   return wrap_angle(th);
 }
 
+// sin(theta) on [-pi, pi]: the hardware approximation (absolute error at most
+// 2^-21.41 there), for the relaxed spins x = sin(theta) of ISING_DS_RELAXED.
+__device__ __forceinline__ float sin_proj(float th) { return __sinf(th); }
+
 // cos(theta) for theta in [-pi, pi] (the projection keeps it there): the
 // hardware approximation, absolute error at most 2^-21.41 on that range, so
 // the gradient cos(theta) F is within 4e-7 |F| of the exact one.
@@ -129,7 +133,11 @@ __device__ __forceinline__ void copy_spin_row_dense(int8_t* dst, const void* spi
 
 // What a step launch does: the full update, only the energies of the input
 // spins (the final evaluation), or only the coupling product G = J s.
-enum StepMode { kModeUpdate = 0, kModeEnergy = 1, kModeCoupling = 2 };
+// kModeRelaxed: the update with the coupling product taken on the relaxed
+// spins x = sin(theta) (ISING_DS_RELAXED); energies then come from a
+// kModeEnergy pass on the rounded spins (dense paths) or from the rounded
+// spins gathered alongside (sparse path).
+enum StepMode { kModeUpdate = 0, kModeEnergy = 1, kModeCoupling = 2, kModeRelaxed = 3 };
 
 }  // namespace ising
 
@@ -160,6 +168,10 @@ struct ising_ds {
   // [B] stopping step, and the count of stopped restarts
   ising::DevMem conv;
   bool conv_all = false;   // every restart has stopped
+  // relaxed product (ISING_DS_RELAXED): x_t = sin(theta) in slot t % 2, laid
+  // out like the state (FP32; BF16 on the tensor-core path)
+  ising::DevMem xbuf[2];
+  bool relaxed() const { return (p.flags & ISING_DS_RELAXED) != 0; }
   double* conv_ring() const { return conv.as<double>(); }
   double* conv_init() const { return conv.as<double>() + 5 * B; }
   long long* conv_step() const { return reinterpret_cast<long long*>(conv.as<double>() + 6 * B); }

@@ -3,7 +3,10 @@
 // per block, K chunks of 16 staged in shared memory, 8 x 8 outputs per
 // thread); the epilogue does, per element: loss field F = cQ G + cH h - mu s,
 // gradient g = cos(theta) F, Adam, projection, rounding of the new spin, and
-// the energy partials of the input spins for this block's 128 rows.
+// the energy partials of the input spins for this block's 128 rows. In the
+// relaxed mode the product runs on x = sin(theta) (X), the epilogue takes the
+// rounded spins from Sr, writes x_{t+1} and leaves the energies to a
+// kModeEnergy pass.
 #include "ds_internal.cuh"
 
 namespace ising {
@@ -20,12 +23,14 @@ __global__ void to_float_kernel(const void* J, int dt, int64_t count, float* out
 template <int MODE, bool INT_E>
 __global__ void __launch_bounds__(256) plain_step_kernel(
     const float* __restrict__ J, int64_t n, int64_t B, const float* __restrict__ S,
+    const float* __restrict__ Sr, float* __restrict__ Xnext,
     float* __restrict__ Snext, float* __restrict__ theta, float* __restrict__ m,
     float* __restrict__ v, const float* __restrict__ hf, const int32_t* __restrict__ hint,
     StepConsts k, const float2* __restrict__ bias, const long long* __restrict__ counters,
     long long* __restrict__ qpart, long long* __restrict__ hpart, float* __restrict__ epart,
     float* __restrict__ Gout) {
-  constexpr bool UPDATE = MODE == kModeUpdate;
+  constexpr bool UPDATE = MODE == kModeUpdate || MODE == kModeRelaxed;
+  constexpr bool PARTIALS = MODE == kModeUpdate || MODE == kModeEnergy;
   __shared__ float As[BK][BM + 4];
   __shared__ float Bs[BK][BN + 4];
   const int tid = threadIdx.x;
@@ -80,7 +85,7 @@ __global__ void __launch_bounds__(256) plain_step_kernel(
           Gout[idx] = G;
           continue;
         }
-        const float s = S[idx];
+        const float s = Sr[idx];
         const float h = hf[i];
         if (INT_E) {
           qs += (int)s * __float2int_rn(G);
@@ -98,6 +103,7 @@ __global__ void __launch_bounds__(256) plain_step_kernel(
           m[idx] = mm;
           v[idx] = vv;
           Snext[idx] = sin_nonneg(th) ? 1.f : -1.f;
+          if (MODE == kModeRelaxed) Xnext[idx] = sin_proj(th);
         }
       }
     }
@@ -111,7 +117,7 @@ __global__ void __launch_bounds__(256) plain_step_kernel(
         es += __shfl_xor_sync(0xffffffffu, es, o);
       }
     }
-    if (MODE != kModeCoupling && tx == 0 && b < B) {
+    if (PARTIALS && tx == 0 && b < B) {
       const int64_t o = (int64_t)blockIdx.x * B + b;
       if (INT_E) {
         qpart[o] = qs;
@@ -144,11 +150,15 @@ int plain_step(ising_ds* ds, int mode, float* Gout) {
   const int64_t t = ds->t + 1;
   const float* S = ds->spins[t % 3].as<float>();
   float* Sn = ds->spins[(t + 1) % 3].as<float>();
+  // relaxed mode: the product's operand is x_t, the rounded spins come along
+  const bool rel = mode == kModeRelaxed;
+  const float* X = rel ? ds->xbuf[t % 2].as<float>() : S;
+  float* Xn = rel ? ds->xbuf[(t + 1) % 2].as<float>() : nullptr;
   const int ps = (int)(t % 2);
   dim3 grid(ceil_div_i(ds->n, BM), ceil_div_i(ds->B, BN));
 #define ISING_PLAIN(U, I)                                                                     \
   plain_step_kernel<U, I><<<grid, 256, 0, ctx->stream>>>(                                     \
-      ds->Jf.as<float>(), ds->n, ds->B, S, Sn, ds->theta.as<float>(), ds->m.as<float>(),      \
+      ds->Jf.as<float>(), ds->n, ds->B, X, S, Xn, Sn, ds->theta.as<float>(), ds->m.as<float>(),\
       ds->v.as<float>(), ds->hf.as<float>(), ds->hint.as<int32_t>(), ds->k,                   \
       ds->bias.as<float2>(), ds->counters.as<long long>(), ds->qpart[ps].as<long long>(),     \
       ds->hpart[ps].as<long long>(), ds->epart[ps].as<float>(), Gout)
@@ -156,6 +166,8 @@ int plain_step(ising_ds* ds, int mode, float* Gout) {
     if (ds->int_energy) ISING_PLAIN(kModeUpdate, true); else ISING_PLAIN(kModeUpdate, false);
   } else if (mode == kModeEnergy) {
     if (ds->int_energy) ISING_PLAIN(kModeEnergy, true); else ISING_PLAIN(kModeEnergy, false);
+  } else if (rel) {
+    if (ds->int_energy) ISING_PLAIN(kModeRelaxed, true); else ISING_PLAIN(kModeRelaxed, false);
   } else {
     ISING_PLAIN(kModeCoupling, true);
   }

@@ -7,7 +7,10 @@
 // access is a coalesced float4 and a neighbour's spins are one broadcast word
 // per group of 8 lanes. The per-row epilogue is the same as the dense paths: F = cQ G +
 // cH h - mu s, g = cos(theta) F, Adam, projection, new spin bit; energy
-// partials of the input spins are summed per block in warp order.
+// partials of the input spins are summed per block in warp order. In the
+// relaxed mode each neighbour also contributes J_ij x_j with x = sin(theta)
+// from the FP32 slot x_t ([n][Bp], float4 per lane): that product drives the
+// update, the bit product the energies, and x_{t+1} is written out.
 #include "ds_internal.cuh"
 
 #include <algorithm>
@@ -20,7 +23,7 @@ namespace {
 // blocks per SM). Both visit rows, lanes and partials in the same order,
 // so their results are identical bit for bit.
 template <int Q, int MODE, bool INT_E, bool VAL_I8>
-__global__ void __launch_bounds__(256, Q == 1 ? 4 : 2) sparse_step_kernel(
+__global__ void __launch_bounds__(256, Q == 1 ? (MODE == kModeRelaxed ? 3 : 4) : 2) sparse_step_kernel(
     int64_t n, int64_t Bp, int64_t rows_per_block, const int32_t* __restrict__ rowptr,
     const int32_t* __restrict__ col, const void* __restrict__ val,
     const uint32_t* __restrict__ bits_in, uint32_t* __restrict__ bits_out,
@@ -28,8 +31,9 @@ __global__ void __launch_bounds__(256, Q == 1 ? 4 : 2) sparse_step_kernel(
     const float* __restrict__ hf, const int32_t* __restrict__ hint, StepConsts k,
     const float2* __restrict__ bias, const long long* __restrict__ counters,
     long long* __restrict__ qpart, long long* __restrict__ hpart, float* __restrict__ epart,
-    float* __restrict__ Gout) {
-  constexpr bool UPDATE = MODE == kModeUpdate;
+    float* __restrict__ Gout, const float* __restrict__ xin, float* __restrict__ xout) {
+  constexpr bool RELAXED = MODE == kModeRelaxed;
+  constexpr bool UPDATE = MODE == kModeUpdate || RELAXED;
   constexpr int W = 8;  // warps per block
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t words = Bp / 32;
@@ -76,11 +80,11 @@ __global__ void __launch_bounds__(256, Q == 1 ? 4 : 2) sparse_step_kernel(
       own[q] = own_n[q];
     }
     if (i + W < r1) fetch(i + W);
-    float G[Q][4];
+    float G[Q][4], Gx[Q][4];
 #pragma unroll
     for (int q = 0; q < Q; ++q)
 #pragma unroll
-      for (int r = 0; r < 4; ++r) G[q][r] = 0.f;
+      for (int r = 0; r < 4; ++r) { G[q][r] = 0.f; Gx[q][r] = 0.f; }
     const int e1 = rowptr[i + 1];
     for (int e = rowptr[i]; e < e1; ++e) {
       const int64_t j = col[e];
@@ -91,6 +95,13 @@ __global__ void __launch_bounds__(256, Q == 1 ? 4 : 2) sparse_step_kernel(
         const uint32_t nib = (__ldg(&bits_in[j * words + wofs + 4 * q]) >> nshift) & 0xFu;
 #pragma unroll
         for (int r = 0; r < 4; ++r) G[q][r] += ((nib >> r) & 1u) ? Jv : -Jv;
+        if (RELAXED) {
+          const float4 xj = __ldg(reinterpret_cast<const float4*>(xin + j * Bp + cb + 128 * q + 4 * lane));
+          Gx[q][0] = fmaf(Jv, xj.x, Gx[q][0]);
+          Gx[q][1] = fmaf(Jv, xj.y, Gx[q][1]);
+          Gx[q][2] = fmaf(Jv, xj.z, Gx[q][2]);
+          Gx[q][3] = fmaf(Jv, xj.w, Gx[q][3]);
+        }
       }
     }
     if (MODE == kModeCoupling) {
@@ -119,7 +130,7 @@ __global__ void __launch_bounds__(256, Q == 1 ? 4 : 2) sparse_step_kernel(
           ee[q][r] += s * fmaf(k.cq, G[q][r], k.ch * h);
         }
         if (UPDATE) {
-          const float F = fmaf(k.cq, G[q][r], fmaf(k.ch, h, -k.mu * s));
+          const float F = fmaf(k.cq, RELAXED ? Gx[q][r] : G[q][r], fmaf(k.ch, h, -k.mu * s));
           const float g = cos_proj(thp[r]) * F;
           thp[r] = adam_update(k, bc.x, bc.y, g, thp[r], mp[r], vp[r]);
           if (sin_nonneg(thp[r])) newnib |= 1u << r;
@@ -129,6 +140,9 @@ __global__ void __launch_bounds__(256, Q == 1 ? 4 : 2) sparse_step_kernel(
         __stcs(reinterpret_cast<float4*>(theta + base), th4[q]);
         __stcs(reinterpret_cast<float4*>(m + base), m4[q]);
         __stcs(reinterpret_cast<float4*>(v + base), v4[q]);
+        if (RELAXED)
+          *reinterpret_cast<float4*>(xout + base) =
+              make_float4(sin_proj(th4[q].x), sin_proj(th4[q].y), sin_proj(th4[q].z), sin_proj(th4[q].w));
         uint32_t word = newnib << nshift;
         word |= __shfl_xor_sync(0xffffffffu, word, 1);
         word |= __shfl_xor_sync(0xffffffffu, word, 2);
@@ -221,6 +235,8 @@ int sparse_step(ising_ds* ds, int mode, float* Gout) {
   const int ps = (int)(t % 2);
   const int64_t rpb = sparse_rows_per_block(ds);
   const int Q = (ds->sp_q == 2 && (ds->Bp / 128) % 2 == 0) ? 2 : 1;
+  const float* xin = mode == kModeRelaxed ? ds->xbuf[t % 2].as<float>() : nullptr;
+  float* xout = mode == kModeRelaxed ? ds->xbuf[(t + 1) % 2].as<float>() : nullptr;
   dim3 grid((unsigned)ds->mtiles, (unsigned)(ds->Bp / (128 * Q)));
 #define ISING_SP(U, I, V)                                                                     \
   do {                                                                                        \
@@ -234,12 +250,13 @@ int sparse_step(ising_ds* ds, int mode, float* Gout) {
       ds->sp_val.p, in, out, ds->theta.as<float>(), ds->m.as<float>(), ds->v.as<float>(),     \
       ds->hf.as<float>(), ds->hint.as<int32_t>(), ds->k, ds->bias.as<float2>(),               \
       ds->counters.as<long long>(), ds->qpart[ps].as<long long>(),                            \
-      ds->hpart[ps].as<long long>(), ds->epart[ps].as<float>(), Gout
+      ds->hpart[ps].as<long long>(), ds->epart[ps].as<float>(), Gout, xin, xout
 #define ISING_SP_V(U, I) \
   do { if (ds->sp_int8) ISING_SP(U, I, true); else ISING_SP(U, I, false); } while (0)
 #define ISING_SP_I(U) \
   do { if (ds->int_energy) ISING_SP_V(U, true); else ISING_SP_V(U, false); } while (0)
   if (mode == kModeUpdate) ISING_SP_I(kModeUpdate);
+  else if (mode == kModeRelaxed) ISING_SP_I(kModeRelaxed);
   else if (mode == kModeEnergy) ISING_SP_I(kModeEnergy);
   else ISING_SP_V(kModeCoupling, true);
 #undef ISING_SP_I

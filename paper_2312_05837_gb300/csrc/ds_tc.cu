@@ -51,6 +51,7 @@ struct TcArgs {
   const long long* counters;
   const void* S;           // S_t, [B][ld] (BF16 or E4M3)
   void* Snext;             // S_{t+1}
+  void* Xnext;             // relaxed mode: x_{t+1} = sin(theta), BF16 [B][ld]
   const float* rowscale;   // FP8 path with scaled rows, else null
   float* theta;
   float* m;
@@ -309,7 +310,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           sv[j] = 0.f;
           if (ok && MODE != kModeCoupling) {
             sv[j] = FP8 ? (Sin8[idx] == 0x38 ? 1.f : -1.f) : __bfloat162float(Sin[idx]);
-            if (MODE == kModeUpdate) {
+            if (MODE == kModeUpdate || MODE == kModeRelaxed) {
               th[j] = theta[idx];
               mm[j] = mvec[idx];
               vv[j] = vvec[idx];
@@ -345,13 +346,14 @@ __global__ void __launch_bounds__(kThreads, 1)
           } else {
             ef[j] = sj * fmaf(P.k.cq, G, P.k.ch * h);
           }
-          if (MODE == kModeUpdate) {
+          if (MODE == kModeUpdate || MODE == kModeRelaxed) {
+            // (relaxed mode: G = J x_t, and the partials above go unused)
             const float F = fmaf(P.k.cq, G, fmaf(P.k.ch, h, -P.k.mu * sj));
             const float g = cos_proj(th[j]) * F;
             th[j] = adam_update(P.k, bc.x, bc.y, g, th[j], mm[j], vv[j]);
           }
         }
-        if (MODE == kModeUpdate) {
+        if (MODE == kModeUpdate || MODE == kModeRelaxed) {
 #pragma unroll
           for (int j = 0; j < kChunk; ++j) {
             const int64_t b = n0 + c0 + j;
@@ -362,9 +364,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             vvec[idx] = vv[j];
             if (FP8) Sout8[idx] = sin_nonneg(th[j]) ? 0x38 : 0xB8;
             else Sout[idx] = __float2bfloat16(sin_nonneg(th[j]) ? 1.f : -1.f);
+            if (MODE == kModeRelaxed)
+              static_cast<__nv_bfloat16*>(P.Xnext)[idx] = __float2bfloat16(sin_proj(th[j]));
           }
         }
-        if (MODE != kModeCoupling) {
+        if (MODE == kModeUpdate || MODE == kModeEnergy) {
           // this warp's 32 spins summed per restart; partial row 4 mt + q
           const int64_t b = n0 + c0 + column_of_lane(lane);
           const int64_t o = ((int64_t)mt * 4 + q) * P.B + b;
@@ -1050,6 +1054,7 @@ struct TcState {
   CUtensorMap A[3];
   CUtensorMap B[3];   // one per spin slot, boxes of BN restarts (streaming kernel)
   CUtensorMap Bg[3];  // one per spin slot, boxes of one restart group (resident kernel)
+  CUtensorMap Bx[2];  // relaxed mode: one per slot of x = sin(theta), boxes of BN restarts
   int BN = 128;
   size_t smem = 0;
   int grid = 1;
@@ -1098,7 +1103,7 @@ int make_map(ising_ctx* ctx, CUtensorMap* map, const void* base, int64_t cols, i
 }
 
 template <int BN, int MODE, bool INT_E, bool FP8>
-int launch_bn(ising_ds* ds, TcState* st, const TcArgs& a, int slot) {
+int launch_bn(ising_ds* ds, TcState* st, const TcArgs& a, const CUtensorMap& mB) {
   auto kern = tc_step_kernel<BN, MODE, INT_E, FP8>;
   const size_t smem = TcLayout<BN>::kBytes;
   static bool attr_set = false;  // per instantiation
@@ -1107,24 +1112,31 @@ int launch_bn(ising_ds* ds, TcState* st, const TcArgs& a, int slot) {
                                              (int)smem));
     attr_set = true;
   }
-  kern<<<st->grid, kThreads, smem, ds->ctx->stream>>>(st->A[0], st->A[1], st->A[2], st->B[slot], a);
+  kern<<<st->grid, kThreads, smem, ds->ctx->stream>>>(st->A[0], st->A[1], st->A[2], mB, a);
   ISING_CUDA(ds->ctx, cudaGetLastError());
   return ISING_OK;
 }
 
 template <int MODE, bool INT_E, bool FP8>
-int launch_bn_sel(ising_ds* ds, TcState* st, const TcArgs& a, int slot) {
+int launch_bn_sel(ising_ds* ds, TcState* st, const TcArgs& a, const CUtensorMap& mB) {
   switch (st->BN) {
-    case 256: return launch_bn<256, MODE, INT_E, FP8>(ds, st, a, slot);
-    case 64: return launch_bn<64, MODE, INT_E, FP8>(ds, st, a, slot);
-    default: return launch_bn<128, MODE, INT_E, FP8>(ds, st, a, slot);
+    case 256: return launch_bn<256, MODE, INT_E, FP8>(ds, st, a, mB);
+    case 64: return launch_bn<64, MODE, INT_E, FP8>(ds, st, a, mB);
+    default: return launch_bn<128, MODE, INT_E, FP8>(ds, st, a, mB);
   }
 }
 
 template <int MODE, bool INT_E>
-int launch_mode(ising_ds* ds, TcState* st, const TcArgs& a, int slot) {
-  return st->fp8 ? launch_bn_sel<MODE, INT_E, true>(ds, st, a, slot)
-                 : launch_bn_sel<MODE, INT_E, false>(ds, st, a, slot);
+int launch_mode(ising_ds* ds, TcState* st, const TcArgs& a, const CUtensorMap& mB) {
+  return st->fp8 ? launch_bn_sel<MODE, INT_E, true>(ds, st, a, mB)
+                 : launch_bn_sel<MODE, INT_E, false>(ds, st, a, mB);
+}
+
+// Relaxed-product update: BF16 operands only (x in E4M3 would be too coarse).
+template <bool INT_E>
+int launch_relaxed(ising_ds* ds, TcState* st, const TcArgs& a, const CUtensorMap& mB) {
+  if (st->fp8) return fail(ds->ctx, ISING_ENOTSUP, "relaxed product needs BF16 operands");
+  return launch_bn_sel<kModeRelaxed, INT_E, false>(ds, st, a, mB);
 }
 
 }  // namespace
@@ -1176,6 +1188,12 @@ int tc_setup(ising_ds* ds) {
   ds->tc = st;
   const bool exact16 = I.j_integer && I.j_absmax <= 16.0;
   const bool exact256 = I.j_integer && I.j_absmax <= 256.0;
+  if (ds->relaxed()) {
+    // x = sin(theta) goes to the tensor cores in BF16, so J does too
+    if (ds->prec == ISING_PREC_FP8)
+      return fail(ctx, ISING_ENOTSUP, "relaxed product: E4M3 is too coarse for x; use BF16");
+    if (ds->prec == ISING_PREC_AUTO) ds->prec = ISING_PREC_TC;
+  }
   // AUTO: E4M3 when it holds J exactly, else the exact BF16 form
   if (ds->prec == ISING_PREC_AUTO) ds->prec = exact16 ? ISING_PREC_FP8 : ISING_PREC_TC;
   st->fp8 = ds->prec == ISING_PREC_FP8;
@@ -1236,7 +1254,7 @@ int tc_setup(ising_ds* ds) {
   // resident form when every (128 x 2 GN) tile gets its own co-resident CTA
   // (a tensor-memory kernel holds its SM alone): two groups of GN restarts
   // per CTA, 64 each, or 32 when B <= 64
-  if (!(ds->p.flags & ISING_DS_STREAMING)) {
+  if (!(ds->p.flags & ISING_DS_STREAMING) && !ds->relaxed()) {
     const int gn = ds->B > 64 ? 64 : 32;
     const int tiles = ceil_div_i(ds->n, kBM) * ceil_div_i(ds->B, 2 * gn);
     // shared memory: resident J tiles (as many as leave room for 4 stages of 2 k-blocks),
@@ -1283,6 +1301,9 @@ static int tc_maps(ising_ds* ds, TcState* st) {
       ISING_TRY(make_map(ds->ctx, &st->Bg[s], ds->spins[s].p, ds->n, ds->B, ds->ld,
                          st->fp8 ? 128 : 64, st->gn, st->fp8));
   }
+  if (ds->relaxed())
+    for (int s = 0; s < 2; ++s)
+      ISING_TRY(make_map(ds->ctx, &st->Bx[s], ds->xbuf[s].p, ds->n, ds->B, ds->ld, 64, st->BN, false));
   return ISING_OK;
 }
 
@@ -1307,6 +1328,7 @@ int tc_run(ising_ds* ds, int mode, float* Gout) {
   a.counters = ds->counters.as<long long>();
   a.S = ds->spins[t % 3].p;
   a.Snext = ds->spins[(t + 1) % 3].p;
+  a.Xnext = ds->relaxed() ? ds->xbuf[(t + 1) % 2].p : nullptr;
   a.rowscale = ds->rowscale.p ? ds->rowscale.as<float>() : nullptr;
   a.theta = ds->theta.as<float>();
   a.m = ds->m.as<float>();
@@ -1326,14 +1348,19 @@ int tc_run(ising_ds* ds, int mode, float* Gout) {
     if (!st->trace.p) ISING_TRY(dev_alloc(ds->ctx, st->trace, (size_t)st->grid * 8 * 8));
     a.trace = st->trace.as<unsigned long long>();
   }
-  const int slot = (int)(t % 3);
+  const CUtensorMap& mS = st->B[t % 3];
   const bool ie = ds->int_energy;
   switch (mode) {
-    case kModeUpdate: return ie ? launch_mode<kModeUpdate, true>(ds, st, a, slot)
-                                : launch_mode<kModeUpdate, false>(ds, st, a, slot);
-    case kModeEnergy: return ie ? launch_mode<kModeEnergy, true>(ds, st, a, slot)
-                                : launch_mode<kModeEnergy, false>(ds, st, a, slot);
-    default: return launch_mode<kModeCoupling, true>(ds, st, a, slot);
+    case kModeUpdate: return ie ? launch_mode<kModeUpdate, true>(ds, st, a, mS)
+                                : launch_mode<kModeUpdate, false>(ds, st, a, mS);
+    case kModeEnergy: return ie ? launch_mode<kModeEnergy, true>(ds, st, a, mS)
+                                : launch_mode<kModeEnergy, false>(ds, st, a, mS);
+    case kModeRelaxed: {
+      // the product runs on x_t; the epilogue reads s_t and writes s_{t+1}, x_{t+1}
+      const CUtensorMap& mX = st->Bx[t % 2];
+      return ie ? launch_relaxed<true>(ds, st, a, mX) : launch_relaxed<false>(ds, st, a, mX);
+    }
+    default: return launch_mode<kModeCoupling, true>(ds, st, a, mS);
   }
 }
 

@@ -35,8 +35,10 @@ def wrapped_diff(a, b):
     return d - 2 * math.pi * np.rint(d / (2 * math.pi))
 
 
-def check_step(inst, st0, st1, last_E, p, exact_energy):
-    """st0: state before step t = st0['t'] + 1, st1: after it."""
+def check_step(inst, st0, st1, last_E, p, exact_energy, tol=TOL, min_clear=0.98):
+    """st0: state before step t = st0['t'] + 1, st1: after it. `tol` bounds
+    the product's error relative to the row scale (TOL for FP32 arithmetic);
+    `min_clear` is the fraction of next spins that must lie outside it."""
     t = st0["t"] + 1
     r = oracle_step(inst, st0, t, p)
     # spins consumed by the step are the oracle's rounding of the same theta
@@ -56,11 +58,11 @@ def check_step(inst, st0, st1, last_E, p, exact_energy):
     # gradient recovered from the first moment: g = (m1 - b1 m0) / (1 - b1)
     m1 = st1["m"].T.astype(np.float64)
     v1 = st1["v"].T.astype(np.float64)
-    assert np.all(np.abs(m1 - r.m) <= TOL * (np.abs(m0) + (1 - p.beta1) * sc) + 1e-30)
-    assert np.all(np.abs(v1 - r.v) <= TOL * (v0 + 2 * (1 - p.beta2) * sc * sc) + 1e-30)
+    assert np.all(np.abs(m1 - r.m) <= tol * (np.abs(m0) + (1 - p.beta1) * sc) + 1e-30)
+    assert np.all(np.abs(v1 - r.v) <= tol * (v0 + 2 * (1 - p.beta2) * sc * sc) + 1e-30)
     if np.all(m0 == 0):
         g = m1 / (1 - p.beta1)
-        assert np.all(np.abs(g - r.grad) <= TOL * sc)
+        assert np.all(np.abs(g - r.grad) <= tol * sc)
     th1 = st1["theta"].T.astype(np.float64)
     # Adam divides by sqrt(v): a gradient error dg moves theta by sens * dg,
     # sens = lr * d(mhat / (sqrt(vhat) + eps)) / dg, evaluated at the oracle's values
@@ -75,12 +77,12 @@ def check_step(inst, st0, st1, last_E, p, exact_energy):
     # gradient error: for integer instances F is exact and only cos(theta) is
     # approximated (absolute error <= 2^-21.41 < 4e-7 on [-pi, pi]); otherwise
     # the FP32 product bounds it
-    dg = np.abs(r.F) * 4e-7 if exact_energy else TOL * sc
-    tol_th = TOL * (1 + p.lr) * (1 + np.abs(mhat) / (rv + p.eps)) + sens * dg
+    dg = np.abs(r.F) * 4e-7 if (exact_energy and tol == TOL and p.grad_mode == "rounded") else tol * sc
+    tol_th = tol * (1 + p.lr) * (1 + np.abs(mhat) / (rv + p.eps)) + sens * dg
     assert np.all(np.abs(wrapped_diff(th1, r.theta)) <= tol_th)
     # next spins: identical wherever the rounding is not within the tolerance
     clear = np.abs(np.sin(r.theta)) > 2 * tol_th
     nxt = st1["spins"].T
     assert np.array_equal(nxt[clear], ods.round_spins(r.theta)[clear].astype(np.int8))
-    assert clear.mean() > 0.98
+    assert clear.mean() > min_clear, clear.mean()
     return r
