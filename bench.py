@@ -269,31 +269,41 @@ def cpu_baseline(a, inst, B, seconds):
 
 # ----------------------------------------------------------------- time to target
 
-def time_to_target(ctx, dinst, B, T, seed, chunk=50):
-    """Device time until the best-so-far energy reaches E*, the final best of
-    the plain FP32 form on the same instance and seed, for the plain form and
-    the default (tensor-core) form; both advance in chunks of `chunk` steps and
-    are checked after each chunk."""
+def time_to_target(ctx, dinst, integer, B, T, seed, chunk=50):
+    """Time until the best-so-far energy reaches E*, the best the plain FP32
+    form reaches on the same instance and seed, for the plain form and the
+    fast form (AUTO: exact E4M3 for integer couplings; row-scaled E4M3 with
+    exact re-evaluation otherwise). Both advance in chunks of `chunk` steps;
+    after each chunk the restarts' best spins are evaluated exactly (FP64 on
+    the device; the tracked integer energies already are exact) and the
+    wall time of steps plus checks is accumulated."""
     import numpy as np
+    import torch
     from paper_2312_05837_gb300 import api
 
     def trace(prec):
         s = api.Session(ctx, dinst, restarts=B, steps=T, seed=seed, precision=prec)
         hist = []
-        done = 0
+        done, ms = 0, 0.0
+        torch.cuda.synchronize()
         while done < T:
             k = min(chunk, T - done)
+            w0 = time.perf_counter()
             s.run(k)
             done += k
-            hist.append((s.result()["device_ms"], float(np.min(s.restart_best()[0]))))
-        s.finish()
-        r = s.result()
+            E, _, sp = s.restart_best(device=True)
+            if not integer:
+                E = api.energy(ctx, dinst, sp)
+            best = float(E.min().item())
+            ms += 1e3 * (time.perf_counter() - w0)
+            hist.append((ms, best))
         s.close()
-        return hist, r
+        return hist, s
 
-    hist_p, rp = trace("fp32")
-    target = rp["best_energy"]
-    hist_f, rf = trace("auto")
+    hist_p, _ = trace("fp32")
+    target = hist_p[-1][1]
+    fast_prec = "auto" if integer else "fp8"
+    hist_f, _ = trace(fast_prec)
 
     def first(hist):
         for ms, e in hist:
@@ -303,9 +313,34 @@ def time_to_target(ctx, dinst, B, T, seed, chunk=50):
 
     tp, tf = first(hist_p), first(hist_f)
     return {"target_energy": target, "plain_fp32_ms": tp, "fast_ms": tf,
-            "fast_precision": {1: "fp32", 2: "tc-bf16", 3: "bf16", 4: "e4m3"}.get(rf["precision"]),
+            "fast_precision": "e4m3 (exact)" if integer else "e4m3 row-scaled, exact re-evaluation",
             "speedup": (tp / tf) if (tp and tf) else None, "chunk_steps": chunk,
-            "fast_best_energy": rf["best_energy"]}
+            "fast_best_energy": hist_f[-1][1],
+            "timing": "wall time of the steps and the exact checks after each chunk"}
+
+
+def precision_sweep(ctx, dinst, n, B, T, seed=1):
+    """One full domain selection per operand precision on the same instance
+    and seed: the plain FP32 CUDA-core form, three BF16 planes (FP32-exact),
+    one BF16 plane and row-scaled E4M3 (SURVEY config 3); spin-updates/s from
+    device time and the best energy, re-evaluated exactly in FP64."""
+    import torch
+    from paper_2312_05837_gb300 import api
+    out = {}
+    for prec in ["fp32", "tc", "bf16", "fp8"]:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = api.select_domain(ctx, dinst, restarts=B, steps=T, seed=seed, precision=prec)
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        out[prec] = {"value": n * B * T / (ms / 1e3), "ms": ms,
+                     "best_energy": float(r["best_energy"].item())}
+    ref = out["fp32"]["best_energy"]
+    for prec in out:
+        out[prec]["gap_vs_fp32"] = (out[prec]["best_energy"] - ref) / abs(ref)
+    return out
 
 
 # ----------------------------------------------------------------- serving
@@ -492,8 +527,10 @@ def main():
     if name.startswith("table2"):
         from paper_2312_05837_gb300.metrics import paper_metrics
         line["paper_metrics"] = paper_metrics(inst, line["best_energy"], max_ms / a.steps / 1e3)
+    if rank == 0 and not a.no_extras and name == "sk4096":
+        line["precision_sweep"] = precision_sweep(ctx, dinst, inst.n, B, T)
     if rank == 0 and not a.no_extras:
-        line["time_to_target"] = time_to_target(ctx, dinst, B, T, seed=3)
+        line["time_to_target"] = time_to_target(ctx, dinst, bool(inst.integer), B, T, seed=3)
         line["serving"] = serving(ctx)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(a, inst, B, a.cpu_seconds)

@@ -456,12 +456,23 @@ class Session:
         self.ctx.check(self.ctx.lib.ising_ds_convergence(self.handle, _ptr(out), L.MEM_HOST))
         return out
 
-    def restart_best(self):
-        E = np.empty(self.B, np.float64)
-        st = np.empty(self.B, np.int64)
-        sp = np.empty((self.B, self.n), np.int8)
+    def restart_best(self, device: bool = False):
+        """Per-restart best energy, step and spins [B][n]; torch tensors on
+        the session's device when `device`, else numpy arrays."""
+        if device:
+            torch = _torch()
+            dev = torch.device("cuda", self.ctx.device)
+            E = torch.empty(self.B, dtype=torch.float64, device=dev)
+            st = torch.empty(self.B, dtype=torch.int64, device=dev)
+            sp = torch.empty((self.B, self.n), dtype=torch.int8, device=dev)
+            mem = L.MEM_DEVICE
+        else:
+            E = np.empty(self.B, np.float64)
+            st = np.empty(self.B, np.int64)
+            sp = np.empty((self.B, self.n), np.int8)
+            mem = L.MEM_HOST
         self.ctx.check(self.ctx.lib.ising_ds_restart_best(self.handle, _ptr(E), _ptr(st),
-                                                          _ptr(sp), L.MEM_HOST))
+                                                          _ptr(sp), mem))
         return E, st, sp
 
     def result(self):
