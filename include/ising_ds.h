@@ -185,6 +185,15 @@ int ising_set_stream(ising_ctx* ctx, void* stream);
 int ising_synchronize(ising_ctx* ctx);
 /* ABI version: major * 10000 + minor * 100 + patch. */
 int ising_version(void);
+/* Diagnostic of the failure handling (the paper has no counterpart): runs
+ * on the context's stream a kernel with two waits that nothing completes,
+ * each bounded by `limit_cycles` SM clock cycles in the same way as the
+ * tensor-core kernels' waits: an mbarrier that receives no arrival and a poll
+ * of a device flag that nothing sets. Both give up; `gave_up` (nullable)
+ * receives the bitmask of the waits that did (1 mbarrier, 2 flag) and the
+ * call returns ISING_ETIMEOUT, after which the context stays usable.
+ * limit_cycles must lie in [1, 2^34]. */
+int ising_selftest_waits(ising_ctx* ctx, int64_t limit_cycles, int32_t* gave_up);
 
 /* ------------------------------------------------------------------ energy */
 

@@ -257,6 +257,14 @@ class Server:
             pass
 
 
+def selftest_waits(ctx: Context, limit_cycles: int):
+    """Runs the bounded-wait diagnostic (ising_selftest_waits); returns the
+    status code and the mask of waits that gave up, without raising."""
+    mask = ctypes.c_int32(-1)
+    rc = ctx.lib.ising_selftest_waits(ctx.handle, int(limit_cycles), byref(mask))
+    return rc, mask.value
+
+
 def energy_noalloc(inst, spins, E_out, stream=None):
     """ising_energy_noalloc: energies of spins[count][n] into the caller's
     E_out[count] (all torch CUDA tensors); queues the work on `stream`

@@ -1,6 +1,7 @@
 // Context management, the energy call (K3) and the full solve
 // (pruning -> domain selection -> reconstruction -> energy).
 #include "common.cuh"
+#include "tcgen05.cuh"
 
 #include <algorithm>
 
@@ -100,6 +101,50 @@ extern "C" int ising_energy(ising_ctx* ctx, const ising_instance* inst, const in
   return ISING_OK;
 }
 
+namespace {
+
+// Two bounded waits that nothing completes (see ising_selftest_waits).
+__global__ void selftest_wait_kernel(const unsigned int* flag, long long limit, int* status) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    ising::tc::mbar_init(&bar, 1);
+    ising::tc::fence_barrier_init();
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  int gave_up = 0;
+  if (!ising::tc::mbar_wait(&bar, 0, nullptr, limit)) gave_up |= 1;
+  const long long c0 = clock64();
+  while (ising::tc::ld_acquire_gpu(flag) == 0u) {
+    if (clock64() - c0 > limit) {
+      gave_up |= 2;
+      break;
+    }
+  }
+  *status = gave_up;
+}
+
+}  // namespace
+
+extern "C" int ising_selftest_waits(ising_ctx* ctx, int64_t limit_cycles, int32_t* gave_up) {
+  if (!ctx) return ISING_EINVAL;
+  if (limit_cycles < 1 || limit_cycles > (int64_t(1) << 34))
+    return fail(ctx, ISING_EINVAL, "limit_cycles must lie in [1, 2^34]");
+  ISING_CUDA(ctx, cudaSetDevice(ctx->device));
+  DevMem buf;
+  ISING_TRY(dev_alloc(ctx, buf, 16));
+  ISING_CUDA(ctx, cudaMemsetAsync(buf.p, 0, 16, ctx->stream));
+  selftest_wait_kernel<<<1, 32, 0, ctx->stream>>>(buf.as<unsigned int>(), (long long)limit_cycles,
+                                                  buf.as<int>() + 1);
+  ISING_CUDA(ctx, cudaGetLastError());
+  int st = 0;
+  ISING_CUDA(ctx, cudaMemcpyAsync(&st, buf.as<int>() + 1, 4, cudaMemcpyDeviceToHost, ctx->stream));
+  ISING_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (gave_up) *gave_up = st;
+  if (st) return fail(ctx, ISING_ETIMEOUT, "bounded waits gave up (mask %d)", st);
+  return ISING_OK;
+}
+
 namespace ising {
 int prune_device(ising_ctx* ctx, const DevInstance& I, int flags, ising_prune_result** out);
 int ds_create_impl(ising_ctx* ctx, const ising_instance* inst, const ising_ds_params* p,
@@ -118,11 +163,18 @@ extern "C" int ising_solve(ising_ctx* ctx, const ising_instance* inst, const isi
   if (prune_flags & ~ISING_PRUNE_ZERO_RULE) return fail(ctx, ISING_EINVAL, "unknown prune flags");
   if (!p) return fail(ctx, ISING_EINVAL, "params is NULL");
   ISING_CUDA(ctx, cudaSetDevice(ctx->device));
+  NvtxRange range("ising_solve");
   cudaStream_t st = ctx->stream;
   DevInstance I;
-  ISING_TRY(upload_instance(ctx, inst, &I));
+  {
+    NvtxRange r("upload+validate");
+    ISING_TRY(upload_instance(ctx, inst, &I));
+  }
   ising_prune_result* pr = nullptr;
-  ISING_TRY(prune_device(ctx, I, prune_flags, &pr));
+  {
+    NvtxRange r("prune");
+    ISING_TRY(prune_device(ctx, I, prune_flags, &pr));
+  }
   int64_t nG = 0;
   ising_prune_info(pr, &nG, nullptr, nullptr, nullptr, nullptr);
   const int64_t n = inst->n;
@@ -134,6 +186,7 @@ extern "C" int ising_solve(ising_ctx* ctx, const ising_instance* inst, const isi
     if ((rc = dev_alloc(ctx, full, n)) != ISING_OK) break;
     if ((rc = dev_alloc(ctx, E, 8)) != ISING_OK) break;
     if (nG > 0) {
+      NvtxRange r("select_domain");
       ising_instance red;
       ising_prune_reduced(pr, &red);
       double eg = 0.0;
@@ -144,6 +197,7 @@ extern "C" int ising_solve(ising_ctx* ctx, const ising_instance* inst, const isi
       ising_ds_destroy(ds);
       if (rc != ISING_OK) break;
     }
+    NvtxRange rr("reconstruct+energy");
     rc = ising_reconstruct(ctx, pr, sG.as<int8_t>(), full.as<int8_t>(), ISING_MEM_DEVICE);
     if (rc != ISING_OK) break;
     // the energy of the reconstructed spins on the full instance

@@ -21,7 +21,18 @@ struct ising_ctx {
   std::string err;
 };
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace ising {
+
+// NVTX range for the duration of a scope (shows the stages of a call on a
+// profiler's timeline; costs nothing without a profiler attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Records a formatted error on the context and returns `code`.
 inline int fail(ising_ctx* ctx, int code, const char* fmt, ...) {

@@ -915,6 +915,7 @@ extern "C" int ising_ds_run(ising_ds* ds, int64_t steps) {
   if (ds->finished) return fail(ctx, ISING_EINVAL, "session already finished");
   int64_t todo = std::min(steps, ds->T - ds->t);
   if (todo <= 0 || ds->conv_all) return ISING_OK;
+  NvtxRange range("ising_ds_run");
   cudaEvent_t e0, e1;
   ISING_CUDA(ctx, cudaEventCreate(&e0));
   ISING_CUDA(ctx, cudaEventCreate(&e1));
@@ -944,6 +945,7 @@ extern "C" int ising_ds_finish(ising_ds* ds) {
   if (ds->finished) return ISING_OK;
   ising_ctx* ctx = ds->ctx;
   ISING_TRY(ising_ds_run(ds, ds->T - ds->t));
+  NvtxRange range("ising_ds_finish");
   // energy of S_{T+1}: the step kernels in energy-only mode, then tracking
   // (nothing to evaluate once every restart has stopped)
   if (!ds->conv_all) {
