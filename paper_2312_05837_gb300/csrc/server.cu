@@ -1,14 +1,16 @@
 // Request server: continuous batching of independent Ising solves on one GPU.
 //
 // A worker thread owns `max_active` slots, each a context with its own
-// stream. Each round it (1) admits queued requests in arrival order while a
-// slot is free and the estimated device footprint of the admitted set stays
-// within the budget, (2) queues `chunk_steps` more domain-selection steps of
-// every admitted request on its slot's stream without waiting, (3) waits for
-// the slots' streams, and (4) finishes the requests whose steps are done
-// (final energy pass, best of restarts, reconstruction, full-instance energy)
-// and releases their memory. Requests arriving during a round are admitted at
-// the next one, so their work overlaps the work already on the device.
+// stream. It loops: (1) admits queued requests in arrival order while a slot
+// is free and the estimated device footprint of the admitted set stays within
+// the budget, and sets them up (upload, pruning, session); (2) for every
+// admitted request whose previous chunk has completed (an event on its
+// stream, polled without blocking), either queues `chunk_steps` more
+// domain-selection steps or, when its steps are done, finishes it (final
+// energy pass, best of restarts, reconstruction, full-instance energy) and
+// releases its memory and slot. Slots progress independently, so a small
+// request never waits for a large one's chunk, and requests arriving at any
+// time are admitted as soon as a slot and memory free up.
 #include "ds_internal.cuh"
 
 #include <chrono>
@@ -45,6 +47,8 @@ struct Request {
   ising_ds* ds = nullptr;
   int64_t nG = 0;
   bool started = false;
+  cudaEvent_t ev = nullptr;  // completion of the request's last queued chunk
+  bool in_flight = false;
   // result
   int status = ISING_OK;
   bool done = false;
@@ -115,6 +119,7 @@ int start_request(ising_server* srv, Request* r) {
     p.flags |= ISING_DS_STREAMING;  // no grid barrier across concurrent requests
     ISING_TRY(ds_create_impl(ctx, &red, &p, &r->ds, false));
   }
+  ISING_CUDA(ctx, cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming));
   r->started = true;
   return ISING_OK;
 }
@@ -152,6 +157,8 @@ void release_request(ising_server* srv, Request* r) {
   r->indptr.clear();
   r->indices.clear();
   if (r->slot >= 0) cudaStreamSynchronize(srv->slots[r->slot]->stream);
+  if (r->ev) cudaEventDestroy(r->ev);
+  r->ev = nullptr;
 }
 
 void worker_loop(ising_server* srv) {
@@ -180,7 +187,6 @@ void worker_loop(ising_server* srv) {
     std::vector<Request*> act = srv->active;
     const int64_t chunk = srv->cfg.chunk_steps;
     lk.unlock();
-    // 2. set-up of new requests, then one chunk of steps for everyone
     for (Request* r : admitted) {
       int rc = start_request(srv, r);
       if (rc != ISING_OK) {
@@ -188,28 +194,32 @@ void worker_loop(ising_server* srv) {
         r->started = false;
       }
     }
-    for (Request* r : act) {
-      if (r->status != ISING_OK || !r->ds) continue;
-      const int64_t todo = std::min<int64_t>(chunk, r->ds->T - r->ds->t);
-      if (todo > 0) {
-        int rc = ds_advance(r->ds, todo);
-        if (rc != ISING_OK) r->status = rc;
-      }
-    }
-    // 3. wait for the round
-    for (Request* r : act) {
-      cudaStreamSynchronize(srv->slots[r->slot]->stream);
-      if (r->status == ISING_OK && r->ds) {
-        int rc = ds_conv_check(r->ds);  // convergence rule: have all restarts stopped?
-        if (rc != ISING_OK) r->status = rc;
-      }
-    }
-    // 4. finish what is done
+    // 2. every request whose last chunk has completed: next chunk, or finish
+    bool progressed = !admitted.empty();
     std::vector<Request*> finished;
     for (Request* r : act) {
+      if (r->in_flight) {
+        const cudaError_t q = cudaEventQuery(r->ev);
+        if (q == cudaErrorNotReady) continue;
+        r->in_flight = false;
+        if (q != cudaSuccess) r->status = ISING_ECUDA;
+        if (r->status == ISING_OK && r->ds) {
+          int rc = ds_conv_check(r->ds);  // convergence rule: have all restarts stopped?
+          if (rc != ISING_OK) r->status = rc;
+        }
+      }
+      progressed = true;
       const bool steps_done =
           r->status != ISING_OK || !r->ds || r->ds->t >= r->ds->T || r->ds->conv_all;
-      if (!steps_done) continue;
+      if (!steps_done) {
+        const int64_t todo = std::min<int64_t>(chunk, r->ds->T - r->ds->t);
+        int rc = ds_advance(r->ds, todo);
+        if (rc == ISING_OK && cudaEventRecord(r->ev, srv->slots[r->slot]->stream) != cudaSuccess)
+          rc = ISING_ECUDA;
+        if (rc != ISING_OK) r->status = rc;
+        else r->in_flight = true;
+        continue;
+      }
       if (r->status == ISING_OK) {
         int rc = finish_request(srv, r);
         if (rc != ISING_OK) r->status = rc;
@@ -230,6 +240,8 @@ void worker_loop(ising_server* srv) {
         }
     }
     if (!finished.empty()) srv->done_cv.notify_all();
+    // nothing completed: wait a little (new submissions wake the worker)
+    if (!progressed) srv->cv.wait_for(lk, std::chrono::microseconds(50));
   }
 }
 
