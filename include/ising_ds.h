@@ -124,9 +124,12 @@ typedef struct ising_ds_params {
  * is then the time per step). */
 #define ISING_DS_PROFILE 1
 /* params.flags: keep the tensor-core path's state in device memory between
- * steps (one launch per step) even when the resident form would fit. The
- * resident form, used when every 128 x BN tile gets its own SM, keeps theta,
- * m and v in tensor memory across a whole run (one cooperative launch). */
+ * steps (one launch per step) even when a resident form would fit. The
+ * resident forms keep theta, m and v in tensor memory across a whole run in
+ * one launch: for n <= 128 the small form (every CTA holds all of J and the
+ * spins of its block of restarts in shared memory, no grid-wide barrier), for
+ * larger n the grid-wide form, used when every 128 x BN tile gets its own SM
+ * (one cooperative launch). */
 #define ISING_DS_STREAMING 2
 /* params.flags: skip the launch-shape autotuner and use the default shape.
  * The autotuner (sparse path) times the first steps of a run once per
@@ -165,7 +168,9 @@ typedef struct ising_ds_stats {
   double device_ms;         /* device time of the steps (CUDA events) */
   double kernel_ms;         /* step kernels only (with ISING_DS_PROFILE) */
   int64_t kernel_launches;  /* step-kernel launches timed in kernel_ms */
-  int32_t resident;         /* 1 if the tensor-core path kept the state in tensor memory */
+  int32_t resident;         /* tensor-core path kept the state in tensor memory: 1 in the
+                               grid-wide form, 2 in the small form (n <= 128, each CTA holds
+                               all of J and its restarts' spins on chip); 0 otherwise */
   int32_t reserved0;
 } ising_ds_stats;
 

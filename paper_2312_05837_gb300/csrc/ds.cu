@@ -1154,7 +1154,7 @@ extern "C" int ising_ds_result(ising_ds* ds, int8_t* best_spins, double* best_en
     stats->device_ms = ds->device_ms;
     stats->kernel_ms = ds->kernel_ms;
     stats->kernel_launches = ds->kernel_launches;
-    stats->resident = (ds->path == ISING_PATH_TC && tc_is_resident(ds)) ? 1 : 0;
+    stats->resident = ds->path == ISING_PATH_TC ? tc_resident_form(ds) : 0;
     stats->reserved0 = 0;
   }
   ISING_CUDA(ctx, cudaStreamSynchronize(ctx->stream));

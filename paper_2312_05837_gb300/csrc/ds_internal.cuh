@@ -221,6 +221,7 @@ int tc_setup(ising_ds* ds);
 int tc_step(ising_ds* ds, int mode, float* Gout);
 int tc_error(ising_ds* ds);  // ISING_ETIMEOUT if a bounded wait gave up
 bool tc_is_resident(ising_ds* ds);            // tensor memory keeps the state between steps
+int tc_resident_form(ising_ds* ds);           // 0 streaming, 1 grid-wide resident, 2 small (n <= 128)
 int tc_run_resident(ising_ds* ds, int64_t steps);  // `steps` steps in one cooperative launch
 int tc_trace(ising_ds* ds, uint64_t* out, int64_t cap, int64_t* count);
 void tc_release(ising_ds* ds);

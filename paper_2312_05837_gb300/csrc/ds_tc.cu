@@ -1050,6 +1050,341 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// Small form: when all n <= 128 spins fit one row tile, every CTA holds all of
+// J in shared memory (loaded once) for its block of BN restarts, so a step
+// needs nothing from other CTAs. The epilogue writes the next spins straight
+// into the shared-memory B operand, in the 128-byte swizzled layout the TMA
+// produces (16-byte chunk c of row r stored at chunk c ^ (r mod 8)); after a
+// proxy fence and a CTA barrier the tensor cores read them. Energies, bests
+// and the copies of improved spins stay inside the CTA: no grid barrier and
+// no global round trip per step. Warp 0 issues TMA and MMAs; warps 1..16 run
+// the epilogue (TMEM lane quarter warp mod 4).
+
+constexpr int kSmallEpi = 16;
+constexpr int kSmallThreads = 32 * (1 + kSmallEpi);
+
+struct TcSmallArgs {
+  TcArgs P;
+  int64_t steps;
+  long long t0;       // steps already taken (the first step here is t0 + 1)
+  void* spins_out;    // global slot receiving S_{t0+K+1}, [B][ld]
+  double* best_E;
+  long long* best_t;
+  int8_t* best_s;
+  double* last_E;
+  int64_t bs_ld;
+  double cq, chs;     // E = cq * Q + chs * H (integer mode)
+};
+
+// Byte offset of element (row r, K index k) in a swizzled operand tile whose
+// rows hold kBK elements of `esize` bytes (128 bytes).
+__device__ __forceinline__ uint32_t swz_offset(int r, int k, int esize) {
+  const uint32_t byte = (uint32_t)k * (uint32_t)esize;
+  return (uint32_t)r * 128u + ((((byte >> 4) ^ (uint32_t)(r & 7)) << 4) | (byte & 15u));
+}
+
+template <int BN, bool FP8>
+struct SmallLayout {
+  static constexpr int kBK = FP8 ? 128 : 64;
+  static constexpr uint32_t kA = kBM * kRowBytes;  // one J k-block tile
+  static constexpr uint32_t kSk = BN * kRowBytes;  // one S k-block tile
+};
+
+template <int BN, bool INT_E, bool FP8>
+__global__ void __launch_bounds__(kSmallThreads, 1)
+    tc_small_kernel(const __grid_constant__ CUtensorMap tmA0,
+                    const __grid_constant__ CUtensorMap tmA1,
+                    const __grid_constant__ CUtensorMap tmA2,
+                    const __grid_constant__ CUtensorMap tmB, const TcSmallArgs R) {
+  using Lay = SmallLayout<BN, FP8>;
+  constexpr int kBK = Lay::kBK;
+  constexpr int esize = FP8 ? 1 : 2;
+  constexpr uint32_t kTmemCols = 4 * BN;
+  constexpr int kCols = BN / 4;
+  const TcArgs& P = R.P;
+  const int nk = P.nk, nkt = P.nk * P.planes;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  uint8_t* Jsm = smem;                                    // nkt x kA
+  uint8_t* Ssm = Jsm + (size_t)nkt * Lay::kA;             // 2 buffers x nk x kSk
+  const size_t kSbuf = (size_t)nk * Lay::kSk;
+  int* part_q = reinterpret_cast<int*>(Ssm + 2 * kSbuf);  // [4][BN]
+  int* part_h = part_q + 4 * BN;                          // [4][BN]
+  float* part_f = reinterpret_cast<float*>(part_h + 4 * BN);  // [4][BN]
+  double* bE = reinterpret_cast<double*>(part_f + 4 * BN);    // [BN] best energy
+  double* lE = bE + BN;                                       // [BN] last energy
+  long long* bT = reinterpret_cast<long long*>(lE + BN);      // [BN] best step
+  int* imp = reinterpret_cast<int*>(bT + BN);                 // [BN] improved flags
+  uint64_t* tma_bar = reinterpret_cast<uint64_t*>(imp + BN);
+  uint64_t* acc_bar = tma_bar + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_bar + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t n0 = (int64_t)blockIdx.x * BN;
+  // (the step count comes from the host: CTAs of a large grid need not run
+  // at the same time, so counters[0] may already be advanced when one starts)
+  const long long t0 = R.t0;
+  const int64_t K = R.steps;
+  if (threadIdx.x == 0) {
+    tc::mbar_init(tma_bar, 1);
+    tc::mbar_init(acc_bar, 1);
+    tc::fence_barrier_init();
+  }
+  if (warp == 0) {
+    tc::tmem_alloc(tmem_slot, kTmemCols);
+    tc::fence_before_sync();
+  }
+  // spin buffers start at 0 (rows past B, columns past n stay 0)
+  for (size_t o = threadIdx.x * 16; o < 2 * kSbuf; o += (size_t)blockDim.x * 16)
+    *reinterpret_cast<uint4*>(Ssm + o) = make_uint4(0, 0, 0, 0);
+  for (int b = threadIdx.x; b < BN; b += blockDim.x) {
+    const int64_t gb = n0 + b;
+    const bool ok = gb < P.B;
+    bE[b] = ok ? R.best_E[gb] : 0.0;
+    lE[b] = ok ? R.last_E[gb] : 0.0;
+    bT[b] = ok ? R.best_t[gb] : 0;
+  }
+  tc::fence_proxy_async_shared();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem_base = *tmem_slot;
+  if (threadIdx.x == 0) {
+    // all of J (every plane and k-block) and S_{t0+1} of this block of restarts
+    tc::mbar_expect_tx(tma_bar, (uint32_t)nkt * Lay::kA + (uint32_t)nk * Lay::kSk);
+    for (int kt = 0; kt < nkt; ++kt) {
+      const int plane = kt / nk, kb = kt - plane * nk;
+      const CUtensorMap* ma = plane == 0 ? &tmA0 : (plane == 1 ? &tmA1 : &tmA2);
+      tc::tma_load_2d(Jsm + (size_t)kt * Lay::kA, ma, tma_bar, kb * kBK, 0);
+    }
+    for (int kb = 0; kb < nk; ++kb)
+      tc::tma_load_2d(Ssm + (size_t)kb * Lay::kSk, &tmB, tma_bar, kb * kBK, (int)n0);
+  }
+  // epilogue lanes: row i, quarter q, column part
+  const int q = warp & 3;
+  const int part = (warp - 1) >> 2;
+  const int64_t i = 32 * q + lane;
+  const bool epi = warp >= 1;
+  const bool row_ok = epi && i < P.n;
+  const uint32_t lane_off = (uint32_t)(32 * q) << 16;
+  const uint32_t t_acc = tmem_base + lane_off + (uint32_t)(part * kCols);
+  const uint32_t t_th = t_acc + BN, t_m = t_acc + 2 * BN, t_v = t_acc + 3 * BN;
+  float h = 0.f, rs = 1.f;
+  int hi = 0;
+  if (row_ok) {
+    h = P.hf[i];
+    hi = P.hint[i];
+    if (P.rowscale) rs = P.rowscale[i];
+  }
+  const float chh = P.k.ch * h;
+  const float hm_pos = fmaf(P.k.ch, h, -P.k.mu), hm_neg = fmaf(P.k.ch, h, P.k.mu);
+  if (epi) {
+    // state of this warp's columns into tensor memory
+#pragma unroll 1
+    for (int c0 = 0; c0 < kCols; c0 += kChunk) {
+      uint32_t a[kChunk], bm[kChunk], c[kChunk];
+#pragma unroll
+      for (int j = 0; j < kChunk; ++j) {
+        const int64_t b = n0 + part * kCols + c0 + j;
+        const bool ok = row_ok && b < P.B;
+        const int64_t idx = b * P.ld + i;
+        a[j] = __float_as_uint(ok ? P.theta[idx] : 0.f);
+        bm[j] = __float_as_uint(ok ? P.m[idx] : 0.f);
+        c[j] = __float_as_uint(ok ? P.v[idx] : 0.f);
+      }
+      tc::tmem_st8(t_th + c0, a);
+      tc::tmem_st8(t_m + c0, bm);
+      tc::tmem_st8(t_v + c0, c);
+    }
+    tc::tmem_wait_st();
+  }
+  int ok = tc::mbar_wait(tma_bar, 0, nullptr, kWaitCycles) ? 1 : 0;
+  tc::fence_before_sync();
+  ok = __syncthreads_and(ok);
+  tc::fence_after_sync();
+  constexpr uint32_t idesc = tc::idesc_make(kBM, BN, FP8 ? 0u : 1u);
+  const bool loaded = ok != 0;
+  int64_t s = 0;
+  for (; s < K && ok; ++s) {
+    const long long t = t0 + s + 1;
+    const int cur = (int)(s & 1);
+    uint8_t* Scur = Ssm + (size_t)cur * kSbuf;
+    uint8_t* Snxt = Ssm + (size_t)(cur ^ 1) * kSbuf;
+    const bool last = s + 1 == K;
+    if (threadIdx.x == 0) {
+      for (int kt = 0; kt < nkt; ++kt) {
+        const int kb = kt % nk;
+        const uint32_t a0 = tc::smem_u32(Jsm + (size_t)kt * Lay::kA);
+        const uint32_t b0 = tc::smem_u32(Scur + (size_t)kb * Lay::kSk);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          if (FP8)
+            tc::mma_f8(tmem_base, tc::desc_k_sw128(a0 + 32 * k), tc::desc_k_sw128(b0 + 32 * k),
+                       idesc, (kt > 0 || k > 0) ? 1u : 0u);
+          else
+            tc::mma_f16(tmem_base, tc::desc_k_sw128(a0 + 32 * k), tc::desc_k_sw128(b0 + 32 * k),
+                        idesc, (kt > 0 || k > 0) ? 1u : 0u);
+        }
+      }
+      tc::mma_commit(acc_bar);
+    }
+    int wok = 1;
+    if (epi) {
+      const float2 bc = P.bias[t];
+      wok = tc::mbar_wait(acc_bar, (uint32_t)(s & 1), nullptr, kWaitCycles) ? 1 : 0;
+      tc::fence_after_sync();
+      if (wok) {
+#pragma unroll 1
+        for (int c0 = 0; c0 < kCols; c0 += kChunk) {
+          uint32_t r[kChunk], th[kChunk], mm[kChunk], vv[kChunk];
+          tc::tmem_ld8(t_acc + c0, r);
+          tc::tmem_ld8(t_th + c0, th);
+          tc::tmem_ld8(t_m + c0, mm);
+          tc::tmem_ld8(t_v + c0, vv);
+          tc::tmem_wait_ld();
+          int eq[kChunk];
+          float ef[kChunk];
+          uint32_t pos_bits = 0;
+#pragma unroll
+          for (int j = 0; j < kChunk; ++j) {
+            float tj = __uint_as_float(th[j]), mj = __uint_as_float(mm[j]), vj = __uint_as_float(vv[j]);
+            const float G = __uint_as_float(r[j]) * rs;
+            const bool pos = sin_nonneg(tj);  // the spin this step consumed
+            pos_bits |= (pos ? 1u : 0u) << j;
+            if (INT_E) eq[j] = __float_as_int(__fadd_rn(pos ? G : -G, 12582912.0f));
+            else ef[j] = (pos ? 1.f : -1.f) * fmaf(P.k.cq, G, chh);
+            const float F = fmaf(P.k.cq, G, pos ? hm_pos : hm_neg);
+            const float g = cos_proj(tj) * F;
+            tj = adam_update(P.k, bc.x, bc.y, g, tj, mj, vj);
+            th[j] = __float_as_uint(tj);
+            mm[j] = __float_as_uint(mj);
+            vv[j] = __float_as_uint(vj);
+          }
+          if (!last) {
+            tc::tmem_st8(t_th + c0, th);
+            tc::tmem_st8(t_m + c0, mm);
+            tc::tmem_st8(t_v + c0, vv);
+          }
+          const int bl0 = part * kCols + c0;  // local restart of column j = 0
+          if (row_ok) {
+            const int kb = (int)(i / kBK), kk = (int)(i % kBK);
+#pragma unroll
+            for (int j = 0; j < kChunk; ++j) {
+              const float tj = __uint_as_float(th[j]);
+              const bool sp = sin_nonneg(tj);
+              uint8_t* dst = Snxt + (size_t)kb * Lay::kSk + swz_offset(bl0 + j, kk, esize);
+              if (FP8) *dst = sp ? 0x38 : 0xB8;
+              else *reinterpret_cast<__nv_bfloat16*>(dst) = __float2bfloat16(sp ? 1.f : -1.f);
+              const int64_t b = n0 + bl0 + j;
+              if (last && b < P.B) {
+                const int64_t idx = b * P.ld + i;
+                P.theta[idx] = tj;
+                P.m[idx] = __uint_as_float(mm[j]);
+                P.v[idx] = __uint_as_float(vv[j]);
+              }
+            }
+          }
+          if (INT_E) {
+            int qv = 0, hv = 0;
+#pragma unroll
+            for (int j = 0; j < kChunk; ++j) {
+              const unsigned int sum = __reduce_add_sync(0xffffffffu, (unsigned int)eq[j]);
+              if (lane == j) qv = (int)(sum - 32u * 0x4B400000u);
+            }
+            if (P.has_h) {
+#pragma unroll
+              for (int j = 0; j < kChunk; ++j) {
+                const int sum = __reduce_add_sync(0xffffffffu, ((pos_bits >> j) & 1u) ? hi : -hi);
+                if (lane == j) hv = sum;
+              }
+            }
+            if (lane < kChunk) {
+              part_q[q * BN + bl0 + lane] = qv;
+              part_h[q * BN + bl0 + lane] = hv;
+            }
+          } else {
+            const float te = column_sums8(ef, lane);
+            if ((lane & 3) == 0) part_f[q * BN + bl0 + column_of_lane(lane)] = te;
+          }
+        }
+        tc::tmem_wait_st();
+      }
+    }
+    // the new spins are operands of the next MMAs; partials are complete
+    tc::fence_proxy_async_shared();
+    tc::fence_before_sync();
+    ok = __syncthreads_and(wok);
+    tc::fence_after_sync();
+    if (!ok) break;
+    // energies and bests of step t (sums in track_kernel's order over the 4 rows)
+    if (threadIdx.x < BN) {
+      const int b = threadIdx.x;
+      double E;
+      if (INT_E) {
+        const long long qs = (long long)part_q[b] + part_q[2 * BN + b] + part_q[BN + b] + part_q[3 * BN + b];
+        const long long hs = (long long)part_h[b] + part_h[2 * BN + b] + part_h[BN + b] + part_h[3 * BN + b];
+        E = R.cq * (double)qs + R.chs * (double)hs;
+      } else {
+        E = ((0.0 + (double)part_f[b]) + (0.0 + (double)part_f[2 * BN + b])) +
+            ((0.0 + (double)part_f[BN + b]) + (0.0 + (double)part_f[3 * BN + b]));
+      }
+      const bool better = E < bE[b] && n0 + b < P.B;
+      lE[b] = E;
+      if (better) {
+        bE[b] = E;
+        bT[b] = t;
+      }
+      imp[b] = better ? 1 : 0;
+    }
+    __syncthreads();
+    // copies of the improved restarts' consumed spins S_t (buffer cur)
+    if (epi) {
+      for (int b = warp - 1; b < BN; b += kSmallEpi) {
+        if (!imp[b]) continue;
+        int8_t* dst = R.best_s + (n0 + b) * R.bs_ld;
+        for (int ii = lane; ii < P.n; ii += 32) {
+          const uint8_t* src = Scur + (size_t)(ii / kBK) * Lay::kSk + swz_offset(b, ii % kBK, esize);
+          const bool pos = FP8 ? (*src == 0x38) : (__bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(src)) > 0.f);
+          dst[ii] = pos ? 1 : -1;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  // S_{t0+K+1} to its global slot, bests back to global, step counter
+  if (ok) {
+    uint8_t* Sfin = Ssm + (size_t)(K & 1) * kSbuf;
+    for (int64_t e = threadIdx.x; e < (int64_t)BN * P.n; e += blockDim.x) {
+      const int b = (int)(e / P.n), ii = (int)(e % P.n);
+      if (n0 + b >= P.B) continue;
+      const uint8_t* src = Sfin + (size_t)(ii / kBK) * Lay::kSk + swz_offset(b, ii % kBK, esize);
+      const int64_t idx = (n0 + b) * P.ld + ii;
+      if (FP8) static_cast<uint8_t*>(R.spins_out)[idx] = *src;
+      else static_cast<__nv_bfloat16*>(R.spins_out)[idx] = *reinterpret_cast<const __nv_bfloat16*>(src);
+    }
+    for (int b = threadIdx.x; b < BN; b += blockDim.x) {
+      const int64_t gb = n0 + b;
+      if (gb >= P.B) continue;
+      R.best_E[gb] = bE[b];
+      R.best_t[gb] = bT[b];
+      R.last_E[gb] = lE[b];
+    }
+    if (threadIdx.x == 0 && blockIdx.x == 0) const_cast<long long*>(P.counters)[0] = t0 + K;
+  } else if (threadIdx.x == 0) {
+    atomicExch(P.err, 5);
+    // copies and MMAs already issued must land before the CTA frees its memory
+    if (!loaded) tc::mbar_wait(tma_bar, 0, nullptr, kWaitCycles / 8);
+    else if (s < K) tc::mbar_wait(acc_bar, (uint32_t)(s & 1), nullptr, kWaitCycles / 8);
+  }
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem_base, kTmemCols);
+  }
+}
+
 struct TcState {
   CUtensorMap A[3];
   CUtensorMap B[3];   // one per spin slot, boxes of BN restarts (streaming kernel)
@@ -1064,6 +1399,8 @@ struct TcState {
   DevMem gsync;           // abort word + per-column barrier counters
   int emode = 0;          // resident epilogue's integer energy mode (0 F2I, 1 offset, 2 packed)
   int gn = 64;            // resident form: restarts per group (a CTA holds two groups)
+  bool small = false;     // small form (n <= 128): all of J per CTA, spins kept on chip
+  size_t small_bytes = 0;
   int jres = 0, nst = 0;  // resident form: J tiles kept in shared memory, stages
   uint32_t bars = 0;      // resident form: offset of the barrier block
   size_t res_bytes = 0;   // resident form: dynamic shared memory
@@ -1173,6 +1510,24 @@ int resident_launch_bn(ising_ds* ds, TcState* st, const TcResArgs& ra) {
   return st->fp8 ? resident_launch<BN, false, true>(ds, st, ra) : resident_launch<BN, false, false>(ds, st, ra);
 }
 
+template <int BN, bool INT_E, bool FP8>
+int small_launch(ising_ds* ds, TcState* st, const TcSmallArgs& a) {
+  auto kern = tc_small_kernel<BN, INT_E, FP8>;
+  ISING_CUDA(ds->ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)st->small_bytes));
+  kern<<<st->grid, kSmallThreads, st->small_bytes, ds->ctx->stream>>>(
+      st->A[0], st->A[1], st->A[2], st->B[(ds->t + 1) % 3], a);
+  ISING_CUDA(ds->ctx, cudaGetLastError());
+  return ISING_OK;
+}
+
+template <int BN>
+int small_launch_bn(ising_ds* ds, TcState* st, const TcSmallArgs& a) {
+  if (ds->int_energy)
+    return st->fp8 ? small_launch<BN, true, true>(ds, st, a) : small_launch<BN, true, false>(ds, st, a);
+  return st->fp8 ? small_launch<BN, false, true>(ds, st, a) : small_launch<BN, false, false>(ds, st, a);
+}
+
 // Abort word, then one arrival counter per restart group of each column, 128
 // bytes apart.
 static size_t gsync_bytes(const ising_ds* ds, const TcState* st) {
@@ -1254,7 +1609,21 @@ int tc_setup(ising_ds* ds) {
   // resident form when every (128 x 2 GN) tile gets its own co-resident CTA
   // (a tensor-memory kernel holds its SM alone): two groups of GN restarts
   // per CTA, 64 each, or 32 when B <= 64
-  if (!(ds->p.flags & ISING_DS_STREAMING) && !ds->relaxed()) {
+  // small form: n <= 128, every CTA self-contained (no co-residency needed)
+  if (!(ds->p.flags & (ISING_DS_STREAMING | ISING_DS_CONVERGE)) && !ds->relaxed() && ds->n <= kBM) {
+    const int bn = ds->B > 64 ? 128 : 64;
+    const int nk = ceil_div_i(ds->n, st->fp8 ? 128 : 64), nkt = nk * ds->planes;
+    const size_t bytes = (size_t)nkt * kBM * kRowBytes + 2 * (size_t)nk * bn * kRowBytes +
+                         (size_t)bn * (3 * 4 * 4 + 8 + 8 + 8 + 4) + 64 + 1024;
+    if (bytes <= (size_t)ctx->smem_optin) {
+      st->small = true;
+      st->resident = true;
+      st->BN = bn;
+      st->grid = ceil_div_i(ds->B, bn);
+      st->small_bytes = bytes;
+    }
+  }
+  if (!st->resident && !(ds->p.flags & ISING_DS_STREAMING) && !ds->relaxed()) {
     const int gn = ds->B > 64 ? 64 : 32;
     const int tiles = ceil_div_i(ds->n, kBM) * ceil_div_i(ds->B, 2 * gn);
     // shared memory: resident J tiles (as many as leave room for 4 stages of 2 k-blocks),
@@ -1281,9 +1650,9 @@ int tc_setup(ising_ds* ds) {
       }
     }
   }
-  if (st->resident) {
+  if (st->resident && !st->small) {
     ISING_TRY(dev_alloc(ctx, st->gsync, gsync_bytes(ds, st)));
-  } else {
+  } else if (!st->resident) {
     const int tiles = ceil_div_i(ds->n, kBM) * ceil_div_i(ds->B, st->BN);
     st->grid = std::max(1, std::min(tiles, ctx->sm_count));
   }
@@ -1297,7 +1666,7 @@ static int tc_maps(ising_ds* ds, TcState* st) {
   for (int s = 0; s < 3; ++s) {
     ISING_TRY(make_map(ds->ctx, &st->B[s], ds->spins[s].p, ds->n, ds->B, ds->ld,
                        st->fp8 ? 128 : 64, st->BN, st->fp8));
-    if (st->resident)
+    if (st->resident && !st->small)
       ISING_TRY(make_map(ds->ctx, &st->Bg[s], ds->spins[s].p, ds->n, ds->B, ds->ld,
                          st->fp8 ? 128 : 64, st->gn, st->fp8));
   }
@@ -1376,11 +1745,57 @@ bool tc_is_resident(ising_ds* ds) {
   return st && st->resident;
 }
 
+int tc_resident_form(ising_ds* ds) {
+  auto st = static_cast<TcState*>(ds->tc);
+  return !st || !st->resident ? 0 : (st->small ? 2 : 1);
+}
+
 int tc_run_resident(ising_ds* ds, int64_t steps) {
   auto st = static_cast<TcState*>(ds->tc);
   if (!st->maps_ready) {
     ISING_TRY(tc_maps(ds, st));
     st->maps_ready = true;
+  }
+  if (st->small) {
+    TcSmallArgs sa;
+    TcArgs& a = sa.P;
+    a.n = ds->n;
+    a.B = ds->B;
+    a.ld = ds->ld;
+    a.nk = ceil_div_i(ds->n, st->fp8 ? 128 : 64);
+    a.planes = ds->planes;
+    a.mtiles = 1;
+    a.ntiles = st->grid;
+    a.k = ds->k;
+    a.bias = ds->bias.as<float2>();
+    a.counters = ds->counters.as<long long>();
+    a.S = nullptr;
+    a.Snext = nullptr;
+    a.Xnext = nullptr;
+    a.rowscale = ds->rowscale.p ? ds->rowscale.as<float>() : nullptr;
+    a.theta = ds->theta.as<float>();
+    a.m = ds->m.as<float>();
+    a.v = ds->v.as<float>();
+    a.hf = ds->hf.as<float>();
+    a.hint = ds->hint.as<int32_t>();
+    a.qpart = a.hpart = nullptr;
+    a.epart = nullptr;
+    a.Gout = nullptr;
+    a.err = st->err.as<int>();
+    a.has_h = ds->inst.has_h ? 1 : 0;
+    a.gmagic = st->emode;
+    a.trace = nullptr;
+    sa.steps = steps;
+    sa.t0 = ds->t;
+    sa.spins_out = ds->spins[(ds->t + steps + 1) % 3].p;
+    sa.best_E = ds->best_E.as<double>();
+    sa.best_t = ds->best_t.as<long long>();
+    sa.best_s = ds->best_s.as<int8_t>();
+    sa.last_E = ds->last_E.as<double>();
+    sa.bs_ld = ds->bs_ld;
+    sa.cq = ds->inst.cq;
+    sa.chs = ds->inst.ch * std::ldexp(1.0, -ds->h_shift);
+    return st->BN == 128 ? small_launch_bn<128>(ds, st, sa) : small_launch_bn<64>(ds, st, sa);
   }
   ISING_CUDA(ds->ctx, cudaMemsetAsync(st->gsync.p, 0, gsync_bytes(ds, st), ds->ctx->stream));
   TcResArgs r;

@@ -164,6 +164,10 @@ __device__ __forceinline__ void tmem_wait_st() {
 
 // Orders this thread's generic-proxy global accesses with async-proxy (TMA)
 // accesses.
+__device__ __forceinline__ void fence_proxy_async_shared() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 __device__ __forceinline__ void fence_proxy_async_global() {
   asm volatile("fence.proxy.async.global;" ::: "memory");
 }

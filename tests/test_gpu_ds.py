@@ -28,6 +28,13 @@ def _instances():
         "torus_small": synth.torus_csr(10, 13, 5),
         "er_pendant_h": synth.er_pendant_csr(200, 3.0, 60, 3, 6, h_mode="int2"),
         "csr_float_h": synth.random_sparse_instance(170, 7, p=0.05, kind="float", h="float"),
+        # n <= 128: the tensor-core path's small form (one k-block in E4M3, one
+        # or two in BF16; 77 and 100 leave ragged row and K tails)
+        "er_small_int": synth.er_dense(77, 22, p=0.1, weights="pm1"),
+        "sk_small_h": synth.sk_dense(100, 21, 0.1, np.float32, h_std=math.sqrt(0.1)),
+        "rand_small_int_h": synth.random_sparse_instance(128, 23, p=0.15, kind="int", h="int",
+                                                         convention="paper", j_scale=0.5,
+                                                         layout="dense"),
     }
 
 
@@ -37,7 +44,9 @@ CASES = [("er_int", "fp32"), ("sk_float", "fp32"), ("sk_float_h", "fp32"),
          ("rand_int_h_paper", "fp32"), ("torus_small", "auto"), ("er_pendant_h", "auto"),
          ("csr_float_h", "auto"), ("er_int", "tc"), ("sk_float", "tc"), ("sk_float_h", "tc"),
          ("rand_int_h_paper", "tc"), ("er_int", "fp8"), ("rand_int_h_paper", "auto"),
-         ("er_int", "fp8-stream"), ("sk_float_h", "tc-stream"), ("rand_int_h_paper", "tc-stream")]
+         ("er_int", "fp8-stream"), ("sk_float_h", "tc-stream"), ("rand_int_h_paper", "tc-stream"),
+         ("er_small_int", "auto"), ("sk_small_h", "tc"), ("rand_small_int_h", "tc"),
+         ("sk_small_h", "fp32")]
 
 
 def _exact(inst):
@@ -192,13 +201,18 @@ def test_graph_replay_equals_step_by_step(gpu_ctx, name, prec):
 
 @pytest.mark.parametrize("name,prec,B", [("er_int", "fp8", 300), ("sk_float_h", "tc", 200),
                                          ("rand_int_h_paper", "tc", 1),
-                                         ("er_int", "fp8", 9000), ("sk_float_h", "tc", 9000)])
+                                         ("er_int", "fp8", 9000), ("sk_float_h", "tc", 9000),
+                                         ("er_small_int", "fp8", 1), ("er_small_int", "auto", 65),
+                                         ("rand_small_int_h", "tc", 64), ("sk_small_h", "tc", 300),
+                                         ("sk_small_h", "tc", 20000), ("er_small_int", "fp8", 20000)])
 def test_resident_equals_streaming(gpu_ctx, name, prec, B):
-    """The resident tensor-core form (state in tensor memory, one cooperative
-    launch for the whole run, tracking inside) gives the same state and bests
-    bit for bit as the streaming form (one launch per step). B = 9000 on two
-    row tiles makes 142 tiles of 128 restarts, nearly one per SM, with a
-    ragged last column."""
+    """The resident tensor-core forms (state in tensor memory, one launch for
+    the whole run, tracking inside) give the same state and bests bit for bit
+    as the streaming form (one launch per step). B = 9000 on two row tiles
+    makes 142 tiles of 128 restarts, nearly one per SM, with a ragged last
+    column. For n <= 128 the small form runs: B = 1, 64 and 65 take one or two
+    CTAs of 64 or 128 restarts, B = 20000 more CTAs than SMs (so CTAs start
+    after others have finished)."""
     inst = INSTANCES[name]
     T = 57
     a = api.Session(gpu_ctx, inst, restarts=B, steps=T, seed=4, precision=prec)
@@ -215,6 +229,7 @@ def test_resident_equals_streaming(gpu_ctx, name, prec, B):
     a.finish()
     b.finish()
     ra, rb = a.result(), b.result()
+    assert (ra["resident"], rb["resident"]) == (2 if inst.n <= 128 else 1, 0)
     assert ra["best_energy"] == rb["best_energy"]
     np.testing.assert_array_equal(ra["best_spins"], rb["best_spins"])
     a.close()
