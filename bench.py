@@ -508,7 +508,7 @@ def main():
             # float J as three BF16 planes: the tensor cores execute 3 x the
             # algorithmic flops counted here
             roof["operand_planes"] = 3
-        kname = "tc_resident_kernel" if st["resident"] else "tc_step_kernel"
+        kname = {0: "tc_step_kernel", 1: "tc_resident_kernel", 2: "tc_small_kernel"}[st["resident"]]
         ksrc = "paper_2312_05837_gb300/csrc/ds_tc.cu"
     else:  # plain FP32 FMA on the CUDA cores: 2 N^2 B flop per step
         alg = 2.0 * n_prof * n_prof * B

@@ -1057,10 +1057,13 @@ __global__ void __launch_bounds__(kThreads, 1)
 // needs nothing from other CTAs. The epilogue writes the next spins straight
 // into the shared-memory B operand, in the 128-byte swizzled layout the TMA
 // produces (16-byte chunk c of row r stored at chunk c ^ (r mod 8)); after a
-// proxy fence and a CTA barrier the tensor cores read them. Energies, bests
-// and the copies of improved spins stay inside the CTA: no grid barrier and
-// no global round trip per step. Warp 0 issues TMA and MMAs; warps 1..16 run
-// the epilogue (TMEM lane quarter warp mod 4).
+// proxy fence and the step's one CTA barrier the tensor cores read them. No
+// grid barrier and no global round trip per step: warp 0 issues TMA and MMAs
+// and, while the tensor cores run step s, turns the energy partials of step
+// s - 1 into energies and bests; warps 1..16 run the epilogue (TMEM lane
+// quarter warp mod 4) and keep, per column, the spins of the best step as bits
+// in a register (updated two steps late, when the improvement bits are known),
+// written to global memory once at the end of the launch.
 
 constexpr int kSmallEpi = 16;
 constexpr int kSmallThreads = 32 * (1 + kSmallEpi);
@@ -1102,7 +1105,8 @@ __global__ void __launch_bounds__(kSmallThreads, 1)
   constexpr int kBK = Lay::kBK;
   constexpr int esize = FP8 ? 1 : 2;
   constexpr uint32_t kTmemCols = 4 * BN;
-  constexpr int kCols = BN / 4;
+  constexpr int kCols = BN / 4;  // columns of one epilogue warp (8, 16 or 32)
+  constexpr int kWords = BN / 32;
   const TcArgs& P = R.P;
   const int nk = P.nk, nkt = P.nk * P.planes;
   extern __shared__ uint8_t smem_raw[];
@@ -1111,14 +1115,14 @@ __global__ void __launch_bounds__(kSmallThreads, 1)
   uint8_t* Jsm = smem;                                    // nkt x kA
   uint8_t* Ssm = Jsm + (size_t)nkt * Lay::kA;             // 2 buffers x nk x kSk
   const size_t kSbuf = (size_t)nk * Lay::kSk;
-  int* part_q = reinterpret_cast<int*>(Ssm + 2 * kSbuf);  // [4][BN]
-  int* part_h = part_q + 4 * BN;                          // [4][BN]
-  float* part_f = reinterpret_cast<float*>(part_h + 4 * BN);  // [4][BN]
-  double* bE = reinterpret_cast<double*>(part_f + 4 * BN);    // [BN] best energy
+  int* part_q = reinterpret_cast<int*>(Ssm + 2 * kSbuf);  // [2][4][BN] (slot s mod 2)
+  int* part_h = part_q + 8 * BN;                          // [2][4][BN]
+  float* part_f = reinterpret_cast<float*>(part_h + 8 * BN);  // [2][4][BN]
+  double* bE = reinterpret_cast<double*>(part_f + 8 * BN);    // [BN] best energy
   double* lE = bE + BN;                                       // [BN] last energy
   long long* bT = reinterpret_cast<long long*>(lE + BN);      // [BN] best step
-  int* imp = reinterpret_cast<int*>(bT + BN);                 // [BN] improved flags
-  uint64_t* tma_bar = reinterpret_cast<uint64_t*>(imp + BN);
+  uint32_t* imp = reinterpret_cast<uint32_t*>(bT + BN);       // [2][4] improvement bits
+  uint64_t* tma_bar = reinterpret_cast<uint64_t*>(imp + 8);
   uint64_t* acc_bar = tma_bar + 1;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_bar + 1);
 
@@ -1204,8 +1208,51 @@ __global__ void __launch_bounds__(kSmallThreads, 1)
   tc::fence_before_sync();
   ok = __syncthreads_and(ok);
   tc::fence_after_sync();
-  constexpr uint32_t idesc = tc::idesc_make(kBM, BN, FP8 ? 0u : 1u);
   const bool loaded = ok != 0;
+
+  // Energies and bests of step index e (E_{t0+e+1}) from partial slot e mod 2,
+  // one lane per restart (sums in track_kernel's order over the four lane
+  // quarters); the improvement bits go to imp[e mod 2]. Warp 0 runs this for
+  // step s - 1 while the tensor cores run step s.
+  auto track = [&](int64_t e) {
+    const int slot = (int)(e & 1);
+    const int* pq = part_q + slot * 4 * BN;
+    const int* ph = part_h + slot * 4 * BN;
+    const float* pf = part_f + slot * 4 * BN;
+#pragma unroll
+    for (int w = 0; w < kWords; ++w) {
+      const int b = 32 * w + lane;
+      double E;
+      if (INT_E) {
+        const long long qs = (long long)pq[b] + pq[2 * BN + b] + pq[BN + b] + pq[3 * BN + b];
+        const long long hs = (long long)ph[b] + ph[2 * BN + b] + ph[BN + b] + ph[3 * BN + b];
+        E = R.cq * (double)qs + R.chs * (double)hs;
+      } else {
+        E = ((0.0 + (double)pf[b]) + (0.0 + (double)pf[2 * BN + b])) +
+            ((0.0 + (double)pf[BN + b]) + (0.0 + (double)pf[3 * BN + b]));
+      }
+      const bool better = E < bE[b] && n0 + b < P.B;
+      lE[b] = E;
+      if (better) {
+        bE[b] = E;
+        bT[b] = t0 + e + 1;
+      }
+      const uint32_t bits = __ballot_sync(0xffffffffu, better);
+      if (lane == 0) imp[slot * 4 + w] = bits;
+    }
+  };
+  // This thread's columns of an improvement word of slot e mod 2.
+  auto imp_mask = [&](int64_t e) -> uint32_t {
+    const int c = part * kCols;
+    const uint32_t w = imp[(int)(e & 1) * 4 + (c >> 5)];
+    return kCols == 32 ? w : (w >> (c & 31)) & ((1u << (kCols & 31)) - 1u);
+  };
+  // spins consumed at steps s - 1 and s - 2 (bit c = column part * kCols + c),
+  // the best spins of each column, and which columns improved in this launch
+  uint32_t prev_bits = 0, prev2_bits = 0, best_bits = 0, any_bits = 0;
+  float2 bc = make_float2(0.f, 0.f);
+  if (epi && K > 0) bc = P.bias[t0 + 1];
+  constexpr uint32_t idesc = tc::idesc_make(kBM, BN, FP8 ? 0u : 1u);
   int64_t s = 0;
   for (; s < K && ok; ++s) {
     const long long t = t0 + s + 1;
@@ -1213,29 +1260,43 @@ __global__ void __launch_bounds__(kSmallThreads, 1)
     uint8_t* Scur = Ssm + (size_t)cur * kSbuf;
     uint8_t* Snxt = Ssm + (size_t)(cur ^ 1) * kSbuf;
     const bool last = s + 1 == K;
-    if (threadIdx.x == 0) {
-      for (int kt = 0; kt < nkt; ++kt) {
-        const int kb = kt % nk;
-        const uint32_t a0 = tc::smem_u32(Jsm + (size_t)kt * Lay::kA);
-        const uint32_t b0 = tc::smem_u32(Scur + (size_t)kb * Lay::kSk);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          if (FP8)
-            tc::mma_f8(tmem_base, tc::desc_k_sw128(a0 + 32 * k), tc::desc_k_sw128(b0 + 32 * k),
-                       idesc, (kt > 0 || k > 0) ? 1u : 0u);
-          else
-            tc::mma_f16(tmem_base, tc::desc_k_sw128(a0 + 32 * k), tc::desc_k_sw128(b0 + 32 * k),
-                        idesc, (kt > 0 || k > 0) ? 1u : 0u);
-        }
-      }
-      tc::mma_commit(acc_bar);
-    }
     int wok = 1;
-    if (epi) {
-      const float2 bc = P.bias[t];
+    if (warp == 0) {
+      if (lane == 0) {
+        for (int kt = 0; kt < nkt; ++kt) {
+          const int kb = kt % nk;
+          const uint32_t a0 = tc::smem_u32(Jsm + (size_t)kt * Lay::kA);
+          const uint32_t b0 = tc::smem_u32(Scur + (size_t)kb * Lay::kSk);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            if (FP8)
+              tc::mma_f8(tmem_base, tc::desc_k_sw128(a0 + 32 * k), tc::desc_k_sw128(b0 + 32 * k),
+                         idesc, (kt > 0 || k > 0) ? 1u : 0u);
+            else
+              tc::mma_f16(tmem_base, tc::desc_k_sw128(a0 + 32 * k), tc::desc_k_sw128(b0 + 32 * k),
+                          idesc, (kt > 0 || k > 0) ? 1u : 0u);
+          }
+        }
+        tc::mma_commit(acc_bar);
+      }
+      __syncwarp();
+      if (s >= 1) track(s - 1);
+    } else {
+      const float2 bcs = bc;
+      if (!last) bc = P.bias[t + 1];  // used by the next step
+      if (s >= 2) {
+        // the bests of step s - 2 are known now
+        const uint32_t mk = imp_mask(s - 2);
+        best_bits = (best_bits & ~mk) | (prev2_bits & mk);
+        any_bits |= mk;
+      }
       wok = tc::mbar_wait(acc_bar, (uint32_t)(s & 1), nullptr, kWaitCycles) ? 1 : 0;
       tc::fence_after_sync();
+      uint32_t cur_bits = 0;
       if (wok) {
+        int* pq = part_q + cur * 4 * BN;
+        int* ph = part_h + cur * 4 * BN;
+        float* pf = part_f + cur * 4 * BN;
 #pragma unroll 1
         for (int c0 = 0; c0 < kCols; c0 += kChunk) {
           uint32_t r[kChunk], th[kChunk], mm[kChunk], vv[kChunk];
@@ -1257,11 +1318,12 @@ __global__ void __launch_bounds__(kSmallThreads, 1)
             else ef[j] = (pos ? 1.f : -1.f) * fmaf(P.k.cq, G, chh);
             const float F = fmaf(P.k.cq, G, pos ? hm_pos : hm_neg);
             const float g = cos_proj(tj) * F;
-            tj = adam_update(P.k, bc.x, bc.y, g, tj, mj, vj);
+            tj = adam_update(P.k, bcs.x, bcs.y, g, tj, mj, vj);
             th[j] = __float_as_uint(tj);
             mm[j] = __float_as_uint(mj);
             vv[j] = __float_as_uint(vj);
           }
+          cur_bits |= pos_bits << c0;
           if (!last) {
             tc::tmem_st8(t_th + c0, th);
             tc::tmem_st8(t_m + c0, mm);
@@ -1301,57 +1363,45 @@ __global__ void __launch_bounds__(kSmallThreads, 1)
               }
             }
             if (lane < kChunk) {
-              part_q[q * BN + bl0 + lane] = qv;
-              part_h[q * BN + bl0 + lane] = hv;
+              pq[q * BN + bl0 + lane] = qv;
+              ph[q * BN + bl0 + lane] = hv;
             }
           } else {
             const float te = column_sums8(ef, lane);
-            if ((lane & 3) == 0) part_f[q * BN + bl0 + column_of_lane(lane)] = te;
+            if ((lane & 3) == 0) pf[q * BN + bl0 + column_of_lane(lane)] = te;
           }
         }
         tc::tmem_wait_st();
       }
+      prev2_bits = prev_bits;
+      prev_bits = cur_bits;
     }
     // the new spins are operands of the next MMAs; partials are complete
     tc::fence_proxy_async_shared();
     tc::fence_before_sync();
     ok = __syncthreads_and(wok);
     tc::fence_after_sync();
-    if (!ok) break;
-    // energies and bests of step t (sums in track_kernel's order over the 4 rows)
-    if (threadIdx.x < BN) {
-      const int b = threadIdx.x;
-      double E;
-      if (INT_E) {
-        const long long qs = (long long)part_q[b] + part_q[2 * BN + b] + part_q[BN + b] + part_q[3 * BN + b];
-        const long long hs = (long long)part_h[b] + part_h[2 * BN + b] + part_h[BN + b] + part_h[3 * BN + b];
-        E = R.cq * (double)qs + R.chs * (double)hs;
-      } else {
-        E = ((0.0 + (double)part_f[b]) + (0.0 + (double)part_f[2 * BN + b])) +
-            ((0.0 + (double)part_f[BN + b]) + (0.0 + (double)part_f[3 * BN + b]));
-      }
-      const bool better = E < bE[b] && n0 + b < P.B;
-      lE[b] = E;
-      if (better) {
-        bE[b] = E;
-        bT[b] = t;
-      }
-      imp[b] = better ? 1 : 0;
-    }
+  }
+  if (ok && K > 0) {
+    // the last step's energies, then the bests of the last two steps
+    if (warp == 0) track(K - 1);
     __syncthreads();
-    // copies of the improved restarts' consumed spins S_t (buffer cur)
     if (epi) {
-      for (int b = warp - 1; b < BN; b += kSmallEpi) {
-        if (!imp[b]) continue;
-        int8_t* dst = R.best_s + (n0 + b) * R.bs_ld;
-        for (int ii = lane; ii < P.n; ii += 32) {
-          const uint8_t* src = Scur + (size_t)(ii / kBK) * Lay::kSk + swz_offset(b, ii % kBK, esize);
-          const bool pos = FP8 ? (*src == 0x38) : (__bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(src)) > 0.f);
-          dst[ii] = pos ? 1 : -1;
+      if (K >= 2) {
+        const uint32_t mk = imp_mask(K - 2);
+        best_bits = (best_bits & ~mk) | (prev2_bits & mk);
+        any_bits |= mk;
+      }
+      const uint32_t mk = imp_mask(K - 1);
+      best_bits = (best_bits & ~mk) | (prev_bits & mk);
+      any_bits |= mk;
+      if (row_ok) {
+        for (int c = 0; c < kCols; ++c) {
+          const int64_t b = n0 + part * kCols + c;
+          if ((any_bits >> c) & 1u) R.best_s[b * R.bs_ld + i] = ((best_bits >> c) & 1u) ? 1 : -1;
         }
       }
     }
-    __syncthreads();
   }
   // S_{t0+K+1} to its global slot, bests back to global, step counter
   if (ok) {
@@ -1398,9 +1448,10 @@ struct TcState {
   bool resident = false;  // one tile per CTA, state kept in tensor memory
   DevMem gsync;           // abort word + per-column barrier counters
   int emode = 0;          // resident epilogue's integer energy mode (0 F2I, 1 offset, 2 packed)
-  int gn = 64;            // resident form: restarts per group (a CTA holds two groups)
+  int gn = 64;            // resident forms: restarts per group (two per CTA; small form: one)
   bool small = false;     // small form (n <= 128): all of J per CTA, spins kept on chip
   size_t small_bytes = 0;
+  int small_grid = 0;     // small form: CTAs (one per block of gn restarts)
   int jres = 0, nst = 0;  // resident form: J tiles kept in shared memory, stages
   uint32_t bars = 0;      // resident form: offset of the barrier block
   size_t res_bytes = 0;   // resident form: dynamic shared memory
@@ -1515,8 +1566,8 @@ int small_launch(ising_ds* ds, TcState* st, const TcSmallArgs& a) {
   auto kern = tc_small_kernel<BN, INT_E, FP8>;
   ISING_CUDA(ds->ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)st->small_bytes));
-  kern<<<st->grid, kSmallThreads, st->small_bytes, ds->ctx->stream>>>(
-      st->A[0], st->A[1], st->A[2], st->B[(ds->t + 1) % 3], a);
+  kern<<<st->small_grid, kSmallThreads, st->small_bytes, ds->ctx->stream>>>(
+      st->A[0], st->A[1], st->A[2], st->Bg[(ds->t + 1) % 3], a);
   ISING_CUDA(ds->ctx, cudaGetLastError());
   return ISING_OK;
 }
@@ -1609,17 +1660,23 @@ int tc_setup(ising_ds* ds) {
   // resident form when every (128 x 2 GN) tile gets its own co-resident CTA
   // (a tensor-memory kernel holds its SM alone): two groups of GN restarts
   // per CTA, 64 each, or 32 when B <= 64
-  // small form: n <= 128, every CTA self-contained (no co-residency needed)
+  // small form: n <= 128, every CTA self-contained (no co-residency needed);
+  // the narrowest block of restarts (32, 64 or 128) that still fits one wave
   if (!(ds->p.flags & (ISING_DS_STREAMING | ISING_DS_CONVERGE)) && !ds->relaxed() && ds->n <= kBM) {
-    const int bn = ds->B > 64 ? 128 : 64;
+    int bn = 128;
+    for (int c : {32, 64})
+      if (ceil_div_i(ds->B, c) <= ctx->sm_count) {
+        bn = c;
+        break;
+      }
     const int nk = ceil_div_i(ds->n, st->fp8 ? 128 : 64), nkt = nk * ds->planes;
     const size_t bytes = (size_t)nkt * kBM * kRowBytes + 2 * (size_t)nk * bn * kRowBytes +
-                         (size_t)bn * (3 * 4 * 4 + 8 + 8 + 8 + 4) + 64 + 1024;
+                         (size_t)bn * (2 * 3 * 4 * 4 + 8 + 8 + 8) + 32 + 64 + 1024;
     if (bytes <= (size_t)ctx->smem_optin) {
       st->small = true;
       st->resident = true;
-      st->BN = bn;
-      st->grid = ceil_div_i(ds->B, bn);
+      st->gn = bn;
+      st->small_grid = ceil_div_i(ds->B, bn);
       st->small_bytes = bytes;
     }
   }
@@ -1652,7 +1709,8 @@ int tc_setup(ising_ds* ds) {
   }
   if (st->resident && !st->small) {
     ISING_TRY(dev_alloc(ctx, st->gsync, gsync_bytes(ds, st)));
-  } else if (!st->resident) {
+  } else {
+    // streaming launches (and, in the small form, the final evaluation)
     const int tiles = ceil_div_i(ds->n, kBM) * ceil_div_i(ds->B, st->BN);
     st->grid = std::max(1, std::min(tiles, ctx->sm_count));
   }
@@ -1666,7 +1724,7 @@ static int tc_maps(ising_ds* ds, TcState* st) {
   for (int s = 0; s < 3; ++s) {
     ISING_TRY(make_map(ds->ctx, &st->B[s], ds->spins[s].p, ds->n, ds->B, ds->ld,
                        st->fp8 ? 128 : 64, st->BN, st->fp8));
-    if (st->resident && !st->small)
+    if (st->resident)
       ISING_TRY(make_map(ds->ctx, &st->Bg[s], ds->spins[s].p, ds->n, ds->B, ds->ld,
                          st->fp8 ? 128 : 64, st->gn, st->fp8));
   }
@@ -1765,7 +1823,7 @@ int tc_run_resident(ising_ds* ds, int64_t steps) {
     a.nk = ceil_div_i(ds->n, st->fp8 ? 128 : 64);
     a.planes = ds->planes;
     a.mtiles = 1;
-    a.ntiles = st->grid;
+    a.ntiles = st->small_grid;
     a.k = ds->k;
     a.bias = ds->bias.as<float2>();
     a.counters = ds->counters.as<long long>();
@@ -1795,7 +1853,8 @@ int tc_run_resident(ising_ds* ds, int64_t steps) {
     sa.bs_ld = ds->bs_ld;
     sa.cq = ds->inst.cq;
     sa.chs = ds->inst.ch * std::ldexp(1.0, -ds->h_shift);
-    return st->BN == 128 ? small_launch_bn<128>(ds, st, sa) : small_launch_bn<64>(ds, st, sa);
+    return st->gn == 128 ? small_launch_bn<128>(ds, st, sa)
+                         : (st->gn == 64 ? small_launch_bn<64>(ds, st, sa) : small_launch_bn<32>(ds, st, sa));
   }
   ISING_CUDA(ds->ctx, cudaMemsetAsync(st->gsync.p, 0, gsync_bytes(ds, st), ds->ctx->stream));
   TcResArgs r;

@@ -204,15 +204,17 @@ def test_graph_replay_equals_step_by_step(gpu_ctx, name, prec):
                                          ("er_int", "fp8", 9000), ("sk_float_h", "tc", 9000),
                                          ("er_small_int", "fp8", 1), ("er_small_int", "auto", 65),
                                          ("rand_small_int_h", "tc", 64), ("sk_small_h", "tc", 300),
-                                         ("sk_small_h", "tc", 20000), ("er_small_int", "fp8", 20000)])
+                                         ("er_small_int", "fp8", 6000), ("sk_small_h", "tc", 20000),
+                                         ("er_small_int", "fp8", 20000)])
 def test_resident_equals_streaming(gpu_ctx, name, prec, B):
     """The resident tensor-core forms (state in tensor memory, one launch for
     the whole run, tracking inside) give the same state and bests bit for bit
     as the streaming form (one launch per step). B = 9000 on two row tiles
     makes 142 tiles of 128 restarts, nearly one per SM, with a ragged last
-    column. For n <= 128 the small form runs: B = 1, 64 and 65 take one or two
-    CTAs of 64 or 128 restarts, B = 20000 more CTAs than SMs (so CTAs start
-    after others have finished)."""
+    column. For n <= 128 the small form runs with blocks of 32 restarts up to
+    B = 32 x SMs (B = 1, 64, 65, 300: one to ten CTAs, ragged), of 64 beyond
+    (B = 6000) and of 128 beyond 64 x SMs (B = 20000: more CTAs than SMs, so
+    CTAs start after others have finished)."""
     inst = INSTANCES[name]
     T = 57
     a = api.Session(gpu_ctx, inst, restarts=B, steps=T, seed=4, precision=prec)
