@@ -66,6 +66,7 @@ struct TcArgs {
   int has_h;
   int gmagic;  // resident epilogue's integer energy mode (EMODE of resident_chunks)
   unsigned long long* trace;  // per-CTA role timeline (profiling), or null
+  int nfull;   // streaming kernel: whole k-blocks loadable in pairs (0: never pair)
 };
 
 __device__ __forceinline__ unsigned long long now_ns() {
@@ -82,11 +83,16 @@ __device__ __forceinline__ unsigned long long now_ns() {
     if (P.trace) P.trace[(size_t)blockIdx.x * 8 + (slot)] = now_ns();                \
   } while (0)
 
+// Streaming form: for BN <= 128 stages of two k-blocks [J, J, S, S], so that
+// two whole k-blocks of one plane arrive by one copy per operand (a thread
+// issues one TMA copy per ~250 cycles whatever its size); for BN = 256 such
+// stages would leave room for two only, so there a stage is one k-block.
 template <int BN>
 struct TcLayout {
+  static constexpr int kKps = BN >= 256 ? 1 : 2;
   static constexpr uint32_t kA = kBM * kRowBytes;
   static constexpr uint32_t kB = BN * kRowBytes;
-  static constexpr uint32_t kStage = kA + kB;
+  static constexpr uint32_t kStage = kKps * (kA + kB);
   static constexpr int kStages = (200 * 1024) / kStage;
   static constexpr uint32_t kBars = kStages * kStage;  // barrier block
   static constexpr uint32_t kBytes = kBars + 256 + 1024;  // + alignment slack
@@ -132,7 +138,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc_step_kernel(const __grid_constant__ CUtensorMap tmA0,
                    const __grid_constant__ CUtensorMap tmA1,
                    const __grid_constant__ CUtensorMap tmA2,
-                   const __grid_constant__ CUtensorMap tmB, const TcArgs P) {
+                   const __grid_constant__ CUtensorMap tmB,
+                   const __grid_constant__ CUtensorMap tmJ2_0,
+                   const __grid_constant__ CUtensorMap tmJ2_1,
+                   const __grid_constant__ CUtensorMap tmJ2_2,
+                   const __grid_constant__ CUtensorMap tmS2, const TcArgs P) {
   using Lay = TcLayout<BN>;
   constexpr int STAGES = Lay::kStages;
   constexpr int kBK = FP8 ? 128 : 64;  // elements per 128-byte row
@@ -150,7 +160,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
-      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&full[s], 2);  // the J and the S producer
       tc::mbar_init(&empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
@@ -165,10 +175,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc::tmem_alloc(tmem_slot, 2 * BN);
     tc::fence_before_sync();
   }
-  if (warp == 0 && lane == 0) {
-    tc::prefetch_map(&tmA0);
-    tc::prefetch_map(&tmB);
-  }
+  if (warp == 0 && lane == 0) tc::prefetch_map(&tmA0);
+  if (warp == 2 && lane == 0) tc::prefetch_map(&tmB);
   __syncthreads();
   tc::fence_after_sync();
   if (threadIdx.x == 0) ISING_TRACE(0);
@@ -176,34 +184,57 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int total = P.mtiles * P.ntiles;
   const int nkt = P.nk * P.planes;
 
-  if (warp == 0) {
+  if (warp == 0 || warp == 2) {
     if (lane == 0) {
-      // ------------------------------------------------ TMA producer
+      // ------------------------------------------------ TMA producers
+      // warp 0 copies the J tiles, warp 2 the S tiles of each stage (one
+      // thread issues a TMA copy only every ~250 cycles); each arrives on the
+      // stage's full barrier with its own byte count
+      const bool jside = warp == 0;
       uint32_t stage = 0, phase = 0;
       int issued = 0;
       bool ok = true;
       for (int tl = blockIdx.x; tl < total && ok; tl += gridDim.x) {
         const int m0 = (tl % P.mtiles) * kBM;
         const int n0 = (tl / P.mtiles) * BN;
-        for (int kt = 0; kt < nkt; ++kt) {
+        for (int kt0 = 0; kt0 < nkt; kt0 += Lay::kKps) {
           if (!tc::mbar_wait(&empty[stage], phase ^ 1, abort_flag, kWaitCycles)) {
             ok = false;
             break;
           }
           uint8_t* sa = smem + stage * Lay::kStage;
-          tc::mbar_expect_tx(&full[stage], Lay::kStage);
-          const int plane = kt / P.nk, kb = kt - plane * P.nk;
-          const CUtensorMap* ma = plane == 0 ? &tmA0 : (plane == 1 ? &tmA1 : &tmA2);
-          tc::tma_load_2d(sa, ma, &full[stage], kb * kBK, m0);
-          tc::tma_load_2d(sa + Lay::kA, &tmB, &full[stage], kb * kBK, n0);
-          if (issued == 0) ISING_TRACE(1);
+          const int cnt = nkt - kt0 < Lay::kKps ? nkt - kt0 : Lay::kKps;
+          tc::mbar_expect_tx(&full[stage], (uint32_t)cnt * (jside ? Lay::kA : Lay::kB));
+          const int plane0 = kt0 / P.nk, kb0 = kt0 - plane0 * P.nk;
+          if (Lay::kKps == 2 && kb0 + 1 < P.nfull) {
+            // two whole k-blocks of one plane: one copy per operand
+            if (jside) {
+              const CUtensorMap* ma = plane0 == 0 ? &tmJ2_0 : (plane0 == 1 ? &tmJ2_1 : &tmJ2_2);
+              tc::tma_load_3d(sa, ma, &full[stage], 0, m0, kb0);
+            } else {
+              tc::tma_load_3d(sa + Lay::kKps * Lay::kA, &tmS2, &full[stage], 0, n0, kb0);
+            }
+          } else {
+            for (int u = 0; u < cnt; ++u) {
+              const int kt = kt0 + u;
+              const int plane = kt / P.nk, kb = kt - plane * P.nk;
+              if (jside) {
+                const CUtensorMap* ma = plane == 0 ? &tmA0 : (plane == 1 ? &tmA1 : &tmA2);
+                tc::tma_load_2d(sa + u * Lay::kA, ma, &full[stage], kb * kBK, m0);
+              } else {
+                tc::tma_load_2d(sa + Lay::kKps * Lay::kA + u * Lay::kB, &tmB, &full[stage], kb * kBK, n0);
+              }
+            }
+          }
+          if (issued == 0 && jside) ISING_TRACE(1);
           ++issued;
           if (++stage == STAGES) { stage = 0; phase ^= 1; }
         }
       }
-      ISING_TRACE(2);
+      if (jside) ISING_TRACE(2);
       if (!ok) {
-        // let the copies already issued land before the CTA exits
+        // let the copies already issued land before the CTA exits (a phase
+        // the other producer never joined gives up after the bounded wait)
         int back = issued < STAGES ? issued : STAGES;
         uint32_t s = stage, ph = phase;
         for (int q = 0; q < back; ++q) {
@@ -229,23 +260,29 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         tc::fence_after_sync();
         const uint32_t d = tmem_base + (uint32_t)(buf * BN);
-        for (int kt = 0; kt < nkt; ++kt) {
+        for (int kt0 = 0; kt0 < nkt; kt0 += Lay::kKps) {
           if (!tc::mbar_wait(&full[stage], phase, abort_flag, kWaitCycles)) {
             ok = false;
             break;
           }
           tc::fence_after_sync();
-          if (it == 0 && kt == 0) ISING_TRACE(3);
-          const uint32_t a0 = tc::smem_u32(smem + stage * Lay::kStage);
-          const uint32_t b0 = a0 + Lay::kA;
+          if (it == 0 && kt0 == 0) ISING_TRACE(3);
+          const uint32_t sb = tc::smem_u32(smem + stage * Lay::kStage);
 #pragma unroll
-          for (int k = 0; k < 4; ++k) {  // 32 bytes of K per MMA (16 BF16 or 32 E4M3)
-            if (FP8)
-              tc::mma_f8(d, tc::desc_k_sw128(a0 + 32 * k), tc::desc_k_sw128(b0 + 32 * k), idesc,
-                         (kt > 0 || k > 0) ? 1u : 0u);
-            else
-              tc::mma_f16(d, tc::desc_k_sw128(a0 + 32 * k), tc::desc_k_sw128(b0 + 32 * k), idesc,
-                          (kt > 0 || k > 0) ? 1u : 0u);
+          for (int u = 0; u < Lay::kKps; ++u) {
+            const int kt = kt0 + u;
+            if (kt >= nkt) break;
+            const uint32_t a0 = sb + u * Lay::kA;
+            const uint32_t b0 = sb + Lay::kKps * Lay::kA + u * Lay::kB;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {  // 32 bytes of K per MMA (16 BF16 or 32 E4M3)
+              if (FP8)
+                tc::mma_f8(d, tc::desc_k_sw128(a0 + 32 * k), tc::desc_k_sw128(b0 + 32 * k), idesc,
+                           (kt > 0 || k > 0) ? 1u : 0u);
+              else
+                tc::mma_f16(d, tc::desc_k_sw128(a0 + 32 * k), tc::desc_k_sw128(b0 + 32 * k), idesc,
+                            (kt > 0 || k > 0) ? 1u : 0u);
+            }
           }
           tc::mma_commit(&empty[stage]);
           if (++stage == STAGES) { stage = 0; phase ^= 1; }
@@ -502,6 +539,7 @@ struct TcResArgs {
   int nst;             // pipeline stages after them
   uint32_t bars;       // shared-memory offset of the barrier block
   int slice;           // restarts of a group tracked per CTA of its column
+  int nfull;           // k-blocks lying wholly below column n (pairs of them load as one box)
 };
 
 // Best tracking of step t for restarts [b0, b1) by one warp, a lane per
@@ -726,7 +764,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                        const __grid_constant__ CUtensorMap tmA2,
                        const __grid_constant__ CUtensorMap tmB0,
                        const __grid_constant__ CUtensorMap tmB1,
-                       const __grid_constant__ CUtensorMap tmB2, const TcResArgs R) {
+                       const __grid_constant__ CUtensorMap tmB2,
+                       const __grid_constant__ CUtensorMap tmJ2_0,
+                       const __grid_constant__ CUtensorMap tmJ2_1,
+                       const __grid_constant__ CUtensorMap tmJ2_2,
+                       const __grid_constant__ CUtensorMap tmS2_0,
+                       const __grid_constant__ CUtensorMap tmS2_1,
+                       const __grid_constant__ CUtensorMap tmS2_2, const TcResArgs R) {
   const TcArgs& P = R.P;
   using Lay = ResLayout<GN>;
   const int STAGES = R.nst;
@@ -812,6 +856,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const long long t = t0 + s + 1;
         const int slot = (int)(t % 3);
         const CUtensorMap* mb = slot == 0 ? &tmB0 : (slot == 1 ? &tmB1 : &tmB2);
+        const CUtensorMap* mb2 = slot == 0 ? &tmS2_0 : (slot == 1 ? &tmS2_1 : &tmS2_2);
         const int nb = (int)(n0 + g * GN);
         if (s > 0) {
           // S_t of the group exists once every CTA of its column is through step t - 1
@@ -835,16 +880,30 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (kt < nkt) bytes += kt < jres ? Lay::kB : Lay::kA + Lay::kB;
           }
           tc::mbar_expect_tx(&full[stage], bytes);
-#pragma unroll
-          for (int u = 0; u < Lay::kKps; ++u) {
-            const int kt = kt0 + u;
-            if (kt >= nkt) break;
-            const int plane = kt / P.nk, kb = kt - plane * P.nk;
-            if (kt >= jres) {
-              const CUtensorMap* ma = plane == 0 ? &tmA0 : (plane == 1 ? &tmA1 : &tmA2);
-              tc::tma_load_2d(sa + u * Lay::kA, ma, &full[stage], kb * kBK, (int)m0);
+          const int plane0 = kt0 / P.nk, kb0 = kt0 - plane0 * P.nk;
+          if (kb0 + 1 < R.nfull) {
+            // two whole k-blocks of one plane: one box each for J and S (the
+            // issue of a TMA instruction, not its bytes, paces this thread)
+            if (kt0 >= jres) {
+              const CUtensorMap* ma = plane0 == 0 ? &tmJ2_0 : (plane0 == 1 ? &tmJ2_1 : &tmJ2_2);
+              tc::tma_load_3d(sa, ma, &full[stage], 0, (int)m0, kb0);
+            } else if (kt0 + 1 >= jres) {
+              const CUtensorMap* ma = plane0 == 0 ? &tmA0 : (plane0 == 1 ? &tmA1 : &tmA2);
+              tc::tma_load_2d(sa + Lay::kA, ma, &full[stage], (kb0 + 1) * kBK, (int)m0);
             }
-            tc::tma_load_2d(sa + Lay::kKps * Lay::kA + u * Lay::kB, mb, &full[stage], kb * kBK, nb);
+            tc::tma_load_3d(sa + Lay::kKps * Lay::kA, mb2, &full[stage], 0, nb, kb0);
+          } else {
+#pragma unroll
+            for (int u = 0; u < Lay::kKps; ++u) {
+              const int kt = kt0 + u;
+              if (kt >= nkt) break;
+              const int plane = kt / P.nk, kb = kt - plane * P.nk;
+              if (kt >= jres) {
+                const CUtensorMap* ma = plane == 0 ? &tmA0 : (plane == 1 ? &tmA1 : &tmA2);
+                tc::tma_load_2d(sa + u * Lay::kA, ma, &full[stage], kb * kBK, (int)m0);
+              }
+              tc::tma_load_2d(sa + Lay::kKps * Lay::kA + u * Lay::kB, mb, &full[stage], kb * kBK, nb);
+            }
           }
           ++issued;
           if (++stage == (uint32_t)STAGES) { stage = 0; phase ^= 1; }
@@ -1439,6 +1498,11 @@ struct TcState {
   CUtensorMap A[3];
   CUtensorMap B[3];   // one per spin slot, boxes of BN restarts (streaming kernel)
   CUtensorMap Bg[3];  // one per spin slot, boxes of one restart group (resident kernel)
+  // resident kernel: views of J (per plane) and of the spin slots as
+  // [k-block][row][128 B] with boxes of two whole k-blocks
+  CUtensorMap J2[3], S2[3];
+  CUtensorMap SP[3];  // streaming kernel: the spin slots' pair views, boxes of BN restarts
+  int nfull = 0;      // k-blocks lying wholly below column n (0 in the small form)
   CUtensorMap Bx[2];  // relaxed mode: one per slot of x = sin(theta), boxes of BN restarts
   int BN = 128;
   size_t smem = 0;
@@ -1490,8 +1554,30 @@ int make_map(ising_ctx* ctx, CUtensorMap* map, const void* base, int64_t cols, i
   return ISING_OK;
 }
 
+// View of a [rows][ld] operand as (128-byte column chunk, row, k-block) over
+// its first `nfull` whole k-blocks, with boxes of two k-blocks: one copy then
+// fills two consecutive k-block tiles of a stage (the k-block stride is 128
+// bytes, so a box never reaches past column nfull * 128 bytes, all below n).
+int make_map_pairs(ising_ctx* ctx, CUtensorMap* map, const void* base, int64_t nfull, int64_t rows,
+                   int64_t ld, int box_rows, bool fp8) {
+  auto fn = encode_fn();
+  if (!fn) return fail(ctx, ISING_ECUDA, "cuTensorMapEncodeTiled is unavailable");
+  const int es = fp8 ? 1 : 2;
+  cuuint64_t dims[3] = {(cuuint64_t)(kRowBytes / es), (cuuint64_t)rows, (cuuint64_t)nfull};
+  cuuint64_t strides[2] = {(cuuint64_t)(ld * es), (cuuint64_t)kRowBytes};
+  cuuint32_t box[3] = {(cuuint32_t)(kRowBytes / es), (cuuint32_t)box_rows, 2};
+  cuuint32_t est[3] = {1, 1, 1};
+  CUresult r = fn(map, fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3,
+                  const_cast<void*>(base), dims, strides, box, est, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(ctx, ISING_ECUDA, "cuTensorMapEncodeTiled (pairs) failed (%d)", (int)r);
+  return ISING_OK;
+}
+
 template <int BN, int MODE, bool INT_E, bool FP8>
-int launch_bn(ising_ds* ds, TcState* st, const TcArgs& a, const CUtensorMap& mB) {
+int launch_bn(ising_ds* ds, TcState* st, const TcArgs& a, const CUtensorMap& mB,
+              const CUtensorMap& mS2) {
   auto kern = tc_step_kernel<BN, MODE, INT_E, FP8>;
   const size_t smem = TcLayout<BN>::kBytes;
   static bool attr_set = false;  // per instantiation
@@ -1500,31 +1586,35 @@ int launch_bn(ising_ds* ds, TcState* st, const TcArgs& a, const CUtensorMap& mB)
                                              (int)smem));
     attr_set = true;
   }
-  kern<<<st->grid, kThreads, smem, ds->ctx->stream>>>(st->A[0], st->A[1], st->A[2], mB, a);
+  kern<<<st->grid, kThreads, smem, ds->ctx->stream>>>(st->A[0], st->A[1], st->A[2], mB, st->J2[0],
+                                                       st->J2[1], st->J2[2], mS2, a);
   ISING_CUDA(ds->ctx, cudaGetLastError());
   return ISING_OK;
 }
 
 template <int MODE, bool INT_E, bool FP8>
-int launch_bn_sel(ising_ds* ds, TcState* st, const TcArgs& a, const CUtensorMap& mB) {
+int launch_bn_sel(ising_ds* ds, TcState* st, const TcArgs& a, const CUtensorMap& mB,
+                  const CUtensorMap& mS2) {
   switch (st->BN) {
-    case 256: return launch_bn<256, MODE, INT_E, FP8>(ds, st, a, mB);
-    case 64: return launch_bn<64, MODE, INT_E, FP8>(ds, st, a, mB);
-    default: return launch_bn<128, MODE, INT_E, FP8>(ds, st, a, mB);
+    case 256: return launch_bn<256, MODE, INT_E, FP8>(ds, st, a, mB, mS2);
+    case 64: return launch_bn<64, MODE, INT_E, FP8>(ds, st, a, mB, mS2);
+    default: return launch_bn<128, MODE, INT_E, FP8>(ds, st, a, mB, mS2);
   }
 }
 
 template <int MODE, bool INT_E>
-int launch_mode(ising_ds* ds, TcState* st, const TcArgs& a, const CUtensorMap& mB) {
-  return st->fp8 ? launch_bn_sel<MODE, INT_E, true>(ds, st, a, mB)
-                 : launch_bn_sel<MODE, INT_E, false>(ds, st, a, mB);
+int launch_mode(ising_ds* ds, TcState* st, const TcArgs& a, const CUtensorMap& mB,
+                const CUtensorMap& mS2) {
+  return st->fp8 ? launch_bn_sel<MODE, INT_E, true>(ds, st, a, mB, mS2)
+                 : launch_bn_sel<MODE, INT_E, false>(ds, st, a, mB, mS2);
 }
 
 // Relaxed-product update: BF16 operands only (x in E4M3 would be too coarse).
 template <bool INT_E>
-int launch_relaxed(ising_ds* ds, TcState* st, const TcArgs& a, const CUtensorMap& mB) {
+int launch_relaxed(ising_ds* ds, TcState* st, const TcArgs& a, const CUtensorMap& mB,
+                   const CUtensorMap& mS2) {
   if (st->fp8) return fail(ds->ctx, ISING_ENOTSUP, "relaxed product needs BF16 operands");
-  return launch_bn_sel<kModeRelaxed, INT_E, false>(ds, st, a, mB);
+  return launch_bn_sel<kModeRelaxed, INT_E, false>(ds, st, a, mB, mS2);
 }
 
 }  // namespace
@@ -1540,7 +1630,8 @@ int resident_attr(ising_ctx* ctx, size_t smem, int* blocks_per_sm) {
 template <int GN, bool INT_E, bool FP8>
 int resident_launch(ising_ds* ds, TcState* st, const TcResArgs& ra) {
   auto kern = tc_resident_kernel<GN, INT_E, FP8>;
-  void* args[] = {&st->A[0], &st->A[1], &st->A[2], &st->Bg[0], &st->Bg[1], &st->Bg[2],
+  void* args[] = {&st->A[0],  &st->A[1],  &st->A[2],  &st->Bg[0], &st->Bg[1], &st->Bg[2],
+                  &st->J2[0], &st->J2[1], &st->J2[2], &st->S2[0], &st->S2[1], &st->S2[2],
                   const_cast<TcResArgs*>(&ra)};
   ISING_CUDA(ds->ctx, cudaLaunchCooperativeKernel((const void*)kern, dim3(st->grid), dim3(kThreads),
                                                   args, st->res_bytes, ds->ctx->stream));
@@ -1657,6 +1748,7 @@ int tc_setup(ising_ds* ds) {
       if (32ull * r < 32768ull) st->emode = 2;
     }
   }
+  st->nfull = (int)(ds->n / (st->fp8 ? 128 : 64));
   // resident form when every (128 x 2 GN) tile gets its own co-resident CTA
   // (a tensor-memory kernel holds its SM alone): two groups of GN restarts
   // per CTA, 64 each, or 32 when B <= 64
@@ -1675,6 +1767,7 @@ int tc_setup(ising_ds* ds) {
     if (bytes <= (size_t)ctx->smem_optin) {
       st->small = true;
       st->resident = true;
+      st->nfull = 0;
       st->gn = bn;
       st->small_grid = ceil_div_i(ds->B, bn);
       st->small_bytes = bytes;
@@ -1724,10 +1817,21 @@ static int tc_maps(ising_ds* ds, TcState* st) {
   for (int s = 0; s < 3; ++s) {
     ISING_TRY(make_map(ds->ctx, &st->B[s], ds->spins[s].p, ds->n, ds->B, ds->ld,
                        st->fp8 ? 128 : 64, st->BN, st->fp8));
+    if (st->nfull >= 2) {
+      ISING_TRY(make_map_pairs(ds->ctx, &st->SP[s], ds->spins[s].p, st->nfull, ds->B, ds->ld, st->BN,
+                               st->fp8));
+      if (st->resident)
+        ISING_TRY(make_map_pairs(ds->ctx, &st->S2[s], ds->spins[s].p, st->nfull, ds->B, ds->ld,
+                                 st->gn, st->fp8));
+    }
     if (st->resident)
       ISING_TRY(make_map(ds->ctx, &st->Bg[s], ds->spins[s].p, ds->n, ds->B, ds->ld,
                          st->fp8 ? 128 : 64, st->gn, st->fp8));
   }
+  if (st->nfull >= 2)
+    for (int p = 0; p < 3; ++p)
+      ISING_TRY(make_map_pairs(ds->ctx, &st->J2[p], ds->Jop[p < ds->planes ? p : 0].p, st->nfull,
+                               ds->n, ds->ld, kBM, st->fp8));
   if (ds->relaxed())
     for (int s = 0; s < 2; ++s)
       ISING_TRY(make_map(ds->ctx, &st->Bx[s], ds->xbuf[s].p, ds->n, ds->B, ds->ld, 64, st->BN, false));
@@ -1776,18 +1880,22 @@ int tc_run(ising_ds* ds, int mode, float* Gout) {
     a.trace = st->trace.as<unsigned long long>();
   }
   const CUtensorMap& mS = st->B[t % 3];
+  const CUtensorMap& mS2 = st->SP[t % 3];
+  a.nfull = st->nfull;
   const bool ie = ds->int_energy;
   switch (mode) {
-    case kModeUpdate: return ie ? launch_mode<kModeUpdate, true>(ds, st, a, mS)
-                                : launch_mode<kModeUpdate, false>(ds, st, a, mS);
-    case kModeEnergy: return ie ? launch_mode<kModeEnergy, true>(ds, st, a, mS)
-                                : launch_mode<kModeEnergy, false>(ds, st, a, mS);
+    case kModeUpdate: return ie ? launch_mode<kModeUpdate, true>(ds, st, a, mS, mS2)
+                                : launch_mode<kModeUpdate, false>(ds, st, a, mS, mS2);
+    case kModeEnergy: return ie ? launch_mode<kModeEnergy, true>(ds, st, a, mS, mS2)
+                                : launch_mode<kModeEnergy, false>(ds, st, a, mS, mS2);
     case kModeRelaxed: {
-      // the product runs on x_t; the epilogue reads s_t and writes s_{t+1}, x_{t+1}
+      // the product runs on x_t; the epilogue reads s_t and writes s_{t+1},
+      // x_{t+1} (x has no pair view: one copy per k-block)
       const CUtensorMap& mX = st->Bx[t % 2];
-      return ie ? launch_relaxed<true>(ds, st, a, mX) : launch_relaxed<false>(ds, st, a, mX);
+      a.nfull = 0;
+      return ie ? launch_relaxed<true>(ds, st, a, mX, mS2) : launch_relaxed<false>(ds, st, a, mX, mS2);
     }
-    default: return launch_mode<kModeCoupling, true>(ds, st, a, mS);
+    default: return launch_mode<kModeCoupling, true>(ds, st, a, mS, mS2);
   }
 }
 
@@ -1916,6 +2024,7 @@ int tc_run_resident(ising_ds* ds, int64_t steps) {
   r.conv_count = conv ? ds->conv_count() : nullptr;
   r.nst = st->nst;
   r.bars = st->bars;
+  r.nfull = st->nfull;
   return st->gn == 64 ? resident_launch_bn<64>(ds, st, r) : resident_launch_bn<32>(ds, st, r);
 }
 
