@@ -172,12 +172,13 @@ __device__ __forceinline__ void tmem_wait_st() {
   asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
-// Orders this thread's generic-proxy global accesses with async-proxy (TMA)
-// accesses.
+// Orders this thread's generic-proxy shared-memory accesses with later
+// async-proxy (TMA, tcgen05.mma operand) accesses of the CTA.
 __device__ __forceinline__ void fence_proxy_async_shared() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+// The same for global memory (spins written by other CTAs, read by TMA).
 __device__ __forceinline__ void fence_proxy_async_global() {
   asm volatile("fence.proxy.async.global;" ::: "memory");
 }
