@@ -151,14 +151,14 @@ def peaks() -> dict:
             "sm_max_mhz": 2070.0, "source": "fallback"}
 
 
-def traffic_for(kernel: str, src_file: str):
+def traffic_for(kernel: str, src_file: str, workload: str):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current source of the kernel."""
+    on this workload and on the current source of the kernel."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
     d = json.load(open(path)).get(kernel)
-    if not d:
+    if not d or d.get("workload") != workload:
         return None
     h = hashlib.sha256(open(os.path.join(ROOT, src_file), "rb").read()).hexdigest()[:16]
     return d["bytes_per_launch"] if d.get("source_sha") == h else None
@@ -518,7 +518,7 @@ def main():
                 "unit": "TFLOP/s"}
         kname, ksrc = "plain_step_kernel", "paper_2312_05837_gb300/csrc/ds_plain.cu"
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = traffic_for(kname, ksrc)
+    roof["traffic"] = traffic_for(kname, ksrc, a.workload)
     roof["kernel"] = kname
     roof["peak_source"] = pk["source"]
     roof["avg_launch_ms"] = avg_ms

@@ -40,3 +40,20 @@ def test_table2_family_shapes():
     assert np.abs(u.J).max() <= 1000 and np.abs(u.h).max() <= 1000
     g = synth.table2_instance("gaussian", 5, n=200)
     assert np.array_equal(g.J, g.J.T)
+
+
+def test_traffic_figure_only_for_its_workload_and_source():
+    """bench.py reports the committed ncu DRAM figure of the dominant kernel
+    only for the workload it was captured on and while the kernel's source
+    is the one profiled."""
+    import json
+    import bench
+    d = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+    for kernel, e in d.items():
+        src = {"sparse_step_kernel": "paper_2312_05837_gb300/csrc/ds_sparse.cu"}.get(
+            kernel, "paper_2312_05837_gb300/csrc/ds_tc.cu")
+        other = "er2000" if e["workload"] != "er2000" else "sk4096"
+        assert bench.traffic_for(kernel, src, other) is None
+        got = bench.traffic_for(kernel, src, e["workload"])
+        assert got in (None, e["bytes_per_launch"])
+    assert bench.traffic_for("no_such_kernel", "bench.py", "er2000") is None
