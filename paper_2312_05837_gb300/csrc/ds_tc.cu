@@ -272,15 +272,16 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (int u = 0; u < Lay::kKps; ++u) {
             const int kt = kt0 + u;
             if (kt >= nkt) break;
-            const uint32_t a0 = sb + u * Lay::kA;
-            const uint32_t b0 = sb + Lay::kKps * Lay::kA + u * Lay::kB;
+            // descriptors of the tiles; K step k adds 32 bytes (2 in the >> 4 address field)
+            const uint64_t da = tc::desc_k_sw128(sb + u * Lay::kA);
+            const uint64_t db = tc::desc_k_sw128(sb + Lay::kKps * Lay::kA + u * Lay::kB);
 #pragma unroll
             for (int k = 0; k < 4; ++k) {  // 32 bytes of K per MMA (16 BF16 or 32 E4M3)
               if (FP8)
-                tc::mma_f8(d, tc::desc_k_sw128(a0 + 32 * k), tc::desc_k_sw128(b0 + 32 * k), idesc,
+                tc::mma_f8(d, da + 2u * k, db + 2u * k, idesc,
                            (kt > 0 || k > 0) ? 1u : 0u);
               else
-                tc::mma_f16(d, tc::desc_k_sw128(a0 + 32 * k), tc::desc_k_sw128(b0 + 32 * k), idesc,
+                tc::mma_f16(d, da + 2u * k, db + 2u * k, idesc,
                             (kt > 0 || k > 0) ? 1u : 0u);
             }
           }
@@ -949,14 +950,16 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int kt = kt0 + u;
             if (kt >= nkt) break;
             const uint32_t a0 = kt < jres ? tc::smem_u32(smem + (size_t)kt * Lay::kA) : sb + u * Lay::kA;
-            const uint32_t b0 = sb + Lay::kKps * Lay::kA + u * Lay::kB;
+            // descriptors of the tiles; K step k adds 32 bytes (2 in the >> 4 address field)
+            const uint64_t da = tc::desc_k_sw128(a0);
+            const uint64_t db = tc::desc_k_sw128(sb + Lay::kKps * Lay::kA + u * Lay::kB);
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
               if (FP8)
-                tc::mma_f8(d, tc::desc_k_sw128(a0 + 32 * k), tc::desc_k_sw128(b0 + 32 * k), idesc,
+                tc::mma_f8(d, da + 2u * k, db + 2u * k, idesc,
                            (kt > 0 || k > 0) ? 1u : 0u);
               else
-                tc::mma_f16(d, tc::desc_k_sw128(a0 + 32 * k), tc::desc_k_sw128(b0 + 32 * k), idesc,
+                tc::mma_f16(d, da + 2u * k, db + 2u * k, idesc,
                             (kt > 0 || k > 0) ? 1u : 0u);
             }
           }
@@ -1324,15 +1327,16 @@ __global__ void __launch_bounds__(kSmallThreads, 1)
       if (lane == 0) {
         for (int kt = 0; kt < nkt; ++kt) {
           const int kb = kt % nk;
-          const uint32_t a0 = tc::smem_u32(Jsm + (size_t)kt * Lay::kA);
-          const uint32_t b0 = tc::smem_u32(Scur + (size_t)kb * Lay::kSk);
+          // descriptors of the tiles; K step k adds 32 bytes (2 in the >> 4 address field)
+          const uint64_t da = tc::desc_k_sw128(tc::smem_u32(Jsm + (size_t)kt * Lay::kA));
+          const uint64_t db = tc::desc_k_sw128(tc::smem_u32(Scur + (size_t)kb * Lay::kSk));
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
             if (FP8)
-              tc::mma_f8(tmem_base, tc::desc_k_sw128(a0 + 32 * k), tc::desc_k_sw128(b0 + 32 * k),
+              tc::mma_f8(tmem_base, da + 2u * k, db + 2u * k,
                          idesc, (kt > 0 || k > 0) ? 1u : 0u);
             else
-              tc::mma_f16(tmem_base, tc::desc_k_sw128(a0 + 32 * k), tc::desc_k_sw128(b0 + 32 * k),
+              tc::mma_f16(tmem_base, da + 2u * k, db + 2u * k,
                           idesc, (kt > 0 || k > 0) ? 1u : 0u);
           }
         }
