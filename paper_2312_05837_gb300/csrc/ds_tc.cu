@@ -630,11 +630,15 @@ struct EpiGroup {
 // times the offset once per column. EMODE 2 (also 32 max_i sum_j |J_ij| <
 // 2^15): two columns share one reduction, packed as a + 2^16 b; the low half
 // of the sum is then sum a exactly and the high half sum b. EMODE 0 converts
-// with F2I.
+// with F2I. `sbits` holds the signs of this lane's theta (bit sh + c: column
+// c of the warp's columns in this group): the spins the step consumes, kept
+// from the previous step instead of evaluated again, and replaced by the new
+// ones.
 template <int GN, bool INT_E, bool FP8, int EMODE>
 __device__ __forceinline__ void resident_chunks(const TcResArgs& R, const EpiLane& E,
                                                 const EpiGroup& Gr, long long t, float2 bc,
-                                                bool last, uint64_t* acc_empty) {
+                                                bool last, uint64_t* acc_empty, uint32_t& sbits,
+                                                int sh) {
   const TcArgs& P = R.P;
   constexpr int kCols = GN / 4;
   const uint32_t t_th = Gr.t_acc + GN, t_m = Gr.t_acc + 2 * GN, t_v = Gr.t_acc + 3 * GN;
@@ -654,15 +658,15 @@ __device__ __forceinline__ void resident_chunks(const TcResArgs& R, const EpiLan
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(acc_empty);
     }
-    uint32_t pos_bits = 0, new_bits = 0;
+    const uint32_t pos_bits = (sbits >> (sh + c0)) & 0xFFu;  // the spins this step consumes
+    uint32_t new_bits = 0;
     int eq[kChunk];
     float ef[kChunk];
 #pragma unroll
     for (int j = 0; j < kChunk; ++j) {
       float tj = __uint_as_float(th[j]), mj = __uint_as_float(mm[j]), vj = __uint_as_float(vv[j]);
       const float G = INT_E ? __uint_as_float(r[j]) : __uint_as_float(r[j]) * E.rs;
-      const bool pos = sin_nonneg(tj);  // the spin this step consumed
-      pos_bits |= (pos ? 1u : 0u) << j;
+      const bool pos = (pos_bits >> j) & 1u;
       if (INT_E) {
         if (EMODE > 0) {
           eq[j] = __float_as_int(__fadd_rn(pos ? G : -G, 12582912.0f));
@@ -681,6 +685,7 @@ __device__ __forceinline__ void resident_chunks(const TcResArgs& R, const EpiLan
       mm[j] = __float_as_uint(mj);
       vv[j] = __float_as_uint(vj);
     }
+    sbits = (sbits & ~(0xFFu << (sh + c0))) | (new_bits << (sh + c0));
     if (!last) {
       tc::tmem_st8(t_th + c0, th);
       tc::tmem_st8(t_m + c0, mm);
@@ -1048,7 +1053,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       Gr.t_acc = tmem_base + lane_off + (uint32_t)(g * 4 * GN + part * kCols);
       return Gr;
     };
-    // state of this warp's columns into tensor memory
+    // state of this warp's columns into tensor memory, and the signs of theta
+    // (bit g kCols + c for column c of group g)
+    uint32_t sbits = 0;
     for (int g = 0; g < 2; ++g) {
       const EpiGroup Gr = group(g);
 #pragma unroll 1
@@ -1059,9 +1066,11 @@ __global__ void __launch_bounds__(kThreads, 1)
           const int64_t b = Gr.nb0 + c0 + j;
           const bool ok = row_ok && b < P.B;
           const int64_t idx = b * P.ld + i;
-          a[j] = __float_as_uint(ok ? P.theta[idx] : 0.f);
+          const float th0 = ok ? P.theta[idx] : 0.f;
+          a[j] = __float_as_uint(th0);
           bm[j] = __float_as_uint(ok ? P.m[idx] : 0.f);
           c[j] = __float_as_uint(ok ? P.v[idx] : 0.f);
+          sbits |= (sin_nonneg(th0) ? 1u : 0u) << (g * kCols + c0 + j);
         }
         tc::tmem_st8(Gr.t_acc + GN + c0, a);
         tc::tmem_st8(Gr.t_acc + 2 * GN + c0, bm);
@@ -1086,11 +1095,14 @@ __global__ void __launch_bounds__(kThreads, 1)
       const bool last = s + 1 == K;
       const EpiGroup Gr = group(g);
       if constexpr (INT_E) {
-        if (P.gmagic == 2) resident_chunks<GN, true, FP8, 2>(R, E, Gr, t, bc, last, &acc_empty[g]);
-        else if (P.gmagic == 1) resident_chunks<GN, true, FP8, 1>(R, E, Gr, t, bc, last, &acc_empty[g]);
-        else resident_chunks<GN, true, FP8, 0>(R, E, Gr, t, bc, last, &acc_empty[g]);
+        if (P.gmagic == 2)
+          resident_chunks<GN, true, FP8, 2>(R, E, Gr, t, bc, last, &acc_empty[g], sbits, g * kCols);
+        else if (P.gmagic == 1)
+          resident_chunks<GN, true, FP8, 1>(R, E, Gr, t, bc, last, &acc_empty[g], sbits, g * kCols);
+        else
+          resident_chunks<GN, true, FP8, 0>(R, E, Gr, t, bc, last, &acc_empty[g], sbits, g * kCols);
       } else {
-        resident_chunks<GN, false, FP8, 0>(R, E, Gr, t, bc, last, &acc_empty[g]);
+        resident_chunks<GN, false, FP8, 0>(R, E, Gr, t, bc, last, &acc_empty[g], sbits, g * kCols);
       }
       tc::tmem_wait_st();
       tc::fence_proxy_async_global();
