@@ -2,15 +2,20 @@
 // tcgen05 tensor cores.
 //
 // G = J S is a GEMM with M = spins (J rows, 128 per tile), N = restarts (BN
-// per tile) and K = spins. J is stored as BF16 planes [n][ld] (one plane when
+// per tile) and K = spins. J is stored as E4M3 [n][ld] when every J is an
+// integer of magnitude <= 16 (exact), else as BF16 planes (one plane when
 // every J is an integer of magnitude <= 256, which BF16 holds exactly; three
-// planes hi + mid + lo otherwise, giving about 24 significant bits), the spins
-// S_t as BF16 +-1 [B][ld] (restart-major, K contiguous). Both operands are
-// K-major, so one TMA box of 64 elements x rows fills a 128-byte swizzled
-// shared-memory tile that tcgen05.mma reads directly.
+// planes hi + mid + lo otherwise, giving about 24 significant bits); the spins
+// S_t as +-1 of the same type [B][ld] (restart-major, K contiguous). Both
+// operands are K-major, so one TMA box of 128 bytes (a k-block: 128 E4M3 or
+// 64 BF16 elements) x rows fills a 128-byte swizzled shared-memory tile that
+// tcgen05.mma reads directly. A thread issues one tcgen05.mma only every ~110
+// cycles and one TMA copy every ~250 whatever their sizes, which shapes the
+// kernels below.
 //
-// One persistent CTA per SM, warp-specialised:
-//   warp 0     TMA producer: STAGES-deep ring of (J tile, S tile) per k-block,
+// Streaming form (tc_step_kernel): one persistent CTA per SM, warp-specialised:
+//   warps 0, 2 TMA producers of the J and the S tiles of a STAGES-deep ring
+//              (stages of two k-blocks for BN <= 128, of one for BN = 256),
 //   warp 1     allocates tensor memory and issues the MMAs (one thread) into
 //              one of two accumulator buffers (2 x BN columns of 128 lanes),
 //   warps 4-19 epilogue: each thread owns one spin i (its TMEM lane) and walks
@@ -503,17 +508,17 @@ __global__ void row_absmax_kernel(const void* J, int dt, int64_t n, float* scale
 // its own tensor-memory block (accumulator, theta, m, v: columns
 // [4 GN g, 4 GN (g + 1))), and the tensor cores alternate between them: while
 // the epilogue warps update group 0 from its accumulator, the MMAs of group 1
-// run, and the other way round, so the operand stream (bound by what one SM
-// can take in) and the epilogue (bound by instruction issue) overlap. Step
-// t + 1 of a group needs S_t of all rows, i.e. the output of every m-tile of
-// the same restarts, so the CTAs of one group's column pass a barrier
-// between steps (an arrival counter per group and column; the cooperative
-// launch keeps all CTAs co-resident, and the waits are bounded); groups and
-// columns run independently. The epilogue warps track the best of step
-// t - 1 of a group for their CTA's slice of its restarts before its step t
-// epilogue. The spins of the current step are re-derived from theta
-// (sgn+(sin theta), as they were written), so the epilogue reads no state
-// from global memory.
+// run, and the other way round, so the MMA stream (paced by one thread's issue
+// rate) and the epilogue (bound by instruction issue) overlap. Step t + 1 of
+// a group needs S_t of all rows, i.e. the output of every m-tile of the same
+// restarts, so the CTAs of one group's column pass a barrier between steps
+// (an arrival counter per group and column; the cooperative launch keeps all
+// CTAs co-resident, and the waits are bounded); groups and columns run
+// independently. After a group's barrier its controller warp tracks the best
+// of that step for the CTA's slice of the group's restarts. The spins a step
+// consumes are the signs of theta the epilogue kept in a register since the
+// previous update (derived from theta when the launch starts), so the
+// epilogue reads no state from global memory.
 
 struct TcResArgs {
   TcArgs P;
