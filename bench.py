@@ -326,7 +326,7 @@ def time_to_target(ctx, dinst, integer, B, T, seed, chunk=50):
 def precision_sweep(ctx, dinst, n, B, T, seed=1):
     """One full domain selection per operand precision on the same instance
     and seed: the plain FP32 CUDA-core form, three BF16 planes (FP32-exact),
-    one BF16 plane and row-scaled E4M3 (SURVEY config 3); spin-updates/s from
+    one BF16 plane and row-scaled E4M3 (the N = 4096 SK workload); spin-updates/s from
     device time and the best energy, re-evaluated exactly in FP64."""
     import torch
     from paper_2312_05837_gb300 import api
