@@ -53,7 +53,7 @@ typedef enum ising_status {
   ISING_ECUDA = 3,    /* a CUDA call failed */
   ISING_ETIMEOUT = 4, /* a bounded device wait gave up */
   ISING_EBUSY = 5,    /* server: request does not fit the memory budget now */
-  ISING_ENOTSUP = 6   /* combination not supported by this build */
+  ISING_ENOTSUP = 6   /* combination of options the library does not support */
 } ising_status;
 
 enum { ISING_LAYOUT_DENSE = 0, ISING_LAYOUT_CSR = 1 };
