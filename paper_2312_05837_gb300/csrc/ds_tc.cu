@@ -1727,6 +1727,8 @@ int tc_setup(ising_ds* ds) {
     ISING_TRY(dev_alloc(ctx, ds->Jop[0], plane_elems));
     const float* rs = nullptr;
     if (!exact16) {
+      // J / scale_i rounded to E4M3: the products are no longer integers
+      ds->int_energy = false;
       ISING_TRY(dev_alloc(ctx, ds->rowscale, ds->n * 4));
       row_absmax_kernel<<<(int)std::min<int64_t>(ds->n, 65535), 256, 0, ctx->stream>>>(
           I.J.p, I.j_dtype, ds->n, ds->rowscale.as<float>());

@@ -96,3 +96,38 @@ def test_fp8_row_scaled_error_is_e4m3_sized(gpu_ctx):
 
 def test_bench_size_fp8(gpu_ctx):
     _check(gpu_ctx, synth.workload("er2000", 0), 1024, "fp8", True)
+
+
+@pytest.mark.parametrize("n,B", [(300, 96), (120, 40)])
+def test_fp8_row_scaled_integer_couplings(gpu_ctx, n, B):
+    """Integer couplings up to 40 in forced E4M3 are row-scaled, so the
+    products are no longer integers: the coupling error is E4M3-sized, the
+    step energies are the FP32 partials' (within that error), the run stays
+    deterministic between the resident and streaming forms, and the result's
+    energy is the exact energy of its spins (n = 120 runs the small form)."""
+    inst = synth.random_sparse_instance(n, 12, p=0.1, kind="int", h="int", layout="dense", jmax=40)
+    s = api.Session(gpu_ctx, inst, restarts=B, steps=1, seed=1, precision="fp8")
+    st = s.export_state()
+    G = s.coupling()
+    J = ising.coupling_matrix(inst)
+    ref = (J @ st["spins"].T.astype(np.float64)).T
+    scale = np.abs(J).sum(axis=1)[None, :]
+    assert np.max(np.abs(G - ref) / scale) <= 2.0 ** -4
+    s.run(1)
+    E = s.last_energies()
+    Eo = ising.energy(inst, st["spins"].T.astype(np.float64))
+    assert np.all(np.abs(E - Eo) <= 2.0 ** -4 * (np.sum(np.abs(J)) + np.abs(inst.h).sum() + 1.0))
+    s.close()
+    a = api.Session(gpu_ctx, inst, restarts=B, steps=30, seed=2, precision="fp8")
+    b = api.Session(gpu_ctx, inst, restarts=B, steps=30, seed=2, precision="fp8", streaming=True)
+    a.run(30)
+    b.run(30)
+    sa, sb = a.export_state(), b.export_state()
+    for k in ["theta", "m", "v", "spins"]:
+        np.testing.assert_array_equal(sa[k], sb[k])
+    a.finish()
+    res = a.result()
+    assert res["best_energy"] == pytest.approx(float(ising.energy(inst, res["best_spins"].astype(np.float64))),
+                                               rel=1e-12, abs=1e-9)
+    a.close()
+    b.close()
