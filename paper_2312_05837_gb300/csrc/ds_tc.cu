@@ -1741,6 +1741,9 @@ int tc_setup(ising_ds* ds) {
       ISING_TRY(make_map(ctx, &st->A[p], ds->Jop[0].p, ds->n, ds->n, ds->ld, 128, kBM, true));
   } else {
     ds->planes = (exact256 || ds->prec == ISING_PREC_BF16) ? 1 : 3;
+    // one BF16 plane of integers beyond 256 rounds J: the sums are no longer
+    // the instance's integers
+    if (!exact256 && ds->planes == 1) ds->int_energy = false;
     for (int p = 0; p < ds->planes; ++p) ISING_TRY(dev_alloc(ctx, ds->Jop[p], plane_elems * 2));
     to_planes_kernel<<<g, 256, 0, ctx->stream>>>(
         I.J.p, I.j_dtype, ds->n, ds->ld, ds->planes, ds->Jop[0].as<__nv_bfloat16>(),

@@ -98,28 +98,31 @@ def test_bench_size_fp8(gpu_ctx):
     _check(gpu_ctx, synth.workload("er2000", 0), 1024, "fp8", True)
 
 
-@pytest.mark.parametrize("n,B", [(300, 96), (120, 40)])
-def test_fp8_row_scaled_integer_couplings(gpu_ctx, n, B):
-    """Integer couplings up to 40 in forced E4M3 are row-scaled, so the
-    products are no longer integers: the coupling error is E4M3-sized, the
-    step energies are the FP32 partials' (within that error), the run stays
+@pytest.mark.parametrize("n,B,prec,jmax,rel", [(300, 96, "fp8", 40, 2.0 ** -4),
+                                               (120, 40, "fp8", 40, 2.0 ** -4),
+                                               (300, 96, "bf16", 400, 2.0 ** -8)])
+def test_rounded_integer_couplings(gpu_ctx, n, B, prec, jmax, rel):
+    """Integer couplings beyond the operand type's exact range (E4M3 row-scaled
+    above 16, one BF16 plane above 256) are rounded, so the products are no
+    longer the instance's integers: the coupling error is the type's, the
+    step energies are FP32 partials (within that error), the run stays
     deterministic between the resident and streaming forms, and the result's
     energy is the exact energy of its spins (n = 120 runs the small form)."""
-    inst = synth.random_sparse_instance(n, 12, p=0.1, kind="int", h="int", layout="dense", jmax=40)
-    s = api.Session(gpu_ctx, inst, restarts=B, steps=1, seed=1, precision="fp8")
+    inst = synth.random_sparse_instance(n, 12, p=0.1, kind="int", h="int", layout="dense", jmax=jmax)
+    s = api.Session(gpu_ctx, inst, restarts=B, steps=1, seed=1, precision=prec)
     st = s.export_state()
     G = s.coupling()
     J = ising.coupling_matrix(inst)
     ref = (J @ st["spins"].T.astype(np.float64)).T
     scale = np.abs(J).sum(axis=1)[None, :]
-    assert np.max(np.abs(G - ref) / scale) <= 2.0 ** -4
+    assert np.max(np.abs(G - ref) / scale) <= rel
     s.run(1)
     E = s.last_energies()
     Eo = ising.energy(inst, st["spins"].T.astype(np.float64))
-    assert np.all(np.abs(E - Eo) <= 2.0 ** -4 * (np.sum(np.abs(J)) + np.abs(inst.h).sum() + 1.0))
+    assert np.all(np.abs(E - Eo) <= rel * (np.sum(np.abs(J)) + np.abs(inst.h).sum() + 1.0))
     s.close()
-    a = api.Session(gpu_ctx, inst, restarts=B, steps=30, seed=2, precision="fp8")
-    b = api.Session(gpu_ctx, inst, restarts=B, steps=30, seed=2, precision="fp8", streaming=True)
+    a = api.Session(gpu_ctx, inst, restarts=B, steps=30, seed=2, precision=prec)
+    b = api.Session(gpu_ctx, inst, restarts=B, steps=30, seed=2, precision=prec, streaming=True)
     a.run(30)
     b.run(30)
     sa, sb = a.export_state(), b.export_state()
