@@ -90,17 +90,20 @@ __device__ __forceinline__ unsigned long long now_ns() {
 
 // Streaming form: for BN <= 128 stages of two k-blocks [J, J, S, S], so that
 // two whole k-blocks of one plane arrive by one copy per operand (a thread
-// issues one TMA copy per ~250 cycles whatever its size); for BN = 256 such
-// stages would leave room for two only, so there a stage is one k-block.
+// issues one TMA copy per ~250 cycles whatever its size); for BN = 224 and
+// 256 such stages would leave room for two only, so there a stage is one
+// k-block.
 template <int BN>
 struct TcLayout {
-  static constexpr int kKps = BN >= 256 ? 1 : 2;
+  static constexpr int kKps = BN >= 192 ? 1 : 2;
   static constexpr uint32_t kA = kBM * kRowBytes;
   static constexpr uint32_t kB = BN * kRowBytes;
   static constexpr uint32_t kStage = kKps * (kA + kB);
   static constexpr int kStages = (200 * 1024) / kStage;
   static constexpr uint32_t kBars = kStages * kStage;  // barrier block
   static constexpr uint32_t kBytes = kBars + 256 + 1024;  // + alignment slack
+  // two accumulator buffers; allocations are powers of two columns
+  static constexpr uint32_t kTmemCols = 2 * BN <= 128 ? 128 : (2 * BN <= 256 ? 256 : 512);
 };
 
 // Resident form: shared memory holds the first `jres` J tiles of the CTA's
@@ -177,7 +180,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc::fence_barrier_init();
   }
   if (warp == 1) {
-    tc::tmem_alloc(tmem_slot, 2 * BN);
+    tc::tmem_alloc(tmem_slot, Lay::kTmemCols);
     tc::fence_before_sync();
   }
   if (warp == 0 && lane == 0) tc::prefetch_map(&tmA0);
@@ -436,7 +439,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (threadIdx.x == 0) ISING_TRACE(7);
   if (warp == 1) {
     tc::fence_after_sync();
-    tc::tmem_dealloc(tmem_base, 2 * BN);
+    tc::tmem_dealloc(tmem_base, Lay::kTmemCols);
   }
 }
 
@@ -1618,6 +1621,7 @@ int launch_bn_sel(ising_ds* ds, TcState* st, const TcArgs& a, const CUtensorMap&
                   const CUtensorMap& mS2) {
   switch (st->BN) {
     case 256: return launch_bn<256, MODE, INT_E, FP8>(ds, st, a, mB, mS2);
+    case 224: return launch_bn<224, MODE, INT_E, FP8>(ds, st, a, mB, mS2);
     case 64: return launch_bn<64, MODE, INT_E, FP8>(ds, st, a, mB, mS2);
     default: return launch_bn<128, MODE, INT_E, FP8>(ds, st, a, mB, mS2);
   }
@@ -1720,6 +1724,15 @@ int tc_setup(ising_ds* ds) {
   ds->spin_kind = st->fp8 ? kSpinE4M3 : kSpinBF16;
   ds->mtiles = 4 * ceil_div_i(ds->n, kBM);  // one energy-partial row per epilogue lane quarter
   st->BN = ds->B <= 64 ? 64 : (ds->B >= 2048 ? 256 : 128);
+  if (st->BN == 256) {
+    // tiles of 224 restarts when they fill the SMs' waves better: the
+    // busiest SM's share, waves x BN, sets the step time
+    auto cost = [&](int bn) {
+      const int64_t tiles = (int64_t)ceil_div_i(ds->n, kBM) * ceil_div_i(ds->B, bn);
+      return (tiles + ctx->sm_count - 1) / ctx->sm_count * bn;
+    };
+    if (cost(224) < cost(256)) st->BN = 224;
+  }
   const int64_t plane_elems = ds->n * ds->ld;
   int g = (int)std::min<int64_t>((plane_elems + 255) / 256, (int64_t)ctx->sm_count * 16);
   if (st->fp8) {
