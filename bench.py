@@ -164,18 +164,19 @@ def traffic_for(kernel: str, src_file: str, workload: str):
     return d["bytes_per_launch"] if d.get("source_sha") == h else None
 
 
-def launches_per_solve(T: int, rounds: int, path: int, resident: bool) -> int:
+def launches_per_solve(T: int, rounds: int, path: int, resident: bool, rowsum: bool) -> int:
     """Kernels of one solve, as the ncu launch list of a solve shows them:
     instance checks (couplings twice, field once), pruning (dense->CSR 2,
     init 1, 7 per round incl. the final empty one, sum + reduced J + reduced
     field 3), session set-up (fills 2, init 1, operand 1, plus the row-sum
-    bound of the integer tensor-core path), the steps (one cooperative launch
-    when resident, else step + track per step, plus the copy of improved
-    bit-packed spins on the sparse path), finish (energy-only step + track
-    (+ copy) + argmin), reconstruction (1), full-instance energy (2)."""
+    bound when the tensor-core path accumulates integer energies: `rowsum`),
+    the steps (one launch when resident, else step + track per step, plus the
+    copy of improved bit-packed spins on the sparse path), finish
+    (energy-only step + track (+ copy) + argmin), reconstruction (1),
+    full-instance energy (2)."""
     per_step = 3 if path == 2 else 2
     steps = 1 if resident else per_step * T
-    setup = 4 + (1 if path == 1 else 0)
+    setup = 4 + (1 if rowsum else 0)
     return 3 + 3 + 7 * (rounds + 1) + 3 + setup + steps + per_step + 1 + 1 + 2
 
 
@@ -535,7 +536,8 @@ def main():
                        "parallelism": f"replicas x{world}"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": input_bytes(inst),
                     "d2h_bytes_per_step": int(inst.n) + 8},
-            "gpu_launches": launches_per_solve(T, rounds, path, bool(last["resident"])) * a.steps,
+            "gpu_launches": launches_per_solve(T, rounds, path, bool(last["resident"]),
+                                               path == 1 and bool(inst.integer)) * a.steps,
             "roofline": roof, "clocks": clk,
             "best_energy": float(last["best_energy"].item())}
     if name.startswith("table2"):
