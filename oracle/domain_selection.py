@@ -110,6 +110,13 @@ CONV_WINDOW = 5
 CONV_TOL = 0.005
 
 
+def converged(window, E_t, E_1):
+    """The Sec. IV-B test on the last CONV_WINDOW energies of each restart
+    (`window`, shape (CONV_WINDOW, B), any order), the current energy E_t and
+    the first E_1: max - min of the window <= CONV_TOL |E_t - E_1|."""
+    return window.max(axis=0) - window.min(axis=0) <= CONV_TOL * np.abs(E_t - E_1)
+
+
 def select_domain(inst, p: Params, trace: bool = False, theta0=None, converge: bool = False):
     """Run T steps on all restarts; return a dict with the overall best
     (energy, spins, restart, step), per-restart bests, the last-step energies
@@ -158,8 +165,7 @@ def select_domain(inst, p: Params, trace: bool = False, theta0=None, converge: b
                 E_init[:] = r.energy
             E_stop[active] = r.energy[active]
             if t >= CONV_WINDOW:
-                spread = ring.max(axis=0) - ring.min(axis=0)
-                hit = active & (spread <= CONV_TOL * np.abs(r.energy - E_init))
+                hit = active & converged(ring, r.energy, E_init)
                 conv_step[hit] = t
             if (conv_step > 0).all():
                 steps_done = t

@@ -101,6 +101,71 @@ def test_first_step_moves_each_angle_by_lr():
     assert np.all(np.abs(r.theta) <= math.pi + 1e-12)
 
 
+def test_sgn_plus_of_zero_is_plus_one():
+    """sgn+(0) = +1 (the reading of the unspecified sign at 0): theta = 0 and
+    -0 round to +1, and so does the initial draw x0 = 0 (theta = asin 0 = 0);
+    just below 0 rounds to -1."""
+    th = np.array([[0.0, -0.0, -1e-300, 1e-300]])
+    np.testing.assert_array_equal(ds.round_spins(th), [[1.0, 1.0, -1.0, 1.0]])
+    inst = synth.er_dense(6, 1, p=0.5, weights="pm1")
+    cq, ch = ising.coefficients(inst.j_scale, inst.convention)
+    J, h = ising.coupling_matrix(inst), ising.field(inst)
+    r = ds.step(J, h, cq, ch, ds.Params(lr=0.1), np.zeros((6, 2)), np.zeros((6, 2)), np.zeros((6, 2)), 1)
+    np.testing.assert_array_equal(r.spins, np.ones((6, 2)))
+    np.testing.assert_array_equal(r.energy, ising.energy(inst, np.ones((6, 2))))
+
+
+def test_projection_is_the_ieee_remainder_modulo_two_pi():
+    """The projection onto the relaxed domain maps an angle to its IEEE
+    remainder modulo 2 pi (math.remainder: theta - 2 pi k, k the nearest
+    integer, result in [-pi, pi]). A first Adam step with lr = 6 from angles
+    near +-pi moves each by lr sgn(g) |g| / (|g| + eps) (m-hat / sqrt(v-hat) =
+    sgn g at t = 1), far outside [-pi, pi]; the oracle's result must be that
+    move's remainder, computed here with the library routine."""
+    inst, cq, ch, J, h, _ = _setup(n=20, B=3)
+    r0 = np.random.default_rng(8)
+    theta = np.where(r0.random((20, 3)) < 0.5, -1.0, 1.0) * r0.uniform(2.9, 3.1, (20, 3))
+    p = ds.Params(lr=6.0, mu=0.05)
+    r = ds.step(J, h, cq, ch, p, theta, np.zeros_like(theta), np.zeros_like(theta), 1)
+    g = r.grad
+    raw = theta - p.lr * np.sign(g) * np.abs(g) / (np.abs(g) + p.eps)
+    want = np.vectorize(lambda x: math.remainder(x, 2 * math.pi))(raw)
+    np.testing.assert_allclose(r.theta, want, rtol=0, atol=1e-12)
+    assert np.all(np.abs(r.theta) <= math.pi)
+    # sin and cos of the projected angle are those of the unprojected one
+    np.testing.assert_allclose(np.sin(r.theta), np.sin(raw), atol=1e-12)
+    np.testing.assert_allclose(np.cos(r.theta), np.cos(raw), atol=1e-12)
+
+
+@pytest.mark.parametrize("trace,stop", [
+    # E_1 = 10; windows 10..1 (spread 9), 5..1 (4), 3..1 (2), 2..1 (1) exceed
+    # 0.005 |E_t - 10| = 0.045; the window of five 1s has spread 0: stop at t = 9
+    ([10, 5, 3, 2, 1, 1, 1, 1, 1, 1], 9),
+    # spread exactly at the tolerance stops (<=): E_1 = 0, E_t = -1000 from
+    # t = 2 on except E_6 = -995; at t = 6 the spread 5 exceeds 0.005 |-995|
+    # = 4.975, at t = 7 it equals 0.005 |-1000| = 5 and the restart stops
+    ([0, -1000, -1000, -1000, -1000, -995, -1000, -1000], 7),
+    # spread just above it does not stop until the 5.0001 leaves the window
+    ([0, -1000, -1000, -1000, -1000, -994.9999, -1000, -1000, -1000, -1000, -1000], 11),
+    # never converging: the energy keeps falling by 1 per step
+    ([-t for t in range(12)], 0),
+    # constant from the start: the window spread 0 <= 0 at t = 5
+    ([-3.5] * 7, 5),
+])
+def test_convergence_rule_on_hand_computed_traces(trace, stop):
+    """The Sec. IV-B stopping rule on energy traces whose stopping step is
+    worked out by hand (the comments): window of 5, tolerance 0.005 of the
+    change since the first step, inclusive comparison."""
+    tr = np.asarray(trace, dtype=np.float64)
+    got = 0
+    for t in range(ds.CONV_WINDOW, len(tr) + 1):
+        w = tr[t - ds.CONV_WINDOW:t][:, None]
+        if ds.converged(w, tr[t - 1:t], tr[0:1])[0]:
+            got = t
+            break
+    assert got == stop
+
+
 def test_best_tracking_follows_the_trace():
     inst = synth.sk_dense(40, 2, 1.0)
     r = ds.select_domain(inst, ds.Params(restarts=6, steps=40, lr=0.3, seed=5), trace=True)
