@@ -269,16 +269,32 @@ def energy_noalloc(inst, spins, E_out, stream=None):
     """ising_energy_noalloc: energies of spins[count][n] into the caller's
     E_out[count] (all torch CUDA tensors); queues the work on `stream`
     (default: torch's current stream) without allocating anything."""
+    torch = _torch()
     lib = L.load()
     s, keep = make_instance(inst)
     if s.mem != L.MEM_DEVICE:
         raise ValueError("energy_noalloc takes a device-memory instance")
+    # the C entry point trusts its pointers: check shapes, types and devices
+    # here, so that a wrong buffer is an exception and not an out-of-bounds access
+    n = int(inst.n)
+    if not (isinstance(spins, torch.Tensor) and spins.is_cuda and spins.dtype == torch.int8):
+        raise ValueError("spins must be a CUDA int8 tensor")
+    if spins.dim() not in (1, 2) or spins.shape[-1] != n or not spins.is_contiguous():
+        raise ValueError(f"spins must be contiguous with shape (count, {n}) or ({n},)")
+    count = spins.shape[0] if spins.dim() == 2 else 1
+    if not (isinstance(E_out, torch.Tensor) and E_out.is_cuda and E_out.dtype == torch.float64
+            and E_out.is_contiguous() and E_out.numel() >= count):
+        raise ValueError(f"E_out must be a contiguous CUDA float64 tensor of at least {count} elements")
+    devs = {spins.device, E_out.device}
+    devs |= {a.device for a in keep if isinstance(a, torch.Tensor)}
+    if len(devs) != 1:
+        raise ValueError("the instance, spins and E_out must be on one device")
     if stream is None:
-        stream = _torch().cuda.current_stream().cuda_stream
+        stream = torch.cuda.current_stream(spins.device).cuda_stream
     elif hasattr(stream, "cuda_stream"):
         stream = stream.cuda_stream
-    count = spins.shape[0] if spins.dim() == 2 else 1
-    rc = lib.ising_energy_noalloc(byref(s), _ptr(spins), count, _ptr(E_out), c_void_p(stream))
+    with torch.cuda.device(spins.device):  # the entry point works on the current device
+        rc = lib.ising_energy_noalloc(byref(s), _ptr(spins), count, _ptr(E_out), c_void_p(stream))
     if rc != L.OK:
         msg = lib.ising_energy_noalloc_error()
         raise IsingError(rc, msg.decode() if msg else "")

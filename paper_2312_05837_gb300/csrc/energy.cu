@@ -8,15 +8,29 @@
 // other couplings in FP64.
 #include "common.cuh"
 
+#include <atomic>
+
 namespace ising {
 namespace {
 
 constexpr int kRowsPerBlock = 64;
 
-template <bool INT>
-__global__ void __launch_bounds__(256) energy_rows(InstView in, const int8_t* __restrict__ spins,
-                                                   int h_shift, int64_t nchunks,
-                                                   void* __restrict__ qpart,
+// The instance as the rows kernel reads it: dense or CSR J with row offsets
+// of type Off (the library's own int32 copy, or a caller's int64 offsets),
+// and h scaled by 2^h_shift to integers in the exact mode.
+template <typename Off>
+struct RowsView {
+  int64_t n;
+  int layout, j_dtype, h_dtype, h_shift;
+  const void* J;
+  const Off* rowptr;
+  const int32_t* indices;
+  const void* h;  // nullable
+};
+
+template <bool INT, typename Off>
+__global__ void __launch_bounds__(256) energy_rows(RowsView<Off> in, const int8_t* __restrict__ spins,
+                                                   int64_t nchunks, void* __restrict__ qpart,
                                                    void* __restrict__ hpart) {
   using Acc = typename std::conditional<INT, long long, double>::type;
   const int64_t n = in.n;
@@ -36,7 +50,7 @@ __global__ void __launch_bounds__(256) energy_rows(InstView in, const int8_t* __
         else dot += load_as_double(in.J, in.j_dtype, base + j) * (double)s[j];
       }
     } else {
-      for (int64_t k = in.rowptr[i] + lane; k < in.rowptr[i + 1]; k += 32) {
+      for (int64_t k = (int64_t)in.rowptr[i] + lane; k < (int64_t)in.rowptr[i + 1]; k += 32) {
         int32_t j = in.indices[k];
         if (INT) dot += (Acc)load_as_int(in.J, in.j_dtype, k) * s[j];
         else dot += load_as_double(in.J, in.j_dtype, k) * (double)s[j];
@@ -46,7 +60,7 @@ __global__ void __launch_bounds__(256) energy_rows(InstView in, const int8_t* __
     if (lane == 0) {
       q_acc += dot * (Acc)s[i];
       if (in.h) {
-        if (INT) h_acc += (Acc)llrint(ldexp(load_as_double(in.h, in.h_dtype, i), h_shift)) * s[i];
+        if (INT) h_acc += (Acc)llrint(ldexp(load_as_double(in.h, in.h_dtype, i), in.h_shift)) * s[i];
         else h_acc += load_as_double(in.h, in.h_dtype, i) * (double)s[i];
       }
     }
@@ -98,13 +112,15 @@ int energy_device(ising_ctx* ctx, const DevInstance& inst, const int8_t* spins, 
   ISING_TRY(dev_alloc(ctx, qp, (size_t)(count * nchunks) * 8));
   ISING_TRY(dev_alloc(ctx, hp, (size_t)(count * nchunks) * 8));
   dim3 grid((unsigned)nchunks, (unsigned)count);
-  InstView v = view(inst);
+  const InstView iv = view(inst);
+  RowsView<int32_t> v{iv.n, iv.layout, iv.j_dtype, iv.h_dtype, exact ? inst.h_shift : 0,
+                      iv.J, iv.rowptr, iv.indices, iv.h};
   if (exact) {
-    energy_rows<true><<<grid, 256, 0, ctx->stream>>>(v, spins, inst.h_shift, nchunks, qp.p, hp.p);
+    energy_rows<true><<<grid, 256, 0, ctx->stream>>>(v, spins, nchunks, qp.p, hp.p);
     energy_finish<true><<<ceil_div_i(count, 128), 128, 0, ctx->stream>>>(
         count, nchunks, qp.p, hp.p, inst.cq, inst.ch, inst.h_shift, E, Q, H);
   } else {
-    energy_rows<false><<<grid, 256, 0, ctx->stream>>>(v, spins, 0, nchunks, qp.p, hp.p);
+    energy_rows<false><<<grid, 256, 0, ctx->stream>>>(v, spins, nchunks, qp.p, hp.p);
     energy_finish<false><<<ceil_div_i(count, 128), 128, 0, ctx->stream>>>(
         count, nchunks, qp.p, hp.p, inst.cq, inst.ch, 0, E, nullptr, nullptr);
   }
@@ -134,66 +150,16 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratch
 
 // Device address of g_noalloc_scratch per device, looked up by the first call
 // made with that device current (the array's host-side name is not a device
-// address).
+// address). Threads racing on a first call store the same address; the slots
+// are atomic so that the race is well defined. A device reset invalidates
+// the cached address (the library does not reset devices).
 constexpr int kMaxDevices = 64;
-void* g_noalloc_ptr[kMaxDevices] = {};
+std::atomic<void*> g_noalloc_ptr[kMaxDevices];
 thread_local char g_noalloc_err[256] = "";
 
 int noalloc_fail(int code, const char* msg) {
   snprintf(g_noalloc_err, sizeof g_noalloc_err, "%s", msg);
   return code;
-}
-
-// The rows kernel of ising_energy with the caller's int64 CSR offsets.
-template <bool INT>
-__global__ void __launch_bounds__(256) energy_rows_i64(int64_t n, int layout, int j_dtype,
-                                                       const void* J, const int64_t* indptr,
-                                                       const int32_t* indices, const void* h,
-                                                       int h_dtype, const int8_t* __restrict__ spins,
-                                                       int64_t nchunks, void* __restrict__ qpart,
-                                                       void* __restrict__ hpart) {
-  using Acc = typename std::conditional<INT, long long, double>::type;
-  const int64_t vec = blockIdx.y;
-  const int8_t* s = spins + vec * n;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  __shared__ Acc sq[8], sh[8];
-  Acc q_acc = 0, h_acc = 0;
-  for (int r = 0; r < kRowsPerBlock / 8; ++r) {
-    int64_t i = (int64_t)blockIdx.x * kRowsPerBlock + warp * (kRowsPerBlock / 8) + r;
-    if (i >= n) break;
-    Acc dot = 0;
-    if (layout == ISING_LAYOUT_DENSE) {
-      for (int64_t j = lane; j < n; j += 32) {
-        if (INT) dot += (Acc)load_as_int(J, j_dtype, i * n + j) * s[j];
-        else dot += load_as_double(J, j_dtype, i * n + j) * (double)s[j];
-      }
-    } else {
-      for (int64_t k = indptr[i] + lane; k < indptr[i + 1]; k += 32) {
-        int32_t j = indices[k];
-        if (INT) dot += (Acc)load_as_int(J, j_dtype, k) * s[j];
-        else dot += load_as_double(J, j_dtype, k) * (double)s[j];
-      }
-    }
-    for (int o = 16; o; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
-    if (lane == 0) {
-      q_acc += dot * (Acc)s[i];
-      if (h) {
-        if (INT) h_acc += (Acc)load_as_int(h, h_dtype, i) * s[i];
-        else h_acc += load_as_double(h, h_dtype, i) * (double)s[i];
-      }
-    }
-  }
-  if (lane == 0) {
-    sq[warp] = q_acc;
-    sh[warp] = h_acc;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    Acc a = 0, b = 0;
-    for (int w = 0; w < 8; ++w) { a += sq[w]; b += sh[w]; }
-    static_cast<Acc*>(qpart)[vec * nchunks + blockIdx.x] = a;
-    static_cast<Acc*>(hpart)[vec * nchunks + blockIdx.x] = b;
-  }
 }
 
 }  // namespace
@@ -227,16 +193,16 @@ extern "C" int ising_energy_noalloc(const ising_instance* inst, const int8_t* sp
     cudaGetLastError();
     return noalloc_fail(ISING_ECUDA, "no current CUDA device");
   }
-  if (!g_noalloc_ptr[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p) {
+  void* sp = g_noalloc_ptr[dev].load(std::memory_order_acquire);
+  if (!sp) {
+    cudaError_t e = cudaGetSymbolAddress(&sp, g_noalloc_scratch);
+    if (e != cudaSuccess || !sp) {
       cudaGetLastError();
       return noalloc_fail(ISING_ECUDA, "cudaGetSymbolAddress of the scratch array failed");
     }
-    g_noalloc_ptr[dev] = p;
+    g_noalloc_ptr[dev].store(sp, std::memory_order_release);
   }
-  unsigned char* scratch = static_cast<unsigned char*>(g_noalloc_ptr[dev]);
+  unsigned char* scratch = static_cast<unsigned char*>(sp);
   void* qp = scratch;
   void* hp = scratch + (size_t)count * nchunks * 8;
   const bool exact = (inst->j_dtype == ISING_I8 || inst->j_dtype == ISING_I32) &&
@@ -245,16 +211,15 @@ extern "C" int ising_energy_noalloc(const ising_instance* inst, const int8_t* sp
   coefficients(inst, &cq, &ch);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   dim3 grid((unsigned)nchunks, (unsigned)count);
+  // integer h (I32) enters the exact sums unscaled
+  const RowsView<int64_t> v{inst->n, inst->layout, inst->j_dtype, inst->h_dtype, 0, inst->J,
+                            inst->indptr, inst->indices, inst->h};
   if (exact) {
-    energy_rows_i64<true><<<grid, 256, 0, st>>>(inst->n, inst->layout, inst->j_dtype, inst->J,
-                                                inst->indptr, inst->indices, inst->h,
-                                                inst->h_dtype, spins, nchunks, qp, hp);
+    energy_rows<true><<<grid, 256, 0, st>>>(v, spins, nchunks, qp, hp);
     energy_finish<true><<<(unsigned)((count + 127) / 128), 128, 0, st>>>(
         count, nchunks, qp, hp, cq, ch, 0, E_out, nullptr, nullptr);
   } else {
-    energy_rows_i64<false><<<grid, 256, 0, st>>>(inst->n, inst->layout, inst->j_dtype, inst->J,
-                                                 inst->indptr, inst->indices, inst->h,
-                                                 inst->h_dtype, spins, nchunks, qp, hp);
+    energy_rows<false><<<grid, 256, 0, st>>>(v, spins, nchunks, qp, hp);
     energy_finish<false><<<(unsigned)((count + 127) / 128), 128, 0, st>>>(
         count, nchunks, qp, hp, cq, ch, 0, E_out, nullptr, nullptr);
   }
