@@ -64,9 +64,12 @@ enum { ISING_MEM_HOST = 0, ISING_MEM_DEVICE = 1 };
 /* Coupling product precision of the domain-selection step (Sec. III-B).
  *  AUTO        dense -> TC, CSR -> sparse FP32/int kernel.
  *  FP32_PLAIN  dense J in FP32 on the CUDA cores (SIMT FMA), the plain form.
- *  TC          dense J on the tensor cores (tcgen05, FP32 accumulate), exact:
- *              integer |J| <= 256 as one BF16 plane, other J as three BF16
- *              planes hi + mid + lo (about 24 significant bits).
+ *  TC          dense J on the tensor cores (tcgen05, FP32 accumulate), exact
+ *              to FP32 level: integer |J| <= 256 as one BF16 plane, integer
+ *              |J| <= 2048 as one FP16 plane, integer |J| <= 65504 as two
+ *              FP16 planes hi + lo (all exact), other J as two FP16 planes of
+ *              J_ij / 2^e_i with a power-of-two scale per row (about 22
+ *              significant bits: |J - hi - lo| <= 2^-22 |J| + 2^-25 2^e_i).
  *  BF16        dense J rounded once to BF16 (lossy for non-integer J).
  *  FP8         dense J as E4M3 with one FP32 scale per row; spins E4M3
  *              (exact for integer |J| <= 16, lossy otherwise).
@@ -171,7 +174,8 @@ typedef struct ising_ds_stats {
   int32_t resident;         /* tensor-core path kept the state in tensor memory: 1 in the
                                grid-wide form, 2 in the small form (n <= 128, each CTA holds
                                all of J and its restarts' spins on chip); 0 otherwise */
-  int32_t reserved0;
+  int32_t operand_planes;   /* tensor-core path: operand planes of J per product (1 or 2;
+                               the tensor cores execute that many products), else 1 */
 } ising_ds_stats;
 
 /* ------------------------------------------------------------------ context */
@@ -221,6 +225,8 @@ int ising_energy(ising_ctx* ctx, const ising_instance* inst, const int8_t* spins
  *     symmetric with zero diagonal, CSR columns sorted).
  *   - Work is queued on `stream` (a cudaStream_t, NULL = legacy default
  *     stream) and is not waited for; E_out is ready when the stream is.
+ *   - count must lie in [0, 65535] (one grid row per vector); larger
+ *     counts return ISING_EINVAL.
  *   - Partial sums live in one 2 MiB static device array per device (held
  *     until the process exits); a call needs count * ceil(n / 64) * 16
  *     bytes of it and larger calls return ISING_EINVAL. Every call reuses the
@@ -228,7 +234,9 @@ int ising_energy(ising_ctx* ctx, const ising_instance* inst, const int8_t* spins
  *     threads) race and give wrong results. Nothing in it has to start at
  *     zero (each call writes every slot it reads).
  *   - The first call made with a device current looks up the array's device
- *     address; make that first call before any stream capture.
+ *     address and keeps it for the process; make that first call before any
+ *     stream capture. A device reset by the caller invalidates the kept
+ *     address.
  * Integer J and h (I8/I32) accumulate exactly in int64; others in FP64.
  * Errors return a status; ising_energy_noalloc_error() describes the last
  * one on the calling thread. */

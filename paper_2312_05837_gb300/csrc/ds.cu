@@ -63,6 +63,9 @@ __global__ void init_kernel(int64_t n, int64_t Bp, int64_t ld, bool spin_major, 
       static_cast<float*>(spins)[e] = pad ? 0.0f : (pos ? 1.0f : -1.0f);
     } else if (KIND == kSpinBF16) {
       static_cast<__nv_bfloat16*>(spins)[e] = __float2bfloat16(pad ? 0.0f : (pos ? 1.0f : -1.0f));
+    } else if (KIND == kSpinF16) {
+      // FP16: +1 = 0x3C00, -1 = 0xBC00
+      static_cast<uint16_t*>(spins)[e] = pad ? 0 : (pos ? 0x3C00 : 0xBC00);
     } else if (KIND == kSpinE4M3) {
       // E4M3: +1 = 0x38, -1 = 0xB8, 0 = 0x00
       static_cast<uint8_t*>(spins)[e] = pad ? 0 : (pos ? 0x38 : 0xB8);
@@ -93,8 +96,8 @@ template <int KIND>
 __device__ __forceinline__ int8_t spin_at(const void* spins, int64_t n, int64_t Bp, int64_t ld,
                                           int64_t b, int64_t i) {
   if (KIND == kSpinF32) return static_cast<const float*>(spins)[b * ld + i] > 0.0f ? 1 : -1;
-  if (KIND == kSpinBF16)
-    return __bfloat162float(static_cast<const __nv_bfloat16*>(spins)[b * ld + i]) > 0.0f ? 1 : -1;
+  if (KIND == kSpinBF16 || KIND == kSpinF16)  // +-1 in either 16-bit type: the sign bit
+    return (static_cast<const uint16_t*>(spins)[b * ld + i] & 0x8000u) ? -1 : 1;
   if (KIND == kSpinE4M3) return static_cast<const uint8_t*>(spins)[b * ld + i] == 0x38 ? 1 : -1;
   const uint32_t w = static_cast<const uint32_t*>(spins)[i * (Bp / 32) + (b >> 5)];
   return (w >> (b & 31)) & 1u ? 1 : -1;
@@ -256,20 +259,22 @@ __global__ void spins_from_theta_dense(int64_t n, int64_t Bp, int64_t ld,
     if (KIND == kSpinF32) static_cast<float*>(spins)[e] = pad ? 0.f : (pos ? 1.f : -1.f);
     if (KIND == kSpinBF16)
       static_cast<__nv_bfloat16*>(spins)[e] = __float2bfloat16(pad ? 0.f : (pos ? 1.f : -1.f));
+    if (KIND == kSpinF16) static_cast<uint16_t*>(spins)[e] = pad ? 0 : (pos ? 0x3C00 : 0xBC00);
     if (KIND == kSpinE4M3) static_cast<uint8_t*>(spins)[e] = pad ? 0 : (pos ? 0x38 : 0xB8);
   }
 }
 
 // Relaxed spins x = sin(theta) of the state (any layout; `ld` > 0 marks the
 // restart-major dense layout, whose padding columns i >= n stay 0) as FP32
-// or BF16.
-__global__ void x_from_theta(int64_t count, int64_t n, int64_t ld, bool bf16,
+// or in the tensor cores' 16-bit type (kind 1 BF16, 2 FP16; 0 FP32).
+__global__ void x_from_theta(int64_t count, int64_t n, int64_t ld, int kind,
                              const float* __restrict__ th, void* __restrict__ x) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count;
        e += (int64_t)gridDim.x * blockDim.x) {
     const bool pad = ld > 0 && e % ld >= n;
     const float v = pad ? 0.f : sin_proj(th[e]);
-    if (bf16) static_cast<__nv_bfloat16*>(x)[e] = __float2bfloat16(v);
+    if (kind == 1) static_cast<__nv_bfloat16*>(x)[e] = __float2bfloat16(v);
+    else if (kind == 2) static_cast<__half*>(x)[e] = __float2half_rn(v);
     else static_cast<float*>(x)[e] = v;
   }
 }
@@ -366,7 +371,8 @@ int track_step(ising_ds* ds) {
       conv ? ds->conv_step() : nullptr, conv ? ds->conv_count() : nullptr)
   switch (ds->spin_kind) {
     case kSpinF32: ISING_TRACK(kSpinF32); break;
-    case kSpinBF16: ISING_TRACK(kSpinBF16); break;
+    case kSpinBF16:
+    case kSpinF16: ISING_TRACK(kSpinBF16); break;  // both read the sign bit
     case kSpinE4M3: ISING_TRACK(kSpinE4M3); break;
     default: {
       ISING_TRACK(kSpinBits);
@@ -391,7 +397,8 @@ int export_spins_int8(ising_ds* ds, int slot, int8_t* out) {
   const void* sp = ds->spins[slot].p;
   switch (ds->spin_kind) {
     case kSpinF32: export_spins_kernel<kSpinF32><<<g, 256, 0, ctx->stream>>>(ds->n, ds->B, ds->Bp, ds->ld, sp, out); break;
-    case kSpinBF16: export_spins_kernel<kSpinBF16><<<g, 256, 0, ctx->stream>>>(ds->n, ds->B, ds->Bp, ds->ld, sp, out); break;
+    case kSpinBF16:
+    case kSpinF16: export_spins_kernel<kSpinBF16><<<g, 256, 0, ctx->stream>>>(ds->n, ds->B, ds->Bp, ds->ld, sp, out); break;
     case kSpinE4M3: export_spins_kernel<kSpinE4M3><<<g, 256, 0, ctx->stream>>>(ds->n, ds->B, ds->Bp, ds->ld, sp, out); break;
     default: export_spins_kernel<kSpinBits><<<g, 256, 0, ctx->stream>>>(ds->n, ds->B, ds->Bp, ds->ld, sp, out); break;
   }
@@ -407,7 +414,8 @@ int derive_x(ising_ds* ds, int slot) {
   const bool dense = ds->path != ISING_PATH_SPARSE;
   const int64_t count = dense ? ds->Bp * ds->ld : ds->n * ds->Bp;
   x_from_theta<<<grid1d(ctx, count), 256, 0, ctx->stream>>>(
-      count, ds->n, dense ? ds->ld : 0, ds->path == ISING_PATH_TC, ds->theta.as<float>(),
+      count, ds->n, dense ? ds->ld : 0,
+      ds->path == ISING_PATH_TC ? (ds->spin_kind == kSpinF16 ? 2 : 1) : 0, ds->theta.as<float>(),
       ds->xbuf[slot].p);
   ISING_CUDA(ctx, cudaGetLastError());
   return ISING_OK;
@@ -423,7 +431,8 @@ int init_state(ising_ds* ds) {
   size_t spin_bytes;
   switch (ds->spin_kind) {
     case kSpinF32: spin_bytes = elems * 4; break;
-    case kSpinBF16: spin_bytes = elems * 2; break;
+    case kSpinBF16:
+    case kSpinF16: spin_bytes = elems * 2; break;
     case kSpinE4M3: spin_bytes = elems; break;
     default: spin_bytes = ds->n * (ds->Bp / 32) * 4; break;
   }
@@ -441,6 +450,7 @@ int init_state(ising_ds* ds) {
   switch (ds->spin_kind) {
     case kSpinF32: init_kernel<kSpinF32><<<g, 256, 0, ctx->stream>>>(ds->n, ds->Bp, ds->ld, false, seed, th, mm, vv, s1); break;
     case kSpinBF16: init_kernel<kSpinBF16><<<g, 256, 0, ctx->stream>>>(ds->n, ds->Bp, ds->ld, false, seed, th, mm, vv, s1); break;
+    case kSpinF16: init_kernel<kSpinF16><<<g, 256, 0, ctx->stream>>>(ds->n, ds->Bp, ds->ld, false, seed, th, mm, vv, s1); break;
     case kSpinE4M3: init_kernel<kSpinE4M3><<<g, 256, 0, ctx->stream>>>(ds->n, ds->Bp, ds->ld, false, seed, th, mm, vv, s1); break;
     default:
       init_kernel<kSpinBits><<<g, 256, 0, ctx->stream>>>(ds->n, ds->Bp, ds->ld, true, seed, th, mm, vv, nullptr);
@@ -1041,6 +1051,7 @@ extern "C" int ising_ds_import_state(ising_ds* ds, const float* theta, const flo
     switch (ds->spin_kind) {
       case kSpinF32: spins_from_theta_dense<kSpinF32><<<g, 256, 0, ctx->stream>>>(n, ds->Bp, ds->ld, ds->theta.as<float>(), ds->spins[slot].p); break;
       case kSpinBF16: spins_from_theta_dense<kSpinBF16><<<g, 256, 0, ctx->stream>>>(n, ds->Bp, ds->ld, ds->theta.as<float>(), ds->spins[slot].p); break;
+      case kSpinF16: spins_from_theta_dense<kSpinF16><<<g, 256, 0, ctx->stream>>>(n, ds->Bp, ds->ld, ds->theta.as<float>(), ds->spins[slot].p); break;
       default: spins_from_theta_dense<kSpinE4M3><<<g, 256, 0, ctx->stream>>>(n, ds->Bp, ds->ld, ds->theta.as<float>(), ds->spins[slot].p); break;
     }
   }
@@ -1155,7 +1166,7 @@ extern "C" int ising_ds_result(ising_ds* ds, int8_t* best_spins, double* best_en
     stats->kernel_ms = ds->kernel_ms;
     stats->kernel_launches = ds->kernel_launches;
     stats->resident = ds->path == ISING_PATH_TC ? tc_resident_form(ds) : 0;
-    stats->reserved0 = 0;
+    stats->operand_planes = ds->path == ISING_PATH_TC ? ds->planes : 1;
   }
   ISING_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   return ISING_OK;

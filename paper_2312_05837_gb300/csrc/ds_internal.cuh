@@ -85,7 +85,7 @@ __device__ __forceinline__ bool conv_update(double* ring, double* init, long lon
   return false;
 }
 
-enum SpinKind { kSpinF32 = 0, kSpinBF16 = 1, kSpinBits = 2, kSpinE4M3 = 3 };
+enum SpinKind { kSpinF32 = 0, kSpinBF16 = 1, kSpinBits = 2, kSpinE4M3 = 3, kSpinF16 = 4 };
 
 // Sign bit of each byte of four E4M3 spins -> four int8 +1 / -1.
 __device__ __forceinline__ uint32_t e4m3x4_to_pm1(uint32_t w) {
@@ -93,7 +93,8 @@ __device__ __forceinline__ uint32_t e4m3x4_to_pm1(uint32_t w) {
   return 0x01010101u + m * 0xFEu;
 }
 
-// Two BF16 spins -> two int8 +1 / -1 in the low 16 bits.
+// Two 16-bit (BF16 or FP16) spins -> two int8 +1 / -1 in the low 16 bits
+// (only the sign bits are read).
 __device__ __forceinline__ uint32_t bf16x2_to_pm1(uint32_t w) {
   return (((w >> 15) & 1u) ? 0xFFu : 0x01u) | ((((w >> 31) & 1u) ? 0xFFu : 0x01u) << 8);
 }
@@ -115,7 +116,7 @@ __device__ __forceinline__ void copy_spin_row_dense(int8_t* dst, const void* spi
       x.w = e4m3x4_to_pm1(x.w);
       d[v] = x;
     }
-  } else if (KIND == kSpinBF16) {
+  } else if (KIND == kSpinBF16 || KIND == kSpinF16) {
     const uint4* src = reinterpret_cast<const uint4*>(static_cast<const __nv_bfloat16*>(spins) + b * ld);
     uint2* d = reinterpret_cast<uint2*>(dst);
     for (int64_t v = lane; v < (n + 7) / 8; v += 32) {
@@ -169,7 +170,7 @@ struct ising_ds {
   ising::DevMem conv;
   bool conv_all = false;   // every restart has stopped
   // relaxed product (ISING_DS_RELAXED): x_t = sin(theta) in slot t % 2, laid
-  // out like the state (FP32; BF16 on the tensor-core path)
+  // out like the state (FP32; the 16-bit operand type on the tensor-core path)
   ising::DevMem xbuf[2];
   bool relaxed() const { return (p.flags & ISING_DS_RELAXED) != 0; }
   double* conv_ring() const { return conv.as<double>(); }
@@ -181,9 +182,9 @@ struct ising_ds {
   ising::DevMem bias;      // float2 [T + 2]: 1/(1-b1^t), 1/(1-b2^t)
   // dense operands
   ising::DevMem Jf;        // plain path: float n x n
-  ising::DevMem Jop[3];    // tensor path: planes (bf16 or e4m3), [n][ld]
+  ising::DevMem Jop[3];    // tensor path: planes (bf16, fp16 or e4m3), [n][ld]
   int planes = 1;
-  ising::DevMem rowscale;  // fp8 path: float per row
+  ising::DevMem rowscale;  // fp8 / fp16-plane paths: float scale per row (null: 1)
   void* tc = nullptr;      // tensor-core path state (tensor maps etc.)
   // sparse operands
   ising::DevMem sp_val;    // int8 or float values

@@ -3,12 +3,15 @@
 //
 // G = J S is a GEMM with M = spins (J rows, 128 per tile), N = restarts (BN
 // per tile) and K = spins. J is stored as E4M3 [n][ld] when every J is an
-// integer of magnitude <= 16 (exact), else as BF16 planes (one plane when
-// every J is an integer of magnitude <= 256, which BF16 holds exactly; three
-// planes hi + mid + lo otherwise, giving about 24 significant bits); the spins
-// S_t as +-1 of the same type [B][ld] (restart-major, K contiguous). Both
-// operands are K-major, so one TMA box of 128 bytes (a k-block: 128 E4M3 or
-// 64 BF16 elements) x rows fills a 128-byte swizzled shared-memory tile that
+// integer of magnitude <= 16 (exact), as one BF16 plane when every J is an
+// integer of magnitude <= 256 (exact), else as FP16 planes: one for integers
+// up to 2048, hi + lo for integers up to 65504 (both exact) and for other J,
+// which are first divided by a power-of-two scale per row (about 22
+// significant bits; the epilogue multiplies the row's product back, exactly).
+// The spins S_t are +-1 of the same type [B][ld] (restart-major, K
+// contiguous; kind::f16 takes both operands in one type). Both operands are
+// K-major, so one TMA box of 128 bytes (a k-block: 128 E4M3 or 64 16-bit
+// elements) x rows fills a 128-byte swizzled shared-memory tile that
 // tcgen05.mma reads directly. A thread issues one tcgen05.mma only every ~110
 // cycles and one TMA copy every ~250 whatever their sizes, which shapes the
 // kernels below.
@@ -25,12 +28,18 @@
 //              new spin into S_{t+1}, and the energy of the input spins, summed
 //              over each warp's 32 spins by a butterfly across lanes into
 //              one partial row per warp (summed in fixed order afterwards).
+// Tiles are numbered row tile by row tile (the restart tiles of one row tile
+// are consecutive), so one wave of persistent CTAs covers whole row tiles: a
+// J row tile is read from HBM about once per step and shared through L2 by
+// the CTAs of its wave, and only the (smaller) spin operand is read by every
+// wave.
 // While the epilogue drains one accumulator the MMA fills the other. Every
 // mbarrier wait is bounded; a timeout sets an error word and the CTA drains
 // its in-flight copies and MMAs, frees tensor memory and returns.
 #include "ds_internal.cuh"
 #include "tcgen05.cuh"
 
+#include <cuda_fp16.h>
 #include <cuda_fp8.h>
 #include <cudaTypedefs.h>
 
@@ -49,7 +58,8 @@ constexpr long long kWaitCycles = 4000000000ll;  // about 2 s
 struct TcArgs {
   int64_t n, B, ld;
   int nk;      // k-blocks per plane
-  int planes;  // 1 or 3
+  int planes;  // 1 or 2
+  int f16;     // 16-bit operands are FP16 (else BF16): MMA input format and spin encoding
   int mtiles, ntiles;
   StepConsts k;
   const float2* bias;
@@ -73,6 +83,23 @@ struct TcArgs {
   unsigned long long* trace;  // per-CTA role timeline (profiling), or null
   int nfull;   // streaming kernel: whole k-blocks loadable in pairs (0: never pair)
 };
+
+// +1 / -1 in the 16-bit operand type (FP16 0x3C00, BF16 0x3F80; bit 15 is the
+// sign in both, so readers of either test that bit).
+__device__ __forceinline__ uint16_t pm1_16(bool pos, int f16) {
+  return (uint16_t)((f16 ? 0x3C00u : 0x3F80u) | (pos ? 0u : 0x8000u));
+}
+
+// x rounded to nearest in the 16-bit operand type, as its bit pattern.
+__device__ __forceinline__ uint16_t to_op16(float x, int f16) {
+  return f16 ? __half_as_ushort(__float2half_rn(x)) : __bfloat16_as_ushort(__float2bfloat16(x));
+}
+
+// Instruction descriptor of a 128 x N tile: kind::f8f6f4 E4M3 (format 0), or
+// kind::f16 with FP16 (format 0) or BF16 (format 1) inputs.
+__device__ __forceinline__ uint32_t op_idesc(int N, bool fp8, int f16) {
+  return tc::idesc_make(128, N, fp8 ? 0u : (f16 ? 0u : 1u));
+}
 
 __device__ __forceinline__ unsigned long long now_ns() {
   unsigned long long t;
@@ -203,8 +230,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       int issued = 0;
       bool ok = true;
       for (int tl = blockIdx.x; tl < total && ok; tl += gridDim.x) {
-        const int m0 = (tl % P.mtiles) * kBM;
-        const int n0 = (tl / P.mtiles) * BN;
+        const int m0 = (tl / P.ntiles) * kBM;
+        const int n0 = (tl % P.ntiles) * BN;
         for (int kt0 = 0; kt0 < nkt; kt0 += Lay::kKps) {
           if (!tc::mbar_wait(&empty[stage], phase ^ 1, abort_flag, kWaitCycles)) {
             ok = false;
@@ -255,7 +282,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp == 1) {
     if (lane == 0) {
       // ------------------------------------------------ MMA issuer
-      constexpr uint32_t idesc = tc::idesc_make(kBM, BN, FP8 ? 0u : 1u);
+      const uint32_t idesc = op_idesc(BN, FP8, P.f16);
       uint32_t stage = 0, phase = 0;
       int it = 0;
       bool ok = true;
@@ -315,17 +342,17 @@ __global__ void __launch_bounds__(kThreads, 1)
     float* __restrict__ theta = P.theta;
     float* __restrict__ mvec = P.m;
     float* __restrict__ vvec = P.v;
-    const __nv_bfloat16* __restrict__ Sin = static_cast<const __nv_bfloat16*>(P.S);
-    __nv_bfloat16* __restrict__ Sout = static_cast<__nv_bfloat16*>(P.Snext);
+    const uint16_t* __restrict__ Sin = static_cast<const uint16_t*>(P.S);
+    uint16_t* __restrict__ Sout = static_cast<uint16_t*>(P.Snext);
     const uint8_t* __restrict__ Sin8 = static_cast<const uint8_t*>(P.S);
     uint8_t* __restrict__ Sout8 = static_cast<uint8_t*>(P.Snext);
     int it = 0;
     for (int tl = blockIdx.x; tl < total; tl += gridDim.x, ++it) {
       const int buf = it & 1;
       const uint32_t use = (uint32_t)(it >> 1);
-      const int mt = tl % P.mtiles;
+      const int mt = tl / P.ntiles;
       const int64_t m0 = (int64_t)mt * kBM;
-      const int64_t n0 = (int64_t)(tl / P.mtiles) * BN + part * kCols;
+      const int64_t n0 = (int64_t)(tl % P.ntiles) * BN + part * kCols;
       if (!tc::mbar_wait(&acc_full[buf], use & 1, abort_flag, kWaitCycles)) {
         atomicExch(P.err, 3);
         break;
@@ -355,7 +382,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           vv[j] = 0.f;
           sv[j] = 0.f;
           if (ok && MODE != kModeCoupling) {
-            sv[j] = FP8 ? (Sin8[idx] == 0x38 ? 1.f : -1.f) : __bfloat162float(Sin[idx]);
+            sv[j] = FP8 ? (Sin8[idx] == 0x38 ? 1.f : -1.f) : ((Sin[idx] & 0x8000u) ? -1.f : 1.f);
             if (MODE == kModeUpdate || MODE == kModeRelaxed) {
               th[j] = theta[idx];
               mm[j] = mvec[idx];
@@ -409,9 +436,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             mvec[idx] = mm[j];
             vvec[idx] = vv[j];
             if (FP8) Sout8[idx] = sin_nonneg(th[j]) ? 0x38 : 0xB8;
-            else Sout[idx] = __float2bfloat16(sin_nonneg(th[j]) ? 1.f : -1.f);
+            else Sout[idx] = pm1_16(sin_nonneg(th[j]), P.f16);
             if (MODE == kModeRelaxed)
-              static_cast<__nv_bfloat16*>(P.Xnext)[idx] = __float2bfloat16(sin_proj(th[j]));
+              static_cast<uint16_t*>(P.Xnext)[idx] = to_op16(sin_proj(th[j]), P.f16);
           }
         }
         if (MODE == kModeUpdate || MODE == kModeEnergy) {
@@ -443,21 +470,51 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
-__global__ void to_planes_kernel(const void* J, int dt, int64_t n, int64_t ld, int planes,
-                                 __nv_bfloat16* p0, __nv_bfloat16* p1, __nv_bfloat16* p2) {
+// 16-bit operand planes of J, [n][ld] each (columns past n are 0):
+//   kind 0  one BF16 plane (exact for integer |J| <= 256),
+//   kind 1  FP16 planes of J_ij * 2^e_i: hi = fp16(x), lo = fp16(x - hi) when
+//           planes == 2; with the power-of-two row exponents e_i of
+//           `rowscale` (2^-e_i per row, from row_pow2_scale_kernel) or e_i = 0
+//           when it is null. Each rounding is to nearest, so
+//           |x - hi - lo| <= 2^-22 |x| + 2^-25 (the smallest FP16 subnormal is 2^-24).
+__global__ void to_planes_kernel(const void* J, int dt, int64_t n, int64_t ld, int kind, int planes,
+                                 const float* rowscale, uint16_t* p0, uint16_t* p1) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * ld;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = e / ld, k = e - i * ld;
-    const double x = k < n ? load_as_double(J, dt, i * n + k) : 0.0;
-    const __nv_bfloat16 hi = __double2bfloat16(x);
-    p0[e] = hi;
-    if (planes == 3) {
-      const double r1 = x - (double)__bfloat162float(hi);
-      const __nv_bfloat16 mid = __double2bfloat16(r1);
-      const double r2 = r1 - (double)__bfloat162float(mid);
-      p1[e] = mid;
-      p2[e] = __double2bfloat16(r2);
+    double x = k < n ? load_as_double(J, dt, i * n + k) : 0.0;
+    if (kind == 0) {
+      p0[e] = __bfloat16_as_ushort(__double2bfloat16(x));
+      continue;
     }
+    if (rowscale) x = x / (double)rowscale[i];  // exact: a power of two
+    const __half hi = __double2half(x);
+    p0[e] = __half_as_ushort(hi);
+    if (planes == 2) p1[e] = __half_as_ushort(__double2half(x - (double)__half2float(hi)));
+  }
+}
+
+// Per-row power-of-two scales for the FP16 planes: with a_i = max_j |J_ij|,
+// scale_i = 2^(E_i - 15) where a_i = f 2^E_i, f in [0.5, 1), so that
+// a_i / scale_i lies in [2^14, 2^15) (below the FP16 maximum 65504, and the
+// low plane stays clear of the subnormal range); 1 for an all-zero row. The
+// epilogue multiplies the accumulated product of row i by scale_i, exactly.
+__global__ void row_pow2_scale_kernel(const void* J, int dt, int64_t n, float* scale) {
+  __shared__ double sm[32];
+  for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
+    double mx = 0.0;
+    for (int64_t k = threadIdx.x; k < n; k += blockDim.x) mx = fmax(mx, fabs(load_as_double(J, dt, i * n + k)));
+    for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mx = fmax(mx, sm[w]);
+      mx = fmax(mx, sm[0]);
+      int ex = 15;
+      if (mx > 0.0) frexp(mx, &ex);
+      scale[i] = ldexpf(1.0f, min(max(ex - 15, -126), 127));
+    }
+    __syncthreads();
   }
 }
 
@@ -707,7 +764,7 @@ __device__ __forceinline__ void resident_chunks(const TcResArgs& R, const EpiLan
         for (int j = 0; j < kChunk; ++j) {
           const bool sp = (new_bits >> j) & 1u;
           if (FP8) static_cast<uint8_t*>(Sout)[base + j * P.ld] = sp ? 0x38 : 0xB8;
-          else static_cast<__nv_bfloat16*>(Sout)[base + j * P.ld] = __float2bfloat16(sp ? 1.f : -1.f);
+          else static_cast<uint16_t*>(Sout)[base + j * P.ld] = pm1_16(sp, P.f16);
         }
       } else {
 #pragma unroll
@@ -715,7 +772,7 @@ __device__ __forceinline__ void resident_chunks(const TcResArgs& R, const EpiLan
           if (j >= nv) break;
           const bool sp = (new_bits >> j) & 1u;
           if (FP8) static_cast<uint8_t*>(Sout)[base + j * P.ld] = sp ? 0x38 : 0xB8;
-          else static_cast<__nv_bfloat16*>(Sout)[base + j * P.ld] = __float2bfloat16(sp ? 1.f : -1.f);
+          else static_cast<uint16_t*>(Sout)[base + j * P.ld] = pm1_16(sp, P.f16);
         }
       }
       if (last) {
@@ -939,7 +996,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp == 1) {
     if (lane == 0) {
       // ------------------------------------------------ MMA issuer
-      constexpr uint32_t idesc = tc::idesc_make(kBM, GN, FP8 ? 0u : 1u);
+      const uint32_t idesc = op_idesc(GN, FP8, P.f16);
       uint32_t stage = 0, phase = 0;
       bool ok = jres == 0 || tc::mbar_wait(jfull, 0, abort_flag, kWaitCycles);
       for (int64_t p = 0; p < NP && ok; ++p) {
@@ -1334,7 +1391,7 @@ __global__ void __launch_bounds__(kSmallThreads, 1)
   uint32_t prev_bits = 0, prev2_bits = 0, best_bits = 0, any_bits = 0;
   float2 bc = make_float2(0.f, 0.f);
   if (epi && K > 0) bc = P.bias[t0 + 1];
-  constexpr uint32_t idesc = tc::idesc_make(kBM, BN, FP8 ? 0u : 1u);
+  const uint32_t idesc = op_idesc(BN, FP8, P.f16);
   int64_t s = 0;
   for (; s < K && ok; ++s) {
     const long long t = t0 + s + 1;
@@ -1421,7 +1478,7 @@ __global__ void __launch_bounds__(kSmallThreads, 1)
               const bool sp = sin_nonneg(tj);
               uint8_t* dst = Snxt + (size_t)kb * Lay::kSk + swz_offset(bl0 + j, kk, esize);
               if (FP8) *dst = sp ? 0x38 : 0xB8;
-              else *reinterpret_cast<__nv_bfloat16*>(dst) = __float2bfloat16(sp ? 1.f : -1.f);
+              else *reinterpret_cast<uint16_t*>(dst) = pm1_16(sp, P.f16);
               const int64_t b = n0 + bl0 + j;
               if (last && b < P.B) {
                 const int64_t idx = b * P.ld + i;
@@ -1495,7 +1552,7 @@ __global__ void __launch_bounds__(kSmallThreads, 1)
       const uint8_t* src = Sfin + (size_t)(ii / kBK) * Lay::kSk + swz_offset(b, ii % kBK, esize);
       const int64_t idx = (n0 + b) * P.ld + ii;
       if (FP8) static_cast<uint8_t*>(R.spins_out)[idx] = *src;
-      else static_cast<__nv_bfloat16*>(R.spins_out)[idx] = *reinterpret_cast<const __nv_bfloat16*>(src);
+      else static_cast<uint16_t*>(R.spins_out)[idx] = *reinterpret_cast<const uint16_t*>(src);
     }
     for (int b = threadIdx.x; b < BN; b += blockDim.x) {
       const int64_t gb = n0 + b;
@@ -1533,6 +1590,7 @@ struct TcState {
   int grid = 1;
   bool maps_ready = false;
   bool fp8 = false;
+  bool f16 = false;       // 16-bit operands are FP16 (two-plane form), else BF16
   bool resident = false;  // one tile per CTA, state kept in tensor memory
   DevMem gsync;           // abort word + per-column barrier counters
   int emode = 0;          // resident epilogue's integer energy mode (0 F2I, 1 offset, 2 packed)
@@ -1752,16 +1810,40 @@ int tc_setup(ising_ds* ds) {
     ISING_CUDA(ctx, cudaGetLastError());
     for (int p = 0; p < 3; ++p)
       ISING_TRY(make_map(ctx, &st->A[p], ds->Jop[0].p, ds->n, ds->n, ds->ld, 128, kBM, true));
+  } else if (exact256 || ds->prec == ISING_PREC_BF16) {
+    // one BF16 plane: exact for integers up to 256; beyond that it rounds J,
+    // and the sums are no longer the instance's integers
+    ds->planes = 1;
+    if (!exact256) ds->int_energy = false;
+    ISING_TRY(dev_alloc(ctx, ds->Jop[0], plane_elems * 2));
+    to_planes_kernel<<<g, 256, 0, ctx->stream>>>(I.J.p, I.j_dtype, ds->n, ds->ld, 0, 1, nullptr,
+                                                 ds->Jop[0].as<uint16_t>(), nullptr);
+    ISING_CUDA(ctx, cudaGetLastError());
+    for (int p = 0; p < 3; ++p)
+      ISING_TRY(make_map(ctx, &st->A[p], ds->Jop[0].p, ds->n, ds->n, ds->ld, 64, kBM, false));
   } else {
-    ds->planes = (exact256 || ds->prec == ISING_PREC_BF16) ? 1 : 3;
-    // one BF16 plane of integers beyond 256 rounds J: the sums are no longer
-    // the instance's integers
-    if (!exact256 && ds->planes == 1) ds->int_energy = false;
+    // FP16 planes: integers up to 2048 in one plane and up to 65504 in two
+    // (hi + lo, both exact); other J as hi + lo of J_ij / scale_i with a
+    // power-of-two scale per row (about 22 significant bits; the products are
+    // then no longer integers)
+    st->f16 = true;
+    ds->spin_kind = kSpinF16;
+    const bool int2048 = I.j_integer && I.j_absmax <= 2048.0;
+    const bool int65504 = I.j_integer && I.j_absmax <= 65504.0;
+    ds->planes = int2048 ? 1 : 2;
+    const float* rs = nullptr;
+    if (!int65504) {
+      ds->int_energy = false;
+      ISING_TRY(dev_alloc(ctx, ds->rowscale, ds->n * 4));
+      row_pow2_scale_kernel<<<(int)std::min<int64_t>(ds->n, 65535), 256, 0, ctx->stream>>>(
+          I.J.p, I.j_dtype, ds->n, ds->rowscale.as<float>());
+      ISING_CUDA(ctx, cudaGetLastError());
+      rs = ds->rowscale.as<float>();
+    }
     for (int p = 0; p < ds->planes; ++p) ISING_TRY(dev_alloc(ctx, ds->Jop[p], plane_elems * 2));
     to_planes_kernel<<<g, 256, 0, ctx->stream>>>(
-        I.J.p, I.j_dtype, ds->n, ds->ld, ds->planes, ds->Jop[0].as<__nv_bfloat16>(),
-        ds->Jop[ds->planes == 3 ? 1 : 0].as<__nv_bfloat16>(),
-        ds->Jop[ds->planes == 3 ? 2 : 0].as<__nv_bfloat16>());
+        I.J.p, I.j_dtype, ds->n, ds->ld, 1, ds->planes, rs, ds->Jop[0].as<uint16_t>(),
+        ds->planes == 2 ? ds->Jop[1].as<uint16_t>() : nullptr);
     ISING_CUDA(ctx, cudaGetLastError());
     for (int p = 0; p < 3; ++p) {
       const void* base = ds->Jop[p < ds->planes ? p : 0].p;
@@ -1891,6 +1973,7 @@ int tc_run(ising_ds* ds, int mode, float* Gout) {
   a.ld = ds->ld;
   a.nk = ceil_div_i(ds->n, st->fp8 ? 128 : 64);
   a.planes = ds->planes;
+  a.f16 = st->f16 ? 1 : 0;
   a.mtiles = ceil_div_i(ds->n, kBM);
   a.ntiles = ceil_div_i(ds->B, st->BN);
   a.k = ds->k;
@@ -1969,6 +2052,7 @@ int tc_run_resident(ising_ds* ds, int64_t steps) {
     a.ld = ds->ld;
     a.nk = ceil_div_i(ds->n, st->fp8 ? 128 : 64);
     a.planes = ds->planes;
+    a.f16 = st->f16 ? 1 : 0;
     a.mtiles = 1;
     a.ntiles = st->small_grid;
     a.k = ds->k;
@@ -2011,6 +2095,7 @@ int tc_run_resident(ising_ds* ds, int64_t steps) {
   a.ld = ds->ld;
   a.nk = ceil_div_i(ds->n, st->fp8 ? 128 : 64);
   a.planes = ds->planes;
+  a.f16 = st->f16 ? 1 : 0;
   a.mtiles = ceil_div_i(ds->n, kBM);
   a.ntiles = ceil_div_i(ds->B, st->BN);
   a.k = ds->k;

@@ -66,7 +66,7 @@ size_t estimate_footprint(const ising_instance* in, const ising_ds_params* p) {
   double bytes;
   if (in->layout == ISING_LAYOUT_DENSE) {
     bytes = n * n * jsz * 2.0          // uploaded instance and the reduced copy
-            + n * ld * 2.0 * 3.0       // operand planes (at most three BF16)
+            + n * ld * 2.0 * 2.0       // operand planes (at most two 16-bit)
             + B * ld * (12.0 + 3.0 * 2.0);  // theta, m, v and three spin slots
   } else {
     const double nnz = (double)in->nnz;

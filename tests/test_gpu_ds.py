@@ -81,9 +81,10 @@ def test_one_step_parity_along_a_run(gpu_ctx, name, prec, lr, mu):
     s = api.Session(gpu_ctx, inst, restarts=40, steps=12, lr=lr, mu=mu, seed=3, **_kw(prec))
     st = s.export_state()
     for _ in range(12):
+        G0 = s.coupling()
         s.run(1)
         nxt = s.export_state()
-        U.check_step(inst, st, nxt, s.last_energies(), p, _exact(inst))
+        U.check_step(inst, st, nxt, s.last_energies(), p, _exact(inst), G0=G0)
         st = nxt
     s.close()
 
