@@ -1,13 +1,17 @@
 #!/usr/bin/env python
 """Benchmark of the pruning + domain-selection hot path on GB300.
 
-One bench step is one full solve through the C ABI on a synthetic max-cut
-instance shaped like the paper's benchmark problems: pruning, B restarts x T
-steps of the fused domain-selection step (Sec. III-B), best-of-restarts,
-reconstruction and the energy of the result on the full instance.
+One bench step is one full solve through the C ABI on a synthetic instance
+shaped like the paper's workloads: pruning, B restarts x T steps of the fused
+domain-selection step (Sec. III-B), best-of-restarts, reconstruction and the
+energy of the result on the full instance.
 
-Default workload: Erdos-Renyi N=2000, mean degree 10, weights +-1, J = -W/2
-(int8 dense), h = 0, 1024 restarts x 2000 steps, lr 6.0.
+Default workload (the largest single-GPU configuration): dense SK N = 4096,
+J_ij ~ N(0, 1/N) FP32, h_i ~ N(0, 0.1), 4096 restarts x 5000 steps, lr 6.0,
+on the tensor cores with J as two FP16 planes (FP32-level products, FP32
+accumulate). The same JSON line also carries the other bench workloads
+(ER N = 2000 max-cut, 2D torus N = 20 000, ER N = 100 000 with pendant trees)
+with their own throughput and roofline figures.
 
 Prints one JSON line (metric: relaxed spin-updates/s = N_reduced * B * T per
 second of device time). ``--impl reference`` times the FP64 CPU oracle on the
@@ -53,11 +57,17 @@ def args_():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="er2000", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="sk4096", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="auto")
     ap.add_argument("--lr", type=float, default=6.0)
     ap.add_argument("--mu", type=float, default=0.0)
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0,
+                    help="bounded oracle sample per CPU-baseline timing")
+    ap.add_argument("--cpu-leg", type=int, default=0, help=argparse.SUPPRESS)
+    ap.add_argument("--secondary", default="er2000,torus20k,er100k_pendant",
+                    help="other workloads measured into the same line ('' for none)")
+    ap.add_argument("--e2e-steps", type=int, default=5,
+                    help="solves timed end to end with host buffers (at most --steps)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the time-to-target and serving legs")
@@ -164,19 +174,20 @@ def traffic_for(kernel: str, src_file: str, workload: str):
     return d["bytes_per_launch"] if d.get("source_sha") == h else None
 
 
-def launches_per_solve(T: int, rounds: int, path: int, resident: bool, rowsum: bool) -> int:
+def launches_per_solve(T: int, rounds: int, path: int, resident: bool, rowsum: bool,
+                       rowscale: bool) -> int:
     """Kernels of one solve, as the ncu launch list of a solve shows them:
     instance checks (couplings twice, field once), pruning (dense->CSR 2,
     init 1, 7 per round incl. the final empty one, sum + reduced J + reduced
     field 3), session set-up (fills 2, init 1, operand 1, plus the row-sum
-    bound when the tensor-core path accumulates integer energies: `rowsum`),
-    the steps (one launch when resident, else step + track per step, plus the
-    copy of improved bit-packed spins on the sparse path), finish
-    (energy-only step + track (+ copy) + argmin), reconstruction (1),
-    full-instance energy (2)."""
+    bound when the tensor-core path accumulates integer energies: `rowsum`,
+    plus the per-row scales of row-scaled operands: `rowscale`), the steps
+    (one launch when resident, else step + track per step, plus the copy of
+    improved bit-packed spins on the sparse path), finish (energy-only step +
+    track (+ copy) + argmin), reconstruction (1), full-instance energy (2)."""
     per_step = 3 if path == 2 else 2
     steps = 1 if resident else per_step * T
-    setup = 4 + (1 if rowsum else 0)
+    setup = 4 + (1 if rowsum else 0) + (1 if rowscale else 0)
     return 3 + 3 + 7 * (rounds + 1) + 3 + setup + steps + per_step + 1 + 1 + 2
 
 
@@ -194,6 +205,18 @@ def over_ranks(dist, x: float, op: str, device) -> float:
     return float(t.item())
 
 
+def reference_sample_steps(name: str) -> int:
+    """Domain-selection steps per bounded oracle sample: one on the N = 4096
+    dense workload (two FP64 products of 4096 x 4096 by 4096 x 4096 per
+    sample with the final evaluation), three elsewhere."""
+    return 1 if name == "sk4096" else 3
+
+
+def host_info() -> dict:
+    import platform
+    return {"uname_m": platform.machine(), "nproc": os.cpu_count()}
+
+
 def run_reference(a, rank, world):
     """The FP64 CPU oracle on the same workload: each step is one bounded
     sample of the solve (pruning, `sample` domain-selection steps over all
@@ -206,7 +229,7 @@ def run_reference(a, rank, world):
     from oracle import ising, pruning
     name, B, T = WORKLOADS[a.workload]
     inst = synth.workload(name, 0)
-    sample = 3
+    sample = reference_sample_steps(name)
 
     def one():
         res = pruning.prune(inst)
@@ -233,7 +256,9 @@ def run_reference(a, rank, world):
                        "sample_steps_per_bench_step": sample, "l2": "n/a (CPU)"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"per bench step: prune + {sample} of {T} steps x {B} "
-                                       "restarts + reconstruct + energy, numpy FP64"},
+                                       "restarts (+ the final evaluation) + reconstruct + "
+                                       "energy, numpy FP64, BLAS threads = all host cores",
+                             **host_info()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -241,15 +266,21 @@ def run_reference(a, rank, world):
 
 # ----------------------------------------------------------------- CPU baseline
 
-def cpu_baseline(a, inst, B, seconds):
+def cpu_leg(a):
+    """Child process of the CPU baseline (BLAS threads fixed by its
+    environment before numpy loads): the oracle's domain-selection step on
+    the workload's instance, repeated for about `cpu_seconds`; prints one
+    JSON object."""
     import numpy as np
+    import synth
     from oracle import domain_selection as ods
-    from oracle import ising
+    from oracle import ising, rng
+    name, B, T = WORKLOADS[a.workload]
+    inst = synth.workload(name, 0)
     cq, ch = ising.coefficients(inst.j_scale, inst.convention)
     J = ising.coupling_matrix(inst)
     h = ising.field(inst)
     p = ods.Params(restarts=B, steps=1 << 30, lr=a.lr, mu=a.mu, seed=0)
-    from oracle import rng
     th = rng.theta_init(0, B, inst.n)
     m = np.zeros_like(th)
     v = np.zeros_like(th)
@@ -259,93 +290,109 @@ def cpu_baseline(a, inst, B, seconds):
         r = ods.step(J, h, cq, ch, p, th, m, v, steps + 1)
         th, m, v = r.theta, r.m, r.v
         steps += 1
-        if time.perf_counter() - t0 >= seconds and steps >= 2:
+        if time.perf_counter() - t0 >= a.cpu_seconds:
             break
     dt = time.perf_counter() - t0
-    return {"value": inst.n * B * steps / dt, "unit": UNIT, "cores": os.cpu_count(),
-            "kind": "oracle",
-            "sample": f"{steps} domain-selection steps x {B} restarts on the same instance "
-                      f"(numpy FP64, {dt:.1f} s)"}
+    print(json.dumps({"n": inst.n, "steps": steps, "seconds": dt,
+                      "value": inst.n * B * steps / dt}), flush=True)
+
+
+def cpu_baseline(a, B, T):
+    """The oracle timed on the host cores twice, single-threaded and with
+    BLAS on every core, each in a fresh interpreter (numpy fixes its thread
+    count when it loads): relaxed spin-updates/s of its domain-selection
+    step on the same instance, over a bounded sample (about `cpu_seconds`
+    each); the full run's time is this rate extrapolated to N B T."""
+    out = {}
+    ncores = os.cpu_count() or 1
+    for label, threads in [("single_thread", 1), ("all_cores", ncores)]:
+        env = dict(os.environ)
+        for k in ["OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"]:
+            env[k] = str(threads)
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-leg", "1",
+                            "--workload", a.workload, "--cpu-seconds", str(a.cpu_seconds),
+                            "--lr", str(a.lr), "--mu", str(a.mu)],
+                           env=env, capture_output=True, text=True, timeout=600)
+        if r.returncode != 0:
+            out[label] = {"error": r.stderr[-400:]}
+            continue
+        d = json.loads(r.stdout.strip().splitlines()[-1])
+        d["threads"] = threads
+        d["extrapolated_full_run_s"] = d["n"] * B * T / d["value"]
+        out[label] = d
+    best = out.get("all_cores", {})
+    return {"value": best.get("value"), "unit": UNIT, "cores": ncores, "kind": "oracle",
+            "sample": f"{best.get('steps')} domain-selection steps x {B} restarts on the same "
+                      f"instance (numpy FP64, BLAS threads = {ncores}, "
+                      f"{best.get('seconds', 0):.1f} s); the full run "
+                      f"({T} steps) extrapolated from it",
+            **host_info(), "single_thread": out.get("single_thread"), "all_cores": best}
 
 
 # ----------------------------------------------------------------- time to target
 
-def time_to_target(ctx, dinst, integer, B, T, seed, chunk=50):
-    """Time until the best-so-far energy reaches E*, the best the plain FP32
-    form reaches on the same instance and seed, for the plain form and the
-    fast form (AUTO: exact E4M3 for integer couplings; row-scaled E4M3 with
-    exact re-evaluation otherwise). Both advance in chunks of `chunk` steps;
-    after each chunk the restarts' best spins are evaluated exactly (FP64 on
-    the device; the tracked integer energies already are exact) and the
-    wall time of steps plus checks is accumulated."""
-    import numpy as np
+def exact_best(ctx, dinst, integer, s):
+    """The lowest exact energy among a session's per-restart bests: exact
+    already for integer couplings; otherwise the restarts whose tracked
+    (FP32-partial) best lies within 1e-4 |E_min| of the minimum (at most 16)
+    are re-evaluated in FP64 on the device."""
     import torch
     from paper_2312_05837_gb300 import api
+    E, _, sp = s.restart_best(device=True)
+    if integer:
+        return float(E.min().item())
+    emin = E.min()
+    cand = torch.nonzero(E <= emin + 1e-4 * emin.abs()).flatten()[:16]
+    return float(api.energy(ctx, dinst, sp[cand].contiguous()).min().item())
 
-    def trace(prec, T=T):
+
+def precision_runs(ctx, dinst, integer, n, B, T, seed, forms, chunk):
+    """Each operand form runs the same instance and seed for T steps in
+    chunks of `chunk` steps; after each chunk the exact best so far is taken
+    (exact_best). Per form: spin-updates/s from the device time of the steps,
+    the final exact best, and the wall time (steps + checks) of each check.
+    Time to target (Sec. IV-C's time-to-solution idea, target E* = the plain
+    FP32 form's final best on the same instance and seed): the first check
+    at which a form's best <= E*."""
+    import torch
+    from paper_2312_05837_gb300 import api
+    out, hist = {}, {}
+    # first uses of a kernel (ours and torch's reductions) load it
+    for prec in forms:
+        s = api.Session(ctx, dinst, restarts=B, steps=2, seed=seed, precision=prec)
+        s.run(2)
+        exact_best(ctx, dinst, integer, s)
+        s.close()
+    for prec in forms:
         s = api.Session(ctx, dinst, restarts=B, steps=T, seed=seed, precision=prec)
-        hist = []
-        done, ms = 0, 0.0
         torch.cuda.synchronize()
+        done, ms, h = 0, 0.0, []
         while done < T:
             k = min(chunk, T - done)
             w0 = time.perf_counter()
             s.run(k)
             done += k
-            E, _, sp = s.restart_best(device=True)
-            if not integer:
-                E = api.energy(ctx, dinst, sp)
-            best = float(E.min().item())
+            best = exact_best(ctx, dinst, integer, s)
             ms += 1e3 * (time.perf_counter() - w0)
-            hist.append((ms, best))
+            h.append((ms, best))
+        s.finish()
+        res = s.result()
         s.close()
-        return hist, s
-
-    fast_prec = "auto" if integer else "fp8"
-    # first uses of a kernel (ours and torch's reduction) load it: run both
-    # forms' code paths once outside the timing
-    for prec in ["fp32", fast_prec]:
-        trace(prec, T=2)
-    hist_p, _ = trace("fp32")
-    target = hist_p[-1][1]
-    hist_f, _ = trace(fast_prec)
-
-    def first(hist):
-        for ms, e in hist:
-            if e <= target:
-                return ms
-        return None
-
-    tp, tf = first(hist_p), first(hist_f)
-    return {"target_energy": target, "plain_fp32_ms": tp, "fast_ms": tf,
-            "fast_precision": "e4m3 (exact)" if integer else "e4m3 row-scaled, exact re-evaluation",
-            "speedup": (tp / tf) if (tp and tf) else None, "chunk_steps": chunk,
-            "fast_best_energy": hist_f[-1][1],
-            "timing": "wall time of the steps and the exact checks after each chunk"}
-
-
-def precision_sweep(ctx, dinst, n, B, T, seed=1):
-    """One full domain selection per operand precision on the same instance
-    and seed: the plain FP32 CUDA-core form, three BF16 planes (FP32-exact),
-    one BF16 plane and row-scaled E4M3 (the N = 4096 SK workload); spin-updates/s from
-    device time and the best energy, re-evaluated exactly in FP64."""
-    import torch
-    from paper_2312_05837_gb300 import api
-    out = {}
-    for prec in ["fp32", "tc", "bf16", "fp8"]:
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        r = api.select_domain(ctx, dinst, restarts=B, steps=T, seed=seed, precision=prec)
-        e1.record()
-        e1.synchronize()
-        ms = e0.elapsed_time(e1)
-        out[prec] = {"value": n * B * T / (ms / 1e3), "ms": ms,
-                     "best_energy": float(r["best_energy"].item())}
-    ref = out["fp32"]["best_energy"]
-    for prec in out:
-        out[prec]["gap_vs_fp32"] = (out[prec]["best_energy"] - ref) / abs(ref)
-    return out
+        hist[prec] = h
+        out[prec] = {"value": n * B * T / (res["device_ms"] / 1e3), "device_ms": res["device_ms"],
+                     "best_energy": res["best_energy"], "operand_planes": res["operand_planes"]}
+    target = out["fp32"]["best_energy"]
+    for prec in forms:
+        out[prec]["gap_vs_fp32"] = (out[prec]["best_energy"] - target) / abs(target)
+        out[prec]["time_to_target_ms"] = next((ms for ms, e in hist[prec] if e <= target), None)
+    tp = out["fp32"]["time_to_target_ms"]
+    for prec in forms:
+        tf = out[prec]["time_to_target_ms"]
+        out[prec]["speedup_vs_fp32"] = (tp / tf) if (tp and tf) else None
+    return {"target_energy": target, "seed": seed, "chunk_steps": chunk, "forms": out,
+            "timing": "wall time of the steps and of the exact check after each chunk "
+                      "(integer couplings: tracked energies are exact; otherwise FP64 "
+                      "re-evaluation of the near-best restarts on the device)"}
 
 
 # ----------------------------------------------------------------- serving
@@ -405,10 +452,125 @@ def serving(ctx, count=40, rate=200.0, n_max=2048, B=256, T=2000, seed=5):
             "all_ok": all(r["status"] == 0 for r in res)}
 
 
+# ----------------------------------------------------------------- roofline
+
+def roofline(ctx, inst, dinst, name, B, kw, steps, pk, sessions=1):
+    """The dominant step kernel, timed launch by launch with CUDA events on
+    the context's stream (ISING_DS_PROFILE) over `steps` steps of a session
+    on the full instance; with several sessions, the median of their average
+    launch times (all kept). Algorithmic work per launch: 2 N^2 B flop on
+    the dense paths, 24.25 B per update (theta, m, v read + write, spin bits)
+    on the sparse path."""
+    from paper_2312_05837_gb300 import api
+    per = []
+    st = None
+    for k in range(sessions):
+        prof = api.Session(ctx, dinst, restarts=B, steps=steps, seed=7 + k, profile=True, **kw)
+        prof.run(steps)
+        st = prof.result()
+        prof.close()
+        per.append(st["kernel_ms"] / max(st["kernel_launches"], 1))
+    avg_ms = statistics.median(per)
+    path = st["path"]
+    n = inst.n
+    if path == 2:  # sparse: HBM bound
+        alg = n * ((B + 127) // 128 * 128) * (24 + 0.25)
+        roof = {"bound": "hbm", "achieved": alg / (avg_ms / 1e3) / 1e9, "peak": pk["hbm_gbs"],
+                "unit": "GB/s", "peak_note": "measured copy bandwidth"}
+        kname, ksrc = "sparse_step_kernel", "paper_2312_05837_gb300/csrc/ds_sparse.cu"
+    elif path == 1:  # tensor cores: 2 N^2 B flop per step
+        alg = 2.0 * n * n * B
+        fp8 = st["precision"] == 4
+        peak = pk["bf16_tflops_sustained"] * (2.0 if fp8 else 1.0)
+        roof = {"bound": "tensor", "achieved": alg / (avg_ms / 1e3) / 1e12, "peak": peak,
+                "unit": "TFLOP/s",
+                "peak_note": ("E4M3: 2 x measured BF16 sustained (nominal FP8/BF16 ratio)" if fp8
+                              else "measured BF16 sustained (FP16 runs at the BF16 rate)")}
+        planes = st["operand_planes"]
+        if planes > 1:
+            # J as hi + lo planes: the tensor cores execute `planes` products
+            roof["operand_planes"] = planes
+            roof["executed_frac"] = planes * roof["achieved"] / peak
+        kname = {0: "tc_step_kernel", 1: "tc_resident_kernel", 2: "tc_small_kernel"}[st["resident"]]
+        ksrc = "paper_2312_05837_gb300/csrc/ds_tc.cu"
+    else:  # plain FP32 FMA on the CUDA cores
+        import torch
+        alg = 2.0 * n * n * B
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        fp32_peak = sms * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": alg / (avg_ms / 1e3) / 1e12, "peak": fp32_peak,
+                "unit": "TFLOP/s", "peak_note": "152 SMs x 128 FP32 lanes x 2 flop x max clock"}
+        kname, ksrc = "plain_step_kernel", "paper_2312_05837_gb300/csrc/ds_plain.cu"
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = traffic_for(kname, ksrc, name)
+    roof["kernel"] = kname
+    roof["peak_source"] = pk["source"]
+    roof["avg_launch_ms"] = avg_ms
+    roof["algorithmic_per_launch"] = alg
+    if sessions > 1:
+        roof["sessions_avg_launch_ms"] = per
+    return roof, st
+
+
+def timed_solves(ctx, dinst, B, T, kw, K, flush, stream, seed0=0):
+    """K solves, each bracketed by CUDA events on the launching stream, the
+    L2 flushed (a 512 MB write) before each one outside the timed region.
+    Returns the summed device milliseconds and the last result."""
+    import torch
+    from paper_2312_05837_gb300 import api
+    total_ms, last = 0.0, None
+    for k in range(K):
+        flush.fill_(float(k))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        last = api.solve(ctx, dinst, restarts=B, steps=T, seed=seed0 + k, **kw)
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+    return total_ms, last
+
+
+def secondary(ctx, name, a, pk, flush, stream, solves=3, warm=2):
+    """Another bench workload measured into the same line: its own
+    throughput over `solves` timed solves (clocks sampled meanwhile) and its
+    dominant kernel's roofline (sparse: median of 5 profiled sessions)."""
+    import torch
+    import synth
+    from paper_2312_05837_gb300 import api
+    inst_name, B, T = WORKLOADS[name]
+    inst = synth.workload(inst_name, 0)
+    dinst = device_instance(inst, torch)
+    kw = dict(lr=a.lr, mu=a.mu, precision="auto")
+    for w in range(warm):
+        api.solve(ctx, dinst, restarts=B, steps=T, seed=1000 + w, **kw)
+    torch.cuda.synchronize()
+    pr = api.prune(ctx, inst)
+    n_red = pr.n_reduced
+    pr.close()
+    clocks = Clocks(torch.cuda.current_device())
+    clocks.start()
+    ms, last = timed_solves(ctx, dinst, B, T, kw, solves, flush, stream)
+    clk = clocks.stop()
+    roof, st = roofline(ctx, inst, dinst, name, B, kw, a.profile_steps, pk,
+                        sessions=5 if last["path"] == 2 else 1)
+    out = {"workload": f"{name}: N={inst.n} (N_reduced={n_red}), restarts={B}, steps={T}",
+           "value": n_red * B * T * solves / (ms / 1e3), "unit": UNIT, "solves": solves,
+           "ms_per_solve": ms / solves, "path": {0: "plain", 1: "tc", 2: "sparse"}[last["path"]],
+           "precision": last["precision"], "kernel_us": roof["avg_launch_ms"] * 1e3,
+           "roofline": roof, "clocks": clk, "best_energy": float(last["best_energy"].item())}
+    del dinst
+    torch.cuda.empty_cache()
+    return out
+
+
 # ----------------------------------------------------------------- main
 
 def main():
     a = args_()
+    if a.cpu_leg:
+        cpu_leg(a)
+        return
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local = int(os.environ.get("LOCAL_RANK", 0))
@@ -439,11 +601,8 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    def solve(seed):
-        return api.solve(ctx, dinst, restarts=B, steps=T, seed=seed, **kw)
-
     for w in range(a.warmup):
-        solve(1000 + w)
+        api.solve(ctx, dinst, restarts=B, steps=T, seed=1000 + w, **kw)
     torch.cuda.synchronize()
     pr = api.prune(ctx, inst)
     n_red, rounds = pr.n_reduced, pr.rounds
@@ -452,17 +611,7 @@ def main():
     clocks = Clocks(local)
     clocks.start()
     barrier()
-    total_ms = 0.0
-    last = None
-    for k in range(a.steps):
-        flush.fill_(float(k))  # L2 flush between timed solves (outside the timed region)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        last = solve(k)
-        e1.record(stream)
-        e1.synchronize()
-        total_ms += e0.elapsed_time(e1)
+    total_ms, last = timed_solves(ctx, dinst, B, T, kw, a.steps, flush, stream)
     barrier()
     clk = clocks.stop()
     max_ms = over_ranks(dist, total_ms, "max", "cuda")
@@ -473,83 +622,61 @@ def main():
     value = job_units * a.steps / (max_ms / 1e3)
 
     # end to end: host (pinned) inputs, host outputs, copies inside the timed region
+    e2e_k = max(1, min(a.steps, a.e2e_steps))
     barrier()
     w0 = time.perf_counter()
-    for k in range(a.steps):
-        out = api.solve(ctx, hinst, restarts=B, steps=T, seed=k, **kw)
+    for k in range(e2e_k):
+        api.solve(ctx, hinst, restarts=B, steps=T, seed=k, **kw)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - w0
-    e2e_value = job_units * a.steps / over_ranks(dist, e2e_s, "max", "cuda")
+    e2e_value = job_units * e2e_k / over_ranks(dist, e2e_s, "max", "cuda")
 
-    # dominant kernel: the fused step, timed launch by launch with events
-    prof = api.Session(ctx, dinst, restarts=B, steps=a.profile_steps, seed=7, profile=True, **kw)
-    prof.run(a.profile_steps)
-    st = prof.result()
-    prof.close()
-    avg_ms = st["kernel_ms"] / max(st["kernel_launches"], 1)
     pk = peaks()
+    roof, st = roofline(ctx, inst, dinst, name, B, kw, a.profile_steps, pk,
+                        sessions=5 if last["path"] == 2 else 1)
     path = last["path"]
-    # the profiled session runs the full instance (no pruning): its size counts
-    n_prof = inst.n
-    if path == 2:  # sparse: HBM bound, 24 B of theta/m/v traffic per update + spin bits
-        alg = n_prof * ((B + 127) // 128 * 128) * (24 + 0.25)
-        roof = {"bound": "hbm", "achieved": alg / (avg_ms / 1e3) / 1e9, "peak": pk["hbm_gbs"],
-                "unit": "GB/s"}
-        kname, ksrc = "sparse_step_kernel", "paper_2312_05837_gb300/csrc/ds_sparse.cu"
-    elif path == 1:  # tensor cores: 2 N^2 B flop per step
-        alg = 2.0 * n_prof * n_prof * B
-        fp8 = st["precision"] == 4
-        # E4M3 operands: the measured BF16 rate times the nominal FP8/BF16 ratio (2)
-        peak = pk["bf16_tflops_sustained"] * (2.0 if fp8 else 1.0)
-        roof = {"bound": "tensor", "achieved": alg / (avg_ms / 1e3) / 1e12, "peak": peak,
-                "unit": "TFLOP/s",
-                "peak_note": ("FP8 = 2 x measured BF16 sustained" if fp8
-                              else "measured BF16 sustained")}
-        if st["precision"] == 2 and not inst.integer:
-            # float J as three BF16 planes: the tensor cores execute 3 x the
-            # algorithmic flops counted here
-            roof["operand_planes"] = 3
-        kname = {0: "tc_step_kernel", 1: "tc_resident_kernel", 2: "tc_small_kernel"}[st["resident"]]
-        ksrc = "paper_2312_05837_gb300/csrc/ds_tc.cu"
-    else:  # plain FP32 FMA on the CUDA cores: 2 N^2 B flop per step
-        alg = 2.0 * n_prof * n_prof * B
-        sms = torch.cuda.get_device_properties(local).multi_processor_count
-        fp32_peak = sms * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-        roof = {"bound": "alu", "achieved": alg / (avg_ms / 1e3) / 1e12, "peak": fp32_peak,
-                "unit": "TFLOP/s"}
-        kname, ksrc = "plain_step_kernel", "paper_2312_05837_gb300/csrc/ds_plain.cu"
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = traffic_for(kname, ksrc, a.workload)
-    roof["kernel"] = kname
-    roof["peak_source"] = pk["source"]
-    roof["avg_launch_ms"] = avg_ms
-
+    prec = st["precision"]
+    dtype = {0: "f32", 2: "f32"}.get(path)
+    if path == 1:
+        dtype = {4: "e4m3", 3: "bf16"}.get(prec, "f16x2" if st["operand_planes"] == 2 else "f16/bf16")
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": max_ms / a.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None,
-            "dtype": ({0: "f32", 1: "bf16", 2: "f32"}[path] if st["precision"] != 4 else "e4m3"),
-            "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
             "config": {"workload": f"{name}: N={inst.n} (N_reduced={n_red}), restarts={B}, "
                                    f"steps={T}, lr={a.lr}, mu={a.mu}",
-                       "precision": a.precision, "path": {0: "plain", 1: "tc", 2: "sparse"}[path],
+                       "precision": a.precision,
+                       "operands": ("J as two FP16 planes hi + lo of J / 2^e_i (power-of-two "
+                                    "row scales, about 22 significant bits), spins FP16 +-1, "
+                                    "FP32 accumulate" if dtype == "f16x2" else dtype),
+                       "path": {0: "plain", 1: "tc", 2: "sparse"}[path],
                        "l2": "flushed (512 MB write) before each timed solve",
                        "parallelism": f"replicas x{world}"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": input_bytes(inst),
-                    "d2h_bytes_per_step": int(inst.n) + 8},
-            "gpu_launches": launches_per_solve(T, rounds, path, bool(last["resident"]),
-                                               path == 1 and bool(inst.integer)) * a.steps,
+                    "d2h_bytes_per_step": int(inst.n) + 8, "solves": e2e_k},
+            "gpu_launches": launches_per_solve(
+                T, rounds, path, bool(last["resident"]), path == 1 and bool(inst.integer),
+                path == 1 and not inst.integer and prec in (2, 4)) * a.steps,
             "roofline": roof, "clocks": clk,
             "best_energy": float(last["best_energy"].item())}
     if name.startswith("table2"):
         from paper_2312_05837_gb300.metrics import paper_metrics
         line["paper_metrics"] = paper_metrics(inst, line["best_energy"], max_ms / a.steps / 1e3)
-    if rank == 0 and not a.no_extras and name == "sk4096":
-        line["precision_sweep"] = precision_sweep(ctx, dinst, inst.n, B, T)
+    del dinst
+    torch.cuda.empty_cache()
+    if rank == 0 and a.secondary:
+        line["workloads"] = {w: secondary(ctx, w, a, pk, flush, stream)
+                             for w in a.secondary.split(",") if w and w != name}
     if rank == 0 and not a.no_extras:
-        line["time_to_target"] = time_to_target(ctx, dinst, bool(inst.integer), B, T, seed=3)
+        forms = ["fp32", "tc", "bf16", "fp8"] if not inst.integer else ["fp32", "auto"]
+        dinst = device_instance(inst, torch)
+        line["precision_and_time_to_target"] = precision_runs(
+            ctx, dinst, bool(inst.integer), inst.n, B, T, seed=3, forms=forms,
+            chunk=100 if T >= 4000 else 50)
+        del dinst
+        torch.cuda.empty_cache()
         line["serving"] = serving(ctx)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(a, inst, B, a.cpu_seconds)
+        line["cpu_baseline"] = cpu_baseline(a, B, T)
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
