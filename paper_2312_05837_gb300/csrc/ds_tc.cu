@@ -126,7 +126,9 @@ struct TcLayout {
   static constexpr uint32_t kA = kBM * kRowBytes;
   static constexpr uint32_t kB = BN * kRowBytes;
   static constexpr uint32_t kStage = kKps * (kA + kB);
-  static constexpr int kStages = (200 * 1024) / kStage;
+  // as many stages as the 227 KB of shared memory hold (the ring's depth
+  // covers the latency of the operand copies from L2)
+  static constexpr int kStages = (225 * 1024) / kStage;
   static constexpr uint32_t kBars = kStages * kStage;  // barrier block
   static constexpr uint32_t kBytes = kBars + 256 + 1024;  // + alignment slack
   // two accumulator buffers; allocations are powers of two columns
@@ -226,6 +228,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       // thread issues a TMA copy only every ~250 cycles); each arrives on the
       // stage's full barrier with its own byte count
       const bool jside = warp == 0;
+      // J row tiles and spin tiles are read by many CTAs of a step: keep
+      // them in L2 ahead of the state, which streams through once
+      const uint64_t pol = tc::policy_evict_last();
       uint32_t stage = 0, phase = 0;
       int issued = 0;
       bool ok = true;
@@ -245,9 +250,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             // two whole k-blocks of one plane: one copy per operand
             if (jside) {
               const CUtensorMap* ma = plane0 == 0 ? &tmJ2_0 : (plane0 == 1 ? &tmJ2_1 : &tmJ2_2);
-              tc::tma_load_3d(sa, ma, &full[stage], 0, m0, kb0);
+              tc::tma_load_3d_hint(sa, ma, &full[stage], 0, m0, kb0, pol);
             } else {
-              tc::tma_load_3d(sa + Lay::kKps * Lay::kA, &tmS2, &full[stage], 0, n0, kb0);
+              tc::tma_load_3d_hint(sa + Lay::kKps * Lay::kA, &tmS2, &full[stage], 0, n0, kb0, pol);
             }
           } else {
             for (int u = 0; u < cnt; ++u) {
@@ -255,9 +260,10 @@ __global__ void __launch_bounds__(kThreads, 1)
               const int plane = kt / P.nk, kb = kt - plane * P.nk;
               if (jside) {
                 const CUtensorMap* ma = plane == 0 ? &tmA0 : (plane == 1 ? &tmA1 : &tmA2);
-                tc::tma_load_2d(sa + u * Lay::kA, ma, &full[stage], kb * kBK, m0);
+                tc::tma_load_2d_hint(sa + u * Lay::kA, ma, &full[stage], kb * kBK, m0, pol);
               } else {
-                tc::tma_load_2d(sa + Lay::kKps * Lay::kA + u * Lay::kB, &tmB, &full[stage], kb * kBK, n0);
+                tc::tma_load_2d_hint(sa + Lay::kKps * Lay::kA + u * Lay::kB, &tmB, &full[stage],
+                                     kb * kBK, n0, pol);
               }
             }
           }
@@ -384,9 +390,11 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (ok && MODE != kModeCoupling) {
             sv[j] = FP8 ? (Sin8[idx] == 0x38 ? 1.f : -1.f) : ((Sin[idx] & 0x8000u) ? -1.f : 1.f);
             if (MODE == kModeUpdate || MODE == kModeRelaxed) {
-              th[j] = theta[idx];
-              mm[j] = mvec[idx];
-              vv[j] = vvec[idx];
+              // the state is read and written once per step: streaming
+              // accesses (evict first) leave L2 to the operand tiles
+              th[j] = __ldcs(theta + idx);
+              mm[j] = __ldcs(mvec + idx);
+              vv[j] = __ldcs(vvec + idx);
             }
           }
         }
@@ -432,9 +440,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int64_t b = n0 + c0 + j;
             if (!row_ok || b >= P.B) continue;
             const int64_t idx = b * P.ld + i;
-            theta[idx] = th[j];
-            mvec[idx] = mm[j];
-            vvec[idx] = vv[j];
+            __stcs(theta + idx, th[j]);
+            __stcs(mvec + idx, mm[j]);
+            __stcs(vvec + idx, vv[j]);
             if (FP8) Sout8[idx] = sin_nonneg(th[j]) ? 0x38 : 0xB8;
             else Sout[idx] = pm1_16(sin_nonneg(th[j]), P.f16);
             if (MODE == kModeRelaxed)
