@@ -244,6 +244,32 @@ int ising_energy_noalloc(const ising_instance* inst, const int8_t* spins, int64_
                          double* E_out, void* stream);
 const char* ising_energy_noalloc_error(void);
 
+/* ------------------------------------------------------------------ batching */
+
+/* Several domain-selection sessions of different sizes advanced together:
+ * each step of every member runs as one persistent tensor-core launch over
+ * the concatenated tiles of all members plus one tracking launch over all
+ * their restarts (the restarts, or "sweeps", of Sec. IV-C batched across
+ * instances), replayed from a CUDA graph. Each member keeps its own step
+ * counter on the device and computes exactly what it computes alone (the
+ * same products in the same order): a member's state, bests and result are
+ * identical to running it by itself.
+ * Members: sessions of the tensor-core path in the streaming form (created
+ * with ISING_DS_STREAMING, without ISING_DS_RELAXED), all with the same
+ * operand type (E4M3 or 16-bit), energy mode (integer or FP32 partials) and
+ * restart tile width; sessions may belong to different contexts of the same
+ * device. Otherwise ISING_ENOTSUP / ISING_EINVAL. The pack borrows the
+ * sessions: destroy it before any member. Work is queued on `ctx`'s stream,
+ * ordered after work already queued on the members' streams and before work
+ * queued on them later. */
+typedef struct ising_pack ising_pack;
+int ising_pack_create(ising_ctx* ctx, ising_ds* const* sessions, int32_t count, ising_pack** out);
+/* Advance every member by `steps` steps (each must have that many left);
+ * waits for the work and returns ISING_ETIMEOUT if a bounded device wait
+ * gave up. */
+int ising_pack_run(ising_pack* pack, int64_t steps);
+int ising_pack_destroy(ising_pack* pack);
+
 /* ------------------------------------------------------------------ pruning */
 
 /* Algorithm 1 (Sec. III-A) on `inst`, rounds run until nothing changes:

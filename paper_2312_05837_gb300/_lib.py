@@ -100,6 +100,9 @@ _PROTOS = {
     "ising_selftest_waits": (c_int, [c_void_p, c_int64, c_void_p]),
     "ising_ds_result": (c_int, [c_void_p, c_void_p, POINTER(c_double), POINTER(DSStats), c_int]),
     "ising_ds_destroy": (c_int, [c_void_p]),
+    "ising_pack_create": (c_int, [c_void_p, POINTER(c_void_p), c_int32, POINTER(c_void_p)]),
+    "ising_pack_run": (c_int, [c_void_p, c_int64]),
+    "ising_pack_destroy": (c_int, [c_void_p]),
     "ising_server_create": (c_int, [c_void_p, POINTER(ServerCfg), POINTER(c_void_p)]),
     "ising_server_submit": (c_int, [c_void_p, POINTER(Instance), POINTER(DSParams), c_int,
                                     POINTER(c_uint64)]),

@@ -96,7 +96,8 @@ class Context:
         """Releases the context after every session / pruning result made on
         it (the library requires those to go first)."""
         if self.handle:
-            for child in list(self._children):
+            # packs borrow sessions: close them first
+            for child in sorted(self._children, key=lambda c: not isinstance(c, Pack)):
                 child.close()
             self.lib.ising_destroy(self.handle)
             self.handle = c_void_p()
@@ -248,6 +249,36 @@ class Server:
     def close(self):
         if self.handle:
             self.ctx.lib.ising_server_destroy(self.handle)
+            self.handle = c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Pack:
+    """ising_pack_*: sessions of different sizes advanced together, one
+    packed step launch and one packed tracking launch per step for all of
+    them. The sessions must be tensor-core sessions in the streaming form
+    (streaming=True) of one operand type and tile width; each computes what
+    it would alone. Close the pack before its sessions."""
+
+    def __init__(self, ctx: Context, sessions):
+        self.ctx = ctx
+        self.sessions = list(sessions)
+        arr = (c_void_p * len(self.sessions))(*[s.handle.value for s in self.sessions])
+        self.handle = c_void_p()
+        ctx._children.add(self)
+        ctx.check(ctx.lib.ising_pack_create(ctx.handle, arr, len(self.sessions), byref(self.handle)))
+
+    def run(self, steps: int):
+        self.ctx.check(self.ctx.lib.ising_pack_run(self.handle, int(steps)))
+
+    def close(self):
+        if self.handle:
+            self.ctx.lib.ising_pack_destroy(self.handle)
             self.handle = c_void_p()
 
     def __del__(self):

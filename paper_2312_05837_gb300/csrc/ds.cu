@@ -103,79 +103,118 @@ __device__ __forceinline__ int8_t spin_at(const void* spins, int64_t n, int64_t 
   return (w >> (b & 31)) & 1u ? 1 : -1;
 }
 
-// Best tracking for step t = counters[0] + 1, one warp per restart: E_t(b)
-// from the partials of slot t % 2 (lane l adds rows l, l+32, ... in order,
-// then a fixed xor tree across lanes, so the sum is deterministic), strict <
-// against the best so far, copy of S_t for improved restarts (for bit-packed
-// spins a per-restart flag instead, which track_bits_copy_kernel reads); the
-// last block advances the step counter. With the convergence rule (conv_step
-// non-null) a stopped restart is left alone, and steps t <= T feed the rule.
+// Best tracking of restart b at step t, by one warp: E_t(b) from the
+// partials of slot t % 2 (lane l adds rows l, l+32, ... in order, then a
+// fixed xor tree across lanes, so the sum is deterministic), strict <
+// against the best so far, copy of S_t for an improved restart (for
+// bit-packed spins a per-restart flag instead, which track_bits_copy_kernel
+// reads). With the convergence rule (conv_step non-null) a stopped restart
+// is left alone, and steps t <= T feed the rule.
 template <int KIND>
-__global__ void __launch_bounds__(256) track_kernel(
-    int64_t n, int64_t B, int64_t Bp, int64_t ld, int mtiles, bool int_mode, double cq,
-    double chs, const long long* __restrict__ qpart, const long long* __restrict__ hpart,
-    const float* __restrict__ epart, const void* __restrict__ spins_t,
-    double* __restrict__ best_E, long long* __restrict__ best_t, int8_t* __restrict__ best_s,
-    double* __restrict__ last_E, long long* __restrict__ counters, int64_t bs_ld,
-    uint8_t* __restrict__ improved_out, int64_t T, double* __restrict__ conv_ring,
-    double* __restrict__ conv_init, long long* __restrict__ conv_step,
-    unsigned long long* __restrict__ conv_count) {
-  const long long t = counters[0] + 1;
+__device__ __forceinline__ void track_restart(const TrackArgs& A, long long t, int64_t b, int lane) {
+  const int ps = (int)(t % 2);
+  double E;
+  if (A.int_mode) {
+    const long long* qpart = A.qpart[ps];
+    const long long* hpart = A.hpart[ps];
+    long long q = 0, hs = 0;
+#pragma unroll 4
+    for (int r = lane; r < A.mtiles; r += 32) {
+      q += qpart[(int64_t)r * A.Bp + b];
+      hs += hpart[(int64_t)r * A.Bp + b];
+    }
+    for (int o = 16; o; o >>= 1) {
+      q += __shfl_xor_sync(0xffffffffu, q, o);
+      hs += __shfl_xor_sync(0xffffffffu, hs, o);
+    }
+    E = A.cq * (double)q + A.chs * (double)hs;
+  } else {
+    const float* epart = A.epart[ps];
+    double e = 0.0;
+#pragma unroll 4
+    for (int r = lane; r < A.mtiles; r += 32) e += (double)epart[(int64_t)r * A.Bp + b];
+    for (int o = 16; o; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+    E = e;
+  }
+  // every lane holds the same E (the xor tree is symmetric)
+  const bool active = A.conv_step == nullptr || A.conv_step[b] == 0;
+  const bool improved = active && E < A.best_E[b];
+  __syncwarp();
+  if (lane == 0 && active) {
+    A.last_E[b] = E;
+    if (improved) {
+      A.best_E[b] = E;
+      A.best_t[b] = t;
+    }
+    if (A.conv_step && t <= A.T)
+      conv_update(A.conv_ring, A.conv_init, A.conv_step, A.conv_count, A.B, b, t, E);
+  }
+  if (KIND == kSpinBits) {
+    // bit-packed spins are copied by track_bits_copy_kernel
+    if (lane == 0) A.improved[b] = improved ? 1 : 0;
+  } else if (improved) {
+    copy_spin_row_dense<KIND>(A.best_s + b * A.bs_ld, A.spins[t % 3], A.n, A.ld, b, lane);
+  }
+}
+
+// Best tracking for step t = counters[0] + 1 of one session, one warp per
+// restart; the last block advances the step counter.
+template <int KIND>
+__global__ void __launch_bounds__(256) track_kernel(const TrackArgs A) {
+  const long long t = A.counters[0] + 1;
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t b = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); b < B;
-       b += warps) {
-    double E;
-    if (int_mode) {
-      long long q = 0, hs = 0;
-#pragma unroll 4
-      for (int r = lane; r < mtiles; r += 32) {
-        q += qpart[(int64_t)r * Bp + b];
-        hs += hpart[(int64_t)r * Bp + b];
-      }
-      for (int o = 16; o; o >>= 1) {
-        q += __shfl_xor_sync(0xffffffffu, q, o);
-        hs += __shfl_xor_sync(0xffffffffu, hs, o);
-      }
-      E = cq * (double)q + chs * (double)hs;
-    } else {
-      double e = 0.0;
-#pragma unroll 4
-      for (int r = lane; r < mtiles; r += 32) e += (double)epart[(int64_t)r * Bp + b];
-      for (int o = 16; o; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
-      E = e;
-    }
-    // every lane holds the same E (the xor tree is symmetric)
-    const bool active = conv_step == nullptr || conv_step[b] == 0;
-    const bool improved = active && E < best_E[b];
-    __syncwarp();
-    if (lane == 0 && active) {
-      last_E[b] = E;
-      if (improved) {
-        best_E[b] = E;
-        best_t[b] = t;
-      }
-      if (conv_step && t <= T) conv_update(conv_ring, conv_init, conv_step, conv_count, B, b, t, E);
-    }
-    if (KIND == kSpinBits) {
-      // bit-packed spins are copied by track_bits_copy_kernel
-      if (lane == 0) improved_out[b] = improved ? 1 : 0;
-    } else if (improved) {
-      copy_spin_row_dense<KIND>(best_s + b * bs_ld, spins_t, n, ld, b, lane);
-    }
-  }
+  for (int64_t b = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); b < A.B;
+       b += warps)
+    track_restart<KIND>(A, t, b, lane);
   __shared__ bool last;
   __syncthreads();
   __threadfence();
   if (threadIdx.x == 0) {
-    unsigned long long prev = atomicAdd(reinterpret_cast<unsigned long long*>(&counters[1]), 1ull);
+    unsigned long long prev = atomicAdd(reinterpret_cast<unsigned long long*>(&A.counters[1]), 1ull);
     last = prev == gridDim.x - 1;
   }
   __syncthreads();
   if (last && threadIdx.x == 0) {
-    counters[0] = t;
-    counters[1] = 0;
+    A.counters[0] = t;
+    A.counters[1] = 0;
     __threadfence();
+  }
+}
+
+// Best tracking of every member of a pack, each at its own step t =
+// counters[0] + 1: member e owns the restarts [rstart[e], rstart[e + 1]) of
+// the launch, one warp per restart; the last block advances every member's
+// step counter (`done` counts finished blocks and is reset).
+template <int KIND>
+__global__ void __launch_bounds__(256) track_pack_kernel(const TrackArgs* __restrict__ M,
+                                                         const int64_t* __restrict__ rstart,
+                                                         int count, unsigned long long* done) {
+  const int lane = threadIdx.x & 31;
+  const int64_t total = rstart[count];
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t g = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); g < total;
+       g += warps) {
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (rstart[mid] <= g) lo = mid; else hi = mid - 1;
+    }
+    const TrackArgs& A = M[lo];
+    track_restart<KIND>(A, A.counters[0] + 1, g - rstart[lo], lane);
+  }
+  __shared__ bool last;
+  __syncthreads();
+  __threadfence();
+  if (threadIdx.x == 0) last = atomicAdd(done, 1ull) == gridDim.x - 1;
+  __syncthreads();
+  if (last) {
+    for (int e = threadIdx.x; e < count; e += blockDim.x) M[e].counters[0] += 1;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      *done = 0;
+      __threadfence();
+    }
   }
 }
 
@@ -353,29 +392,50 @@ int check_params(ising_ctx* ctx, const ising_ds_params* p) {
 
 }  // namespace
 
+TrackArgs track_args(const ising_ds* ds) {
+  TrackArgs A;
+  A.n = ds->n;
+  A.B = ds->B;
+  A.Bp = ds->Bp;
+  A.ld = ds->ld;
+  A.mtiles = ds->mtiles;
+  A.int_mode = ds->int_energy;
+  A.cq = ds->inst.cq;
+  A.chs = ds->inst.ch * std::ldexp(1.0, -ds->h_shift);
+  for (int k = 0; k < 2; ++k) {
+    A.qpart[k] = ds->qpart[k].as<long long>();
+    A.hpart[k] = ds->hpart[k].as<long long>();
+    A.epart[k] = ds->epart[k].as<float>();
+  }
+  for (int k = 0; k < 3; ++k) A.spins[k] = ds->spins[k].p;
+  A.best_E = ds->best_E.as<double>();
+  A.best_t = ds->best_t.as<long long>();
+  A.best_s = ds->best_s.as<int8_t>();
+  A.last_E = ds->last_E.as<double>();
+  A.counters = ds->counters.as<long long>();
+  A.bs_ld = ds->bs_ld;
+  A.improved = ds->improved.as<uint8_t>();
+  A.T = ds->T;
+  const bool conv = ds->conv.p != nullptr;
+  A.conv_ring = conv ? ds->conv_ring() : nullptr;
+  A.conv_init = conv ? ds->conv_init() : nullptr;
+  A.conv_step = conv ? ds->conv_step() : nullptr;
+  A.conv_count = conv ? ds->conv_count() : nullptr;
+  return A;
+}
+
 int track_step(ising_ds* ds) {
   ising_ctx* ctx = ds->ctx;
   const int slot = (int)((ds->t + 1) % 3);
-  const int pslot = (int)((ds->t + 1) % 2);
-  const double chs = ds->inst.ch * std::ldexp(1.0, -ds->h_shift);
   int grid = (int)std::min<int64_t>((ds->B + 7) / 8, (int64_t)ctx->sm_count * 4);
-  const bool conv = ds->conv.p != nullptr;
-#define ISING_TRACK(KIND)                                                                    \
-  track_kernel<KIND><<<grid, 256, 0, ctx->stream>>>(                                         \
-      ds->n, ds->B, ds->Bp, ds->ld, ds->mtiles, ds->int_energy, ds->inst.cq, chs,            \
-      ds->qpart[pslot].as<long long>(), ds->hpart[pslot].as<long long>(),                    \
-      ds->epart[pslot].as<float>(), ds->spins[slot].p, ds->best_E.as<double>(),              \
-      ds->best_t.as<long long>(), ds->best_s.as<int8_t>(), ds->last_E.as<double>(),          \
-      ds->counters.as<long long>(), ds->bs_ld, ds->improved.as<uint8_t>(), ds->T,             \
-      conv ? ds->conv_ring() : nullptr, conv ? ds->conv_init() : nullptr,                   \
-      conv ? ds->conv_step() : nullptr, conv ? ds->conv_count() : nullptr)
+  const TrackArgs A = track_args(ds);
   switch (ds->spin_kind) {
-    case kSpinF32: ISING_TRACK(kSpinF32); break;
+    case kSpinF32: track_kernel<kSpinF32><<<grid, 256, 0, ctx->stream>>>(A); break;
     case kSpinBF16:
-    case kSpinF16: ISING_TRACK(kSpinBF16); break;  // both read the sign bit
-    case kSpinE4M3: ISING_TRACK(kSpinE4M3); break;
+    case kSpinF16: track_kernel<kSpinBF16><<<grid, 256, 0, ctx->stream>>>(A); break;  // sign bits
+    case kSpinE4M3: track_kernel<kSpinE4M3><<<grid, 256, 0, ctx->stream>>>(A); break;
     default: {
-      ISING_TRACK(kSpinBits);
+      track_kernel<kSpinBits><<<grid, 256, 0, ctx->stream>>>(A);
       const int64_t words = ds->Bp / 32;
       const int64_t tasks = (ds->n + 31) / 32 * words;
       const int cgrid = (int)std::max<int64_t>(
@@ -386,7 +446,24 @@ int track_step(ising_ds* ds) {
       break;
     }
   }
-#undef ISING_TRACK
+  ISING_CUDA(ctx, cudaGetLastError());
+  return ISING_OK;
+}
+
+int track_pack(ising_ctx* ctx, int spin_kind, const TrackArgs* members, const int64_t* rstart,
+               int count, int64_t total_restarts, unsigned long long* done) {
+  const int grid = (int)std::max<int64_t>(
+      1, std::min<int64_t>((total_restarts + 7) / 8, (int64_t)ctx->sm_count * 4));
+  switch (spin_kind) {
+    case kSpinE4M3:
+      track_pack_kernel<kSpinE4M3><<<grid, 256, 0, ctx->stream>>>(members, rstart, count, done);
+      break;
+    case kSpinBF16:
+    case kSpinF16:
+      track_pack_kernel<kSpinBF16><<<grid, 256, 0, ctx->stream>>>(members, rstart, count, done);
+      break;
+    default: return fail(ctx, ISING_ENOTSUP, "packed tracking: dense spin slots only");
+  }
   ISING_CUDA(ctx, cudaGetLastError());
   return ISING_OK;
 }

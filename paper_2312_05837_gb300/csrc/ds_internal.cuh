@@ -132,6 +132,31 @@ __device__ __forceinline__ void copy_spin_row_dense(int8_t* dst, const void* spi
   }
 }
 
+// What best tracking of one session reads and writes; the partial and spin
+// slots of step t are qpart / hpart / epart[t % 2] and spins[t % 3].
+struct TrackArgs {
+  int64_t n, B, Bp, ld;
+  int mtiles;
+  bool int_mode;
+  double cq, chs;
+  const long long* qpart[2];
+  const long long* hpart[2];
+  const float* epart[2];
+  const void* spins[3];
+  double* best_E;
+  long long* best_t;
+  int8_t* best_s;
+  double* last_E;
+  long long* counters;
+  int64_t bs_ld;
+  uint8_t* improved;
+  int64_t T;
+  double* conv_ring;
+  double* conv_init;
+  long long* conv_step;
+  unsigned long long* conv_count;
+};
+
 // What a step launch does: the full update, only the energies of the input
 // spins (the final evaluation), or only the coupling product G = J s.
 // kModeRelaxed: the update with the coupling product taken on the relaxed
@@ -233,6 +258,21 @@ int ds_advance(ising_ds* ds, int64_t todo);  // queue steps without waiting
 int ds_create_impl(ising_ctx* ctx, const ising_instance* inst, const ising_ds_params* p,
                    ising_ds** out, bool validate);
 int track_step(ising_ds* ds);  // reduce partials of step t+1, best tracking, t += 1
+TrackArgs track_args(const ising_ds* ds);
+// Best tracking of every member of a pack (device arrays: members[count],
+// rstart[count + 1] restart offsets, `done` a zeroed block counter).
+int track_pack(ising_ctx* ctx, int spin_kind, const TrackArgs* members, const int64_t* rstart,
+               int count, int64_t total_restarts, unsigned long long* done);
+// Pack hooks of the tensor-core path (ds_tc.cu): whether the session can be
+// a pack member (streaming form, update-only), its pack key (members of one
+// launch share it), the bytes and contents of its device entry, and one
+// packed step launch.
+bool tc_packable(const ising_ds* ds);
+uint64_t tc_pack_key(const ising_ds* ds);
+size_t tc_pack_entry_bytes();
+int tc_pack_entry(ising_ds* ds, void* host_entry);
+int tc_pack_launch(ising_ctx* ctx, uint64_t key, const void* entries, const int* start, int count,
+                   int tiles, int* err);
 int export_spins_int8(ising_ds* ds, int slot, int8_t* out);  // spins[slot] -> int8 [B][n]
 
 }  // namespace ising

@@ -110,10 +110,6 @@ __device__ __forceinline__ unsigned long long now_ns() {
 // Trace slots per CTA (globaltimer, ns): 0 start, 1 first TMA issued, 2 last
 // TMA issued, 3 first MMA issued, 4 last MMA committed, 5 epilogue has its
 // first accumulator, 6 epilogue done (warp 4), 7 end.
-#define ISING_TRACE(slot)                                                            \
-  do {                                                                               \
-    if (P.trace) P.trace[(size_t)blockIdx.x * 8 + (slot)] = now_ns();                \
-  } while (0)
 
 // Streaming form: for BN <= 128 stages of two k-blocks [J, J, S, S], so that
 // two whole k-blocks of one plane arrive by one copy per operand (a thread
@@ -170,16 +166,121 @@ __device__ __forceinline__ int column_of_lane(int lane) {
   return ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
 }
 
-template <int BN, int MODE, bool INT_E, bool FP8>
-__global__ void __launch_bounds__(kThreads, 1)
-    tc_step_kernel(const __grid_constant__ CUtensorMap tmA0,
-                   const __grid_constant__ CUtensorMap tmA1,
-                   const __grid_constant__ CUtensorMap tmA2,
-                   const __grid_constant__ CUtensorMap tmB,
-                   const __grid_constant__ CUtensorMap tmJ2_0,
-                   const __grid_constant__ CUtensorMap tmJ2_1,
-                   const __grid_constant__ CUtensorMap tmJ2_2,
-                   const __grid_constant__ CUtensorMap tmS2, const TcArgs P) {
+// One tile of a step launch: the instance it belongs to (its arguments, the
+// operand maps, the spin and partial slots of its current step) and where
+// the tile lies (row tile mt, first row m0, first restart n0).
+struct TileRef {
+  const TcArgs* P;
+  const CUtensorMap *A0, *A1, *A2;  // J planes, boxes of one k-block
+  const CUtensorMap *J0, *J1, *J2;  // J planes, boxes of two k-blocks
+  const CUtensorMap* B;      // S_t, boxes of one k-block x BN restarts
+  const CUtensorMap* S2;     // S_t, boxes of two k-blocks
+  const void* S;             // S_t
+  void* Snext;               // S_{t+1}
+  long long* qpart;
+  long long* hpart;
+  float* epart;
+  int mt, m0, n0;
+  __device__ const CUtensorMap* a(int plane) const { return plane == 0 ? A0 : (plane == 1 ? A1 : A2); }
+  __device__ const CUtensorMap* j2(int plane) const { return plane == 0 ? J0 : (plane == 1 ? J1 : J2); }
+};
+
+// Tiles of one instance: everything comes from the kernel's parameters (the
+// host chose the slots of step t), tiles numbered row tile by row tile.
+template <int BN>
+struct OneInstance {
+  static constexpr bool kGlobalMaps = false;  // kernel parameters
+  const TcArgs& P;  // the kernel's parameter
+  const CUtensorMap *A0, *A1, *A2, *B, *J0, *J1, *J2, *S2;
+  __device__ int total() const { return P.mtiles * P.ntiles; }
+  __device__ int* err() const { return P.err; }
+  __device__ unsigned long long* trace() const { return P.trace; }
+  __device__ const TcArgs& args(const TileRef&) const { return P; }
+  __device__ TileRef tile(int tl) const {
+    TileRef r;
+    r.P = &P;
+    r.A0 = A0; r.A1 = A1; r.A2 = A2;
+    r.J0 = J0; r.J1 = J1; r.J2 = J2;
+    r.B = B;
+    r.S2 = S2;
+    r.S = P.S;
+    r.Snext = P.Snext;
+    r.qpart = P.qpart;
+    r.hpart = P.hpart;
+    r.epart = P.epart;
+    r.mt = tl / P.ntiles;
+    r.m0 = r.mt * kBM;
+    r.n0 = (tl % P.ntiles) * BN;
+    return r;
+  }
+};
+
+// One member of a packed launch (several instances advanced by one step in
+// one launch): its arguments and maps in device memory, with all three spin
+// slots and both partial slots; the slots of its step come from its own
+// device step counter, so every launch of a pack is identical whatever the
+// members' progress (the step loop can be replayed from a CUDA graph).
+struct __align__(64) PackEntry {
+  CUtensorMap A[3];
+  CUtensorMap J2[3];
+  CUtensorMap B[3];   // per spin slot
+  CUtensorMap S2[3];  // per spin slot
+  TcArgs args;
+  void* spins[3];
+  long long* qpart[2];
+  long long* hpart[2];
+  float* epart[2];
+};
+
+// Tiles of a pack: member e owns tiles [start[e], start[e + 1]).
+template <int BN>
+struct PackedInstances {
+  static constexpr bool kGlobalMaps = true;  // copied to device memory by the host
+  const PackEntry* E;
+  const int* start;
+  int count;
+  int* errp;
+  __device__ int total() const { return start[count]; }
+  __device__ int* err() const { return errp; }
+  __device__ unsigned long long* trace() const { return nullptr; }
+  __device__ const TcArgs& args(const TileRef& T) const { return *T.P; }
+  __device__ TileRef tile(int tl) const {
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {  // last member whose first tile is <= tl
+      const int mid = (lo + hi + 1) >> 1;
+      if (start[mid] <= tl) lo = mid; else hi = mid - 1;
+    }
+    const PackEntry& e = E[lo];
+    const long long t = e.args.counters[0] + 1;
+    const int s0 = (int)(t % 3), s1 = (int)((t + 1) % 3), ps = (int)(t % 2);
+    TileRef r;
+    r.P = &e.args;
+    r.A0 = &e.A[0]; r.A1 = &e.A[1]; r.A2 = &e.A[2];
+    r.J0 = &e.J2[0]; r.J1 = &e.J2[1]; r.J2 = &e.J2[2];
+    r.B = &e.B[s0];
+    r.S2 = &e.S2[s0];
+    r.S = e.spins[s0];
+    r.Snext = e.spins[s1];
+    r.qpart = e.qpart[ps];
+    r.hpart = e.hpart[ps];
+    r.epart = e.epart[ps];
+    const int local = tl - start[lo];
+    r.mt = local / e.args.ntiles;
+    r.m0 = r.mt * kBM;
+    r.n0 = (local % e.args.ntiles) * BN;
+    return r;
+  }
+};
+
+#define ISING_TRACE(slot)                                                            \
+  do {                                                                               \
+    if (trace_) trace_[(size_t)blockIdx.x * 8 + (slot)] = now_ns();                  \
+  } while (0)
+
+// The persistent, warp-specialised step over the tiles of `src` (one
+// instance, or the members of a pack). Roles as described at the top.
+template <int BN, int MODE, bool INT_E, bool FP8, class Src>
+__device__ __forceinline__ void step_tiles(const Src& src) {
   using Lay = TcLayout<BN>;
   constexpr int STAGES = Lay::kStages;
   constexpr int kBK = FP8 ? 128 : 64;  // elements per 128-byte row
@@ -193,6 +294,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* drain = acc_empty + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  unsigned long long* const trace_ = src.trace();
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -212,14 +314,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc::tmem_alloc(tmem_slot, Lay::kTmemCols);
     tc::fence_before_sync();
   }
-  if (warp == 0 && lane == 0) tc::prefetch_map(&tmA0);
-  if (warp == 2 && lane == 0) tc::prefetch_map(&tmB);
   __syncthreads();
   tc::fence_after_sync();
   if (threadIdx.x == 0) ISING_TRACE(0);
   const uint32_t tmem_base = *tmem_slot;
-  const int total = P.mtiles * P.ntiles;
-  const int nkt = P.nk * P.planes;
+  const int total = src.total();
 
   if (warp == 0 || warp == 2) {
     if (lane == 0) {
@@ -235,8 +334,22 @@ __global__ void __launch_bounds__(kThreads, 1)
       int issued = 0;
       bool ok = true;
       for (int tl = blockIdx.x; tl < total && ok; tl += gridDim.x) {
-        const int m0 = (tl / P.ntiles) * kBM;
-        const int n0 = (tl % P.ntiles) * BN;
+        const TileRef T = src.tile(tl);
+        const TcArgs& P = src.args(T);
+        const int nk = P.nk, nfull = P.nfull, planes = P.planes;
+        const int nkt = nk * planes;
+        if (Src::kGlobalMaps) {
+          if (jside) {
+            for (int p = 0; p < planes; ++p) {
+              tc::fence_map_acquire(T.a(p));
+              tc::fence_map_acquire(T.j2(p));
+            }
+          } else {
+            tc::fence_map_acquire(T.B);
+            tc::fence_map_acquire(T.S2);
+          }
+        }
+        if (tl == (int)blockIdx.x) tc::prefetch_map(jside ? T.A0 : T.B);
         for (int kt0 = 0; kt0 < nkt; kt0 += Lay::kKps) {
           if (!tc::mbar_wait(&empty[stage], phase ^ 1, abort_flag, kWaitCycles)) {
             ok = false;
@@ -245,26 +358,21 @@ __global__ void __launch_bounds__(kThreads, 1)
           uint8_t* sa = smem + stage * Lay::kStage;
           const int cnt = nkt - kt0 < Lay::kKps ? nkt - kt0 : Lay::kKps;
           tc::mbar_expect_tx(&full[stage], (uint32_t)cnt * (jside ? Lay::kA : Lay::kB));
-          const int plane0 = kt0 / P.nk, kb0 = kt0 - plane0 * P.nk;
-          if (Lay::kKps == 2 && kb0 + 1 < P.nfull) {
+          const int plane0 = kt0 / nk, kb0 = kt0 - plane0 * nk;
+          if (Lay::kKps == 2 && kb0 + 1 < nfull) {
             // two whole k-blocks of one plane: one copy per operand
-            if (jside) {
-              const CUtensorMap* ma = plane0 == 0 ? &tmJ2_0 : (plane0 == 1 ? &tmJ2_1 : &tmJ2_2);
-              tc::tma_load_3d_hint(sa, ma, &full[stage], 0, m0, kb0, pol);
-            } else {
-              tc::tma_load_3d_hint(sa + Lay::kKps * Lay::kA, &tmS2, &full[stage], 0, n0, kb0, pol);
-            }
+            if (jside) tc::tma_load_3d_hint(sa, T.j2(plane0), &full[stage], 0, T.m0, kb0, pol);
+            else
+              tc::tma_load_3d_hint(sa + Lay::kKps * Lay::kA, T.S2, &full[stage], 0, T.n0, kb0, pol);
           } else {
             for (int u = 0; u < cnt; ++u) {
               const int kt = kt0 + u;
-              const int plane = kt / P.nk, kb = kt - plane * P.nk;
-              if (jside) {
-                const CUtensorMap* ma = plane == 0 ? &tmA0 : (plane == 1 ? &tmA1 : &tmA2);
-                tc::tma_load_2d_hint(sa + u * Lay::kA, ma, &full[stage], kb * kBK, m0, pol);
-              } else {
-                tc::tma_load_2d_hint(sa + Lay::kKps * Lay::kA + u * Lay::kB, &tmB, &full[stage],
-                                     kb * kBK, n0, pol);
-              }
+              const int plane = kt / nk, kb = kt - plane * nk;
+              if (jside)
+                tc::tma_load_2d_hint(sa + u * Lay::kA, T.a(plane), &full[stage], kb * kBK, T.m0, pol);
+              else
+                tc::tma_load_2d_hint(sa + Lay::kKps * Lay::kA + u * Lay::kB, T.B, &full[stage],
+                                     kb * kBK, T.n0, pol);
             }
           }
           if (issued == 0 && jside) ISING_TRACE(1);
@@ -282,17 +390,20 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (s == 0) { s = STAGES - 1; ph ^= 1; } else { --s; }
           tc::mbar_wait(&full[s], ph, nullptr, kWaitCycles / 8);
         }
-        atomicExch(P.err, 1);
+        atomicExch(src.err(), 1);
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
       // ------------------------------------------------ MMA issuer
-      const uint32_t idesc = op_idesc(BN, FP8, P.f16);
       uint32_t stage = 0, phase = 0;
       int it = 0;
       bool ok = true;
       for (int tl = blockIdx.x; tl < total && ok; tl += gridDim.x, ++it) {
+        const TileRef T = src.tile(tl);
+        const TcArgs& P = src.args(T);
+        const int nkt = P.nk * P.planes;
+        const uint32_t idesc = op_idesc(BN, FP8, P.f16);
         const int buf = it & 1;
         const uint32_t use = (uint32_t)(it >> 1);
         if (!tc::mbar_wait(&acc_empty[buf], (use & 1) ^ 1, abort_flag, kWaitCycles)) {
@@ -335,7 +446,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!ok) {
         tc::mma_commit(drain);
         tc::mbar_wait(drain, 0, nullptr, kWaitCycles / 8);
-        atomicExch(P.err, 2);
+        atomicExch(src.err(), 2);
       }
     }
   } else if (warp >= 4) {
@@ -343,24 +454,26 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int q = warp & 3;             // TMEM lane quarter of this warp
     const int part = (warp - 4) >> 2;   // which quarter of the tile's columns
     constexpr int kCols = BN / 4;
-    const long long t = P.counters[0] + 1;
-    const float2 bc = P.bias[t];
-    float* __restrict__ theta = P.theta;
-    float* __restrict__ mvec = P.m;
-    float* __restrict__ vvec = P.v;
-    const uint16_t* __restrict__ Sin = static_cast<const uint16_t*>(P.S);
-    uint16_t* __restrict__ Sout = static_cast<uint16_t*>(P.Snext);
-    const uint8_t* __restrict__ Sin8 = static_cast<const uint8_t*>(P.S);
-    uint8_t* __restrict__ Sout8 = static_cast<uint8_t*>(P.Snext);
     int it = 0;
     for (int tl = blockIdx.x; tl < total; tl += gridDim.x, ++it) {
+      const TileRef T = src.tile(tl);
+      const TcArgs& P = src.args(T);
+      const long long t = P.counters[0] + 1;
+      const float2 bc = P.bias[t];
+      float* __restrict__ theta = P.theta;
+      float* __restrict__ mvec = P.m;
+      float* __restrict__ vvec = P.v;
+      const uint16_t* __restrict__ Sin = static_cast<const uint16_t*>(T.S);
+      uint16_t* __restrict__ Sout = static_cast<uint16_t*>(T.Snext);
+      const uint8_t* __restrict__ Sin8 = static_cast<const uint8_t*>(T.S);
+      uint8_t* __restrict__ Sout8 = static_cast<uint8_t*>(T.Snext);
       const int buf = it & 1;
       const uint32_t use = (uint32_t)(it >> 1);
-      const int mt = tl / P.ntiles;
-      const int64_t m0 = (int64_t)mt * kBM;
-      const int64_t n0 = (int64_t)(tl % P.ntiles) * BN + part * kCols;
+      const int mt = T.mt;
+      const int64_t m0 = T.m0;
+      const int64_t n0 = (int64_t)T.n0 + part * kCols;
       if (!tc::mbar_wait(&acc_full[buf], use & 1, abort_flag, kWaitCycles)) {
-        atomicExch(P.err, 3);
+        atomicExch(src.err(), 3);
         break;
       }
       tc::fence_after_sync();
@@ -457,12 +570,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int tq = column_sums8(eq, lane);
             const int th2 = P.has_h ? column_sums8(eh, lane) : 0;
             if ((lane & 3) == 0 && b < P.B) {
-              P.qpart[o] = tq;
-              P.hpart[o] = th2;
+              T.qpart[o] = tq;
+              T.hpart[o] = th2;
             }
           } else {
             const float te = column_sums8(ef, lane);
-            if ((lane & 3) == 0 && b < P.B) P.epart[o] = te;
+            if ((lane & 3) == 0 && b < P.B) T.epart[o] = te;
           }
         }
       }
@@ -476,6 +589,30 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc::fence_after_sync();
     tc::tmem_dealloc(tmem_base, Lay::kTmemCols);
   }
+}
+#undef ISING_TRACE
+
+template <int BN, int MODE, bool INT_E, bool FP8>
+__global__ void __launch_bounds__(kThreads, 1)
+    tc_step_kernel(const __grid_constant__ CUtensorMap tmA0,
+                   const __grid_constant__ CUtensorMap tmA1,
+                   const __grid_constant__ CUtensorMap tmA2,
+                   const __grid_constant__ CUtensorMap tmB,
+                   const __grid_constant__ CUtensorMap tmJ2_0,
+                   const __grid_constant__ CUtensorMap tmJ2_1,
+                   const __grid_constant__ CUtensorMap tmJ2_2,
+                   const __grid_constant__ CUtensorMap tmS2, const __grid_constant__ TcArgs P) {
+  const OneInstance<BN> src{P, &tmA0, &tmA1, &tmA2, &tmB, &tmJ2_0, &tmJ2_1, &tmJ2_2, &tmS2};
+  step_tiles<BN, MODE, INT_E, FP8>(src);
+}
+
+// One step of every member of a pack (the update mode only).
+template <int BN, bool INT_E, bool FP8>
+__global__ void __launch_bounds__(kThreads, 1)
+    tc_pack_kernel(const PackEntry* __restrict__ entries, const int* __restrict__ start, int count,
+                   int* err) {
+  const PackedInstances<BN> src{entries, start, count, err};
+  step_tiles<BN, kModeUpdate, INT_E, FP8>(src);
 }
 
 // 16-bit operand planes of J, [n][ld] each (columns past n are 0):
@@ -2180,6 +2317,104 @@ int tc_trace(ising_ds* ds, uint64_t* out, int64_t cap, int64_t* count) {
   ISING_CUDA(ds->ctx, cudaStreamSynchronize(ds->ctx->stream));
   *count = (int64_t)st->grid * 8;
   return ISING_OK;
+}
+
+bool tc_packable(const ising_ds* ds) {
+  auto st = static_cast<const TcState*>(ds->tc);
+  return ds->path == ISING_PATH_TC && st && !st->resident && !ds->relaxed();
+}
+
+uint64_t tc_pack_key(const ising_ds* ds) {
+  auto st = static_cast<const TcState*>(ds->tc);
+  return (st->fp8 ? 1u : 0u) | (ds->int_energy ? 2u : 0u) | ((uint64_t)st->BN << 2);
+}
+
+size_t tc_pack_entry_bytes() { return sizeof(PackEntry); }
+
+// The session's pack entry (host copy): its maps, all spin and partial
+// slots, and the arguments tc_run would pass (slot fields unused).
+int tc_pack_entry(ising_ds* ds, void* host_entry) {
+  auto st = static_cast<TcState*>(ds->tc);
+  if (!st->maps_ready) {
+    ISING_TRY(tc_maps(ds, st));
+    st->maps_ready = true;
+  }
+  PackEntry* e = static_cast<PackEntry*>(host_entry);
+  memset(e, 0, sizeof(PackEntry));
+  for (int p = 0; p < 3; ++p) {
+    e->A[p] = st->A[p];
+    e->J2[p] = st->nfull >= 2 ? st->J2[p] : st->A[p];
+    e->B[p] = st->B[p];
+    e->S2[p] = st->nfull >= 2 ? st->SP[p] : st->B[p];
+    e->spins[p] = ds->spins[p].p;
+  }
+  for (int k = 0; k < 2; ++k) {
+    e->qpart[k] = ds->qpart[k].as<long long>();
+    e->hpart[k] = ds->hpart[k].as<long long>();
+    e->epart[k] = ds->epart[k].as<float>();
+  }
+  TcArgs& a = e->args;
+  a.n = ds->n;
+  a.B = ds->B;
+  a.ld = ds->ld;
+  a.nk = ceil_div_i(ds->n, st->fp8 ? 128 : 64);
+  a.planes = ds->planes;
+  a.f16 = st->f16 ? 1 : 0;
+  a.mtiles = ceil_div_i(ds->n, kBM);
+  a.ntiles = ceil_div_i(ds->B, st->BN);
+  a.k = ds->k;
+  a.bias = ds->bias.as<float2>();
+  a.counters = ds->counters.as<long long>();
+  a.rowscale = ds->rowscale.p ? ds->rowscale.as<float>() : nullptr;
+  a.theta = ds->theta.as<float>();
+  a.m = ds->m.as<float>();
+  a.v = ds->v.as<float>();
+  a.hf = ds->hf.as<float>();
+  a.hint = ds->hint.as<int32_t>();
+  a.err = st->err.as<int>();
+  a.has_h = ds->inst.has_h ? 1 : 0;
+  a.gmagic = st->emode;
+  a.nfull = st->nfull;
+  return ISING_OK;
+}
+
+namespace {
+template <int BN, bool INT_E, bool FP8>
+int pack_launch_t(ising_ctx* ctx, const void* entries, const int* start, int count, int tiles,
+                  int* err) {
+  auto kern = tc_pack_kernel<BN, INT_E, FP8>;
+  const size_t smem = TcLayout<BN>::kBytes;
+  static bool attr_set = false;  // per instantiation
+  if (!attr_set) {
+    ISING_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr_set = true;
+  }
+  const int grid = std::max(1, std::min(tiles, ctx->sm_count));
+  kern<<<grid, kThreads, smem, ctx->stream>>>(static_cast<const PackEntry*>(entries), start, count, err);
+  ISING_CUDA(ctx, cudaGetLastError());
+  return ISING_OK;
+}
+
+template <int BN>
+int pack_launch_bn(ising_ctx* ctx, bool ie, bool fp8, const void* entries, const int* start,
+                   int count, int tiles, int* err) {
+  if (ie) return fp8 ? pack_launch_t<BN, true, true>(ctx, entries, start, count, tiles, err)
+                     : pack_launch_t<BN, true, false>(ctx, entries, start, count, tiles, err);
+  return fp8 ? pack_launch_t<BN, false, true>(ctx, entries, start, count, tiles, err)
+             : pack_launch_t<BN, false, false>(ctx, entries, start, count, tiles, err);
+}
+}  // namespace
+
+int tc_pack_launch(ising_ctx* ctx, uint64_t key, const void* entries, const int* start, int count,
+                   int tiles, int* err) {
+  const bool fp8 = key & 1u, ie = (key & 2u) != 0;
+  switch ((int)(key >> 2)) {
+    case 256: return pack_launch_bn<256>(ctx, ie, fp8, entries, start, count, tiles, err);
+    case 224: return pack_launch_bn<224>(ctx, ie, fp8, entries, start, count, tiles, err);
+    case 128: return pack_launch_bn<128>(ctx, ie, fp8, entries, start, count, tiles, err);
+    case 64: return pack_launch_bn<64>(ctx, ie, fp8, entries, start, count, tiles, err);
+    default: return fail(ctx, ISING_EINVAL, "pack: unknown tile width");
+  }
 }
 
 void tc_release(ising_ds* ds) {

@@ -1,0 +1,229 @@
+// Batching: several domain-selection sessions (Sec. III-B), of different
+// sizes and restart counts, advanced together. One step of every member is
+// one persistent tensor-core launch over the concatenation of the members'
+// tiles plus one tracking launch over all their restarts; each member keeps
+// its own device step counter, from which the launches pick its spin and
+// partial slots, so the two launches are the same for every step whatever
+// the members' progress and the step loop is replayed from a CUDA graph.
+// A small instance that would leave most SMs idle alone shares the SMs with
+// the other members instead (the restarts of Sec. IV-C, across instances).
+#include "ds_internal.cuh"
+
+#include <algorithm>
+#include <vector>
+
+using namespace ising;
+
+struct ising_pack {
+  ising_ctx* ctx = nullptr;
+  std::vector<ising_ds*> members;
+  uint64_t key = 0;
+  int spin_kind = 0;
+  int tiles = 0;
+  int64_t restarts = 0;
+  DevMem entries;   // PackEntry[count]
+  DevMem start;     // int[count + 1] tile offsets
+  DevMem targs;     // TrackArgs[count]
+  DevMem rstart;    // int64[count + 1] restart offsets
+  DevMem words;     // [0] track block counter, [1] error word
+  cudaGraphExec_t graph = nullptr;
+  cudaStream_t gstream = nullptr;
+  cudaEvent_t ev = nullptr;
+  bool launched = false;  // the kernels have run once outside capture
+};
+
+namespace {
+
+constexpr int64_t kPackGraphSteps = 25;
+
+int pack_step(ising_pack* pk) {
+  ising_ctx* ctx = pk->ctx;
+  int* err = reinterpret_cast<int*>(pk->words.as<unsigned long long>() + 1);
+  ISING_TRY(tc_pack_launch(ctx, pk->key, pk->entries.p, pk->start.as<int>(),
+                           (int)pk->members.size(), pk->tiles, err));
+  return track_pack(ctx, pk->spin_kind, pk->targs.as<TrackArgs>(), pk->rstart.as<int64_t>(),
+                    (int)pk->members.size(), pk->restarts, pk->words.as<unsigned long long>());
+}
+
+// Captures kPackGraphSteps steps on a private stream.
+int pack_graph(ising_pack* pk) {
+  ising_ctx* ctx = pk->ctx;
+  ISING_CUDA(ctx, cudaStreamCreateWithFlags(&pk->gstream, cudaStreamNonBlocking));
+  cudaStream_t saved = ctx->stream;
+  ctx->stream = pk->gstream;
+  cudaGraph_t g = nullptr;
+  int rc = ISING_OK;
+  cudaError_t e = cudaStreamBeginCapture(pk->gstream, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    for (int64_t s = 0; s < kPackGraphSteps && rc == ISING_OK; ++s) rc = pack_step(pk);
+    e = cudaStreamEndCapture(pk->gstream, &g);
+  }
+  ctx->stream = saved;
+  if (rc != ISING_OK) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) return fail(ctx, ISING_ECUDA, "pack graph capture failed: %s", cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&pk->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    pk->graph = nullptr;
+    return fail(ctx, ISING_ECUDA, "pack graph instantiation failed: %s", cudaGetErrorString(e));
+  }
+  return ISING_OK;
+}
+
+// Orders the pack's stream after the work already queued on every member's
+// own stream (set-up, earlier steps).
+int wait_for_members(ising_pack* pk) {
+  for (ising_ds* ds : pk->members) {
+    if (ds->ctx->stream == pk->ctx->stream) continue;
+    ISING_CUDA(pk->ctx, cudaEventRecord(pk->ev, ds->ctx->stream));
+    ISING_CUDA(pk->ctx, cudaStreamWaitEvent(pk->ctx->stream, pk->ev, 0));
+  }
+  return ISING_OK;
+}
+
+// Orders every member's stream after the pack's work so far.
+int members_wait(ising_pack* pk) {
+  ISING_CUDA(pk->ctx, cudaEventRecord(pk->ev, pk->ctx->stream));
+  for (ising_ds* ds : pk->members)
+    if (ds->ctx->stream != pk->ctx->stream)
+      ISING_CUDA(pk->ctx, cudaStreamWaitEvent(ds->ctx->stream, pk->ev, 0));
+  return ISING_OK;
+}
+
+}  // namespace
+
+namespace ising {
+
+// Queues `steps` steps of every member on the pack's stream (no wait).
+int pack_advance(ising_pack* pk, int64_t steps) {
+  ising_ctx* ctx = pk->ctx;
+  for (ising_ds* ds : pk->members)
+    if (ds->finished || steps > ds->T - ds->t)
+      return fail(ctx, ISING_EINVAL, "pack: a member has fewer than %lld steps left",
+                  (long long)steps);
+  ISING_TRY(wait_for_members(pk));
+  int64_t s = 0;
+  // the first steps run outside capture (the kernels' attributes are set
+  // on their first launch), then graph replays, then single steps
+  while (s < steps) {
+    if (pk->launched && steps - s >= kPackGraphSteps) {
+      if (!pk->graph) ISING_TRY(pack_graph(pk));
+      ISING_CUDA(ctx, cudaEventRecord(pk->ev, ctx->stream));
+      ISING_CUDA(ctx, cudaStreamWaitEvent(pk->gstream, pk->ev, 0));
+      ISING_CUDA(ctx, cudaGraphLaunch(pk->graph, pk->gstream));
+      ISING_CUDA(ctx, cudaEventRecord(pk->ev, pk->gstream));
+      ISING_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, pk->ev, 0));
+      s += kPackGraphSteps;
+    } else {
+      ISING_TRY(pack_step(pk));
+      s += 1;
+      pk->launched = true;
+    }
+  }
+  for (ising_ds* ds : pk->members) ds->t += steps;
+  return members_wait(pk);
+}
+
+// Whether a bounded wait of a packed launch gave up (synchronises).
+int pack_error(ising_pack* pk) {
+  int e = 0;
+  ISING_CUDA(pk->ctx, cudaMemcpyAsync(&e, pk->words.as<unsigned long long>() + 1, 4,
+                                      cudaMemcpyDeviceToHost, pk->ctx->stream));
+  ISING_CUDA(pk->ctx, cudaStreamSynchronize(pk->ctx->stream));
+  if (e) return fail(pk->ctx, ISING_ETIMEOUT, "packed step: a bounded wait gave up (role %d)", e);
+  return ISING_OK;
+}
+
+}  // namespace ising
+
+extern "C" int ising_pack_create(ising_ctx* ctx, ising_ds* const* sessions, int32_t count,
+                                 ising_pack** out) {
+  if (!ctx) return ISING_EINVAL;
+  if (!out || !sessions || count < 1 || count > 4096)
+    return fail(ctx, ISING_EINVAL, "pack: 1 to 4096 sessions are required");
+  *out = nullptr;
+  uint64_t key = 0;
+  for (int k = 0; k < count; ++k) {
+    ising_ds* ds = sessions[k];
+    if (!ds || !tc_packable(ds))
+      return fail(ctx, ISING_ENOTSUP,
+                  "pack: member %d is not a tensor-core session in the streaming form "
+                  "(create it with ISING_DS_STREAMING, rounded product)", k);
+    if (ds->ctx->device != ctx->device) return fail(ctx, ISING_EINVAL, "pack: members on another device");
+    for (int j = 0; j < k; ++j)
+      if (sessions[j] == ds) return fail(ctx, ISING_EINVAL, "pack: session %d appears twice", k);
+    const uint64_t kk = tc_pack_key(ds);
+    if (k == 0) key = kk;
+    else if (kk != key)
+      return fail(ctx, ISING_EINVAL,
+                  "pack: members differ in operand type, energy mode or tile width (member %d)", k);
+  }
+  auto pk = new ising_pack();
+  pk->ctx = ctx;
+  pk->members.assign(sessions, sessions + count);
+  pk->key = key;
+  pk->spin_kind = sessions[0]->spin_kind;
+  int rc = [&]() -> int {
+    ISING_CUDA(ctx, cudaEventCreateWithFlags(&pk->ev, cudaEventDisableTiming));
+    const size_t eb = tc_pack_entry_bytes();
+    std::vector<unsigned char> ent(eb * count);
+    std::vector<int> start(count + 1, 0);
+    std::vector<TrackArgs> targs(count);
+    std::vector<int64_t> rstart(count + 1, 0);
+    for (int k = 0; k < count; ++k) {
+      ising_ds* ds = sessions[k];
+      ISING_TRY(tc_pack_entry(ds, ent.data() + eb * k));
+      const int64_t bn = (int64_t)(key >> 2);
+      start[k + 1] = start[k] + ceil_div_i(ds->n, 128) * ceil_div_i(ds->B, bn);
+      targs[k] = track_args(ds);
+      rstart[k + 1] = rstart[k] + ds->B;
+    }
+    pk->tiles = start[count];
+    pk->restarts = rstart[count];
+    ISING_TRY(dev_alloc(ctx, pk->entries, ent.size()));
+    ISING_TRY(dev_alloc(ctx, pk->start, start.size() * sizeof(int)));
+    ISING_TRY(dev_alloc(ctx, pk->targs, targs.size() * sizeof(TrackArgs)));
+    ISING_TRY(dev_alloc(ctx, pk->rstart, rstart.size() * sizeof(int64_t)));
+    ISING_TRY(dev_alloc(ctx, pk->words, 16));
+    ISING_CUDA(ctx, cudaMemcpyAsync(pk->entries.p, ent.data(), ent.size(), cudaMemcpyHostToDevice, ctx->stream));
+    ISING_CUDA(ctx, cudaMemcpyAsync(pk->start.p, start.data(), start.size() * sizeof(int),
+                                    cudaMemcpyHostToDevice, ctx->stream));
+    ISING_CUDA(ctx, cudaMemcpyAsync(pk->targs.p, targs.data(), targs.size() * sizeof(TrackArgs),
+                                    cudaMemcpyHostToDevice, ctx->stream));
+    ISING_CUDA(ctx, cudaMemcpyAsync(pk->rstart.p, rstart.data(), rstart.size() * sizeof(int64_t),
+                                    cudaMemcpyHostToDevice, ctx->stream));
+    ISING_CUDA(ctx, cudaMemsetAsync(pk->words.p, 0, 16, ctx->stream));
+    // (the host vectors go away on return: the copies must have happened)
+    ISING_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return ISING_OK;
+  }();
+  if (rc != ISING_OK) {
+    ising_pack_destroy(pk);
+    return rc;
+  }
+  *out = pk;
+  return ISING_OK;
+}
+
+extern "C" int ising_pack_run(ising_pack* pk, int64_t steps) {
+  if (!pk) return ISING_EINVAL;
+  if (steps < 0) return fail(pk->ctx, ISING_EINVAL, "steps must be >= 0");
+  if (steps == 0) return ISING_OK;
+  NvtxRange range("ising_pack_run");
+  ISING_TRY(pack_advance(pk, steps));
+  return pack_error(pk);
+}
+
+extern "C" int ising_pack_destroy(ising_pack* pk) {
+  if (!pk) return ISING_OK;
+  if (pk->ctx) cudaStreamSynchronize(pk->ctx->stream);
+  if (pk->gstream) cudaStreamSynchronize(pk->gstream);
+  if (pk->graph) cudaGraphExecDestroy(pk->graph);
+  if (pk->gstream) cudaStreamDestroy(pk->gstream);
+  if (pk->ev) cudaEventDestroy(pk->ev);
+  delete pk;
+  return ISING_OK;
+}
