@@ -135,9 +135,11 @@ typedef struct ising_ds_params {
  * (one cooperative launch). */
 #define ISING_DS_STREAMING 2
 /* params.flags: skip the launch-shape autotuner and use the default shape.
- * The autotuner (sparse path) times the first steps of a run once per
- * problem shape with each candidate shape and keeps the fastest; results do
- * not depend on the shape. Choices are cached per process and, when the
+ * The autotuner times the first steps of a run once per problem shape with
+ * each candidate shape and keeps the fastest: on the sparse path one or two
+ * slices of 128 restarts per warp, on the tensor cores' streaming form the
+ * restart-tile width (64, 128, 224 or 256 restarts per tile); results do not
+ * depend on the shape. Choices are cached per process and, when the
  * environment variable ISING_TUNE_CACHE names a file, across processes. */
 #define ISING_DS_NO_AUTOTUNE 4
 /* params.flags: the convergence rule of Sec. IV-B, read on the energy of the
@@ -256,9 +258,10 @@ const char* ising_energy_noalloc_error(void);
  * identical to running it by itself.
  * Members: sessions of the tensor-core path in the streaming form (created
  * with ISING_DS_STREAMING, without ISING_DS_RELAXED), all with the same
- * operand type (E4M3 or 16-bit), energy mode (integer or FP32 partials) and
- * restart tile width; sessions may belong to different contexts of the same
- * device. Otherwise ISING_ENOTSUP / ISING_EINVAL. The pack borrows the
+ * operand type (E4M3 or 16-bit) and energy mode (integer or FP32 partials);
+ * every member is switched to the first member's restart-tile width (the
+ * results do not depend on it). Sessions may belong to different contexts
+ * of the same device. Otherwise ISING_ENOTSUP / ISING_EINVAL. The pack borrows the
  * sessions: destroy it before any member. Work is queued on `ctx`'s stream,
  * ordered after work already queued on the members' streams and before work
  * queued on them later. */
@@ -390,9 +393,15 @@ typedef struct ising_server_cfg {
   uint64_t budget_bytes; /* device memory the admitted requests may use */
   int32_t max_active;    /* requests on the GPU at once (streams), >= 1 */
   int32_t chunk_steps;   /* steps per request per scheduling round, >= 1 */
-  int32_t flags;         /* reserved, 0 */
+  int32_t flags;         /* 0 or ISING_SERVER_PACK */
   int32_t reserved;
 } ising_server_cfg;
+
+/* cfg.flags: the dense tensor-core requests ready in a scheduling round are
+ * grouped by kind (operand type, energy mode, restart tile width) and each
+ * group advances its chunk as one pack (see ising_pack_create) on the
+ * server's own stream; results are those of the requests alone. */
+#define ISING_SERVER_PACK 1
 
 typedef struct ising_result {
   int32_t status;        /* ISING_OK, or the error the request failed with */

@@ -21,6 +21,7 @@ MEM_HOST, MEM_DEVICE = 0, 1
 PREC_AUTO, PREC_FP32_PLAIN, PREC_TC, PREC_BF16, PREC_FP8 = range(5)
 PATH_PLAIN, PATH_TC, PATH_SPARSE = range(3)
 PRUNE_ZERO_RULE = 1
+SERVER_PACK = 1
 DS_PROFILE = 1
 DS_STREAMING = 2
 DS_NO_AUTOTUNE = 4

@@ -202,13 +202,13 @@ class Server:
     energy on the full instance and submit / admit / done times (ms)."""
 
     def __init__(self, ctx: Context, budget_bytes: int, max_active: int = 8,
-                 chunk_steps: int = 250):
+                 chunk_steps: int = 250, pack: bool = True):
         self.ctx = ctx
         cfg = L.ServerCfg()
         cfg.budget_bytes = int(budget_bytes)
         cfg.max_active = int(max_active)
         cfg.chunk_steps = int(chunk_steps)
-        cfg.flags = 0
+        cfg.flags = L.SERVER_PACK if pack else 0
         cfg.reserved = 0
         self.handle = c_void_p()
         ctx._children.add(self)

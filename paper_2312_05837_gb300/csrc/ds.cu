@@ -935,6 +935,67 @@ int autotune_sparse(ising_ds* ds, int64_t budget, int64_t* done) {
   return rc;
 }
 
+std::string dense_key(const ising_ds* ds) {
+  std::ostringstream k;
+  k << "dense n=" << ds->n << " B=" << ds->B << " spins=" << ds->spin_kind << " planes=" << ds->planes
+    << " ie=" << ds->int_energy;
+  return k.str();
+}
+
+// Tensor-core streaming form: one untimed step, then each candidate tile
+// width for one timed step in the order c0 .. c(k-1), c(k-1) .. c0 (every
+// candidate sees early and late positions), the fastest total kept.
+int autotune_dense(ising_ds* ds, int64_t budget, int64_t* done) {
+  *done = 0;
+  ds->tuned = true;
+  int cand[4];
+  const int nc = tc_bn_candidates(ds, cand);
+  if ((ds->p.flags & ISING_DS_NO_AUTOTUNE) || nc <= 1) return ISING_OK;
+  const std::string key = dense_key(ds);
+  {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    tune_load_locked();
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) return tc_set_bn(ds, it->second);
+  }
+  if (budget < 1 + 2 * nc) return ISING_OK;
+  ising_ctx* ctx = ds->ctx;
+  cudaEvent_t ev[9];
+  for (int k = 0; k <= 2 * nc; ++k) ISING_CUDA(ctx, cudaEventCreate(&ev[k]));
+  int rc = ISING_OK;
+  for (int k = 0; k <= 2 * nc && rc == ISING_OK; ++k) {
+    if (k >= 1) {
+      const int c = k - 1 < nc ? cand[k - 1] : cand[2 * nc - k];
+      rc = tc_set_bn(ds, c);
+      if (rc == ISING_OK) cudaEventRecord(ev[k - 1], ctx->stream);
+    }
+    if (rc == ISING_OK) rc = path_step(ds, true);
+    if (rc == ISING_OK) rc = track_step(ds);
+    ds->t += 1;
+    *done += 1;
+  }
+  if (rc == ISING_OK) cudaEventRecord(ev[2 * nc], ctx->stream);
+  if (rc == ISING_OK) {
+    cudaEventSynchronize(ev[2 * nc]);
+    float best = 0.f;
+    int pick = cand[0];
+    for (int c = 0; c < nc; ++c) {
+      float a = 0.f, b = 0.f;
+      cudaEventElapsedTime(&a, ev[c], ev[c + 1]);
+      cudaEventElapsedTime(&b, ev[2 * nc - 1 - c], ev[2 * nc - c]);
+      if (c == 0 || a + b < best) {
+        best = a + b;
+        pick = cand[c];
+      }
+    }
+    rc = tc_set_bn(ds, pick);
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    tune_store_locked(key, pick);
+  }
+  for (int k = 0; k <= 2 * nc; ++k) cudaEventDestroy(ev[k]);
+  return rc;
+}
+
 }  // namespace
 }  // namespace ising
 
@@ -950,6 +1011,7 @@ int ising::ds_advance(ising_ds* ds, int64_t todo) {
   }
   int64_t s0 = 0;
   if (ds->path == ISING_PATH_SPARSE && !ds->tuned) ISING_TRY(autotune_sparse(ds, todo, &s0));
+  if (ds->path == ISING_PATH_TC && !ds->tuned) ISING_TRY(autotune_dense(ds, todo, &s0));
   const bool use_graph = !(ds->p.flags & ISING_DS_PROFILE) && todo >= 2 * kGraphSteps;
   for (int64_t s = s0; s < todo;) {
     // (t > 0: the kernels have run once outside capture, which sets their attributes)

@@ -269,10 +269,13 @@ int track_pack(ising_ctx* ctx, int spin_kind, const TrackArgs* members, const in
 // packed step launch.
 bool tc_packable(const ising_ds* ds);
 uint64_t tc_pack_key(const ising_ds* ds);
+int tc_bn(const ising_ds* ds);                        // restart-tile width
+int tc_bn_candidates(const ising_ds* ds, int* out);   // widths the autotuner may try (<= 4)
+int tc_set_bn(ising_ds* ds, int bn);
 size_t tc_pack_entry_bytes();
 int tc_pack_entry(ising_ds* ds, void* host_entry);
-int tc_pack_launch(ising_ctx* ctx, uint64_t key, const void* entries, const int* start, int count,
-                   int tiles, int* err);
+int tc_pack_launch(ising_ctx* ctx, uint64_t key, int bn, const void* entries, const int* start,
+                   int count, int tiles, int* err);
 int export_spins_int8(ising_ds* ds, int slot, int8_t* out);  // spins[slot] -> int8 [B][n]
 
 }  // namespace ising

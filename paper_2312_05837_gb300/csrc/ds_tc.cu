@@ -2326,7 +2326,35 @@ bool tc_packable(const ising_ds* ds) {
 
 uint64_t tc_pack_key(const ising_ds* ds) {
   auto st = static_cast<const TcState*>(ds->tc);
-  return (st->fp8 ? 1u : 0u) | (ds->int_energy ? 2u : 0u) | ((uint64_t)st->BN << 2);
+  return (st->fp8 ? 1u : 0u) | (ds->int_energy ? 2u : 0u);
+}
+
+int tc_bn(const ising_ds* ds) { return static_cast<const TcState*>(ds->tc)->BN; }
+
+// Restart-tile widths the streaming form can take for this session (tiles at
+// least half used); none for the resident forms.
+int tc_bn_candidates(const ising_ds* ds, int* out) {
+  auto st = static_cast<const TcState*>(ds->tc);
+  if (!st || st->resident) return 0;
+  int k = 0;
+  for (int bn : {64, 128, 224, 256})
+    if (bn == 64 || bn / 2 < ds->B) out[k++] = bn;
+  return k;
+}
+
+// Switches the streaming form to tiles of `bn` restarts (the products, and
+// so the results, do not depend on it); the operand maps are rebuilt on the
+// next launch.
+int tc_set_bn(ising_ds* ds, int bn) {
+  auto st = static_cast<TcState*>(ds->tc);
+  if (st->resident) return fail(ds->ctx, ISING_EINVAL, "tile width of a resident form");
+  if (st->BN == bn) return ISING_OK;
+  st->BN = bn;
+  st->maps_ready = false;
+  st->trace.release();
+  const int tiles = ceil_div_i(ds->n, kBM) * ceil_div_i(ds->B, bn);
+  st->grid = std::max(1, std::min(tiles, ds->ctx->sm_count));
+  return ISING_OK;
 }
 
 size_t tc_pack_entry_bytes() { return sizeof(PackEntry); }
@@ -2405,10 +2433,10 @@ int pack_launch_bn(ising_ctx* ctx, bool ie, bool fp8, const void* entries, const
 }
 }  // namespace
 
-int tc_pack_launch(ising_ctx* ctx, uint64_t key, const void* entries, const int* start, int count,
-                   int tiles, int* err) {
+int tc_pack_launch(ising_ctx* ctx, uint64_t key, int bn, const void* entries, const int* start,
+                   int count, int tiles, int* err) {
   const bool fp8 = key & 1u, ie = (key & 2u) != 0;
-  switch ((int)(key >> 2)) {
+  switch (bn) {
     case 256: return pack_launch_bn<256>(ctx, ie, fp8, entries, start, count, tiles, err);
     case 224: return pack_launch_bn<224>(ctx, ie, fp8, entries, start, count, tiles, err);
     case 128: return pack_launch_bn<128>(ctx, ie, fp8, entries, start, count, tiles, err);

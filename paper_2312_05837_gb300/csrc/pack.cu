@@ -18,6 +18,7 @@ struct ising_pack {
   ising_ctx* ctx = nullptr;
   std::vector<ising_ds*> members;
   uint64_t key = 0;
+  int bn = 128;     // restart-tile width of every member's tiles
   int spin_kind = 0;
   int tiles = 0;
   int64_t restarts = 0;
@@ -39,7 +40,7 @@ constexpr int64_t kPackGraphSteps = 25;
 int pack_step(ising_pack* pk) {
   ising_ctx* ctx = pk->ctx;
   int* err = reinterpret_cast<int*>(pk->words.as<unsigned long long>() + 1);
-  ISING_TRY(tc_pack_launch(ctx, pk->key, pk->entries.p, pk->start.as<int>(),
+  ISING_TRY(tc_pack_launch(ctx, pk->key, pk->bn, pk->entries.p, pk->start.as<int>(),
                            (int)pk->members.size(), pk->tiles, err));
   return track_pack(ctx, pk->spin_kind, pk->targs.as<TrackArgs>(), pk->rstart.as<int64_t>(),
                     (int)pk->members.size(), pk->restarts, pk->words.as<unsigned long long>());
@@ -158,13 +159,13 @@ extern "C" int ising_pack_create(ising_ctx* ctx, ising_ds* const* sessions, int3
     const uint64_t kk = tc_pack_key(ds);
     if (k == 0) key = kk;
     else if (kk != key)
-      return fail(ctx, ISING_EINVAL,
-                  "pack: members differ in operand type, energy mode or tile width (member %d)", k);
+      return fail(ctx, ISING_EINVAL, "pack: members differ in operand type or energy mode (member %d)", k);
   }
   auto pk = new ising_pack();
   pk->ctx = ctx;
   pk->members.assign(sessions, sessions + count);
   pk->key = key;
+  pk->bn = tc_bn(sessions[0]);
   pk->spin_kind = sessions[0]->spin_kind;
   int rc = [&]() -> int {
     ISING_CUDA(ctx, cudaEventCreateWithFlags(&pk->ev, cudaEventDisableTiming));
@@ -175,9 +176,10 @@ extern "C" int ising_pack_create(ising_ctx* ctx, ising_ds* const* sessions, int3
     std::vector<int64_t> rstart(count + 1, 0);
     for (int k = 0; k < count; ++k) {
       ising_ds* ds = sessions[k];
+      // one tile width for all (the first member's): the results do not depend on it
+      ISING_TRY(tc_set_bn(ds, pk->bn));
       ISING_TRY(tc_pack_entry(ds, ent.data() + eb * k));
-      const int64_t bn = (int64_t)(key >> 2);
-      start[k + 1] = start[k] + ceil_div_i(ds->n, 128) * ceil_div_i(ds->B, bn);
+      start[k + 1] = start[k] + ceil_div_i(ds->n, 128) * ceil_div_i(ds->B, pk->bn);
       targs[k] = track_args(ds);
       rstart[k + 1] = rstart[k] + ds->B;
     }
@@ -217,10 +219,11 @@ extern "C" int ising_pack_run(ising_pack* pk, int64_t steps) {
   return pack_error(pk);
 }
 
+// Nothing waits here: the pack's buffers are freed in stream order after its
+// launches, and a stream or event destroyed with work pending is released
+// once that work completes.
 extern "C" int ising_pack_destroy(ising_pack* pk) {
   if (!pk) return ISING_OK;
-  if (pk->ctx) cudaStreamSynchronize(pk->ctx->stream);
-  if (pk->gstream) cudaStreamSynchronize(pk->gstream);
   if (pk->graph) cudaGraphExecDestroy(pk->graph);
   if (pk->gstream) cudaStreamDestroy(pk->gstream);
   if (pk->ev) cudaEventDestroy(pk->ev);

@@ -11,8 +11,14 @@
 // releases its memory and slot. Slots progress independently, so a small
 // request never waits for a large one's chunk, and requests arriving at any
 // time are admitted as soon as a slot and memory free up.
+// With ISING_SERVER_PACK, the dense tensor-core requests that are ready in a
+// round are grouped by kind (operand type, energy mode, tile width) and each
+// group advances its chunk as one pack (ising_pack: one launch per step for
+// all of them, on the server's own stream); a group's pack is kept, with its
+// captured step graph, while the group stays the same.
 #include "ds_internal.cuh"
 
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -25,6 +31,7 @@ using namespace ising;
 
 namespace ising {
 int prune_device(ising_ctx* ctx, const DevInstance& I, int flags, ising_prune_result** out);
+int pack_advance(ising_pack* pk, int64_t steps);
 }
 
 namespace {
@@ -96,6 +103,10 @@ struct ising_server {
   size_t used = 0;
   bool stop = false;
   uint64_t next_id = 1;
+  // packed advancement (ISING_SERVER_PACK): the server's stream, and the
+  // pack of each current group of requests (keyed by its members' ids)
+  std::unique_ptr<ising_ctx> pack_ctx;
+  std::map<std::vector<uint64_t>, ising_pack*> packs;
   std::chrono::steady_clock::time_point t0;
 
   double now_ms() const {
@@ -197,6 +208,7 @@ void worker_loop(ising_server* srv) {
     // 2. every request whose last chunk has completed: next chunk, or finish
     bool progressed = !admitted.empty();
     std::vector<Request*> finished;
+    std::map<uint64_t, std::vector<Request*>> groups;  // packable requests by kind
     for (Request* r : act) {
       if (r->in_flight) {
         const cudaError_t q = cudaEventQuery(r->ev);
@@ -212,6 +224,10 @@ void worker_loop(ising_server* srv) {
       const bool steps_done =
           r->status != ISING_OK || !r->ds || r->ds->t >= r->ds->T || r->ds->conv_all;
       if (!steps_done) {
+        if (srv->pack_ctx && tc_packable(r->ds) && !r->ds->conv.p) {
+          groups[tc_pack_key(r->ds)].push_back(r);
+          continue;
+        }
         const int64_t todo = std::min<int64_t>(chunk, r->ds->T - r->ds->t);
         int rc = ds_advance(r->ds, todo);
         if (rc == ISING_OK && cudaEventRecord(r->ev, srv->slots[r->slot]->stream) != cudaSuccess)
@@ -227,6 +243,55 @@ void worker_loop(ising_server* srv) {
       release_request(srv, r);
       r->t_done = srv->now_ms();
       finished.push_back(r);
+    }
+    // 3. each group of ready dense tensor-core requests of one kind: one
+    // packed chunk (their chunks end together, at the group's smallest
+    // remaining step count)
+    for (auto& kv : groups) {
+      std::vector<Request*>& grp = kv.second;
+      std::vector<uint64_t> ids;
+      for (Request* r : grp) ids.push_back(r->id);
+      int64_t todo = chunk;
+      for (Request* r : grp) todo = std::min<int64_t>(todo, r->ds->T - r->ds->t);
+      int rc = ISING_OK;
+      ising_pack* pk = nullptr;
+      auto it = srv->packs.find(ids);
+      if (it != srv->packs.end()) {
+        pk = it->second;
+      } else {
+        std::vector<ising_ds*> ds;
+        for (Request* r : grp) ds.push_back(r->ds);
+        rc = ising_pack_create(srv->pack_ctx.get(), ds.data(), (int32_t)ds.size(), &pk);
+        if (rc == ISING_OK) srv->packs[ids] = pk;
+      }
+      if (rc == ISING_OK) rc = pack_advance(pk, todo);
+      for (Request* r : grp) {
+        int rr = rc;
+        if (rr == ISING_OK && cudaEventRecord(r->ev, srv->pack_ctx->stream) != cudaSuccess)
+          rr = ISING_ECUDA;
+        if (rr != ISING_OK) r->status = rr;
+        else r->in_flight = true;
+      }
+    }
+    // packs whose group no longer exists (a member finished, or the group
+    // changed): their launches are complete (every member was ready)
+    for (auto it = srv->packs.begin(); it != srv->packs.end();) {
+      bool live = false;
+      for (auto& kv : groups) {
+        std::vector<uint64_t> ids;
+        for (Request* r : kv.second) ids.push_back(r->id);
+        if (ids == it->first) live = true;
+      }
+      bool in_flight = false;
+      for (Request* r : act)
+        if (r->in_flight && std::find(it->first.begin(), it->first.end(), r->id) != it->first.end())
+          in_flight = true;
+      if (!live && !in_flight) {
+        ising_pack_destroy(it->second);
+        it = srv->packs.erase(it);
+      } else {
+        ++it;
+      }
     }
     lk.lock();
     for (Request* r : finished) {
@@ -274,7 +339,8 @@ extern "C" int ising_server_create(ising_ctx* ctx, const ising_server_cfg* cfg,
                                    ising_server** out) {
   if (!ctx) return ISING_EINVAL;
   if (!cfg || !out) return fail(ctx, ISING_EINVAL, "cfg and out are required");
-  if (cfg->max_active < 1 || cfg->max_active > 256 || cfg->chunk_steps < 1 || cfg->flags != 0)
+  if (cfg->max_active < 1 || cfg->max_active > 256 || cfg->chunk_steps < 1 ||
+      (cfg->flags & ~ISING_SERVER_PACK) != 0)
     return fail(ctx, ISING_EINVAL, "bad server configuration");
   *out = nullptr;
   auto srv = new ising_server();
@@ -295,6 +361,18 @@ extern "C" int ising_server_create(ising_ctx* ctx, const ising_server_cfg* cfg,
     srv->slots.push_back(std::move(c));
   }
   srv->slot_busy.assign(cfg->max_active, false);
+  if (cfg->flags & ISING_SERVER_PACK) {
+    auto c = std::make_unique<ising_ctx>();
+    c->device = ctx->device;
+    c->sm_count = ctx->sm_count;
+    c->smem_optin = ctx->smem_optin;
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      for (auto& s : srv->slots) cudaStreamDestroy(s->stream);
+      delete srv;
+      return fail(ctx, ISING_ECUDA, "stream creation failed");
+    }
+    srv->pack_ctx = std::move(c);
+  }
   srv->worker = std::thread(worker_loop, srv);
   *out = srv;
   return ISING_OK;
@@ -401,6 +479,12 @@ extern "C" int ising_server_destroy(ising_server* srv) {
     srv->cv.notify_all();
   }
   if (srv->worker.joinable()) srv->worker.join();
+  for (auto& kv : srv->packs) ising_pack_destroy(kv.second);
+  srv->packs.clear();
+  if (srv->pack_ctx) {
+    cudaStreamSynchronize(srv->pack_ctx->stream);
+    cudaStreamDestroy(srv->pack_ctx->stream);
+  }
   for (auto& s : srv->slots) {
     cudaStreamSynchronize(s->stream);
     cudaStreamDestroy(s->stream);

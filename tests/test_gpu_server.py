@@ -24,13 +24,19 @@ def _mix():
         (synth.er_dense(520, 5, mean_degree=8, weights="pm1"), dict(restarts=300, steps=250)),
         (synth.random_sparse_instance(90, 6, p=0.1, kind="int", h="int", layout="dense"),
          dict(restarts=64, steps=500, precision="fp32")),
+        (synth.er_dense(180, 7, p=0.05, weights="pm1"), dict(restarts=100, steps=300)),
     ]
 
 
-def test_results_in_the_mix_equal_results_alone(gpu_ctx):
+@pytest.mark.parametrize("pack", [False, True])
+def test_results_in_the_mix_equal_results_alone(gpu_ctx, pack):
+    """With packing, the dense tensor-core requests of one kind that are
+    ready together advance in packed launches (the three E4M3 max-cut ones
+    here share a pack, different sizes and restart counts)."""
     mix = _mix()
     alone = [api.solve(gpu_ctx, inst, seed=11 + k, **kw) for k, (inst, kw) in enumerate(mix)]
-    srv = api.Server(gpu_ctx, budget_bytes=8 << 30, max_active=4, chunk_steps=64)
+    srv = api.Server(gpu_ctx, budget_bytes=8 << 30, max_active=4 if not pack else 6,
+                     chunk_steps=64, pack=pack)
     ids = [srv.submit(inst, seed=11 + k, **kw) for k, (inst, kw) in enumerate(mix)]
     for k, rid in enumerate(ids):
         res = srv.wait(rid, timeout=300)
