@@ -146,7 +146,9 @@ typedef struct ising_ds_params {
  * rounded spins: restart b stops at the first step t >= 5 where
  * max - min of E_{t-4..t}(b) <= 0.005 |E_t(b) - E_1(b)| (at convergence
  * sin(theta) -> s and the paper's loss equals E - mu d). A stopped restart's
- * best and last energy are those of steps 1..t; the run ends once every
+ * best and last energy are those of steps 1..t; the streaming tensor-core,
+ * sparse and plain step kernels skip every tile or slice whose restarts have
+ * all stopped (early retirement, see ising_ds_work); the run ends once every
  * restart has stopped (checked every 48 steps, so up to 47 more steps may run,
  * which change nothing) and ising_ds_stats.steps_done tells how far it went;
  * the final evaluation (step T+1) applies to restarts still running after T.
@@ -365,6 +367,14 @@ int ising_ds_trace(ising_ds* ds, uint64_t* out, int64_t cap, int64_t* count);
 /* Energies E(s_t) of the spins consumed by the most recent step, [B]. */
 int ising_ds_last_energies(ising_ds* ds, double* E, int mem);
 /* Per-restart best so far: energy [B], step [B], spins [B][n] (any NULL). */
+/* Restart-steps the session's update launches computed so far: every tile
+ * or slice of restarts counts its restarts once per step (the resident
+ * tensor-core forms count B per step). Without ISING_DS_CONVERGE this is
+ * B x steps; with it, tiles and slices whose restarts have all stopped are
+ * skipped (early retirement: their results are final, their state is left
+ * where it stopped), so it falls below B x steps. The resident tensor-core
+ * forms keep every restart running. Synchronises the session's stream. */
+int ising_ds_work(ising_ds* ds, int64_t* restart_steps);
 /* With ISING_DS_CONVERGE: the step at which each restart stopped (0 while it
  * runs), [B] int64 in memory `mem`. Without the flag all zeros. */
 int ising_ds_convergence(ising_ds* ds, int64_t* step, int mem);

@@ -504,6 +504,13 @@ class Session:
         self.ctx.check(self.ctx.lib.ising_ds_last_energies(self.handle, _ptr(E), L.MEM_HOST))
         return E
 
+    def work(self) -> int:
+        """Restart-steps the update launches computed (below B x steps when
+        the convergence rule retires restarts)."""
+        w = c_int64()
+        self.ctx.check(self.ctx.lib.ising_ds_work(self.handle, byref(w)))
+        return w.value
+
     def convergence(self) -> np.ndarray:
         """Step at which each restart stopped under the convergence rule (0
         while it runs)."""

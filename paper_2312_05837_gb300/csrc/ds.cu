@@ -146,8 +146,9 @@ __device__ __forceinline__ void track_restart(const TrackArgs& A, long long t, i
       A.best_E[b] = E;
       A.best_t[b] = t;
     }
-    if (A.conv_step && t <= A.T)
-      conv_update(A.conv_ring, A.conv_init, A.conv_step, A.conv_count, A.B, b, t, E);
+    if (A.conv_step && t <= A.T &&
+        conv_update(A.conv_ring, A.conv_init, A.conv_step, A.conv_count, A.B, b, t, E) && A.live32)
+      atomicSub(&A.live32[b >> 5], 1);
   }
   if (KIND == kSpinBits) {
     // bit-packed spins are copied by track_bits_copy_kernel
@@ -421,6 +422,7 @@ TrackArgs track_args(const ising_ds* ds) {
   A.conv_init = conv ? ds->conv_init() : nullptr;
   A.conv_step = conv ? ds->conv_step() : nullptr;
   A.conv_count = conv ? ds->conv_count() : nullptr;
+  A.live32 = conv ? ds->live.as<int>() : nullptr;
   return A;
 }
 
@@ -565,7 +567,15 @@ int common_alloc(ising_ds* ds) {
   if (ds->p.flags & ISING_DS_CONVERGE) {
     ISING_TRY(dev_alloc(ctx, ds->conv, (size_t)(7 * B + 1) * 8));
     ISING_CUDA(ctx, cudaMemsetAsync(ds->conv.p, 0, ds->conv.bytes, ctx->stream));
+    const int64_t nb = (B + 31) / 32;
+    std::vector<int> live(nb);
+    for (int64_t k = 0; k < nb; ++k) live[k] = (int)std::min<int64_t>(32, B - 32 * k);
+    ISING_TRY(dev_alloc(ctx, ds->live, nb * 4));
+    ISING_CUDA(ctx, cudaMemcpyAsync(ds->live.p, live.data(), nb * 4, cudaMemcpyHostToDevice, ctx->stream));
+    ISING_CUDA(ctx, cudaStreamSynchronize(ctx->stream));  // (the host vector goes away)
   }
+  ISING_TRY(dev_alloc(ctx, ds->work, 8));
+  ISING_CUDA(ctx, cudaMemsetAsync(ds->work.p, 0, 8, ctx->stream));
   ISING_TRY(dev_alloc(ctx, ds->counters, 16));
   ISING_TRY(dev_alloc(ctx, ds->scratch, 64));
   fill_double<<<grid1d(ctx, B), 256, 0, ctx->stream>>>(ds->best_E.as<double>(), B, INFINITY);
@@ -1006,6 +1016,7 @@ int ising::ds_advance(ising_ds* ds, int64_t todo) {
   if (ds->path == ISING_PATH_TC && tc_is_resident(ds)) {
     ISING_TRY(tc_run_resident(ds, todo));
     ds->t += todo;
+    ds->work_host += todo * ds->B;
     if (ds->p.flags & ISING_DS_PROFILE) ds->kernel_launches += todo;
     return ISING_OK;
   }
@@ -1243,6 +1254,16 @@ extern "C" int ising_ds_last_energies(ising_ds* ds, double* E, int mem) {
   if (!E) return fail(ds->ctx, ISING_EINVAL, "E is NULL");
   ISING_TRY(copy_out(ds->ctx, E, ds->last_E.p, ds->B * 8, mem));
   ISING_CUDA(ds->ctx, cudaStreamSynchronize(ds->ctx->stream));
+  return ISING_OK;
+}
+
+extern "C" int ising_ds_work(ising_ds* ds, int64_t* restart_steps) {
+  if (!ds) return ISING_EINVAL;
+  if (!restart_steps) return fail(ds->ctx, ISING_EINVAL, "restart_steps is NULL");
+  unsigned long long w = 0;
+  ISING_CUDA(ds->ctx, cudaMemcpyAsync(&w, ds->work.p, 8, cudaMemcpyDeviceToHost, ds->ctx->stream));
+  ISING_CUDA(ds->ctx, cudaStreamSynchronize(ds->ctx->stream));
+  *restart_steps = (int64_t)w + ds->work_host;
   return ISING_OK;
 }
 

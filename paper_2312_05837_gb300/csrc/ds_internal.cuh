@@ -85,6 +85,17 @@ __device__ __forceinline__ bool conv_update(double* ring, double* init, long lon
   return false;
 }
 
+// Early retirement under the convergence rule: live32[k] counts the restarts
+// of block [32 k, 32 k + 32) that have not stopped (null when the rule is
+// off). A step kernel skips a tile or slice whose restarts [b0, b1) have all
+// stopped: their results are final and their state is left as it is.
+__device__ __forceinline__ bool restarts_retired(const int* live32, int64_t b0, int64_t b1) {
+  if (!live32) return false;
+  for (int64_t k = b0 >> 5; k < ((b1 + 31) >> 5); ++k)
+    if (live32[k] > 0) return false;
+  return true;
+}
+
 enum SpinKind { kSpinF32 = 0, kSpinBF16 = 1, kSpinBits = 2, kSpinE4M3 = 3, kSpinF16 = 4 };
 
 // Sign bit of each byte of four E4M3 spins -> four int8 +1 / -1.
@@ -155,6 +166,7 @@ struct TrackArgs {
   double* conv_init;
   long long* conv_step;
   unsigned long long* conv_count;
+  int* live32;  // live restarts per block of 32 (convergence rule), or null
 };
 
 // What a step launch does: the full update, only the energies of the input
@@ -193,7 +205,13 @@ struct ising_ds {
   // convergence rule (ISING_DS_CONVERGE): [5][B] ring of energies, [B] E_1,
   // [B] stopping step, and the count of stopped restarts
   ising::DevMem conv;
+  ising::DevMem live;      // convergence rule: int32 live restarts per block of 32
   bool conv_all = false;   // every restart has stopped
+  // restart-steps the update kernels computed: a device counter (tiles and
+  // slices add their restarts once per step) plus the resident forms' steps
+  // x B counted on the host
+  ising::DevMem work;
+  int64_t work_host = 0;
   // relaxed product (ISING_DS_RELAXED): x_t = sin(theta) in slot t % 2, laid
   // out like the state (FP32; the 16-bit operand type on the tensor-core path)
   ising::DevMem xbuf[2];

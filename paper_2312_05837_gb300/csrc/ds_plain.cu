@@ -28,7 +28,7 @@ __global__ void __launch_bounds__(256) plain_step_kernel(
     float* __restrict__ v, const float* __restrict__ hf, const int32_t* __restrict__ hint,
     StepConsts k, const float2* __restrict__ bias, const long long* __restrict__ counters,
     long long* __restrict__ qpart, long long* __restrict__ hpart, float* __restrict__ epart,
-    float* __restrict__ Gout) {
+    float* __restrict__ Gout, const int* __restrict__ live32, unsigned long long* __restrict__ work) {
   constexpr bool UPDATE = MODE == kModeUpdate || MODE == kModeRelaxed;
   constexpr bool PARTIALS = MODE == kModeUpdate || MODE == kModeEnergy;
   __shared__ float As[BK][BM + 4];
@@ -36,6 +36,9 @@ __global__ void __launch_bounds__(256) plain_step_kernel(
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   const int64_t m0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * BN;
+  const int64_t ne = n0 + BN < B ? n0 + BN : B;
+  if (MODE != kModeCoupling && restarts_retired(live32, n0, ne)) return;  // (uniform per block)
+  if (UPDATE && work && blockIdx.x == 0 && tid == 0) atomicAdd(work, (unsigned long long)(ne - n0));
   float acc[8][8];
 #pragma unroll
   for (int r = 0; r < 8; ++r)
@@ -161,7 +164,8 @@ int plain_step(ising_ds* ds, int mode, float* Gout) {
       ds->Jf.as<float>(), ds->n, ds->B, X, S, Xn, Sn, ds->theta.as<float>(), ds->m.as<float>(),\
       ds->v.as<float>(), ds->hf.as<float>(), ds->hint.as<int32_t>(), ds->k,                   \
       ds->bias.as<float2>(), ds->counters.as<long long>(), ds->qpart[ps].as<long long>(),     \
-      ds->hpart[ps].as<long long>(), ds->epart[ps].as<float>(), Gout)
+      ds->hpart[ps].as<long long>(), ds->epart[ps].as<float>(), Gout,                        \
+      ds->live.p ? ds->live.as<int>() : nullptr, ds->work.as<unsigned long long>())
   if (mode == kModeUpdate) {
     if (ds->int_energy) ISING_PLAIN(kModeUpdate, true); else ISING_PLAIN(kModeUpdate, false);
   } else if (mode == kModeEnergy) {

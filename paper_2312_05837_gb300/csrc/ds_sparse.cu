@@ -31,13 +31,18 @@ __global__ void __launch_bounds__(256, Q == 1 ? (MODE == kModeRelaxed ? 3 : 4) :
     const float* __restrict__ hf, const int32_t* __restrict__ hint, StepConsts k,
     const float2* __restrict__ bias, const long long* __restrict__ counters,
     long long* __restrict__ qpart, long long* __restrict__ hpart, float* __restrict__ epart,
-    float* __restrict__ Gout, const float* __restrict__ xin, float* __restrict__ xout) {
+    float* __restrict__ Gout, const float* __restrict__ xin, float* __restrict__ xout,
+    int64_t B, const int* __restrict__ live32, unsigned long long* __restrict__ work) {
   constexpr bool RELAXED = MODE == kModeRelaxed;
   constexpr bool UPDATE = MODE == kModeUpdate || RELAXED;
   constexpr int W = 8;  // warps per block
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t words = Bp / 32;
   const int64_t cb = (int64_t)blockIdx.y * (128 * Q);  // first restart of this slice
+  const int64_t ce = cb + 128 * Q < B ? cb + 128 * Q : B;
+  if (MODE != kModeCoupling && restarts_retired(live32, cb, ce)) return;  // (uniform per block)
+  if (UPDATE && work && blockIdx.x == 0 && threadIdx.x == 0)
+    atomicAdd(work, (unsigned long long)(ce - cb));
   const int64_t wofs = cb / 32 + (lane >> 3);
   const int nshift = 4 * (lane & 7);
   const int64_t r0 = (int64_t)blockIdx.x * rows_per_block;
@@ -250,7 +255,8 @@ int sparse_step(ising_ds* ds, int mode, float* Gout) {
       ds->sp_val.p, in, out, ds->theta.as<float>(), ds->m.as<float>(), ds->v.as<float>(),     \
       ds->hf.as<float>(), ds->hint.as<int32_t>(), ds->k, ds->bias.as<float2>(),               \
       ds->counters.as<long long>(), ds->qpart[ps].as<long long>(),                            \
-      ds->hpart[ps].as<long long>(), ds->epart[ps].as<float>(), Gout, xin, xout
+      ds->hpart[ps].as<long long>(), ds->epart[ps].as<float>(), Gout, xin, xout, ds->B,          \
+      ds->live.p ? ds->live.as<int>() : nullptr, ds->work.as<unsigned long long>()
 #define ISING_SP_V(U, I) \
   do { if (ds->sp_int8) ISING_SP(U, I, true); else ISING_SP(U, I, false); } while (0)
 #define ISING_SP_I(U) \

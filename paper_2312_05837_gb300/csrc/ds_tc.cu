@@ -82,6 +82,8 @@ struct TcArgs {
   int gmagic;  // resident epilogue's integer energy mode (EMODE of resident_chunks)
   unsigned long long* trace;  // per-CTA role timeline (profiling), or null
   int nfull;   // streaming kernel: whole k-blocks loadable in pairs (0: never pair)
+  const int* live32;          // convergence rule: live restarts per 32 (tiles retire), or null
+  unsigned long long* work;   // restart-steps computed (update launches), or null
 };
 
 // +1 / -1 in the 16-bit operand type (FP16 0x3C00, BF16 0x3F80; bit 15 is the
@@ -181,6 +183,7 @@ struct TileRef {
   long long* hpart;
   float* epart;
   int mt, m0, n0;
+  bool skip;  // every restart of the tile has stopped (convergence rule)
   __device__ const CUtensorMap* a(int plane) const { return plane == 0 ? A0 : (plane == 1 ? A1 : A2); }
   __device__ const CUtensorMap* j2(int plane) const { return plane == 0 ? J0 : (plane == 1 ? J1 : J2); }
 };
@@ -211,6 +214,7 @@ struct OneInstance {
     r.mt = tl / P.ntiles;
     r.m0 = r.mt * kBM;
     r.n0 = (tl % P.ntiles) * BN;
+    r.skip = restarts_retired(P.live32, r.n0, min((int64_t)r.n0 + BN, P.B));
     return r;
   }
 };
@@ -268,6 +272,7 @@ struct PackedInstances {
     r.mt = local / e.args.ntiles;
     r.m0 = r.mt * kBM;
     r.n0 = (local % e.args.ntiles) * BN;
+    r.skip = restarts_retired(e.args.live32, r.n0, min((int64_t)r.n0 + BN, e.args.B));
     return r;
   }
 };
@@ -335,6 +340,7 @@ __device__ __forceinline__ void step_tiles(const Src& src) {
       bool ok = true;
       for (int tl = blockIdx.x; tl < total && ok; tl += gridDim.x) {
         const TileRef T = src.tile(tl);
+        if (T.skip) continue;
         const TcArgs& P = src.args(T);
         const int nk = P.nk, nfull = P.nfull, planes = P.planes;
         const int nkt = nk * planes;
@@ -349,7 +355,7 @@ __device__ __forceinline__ void step_tiles(const Src& src) {
             tc::fence_map_acquire(T.S2);
           }
         }
-        if (tl == (int)blockIdx.x) tc::prefetch_map(jside ? T.A0 : T.B);
+        if (issued == 0) tc::prefetch_map(jside ? T.A0 : T.B);
         for (int kt0 = 0; kt0 < nkt; kt0 += Lay::kKps) {
           if (!tc::mbar_wait(&empty[stage], phase ^ 1, abort_flag, kWaitCycles)) {
             ok = false;
@@ -399,8 +405,9 @@ __device__ __forceinline__ void step_tiles(const Src& src) {
       uint32_t stage = 0, phase = 0;
       int it = 0;
       bool ok = true;
-      for (int tl = blockIdx.x; tl < total && ok; tl += gridDim.x, ++it) {
+      for (int tl = blockIdx.x; tl < total && ok; tl += gridDim.x) {
         const TileRef T = src.tile(tl);
+        if (T.skip) continue;
         const TcArgs& P = src.args(T);
         const int nkt = P.nk * P.planes;
         const uint32_t idesc = op_idesc(BN, FP8, P.f16);
@@ -441,6 +448,7 @@ __device__ __forceinline__ void step_tiles(const Src& src) {
           if (++stage == STAGES) { stage = 0; phase ^= 1; }
         }
         if (ok) tc::mma_commit(&acc_full[buf]);
+        ++it;
       }
       ISING_TRACE(4);
       if (!ok) {
@@ -455,8 +463,9 @@ __device__ __forceinline__ void step_tiles(const Src& src) {
     const int part = (warp - 4) >> 2;   // which quarter of the tile's columns
     constexpr int kCols = BN / 4;
     int it = 0;
-    for (int tl = blockIdx.x; tl < total; tl += gridDim.x, ++it) {
+    for (int tl = blockIdx.x; tl < total; tl += gridDim.x) {
       const TileRef T = src.tile(tl);
+      if (T.skip) continue;
       const TcArgs& P = src.args(T);
       const long long t = P.counters[0] + 1;
       const float2 bc = P.bias[t];
@@ -469,9 +478,13 @@ __device__ __forceinline__ void step_tiles(const Src& src) {
       uint8_t* __restrict__ Sout8 = static_cast<uint8_t*>(T.Snext);
       const int buf = it & 1;
       const uint32_t use = (uint32_t)(it >> 1);
+      ++it;
       const int mt = T.mt;
       const int64_t m0 = T.m0;
       const int64_t n0 = (int64_t)T.n0 + part * kCols;
+      if ((MODE == kModeUpdate || MODE == kModeRelaxed) && P.work && mt == 0 && warp == 4 &&
+          lane == 0)
+        atomicAdd(P.work, (unsigned long long)min((int64_t)BN, P.B - T.n0));
       if (!tc::mbar_wait(&acc_full[buf], use & 1, abort_flag, kWaitCycles)) {
         atomicExch(src.err(), 3);
         break;
@@ -2142,6 +2155,8 @@ int tc_run(ising_ds* ds, int mode, float* Gout) {
   // |G_i| <= max |J_ij| * n in stored units
   a.gmagic = st->emode;
   a.trace = nullptr;
+  a.live32 = ds->live.p ? ds->live.as<int>() : nullptr;
+  a.work = ds->work.as<unsigned long long>();
   if (ds->p.flags & ISING_DS_PROFILE) {
     if (!st->trace.p) ISING_TRY(dev_alloc(ds->ctx, st->trace, (size_t)st->grid * 8 * 8));
     a.trace = st->trace.as<unsigned long long>();
@@ -2219,6 +2234,8 @@ int tc_run_resident(ising_ds* ds, int64_t steps) {
     a.has_h = ds->inst.has_h ? 1 : 0;
     a.gmagic = st->emode;
     a.trace = nullptr;
+    a.live32 = nullptr;  // the resident forms do not retire restarts
+    a.work = nullptr;
     sa.steps = steps;
     sa.t0 = ds->t;
     sa.spins_out = ds->spins[(ds->t + steps + 1) % 3].p;
@@ -2262,6 +2279,8 @@ int tc_run_resident(ising_ds* ds, int64_t steps) {
   // |G_i| <= max |J_ij| * n in stored units
   a.gmagic = st->emode;
   a.trace = nullptr;
+  a.live32 = nullptr;  // the resident forms do not retire restarts
+  a.work = nullptr;
   if (ds->p.flags & ISING_DS_PROFILE) {
     if (!st->trace.p) ISING_TRY(dev_alloc(ds->ctx, st->trace, (size_t)st->grid * 8 * 8));
     a.trace = st->trace.as<unsigned long long>();
@@ -2403,6 +2422,8 @@ int tc_pack_entry(ising_ds* ds, void* host_entry) {
   a.has_h = ds->inst.has_h ? 1 : 0;
   a.gmagic = st->emode;
   a.nfull = st->nfull;
+  a.live32 = ds->live.p ? ds->live.as<int>() : nullptr;
+  a.work = ds->work.as<unsigned long long>();
   return ISING_OK;
 }
 

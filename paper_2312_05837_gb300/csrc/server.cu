@@ -224,7 +224,7 @@ void worker_loop(ising_server* srv) {
       const bool steps_done =
           r->status != ISING_OK || !r->ds || r->ds->t >= r->ds->T || r->ds->conv_all;
       if (!steps_done) {
-        if (srv->pack_ctx && tc_packable(r->ds) && !r->ds->conv.p) {
+        if (srv->pack_ctx && tc_packable(r->ds)) {
           groups[tc_pack_key(r->ds)].push_back(r);
           continue;
         }

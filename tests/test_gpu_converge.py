@@ -100,3 +100,33 @@ def test_server_request_with_the_rule_matches_the_session(gpu_ctx):
     assert res["status"] == 0
     assert res["best_energy"] == alone["best_energy"]
     np.testing.assert_array_equal(res["best_spins"], alone["best_spins"])
+
+
+@pytest.mark.parametrize("name,inst,kw,width", [
+    ("tc_stream", synth.er_dense(150, 1, p=0.08, weights="pm1"),
+     dict(precision="fp8", streaming=True), 128),
+    ("plain", synth.random_sparse_instance(130, 4, p=0.1, kind="int", h="int", layout="dense"),
+     dict(precision="fp32"), 128),
+    ("sparse", synth.torus_csr(10, 13, 5), dict(), 128),
+])
+def test_retired_tiles_are_skipped(gpu_ctx, name, inst, kw, width):
+    """Early retirement: a tile (or slice) of restarts is computed at step t
+    exactly when one of its restarts is still running then, i.e. has not
+    stopped or stopped at a step >= t. The restart-steps the kernels report
+    equal that count over the steps run, below B x steps, and the results
+    are those of the rule (the trace test above)."""
+    B, T = 520, 400
+    s = api.Session(gpu_ctx, inst, restarts=B, steps=T, lr=0.05, seed=3, converge=True,
+                    autotune=False, **kw)
+    s.run(T)
+    done = s.result()["steps_done"]
+    conv = s.convergence()
+    last = np.where(conv > 0, conv, np.iinfo(np.int64).max)
+    want = 0
+    for b0 in range(0, B, width):
+        b1 = min(b0 + width, B)
+        want += (b1 - b0) * min(int(last[b0:b1].max()), done)
+    got = s.work()
+    assert got == want, (got, want, done)
+    assert got < B * done
+    s.close()

@@ -35,3 +35,14 @@ def test_aggregate_has_every_column(gpu_ctx):
         mean, std = out[key]
         assert np.isfinite(mean) and std >= 0
     assert 0.5 < out["eta"][0] <= 1.0
+
+
+def test_aggregate_with_the_convergence_rule(gpu_ctx):
+    """Table 1's iterations column: with the Sec. IV-B rule each DS run stops
+    by itself; the mean stopping step lies inside the run and the run ends at
+    or after it (the rule is checked every 48 steps)."""
+    out = experiments.table1(gpu_ctx, "gaussian", trials=3, restarts=1, steps=600, converge=True)
+    it_mean, _ = out["iters"]
+    run_mean, _ = out["steps_run_ds"]
+    assert 5 <= it_mean < 600
+    assert it_mean <= run_mean <= 600
