@@ -346,110 +346,188 @@ def exact_best(ctx, dinst, integer, s):
     return float(api.energy(ctx, dinst, sp[cand].contiguous()).min().item())
 
 
-def precision_runs(ctx, dinst, integer, n, B, T, seed, forms, chunk):
-    """Each operand form runs the same instance and seed for T steps in
-    chunks of `chunk` steps; after each chunk the exact best so far is taken
-    (exact_best). Per form: spin-updates/s from the device time of the steps,
-    the final exact best, and the wall time (steps + checks) of each check.
-    Time to target (Sec. IV-C's time-to-solution idea, target E* = the plain
-    FP32 form's final best on the same instance and seed): the first check
-    at which a form's best <= E*."""
+def run_checked(ctx, dinst, integer, B, T, seed, prec, chunk, target=None, t0_ms=0.0):
+    """One session of T steps in chunks of `chunk` steps, the exact best so
+    far taken after each chunk; stops early once it is <= target. Returns
+    [(wall ms of steps + checks, cumulative from t0_ms, best)], the result."""
     import torch
     from paper_2312_05837_gb300 import api
+    s = api.Session(ctx, dinst, restarts=B, steps=T, seed=seed, precision=prec)
+    torch.cuda.synchronize()
+    done, ms, h = 0, t0_ms, []
+    while done < T:
+        k = min(chunk, T - done)
+        w0 = time.perf_counter()
+        s.run(k)
+        done += k
+        best = exact_best(ctx, dinst, integer, s)
+        ms += 1e3 * (time.perf_counter() - w0)
+        h.append((ms, best))
+        if target is not None and best <= target:
+            break
+    s.finish()
+    res = s.result()
+    s.close()
+    return h, res
+
+
+def precision_runs(ctx, dinst, integer, n, B, T, seed, forms, chunk):
+    """Each operand form runs the same instance and seed for T steps (chunks
+    of `chunk` steps, the exact best after each): spin-updates/s from the
+    device time of the steps, the final exact best, its gap to the plain
+    FP32 form's, and the plain form's history (its time to its own final
+    best is the time-to-target reference)."""
     out, hist = {}, {}
     # first uses of a kernel (ours and torch's reductions) load it
     for prec in forms:
-        s = api.Session(ctx, dinst, restarts=B, steps=2, seed=seed, precision=prec)
-        s.run(2)
-        exact_best(ctx, dinst, integer, s)
-        s.close()
+        run_checked(ctx, dinst, integer, B, 2, seed, prec, 2)
     for prec in forms:
-        s = api.Session(ctx, dinst, restarts=B, steps=T, seed=seed, precision=prec)
-        torch.cuda.synchronize()
-        done, ms, h = 0, 0.0, []
-        while done < T:
-            k = min(chunk, T - done)
-            w0 = time.perf_counter()
-            s.run(k)
-            done += k
-            best = exact_best(ctx, dinst, integer, s)
-            ms += 1e3 * (time.perf_counter() - w0)
-            h.append((ms, best))
-        s.finish()
-        res = s.result()
-        s.close()
+        h, res = run_checked(ctx, dinst, integer, B, T, seed, prec, chunk)
         hist[prec] = h
         out[prec] = {"value": n * B * T / (res["device_ms"] / 1e3), "device_ms": res["device_ms"],
                      "best_energy": res["best_energy"], "operand_planes": res["operand_planes"]}
-    target = out["fp32"]["best_energy"]
+    ref = out["fp32"]["best_energy"]
     for prec in forms:
-        out[prec]["gap_vs_fp32"] = (out[prec]["best_energy"] - target) / abs(target)
-        out[prec]["time_to_target_ms"] = next((ms for ms, e in hist[prec] if e <= target), None)
-    tp = out["fp32"]["time_to_target_ms"]
-    for prec in forms:
-        tf = out[prec]["time_to_target_ms"]
-        out[prec]["speedup_vs_fp32"] = (tp / tf) if (tp and tf) else None
-    return {"target_energy": target, "seed": seed, "chunk_steps": chunk, "forms": out,
-            "timing": "wall time of the steps and of the exact check after each chunk "
-                      "(integer couplings: tracked energies are exact; otherwise FP64 "
-                      "re-evaluation of the near-best restarts on the device)"}
+        out[prec]["gap_vs_fp32"] = (out[prec]["best_energy"] - ref) / abs(ref)
+    return out, hist["fp32"]
+
+
+def time_to_target(ctx, dinst, integer, B, T, seed, plain_hist, fast_forms, chunk, budget_s=20.0):
+    """Time to the plain FP32 form's final best E* (wall time of steps and
+    exact checks). The plain form's time is when its own run (seed `seed`)
+    first reached E*. Each fast form runs the same configuration (B
+    restarts, T steps) in batches: the first with the plain run's seed, then
+    fresh seeds, each stopped as soon as its best reaches E*, until E* is
+    reached or `budget_s` seconds have gone by. With integer couplings the
+    exact fast form computes the plain form's arithmetic, so its first batch
+    follows the same trajectory."""
+    target = plain_hist[-1][1]
+    t_plain = next(ms for ms, e in plain_hist if e <= target)
+    out = {"target_energy": target, "plain_fp32_ms": t_plain,
+           "plain_fp32_full_run_ms": plain_hist[-1][0], "restarts": B, "steps": T,
+           "chunk_steps": chunk, "budget_s": budget_s, "forms": {}}
+    for prec in fast_forms:
+        ms, batches, hit = 0.0, 0, None
+        while ms < 1e3 * budget_s:
+            h, _ = run_checked(ctx, dinst, integer, B, T, seed if batches == 0 else 1000 + batches,
+                               prec, chunk, target=target, t0_ms=ms)
+            batches += 1
+            ms = h[-1][0]
+            if h[-1][1] <= target:
+                hit = ms
+                break
+        out["forms"][prec] = {"time_ms": hit, "batches": batches,
+                              "speedup": (t_plain / hit) if hit else None}
+    out["timing"] = ("wall time of the steps and of the exact check after each chunk (integer "
+                     "couplings: tracked energies are exact; otherwise FP64 re-evaluation of the "
+                     "near-best restarts on the device)")
+    return out
 
 
 # ----------------------------------------------------------------- serving
 
-def serving(ctx, count=40, rate=200.0, n_max=2048, B=256, T=2000, seed=5):
-    """A Poisson stream of mixed requests (half dense Gaussian SK, half sparse
-    ER, N log-uniform in [64, n_max]) through the request server, against the
-    plain per-request FP32 form processing the same stream one request at a
-    time in arrival order. Latency = done - arrival."""
-    import numpy as np
-    import synth
+def serve_stream(ctx, reqs, B, T, precision_dense, pack, max_active, budget, chunk=250):
+    """Submits the requests at their arrival times to a server and waits for
+    all; returns per-request results (latency = done - submit)."""
     from paper_2312_05837_gb300 import api
-    reqs = synth.serving_stream(count, seed, rate=rate, n_max=n_max)
-    # first launches of a kernel load it: warm both forms up on a dense and a
-    # sparse request of the stream, outside the timing
-    kinds = {}
-    for _, inst in reqs:
-        kinds.setdefault(inst.layout, inst)
-    warm = api.Server(ctx, budget_bytes=120 << 30, max_active=2, chunk_steps=250)
-    for inst in kinds.values():
-        warm.wait(warm.submit(inst, restarts=B, steps=2, seed=0), timeout=600)
-        api.solve(ctx, inst, restarts=B, steps=2, seed=0, precision="fp32")
-    warm.close()
-    srv = api.Server(ctx, budget_bytes=120 << 30, max_active=8, chunk_steps=250)
+    srv = api.Server(ctx, budget_bytes=budget, max_active=max_active, chunk_steps=chunk, pack=pack)
     t0 = time.perf_counter()
     ids = []
     for k, (ta, inst) in enumerate(reqs):
         wait = t0 + ta - time.perf_counter()
         if wait > 0:
             time.sleep(wait)
-        ids.append(srv.submit(inst, restarts=B, steps=T, seed=k))
-    res = [srv.wait(r, timeout=1200) for r in ids]
+        prec = precision_dense if inst.layout == "dense" else "auto"
+        ids.append(srv.submit(inst, restarts=B, steps=T, seed=k, precision=prec))
+    res = [srv.wait(r, timeout=3600) for r in ids]
     srv.close()
+    return res
+
+
+def latency_summary(res, rate):
+    import numpy as np
     lat = np.array([r["t_done_ms"] - r["t_submit_ms"] for r in res])
+    adm = np.array([r["t_admit_ms"] - r["t_submit_ms"] for r in res])
     span = (max(r["t_done_ms"] for r in res) - min(r["t_submit_ms"] for r in res)) / 1e3
-    # plain per-request FP32: measured service time of each request alone,
-    # served first come first served from the same arrival times
-    service = []
-    for k, (ta, inst) in enumerate(reqs):
-        w0 = time.perf_counter()
-        api.solve(ctx, inst, restarts=B, steps=T, seed=k, precision="fp32")
-        service.append(time.perf_counter() - w0)
-    done = 0.0
-    lat_p = []
-    for (ta, _), sv in zip(reqs, service):
-        start = max(ta, done)
-        done = start + sv
-        lat_p.append(1e3 * (done - ta))
-    lat_p = np.array(lat_p)
-    return {"requests": count, "rate_per_s": rate, "n_range": [64, n_max], "restarts": B,
-            "steps": T, "mix": "50% dense SK J~N(0,1/N) h~N(0,0.1), 50% sparse ER deg 8 +-1",
-            "served": {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                       "instances_per_s": count / span, "max_active": 8, "chunk_steps": 250},
-            "plain_fp32_per_request": {"p50_ms": float(np.percentile(lat_p, 50)),
-                                       "p99_ms": float(np.percentile(lat_p, 99)),
-                                       "instances_per_s": count / (done - reqs[0][0])},
+    thr = len(res) / span
+    return {"requests": len(res), "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
+            "admission_wait_p50_ms": float(np.percentile(adm, 50)),
+            "admission_wait_p99_ms": float(np.percentile(adm, 99)),
+            "instances_per_s": thr, "offered_per_s": rate,
+            "sustains_offered_load": bool(thr >= 0.95 * rate),
             "all_ok": all(r["status"] == 0 for r in res)}
+
+
+def serving(ctx, count=1000, rate=200.0, n_max=8192, B=256, T=2000, seed=5, plain_count=200):
+    """The serving stream (Poisson arrivals at `rate`, N log-uniform in
+    [64, n_max] over pooled instances, half dense SK J ~ N(0, 1/N) with
+    h ~ N(0, 0.1), half sparse ER degree 8 +-1; B restarts x T steps each,
+    120 GB admission budget) through the server in its served form: dense
+    requests in row-scaled E4M3 (mixed precision: FP32 accumulate, the
+    result's energy re-evaluated in FP64), packed launches, 32 requests
+    admitted at once. Baseline: the plain per-request FP32 form served live,
+    one request at a time in arrival order (the CUDA-core SGEMM for dense
+    requests), on the first `plain_count` requests of the same stream; the
+    served form's figures on those same requests come from its full run."""
+    import synth
+    from paper_2312_05837_gb300 import api
+    reqs = synth.serving_stream_pooled(count, seed, rate=rate, n_max=n_max)
+    budget = 120 << 30
+    # first launches of a kernel load it: warm both forms on small requests
+    small = [(0.0, inst) for _, inst in sorted(reqs, key=lambda r: r[1].n)[:4]]
+    serve_stream(ctx, small, B, 4, "fp8", True, 4, budget)
+    serve_stream(ctx, small, B, 4, "fp32", False, 1, budget)
+    served = serve_stream(ctx, reqs, B, T, "fp8", True, 32, budget)
+    plain = serve_stream(ctx, reqs[:plain_count], B, T, "fp32", False, 1, budget)
+    out = {"requests": count, "rate_per_s": rate, "n_range": [64, n_max], "restarts": B,
+           "steps": T, "budget_gb": 120,
+           "mix": "50% dense SK J~N(0,1/N) h~N(0,0.1), 50% sparse ER deg 8 +-1 (24 pooled sizes "
+                  "per kind, N drawn log-uniformly, nearest pooled size)",
+           "served": {**latency_summary(served, rate), "form": "packed launches, dense in "
+                      "row-scaled E4M3 + FP64 final energy, max_active 32, chunk 250"},
+           "served_first_%d" % plain_count: latency_summary(served[:plain_count], rate),
+           "plain_fp32_per_request_live": {**latency_summary(plain, rate),
+                                           "form": "one request at a time, dense on the "
+                                                   "CUDA-core FP32 SGEMM"}}
+    import numpy as np
+    # the served answers against the plain ones on the same requests (energies
+    # of the full instances, exact)
+    gaps = [(a["best_energy"] - b["best_energy"]) / abs(b["best_energy"])
+            for a, b in zip(served[:plain_count], plain) if b["best_energy"] != 0]
+    out["served_vs_plain_energy_gap"] = {"mean": float(np.mean(gaps)), "max": float(np.max(gaps))}
+    return out
+
+
+# ----------------------------------------------------------------- early retirement
+
+def early_retirement(ctx, B=1024, T=1000, families=("uniform", "gaussian", "binary")):
+    """The Sec. IV-B convergence rule on one 1000-spin 6-regular instance of
+    each Table 1 family, B restarts, at most T steps: the restart-steps the
+    kernels computed (tiles whose restarts have all stopped are skipped) and
+    the device time, against the same run without the rule."""
+    import synth
+    from paper_2312_05837_gb300 import api
+    out = {}
+    for fam in families:
+        inst = synth.table1_instance(fam, 0)
+        row = {}
+        for conv in (False, True):
+            s = api.Session(ctx, inst, restarts=B, steps=T, seed=1, converge=conv)
+            s.run(T)
+            r = s.result()
+            row["converge" if conv else "fixed"] = {
+                "steps_run": r["steps_done"], "restart_steps": s.work(), "device_ms": r["device_ms"],
+                "best_energy": r["best_energy"]}
+            if conv:
+                c = s.convergence()
+                row["stopped_fraction"] = float((c > 0).mean())
+            s.close()
+        row["work_saved"] = 1.0 - row["converge"]["restart_steps"] / (B * T)
+        row["time_saved"] = 1.0 - row["converge"]["device_ms"] / row["fixed"]["device_ms"]
+        out[fam] = row
+    out["config"] = {"restarts": B, "max_steps": T, "lr": 6.0, "n": 1000}
+    return out
 
 
 # ----------------------------------------------------------------- roofline
@@ -669,11 +747,27 @@ def main():
     if rank == 0 and not a.no_extras:
         forms = ["fp32", "tc", "bf16", "fp8"] if not inst.integer else ["fp32", "auto"]
         dinst = device_instance(inst, torch)
-        line["precision_and_time_to_target"] = precision_runs(
-            ctx, dinst, bool(inst.integer), inst.n, B, T, seed=3, forms=forms,
-            chunk=100 if T >= 4000 else 50)
+        chunk = 100 if T >= 4000 else 50
+        sweep, plain_hist = precision_runs(ctx, dinst, bool(inst.integer), inst.n, B, T, seed=3,
+                                           forms=forms, chunk=chunk)
+        line["precision_sweep"] = sweep
+        line["time_to_target"] = {name: time_to_target(
+            ctx, dinst, bool(inst.integer), B, T, 3, plain_hist,
+            ["fp8", "tc"] if not inst.integer else ["auto"], chunk)}
         del dinst
         torch.cuda.empty_cache()
+        if name != "er2000":
+            # the integer max-cut workload: exact E4M3 against plain FP32
+            w_name, wB, wT = WORKLOADS["er2000"]
+            winst = synth.workload(w_name, 0)
+            wd = device_instance(winst, torch)
+            _, w_hist = precision_runs(ctx, wd, True, winst.n, wB, wT, seed=3, forms=["fp32"],
+                                       chunk=50)
+            line["time_to_target"]["er2000"] = time_to_target(ctx, wd, True, wB, wT, 3, w_hist,
+                                                              ["auto"], 50)
+            del wd
+            torch.cuda.empty_cache()
+        line["early_retirement"] = early_retirement(ctx)
         line["serving"] = serving(ctx)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(a, B, T)

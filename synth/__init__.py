@@ -25,4 +25,5 @@ from .instances import (  # noqa: F401
     random_sparse_instance,
     workload,
     serving_stream,
+    serving_stream_pooled,
 )

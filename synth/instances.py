@@ -430,3 +430,35 @@ def serving_stream(count: int, seed: int, rate: float = 200.0, n_min: int = 64,
                             j_scale=1.0, convention="physics", name=f"req{k}-er{n}")
         out.append((t, inst))
     return out
+
+
+def serving_stream_pooled(count: int, seed: int, rate: float = 200.0, n_min: int = 64,
+                          n_max: int = 8192, dense_fraction: float = 0.5,
+                          sparse_degree: float = 8.0, pool: int = 24):
+    """The serving stream of serving_stream at a scale whose instances do not
+    all fit host memory: `pool` dense SK and `pool` sparse ER instances at
+    log-spaced sizes in [n_min, n_max] are generated once, and each request
+    (Poisson arrivals at `rate`, N drawn log-uniformly, dense with
+    probability `dense_fraction`) takes the pooled instance of the nearest
+    size on the log scale. Returns a list of (arrival time in seconds,
+    Instance); requests share Instance objects."""
+    sizes = np.unique(np.round(np.exp(np.linspace(math.log(n_min), math.log(n_max), pool))).astype(int))
+    dense = [sk_dense(int(n), seed * 100003 + 7 * k, math.sqrt(1.0 / n), np.float32,
+                      h_std=math.sqrt(0.1), name=f"pool-sk{n}") for k, n in enumerate(sizes)]
+    sparse = []
+    for k, n in enumerate(sizes):
+        e = er_graph_edges(int(n), seed * 100003 + 7 * k + 1, mean_degree=min(sparse_degree, n - 1))
+        w = _pm1(_rng(seed * 100003 + 7 * k + 1, 11), e.shape[0])
+        indptr, indices, data = csr_from_edges(int(n), e, w)
+        sparse.append(Instance(n=int(n), layout="csr", indptr=indptr, indices=indices, data=data,
+                               j_scale=1.0, convention="physics", name=f"pool-er{n}"))
+    logs = np.log(sizes)
+    rng = _rng(seed, 12)
+    t = 0.0
+    out = []
+    for _ in range(count):
+        t += float(rng.exponential(1.0 / rate))
+        x = rng.uniform(math.log(n_min), math.log(n_max))
+        k = int(np.argmin(np.abs(logs - x)))
+        out.append((t, dense[k] if rng.random() < dense_fraction else sparse[k]))
+    return out
