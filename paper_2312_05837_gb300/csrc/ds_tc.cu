@@ -476,9 +476,9 @@ __device__ __forceinline__ void step_tiles(const Src& src) {
       uint16_t* __restrict__ Sout = static_cast<uint16_t*>(T.Snext);
       const uint8_t* __restrict__ Sin8 = static_cast<const uint8_t*>(T.S);
       uint8_t* __restrict__ Sout8 = static_cast<uint8_t*>(T.Snext);
-      const int buf = it & 1;
-      const uint32_t use = (uint32_t)(it >> 1);
-      ++it;
+      const int my_it = it++;
+      const int buf = my_it & 1;
+      const uint32_t use = (uint32_t)(my_it >> 1);
       const int mt = T.mt;
       const int64_t m0 = T.m0;
       const int64_t n0 = (int64_t)T.n0 + part * kCols;
@@ -490,7 +490,7 @@ __device__ __forceinline__ void step_tiles(const Src& src) {
         break;
       }
       tc::fence_after_sync();
-      if (it == 0 && warp == 4 && lane == 0) ISING_TRACE(5);
+      if (my_it == 0 && warp == 4 && lane == 0) ISING_TRACE(5);
       const int64_t i = m0 + 32 * q + lane;
       const bool row_ok = i < P.n;
       const float h = row_ok ? P.hf[i] : 0.f;
