@@ -514,13 +514,17 @@ __device__ __forceinline__ void step_tiles(const Src& src) {
           vv[j] = 0.f;
           sv[j] = 0.f;
           if (ok && MODE != kModeCoupling) {
-            sv[j] = FP8 ? (Sin8[idx] == 0x38 ? 1.f : -1.f) : ((Sin[idx] & 0x8000u) ? -1.f : 1.f);
             if (MODE == kModeUpdate || MODE == kModeRelaxed) {
               // the state is read and written once per step: streaming
-              // accesses (evict first) leave L2 to the operand tiles
+              // accesses (evict first) leave L2 to the operand tiles. The
+              // spins S_t the step consumes are sgn+(sin theta_{t-1}), as
+              // every writer of a spin slot makes them (previous update,
+              // initial draw, imported state): taken from theta, not loaded
               th[j] = __ldcs(theta + idx);
               mm[j] = __ldcs(mvec + idx);
               vv[j] = __ldcs(vvec + idx);
+            } else {
+              sv[j] = FP8 ? (Sin8[idx] == 0x38 ? 1.f : -1.f) : ((Sin[idx] & 0x8000u) ? -1.f : 1.f);
             }
           }
         }
@@ -546,7 +550,8 @@ __device__ __forceinline__ void step_tiles(const Src& src) {
             P.Gout[idx] = G;
             continue;
           }
-          const float sj = sv[j];
+          const float sj = (MODE == kModeUpdate || MODE == kModeRelaxed)
+                               ? (sin_nonneg(th[j]) ? 1.f : -1.f) : sv[j];
           if (INT_E) {
             eq[j] = (int)sj * __float2int_rn(G);
             eh[j] = (int)sj * hi;
