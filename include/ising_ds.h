@@ -375,6 +375,14 @@ int ising_ds_last_energies(ising_ds* ds, double* E, int mem);
  * where it stopped), so it falls below B x steps. The resident tensor-core
  * forms keep every restart running. Synchronises the session's stream. */
 int ising_ds_work(ising_ds* ds, int64_t* restart_steps);
+/* Launch shape of the tensor-core streaming form set by hand: 64, 128, 224
+ * or 256 restarts per tile; pair = 1 runs the tiles over clusters of two
+ * CTAs that share each spin tile (each loads half and multicasts it to
+ * both; widths 224 and 256, more than 128 spins). The autotuner leaves the
+ * session alone afterwards. Results do not depend on the shape. ISING_ENOTSUP
+ * on other forms, ISING_EINVAL for a shape the session cannot take. No
+ * counterpart in the paper: a tuning control. */
+int ising_ds_set_tiles(ising_ds* ds, int32_t restarts_per_tile, int32_t pair);
 /* With ISING_DS_CONVERGE: the step at which each restart stopped (0 while it
  * runs), [B] int64 in memory `mem`. Without the flag all zeros. */
 int ising_ds_convergence(ising_ds* ds, int64_t* step, int mem);

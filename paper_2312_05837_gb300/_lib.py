@@ -99,6 +99,7 @@ _PROTOS = {
     "ising_ds_restart_best": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int]),
     "ising_ds_convergence": (c_int, [c_void_p, c_void_p, c_int]),
     "ising_ds_work": (c_int, [c_void_p, POINTER(c_int64)]),
+    "ising_ds_set_tiles": (c_int, [c_void_p, c_int32, c_int32]),
     "ising_selftest_waits": (c_int, [c_void_p, c_int64, c_void_p]),
     "ising_ds_result": (c_int, [c_void_p, c_void_p, POINTER(c_double), POINTER(DSStats), c_int]),
     "ising_ds_destroy": (c_int, [c_void_p]),

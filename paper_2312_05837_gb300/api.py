@@ -504,6 +504,12 @@ class Session:
         self.ctx.check(self.ctx.lib.ising_ds_last_energies(self.handle, _ptr(E), L.MEM_HOST))
         return E
 
+    def set_tiles(self, restarts_per_tile: int, pair: bool = False):
+        """Tensor-core streaming form: tile width and whether two CTAs share
+        each spin tile (see ising_ds_set_tiles)."""
+        self.ctx.check(self.ctx.lib.ising_ds_set_tiles(self.handle, int(restarts_per_tile),
+                                                       1 if pair else 0))
+
     def work(self) -> int:
         """Restart-steps the update launches computed (below B x steps when
         the convergence rule retires restarts)."""

@@ -958,7 +958,7 @@ std::string dense_key(const ising_ds* ds) {
 int autotune_dense(ising_ds* ds, int64_t budget, int64_t* done) {
   *done = 0;
   ds->tuned = true;
-  int cand[4];
+  int cand[6];
   const int nc = tc_bn_candidates(ds, cand);
   if ((ds->p.flags & ISING_DS_NO_AUTOTUNE) || nc <= 1) return ISING_OK;
   const std::string key = dense_key(ds);
@@ -970,7 +970,7 @@ int autotune_dense(ising_ds* ds, int64_t budget, int64_t* done) {
   }
   if (budget < 1 + 2 * nc) return ISING_OK;
   ising_ctx* ctx = ds->ctx;
-  cudaEvent_t ev[9];
+  cudaEvent_t ev[13];
   for (int k = 0; k <= 2 * nc; ++k) ISING_CUDA(ctx, cudaEventCreate(&ev[k]));
   int rc = ISING_OK;
   for (int k = 0; k <= 2 * nc && rc == ISING_OK; ++k) {
@@ -1254,6 +1254,24 @@ extern "C" int ising_ds_last_energies(ising_ds* ds, double* E, int mem) {
   if (!E) return fail(ds->ctx, ISING_EINVAL, "E is NULL");
   ISING_TRY(copy_out(ds->ctx, E, ds->last_E.p, ds->B * 8, mem));
   ISING_CUDA(ds->ctx, cudaStreamSynchronize(ds->ctx->stream));
+  return ISING_OK;
+}
+
+extern "C" int ising_ds_set_tiles(ising_ds* ds, int32_t restarts_per_tile, int32_t pair) {
+  if (!ds) return ISING_EINVAL;
+  ising_ctx* ctx = ds->ctx;
+  if (ds->path != ISING_PATH_TC || tc_is_resident(ds))
+    return fail(ctx, ISING_ENOTSUP, "tile shapes apply to the tensor-core streaming form");
+  const int code = restarts_per_tile | (pair ? kTcPair : 0);
+  int cand[6];
+  const int nc = tc_bn_candidates(ds, cand);
+  bool ok = restarts_per_tile == 64 || restarts_per_tile == 128 || restarts_per_tile == 224 ||
+            restarts_per_tile == 256;
+  if (pair) ok = ok && std::find(cand, cand + nc, code) != cand + nc;
+  if (!ok) return fail(ctx, ISING_EINVAL, "tile shape %d%s is not available for this session",
+                       restarts_per_tile, pair ? " in pairs" : "");
+  ISING_TRY(tc_set_bn(ds, code));
+  ds->tuned = true;
   return ISING_OK;
 }
 

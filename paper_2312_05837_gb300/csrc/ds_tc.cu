@@ -193,8 +193,11 @@ struct TileRef {
 template <int BN>
 struct OneInstance {
   static constexpr bool kGlobalMaps = false;  // kernel parameters
+  static constexpr bool kPair = false;
   const TcArgs& P;  // the kernel's parameter
   const CUtensorMap *A0, *A1, *A2, *B, *J0, *J1, *J2, *S2;
+  __device__ int first() const { return blockIdx.x; }
+  __device__ int stride() const { return gridDim.x; }
   __device__ int total() const { return P.mtiles * P.ntiles; }
   __device__ int* err() const { return P.err; }
   __device__ unsigned long long* trace() const { return P.trace; }
@@ -240,6 +243,9 @@ struct __align__(64) PackEntry {
 template <int BN>
 struct PackedInstances {
   static constexpr bool kGlobalMaps = true;  // copied to device memory by the host
+  static constexpr bool kPair = false;
+  __device__ int first() const { return blockIdx.x; }
+  __device__ int stride() const { return gridDim.x; }
   const PackEntry* E;
   const int* start;
   int count;
@@ -277,6 +283,46 @@ struct PackedInstances {
   }
 };
 
+// Tiles of one instance for clusters of two CTAs: a cluster takes pair tile
+// (pm, nt), its CTA of rank r the row tile 2 pm + r of restart tile nt. Both
+// CTAs need the same spin tile: each loads one half of it and multicasts the
+// half to both (the J tiles are their own), so a CTA reads 30 instead of 44
+// KB per stage from L2 at tiles of 224 restarts. With an odd number of row
+// tiles the last pair's second tile lies past n (zero rows, nothing written).
+template <int BN>
+struct PairInstance {
+  static constexpr bool kGlobalMaps = false;
+  static constexpr bool kPair = true;
+  const TcArgs& P;
+  const CUtensorMap *A0, *A1, *A2, *B, *J0, *J1, *J2, *S2;
+  const CUtensorMap* Bh;  // S_t, boxes of one k-block x BN / 2 restarts
+  uint32_t rank;
+  __device__ int first() const { return (int)tc::cluster_index(); }
+  __device__ int stride() const { return (int)tc::cluster_count(); }
+  __device__ int total() const { return (P.mtiles + 1) / 2 * P.ntiles; }
+  __device__ int* err() const { return P.err; }
+  __device__ unsigned long long* trace() const { return P.trace; }
+  __device__ const TcArgs& args(const TileRef&) const { return P; }
+  __device__ TileRef tile(int tl) const {
+    TileRef r;
+    r.P = &P;
+    r.A0 = A0; r.A1 = A1; r.A2 = A2;
+    r.J0 = J0; r.J1 = J1; r.J2 = J2;
+    r.B = Bh;
+    r.S2 = S2;
+    r.S = P.S;
+    r.Snext = P.Snext;
+    r.qpart = P.qpart;
+    r.hpart = P.hpart;
+    r.epart = P.epart;
+    r.mt = 2 * (tl / P.ntiles) + (int)rank;
+    r.m0 = r.mt * kBM;
+    r.n0 = (tl % P.ntiles) * BN;
+    r.skip = restarts_retired(P.live32, r.n0, min((int64_t)r.n0 + BN, P.B));
+    return r;
+  }
+};
+
 #define ISING_TRACE(slot)                                                            \
   do {                                                                               \
     if (trace_) trace_[(size_t)blockIdx.x * 8 + (slot)] = now_ns();                  \
@@ -289,6 +335,7 @@ __device__ __forceinline__ void step_tiles(const Src& src) {
   using Lay = TcLayout<BN>;
   constexpr int STAGES = Lay::kStages;
   constexpr int kBK = FP8 ? 128 : 64;  // elements per 128-byte row
+  static_assert(!Src::kPair || Lay::kKps == 1, "pair tiles take one k-block per stage");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -305,7 +352,7 @@ __device__ __forceinline__ void step_tiles(const Src& src) {
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       tc::mbar_init(&full[s], 2);  // the J and the S producer
-      tc::mbar_init(&empty[s], 1);
+      tc::mbar_init(&empty[s], Src::kPair ? 2 : 1);  // the MMA issuer of each CTA of the pair
     }
     for (int b = 0; b < 2; ++b) {
       tc::mbar_init(&acc_full[b], 1);
@@ -320,6 +367,8 @@ __device__ __forceinline__ void step_tiles(const Src& src) {
     tc::fence_before_sync();
   }
   __syncthreads();
+  // pairs: the partner's barriers are initialised before copies or commits target them
+  if (Src::kPair) tc::cluster_sync();
   tc::fence_after_sync();
   if (threadIdx.x == 0) ISING_TRACE(0);
   const uint32_t tmem_base = *tmem_slot;
@@ -338,7 +387,7 @@ __device__ __forceinline__ void step_tiles(const Src& src) {
       uint32_t stage = 0, phase = 0;
       int issued = 0;
       bool ok = true;
-      for (int tl = blockIdx.x; tl < total && ok; tl += gridDim.x) {
+      for (int tl = src.first(); tl < total && ok; tl += src.stride()) {
         const TileRef T = src.tile(tl);
         if (T.skip) continue;
         const TcArgs& P = src.args(T);
@@ -374,11 +423,16 @@ __device__ __forceinline__ void step_tiles(const Src& src) {
             for (int u = 0; u < cnt; ++u) {
               const int kt = kt0 + u;
               const int plane = kt / nk, kb = kt - plane * nk;
-              if (jside)
+              if (jside) {
                 tc::tma_load_2d_hint(sa + u * Lay::kA, T.a(plane), &full[stage], kb * kBK, T.m0, pol);
-              else
+              } else if constexpr (Src::kPair) {
+                // this CTA's half of the spin tile, to both CTAs of the pair
+                tc::tma_load_2d_mc(sa + Lay::kA + src.rank * (BN / 2) * kRowBytes, T.B,
+                                   &full[stage], kb * kBK, T.n0 + (int)src.rank * (BN / 2), 0x3, pol);
+              } else {
                 tc::tma_load_2d_hint(sa + Lay::kKps * Lay::kA + u * Lay::kB, T.B, &full[stage],
                                      kb * kBK, T.n0, pol);
+              }
             }
           }
           if (issued == 0 && jside) ISING_TRACE(1);
@@ -387,6 +441,15 @@ __device__ __forceinline__ void step_tiles(const Src& src) {
         }
       }
       if (jside) ISING_TRACE(2);
+      if (Src::kPair && ok && jside) {
+        // pairs: wait until both CTAs' MMA issuers have released every stage,
+        // so that no commit of the partner arrives on this CTA's barriers
+        // after it has left (the cluster barrier at the end follows)
+        for (int q = 0; q < STAGES && ok; ++q) {
+          ok = tc::mbar_wait(&empty[stage], phase ^ 1, abort_flag, kWaitCycles);
+          if (++stage == STAGES) { stage = 0; phase ^= 1; }
+        }
+      }
       if (!ok) {
         // let the copies already issued land before the CTA exits (a phase
         // the other producer never joined gives up after the bounded wait)
@@ -405,7 +468,7 @@ __device__ __forceinline__ void step_tiles(const Src& src) {
       uint32_t stage = 0, phase = 0;
       int it = 0;
       bool ok = true;
-      for (int tl = blockIdx.x; tl < total && ok; tl += gridDim.x) {
+      for (int tl = src.first(); tl < total && ok; tl += src.stride()) {
         const TileRef T = src.tile(tl);
         if (T.skip) continue;
         const TcArgs& P = src.args(T);
@@ -444,7 +507,10 @@ __device__ __forceinline__ void step_tiles(const Src& src) {
                             (kt > 0 || k > 0) ? 1u : 0u);
             }
           }
-          tc::mma_commit(&empty[stage]);
+          // the stage is free once this CTA's MMAs (and, for pairs, the
+          // partner's, whose spin half it also holds) have read it
+          if constexpr (Src::kPair) tc::mma_commit_mc(&empty[stage], 0x3);
+          else tc::mma_commit(&empty[stage]);
           if (++stage == STAGES) { stage = 0; phase ^= 1; }
         }
         if (ok) tc::mma_commit(&acc_full[buf]);
@@ -463,7 +529,7 @@ __device__ __forceinline__ void step_tiles(const Src& src) {
     const int part = (warp - 4) >> 2;   // which quarter of the tile's columns
     constexpr int kCols = BN / 4;
     int it = 0;
-    for (int tl = blockIdx.x; tl < total; tl += gridDim.x) {
+    for (int tl = src.first(); tl < total; tl += src.stride()) {
       const TileRef T = src.tile(tl);
       if (T.skip) continue;
       const TcArgs& P = src.args(T);
@@ -580,7 +646,7 @@ __device__ __forceinline__ void step_tiles(const Src& src) {
               static_cast<uint16_t*>(P.Xnext)[idx] = to_op16(sin_proj(th[j]), P.f16);
           }
         }
-        if (MODE == kModeUpdate || MODE == kModeEnergy) {
+        if ((MODE == kModeUpdate || MODE == kModeEnergy) && mt < P.mtiles) {
           // this warp's 32 spins summed per restart; partial row 4 mt + q
           const int64_t b = n0 + c0 + column_of_lane(lane);
           const int64_t o = ((int64_t)mt * 4 + q) * P.B + b;
@@ -602,6 +668,9 @@ __device__ __forceinline__ void step_tiles(const Src& src) {
   if (warp == 4 && lane == 0) ISING_TRACE(6);
   __syncwarp();
   __syncthreads();
+  // pairs: neither CTA leaves while the other may still copy into its shared
+  // memory or arrive on its barriers
+  if (Src::kPair) tc::cluster_sync();
   if (threadIdx.x == 0) ISING_TRACE(7);
   if (warp == 1) {
     tc::fence_after_sync();
@@ -621,6 +690,22 @@ __global__ void __launch_bounds__(kThreads, 1)
                    const __grid_constant__ CUtensorMap tmJ2_2,
                    const __grid_constant__ CUtensorMap tmS2, const __grid_constant__ TcArgs P) {
   const OneInstance<BN> src{P, &tmA0, &tmA1, &tmA2, &tmB, &tmJ2_0, &tmJ2_1, &tmJ2_2, &tmS2};
+  step_tiles<BN, MODE, INT_E, FP8>(src);
+}
+
+// The same over clusters of two CTAs sharing each spin tile (PairInstance).
+template <int BN, int MODE, bool INT_E, bool FP8>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
+    tc_step_pair_kernel(const __grid_constant__ CUtensorMap tmA0,
+                        const __grid_constant__ CUtensorMap tmA1,
+                        const __grid_constant__ CUtensorMap tmA2,
+                        const __grid_constant__ CUtensorMap tmBh,
+                        const __grid_constant__ CUtensorMap tmJ2_0,
+                        const __grid_constant__ CUtensorMap tmJ2_1,
+                        const __grid_constant__ CUtensorMap tmJ2_2,
+                        const __grid_constant__ CUtensorMap tmS2, const __grid_constant__ TcArgs P) {
+  const PairInstance<BN> src{P,      &tmA0,   &tmA1,   &tmA2, &tmBh, &tmJ2_0,
+                             &tmJ2_1, &tmJ2_2, &tmS2,   &tmBh, tc::cluster_rank()};
   step_tiles<BN, MODE, INT_E, FP8>(src);
 }
 
@@ -1746,6 +1831,8 @@ struct TcState {
   // [k-block][row][128 B] with boxes of two whole k-blocks
   CUtensorMap J2[3], S2[3];
   CUtensorMap SP[3];  // streaming kernel: the spin slots' pair views, boxes of BN restarts
+  CUtensorMap Bh[3];  // pair tiles: the spin slots, boxes of BN / 2 restarts
+  bool pair = false;  // streaming kernel over clusters of two CTAs sharing spin tiles
   int nfull = 0;      // k-blocks lying wholly below column n (0 in the small form)
   CUtensorMap Bx[2];  // relaxed mode: one per slot of x = sin(theta), boxes of BN restarts
   int BN = 128;
@@ -1822,9 +1909,28 @@ int make_map_pairs(ising_ctx* ctx, CUtensorMap* map, const void* base, int64_t n
 
 template <int BN, int MODE, bool INT_E, bool FP8>
 int launch_bn(ising_ds* ds, TcState* st, const TcArgs& a, const CUtensorMap& mB,
-              const CUtensorMap& mS2) {
-  auto kern = tc_step_kernel<BN, MODE, INT_E, FP8>;
+              const CUtensorMap& mS2, const CUtensorMap& mBh) {
   const size_t smem = TcLayout<BN>::kBytes;
+  if constexpr (BN >= 192) {
+    if (st->pair) {
+      auto kern = tc_step_pair_kernel<BN, MODE, INT_E, FP8>;
+      static bool attr_set = false;  // per instantiation
+      if (!attr_set) {
+        ISING_CUDA(ds->ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem));
+        attr_set = true;
+      }
+      // one cluster of two CTAs per pair of SMs, at most one per pair tile
+      const int pairs = (a.mtiles + 1) / 2 * a.ntiles;
+      const int clusters = std::max(1, std::min(pairs, ds->ctx->sm_count / 2));
+      kern<<<2 * clusters, kThreads, smem, ds->ctx->stream>>>(st->A[0], st->A[1], st->A[2], mBh,
+                                                              st->J2[0], st->J2[1], st->J2[2],
+                                                              mS2, a);
+      ISING_CUDA(ds->ctx, cudaGetLastError());
+      return ISING_OK;
+    }
+  }
+  auto kern = tc_step_kernel<BN, MODE, INT_E, FP8>;
   static bool attr_set = false;  // per instantiation
   if (!attr_set) {
     ISING_CUDA(ds->ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1839,28 +1945,29 @@ int launch_bn(ising_ds* ds, TcState* st, const TcArgs& a, const CUtensorMap& mB,
 
 template <int MODE, bool INT_E, bool FP8>
 int launch_bn_sel(ising_ds* ds, TcState* st, const TcArgs& a, const CUtensorMap& mB,
-                  const CUtensorMap& mS2) {
+                  const CUtensorMap& mS2, const CUtensorMap& mBh) {
   switch (st->BN) {
-    case 256: return launch_bn<256, MODE, INT_E, FP8>(ds, st, a, mB, mS2);
-    case 224: return launch_bn<224, MODE, INT_E, FP8>(ds, st, a, mB, mS2);
-    case 64: return launch_bn<64, MODE, INT_E, FP8>(ds, st, a, mB, mS2);
-    default: return launch_bn<128, MODE, INT_E, FP8>(ds, st, a, mB, mS2);
+    case 256: return launch_bn<256, MODE, INT_E, FP8>(ds, st, a, mB, mS2, mBh);
+    case 224: return launch_bn<224, MODE, INT_E, FP8>(ds, st, a, mB, mS2, mBh);
+    case 64: return launch_bn<64, MODE, INT_E, FP8>(ds, st, a, mB, mS2, mBh);
+    default: return launch_bn<128, MODE, INT_E, FP8>(ds, st, a, mB, mS2, mBh);
   }
 }
 
 template <int MODE, bool INT_E>
 int launch_mode(ising_ds* ds, TcState* st, const TcArgs& a, const CUtensorMap& mB,
-                const CUtensorMap& mS2) {
-  return st->fp8 ? launch_bn_sel<MODE, INT_E, true>(ds, st, a, mB, mS2)
-                 : launch_bn_sel<MODE, INT_E, false>(ds, st, a, mB, mS2);
+                const CUtensorMap& mS2, const CUtensorMap& mBh) {
+  return st->fp8 ? launch_bn_sel<MODE, INT_E, true>(ds, st, a, mB, mS2, mBh)
+                 : launch_bn_sel<MODE, INT_E, false>(ds, st, a, mB, mS2, mBh);
 }
 
-// Relaxed-product update: BF16 operands only (x in E4M3 would be too coarse).
+// Relaxed-product update: 16-bit operands only (x in E4M3 would be too
+// coarse); never in pairs (the relaxed spins have no half-box maps).
 template <bool INT_E>
 int launch_relaxed(ising_ds* ds, TcState* st, const TcArgs& a, const CUtensorMap& mB,
                    const CUtensorMap& mS2) {
   if (st->fp8) return fail(ds->ctx, ISING_ENOTSUP, "relaxed product needs BF16 operands");
-  return launch_bn_sel<kModeRelaxed, INT_E, false>(ds, st, a, mB, mS2);
+  return launch_bn_sel<kModeRelaxed, INT_E, false>(ds, st, a, mB, mS2, mB);
 }
 
 }  // namespace
@@ -2111,6 +2218,9 @@ static int tc_maps(ising_ds* ds, TcState* st) {
     if (st->resident)
       ISING_TRY(make_map(ds->ctx, &st->Bg[s], ds->spins[s].p, ds->n, ds->B, ds->ld,
                          st->fp8 ? 128 : 64, st->gn, st->fp8));
+    if (st->pair)
+      ISING_TRY(make_map(ds->ctx, &st->Bh[s], ds->spins[s].p, ds->n, ds->B, ds->ld,
+                         st->fp8 ? 128 : 64, st->BN / 2, st->fp8));
   }
   if (st->nfull >= 2)
     for (int p = 0; p < 3; ++p)
@@ -2168,13 +2278,14 @@ int tc_run(ising_ds* ds, int mode, float* Gout) {
   }
   const CUtensorMap& mS = st->B[t % 3];
   const CUtensorMap& mS2 = st->SP[t % 3];
+  const CUtensorMap& mSh = st->Bh[t % 3];
   a.nfull = st->nfull;
   const bool ie = ds->int_energy;
   switch (mode) {
-    case kModeUpdate: return ie ? launch_mode<kModeUpdate, true>(ds, st, a, mS, mS2)
-                                : launch_mode<kModeUpdate, false>(ds, st, a, mS, mS2);
-    case kModeEnergy: return ie ? launch_mode<kModeEnergy, true>(ds, st, a, mS, mS2)
-                                : launch_mode<kModeEnergy, false>(ds, st, a, mS, mS2);
+    case kModeUpdate: return ie ? launch_mode<kModeUpdate, true>(ds, st, a, mS, mS2, mSh)
+                                : launch_mode<kModeUpdate, false>(ds, st, a, mS, mS2, mSh);
+    case kModeEnergy: return ie ? launch_mode<kModeEnergy, true>(ds, st, a, mS, mS2, mSh)
+                                : launch_mode<kModeEnergy, false>(ds, st, a, mS, mS2, mSh);
     case kModeRelaxed: {
       // the product runs on x_t; the epilogue reads s_t and writes s_{t+1},
       // x_{t+1} (x has no pair view: one copy per k-block)
@@ -2182,7 +2293,7 @@ int tc_run(ising_ds* ds, int mode, float* Gout) {
       a.nfull = 0;
       return ie ? launch_relaxed<true>(ds, st, a, mX, mS2) : launch_relaxed<false>(ds, st, a, mX, mS2);
     }
-    default: return launch_mode<kModeCoupling, true>(ds, st, a, mS, mS2);
+    default: return launch_mode<kModeCoupling, true>(ds, st, a, mS, mS2, mSh);
   }
 }
 
@@ -2363,17 +2474,25 @@ int tc_bn_candidates(const ising_ds* ds, int* out) {
   int k = 0;
   for (int bn : {64, 128, 224, 256})
     if (bn == 64 || bn / 2 < ds->B) out[k++] = bn;
+  // the same wide tiles over clusters of two CTAs sharing spin tiles
+  // (kTcPair: a flag on the width), when there are two row tiles to pair
+  if (!ds->relaxed() && ds->n > kBM)
+    for (int bn : {224, 256})
+      if (bn / 2 < ds->B) out[k++] = bn | kTcPair;
   return k;
 }
 
 // Switches the streaming form to tiles of `bn` restarts (the products, and
 // so the results, do not depend on it); the operand maps are rebuilt on the
 // next launch.
-int tc_set_bn(ising_ds* ds, int bn) {
+int tc_set_bn(ising_ds* ds, int code) {
   auto st = static_cast<TcState*>(ds->tc);
   if (st->resident) return fail(ds->ctx, ISING_EINVAL, "tile width of a resident form");
-  if (st->BN == bn) return ISING_OK;
+  const int bn = code & ~kTcPair;
+  const bool pair = (code & kTcPair) != 0 && bn >= 192 && !ds->relaxed();
+  if (st->BN == bn && st->pair == pair) return ISING_OK;
   st->BN = bn;
+  st->pair = pair;
   st->maps_ready = false;
   st->trace.release();
   const int tiles = ceil_div_i(ds->n, kBM) * ceil_div_i(ds->B, bn);
