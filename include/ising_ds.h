@@ -378,7 +378,9 @@ int ising_ds_work(ising_ds* ds, int64_t* restart_steps);
 /* Launch shape of the tensor-core streaming form set by hand: 64, 128, 224
  * or 256 restarts per tile; pair = 1 runs the tiles over clusters of two
  * CTAs that share each spin tile (each loads half and multicasts it to
- * both; widths 224 and 256, more than 128 spins). The autotuner leaves the
+ * both; widths 224 and 256, more than 128 spins); pair = 2 as well, but
+ * each CTA keeps its half and the pair's MMAs run as one (M 256 over the
+ * two CTAs, cta_group::2). The autotuner leaves the
  * session alone afterwards. Results do not depend on the shape. ISING_ENOTSUP
  * on other forms, ISING_EINVAL for a shape the session cannot take. No
  * counterpart in the paper: a tuning control. */

@@ -504,11 +504,12 @@ class Session:
         self.ctx.check(self.ctx.lib.ising_ds_last_energies(self.handle, _ptr(E), L.MEM_HOST))
         return E
 
-    def set_tiles(self, restarts_per_tile: int, pair: bool = False):
-        """Tensor-core streaming form: tile width and whether two CTAs share
-        each spin tile (see ising_ds_set_tiles)."""
+    def set_tiles(self, restarts_per_tile: int, pair: int = 0):
+        """Tensor-core streaming form: tile width and CTA pairs (0 none, 1
+        sharing spin tiles by multicast, 2 one MMA per pair; see
+        ising_ds_set_tiles)."""
         self.ctx.check(self.ctx.lib.ising_ds_set_tiles(self.handle, int(restarts_per_tile),
-                                                       1 if pair else 0))
+                                                       int(pair)))
 
     def work(self) -> int:
         """Restart-steps the update launches computed (below B x steps when

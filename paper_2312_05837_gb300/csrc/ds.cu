@@ -958,7 +958,7 @@ std::string dense_key(const ising_ds* ds) {
 int autotune_dense(ising_ds* ds, int64_t budget, int64_t* done) {
   *done = 0;
   ds->tuned = true;
-  int cand[6];
+  int cand[8];
   const int nc = tc_bn_candidates(ds, cand);
   if ((ds->p.flags & ISING_DS_NO_AUTOTUNE) || nc <= 1) return ISING_OK;
   const std::string key = dense_key(ds);
@@ -970,7 +970,7 @@ int autotune_dense(ising_ds* ds, int64_t budget, int64_t* done) {
   }
   if (budget < 1 + 2 * nc) return ISING_OK;
   ising_ctx* ctx = ds->ctx;
-  cudaEvent_t ev[13];
+  cudaEvent_t ev[17];
   for (int k = 0; k <= 2 * nc; ++k) ISING_CUDA(ctx, cudaEventCreate(&ev[k]));
   int rc = ISING_OK;
   for (int k = 0; k <= 2 * nc && rc == ISING_OK; ++k) {
@@ -1262,8 +1262,9 @@ extern "C" int ising_ds_set_tiles(ising_ds* ds, int32_t restarts_per_tile, int32
   ising_ctx* ctx = ds->ctx;
   if (ds->path != ISING_PATH_TC || tc_is_resident(ds))
     return fail(ctx, ISING_ENOTSUP, "tile shapes apply to the tensor-core streaming form");
-  const int code = restarts_per_tile | (pair ? kTcPair : 0);
-  int cand[6];
+  if (pair < 0 || pair > 2) return fail(ctx, ISING_EINVAL, "pair must be 0, 1 or 2");
+  const int code = restarts_per_tile | (pair ? kTcPair : 0) | (pair == 2 ? kTcSplit : 0);
+  int cand[8];
   const int nc = tc_bn_candidates(ds, cand);
   bool ok = restarts_per_tile == 64 || restarts_per_tile == 128 || restarts_per_tile == 224 ||
             restarts_per_tile == 256;

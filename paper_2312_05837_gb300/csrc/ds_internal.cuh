@@ -288,8 +288,9 @@ int track_pack(ising_ctx* ctx, int spin_kind, const TrackArgs* members, const in
 bool tc_packable(const ising_ds* ds);
 uint64_t tc_pack_key(const ising_ds* ds);
 int tc_bn(const ising_ds* ds);                        // restart-tile width
-constexpr int kTcPair = 1 << 16;  // flag on a width: clusters of two CTAs share spin tiles
-int tc_bn_candidates(const ising_ds* ds, int* out);   // widths the autotuner may try (<= 6)
+constexpr int kTcPair = 1 << 16;   // flag on a width: clusters of two CTAs share spin tiles
+constexpr int kTcSplit = 1 << 17;  // ... and issue their MMAs as one (with kTcPair)
+int tc_bn_candidates(const ising_ds* ds, int* out);   // widths the autotuner may try (<= 8)
 int tc_set_bn(ising_ds* ds, int code);                // a width, with kTcPair or not
 size_t tc_pack_entry_bytes();
 int tc_pack_entry(ising_ds* ds, void* host_entry);

@@ -97,10 +97,11 @@ __device__ __forceinline__ uint16_t to_op16(float x, int f16) {
   return f16 ? __half_as_ushort(__float2half_rn(x)) : __bfloat16_as_ushort(__float2bfloat16(x));
 }
 
-// Instruction descriptor of a 128 x N tile: kind::f8f6f4 E4M3 (format 0), or
-// kind::f16 with FP16 (format 0) or BF16 (format 1) inputs.
-__device__ __forceinline__ uint32_t op_idesc(int N, bool fp8, int f16) {
-  return tc::idesc_make(128, N, fp8 ? 0u : (f16 ? 0u : 1u));
+// Instruction descriptor of an M x N tile (M 128, or 256 for a CTA pair):
+// kind::f8f6f4 E4M3 (format 0), or kind::f16 with FP16 (format 0) or BF16
+// (format 1) inputs.
+__device__ __forceinline__ uint32_t op_idesc(int N, bool fp8, int f16, int M = 128) {
+  return tc::idesc_make(M, N, fp8 ? 0u : (f16 ? 0u : 1u));
 }
 
 __device__ __forceinline__ unsigned long long now_ns() {
@@ -118,16 +119,21 @@ __device__ __forceinline__ unsigned long long now_ns() {
 // issues one TMA copy per ~250 cycles whatever its size); for BN = 224 and
 // 256 such stages would leave room for two only, so there a stage is one
 // k-block.
-template <int BN>
+template <int BN, bool SPLIT = false>
 struct TcLayout {
   static constexpr int kKps = BN >= 192 ? 1 : 2;
   static constexpr uint32_t kA = kBM * kRowBytes;
-  static constexpr uint32_t kB = BN * kRowBytes;
+  // SPLIT (the MMA of a CTA pair): each CTA holds half of the spin tile
+  static constexpr uint32_t kB = (SPLIT ? BN / 2 : BN) * kRowBytes;
   static constexpr uint32_t kStage = kKps * (kA + kB);
+  // SPLIT: a spin half's worth of room after the last stage, so that every
+  // operand read of a stage stays inside this CTA's shared memory whatever
+  // part of the pair's tile it covers
+  static constexpr uint32_t kTail = SPLIT ? kB : 0;
   // as many stages as the 227 KB of shared memory hold (the ring's depth
   // covers the latency of the operand copies from L2)
-  static constexpr int kStages = (225 * 1024) / kStage;
-  static constexpr uint32_t kBars = kStages * kStage;  // barrier block
+  static constexpr int kStages = (225 * 1024 - kTail) / kStage;
+  static constexpr uint32_t kBars = kStages * kStage + kTail;  // barrier block
   static constexpr uint32_t kBytes = kBars + 256 + 1024;  // + alignment slack
   // two accumulator buffers; allocations are powers of two columns
   static constexpr uint32_t kTmemCols = 2 * BN <= 128 ? 128 : (2 * BN <= 256 ? 256 : 512);
@@ -194,6 +200,7 @@ template <int BN>
 struct OneInstance {
   static constexpr bool kGlobalMaps = false;  // kernel parameters
   static constexpr bool kPair = false;
+  static constexpr bool kSplit = false;
   const TcArgs& P;  // the kernel's parameter
   const CUtensorMap *A0, *A1, *A2, *B, *J0, *J1, *J2, *S2;
   __device__ int first() const { return blockIdx.x; }
@@ -244,6 +251,7 @@ template <int BN>
 struct PackedInstances {
   static constexpr bool kGlobalMaps = true;  // copied to device memory by the host
   static constexpr bool kPair = false;
+  static constexpr bool kSplit = false;
   __device__ int first() const { return blockIdx.x; }
   __device__ int stride() const { return gridDim.x; }
   const PackEntry* E;
@@ -289,10 +297,17 @@ struct PackedInstances {
 // half to both (the J tiles are their own), so a CTA reads 30 instead of 44
 // KB per stage from L2 at tiles of 224 restarts. With an odd number of row
 // tiles the last pair's second tile lies past n (zero rows, nothing written).
-template <int BN>
+// SPLIT: instead of multicasting, each CTA keeps its half of the spin tile
+// and the first CTA issues the MMAs of the pair (cta_group::2, M 256): a
+// CTA's shared memory then holds and serves 30 instead of 44 KB per stage,
+// which is what limits the operand stream of single-CTA tiles (the tensor
+// cores read a stage as fast as TMA writes it, both through the SM's shared
+// memory).
+template <int BN, bool SPLIT = false>
 struct PairInstance {
   static constexpr bool kGlobalMaps = false;
   static constexpr bool kPair = true;
+  static constexpr bool kSplit = SPLIT;
   const TcArgs& P;
   const CUtensorMap *A0, *A1, *A2, *B, *J0, *J1, *J2, *S2;
   const CUtensorMap* Bh;  // S_t, boxes of one k-block x BN / 2 restarts
@@ -332,7 +347,8 @@ struct PairInstance {
 // instance, or the members of a pack). Roles as described at the top.
 template <int BN, int MODE, bool INT_E, bool FP8, class Src>
 __device__ __forceinline__ void step_tiles(const Src& src) {
-  using Lay = TcLayout<BN>;
+  constexpr bool SPLIT = Src::kSplit;
+  using Lay = TcLayout<BN, SPLIT>;
   constexpr int STAGES = Lay::kStages;
   constexpr int kBK = FP8 ? 128 : 64;  // elements per 128-byte row
   static_assert(!Src::kPair || Lay::kKps == 1, "pair tiles take one k-block per stage");
@@ -347,23 +363,30 @@ __device__ __forceinline__ void step_tiles(const Src& src) {
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   unsigned long long* const trace_ = src.trace();
+  // SPLIT: the first CTA of the pair (rank 0) issues the MMAs of both
+  bool lead = true;
+  if constexpr (SPLIT) lead = src.rank == 0;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       tc::mbar_init(&full[s], 2);  // the J and the S producer
-      tc::mbar_init(&empty[s], Src::kPair ? 2 : 1);  // the MMA issuer of each CTA of the pair
+      // released by the MMA issuer of each CTA of a multicasting pair, or by
+      // the one issuer of a split pair (or of a single CTA)
+      tc::mbar_init(&empty[s], (Src::kPair && !SPLIT) ? 2 : 1);
     }
     for (int b = 0; b < 2; ++b) {
       tc::mbar_init(&acc_full[b], 1);
-      tc::mbar_init(&acc_empty[b], kEpiWarps);
+      // SPLIT: the first CTA's buffer is released by the epilogues of both
+      tc::mbar_init(&acc_empty[b], SPLIT ? 2 * kEpiWarps : kEpiWarps);
     }
     tc::mbar_init(drain, 1);
     *abort_flag = 0;
     tc::fence_barrier_init();
   }
   if (warp == 1) {
-    tc::tmem_alloc(tmem_slot, Lay::kTmemCols);
+    if constexpr (SPLIT) tc::tmem_alloc_pair(tmem_slot, Lay::kTmemCols);
+    else tc::tmem_alloc(tmem_slot, Lay::kTmemCols);
     tc::fence_before_sync();
   }
   __syncthreads();
@@ -412,7 +435,12 @@ __device__ __forceinline__ void step_tiles(const Src& src) {
           }
           uint8_t* sa = smem + stage * Lay::kStage;
           const int cnt = nkt - kt0 < Lay::kKps ? nkt - kt0 : Lay::kKps;
-          tc::mbar_expect_tx(&full[stage], (uint32_t)cnt * (jside ? Lay::kA : Lay::kB));
+          // split pairs: every copy of the pair lands on the first CTA's
+          // barrier, whose producers expect both CTAs' bytes
+          if (!SPLIT || lead)
+            tc::mbar_expect_tx(&full[stage], (uint32_t)cnt * (jside ? Lay::kA : Lay::kB) *
+                                                 (SPLIT ? 2u : 1u));
+          const uint32_t lead_full = SPLIT ? tc::mapa(tc::smem_u32(&full[stage]), 0) : 0u;
           const int plane0 = kt0 / nk, kb0 = kt0 - plane0 * nk;
           if (Lay::kKps == 2 && kb0 + 1 < nfull) {
             // two whole k-blocks of one plane: one copy per operand
@@ -423,7 +451,22 @@ __device__ __forceinline__ void step_tiles(const Src& src) {
             for (int u = 0; u < cnt; ++u) {
               const int kt = kt0 + u;
               const int plane = kt / nk, kb = kt - plane * nk;
-              if (jside) {
+              if constexpr (SPLIT) {
+                // this CTA's J rows and half of the spin tile, kept here (the
+                // pair's MMA reads both CTAs' stages where they are)
+                if (lead) {
+                  if (jside)
+                    tc::tma_load_2d_hint(sa, T.a(plane), &full[stage], kb * kBK, T.m0, pol);
+                  else
+                    tc::tma_load_2d_hint(sa + Lay::kA, T.B, &full[stage], kb * kBK, T.n0, pol);
+                } else {
+                  if (jside)
+                    tc::tma_load_2d_to_pair(sa, T.a(plane), lead_full, kb * kBK, T.m0, pol);
+                  else
+                    tc::tma_load_2d_to_pair(sa + Lay::kA, T.B, lead_full, kb * kBK,
+                                            T.n0 + BN / 2, pol);
+                }
+              } else if (jside) {
                 tc::tma_load_2d_hint(sa + u * Lay::kA, T.a(plane), &full[stage], kb * kBK, T.m0, pol);
               } else if constexpr (Src::kPair) {
                 // this CTA's half of the spin tile, to both CTAs of the pair
@@ -462,6 +505,8 @@ __device__ __forceinline__ void step_tiles(const Src& src) {
         atomicExch(src.err(), 1);
       }
     }
+  } else if (warp == 1 && SPLIT && !lead) {
+    // (second CTA of a split pair: the first CTA issues the pair's MMAs)
   } else if (warp == 1) {
     if (lane == 0) {
       // ------------------------------------------------ MMA issuer
@@ -473,10 +518,11 @@ __device__ __forceinline__ void step_tiles(const Src& src) {
         if (T.skip) continue;
         const TcArgs& P = src.args(T);
         const int nkt = P.nk * P.planes;
-        const uint32_t idesc = op_idesc(BN, FP8, P.f16);
+        const uint32_t idesc = op_idesc(BN, FP8, P.f16, SPLIT ? 256 : 128);
         const int buf = it & 1;
         const uint32_t use = (uint32_t)(it >> 1);
-        if (!tc::mbar_wait(&acc_empty[buf], (use & 1) ^ 1, abort_flag, kWaitCycles)) {
+        // (split pairs: both CTAs' epilogues release it, from the cluster)
+        if (!tc::mbar_wait<SPLIT>(&acc_empty[buf], (use & 1) ^ 1, abort_flag, kWaitCycles)) {
           ok = false;
           break;
         }
@@ -499,26 +545,34 @@ __device__ __forceinline__ void step_tiles(const Src& src) {
             const uint64_t db = tc::desc_k_sw128(sb + Lay::kKps * Lay::kA + u * Lay::kB);
 #pragma unroll
             for (int k = 0; k < 4; ++k) {  // 32 bytes of K per MMA (16 BF16 or 32 E4M3)
-              if (FP8)
-                tc::mma_f8(d, da + 2u * k, db + 2u * k, idesc,
-                           (kt > 0 || k > 0) ? 1u : 0u);
-              else
-                tc::mma_f16(d, da + 2u * k, db + 2u * k, idesc,
-                            (kt > 0 || k > 0) ? 1u : 0u);
+              const uint32_t acc = (kt > 0 || k > 0) ? 1u : 0u;
+              if constexpr (SPLIT) {
+                if (FP8) tc::mma_f8_pair(d, da + 2u * k, db + 2u * k, idesc, acc);
+                else tc::mma_f16_pair(d, da + 2u * k, db + 2u * k, idesc, acc);
+              } else {
+                if (FP8) tc::mma_f8(d, da + 2u * k, db + 2u * k, idesc, acc);
+                else tc::mma_f16(d, da + 2u * k, db + 2u * k, idesc, acc);
+              }
             }
           }
           // the stage is free once this CTA's MMAs (and, for pairs, the
-          // partner's, whose spin half it also holds) have read it
-          if constexpr (Src::kPair) tc::mma_commit_mc(&empty[stage], 0x3);
+          // partner's, whose spin half it also holds) have read it; a split
+          // pair's MMAs read both CTAs' stages
+          if constexpr (SPLIT) tc::mma_commit_pair_mc(&empty[stage], 0x3);
+          else if constexpr (Src::kPair) tc::mma_commit_mc(&empty[stage], 0x3);
           else tc::mma_commit(&empty[stage]);
           if (++stage == STAGES) { stage = 0; phase ^= 1; }
         }
-        if (ok) tc::mma_commit(&acc_full[buf]);
+        if (ok) {
+          if constexpr (SPLIT) tc::mma_commit_pair_mc(&acc_full[buf], 0x3);  // both halves of D
+          else tc::mma_commit(&acc_full[buf]);
+        }
         ++it;
       }
       ISING_TRACE(4);
       if (!ok) {
-        tc::mma_commit(drain);
+        if constexpr (SPLIT) tc::mma_commit_pair(drain);
+        else tc::mma_commit(drain);
         tc::mbar_wait(drain, 0, nullptr, kWaitCycles / 8);
         atomicExch(src.err(), 2);
       }
@@ -598,7 +652,11 @@ __device__ __forceinline__ void step_tiles(const Src& src) {
         if (c0 + kChunk == kCols) {
           tc::fence_before_sync();
           __syncwarp();
-          if (lane == 0) tc::mbar_arrive(&acc_empty[buf]);
+          if (lane == 0) {
+            // split pairs: the first CTA's issuer waits for both epilogues
+            if (SPLIT && !lead) tc::mbar_arrive_cluster(tc::mapa(tc::smem_u32(&acc_empty[buf]), 0));
+            else tc::mbar_arrive(&acc_empty[buf]);
+          }
         }
         float ef[kChunk];
         int eq[kChunk], eh[kChunk];
@@ -674,7 +732,8 @@ __device__ __forceinline__ void step_tiles(const Src& src) {
   if (threadIdx.x == 0) ISING_TRACE(7);
   if (warp == 1) {
     tc::fence_after_sync();
-    tc::tmem_dealloc(tmem_base, Lay::kTmemCols);
+    if constexpr (SPLIT) tc::tmem_dealloc_pair(tmem_base, Lay::kTmemCols);
+    else tc::tmem_dealloc(tmem_base, Lay::kTmemCols);
   }
 }
 #undef ISING_TRACE
@@ -706,6 +765,22 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                         const __grid_constant__ CUtensorMap tmS2, const __grid_constant__ TcArgs P) {
   const PairInstance<BN> src{P,      &tmA0,   &tmA1,   &tmA2, &tmBh, &tmJ2_0,
                              &tmJ2_1, &tmJ2_2, &tmS2,   &tmBh, tc::cluster_rank()};
+  step_tiles<BN, MODE, INT_E, FP8>(src);
+}
+
+// The same with the MMAs of each pair issued as one (cta_group::2, M 256).
+template <int BN, int MODE, bool INT_E, bool FP8>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
+    tc_step_split_kernel(const __grid_constant__ CUtensorMap tmA0,
+                         const __grid_constant__ CUtensorMap tmA1,
+                         const __grid_constant__ CUtensorMap tmA2,
+                         const __grid_constant__ CUtensorMap tmBh,
+                         const __grid_constant__ CUtensorMap tmJ2_0,
+                         const __grid_constant__ CUtensorMap tmJ2_1,
+                         const __grid_constant__ CUtensorMap tmJ2_2,
+                         const __grid_constant__ CUtensorMap tmS2, const __grid_constant__ TcArgs P) {
+  const PairInstance<BN, true> src{P,      &tmA0,   &tmA1, &tmA2, &tmBh, &tmJ2_0,
+                                   &tmJ2_1, &tmJ2_2, &tmS2, &tmBh, tc::cluster_rank()};
   step_tiles<BN, MODE, INT_E, FP8>(src);
 }
 
@@ -1833,6 +1908,7 @@ struct TcState {
   CUtensorMap SP[3];  // streaming kernel: the spin slots' pair views, boxes of BN restarts
   CUtensorMap Bh[3];  // pair tiles: the spin slots, boxes of BN / 2 restarts
   bool pair = false;  // streaming kernel over clusters of two CTAs sharing spin tiles
+  bool split = false; // ... whose MMAs run as one per pair (cta_group::2)
   int nfull = 0;      // k-blocks lying wholly below column n (0 in the small form)
   CUtensorMap Bx[2];  // relaxed mode: one per slot of x = sin(theta), boxes of BN restarts
   int BN = 128;
@@ -1912,6 +1988,23 @@ int launch_bn(ising_ds* ds, TcState* st, const TcArgs& a, const CUtensorMap& mB,
               const CUtensorMap& mS2, const CUtensorMap& mBh) {
   const size_t smem = TcLayout<BN>::kBytes;
   if constexpr (BN >= 192) {
+    if (st->pair && st->split) {
+      auto kern = tc_step_split_kernel<BN, MODE, INT_E, FP8>;
+      const size_t ssmem = TcLayout<BN, true>::kBytes;
+      static bool attr_set = false;  // per instantiation
+      if (!attr_set) {
+        ISING_CUDA(ds->ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)ssmem));
+        attr_set = true;
+      }
+      const int pairs = (a.mtiles + 1) / 2 * a.ntiles;
+      const int clusters = std::max(1, std::min(pairs, ds->ctx->sm_count / 2));
+      kern<<<2 * clusters, kThreads, ssmem, ds->ctx->stream>>>(st->A[0], st->A[1], st->A[2], mBh,
+                                                               st->J2[0], st->J2[1], st->J2[2],
+                                                               mS2, a);
+      ISING_CUDA(ds->ctx, cudaGetLastError());
+      return ISING_OK;
+    }
     if (st->pair) {
       auto kern = tc_step_pair_kernel<BN, MODE, INT_E, FP8>;
       static bool attr_set = false;  // per instantiation
@@ -2475,10 +2568,14 @@ int tc_bn_candidates(const ising_ds* ds, int* out) {
   for (int bn : {64, 128, 224, 256})
     if (bn == 64 || bn / 2 < ds->B) out[k++] = bn;
   // the same wide tiles over clusters of two CTAs sharing spin tiles
-  // (kTcPair: a flag on the width), when there are two row tiles to pair
+  // (kTcPair: a flag on the width; with kTcSplit their MMAs run as one),
+  // when there are two row tiles to pair
   if (!ds->relaxed() && ds->n > kBM)
     for (int bn : {224, 256})
-      if (bn / 2 < ds->B) out[k++] = bn | kTcPair;
+      if (bn / 2 < ds->B) {
+        out[k++] = bn | kTcPair;
+        out[k++] = bn | kTcPair | kTcSplit;
+      }
   return k;
 }
 
@@ -2488,11 +2585,13 @@ int tc_bn_candidates(const ising_ds* ds, int* out) {
 int tc_set_bn(ising_ds* ds, int code) {
   auto st = static_cast<TcState*>(ds->tc);
   if (st->resident) return fail(ds->ctx, ISING_EINVAL, "tile width of a resident form");
-  const int bn = code & ~kTcPair;
+  const int bn = code & ~(kTcPair | kTcSplit);
   const bool pair = (code & kTcPair) != 0 && bn >= 192 && !ds->relaxed();
-  if (st->BN == bn && st->pair == pair) return ISING_OK;
+  const bool split = pair && (code & kTcSplit) != 0;
+  if (st->BN == bn && st->pair == pair && st->split == split) return ISING_OK;
   st->BN = bn;
   st->pair = pair;
+  st->split = split;
   st->maps_ready = false;
   st->trace.release();
   const int tiles = ceil_div_i(ds->n, kBM) * ceil_div_i(ds->B, bn);
