@@ -254,7 +254,8 @@ const char* ising_energy_noalloc_error(void);
  * each step of every member runs as one persistent tensor-core launch over
  * the concatenated tiles of all members plus one tracking launch over all
  * their restarts (the restarts, or "sweeps", of Sec. IV-C batched across
- * instances), replayed from a CUDA graph. Each member keeps its own step
+ * instances); from the pack's second ising_pack_run on, the step loop is
+ * replayed from a CUDA graph captured then. Each member keeps its own step
  * counter on the device and computes exactly what it computes alone (the
  * same products in the same order): a member's state, bests and result are
  * identical to running it by itself.
@@ -402,11 +403,18 @@ int ising_ds_destroy(ising_ds* ds);
  * memory budget and a slot is free, advances every admitted request by
  * `chunk_steps` steps per round on its own stream (the kernels of different
  * requests overlap on the device, and requests that arrive meanwhile join at
- * the next round), and posts each result when its steps are done. A request
+ * the next round), and posts each result when its steps are done; each
+ * request's set-up (upload, pruning, session) and finishing run on helper
+ * threads, so they do not hold up the other requests' chunks. A request
  * is solved exactly as ising_solve would solve it alone (pruning, domain
  * selection with the state kept in device memory between steps, best of
  * restarts, reconstruction, energy), so its result does not depend on what
- * else is being served. The paper has no counterpart. */
+ * else is being served. The paper has no counterpart.
+ * The requests' streams reach the device through the context's hardware
+ * work queues (8 unless the environment variable CUDA_DEVICE_MAX_CONNECTIONS,
+ * read when the process creates its CUDA context, says more): with more
+ * requests active than queues, streams share queues and their kernels
+ * overlap less. */
 typedef struct ising_server ising_server;
 
 typedef struct ising_server_cfg {
@@ -414,7 +422,7 @@ typedef struct ising_server_cfg {
   int32_t max_active;    /* requests on the GPU at once (streams), >= 1 */
   int32_t chunk_steps;   /* steps per request per scheduling round, >= 1 */
   int32_t flags;         /* 0 or ISING_SERVER_PACK */
-  int32_t reserved;
+  int32_t helper_threads;/* threads for requests' set-up and finishing, 0..16 (0: 2) */
 } ising_server_cfg;
 
 /* cfg.flags: the dense tensor-core requests ready in a scheduling round are
@@ -434,6 +442,9 @@ typedef struct ising_result {
   double t_submit_ms;    /* host clock, ms since the server was created */
   double t_admit_ms;
   double t_done_ms;
+  int64_t steps_done;    /* domain-selection steps the request ran */
+  int32_t reached;       /* submitted with a target: 1 if best_energy <= target */
+  int32_t reserved;
 } ising_result;
 
 /* Creates the server on the context's device; the context must outlive it. */
@@ -443,6 +454,18 @@ int ising_server_create(ising_ctx* ctx, const ising_server_cfg* cfg, ising_serve
  * estimated footprint exceeds the whole budget (it could never be admitted). */
 int ising_server_submit(ising_server* srv, const ising_instance* inst, const ising_ds_params* p,
                         int prune_flags, uint64_t* req_id);
+/* Like ising_server_submit, for a time-to-target query: after every chunk
+ * of steps the server evaluates the energy of the request's best spins so
+ * far on the full instance (the best restart by tracked energy, the
+ * near-best re-evaluated exactly as in ising_ds_result, reconstructed, then
+ * ising_energy) and finishes the request as soon as it is <= target_energy,
+ * without running its remaining steps (ising_result.steps_done tells how
+ * many ran, .reached whether the target was met). Otherwise the request
+ * runs all its steps. The check synchronises the request's stream once per
+ * chunk. */
+int ising_server_submit_target(ising_server* srv, const ising_instance* inst,
+                               const ising_ds_params* p, int prune_flags, double target_energy,
+                               uint64_t* req_id);
 /* Non-blocking: fills *res (res->done tells whether it is final) and, once
  * done, copies the n best spins to host `spins` if not NULL. ISING_EINVAL for
  * an unknown id. */
@@ -450,8 +473,34 @@ int ising_server_poll(ising_server* srv, uint64_t req_id, ising_result* res, int
 /* Blocks until the request is done or `timeout_s` passes (ISING_ETIMEOUT). */
 int ising_server_wait(ising_server* srv, uint64_t req_id, double timeout_s, ising_result* res,
                       int8_t* spins);
+/* The message of a finished request's failure (empty when it succeeded or
+ * is not done), truncated to len - 1 bytes and NUL-terminated. */
+int ising_server_error(ising_server* srv, uint64_t req_id, char* buf, int64_t len);
 /* Drops a finished request's stored result. */
 int ising_server_release(ising_server* srv, uint64_t req_id);
+/* Where the server threads' host time went since the server was created
+ * (ms of the host clock, summed over the worker and the helper threads; the
+ * device work of the chunks overlaps it and is not included). */
+typedef struct ising_server_stats {
+  int64_t completed;     /* requests finished */
+  int64_t rounds;        /* scheduling rounds that found work */
+  int64_t chunks;        /* chunks queued for single requests */
+  int64_t pack_chunks;   /* chunks queued as packs (one per pack) */
+  int64_t packs_created; /* packs built (a new group of ready requests) */
+  int64_t target_checks; /* time-to-target evaluations */
+  double setup_ms;       /* admitted requests' set-up: upload, pruning, session */
+  double setup_upload_ms;  /* of which the instance's upload */
+  double setup_prune_ms;   /* of which pruning */
+  double setup_session_ms; /* of which the session's creation */
+  double advance_ms;     /* queueing chunks, single and packed (pack creation included) */
+  double pack_create_ms; /* of which building packs */
+  double check_ms;       /* convergence-count reads and target evaluations */
+  double finish_ms;      /* finishing requests: final pass, result, reconstruction, energy */
+  double release_ms;     /* freeing finished requests' device memory and session */
+  double idle_ms;        /* waiting with no request ready */
+  double elapsed_ms;     /* since the server was created */
+} ising_server_stats;
+int ising_server_stats_get(ising_server* srv, ising_server_stats* out);
 /* Finishes the queued and active requests, stops the worker, frees all. */
 int ising_server_destroy(ising_server* srv);
 

@@ -52,14 +52,25 @@ class DSStats(ctypes.Structure):
 
 class ServerCfg(ctypes.Structure):
     _fields_ = [("budget_bytes", c_uint64), ("max_active", c_int32), ("chunk_steps", c_int32),
-                ("flags", c_int32), ("reserved", c_int32)]
+                ("flags", c_int32), ("helper_threads", c_int32)]
 
 
 class Result(ctypes.Structure):
     _fields_ = [("status", c_int32), ("done", c_int32), ("n", c_int64),
                 ("best_energy", c_double), ("best_restart", c_int64), ("best_step", c_int64),
                 ("footprint", c_int64), ("t_submit_ms", c_double), ("t_admit_ms", c_double),
-                ("t_done_ms", c_double)]
+                ("t_done_ms", c_double), ("steps_done", c_int64), ("reached", c_int32),
+                ("reserved", c_int32)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("completed", c_int64), ("rounds", c_int64), ("chunks", c_int64),
+                ("pack_chunks", c_int64), ("packs_created", c_int64), ("target_checks", c_int64),
+                ("setup_ms", c_double), ("setup_upload_ms", c_double),
+                ("setup_prune_ms", c_double), ("setup_session_ms", c_double),
+                ("advance_ms", c_double), ("pack_create_ms", c_double),
+                ("check_ms", c_double), ("finish_ms", c_double), ("release_ms", c_double),
+                ("idle_ms", c_double), ("elapsed_ms", c_double)]
 
 
 _PROTOS = {
@@ -109,6 +120,10 @@ _PROTOS = {
     "ising_server_create": (c_int, [c_void_p, POINTER(ServerCfg), POINTER(c_void_p)]),
     "ising_server_submit": (c_int, [c_void_p, POINTER(Instance), POINTER(DSParams), c_int,
                                     POINTER(c_uint64)]),
+    "ising_server_submit_target": (c_int, [c_void_p, POINTER(Instance), POINTER(DSParams), c_int,
+                                           c_double, POINTER(c_uint64)]),
+    "ising_server_stats_get": (c_int, [c_void_p, POINTER(ServerStats)]),
+    "ising_server_error": (c_int, [c_void_p, c_uint64, c_char_p, c_int64]),
     "ising_server_poll": (c_int, [c_void_p, c_uint64, POINTER(Result), c_void_p]),
     "ising_server_wait": (c_int, [c_void_p, c_uint64, c_double, POINTER(Result), c_void_p]),
     "ising_server_release": (c_int, [c_void_p, c_uint64]),

@@ -202,45 +202,64 @@ class Server:
     energy on the full instance and submit / admit / done times (ms)."""
 
     def __init__(self, ctx: Context, budget_bytes: int, max_active: int = 8,
-                 chunk_steps: int = 250, pack: bool = True):
+                 chunk_steps: int = 250, pack: bool = True, helper_threads: int = 0):
         self.ctx = ctx
         cfg = L.ServerCfg()
         cfg.budget_bytes = int(budget_bytes)
         cfg.max_active = int(max_active)
         cfg.chunk_steps = int(chunk_steps)
         cfg.flags = L.SERVER_PACK if pack else 0
-        cfg.reserved = 0
+        cfg.helper_threads = int(helper_threads)
         self.handle = c_void_p()
         ctx._children.add(self)
         ctx.check(ctx.lib.ising_server_create(ctx.handle, byref(cfg), byref(self.handle)))
         self._n = {}
 
-    def submit(self, inst, restarts, steps, zero_rule=True, **kw) -> int:
+    def submit(self, inst, restarts, steps, zero_rule=True, target=None, **kw) -> int:
+        """Queues a request; with `target` (an energy) it is a time-to-target
+        query that finishes once its best energy on the full instance is <=
+        target (see ising_server_submit_target)."""
         s, keep = make_instance(inst)
         p = params(restarts, steps, **kw)
         rid = ctypes.c_uint64()
-        self.ctx.check(self.ctx.lib.ising_server_submit(
-            self.handle, byref(s), byref(p), L.PRUNE_ZERO_RULE if zero_rule else 0, byref(rid)))
+        flags = L.PRUNE_ZERO_RULE if zero_rule else 0
+        if target is None:
+            self.ctx.check(self.ctx.lib.ising_server_submit(self.handle, byref(s), byref(p), flags,
+                                                            byref(rid)))
+        else:
+            self.ctx.check(self.ctx.lib.ising_server_submit_target(
+                self.handle, byref(s), byref(p), flags, float(target), byref(rid)))
         self._n[rid.value] = int(inst.n)
         return rid.value
 
-    def _result(self, res, spins):
+    def stats(self) -> dict:
+        """Where the worker thread's host time went (ising_server_stats_get)."""
+        st = L.ServerStats()
+        self.ctx.check(self.ctx.lib.ising_server_stats_get(self.handle, byref(st)))
+        return {f: getattr(st, f) for f, _ in L.ServerStats._fields_}
+
+    def _result(self, res, rid, spins):
         d = {f: getattr(res, f) for f, _ in L.Result._fields_}
         d["best_spins"] = spins if res.done else None
+        d["error"] = ""
+        if res.done and res.status != 0:
+            buf = ctypes.create_string_buffer(512)
+            self.ctx.check(self.ctx.lib.ising_server_error(self.handle, rid, buf, 512))
+            d["error"] = buf.value.decode(errors="replace")
         return d
 
     def poll(self, rid: int):
         res = L.Result()
         spins = np.empty(self._n.get(rid, 1), np.int8)
         self.ctx.check(self.ctx.lib.ising_server_poll(self.handle, rid, byref(res), _ptr(spins)))
-        return self._result(res, spins)
+        return self._result(res, rid, spins)
 
     def wait(self, rid: int, timeout: float = 600.0):
         res = L.Result()
         spins = np.empty(self._n[rid], np.int8)
         self.ctx.check(self.ctx.lib.ising_server_wait(self.handle, rid, float(timeout), byref(res),
                                                       _ptr(spins)))
-        return self._result(res, spins)
+        return self._result(res, rid, spins)
 
     def release(self, rid: int):
         self.ctx.check(self.ctx.lib.ising_server_release(self.handle, rid))

@@ -4,10 +4,51 @@
 #include "tcgen05.cuh"
 
 #include <algorithm>
+#include <cstring>
 
 using namespace ising;
 
 extern "C" int ising_version(void) { return 10000; }
+
+namespace ising {
+
+// One launch carries up to kUploadBytes (kernel parameters may take up to
+// 32764 bytes in all).
+constexpr int kUploadBytes = 30720;
+struct UploadChunk {
+  unsigned char* dst;
+  int len;
+  unsigned char bytes[kUploadBytes];
+};
+
+__global__ void upload_kernel(const UploadChunk c) {
+  for (int i = threadIdx.x; i < c.len; i += blockDim.x) c.dst[i] = c.bytes[i];
+}
+
+int upload_async(ising_ctx* ctx, void* dst, const void* src, size_t bytes) {
+  static_assert(sizeof(UploadChunk) <= 32764, "kernel parameter limit");
+  if (bytes > 16 * (size_t)kUploadBytes) {
+    // large: one copy, then a wait for it (the host buffer goes away on return)
+    ISING_CUDA(ctx, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    ISING_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return ISING_OK;
+  }
+  const unsigned char* s = static_cast<const unsigned char*>(src);
+  unsigned char* d = static_cast<unsigned char*>(dst);
+  UploadChunk* c = new UploadChunk;
+  for (size_t off = 0; off < bytes; off += kUploadBytes) {
+    const int len = (int)std::min<size_t>(kUploadBytes, bytes - off);
+    c->dst = d + off;
+    c->len = len;
+    memcpy(c->bytes, s + off, len);
+    upload_kernel<<<1, 256, 0, ctx->stream>>>(*c);
+  }
+  delete c;
+  ISING_CUDA(ctx, cudaGetLastError());
+  return ISING_OK;
+}
+
+}  // namespace ising
 
 extern "C" int ising_create(ising_ctx** out, int device, void* stream) {
   if (!out) return ISING_EINVAL;

@@ -94,6 +94,13 @@ struct DevMem {
   template <class T> T* as() const { return static_cast<T*>(p); }
 };
 
+// Copies `bytes` of host memory to device memory `dst` in the order of the
+// context's stream; the host buffer may go away on return. Up to 480 KB the
+// bytes travel as kernel parameters (copied when each launch is queued), so
+// nothing waits for the stream's earlier work (a copy from pageable memory
+// first waits for the stream); larger tables are copied and waited for.
+int upload_async(ising_ctx* ctx, void* dst, const void* src, size_t bytes);
+
 inline int dev_alloc(ising_ctx* ctx, DevMem& m, size_t bytes) {
   m.release();
   if (bytes == 0) bytes = 16;

@@ -571,8 +571,7 @@ int common_alloc(ising_ds* ds) {
     std::vector<int> live(nb);
     for (int64_t k = 0; k < nb; ++k) live[k] = (int)std::min<int64_t>(32, B - 32 * k);
     ISING_TRY(dev_alloc(ctx, ds->live, nb * 4));
-    ISING_CUDA(ctx, cudaMemcpyAsync(ds->live.p, live.data(), nb * 4, cudaMemcpyHostToDevice, ctx->stream));
-    ISING_CUDA(ctx, cudaStreamSynchronize(ctx->stream));  // (the host vector goes away)
+    ISING_TRY(upload_async(ctx, ds->live.p, live.data(), nb * 4));
   }
   ISING_TRY(dev_alloc(ctx, ds->work, 8));
   ISING_CUDA(ctx, cudaMemsetAsync(ds->work.p, 0, 8, ctx->stream));
@@ -592,10 +591,7 @@ int common_alloc(ising_ds* ds) {
   }
   bias[0] = bias[1] = 1.0f;
   ISING_TRY(dev_alloc(ctx, ds->bias, bias.size() * 4));
-  ISING_CUDA(ctx, cudaMemcpyAsync(ds->bias.p, bias.data(), bias.size() * 4,
-                                  cudaMemcpyHostToDevice, ctx->stream));
-  ISING_CUDA(ctx, cudaStreamSynchronize(ctx->stream));  // `bias` is a host temporary
-  return ISING_OK;
+  return upload_async(ctx, ds->bias.p, bias.data(), bias.size() * 4);
 }
 
 int setup_field(ising_ds* ds) {
@@ -624,10 +620,8 @@ int setup_field(ising_ds* ds) {
     hf[i] = (float)h[i];
     hi[i] = ds->int_energy ? (int32_t)std::llrint(std::ldexp(h[i], ds->h_shift)) : 0;
   }
-  ISING_CUDA(ctx, cudaMemcpyAsync(ds->hf.p, hf.data(), n * 4, cudaMemcpyHostToDevice, ctx->stream));
-  ISING_CUDA(ctx, cudaMemcpyAsync(ds->hint.p, hi.data(), n * 4, cudaMemcpyHostToDevice, ctx->stream));
-  ISING_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-  return ISING_OK;
+  ISING_TRY(upload_async(ctx, ds->hf.p, hf.data(), n * 4));
+  return upload_async(ctx, ds->hint.p, hi.data(), n * 4);
 }
 
 int path_step_raw(ising_ds* ds, bool update) {

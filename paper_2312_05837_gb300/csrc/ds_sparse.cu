@@ -5,9 +5,13 @@
 // a range of rows and one 128-restart slice (grid.y); a warp owns one row at a
 // time and lane l owns restarts 4 l + {0..3} of the slice, so every state
 // access is a coalesced float4 and a neighbour's spins are one broadcast word
-// per group of 8 lanes. The per-row epilogue is the same as the dense paths: F = cQ G +
-// cH h - mu s, g = cos(theta) F, Adam, projection, new spin bit; energy
-// partials of the input spins are summed per block in warp order. In the
+// per group of 8 lanes. A row's edges are read either by every lane
+// (many rows per warp, the next row's state in flight meanwhile) or one edge
+// per lane and broadcast (few rows per warp: the gathers then overlap); both
+// visit the edges in order, so G is the same. The per-row epilogue is the
+// same as the dense paths: F = cQ G + cH h - mu s, g = cos(theta) F, Adam,
+// projection, new spin bit; energy partials of the input spins are summed
+// per block in warp order. In the
 // relaxed mode each neighbour also contributes J_ij x_j with x = sin(theta)
 // from the FP32 slot x_t ([n][Bp], float4 per lane): that product drives the
 // update, the bit product the energies, and x_{t+1} is written out.
@@ -32,7 +36,8 @@ __global__ void __launch_bounds__(256, Q == 1 ? (MODE == kModeRelaxed ? 3 : 4) :
     const float2* __restrict__ bias, const long long* __restrict__ counters,
     long long* __restrict__ qpart, long long* __restrict__ hpart, float* __restrict__ epart,
     float* __restrict__ Gout, const float* __restrict__ xin, float* __restrict__ xout,
-    int64_t B, const int* __restrict__ live32, unsigned long long* __restrict__ work) {
+    int64_t B, const int* __restrict__ live32, unsigned long long* __restrict__ work,
+    int lane_edges) {
   constexpr bool RELAXED = MODE == kModeRelaxed;
   constexpr bool UPDATE = MODE == kModeUpdate || RELAXED;
   constexpr int W = 8;  // warps per block
@@ -61,7 +66,10 @@ __global__ void __launch_bounds__(256, Q == 1 ? (MODE == kModeRelaxed ? 3 : 4) :
   // per step, evict-first), so HBM latency overlaps the dependent gather
   float4 th_n[Q], m_n[Q], v_n[Q];
   uint32_t own_n[Q];
+  int rb_n = 0, re_n = 0;
   auto fetch = [&](int64_t row) {
+    rb_n = rowptr[row];
+    re_n = rowptr[row + 1];
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
       const int64_t base = row * Bp + cb + 128 * q + 4 * lane;
@@ -77,6 +85,7 @@ __global__ void __launch_bounds__(256, Q == 1 ? (MODE == kModeRelaxed ? 3 : 4) :
   for (int64_t i = r0 + warp; i < r1; i += W) {
     float4 th4[Q], m4[Q], v4[Q];
     uint32_t own[Q];
+    const int rb = rb_n, re = re_n;
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
       th4[q] = th_n[q];
@@ -90,14 +99,10 @@ __global__ void __launch_bounds__(256, Q == 1 ? (MODE == kModeRelaxed ? 3 : 4) :
     for (int q = 0; q < Q; ++q)
 #pragma unroll
       for (int r = 0; r < 4; ++r) { G[q][r] = 0.f; Gx[q][r] = 0.f; }
-    const int e1 = rowptr[i + 1];
-    for (int e = rowptr[i]; e < e1; ++e) {
-      const int64_t j = col[e];
-      const float Jv = VAL_I8 ? (float)static_cast<const int8_t*>(val)[e]
-                              : static_cast<const float*>(val)[e];
+    auto add_edge = [&](int64_t j, float Jv, const uint32_t* w) {
 #pragma unroll
       for (int q = 0; q < Q; ++q) {
-        const uint32_t nib = (__ldg(&bits_in[j * words + wofs + 4 * q]) >> nshift) & 0xFu;
+        const uint32_t nib = (w[q] >> nshift) & 0xFu;
 #pragma unroll
         for (int r = 0; r < 4; ++r) G[q][r] += ((nib >> r) & 1u) ? Jv : -Jv;
         if (RELAXED) {
@@ -107,6 +112,52 @@ __global__ void __launch_bounds__(256, Q == 1 ? (MODE == kModeRelaxed ? 3 : 4) :
           Gx[q][2] = fmaf(Jv, xj.z, Gx[q][2]);
           Gx[q][3] = fmaf(Jv, xj.w, Gx[q][3]);
         }
+      }
+    };
+    if (lane_edges) {
+      // few rows per warp (small instances): the row's edges, up to 32 at a
+      // time, lane k loading edge k (one coalesced load), then visited in
+      // order by broadcast, each neighbour's spin word requested one edge
+      // ahead, so the gathers do not wait on one another
+      for (int eb = rb; eb < re; eb += 32) {
+        const int cnt = re - eb < 32 ? re - eb : 32;
+        int jl = 0;
+        float vl = 0.f;
+        if (lane < cnt) {
+          jl = col[eb + lane];
+          vl = VAL_I8 ? (float)static_cast<const int8_t*>(val)[eb + lane]
+                      : static_cast<const float*>(val)[eb + lane];
+        }
+        uint32_t w_next[Q];
+        int64_t j_next = __shfl_sync(0xffffffffu, jl, 0);
+#pragma unroll
+        for (int q = 0; q < Q; ++q) w_next[q] = __ldg(&bits_in[j_next * words + wofs + 4 * q]);
+#pragma unroll 1
+        for (int k = 0; k < cnt; ++k) {
+          const int64_t j = j_next;
+          const float Jv = __shfl_sync(0xffffffffu, vl, k);
+          uint32_t w[Q];
+#pragma unroll
+          for (int q = 0; q < Q; ++q) w[q] = w_next[q];
+          if (k + 1 < cnt) {
+            j_next = __shfl_sync(0xffffffffu, jl, k + 1);
+#pragma unroll
+            for (int q = 0; q < Q; ++q) w_next[q] = __ldg(&bits_in[j_next * words + wofs + 4 * q]);
+          }
+          add_edge(j, Jv, w);
+        }
+      }
+    } else {
+      // many rows per warp: every lane reads each edge (broadcast) and the
+      // next row's state is already in flight
+      for (int e = rb; e < re; ++e) {
+        const int64_t j = col[e];
+        const float Jv = VAL_I8 ? (float)static_cast<const int8_t*>(val)[e]
+                                : static_cast<const float*>(val)[e];
+        uint32_t w[Q];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) w[q] = __ldg(&bits_in[j * words + wofs + 4 * q]);
+        add_edge(j, Jv, w);
       }
     }
     if (MODE == kModeCoupling) {
@@ -202,12 +253,13 @@ __global__ void csr_values_kernel(const void* J, int dt, int64_t nnz, bool to_i8
 }
 
 // Row blocks: one wave of the Q = 1 kernel (four blocks per SM over the
-// 128-restart slices), at least 64 rows each; a warp then streams its rows
-// back to back with the next row's state in flight.
+// 128-restart slices), at least 8 rows (one per warp) each; a warp then
+// streams its rows back to back with the next row's state in flight. Small
+// instances thus spread over as many warps as they have rows.
 int64_t sparse_rows_per_block(ising_ds* ds) {
   const int64_t slices = std::max<int64_t>(ds->Bp / 128, 1);
   const int64_t target = std::max<int64_t>((int64_t)ds->ctx->sm_count * 4 / slices, 1);
-  const int64_t nb = std::min<int64_t>((ds->n + 63) / 64, target);
+  const int64_t nb = std::min<int64_t>((ds->n + 7) / 8, target);
   return (ds->n + nb - 1) / nb;
 }
 
@@ -243,6 +295,7 @@ int sparse_step(ising_ds* ds, int mode, float* Gout) {
   const float* xin = mode == kModeRelaxed ? ds->xbuf[t % 2].as<float>() : nullptr;
   float* xout = mode == kModeRelaxed ? ds->xbuf[(t + 1) % 2].as<float>() : nullptr;
   dim3 grid((unsigned)ds->mtiles, (unsigned)(ds->Bp / (128 * Q)));
+  const int lane_edges = (rpb + 7) / 8 <= 4;  // rows per warp
 #define ISING_SP(U, I, V)                                                                     \
   do {                                                                                        \
     if (Q == 2)                                                                               \
@@ -256,7 +309,8 @@ int sparse_step(ising_ds* ds, int mode, float* Gout) {
       ds->hf.as<float>(), ds->hint.as<int32_t>(), ds->k, ds->bias.as<float2>(),               \
       ds->counters.as<long long>(), ds->qpart[ps].as<long long>(),                            \
       ds->hpart[ps].as<long long>(), ds->epart[ps].as<float>(), Gout, xin, xout, ds->B,          \
-      ds->live.p ? ds->live.as<int>() : nullptr, ds->work.as<unsigned long long>()
+      ds->live.p ? ds->live.as<int>() : nullptr, ds->work.as<unsigned long long>(),          \
+      lane_edges
 #define ISING_SP_V(U, I) \
   do { if (ds->sp_int8) ISING_SP(U, I, true); else ISING_SP(U, I, false); } while (0)
 #define ISING_SP_I(U) \

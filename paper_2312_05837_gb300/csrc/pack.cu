@@ -31,6 +31,7 @@ struct ising_pack {
   cudaStream_t gstream = nullptr;
   cudaEvent_t ev = nullptr;
   bool launched = false;  // the kernels have run once outside capture
+  int64_t advances = 0;   // pack_advance calls so far
 };
 
 namespace {
@@ -108,9 +109,12 @@ int pack_advance(ising_pack* pk, int64_t steps) {
   ISING_TRY(wait_for_members(pk));
   int64_t s = 0;
   // the first steps run outside capture (the kernels' attributes are set
-  // on their first launch), then graph replays, then single steps
+  // on their first launch), then graph replays, then single steps; the
+  // graph is captured once the pack is advanced a second time (a pack that
+  // lives for one call does not pay for a capture)
+  const bool replay = pk->advances > 0;
   while (s < steps) {
-    if (pk->launched && steps - s >= kPackGraphSteps) {
+    if (replay && pk->launched && steps - s >= kPackGraphSteps) {
       if (!pk->graph) ISING_TRY(pack_graph(pk));
       ISING_CUDA(ctx, cudaEventRecord(pk->ev, ctx->stream));
       ISING_CUDA(ctx, cudaStreamWaitEvent(pk->gstream, pk->ev, 0));
@@ -125,6 +129,7 @@ int pack_advance(ising_pack* pk, int64_t steps) {
     }
   }
   for (ising_ds* ds : pk->members) ds->t += steps;
+  pk->advances += 1;
   return members_wait(pk);
 }
 
@@ -190,16 +195,13 @@ extern "C" int ising_pack_create(ising_ctx* ctx, ising_ds* const* sessions, int3
     ISING_TRY(dev_alloc(ctx, pk->targs, targs.size() * sizeof(TrackArgs)));
     ISING_TRY(dev_alloc(ctx, pk->rstart, rstart.size() * sizeof(int64_t)));
     ISING_TRY(dev_alloc(ctx, pk->words, 16));
-    ISING_CUDA(ctx, cudaMemcpyAsync(pk->entries.p, ent.data(), ent.size(), cudaMemcpyHostToDevice, ctx->stream));
-    ISING_CUDA(ctx, cudaMemcpyAsync(pk->start.p, start.data(), start.size() * sizeof(int),
-                                    cudaMemcpyHostToDevice, ctx->stream));
-    ISING_CUDA(ctx, cudaMemcpyAsync(pk->targs.p, targs.data(), targs.size() * sizeof(TrackArgs),
-                                    cudaMemcpyHostToDevice, ctx->stream));
-    ISING_CUDA(ctx, cudaMemcpyAsync(pk->rstart.p, rstart.data(), rstart.size() * sizeof(int64_t),
-                                    cudaMemcpyHostToDevice, ctx->stream));
+    // the tables travel as kernel parameters: nothing here waits for the
+    // stream's earlier work (other packs' steps on a shared stream)
+    ISING_TRY(upload_async(ctx, pk->entries.p, ent.data(), ent.size()));
+    ISING_TRY(upload_async(ctx, pk->start.p, start.data(), start.size() * sizeof(int)));
+    ISING_TRY(upload_async(ctx, pk->targs.p, targs.data(), targs.size() * sizeof(TrackArgs)));
+    ISING_TRY(upload_async(ctx, pk->rstart.p, rstart.data(), rstart.size() * sizeof(int64_t)));
     ISING_CUDA(ctx, cudaMemsetAsync(pk->words.p, 0, 16, ctx->stream));
-    // (the host vectors go away on return: the copies must have happened)
-    ISING_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     return ISING_OK;
   }();
   if (rc != ISING_OK) {

@@ -3,14 +3,17 @@
 // A worker thread owns `max_active` slots, each a context with its own
 // stream. It loops: (1) admits queued requests in arrival order while a slot
 // is free and the estimated device footprint of the admitted set stays within
-// the budget, and sets them up (upload, pruning, session); (2) for every
-// admitted request whose previous chunk has completed (an event on its
-// stream, polled without blocking), either queues `chunk_steps` more
-// domain-selection steps or, when its steps are done, finishes it (final
-// energy pass, best of restarts, reconstruction, full-instance energy) and
-// releases its memory and slot. Slots progress independently, so a small
-// request never waits for a large one's chunk, and requests arriving at any
-// time are admitted as soon as a slot and memory free up.
+// the budget, and hands their set-up (upload, pruning, session) to a helper
+// thread; (2) for every set-up request whose previous chunk has completed (an
+// event on its stream, polled without blocking), either queues `chunk_steps`
+// more domain-selection steps or, when its steps are done, hands it to a
+// helper that finishes it (final energy pass, best of restarts,
+// reconstruction, full-instance energy) and releases its memory and slot.
+// Slots progress independently, so a small request never waits for a large
+// one's chunk, requests arriving at any time are admitted as soon as a slot
+// and memory free up, and set-up and finishing (host work and
+// synchronisations of a request's own stream) do not hold up the chunks of
+// the others.
 // With ISING_SERVER_PACK, the dense tensor-core requests that are ready in a
 // round are grouped by kind (operand type, energy mode, tile width) and each
 // group advances its chunk as one pack (ising_pack: one launch per step for
@@ -19,12 +22,14 @@
 #include "ds_internal.cuh"
 
 #include <algorithm>
+#include <cmath>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
 #include <map>
 #include <memory>
 #include <mutex>
+#include <string>
 #include <thread>
 
 using namespace ising;
@@ -46,8 +51,12 @@ struct Request {
   ising_ds_params p{};
   int prune_flags = 0;
   size_t footprint = 0;
+  bool has_target = false;  // time-to-target query
+  double target = 0.0;
+  bool reached = false;
   double t_submit = 0, t_admit = 0, t_done = 0;
   int slot = -1;
+  int phase = 0;  // kQueued, kSettingUp, kReady, kFinishing, kDone
   // running state
   DevInstance I;
   ising_prune_result* pr = nullptr;
@@ -58,11 +67,14 @@ struct Request {
   bool in_flight = false;
   // result
   int status = ISING_OK;
+  std::string error;  // the failure's message
   bool done = false;
   std::vector<int8_t> spins;
   double energy = 0.0;
   ising_ds_stats stats{};
 };
+
+enum Phase { kQueued = 0, kSettingUp, kReady, kFinishing, kDone };
 
 // Device bytes a request holds while admitted (instance copy, pruning work,
 // operands, state, spins, partials, bests), estimated from its shape.
@@ -94,9 +106,13 @@ struct ising_server {
   std::vector<std::unique_ptr<ising_ctx>> slots;
   std::vector<bool> slot_busy;
   std::thread worker;
+  std::vector<std::thread> helpers;
   std::mutex mu;
-  std::condition_variable cv;       // work arrived / stop
+  std::condition_variable cv;       // work arrived / a request is ready / stop
   std::condition_variable done_cv;  // a request finished
+  std::condition_variable task_cv;  // set-up or finishing for the helpers
+  std::deque<Request*> tasks;
+  bool helpers_stop = false;
   std::deque<Request*> queue;
   std::vector<Request*> active;
   std::map<uint64_t, std::unique_ptr<Request>> all;
@@ -108,6 +124,7 @@ struct ising_server {
   std::unique_ptr<ising_ctx> pack_ctx;
   std::map<std::vector<uint64_t>, ising_pack*> packs;
   std::chrono::steady_clock::time_point t0;
+  ising_server_stats st{};  // guarded by mu
 
   double now_ms() const {
     return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -116,13 +133,24 @@ struct ising_server {
 
 namespace {
 
-// Pruning and session set-up of an admitted request on its slot's stream.
-int start_request(ising_server* srv, Request* r) {
+using Clock = std::chrono::steady_clock;
+double ms_since(Clock::time_point t) {
+  return std::chrono::duration<double, std::milli>(Clock::now() - t).count();
+}
+
+// Pruning and session set-up of an admitted request on its slot's stream;
+// `ms` receives the upload, pruning and session times.
+int start_request(ising_server* srv, Request* r, double ms[3]) {
   ising_ctx* ctx = srv->slots[r->slot].get();
   ISING_CUDA(ctx, cudaSetDevice(ctx->device));
+  auto t = Clock::now();
   ISING_TRY(upload_instance(ctx, &r->inst, &r->I));
+  ms[0] = ms_since(t);
+  t = Clock::now();
   ISING_TRY(prune_device(ctx, r->I, r->prune_flags, &r->pr));
   ising_prune_info(r->pr, &r->nG, nullptr, nullptr, nullptr, nullptr);
+  ms[1] = ms_since(t);
+  t = Clock::now();
   if (r->nG > 0) {
     ising_instance red;
     ising_prune_reduced(r->pr, &red);
@@ -131,6 +159,7 @@ int start_request(ising_server* srv, Request* r) {
     ISING_TRY(ds_create_impl(ctx, &red, &p, &r->ds, false));
   }
   ISING_CUDA(ctx, cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming));
+  ms[2] = ms_since(t);
   r->started = true;
   return ISING_OK;
 }
@@ -143,9 +172,8 @@ int finish_request(ising_server* srv, Request* r) {
   ISING_TRY(dev_alloc(ctx, full, r->inst.n));
   ISING_TRY(dev_alloc(ctx, E, 8));
   if (r->ds) {
-    double eg = 0.0;
     ISING_TRY(ising_ds_finish(r->ds));
-    ISING_TRY(ising_ds_result(r->ds, sG.as<int8_t>(), &eg, &r->stats, ISING_MEM_DEVICE));
+    ISING_TRY(ising_ds_result(r->ds, sG.as<int8_t>(), nullptr, &r->stats, ISING_MEM_DEVICE));
   }
   ISING_TRY(ising_reconstruct(ctx, r->pr, sG.as<int8_t>(), full.as<int8_t>(), ISING_MEM_DEVICE));
   ISING_TRY(energy_device(ctx, r->I, full.as<int8_t>(), 1, E.as<double>(), nullptr, nullptr));
@@ -154,6 +182,31 @@ int finish_request(ising_server* srv, Request* r) {
   ISING_CUDA(ctx, cudaMemcpyAsync(&r->energy, E.p, 8, cudaMemcpyDeviceToHost, ctx->stream));
   ISING_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   return ISING_OK;
+}
+
+// Time-to-target check: the full-instance energy of the best spins so far
+// (as finish_request would report them, without the final pass).
+int check_target(ising_server* srv, Request* r, bool* hit) {
+  ising_ctx* ctx = srv->slots[r->slot].get();
+  DevMem sG, full, E;
+  ISING_TRY(dev_alloc(ctx, sG, std::max<int64_t>(r->nG, 1)));
+  ISING_TRY(dev_alloc(ctx, full, r->inst.n));
+  ISING_TRY(dev_alloc(ctx, E, 8));
+  ISING_TRY(ising_ds_result(r->ds, sG.as<int8_t>(), nullptr, nullptr, ISING_MEM_DEVICE));
+  ISING_TRY(ising_reconstruct(ctx, r->pr, sG.as<int8_t>(), full.as<int8_t>(), ISING_MEM_DEVICE));
+  ISING_TRY(energy_device(ctx, r->I, full.as<int8_t>(), 1, E.as<double>(), nullptr, nullptr));
+  double e = 0.0;
+  ISING_CUDA(ctx, cudaMemcpyAsync(&e, E.p, 8, cudaMemcpyDeviceToHost, ctx->stream));
+  ISING_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  *hit = e <= r->target;
+  return ISING_OK;
+}
+
+// Records a request's failure with the message of the context that saw it.
+void set_failed(Request* r, int rc, const ising_ctx* ctx) {
+  if (r->status != ISING_OK) return;  // keep the first
+  r->status = rc;
+  r->error = ctx ? ctx->err : std::string("a CUDA call failed");
 }
 
 void release_request(ising_server* srv, Request* r) {
@@ -172,11 +225,74 @@ void release_request(ising_server* srv, Request* r) {
   r->ev = nullptr;
 }
 
-void worker_loop(ising_server* srv) {
+// Helper threads: the set-up of admitted requests and the finishing of
+// requests whose steps are done run here, so the worker keeps queueing chunks
+// meanwhile. A request is handed from thread to thread by its phase, under
+// the server's lock, so one thread at a time works on it.
+void helper_loop(ising_server* srv) {
+  cudaSetDevice(srv->parent->device);  // (as in worker_loop)
   std::unique_lock<std::mutex> lk(srv->mu);
   while (true) {
-    // 1. admission, in arrival order
-    std::vector<Request*> admitted;
+    srv->task_cv.wait(lk, [&] { return srv->helpers_stop || !srv->tasks.empty(); });
+    if (srv->tasks.empty()) break;  // stopping, nothing left
+    Request* r = srv->tasks.front();
+    srv->tasks.pop_front();
+    const bool setup = r->phase == kSettingUp;
+    lk.unlock();
+    const auto t0 = Clock::now();
+    double release_ms = 0.0;
+    ising_ctx* sctx = srv->slots[r->slot].get();
+    double part[3] = {0.0, 0.0, 0.0};
+    if (setup) {
+      int rc = start_request(srv, r, part);
+      if (rc != ISING_OK) {
+        set_failed(r, rc, sctx);
+        r->started = false;
+      }
+    } else {
+      if (r->status == ISING_OK) {
+        int rc = finish_request(srv, r);
+        if (rc != ISING_OK) set_failed(r, rc, sctx);
+      }
+      const auto t1 = Clock::now();
+      release_request(srv, r);
+      release_ms = ms_since(t1);
+    }
+    const double ms = ms_since(t0);
+    lk.lock();
+    if (setup) {
+      srv->st.setup_ms += ms;
+      srv->st.setup_upload_ms += part[0];
+      srv->st.setup_prune_ms += part[1];
+      srv->st.setup_session_ms += part[2];
+      r->phase = kReady;
+    } else {
+      srv->st.finish_ms += ms - release_ms;
+      srv->st.release_ms += release_ms;
+      srv->st.completed += 1;
+      r->t_done = srv->now_ms();
+      r->phase = kDone;
+      r->done = true;
+      srv->slot_busy[r->slot] = false;
+      srv->used -= r->footprint;
+      for (size_t k = 0; k < srv->active.size(); ++k)
+        if (srv->active[k] == r) {
+          srv->active.erase(srv->active.begin() + k);
+          break;
+        }
+      srv->done_cv.notify_all();
+    }
+    srv->cv.notify_all();  // a request is ready, or a slot and memory are free
+  }
+}
+
+void worker_loop(ising_server* srv) {
+  // the thread's current device (and context: some launches first encode
+  // tensor maps through the driver, which needs one)
+  cudaSetDevice(srv->parent->device);
+  std::unique_lock<std::mutex> lk(srv->mu);
+  while (true) {
+    // 1. admission, in arrival order; the set-up runs on a helper thread
     while (!srv->queue.empty() && (int)srv->active.size() < srv->cfg.max_active) {
       Request* r = srv->queue.front();
       if (srv->used + r->footprint > srv->cfg.budget_bytes) break;
@@ -187,38 +303,57 @@ void worker_loop(ising_server* srv) {
       r->slot = slot;
       r->t_admit = srv->now_ms();
       srv->used += r->footprint;
+      r->phase = kSettingUp;
       srv->active.push_back(r);
-      admitted.push_back(r);
+      srv->tasks.push_back(r);
+      srv->task_cv.notify_one();
     }
     if (srv->active.empty()) {
       if (srv->stop && srv->queue.empty()) break;
+      const auto tw = Clock::now();
       srv->cv.wait_for(lk, std::chrono::milliseconds(5));
+      srv->st.idle_ms += ms_since(tw);
       continue;
     }
-    std::vector<Request*> act = srv->active;
+    std::vector<Request*> act;
+    for (Request* r : srv->active)
+      if (r->phase == kReady) act.push_back(r);
     const int64_t chunk = srv->cfg.chunk_steps;
     lk.unlock();
-    for (Request* r : admitted) {
-      int rc = start_request(srv, r);
-      if (rc != ISING_OK) {
-        r->status = rc;
-        r->started = false;
-      }
-    }
-    // 2. every request whose last chunk has completed: next chunk, or finish
-    bool progressed = !admitted.empty();
-    std::vector<Request*> finished;
+    ising_server_stats rs{};  // this round's share, merged under the lock
+    auto tp = Clock::now();
+    // 2. every ready request whose last chunk has completed: next chunk, or
+    // (its steps done, its target met or a failure) hand it to a helper
+    bool progressed = false;
+    std::vector<Request*> finishing;
     std::map<uint64_t, std::vector<Request*>> groups;  // packable requests by kind
     for (Request* r : act) {
       if (r->in_flight) {
         const cudaError_t q = cudaEventQuery(r->ev);
         if (q == cudaErrorNotReady) continue;
         r->in_flight = false;
-        if (q != cudaSuccess) r->status = ISING_ECUDA;
+        ising_ctx* sctx = srv->slots[r->slot].get();
+        if (q != cudaSuccess) {
+          fail(sctx, ISING_ECUDA, "a chunk of steps failed: %s", cudaGetErrorString(q));
+          set_failed(r, ISING_ECUDA, sctx);
+        }
+        tp = Clock::now();
         if (r->status == ISING_OK && r->ds) {
           int rc = ds_conv_check(r->ds);  // convergence rule: have all restarts stopped?
-          if (rc != ISING_OK) r->status = rc;
+          if (rc != ISING_OK) set_failed(r, rc, sctx);
         }
+        if (r->status == ISING_OK && r->ds && r->has_target && r->ds->t < r->ds->T) {
+          bool hit = false;
+          int rc = check_target(srv, r, &hit);
+          rs.target_checks += 1;
+          if (rc != ISING_OK) {
+            set_failed(r, rc, sctx);
+          } else if (hit) {
+            r->reached = true;
+            r->ds->T = r->ds->t;  // finish without the remaining steps
+          }
+        }
+        rs.check_ms += ms_since(tp);
       }
       progressed = true;
       const bool steps_done =
@@ -229,20 +364,21 @@ void worker_loop(ising_server* srv) {
           continue;
         }
         const int64_t todo = std::min<int64_t>(chunk, r->ds->T - r->ds->t);
+        tp = Clock::now();
+        ising_ctx* sctx = srv->slots[r->slot].get();
         int rc = ds_advance(r->ds, todo);
-        if (rc == ISING_OK && cudaEventRecord(r->ev, srv->slots[r->slot]->stream) != cudaSuccess)
-          rc = ISING_ECUDA;
-        if (rc != ISING_OK) r->status = rc;
+        if (rc == ISING_OK) {
+          const cudaError_t e = cudaEventRecord(r->ev, sctx->stream);
+          if (e != cudaSuccess)
+            rc = fail(sctx, ISING_ECUDA, "cudaEventRecord failed: %s", cudaGetErrorString(e));
+        }
+        rs.advance_ms += ms_since(tp);
+        rs.chunks += 1;
+        if (rc != ISING_OK) set_failed(r, rc, sctx);
         else r->in_flight = true;
         continue;
       }
-      if (r->status == ISING_OK) {
-        int rc = finish_request(srv, r);
-        if (rc != ISING_OK) r->status = rc;
-      }
-      release_request(srv, r);
-      r->t_done = srv->now_ms();
-      finished.push_back(r);
+      finishing.push_back(r);
     }
     // 3. each group of ready dense tensor-core requests of one kind: one
     // packed chunk (their chunks end together, at the group's smallest
@@ -255,6 +391,7 @@ void worker_loop(ising_server* srv) {
       for (Request* r : grp) todo = std::min<int64_t>(todo, r->ds->T - r->ds->t);
       int rc = ISING_OK;
       ising_pack* pk = nullptr;
+      tp = Clock::now();
       auto it = srv->packs.find(ids);
       if (it != srv->packs.end()) {
         pk = it->second;
@@ -263,13 +400,21 @@ void worker_loop(ising_server* srv) {
         for (Request* r : grp) ds.push_back(r->ds);
         rc = ising_pack_create(srv->pack_ctx.get(), ds.data(), (int32_t)ds.size(), &pk);
         if (rc == ISING_OK) srv->packs[ids] = pk;
+        rs.packs_created += 1;
+        rs.pack_create_ms += ms_since(tp);
       }
       if (rc == ISING_OK) rc = pack_advance(pk, todo);
+      rs.advance_ms += ms_since(tp);
+      rs.pack_chunks += 1;
       for (Request* r : grp) {
         int rr = rc;
-        if (rr == ISING_OK && cudaEventRecord(r->ev, srv->pack_ctx->stream) != cudaSuccess)
-          rr = ISING_ECUDA;
-        if (rr != ISING_OK) r->status = rr;
+        if (rr == ISING_OK) {
+          const cudaError_t e = cudaEventRecord(r->ev, srv->pack_ctx->stream);
+          if (e != cudaSuccess)
+            rr = fail(srv->pack_ctx.get(), ISING_ECUDA, "cudaEventRecord failed: %s",
+                      cudaGetErrorString(e));
+        }
+        if (rr != ISING_OK) set_failed(r, rr, srv->pack_ctx.get());
         else r->in_flight = true;
       }
     }
@@ -294,19 +439,27 @@ void worker_loop(ising_server* srv) {
       }
     }
     lk.lock();
-    for (Request* r : finished) {
-      srv->slot_busy[r->slot] = false;
-      srv->used -= r->footprint;
-      r->done = true;
-      for (size_t k = 0; k < srv->active.size(); ++k)
-        if (srv->active[k] == r) {
-          srv->active.erase(srv->active.begin() + k);
-          break;
-        }
+    rs.rounds = progressed ? 1 : 0;
+    ising_server_stats& t = srv->st;
+    t.rounds += rs.rounds;
+    t.chunks += rs.chunks;
+    t.pack_chunks += rs.pack_chunks;
+    t.packs_created += rs.packs_created;
+    t.target_checks += rs.target_checks;
+    t.advance_ms += rs.advance_ms;
+    t.pack_create_ms += rs.pack_create_ms;
+    t.check_ms += rs.check_ms;
+    for (Request* r : finishing) {
+      r->phase = kFinishing;
+      srv->tasks.push_back(r);
     }
-    if (!finished.empty()) srv->done_cv.notify_all();
-    // nothing completed: wait a little (new submissions wake the worker)
-    if (!progressed) srv->cv.wait_for(lk, std::chrono::microseconds(50));
+    if (!finishing.empty()) srv->task_cv.notify_all();
+    // nothing completed: wait a little (submissions and helpers wake the worker)
+    if (!progressed) {
+      const auto tw = Clock::now();
+      srv->cv.wait_for(lk, std::chrono::microseconds(50));
+      srv->st.idle_ms += ms_since(tw);
+    }
   }
 }
 
@@ -321,6 +474,9 @@ void fill_result(const Request* r, ising_result* res) {
   res->t_submit_ms = r->t_submit;
   res->t_admit_ms = r->t_admit;
   res->t_done_ms = r->t_done;
+  res->steps_done = r->stats.steps_done;
+  res->reached = r->reached ? 1 : 0;
+  res->reserved = 0;
 }
 
 int copy_in(ising_ctx* ctx, void* dst, const void* src, size_t bytes, int mem) {
@@ -340,6 +496,7 @@ extern "C" int ising_server_create(ising_ctx* ctx, const ising_server_cfg* cfg,
   if (!ctx) return ISING_EINVAL;
   if (!cfg || !out) return fail(ctx, ISING_EINVAL, "cfg and out are required");
   if (cfg->max_active < 1 || cfg->max_active > 256 || cfg->chunk_steps < 1 ||
+      cfg->helper_threads < 0 || cfg->helper_threads > 16 ||
       (cfg->flags & ~ISING_SERVER_PACK) != 0)
     return fail(ctx, ISING_EINVAL, "bad server configuration");
   *out = nullptr;
@@ -373,13 +530,17 @@ extern "C" int ising_server_create(ising_ctx* ctx, const ising_server_cfg* cfg,
     }
     srv->pack_ctx = std::move(c);
   }
+  const int helpers = cfg->helper_threads > 0 ? cfg->helper_threads : 2;
+  for (int k = 0; k < helpers; ++k) srv->helpers.emplace_back(helper_loop, srv);
   srv->worker = std::thread(worker_loop, srv);
   *out = srv;
   return ISING_OK;
 }
 
-extern "C" int ising_server_submit(ising_server* srv, const ising_instance* inst,
-                                   const ising_ds_params* p, int prune_flags, uint64_t* req_id) {
+namespace {
+
+int submit_impl(ising_server* srv, const ising_instance* inst, const ising_ds_params* p,
+                int prune_flags, const double* target, uint64_t* req_id) {
   if (!srv) return ISING_EINVAL;
   ising_ctx* ctx = srv->parent;
   if (!inst || !p || !req_id) return fail(ctx, ISING_EINVAL, "inst, p and req_id are required");
@@ -418,6 +579,10 @@ extern "C" int ising_server_submit(ising_server* srv, const ising_instance* inst
   r->inst.h = inst->h ? r->h.data() : nullptr;
   r->p = *p;
   r->prune_flags = prune_flags;
+  if (target) {
+    r->has_target = true;
+    r->target = *target;
+  }
   std::lock_guard<std::mutex> g(srv->mu);
   if (srv->stop) return fail(ctx, ISING_EINVAL, "server is stopping");
   r->id = srv->next_id++;
@@ -426,6 +591,44 @@ extern "C" int ising_server_submit(ising_server* srv, const ising_instance* inst
   srv->queue.push_back(r.get());
   srv->all[r->id] = std::move(r);
   srv->cv.notify_all();
+  return ISING_OK;
+}
+
+}  // namespace
+
+extern "C" int ising_server_submit(ising_server* srv, const ising_instance* inst,
+                                   const ising_ds_params* p, int prune_flags, uint64_t* req_id) {
+  return submit_impl(srv, inst, p, prune_flags, nullptr, req_id);
+}
+
+extern "C" int ising_server_submit_target(ising_server* srv, const ising_instance* inst,
+                                          const ising_ds_params* p, int prune_flags,
+                                          double target_energy, uint64_t* req_id) {
+  if (srv && std::isnan(target_energy))
+    return fail(srv->parent, ISING_EINVAL, "target energy is NaN");
+  return submit_impl(srv, inst, p, prune_flags, &target_energy, req_id);
+}
+
+extern "C" int ising_server_error(ising_server* srv, uint64_t req_id, char* buf, int64_t len) {
+  if (!srv) return ISING_EINVAL;
+  if (!buf || len < 1) return fail(srv->parent, ISING_EINVAL, "buf and len >= 1 are required");
+  std::lock_guard<std::mutex> g(srv->mu);
+  auto it = srv->all.find(req_id);
+  if (it == srv->all.end()) return fail(srv->parent, ISING_EINVAL, "unknown request id");
+  const Request* r = it->second.get();
+  const std::string msg = r->done ? r->error : std::string();
+  const size_t k = std::min<size_t>(msg.size(), (size_t)(len - 1));
+  memcpy(buf, msg.data(), k);
+  buf[k] = 0;
+  return ISING_OK;
+}
+
+extern "C" int ising_server_stats_get(ising_server* srv, ising_server_stats* out) {
+  if (!srv) return ISING_EINVAL;
+  if (!out) return fail(srv->parent, ISING_EINVAL, "out is required");
+  std::lock_guard<std::mutex> g(srv->mu);
+  *out = srv->st;
+  out->elapsed_ms = srv->now_ms();
   return ISING_OK;
 }
 
@@ -479,6 +682,13 @@ extern "C" int ising_server_destroy(ising_server* srv) {
     srv->cv.notify_all();
   }
   if (srv->worker.joinable()) srv->worker.join();
+  {
+    std::lock_guard<std::mutex> g(srv->mu);
+    srv->helpers_stop = true;
+    srv->task_cv.notify_all();
+  }
+  for (auto& h : srv->helpers)
+    if (h.joinable()) h.join();
   for (auto& kv : srv->packs) ising_pack_destroy(kv.second);
   srv->packs.clear();
   if (srv->pack_ctx) {

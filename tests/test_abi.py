@@ -45,7 +45,7 @@ def test_struct_layouts_match_the_header(tmp_path):
         pytest.skip("no C compiler")
     structs = {"ising_instance": L.Instance, "ising_ds_params": L.DSParams,
                "ising_ds_stats": L.DSStats, "ising_server_cfg": L.ServerCfg,
-               "ising_result": L.Result}
+               "ising_result": L.Result, "ising_server_stats": L.ServerStats}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "ising_ds.h"',
              'int main(void) {']
     for cname, cls in structs.items():

@@ -76,3 +76,41 @@ def test_oversized_request_is_refused_and_unknown_ids_are_errors(gpu_ctx):
     with pytest.raises(api.IsingError):
         srv.poll(12345)
     srv.close()
+
+
+@pytest.mark.parametrize("pack", [False, True])
+def test_time_to_target_queries(gpu_ctx, pack):
+    """ising_server_submit_target: a target every spin vector meets stops the
+    request after its first chunk; an unreachable one runs every step and
+    gives the plain request's result; a target between the two stops it at
+    the first chunk whose best meets it, with fewer steps and an energy at or
+    below the target (exact on the full instance)."""
+    inst = synth.sk_dense(300, 9, 1 / math.sqrt(300), np.float32, h_std=0.3)
+    kw = dict(restarts=256, steps=400, seed=5, precision="fp8")
+    chunk = 50
+    plain = api.solve(gpu_ctx, inst, **kw)
+    srv = api.Server(gpu_ctx, budget_bytes=8 << 30, max_active=4, chunk_steps=chunk, pack=pack)
+    # the plain run's energy after its first chunk of steps bounds a target it meets early
+    s = api.Session(gpu_ctx, inst, streaming=True, **kw)
+    s.run(2 * chunk)
+    early = s.result()["best_energy"]
+    s.close()
+    mid = early + 1e-9 * abs(early)
+    ids = [srv.submit(inst, target=math.inf, **kw), srv.submit(inst, target=-math.inf, **kw),
+           srv.submit(inst, target=mid, **kw)]
+    r_inf, r_none, r_mid = [srv.wait(r, timeout=300) for r in ids]
+    st = srv.stats()
+    srv.close()
+    for r in (r_inf, r_none, r_mid):
+        assert r["status"] == 0 and r["done"] == 1, r["error"]
+        e = ising.energy(inst, r["best_spins"].astype(np.float64))
+        assert r["best_energy"] == pytest.approx(float(e), rel=1e-12, abs=1e-9)
+    assert r_inf["reached"] == 1 and r_inf["steps_done"] == chunk
+    assert r_none["reached"] == 0 and r_none["steps_done"] == kw["steps"]
+    np.testing.assert_array_equal(r_none["best_spins"], plain["best_spins"])
+    assert r_none["best_energy"] == plain["best_energy"]
+    assert r_mid["reached"] == 1 and r_mid["best_energy"] <= mid
+    assert r_mid["steps_done"] <= 2 * chunk
+    assert st["completed"] == 3 and st["target_checks"] >= 1 + kw["steps"] // chunk
+    for key in ("setup_ms", "advance_ms", "check_ms", "finish_ms", "release_ms", "idle_ms"):
+        assert 0.0 <= st[key] <= st["elapsed_ms"]
