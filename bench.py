@@ -23,6 +23,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -335,40 +336,25 @@ def cpu_baseline(a, B, T):
 
 # ----------------------------------------------------------------- time to target
 
-def exact_best(ctx, dinst, integer, s):
-    """The lowest exact energy among a session's per-restart bests: exact
-    already for integer couplings; otherwise the restarts whose tracked
-    (FP32-partial) best lies within 1e-4 |E_min| of the minimum (at most 16)
-    are re-evaluated in FP64 on the device."""
-    import torch
-    from paper_2312_05837_gb300 import api
-    E, _, sp = s.restart_best(device=True)
-    if integer:
-        return float(E.min().item())
-    emin = E.min()
-    cand = torch.nonzero(E <= emin + 1e-4 * emin.abs()).flatten()[:16]
-    return float(api.energy(ctx, dinst, sp[cand].contiguous()).min().item())
-
-
-def run_checked(ctx, dinst, integer, B, T, seed, prec, chunk, target=None, t0_ms=0.0):
-    """One session of T steps in chunks of `chunk` steps, the exact best so
-    far taken after each chunk; stops early once it is <= target. Returns
-    [(wall ms of steps + checks, cumulative from t0_ms, best)], the result."""
+def run_checked(ctx, dinst, integer, B, T, seed, prec, chunk):
+    """One session of T steps in chunks of `chunk` steps, the best so far
+    taken after each chunk as the session reports it (ising_ds_result: exact
+    for integer couplings, otherwise the near-best restarts re-evaluated in
+    FP64). Returns [(cumulative wall ms of steps + checks, best)], the
+    result."""
     import torch
     from paper_2312_05837_gb300 import api
     s = api.Session(ctx, dinst, restarts=B, steps=T, seed=seed, precision=prec)
     torch.cuda.synchronize()
-    done, ms, h = 0, t0_ms, []
+    done, ms, h = 0, 0.0, []
     while done < T:
         k = min(chunk, T - done)
         w0 = time.perf_counter()
         s.run(k)
         done += k
-        best = exact_best(ctx, dinst, integer, s)
+        best = float(s.result()["best_energy"])
         ms += 1e3 * (time.perf_counter() - w0)
         h.append((ms, best))
-        if target is not None and best <= target:
-            break
     s.finish()
     res = s.result()
     s.close()
@@ -396,35 +382,85 @@ def precision_runs(ctx, dinst, integer, n, B, T, seed, forms, chunk):
     return out, hist["fp32"]
 
 
-def time_to_target(ctx, dinst, integer, B, T, seed, plain_hist, fast_forms, chunk, budget_s=20.0):
-    """Time to the plain FP32 form's final best E* (wall time of steps and
-    exact checks). The plain form's time is when its own run (seed `seed`)
-    first reached E*. Each fast form runs the same configuration (B
-    restarts, T steps) in batches: the first with the plain run's seed, then
-    fresh seeds, each stopped as soon as its best reaches E*, until E* is
-    reached or `budget_s` seconds have gone by. With integer couplings the
-    exact fast form computes the plain form's arithmetic, so its first batch
-    follows the same trajectory."""
-    target = plain_hist[-1][1]
-    t_plain = next(ms for ms, e in plain_hist if e <= target)
-    out = {"target_energy": target, "plain_fp32_ms": t_plain,
-           "plain_fp32_full_run_ms": plain_hist[-1][0], "restarts": B, "steps": T,
-           "chunk_steps": chunk, "budget_s": budget_s, "forms": {}}
-    for prec in fast_forms:
-        ms, batches, hit = 0.0, 0, None
-        while ms < 1e3 * budget_s:
-            h, _ = run_checked(ctx, dinst, integer, B, T, seed if batches == 0 else 1000 + batches,
-                               prec, chunk, target=target, t0_ms=ms)
-            batches += 1
-            ms = h[-1][0]
-            if h[-1][1] <= target:
-                hit = ms
-                break
-        out["forms"][prec] = {"time_ms": hit, "batches": batches,
-                              "speedup": (t_plain / hit) if hit else None}
-    out["timing"] = ("wall time of the steps and of the exact check after each chunk (integer "
-                     "couplings: tracked energies are exact; otherwise FP64 re-evaluation of the "
-                     "near-best restarts on the device)")
+def served_time_to_target(ctx, inst, B, T, seed, target, prec, chunk, batch, budget_s, pack,
+                          max_rounds=1000):
+    """Wall time from the first submission of (B restarts, T steps) requests
+    to the server until one of them returns a result at or below `target`
+    (ising_server_submit_target: the full-instance energy of the request's
+    best spins is evaluated exactly after every chunk of `chunk` steps, and
+    the request finishes as soon as it meets the target). `batch` requests
+    with different seeds (the first `seed`) are submitted together and run
+    side by side (packed when `pack`); once one meets the target the others
+    are cancelled. Further batches (fresh seeds) follow until the target is
+    met, `budget_s` has passed or `max_rounds` batches have run. The timed
+    region holds everything a client waits for: the instance copies at
+    submission, upload, pruning, set-up, steps, checks, finishing."""
+    from paper_2312_05837_gb300 import api
+    srv = api.Server(ctx, budget_bytes=120 << 30, max_active=max(batch, 1), chunk_steps=chunk,
+                     pack=pack)
+    t0 = time.perf_counter()
+    hit, rounds, steps = None, 0, None
+    while hit is None and rounds < max_rounds and time.perf_counter() - t0 < budget_s:
+        seeds = [seed + k if rounds == 0 else seed + 1000 * rounds + k for k in range(batch)]
+        pending = [srv.submit(inst, restarts=B, steps=T, seed=sd, precision=prec, target=target)
+                   for sd in seeds]
+        while pending:
+            for rid in list(pending):
+                r = srv.poll(rid)
+                if not r["done"]:
+                    continue
+                pending.remove(rid)
+                if r["status"] != 0:
+                    srv.close()
+                    raise RuntimeError(f"time to target: request failed: {r['error']}")
+                if r["reached"] and hit is None:
+                    hit = time.perf_counter() - t0
+                    steps = r["steps_done"]
+                    for other in pending:
+                        srv.cancel(other)
+            time.sleep(2e-4)
+        rounds += 1
+    srv.close()
+    return {"time_ms": 1e3 * hit if hit is not None else None, "rounds": rounds, "batch": batch,
+            "steps_to_target": steps}
+
+
+def time_to_target(ctx, inst, integer, B, T, seed, plain_hist, fast_forms, chunk, budget_s=20.0):
+    """Time to the plain FP32 form's best energy E* (its final best over the
+    configuration's run with seed `seed`), measured on the served form
+    against the plain form served the same way (served_time_to_target):
+    (1) within the tolerance the reduced-precision forms are held to, E* +
+    0.005 |E*| (one request each, seed `seed`); (2) E* itself. The plain
+    form reaches E* in its own run by construction; the served mixed-
+    precision forms follow other trajectories (other operand roundings), so
+    for (2) they submit batches of 4 seeds at once until one meets it. With
+    integer couplings the exact fast form computes the plain arithmetic, so
+    one request each suffices."""
+    E = plain_hist[-1][1]
+    tol = 0.005
+    out = {"target_energy": E, "tolerance": tol, "tolerance_target": E + tol * abs(E),
+           "restarts": B, "steps": T, "chunk_steps": chunk,
+           "plain_fp32_session_ms_to_E": next(ms for ms, e in plain_hist if e <= E),
+           "plain_fp32_full_run_ms": plain_hist[-1][0],
+           "timing": ("wall time from submission to the returned result through the server "
+                      "(ising_server_submit_target), exact energy checks every chunk_steps "
+                      "steps; plain FP32 served alone (CUDA-core SGEMM / sparse kernel), fast "
+                      "forms packed")}
+    # untimed: first launches of each form's kernels and its tile autotuning
+    for prec in ["fp32"] + list(fast_forms):
+        served_time_to_target(ctx, inst, B, 2 * chunk, seed, -math.inf, prec, chunk, 1,
+                              budget_s=1e9, pack=prec != "fp32", max_rounds=1)
+    for label, tgt, batch in [("within_tolerance", out["tolerance_target"], 1), ("exact", E, 4)]:
+        b = 1 if integer else batch
+        plain = served_time_to_target(ctx, inst, B, T, seed, tgt, "fp32", chunk, 1,
+                                      budget_s=1e9, pack=False, max_rounds=1)
+        row = {"plain_fp32": plain, "forms": {}}
+        for prec in fast_forms:
+            f = served_time_to_target(ctx, inst, B, T, seed, tgt, prec, chunk, b, budget_s, True)
+            if plain["time_ms"] and f["time_ms"]:
+                f["speedup"] = plain["time_ms"] / f["time_ms"]
+            row["forms"][prec] = f
+        out[label] = row
     return out
 
 
@@ -432,7 +468,8 @@ def time_to_target(ctx, dinst, integer, B, T, seed, plain_hist, fast_forms, chun
 
 def serve_stream(ctx, reqs, B, T, precision_dense, pack, max_active, budget, chunk=250):
     """Submits the requests at their arrival times to a server and waits for
-    all; returns per-request results (latency = done - submit)."""
+    all; returns per-request results (latency = done - submit) and the
+    server's host-time stats."""
     from paper_2312_05837_gb300 import api
     srv = api.Server(ctx, budget_bytes=budget, max_active=max_active, chunk_steps=chunk, pack=pack)
     t0 = time.perf_counter()
@@ -444,8 +481,9 @@ def serve_stream(ctx, reqs, B, T, precision_dense, pack, max_active, budget, chu
         prec = precision_dense if inst.layout == "dense" else "auto"
         ids.append(srv.submit(inst, restarts=B, steps=T, seed=k, precision=prec))
     res = [srv.wait(r, timeout=3600) for r in ids]
+    st = srv.stats()
     srv.close()
-    return res
+    return res, st
 
 
 def latency_summary(res, rate):
@@ -482,14 +520,15 @@ def serving(ctx, count=1000, rate=200.0, n_max=8192, B=256, T=2000, seed=5, plai
     small = [(0.0, inst) for _, inst in sorted(reqs, key=lambda r: r[1].n)[:4]]
     serve_stream(ctx, small, B, 4, "fp8", True, 4, budget)
     serve_stream(ctx, small, B, 4, "fp32", False, 1, budget)
-    served = serve_stream(ctx, reqs, B, T, "fp8", True, 32, budget)
-    plain = serve_stream(ctx, reqs[:plain_count], B, T, "fp32", False, 1, budget)
+    served, st = serve_stream(ctx, reqs, B, T, "fp8", True, 32, budget)
+    plain, _ = serve_stream(ctx, reqs[:plain_count], B, T, "fp32", False, 1, budget)
     out = {"requests": count, "rate_per_s": rate, "n_range": [64, n_max], "restarts": B,
            "steps": T, "budget_gb": 120,
            "mix": "50% dense SK J~N(0,1/N) h~N(0,0.1), 50% sparse ER deg 8 +-1 (24 pooled sizes "
                   "per kind, N drawn log-uniformly, nearest pooled size)",
            "served": {**latency_summary(served, rate), "form": "packed launches, dense in "
-                      "row-scaled E4M3 + FP64 final energy, max_active 32, chunk 250"},
+                      "row-scaled E4M3 + FP64 final energy, max_active 32, chunk 250, 2 helper "
+                      "threads", "server_host_ms": {k: round(v, 1) for k, v in st.items()}},
            "served_first_%d" % plain_count: latency_summary(served[:plain_count], rate),
            "plain_fp32_per_request_live": {**latency_summary(plain, rate),
                                            "form": "one request at a time, dense on the "
@@ -755,11 +794,11 @@ def main():
         sweep, plain_hist = precision_runs(ctx, dinst, bool(inst.integer), inst.n, B, T, seed=3,
                                            forms=forms, chunk=chunk)
         line["precision_sweep"] = sweep
-        line["time_to_target"] = {name: time_to_target(
-            ctx, dinst, bool(inst.integer), B, T, 3, plain_hist,
-            ["fp8", "tc"] if not inst.integer else ["auto"], chunk)}
         del dinst
         torch.cuda.empty_cache()
+        line["time_to_target"] = {name: time_to_target(
+            ctx, hinst, bool(inst.integer), B, T, 3, plain_hist,
+            ["fp8", "tc"] if not inst.integer else ["auto"], chunk)}
         if name != "er2000":
             # the integer max-cut workload: exact E4M3 against plain FP32
             w_name, wB, wT = WORKLOADS["er2000"]
@@ -767,10 +806,10 @@ def main():
             wd = device_instance(winst, torch)
             _, w_hist = precision_runs(ctx, wd, True, winst.n, wB, wT, seed=3, forms=["fp32"],
                                        chunk=50)
-            line["time_to_target"]["er2000"] = time_to_target(ctx, wd, True, wB, wT, 3, w_hist,
-                                                              ["auto"], 50)
             del wd
             torch.cuda.empty_cache()
+            line["time_to_target"]["er2000"] = time_to_target(
+                ctx, pinned_instance(winst, torch), True, wB, wT, 3, w_hist, ["auto"], 50)
         line["early_retirement"] = early_retirement(ctx)
         line["serving"] = serving(ctx)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:

@@ -444,7 +444,7 @@ typedef struct ising_result {
   double t_done_ms;
   int64_t steps_done;    /* domain-selection steps the request ran */
   int32_t reached;       /* submitted with a target: 1 if best_energy <= target */
-  int32_t reserved;
+  int32_t cancelled;     /* 1 if ising_server_cancel ended it early */
 } ising_result;
 
 /* Creates the server on the context's device; the context must outlive it. */
@@ -460,8 +460,8 @@ int ising_server_submit(ising_server* srv, const ising_instance* inst, const isi
  * near-best re-evaluated exactly as in ising_ds_result, reconstructed, then
  * ising_energy) and finishes the request as soon as it is <= target_energy,
  * without running its remaining steps (ising_result.steps_done tells how
- * many ran, .reached whether the target was met). Otherwise the request
- * runs all its steps. The check synchronises the request's stream once per
+ * many ran, .reached whether the target was met, by a check or by the
+ * final result). Otherwise the request runs all its steps. The check synchronises the request's stream once per
  * chunk. */
 int ising_server_submit_target(ising_server* srv, const ising_instance* inst,
                                const ising_ds_params* p, int prune_flags, double target_energy,
@@ -473,6 +473,11 @@ int ising_server_poll(ising_server* srv, uint64_t req_id, ising_result* res, int
 /* Blocks until the request is done or `timeout_s` passes (ISING_ETIMEOUT). */
 int ising_server_wait(ising_server* srv, uint64_t req_id, double timeout_s, ising_result* res,
                       int8_t* spins);
+/* Ends a request early: an admitted one finishes at the end of its current
+ * chunk with the best of the steps run so far (its result as usual, with
+ * cancelled = 1); a queued one is dropped and done at once, without spins
+ * (best_energy NaN, steps_done 0). No effect on a finished request. */
+int ising_server_cancel(ising_server* srv, uint64_t req_id);
 /* The message of a finished request's failure (empty when it succeeded or
  * is not done), truncated to len - 1 bytes and NUL-terminated. */
 int ising_server_error(ising_server* srv, uint64_t req_id, char* buf, int64_t len);

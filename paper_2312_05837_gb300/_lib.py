@@ -60,7 +60,7 @@ class Result(ctypes.Structure):
                 ("best_energy", c_double), ("best_restart", c_int64), ("best_step", c_int64),
                 ("footprint", c_int64), ("t_submit_ms", c_double), ("t_admit_ms", c_double),
                 ("t_done_ms", c_double), ("steps_done", c_int64), ("reached", c_int32),
-                ("reserved", c_int32)]
+                ("cancelled", c_int32)]
 
 
 class ServerStats(ctypes.Structure):
@@ -124,6 +124,7 @@ _PROTOS = {
                                            c_double, POINTER(c_uint64)]),
     "ising_server_stats_get": (c_int, [c_void_p, POINTER(ServerStats)]),
     "ising_server_error": (c_int, [c_void_p, c_uint64, c_char_p, c_int64]),
+    "ising_server_cancel": (c_int, [c_void_p, c_uint64]),
     "ising_server_poll": (c_int, [c_void_p, c_uint64, POINTER(Result), c_void_p]),
     "ising_server_wait": (c_int, [c_void_p, c_uint64, c_double, POINTER(Result), c_void_p]),
     "ising_server_release": (c_int, [c_void_p, c_uint64]),

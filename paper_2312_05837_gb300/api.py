@@ -240,7 +240,8 @@ class Server:
 
     def _result(self, res, rid, spins):
         d = {f: getattr(res, f) for f, _ in L.Result._fields_}
-        d["best_spins"] = spins if res.done else None
+        # (a request cancelled before admission has no spins)
+        d["best_spins"] = spins if res.done and res.best_energy == res.best_energy else None
         d["error"] = ""
         if res.done and res.status != 0:
             buf = ctypes.create_string_buffer(512)
@@ -260,6 +261,10 @@ class Server:
         self.ctx.check(self.ctx.lib.ising_server_wait(self.handle, rid, float(timeout), byref(res),
                                                       _ptr(spins)))
         return self._result(res, rid, spins)
+
+    def cancel(self, rid: int):
+        """Ends a request early (ising_server_cancel)."""
+        self.ctx.check(self.ctx.lib.ising_server_cancel(self.handle, rid))
 
     def release(self, rid: int):
         self.ctx.check(self.ctx.lib.ising_server_release(self.handle, rid))

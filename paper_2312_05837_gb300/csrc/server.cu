@@ -22,6 +22,7 @@
 #include "ds_internal.cuh"
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <chrono>
 #include <condition_variable>
@@ -54,6 +55,8 @@ struct Request {
   bool has_target = false;  // time-to-target query
   double target = 0.0;
   bool reached = false;
+  std::atomic<bool> cancel{false};  // set by ising_server_cancel
+  bool cancelled = false;
   double t_submit = 0, t_admit = 0, t_done = 0;
   int slot = -1;
   int phase = 0;  // kQueued, kSettingUp, kReady, kFinishing, kDone
@@ -253,6 +256,8 @@ void helper_loop(ising_server* srv) {
       if (r->status == ISING_OK) {
         int rc = finish_request(srv, r);
         if (rc != ISING_OK) set_failed(r, rc, sctx);
+        // a target met by the steps of the last chunk or the final pass
+        else if (r->has_target && r->energy <= r->target) r->reached = true;
       }
       const auto t1 = Clock::now();
       release_request(srv, r);
@@ -356,6 +361,10 @@ void worker_loop(ising_server* srv) {
         rs.check_ms += ms_since(tp);
       }
       progressed = true;
+      if (r->cancel.load() && r->ds && r->ds->t < r->ds->T) {
+        r->cancelled = true;
+        r->ds->T = r->ds->t;  // finish with the steps run so far
+      }
       const bool steps_done =
           r->status != ISING_OK || !r->ds || r->ds->t >= r->ds->T || r->ds->conv_all;
       if (!steps_done) {
@@ -476,7 +485,7 @@ void fill_result(const Request* r, ising_result* res) {
   res->t_done_ms = r->t_done;
   res->steps_done = r->stats.steps_done;
   res->reached = r->reached ? 1 : 0;
-  res->reserved = 0;
+  res->cancelled = r->cancelled ? 1 : 0;
 }
 
 int copy_in(ising_ctx* ctx, void* dst, const void* src, size_t bytes, int mem) {
@@ -607,6 +616,33 @@ extern "C" int ising_server_submit_target(ising_server* srv, const ising_instanc
   if (srv && std::isnan(target_energy))
     return fail(srv->parent, ISING_EINVAL, "target energy is NaN");
   return submit_impl(srv, inst, p, prune_flags, &target_energy, req_id);
+}
+
+extern "C" int ising_server_cancel(ising_server* srv, uint64_t req_id) {
+  if (!srv) return ISING_EINVAL;
+  std::lock_guard<std::mutex> g(srv->mu);
+  auto it = srv->all.find(req_id);
+  if (it == srv->all.end()) return fail(srv->parent, ISING_EINVAL, "unknown request id");
+  Request* r = it->second.get();
+  if (r->done) return ISING_OK;
+  if (r->phase == kQueued) {
+    // not admitted yet: dropped, done at once without a result
+    for (size_t k = 0; k < srv->queue.size(); ++k)
+      if (srv->queue[k] == r) {
+        srv->queue.erase(srv->queue.begin() + k);
+        break;
+      }
+    r->cancelled = true;
+    r->energy = std::nan("");
+    r->t_admit = r->t_done = srv->now_ms();
+    r->phase = kDone;
+    r->done = true;
+    srv->done_cv.notify_all();
+    return ISING_OK;
+  }
+  r->cancel.store(true);
+  srv->cv.notify_all();
+  return ISING_OK;
 }
 
 extern "C" int ising_server_error(ising_server* srv, uint64_t req_id, char* buf, int64_t len) {

@@ -3,6 +3,7 @@ result equals the same request solved alone, admission follows the memory
 budget, and oversized requests are refused."""
 
 import math
+import time
 
 import numpy as np
 import pytest
@@ -114,3 +115,28 @@ def test_time_to_target_queries(gpu_ctx, pack):
     assert st["completed"] == 3 and st["target_checks"] >= 1 + kw["steps"] // chunk
     for key in ("setup_ms", "advance_ms", "check_ms", "finish_ms", "release_ms", "idle_ms"):
         assert 0.0 <= st[key] <= st["elapsed_ms"]
+
+
+def test_cancel(gpu_ctx):
+    """ising_server_cancel: an admitted request ends at the end of its chunk
+    with the best of the steps it ran (an exact result, cancelled = 1); a
+    queued one is dropped at once without spins; a finished one is left as
+    it is."""
+    inst = synth.er_dense(400, 3, p=0.05, weights="pm1")
+    srv = api.Server(gpu_ctx, budget_bytes=8 << 30, max_active=1, chunk_steps=20, pack=False)
+    a = srv.submit(inst, restarts=256, steps=1000000, seed=1)
+    b = srv.submit(inst, restarts=256, steps=100, seed=2)
+    srv.cancel(b)  # still queued behind a (one slot)
+    rb = srv.wait(b, timeout=60)
+    assert rb["done"] == 1 and rb["cancelled"] == 1 and rb["steps_done"] == 0
+    assert rb["best_spins"] is None and math.isnan(rb["best_energy"])
+    time.sleep(0.3)  # (set up, and running its chunks)
+    srv.cancel(a)
+    ra = srv.wait(a, timeout=120)
+    assert ra["status"] == 0 and ra["cancelled"] == 1 and 0 < ra["steps_done"] < 1000000
+    assert ra["steps_done"] % 20 == 0
+    e = ising.energy(inst, ra["best_spins"].astype(np.float64))
+    assert ra["best_energy"] == float(e)
+    srv.cancel(a)  # finished: nothing happens
+    assert srv.poll(a)["steps_done"] == ra["steps_done"]
+    srv.close()
