@@ -38,6 +38,33 @@ namespace {
 
 constexpr int64_t kPackGraphSteps = 25;
 
+// The pack's restart-tile width: the least padding over all members (tiles
+// of bn restarts hold ceil(B / bn) x bn columns of a member's B), then,
+// among the widths that pad least, the widest whose tiles still give every
+// SM one (wider tiles issue fewer, longer MMAs), else the narrowest.
+int pack_width(const ising_ctx* ctx, ising_ds* const* s, int count) {
+  const int widths[4] = {256, 224, 128, 64};
+  double pad[4];
+  int64_t tiles[4];
+  double least = 1e300;
+  for (int w = 0; w < 4; ++w) {
+    pad[w] = 0.0;
+    tiles[w] = 0;
+    for (int k = 0; k < count; ++k) {
+      const int64_t rt = ceil_div_i(s[k]->n, 128), ct = ceil_div_i(s[k]->B, widths[w]);
+      pad[w] += (double)rt * (double)(ct * widths[w] - s[k]->B);
+      tiles[w] += rt * ct;
+    }
+    least = std::min(least, pad[w]);
+  }
+  int pick = -1;
+  for (int w = 0; w < 4 && pick < 0; ++w)  // widest first
+    if (pad[w] <= least && tiles[w] >= ctx->sm_count) pick = w;
+  for (int w = 3; w >= 0 && pick < 0; --w)  // narrowest first
+    if (pad[w] <= least) pick = w;
+  return widths[pick];
+}
+
 int pack_step(ising_pack* pk) {
   ising_ctx* ctx = pk->ctx;
   int* err = reinterpret_cast<int*>(pk->words.as<unsigned long long>() + 1);
@@ -170,7 +197,7 @@ extern "C" int ising_pack_create(ising_ctx* ctx, ising_ds* const* sessions, int3
   pk->ctx = ctx;
   pk->members.assign(sessions, sessions + count);
   pk->key = key;
-  pk->bn = tc_bn(sessions[0]);
+  pk->bn = pack_width(ctx, sessions, count);
   pk->spin_kind = sessions[0]->spin_kind;
   int rc = [&]() -> int {
     ISING_CUDA(ctx, cudaEventCreateWithFlags(&pk->ev, cudaEventDisableTiming));
@@ -181,7 +208,7 @@ extern "C" int ising_pack_create(ising_ctx* ctx, ising_ds* const* sessions, int3
     std::vector<int64_t> rstart(count + 1, 0);
     for (int k = 0; k < count; ++k) {
       ising_ds* ds = sessions[k];
-      // one tile width for all (the first member's): the results do not depend on it
+      // one tile width for all: the results do not depend on it
       ISING_TRY(tc_set_bn(ds, pk->bn));
       ISING_TRY(tc_pack_entry(ds, ent.data() + eb * k));
       start[k + 1] = start[k] + ceil_div_i(ds->n, 128) * ceil_div_i(ds->B, pk->bn);

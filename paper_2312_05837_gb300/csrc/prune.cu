@@ -43,91 +43,184 @@ struct PruneDev {
   double* jkp;    // coupling to it
   double* b;      // paper-form field
   double* contrib;
-  unsigned int* count;
+  unsigned int* count;  // spins fixed this round
+  unsigned int* nD;     // spins determined this round
+  unsigned int* nS;     // spins semi-determined this round
   double cq, twocq, twocq_abs;
 };
 
+constexpr unsigned kFull = 0xffffffffu;
+
+// Row kernels: one warp per row, lane l holding edge e0 + l of each chunk of
+// 32 (coalesced loads). Sums whose decisions depend on their rounding are
+// formed in row order: the relevant edges of a chunk are flagged by ballot
+// and added one after another from lane 0 up, so every lane holds exactly
+// the sequential sum.
+__device__ __forceinline__ double add_in_order(double acc, double term, unsigned mask) {
+  while (mask) {
+    const int k = __ffs(mask) - 1;
+    acc = __dadd_rn(acc, __shfl_sync(kFull, term, k));
+    mask &= mask - 1;
+  }
+  return acc;
+}
+
+struct WarpRows {
+  int lane;
+  int64_t first, stride;
+  __device__ WarpRows() {
+    lane = threadIdx.x & 31;
+    first = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    stride = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  }
+};
+
+// Determined spins: 2|cQ| S_i < |b_i|. The lanes' partial sums, reduced by a
+// butterfly (every lane gets the same value), give S in some order; any
+// order of a sum of m nonnegative terms lies within gamma_(m-1) S of S, so
+// the comparison is certain unless 2|cQ| S is within that bound of |b_i|,
+// and only then is S summed again in row order.
 __global__ void k_determined(PruneDev P) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P.n;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  const WarpRows w;
+  for (int64_t i = w.first; i < P.n; i += w.stride) {
     uint8_t d = 0;
     if (P.alive[i]) {
-      double S = 0.0;
-      for (int e = P.rowptr[i]; e < P.rowptr[i + 1]; ++e) {
-        double x = P.val[e];
-        if (x != 0.0 && P.alive[P.col[e]]) S = __dadd_rn(S, fabs(x));
+      const int e0 = P.rowptr[i], e1 = P.rowptr[i + 1];
+      double s = 0.0;
+      for (int e = e0 + w.lane; e < e1; e += 32) {
+        const double x = P.val[e];
+        if (x != 0.0 && P.alive[P.col[e]]) s = __dadd_rn(s, fabs(x));
       }
-      d = __dmul_rn(P.twocq_abs, S) < fabs(P.b[i]);
-      if (d) P.value[i] = P.b[i] < 0.0 ? 1 : -1;
+      for (int o = 16; o; o >>= 1) s = __dadd_rn(s, __shfl_xor_sync(kFull, s, o));
+      const double bi = fabs(P.b[i]);
+      const double eps = (4.0 * (double)(e1 - e0) + 16.0) * 0x1p-53;
+      const double ts = __dmul_rn(P.twocq_abs, s);
+      if (__dmul_rn(ts, 1.0 - eps) > bi) {
+        d = 0;
+      } else if (__dmul_rn(ts, 1.0 + eps) < bi) {
+        d = 1;
+      } else {
+        double S = 0.0;
+        for (int c = e0; c < e1; c += 32) {
+          const int e = c + w.lane;
+          double term = 0.0;
+          if (e < e1) {
+            const double x = P.val[e];
+            if (x != 0.0 && P.alive[P.col[e]]) term = fabs(x);
+          }
+          S = add_in_order(S, term, __ballot_sync(kFull, term != 0.0));
+        }
+        d = __dmul_rn(P.twocq_abs, S) < bi;
+      }
     }
-    P.isD[i] = d;
+    if (w.lane == 0) {
+      if (d) {
+        P.value[i] = P.b[i] < 0.0 ? 1 : -1;
+        atomicAdd(P.nD, 1u);
+      }
+      P.isD[i] = d;
+    }
   }
 }
 
 __global__ void k_fold_determined(PruneDev P, int r) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P.n;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  if (*P.nD == 0) return;  // nothing determined this round
+  const WarpRows w;
+  for (int64_t i = w.first; i < P.n; i += w.stride) {
     if (!P.alive[i]) continue;
+    const int e0 = P.rowptr[i], e1 = P.rowptr[i + 1];
     if (P.isD[i]) {
       // own share of the constant: b_i s_i + sum over determined neighbours of cQ J_ij s_i s_j
       const double si = (double)P.value[i];
       double c = __dmul_rn(P.b[i], si);
-      for (int e = P.rowptr[i]; e < P.rowptr[i + 1]; ++e) {
-        int32_t j = P.col[e];
-        double x = P.val[e];
-        if (x != 0.0 && P.isD[j])
-          c = __dadd_rn(c, __dmul_rn(__dmul_rn(__dmul_rn(P.cq, x), si), (double)P.value[j]));
+      for (int cb = e0; cb < e1; cb += 32) {
+        const int e = cb + w.lane;
+        double term = 0.0;
+        bool rel = false;
+        if (e < e1) {
+          const int32_t j = P.col[e];
+          const double x = P.val[e];
+          if (x != 0.0 && P.isD[j]) {
+            rel = true;
+            term = __dmul_rn(__dmul_rn(__dmul_rn(P.cq, x), si), (double)P.value[j]);
+          }
+        }
+        c = add_in_order(c, term, __ballot_sync(kFull, rel));
       }
-      P.contrib[i] = c;
-      P.kind[i] = KD;
-      P.rnd[i] = r;
-      atomicAdd(P.count, 1u);
+      if (w.lane == 0) {
+        P.contrib[i] = c;
+        P.kind[i] = KD;
+        P.rnd[i] = r;
+        atomicAdd(P.count, 1u);
+      }
     } else {
       double acc = 0.0;
       bool recv = false;
-      for (int e = P.rowptr[i]; e < P.rowptr[i + 1]; ++e) {
-        int32_t j = P.col[e];
-        double x = P.val[e];
-        if (x != 0.0 && P.isD[j]) {
-          acc = __dadd_rn(acc, __dmul_rn(__dmul_rn(P.twocq, x), (double)P.value[j]));
-          recv = true;
+      for (int cb = e0; cb < e1; cb += 32) {
+        const int e = cb + w.lane;
+        double term = 0.0;
+        bool rel = false;
+        if (e < e1) {
+          const int32_t j = P.col[e];
+          const double x = P.val[e];
+          if (x != 0.0 && P.isD[j]) {
+            rel = true;
+            term = __dmul_rn(__dmul_rn(P.twocq, x), (double)P.value[j]);
+          }
         }
+        const unsigned mask = __ballot_sync(kFull, rel);
+        recv |= mask != 0u;
+        acc = add_in_order(acc, term, mask);
       }
-      if (recv) P.b[i] = __dadd_rn(P.b[i], acc);
+      if (recv && w.lane == 0) P.b[i] = __dadd_rn(P.b[i], acc);
     }
   }
 }
 
+// Alive, undetermined neighbours: their count, and the last of them in row
+// order (the single neighbour when the count is one).
 __global__ void k_degree(PruneDev P, int r, bool zero_rule) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P.n;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  const WarpRows w;
+  for (int64_t i = w.first; i < P.n; i += w.stride) {
     uint8_t c = 0;
     if (P.alive[i] && !P.isD[i]) {
+      const int e0 = P.rowptr[i], e1 = P.rowptr[i + 1];
       int deg = 0;
       int32_t p = -1;
       double jv = 0.0;
-      for (int e = P.rowptr[i]; e < P.rowptr[i + 1]; ++e) {
-        int32_t j = P.col[e];
-        double x = P.val[e];
-        if (x != 0.0 && P.alive[j] && !P.isD[j]) {
-          ++deg;
-          p = j;
-          jv = x;
+      for (int cb = e0; cb < e1; cb += 32) {
+        const int e = cb + w.lane;
+        int32_t j = 0;
+        double x = 0.0;
+        bool rel = false;
+        if (e < e1) {
+          j = P.col[e];
+          x = P.val[e];
+          rel = x != 0.0 && P.alive[j] && !P.isD[j];
+        }
+        const unsigned mask = __ballot_sync(kFull, rel);
+        deg += __popc(mask);
+        if (mask) {
+          const int last = 31 - __clz(mask);
+          p = __shfl_sync(kFull, j, last);
+          jv = __shfl_sync(kFull, x, last);
         }
       }
-      if (deg == 0 && zero_rule && P.b[i] == 0.0) {
-        P.kind[i] = KZ;
-        P.rnd[i] = r;
-        P.value[i] = 1;
-        P.contrib[i] = 0.0;
-        atomicAdd(P.count, 1u);
-      } else if (deg == 1) {
-        P.par[i] = p;
-        P.jkp[i] = jv;
-        c = __dmul_rn(P.twocq_abs, fabs(jv)) >= fabs(P.b[i]);
+      if (w.lane == 0) {
+        if (deg == 0 && zero_rule && P.b[i] == 0.0) {
+          P.kind[i] = KZ;
+          P.rnd[i] = r;
+          P.value[i] = 1;
+          P.contrib[i] = 0.0;
+          atomicAdd(P.count, 1u);
+        } else if (deg == 1) {
+          P.par[i] = p;
+          P.jkp[i] = jv;
+          c = __dmul_rn(P.twocq_abs, fabs(jv)) >= fabs(P.b[i]);
+        }
       }
     }
-    P.cand[i] = c;
+    if (w.lane == 0) P.cand[i] = c;
   }
 }
 
@@ -147,35 +240,48 @@ __global__ void k_select_semi(PruneDev P) {
       s = !(mutual && (int32_t)k < p);
     }
     P.isS[k] = s;
+    if (s) atomicAdd(P.nS, 1u);
   }
 }
 
 __global__ void k_fold_semi(PruneDev P, int r) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P.n;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  if (*P.nS == 0) return;  // no semi-determined spins this round
+  const WarpRows w;
+  for (int64_t i = w.first; i < P.n; i += w.stride) {
     if (!P.alive[i]) continue;
     if (P.isS[i]) {
-      const double jv = P.jkp[i];
-      const double prod = __dmul_rn(P.cq, jv);
-      P.psign[i] = prod > 0.0 ? -1 : 1;
-      P.parent[i] = P.par[i];
-      P.contrib[i] = -__dmul_rn(P.twocq_abs, fabs(jv));
-      P.kind[i] = KS;
-      P.rnd[i] = r;
-      atomicAdd(P.count, 1u);
+      if (w.lane == 0) {
+        const double jv = P.jkp[i];
+        const double prod = __dmul_rn(P.cq, jv);
+        P.psign[i] = prod > 0.0 ? -1 : 1;
+        P.parent[i] = P.par[i];
+        P.contrib[i] = -__dmul_rn(P.twocq_abs, fabs(jv));
+        P.kind[i] = KS;
+        P.rnd[i] = r;
+        atomicAdd(P.count, 1u);
+      }
     } else {
+      const int e0 = P.rowptr[i], e1 = P.rowptr[i + 1];
       double acc = 0.0;
       bool recv = false;
-      for (int e = P.rowptr[i]; e < P.rowptr[i + 1]; ++e) {
-        int32_t k = P.col[e];
-        double x = P.val[e];
-        if (x != 0.0 && P.isS[k]) {
-          const double sg = __dmul_rn(P.cq, P.jkp[k]) > 0.0 ? -1.0 : 1.0;
-          acc = __dadd_rn(acc, __dmul_rn(sg, P.b[k]));
-          recv = true;
+      for (int cb = e0; cb < e1; cb += 32) {
+        const int e = cb + w.lane;
+        double term = 0.0;
+        bool rel = false;
+        if (e < e1) {
+          const int32_t k = P.col[e];
+          const double x = P.val[e];
+          if (x != 0.0 && P.isS[k]) {
+            rel = true;
+            const double sg = __dmul_rn(P.cq, P.jkp[k]) > 0.0 ? -1.0 : 1.0;
+            term = __dmul_rn(sg, P.b[k]);
+          }
         }
+        const unsigned mask = __ballot_sync(kFull, rel);
+        recv |= mask != 0u;
+        acc = add_in_order(acc, term, mask);
       }
-      if (recv) P.b[i] = __dadd_rn(P.b[i], acc);
+      if (recv && w.lane == 0) P.b[i] = __dadd_rn(P.b[i], acc);
     }
   }
 }
@@ -434,22 +540,25 @@ int ising::prune_device(ising_ctx* ctx, const DevInstance& I, int flags,
     P.b = b.as<double>();
     P.contrib = contrib.as<double>();
     P.count = count.as<unsigned int>();
+    P.nD = count.as<unsigned int>() + 1;
+    P.nS = count.as<unsigned int>() + 2;
     P.cq = I.cq;
     P.twocq = 2.0 * I.cq;
     P.twocq_abs = std::fabs(2.0 * I.cq);
     const int g = grid_n(ctx, n);
+    const int gw = grid_n(ctx, n * 32);  // warp-per-row kernels
     k_init<<<g, 256, 0, st>>>(P, I.has_h ? I.h.p : nullptr, I.h_dtype, I.ch);
     ISING_CUDA(ctx, cudaGetLastError());
     const bool zero_rule = (flags & ISING_PRUNE_ZERO_RULE) != 0;
     int rounds = 0;
     for (int r = 1; r <= n + 1; ++r) {
-      ISING_CUDA(ctx, cudaMemsetAsync(count.p, 0, 4, st));
-      k_determined<<<g, 256, 0, st>>>(P);
-      k_fold_determined<<<g, 256, 0, st>>>(P, r);
-      k_degree<<<g, 256, 0, st>>>(P, r, zero_rule);
+      ISING_CUDA(ctx, cudaMemsetAsync(count.p, 0, 12, st));
+      k_determined<<<gw, 256, 0, st>>>(P);
+      k_fold_determined<<<gw, 256, 0, st>>>(P, r);
+      k_degree<<<gw, 256, 0, st>>>(P, r, zero_rule);
       k_remove_determined<<<g, 256, 0, st>>>(P);
       k_select_semi<<<g, 256, 0, st>>>(P);
-      k_fold_semi<<<g, 256, 0, st>>>(P, r);
+      k_fold_semi<<<gw, 256, 0, st>>>(P, r);
       k_remove_semi<<<g, 256, 0, st>>>(P);
       ISING_CUDA(ctx, cudaGetLastError());
       unsigned int changed = 0;

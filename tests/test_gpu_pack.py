@@ -44,7 +44,8 @@ def _state(s):
 def test_packed_members_match_each_alone(gpu_ctx, members, steps):
     mem = members()
     prec = "auto"
-    # tile width 128 for every member (restart counts between 65 and 2047)
+    # one restart-tile width for every member, chosen by the pack (the
+    # members alone keep their own)
     packed = [api.Session(gpu_ctx, inst, restarts=B, steps=steps, seed=5 + k, precision=prec,
                           streaming=True) for k, (inst, B) in enumerate(mem)]
     pk = api.Pack(gpu_ctx, packed)
