@@ -427,9 +427,10 @@ typedef struct ising_server_cfg {
 } ising_server_cfg;
 
 /* cfg.flags: the dense tensor-core requests ready in a scheduling round are
- * grouped by kind (operand type, energy mode, restart tile width) and each
- * group advances its chunk as one pack (see ising_pack_create) on the
- * server's own stream; results are those of the requests alone. */
+ * grouped by kind (operand type, energy mode) and each group advances its
+ * chunk as one pack (see ising_pack_create) on one of four server streams
+ * that the packs take in turn (the chunks of different groups overlap);
+ * results are those of the requests alone. */
 #define ISING_SERVER_PACK 1
 
 typedef struct ising_result {

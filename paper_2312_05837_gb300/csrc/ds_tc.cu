@@ -205,6 +205,8 @@ struct OneInstance {
   const CUtensorMap *A0, *A1, *A2, *B, *J0, *J1, *J2, *S2;
   __device__ int first() const { return blockIdx.x; }
   __device__ int stride() const { return gridDim.x; }
+  // the CTA's j-th tile
+  __device__ int at(int j) const { return first() + j * stride(); }
   __device__ int total() const { return P.mtiles * P.ntiles; }
   __device__ int* err() const { return P.err; }
   __device__ unsigned long long* trace() const { return P.trace; }
@@ -254,6 +256,14 @@ struct PackedInstances {
   static constexpr bool kSplit = false;
   __device__ int first() const { return blockIdx.x; }
   __device__ int stride() const { return gridDim.x; }
+  // the CTA's j-th tile: the tiles are taken wave by wave (a wave is one
+  // tile per CTA), every other wave in reverse CTA order, so that over the
+  // waves of a pack sorted by tile size no CTA draws the largest tile of
+  // each wave
+  __device__ int at(int j) const {
+    const int g = gridDim.x, c = blockIdx.x;
+    return j * g + ((j & 1) ? g - 1 - c : c);
+  }
   const PackEntry* E;
   const int* start;
   int count;
@@ -314,6 +324,8 @@ struct PairInstance {
   uint32_t rank;
   __device__ int first() const { return (int)tc::cluster_index(); }
   __device__ int stride() const { return (int)tc::cluster_count(); }
+  // the CTA's j-th tile (row-tile-major order)
+  __device__ int at(int j) const { return first() + j * stride(); }
   __device__ int total() const { return (P.mtiles + 1) / 2 * P.ntiles; }
   __device__ int* err() const { return P.err; }
   __device__ unsigned long long* trace() const { return P.trace; }
@@ -410,7 +422,7 @@ __device__ __forceinline__ void step_tiles(const Src& src) {
       uint32_t stage = 0, phase = 0;
       int issued = 0;
       bool ok = true;
-      for (int tl = src.first(); tl < total && ok; tl += src.stride()) {
+      for (int j = 0, tl = src.at(0); tl < total && ok; tl = src.at(++j)) {
         const TileRef T = src.tile(tl);
         if (T.skip) continue;
         const TcArgs& P = src.args(T);
@@ -513,7 +525,7 @@ __device__ __forceinline__ void step_tiles(const Src& src) {
       uint32_t stage = 0, phase = 0;
       int it = 0;
       bool ok = true;
-      for (int tl = src.first(); tl < total && ok; tl += src.stride()) {
+      for (int j = 0, tl = src.at(0); tl < total && ok; tl = src.at(++j)) {
         const TileRef T = src.tile(tl);
         if (T.skip) continue;
         const TcArgs& P = src.args(T);
@@ -583,7 +595,7 @@ __device__ __forceinline__ void step_tiles(const Src& src) {
     const int part = (warp - 4) >> 2;   // which quarter of the tile's columns
     constexpr int kCols = BN / 4;
     int it = 0;
-    for (int tl = src.first(); tl < total; tl += src.stride()) {
+    for (int j = 0, tl = src.at(0); tl < total; tl = src.at(++j)) {
       const TileRef T = src.tile(tl);
       if (T.skip) continue;
       const TcArgs& P = src.args(T);

@@ -195,7 +195,11 @@ extern "C" int ising_pack_create(ising_ctx* ctx, ising_ds* const* sessions, int3
   }
   auto pk = new ising_pack();
   pk->ctx = ctx;
+  // members by size, largest first: their tiles then come in decreasing cost
+  // (K = n), which the packed launch's wave-by-wave tile order spreads evenly
   pk->members.assign(sessions, sessions + count);
+  std::stable_sort(pk->members.begin(), pk->members.end(),
+                   [](const ising_ds* a, const ising_ds* b) { return a->n > b->n; });
   pk->key = key;
   pk->bn = pack_width(ctx, sessions, count);
   pk->spin_kind = sessions[0]->spin_kind;
@@ -207,7 +211,7 @@ extern "C" int ising_pack_create(ising_ctx* ctx, ising_ds* const* sessions, int3
     std::vector<TrackArgs> targs(count);
     std::vector<int64_t> rstart(count + 1, 0);
     for (int k = 0; k < count; ++k) {
-      ising_ds* ds = sessions[k];
+      ising_ds* ds = pk->members[k];
       // one tile width for all: the results do not depend on it
       ISING_TRY(tc_set_bn(ds, pk->bn));
       ISING_TRY(tc_pack_entry(ds, ent.data() + eb * k));

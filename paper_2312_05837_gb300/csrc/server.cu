@@ -15,9 +15,10 @@
 // synchronisations of a request's own stream) do not hold up the chunks of
 // the others.
 // With ISING_SERVER_PACK, the dense tensor-core requests that are ready in a
-// round are grouped by kind (operand type, energy mode, tile width) and each
-// group advances its chunk as one pack (ising_pack: one launch per step for
-// all of them, on the server's own stream); a group's pack is kept, with its
+// round are grouped by kind (operand type, energy mode) and each group
+// advances its chunk as one pack (ising_pack: one launch per step for all of
+// them, on one of the server's pack streams, which packs take in turn so
+// that different groups' chunks overlap); a group's pack is kept, with its
 // captured step graph, while the group stays the same.
 #include "ds_internal.cuh"
 
@@ -79,6 +80,8 @@ struct Request {
 
 enum Phase { kQueued = 0, kSettingUp, kReady, kFinishing, kDone };
 
+constexpr int kPackStreams = 4;  // streams the server's packs take in turn
+
 // Device bytes a request holds while admitted (instance copy, pruning work,
 // operands, state, spins, partials, bests), estimated from its shape.
 size_t estimate_footprint(const ising_instance* in, const ising_ds_params* p) {
@@ -122,10 +125,18 @@ struct ising_server {
   size_t used = 0;
   bool stop = false;
   uint64_t next_id = 1;
-  // packed advancement (ISING_SERVER_PACK): the server's stream, and the
-  // pack of each current group of requests (keyed by its members' ids)
-  std::unique_ptr<ising_ctx> pack_ctx;
-  std::map<std::vector<uint64_t>, ising_pack*> packs;
+  // packed advancement (ISING_SERVER_PACK): the server's pack streams, and
+  // the pack of each current group of requests (keyed by its members' ids)
+  // with the stream it runs on; packs take the streams in turn, so the
+  // chunks of different groups overlap on the device (a pack of a few small
+  // requests holds only a few SMs)
+  std::vector<std::unique_ptr<ising_ctx>> pack_ctxs;
+  int next_pack_ctx = 0;
+  struct PackSlot {
+    ising_pack* pk;
+    ising_ctx* ctx;
+  };
+  std::map<std::vector<uint64_t>, PackSlot> packs;
   std::chrono::steady_clock::time_point t0;
   ising_server_stats st{};  // guarded by mu
 
@@ -368,7 +379,7 @@ void worker_loop(ising_server* srv) {
       const bool steps_done =
           r->status != ISING_OK || !r->ds || r->ds->t >= r->ds->T || r->ds->conv_all;
       if (!steps_done) {
-        if (srv->pack_ctx && tc_packable(r->ds)) {
+        if (!srv->pack_ctxs.empty() && tc_packable(r->ds)) {
           groups[tc_pack_key(r->ds)].push_back(r);
           continue;
         }
@@ -400,15 +411,19 @@ void worker_loop(ising_server* srv) {
       for (Request* r : grp) todo = std::min<int64_t>(todo, r->ds->T - r->ds->t);
       int rc = ISING_OK;
       ising_pack* pk = nullptr;
+      ising_ctx* pctx = nullptr;
       tp = Clock::now();
       auto it = srv->packs.find(ids);
       if (it != srv->packs.end()) {
-        pk = it->second;
+        pk = it->second.pk;
+        pctx = it->second.ctx;
       } else {
         std::vector<ising_ds*> ds;
         for (Request* r : grp) ds.push_back(r->ds);
-        rc = ising_pack_create(srv->pack_ctx.get(), ds.data(), (int32_t)ds.size(), &pk);
-        if (rc == ISING_OK) srv->packs[ids] = pk;
+        pctx = srv->pack_ctxs[srv->next_pack_ctx].get();
+        srv->next_pack_ctx = (srv->next_pack_ctx + 1) % (int)srv->pack_ctxs.size();
+        rc = ising_pack_create(pctx, ds.data(), (int32_t)ds.size(), &pk);
+        if (rc == ISING_OK) srv->packs[ids] = {pk, pctx};
         rs.packs_created += 1;
         rs.pack_create_ms += ms_since(tp);
       }
@@ -418,12 +433,11 @@ void worker_loop(ising_server* srv) {
       for (Request* r : grp) {
         int rr = rc;
         if (rr == ISING_OK) {
-          const cudaError_t e = cudaEventRecord(r->ev, srv->pack_ctx->stream);
+          const cudaError_t e = cudaEventRecord(r->ev, pctx->stream);
           if (e != cudaSuccess)
-            rr = fail(srv->pack_ctx.get(), ISING_ECUDA, "cudaEventRecord failed: %s",
-                      cudaGetErrorString(e));
+            rr = fail(pctx, ISING_ECUDA, "cudaEventRecord failed: %s", cudaGetErrorString(e));
         }
-        if (rr != ISING_OK) set_failed(r, rr, srv->pack_ctx.get());
+        if (rr != ISING_OK) set_failed(r, rr, pctx);
         else r->in_flight = true;
       }
     }
@@ -441,7 +455,7 @@ void worker_loop(ising_server* srv) {
         if (r->in_flight && std::find(it->first.begin(), it->first.end(), r->id) != it->first.end())
           in_flight = true;
       if (!live && !in_flight) {
-        ising_pack_destroy(it->second);
+        ising_pack_destroy(it->second.pk);
         it = srv->packs.erase(it);
       } else {
         ++it;
@@ -528,16 +542,19 @@ extern "C" int ising_server_create(ising_ctx* ctx, const ising_server_cfg* cfg,
   }
   srv->slot_busy.assign(cfg->max_active, false);
   if (cfg->flags & ISING_SERVER_PACK) {
-    auto c = std::make_unique<ising_ctx>();
-    c->device = ctx->device;
-    c->sm_count = ctx->sm_count;
-    c->smem_optin = ctx->smem_optin;
-    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
-      for (auto& s : srv->slots) cudaStreamDestroy(s->stream);
-      delete srv;
-      return fail(ctx, ISING_ECUDA, "stream creation failed");
+    for (int k = 0; k < kPackStreams; ++k) {
+      auto c = std::make_unique<ising_ctx>();
+      c->device = ctx->device;
+      c->sm_count = ctx->sm_count;
+      c->smem_optin = ctx->smem_optin;
+      if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        for (auto& s : srv->slots) cudaStreamDestroy(s->stream);
+        for (auto& s : srv->pack_ctxs) cudaStreamDestroy(s->stream);
+        delete srv;
+        return fail(ctx, ISING_ECUDA, "stream creation failed");
+      }
+      srv->pack_ctxs.push_back(std::move(c));
     }
-    srv->pack_ctx = std::move(c);
   }
   const int helpers = cfg->helper_threads > 0 ? cfg->helper_threads : 2;
   for (int k = 0; k < helpers; ++k) srv->helpers.emplace_back(helper_loop, srv);
@@ -725,11 +742,11 @@ extern "C" int ising_server_destroy(ising_server* srv) {
   }
   for (auto& h : srv->helpers)
     if (h.joinable()) h.join();
-  for (auto& kv : srv->packs) ising_pack_destroy(kv.second);
+  for (auto& kv : srv->packs) ising_pack_destroy(kv.second.pk);
   srv->packs.clear();
-  if (srv->pack_ctx) {
-    cudaStreamSynchronize(srv->pack_ctx->stream);
-    cudaStreamDestroy(srv->pack_ctx->stream);
+  for (auto& c : srv->pack_ctxs) {
+    cudaStreamSynchronize(c->stream);
+    cudaStreamDestroy(c->stream);
   }
   for (auto& s : srv->slots) {
     cudaStreamSynchronize(s->stream);
