@@ -501,7 +501,26 @@ def latency_summary(res, rate):
             "all_ok": all(r["status"] == 0 for r in res)}
 
 
-def serving(ctx, count=1000, rate=200.0, n_max=8192, B=256, T=2000, seed=5, plain_count=200):
+def serving_capacity(reqs, B, T, pk):
+    """Requests per second the GPU could complete at its measured peaks for
+    this stream's mix, from the sizes alone (before pruning): a dense
+    request needs 2 N^2 B T flop at the E4M3 rate (2 x the sustained BF16
+    figure) and moves at least 24 B of state per update plus its E4M3 J once
+    per step; a sparse one moves 24.25 B per update (restarts padded to 128);
+    each takes the longer of its compute and memory times."""
+    fp8 = 2.0 * pk["bf16_tflops_sustained"] * 1e12
+    hbm = pk["hbm_gbs"] * 1e9
+    total = 0.0
+    for _, inst in reqs:
+        n = float(inst.n)
+        if inst.layout == "dense":
+            total += max(2.0 * n * n * B * T / fp8, (24.0 * n * B + n * n) * T / hbm)
+        else:
+            total += 24.25 * n * ((B + 127) // 128 * 128) * T / hbm
+    return len(reqs) / total
+
+
+def serving(ctx, pk, count=1000, rate=200.0, n_max=8192, B=256, T=2000, seed=5, plain_count=200):
     """The serving stream (Poisson arrivals at `rate`, N log-uniform in
     [64, n_max] over pooled instances, half dense SK J ~ N(0, 1/N) with
     h ~ N(0, 0.1), half sparse ER degree 8 +-1; B restarts x T steps each,
@@ -524,6 +543,7 @@ def serving(ctx, count=1000, rate=200.0, n_max=8192, B=256, T=2000, seed=5, plai
     plain, _ = serve_stream(ctx, reqs[:plain_count], B, T, "fp32", False, 1, budget)
     out = {"requests": count, "rate_per_s": rate, "n_range": [64, n_max], "restarts": B,
            "steps": T, "budget_gb": 120,
+           "capacity_at_roofline_per_s": serving_capacity(reqs, B, T, pk),
            "mix": "50% dense SK J~N(0,1/N) h~N(0,0.1), 50% sparse ER deg 8 +-1 (24 pooled sizes "
                   "per kind, N drawn log-uniformly, nearest pooled size)",
            "served": {**latency_summary(served, rate), "form": "packed launches, dense in "
@@ -811,7 +831,7 @@ def main():
             line["time_to_target"]["er2000"] = time_to_target(
                 ctx, pinned_instance(winst, torch), True, wB, wT, 3, w_hist, ["auto"], 50)
         line["early_retirement"] = early_retirement(ctx)
-        line["serving"] = serving(ctx)
+        line["serving"] = serving(ctx, pk)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(a, B, T)
     if rank == 0:
