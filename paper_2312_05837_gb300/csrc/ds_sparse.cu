@@ -26,8 +26,11 @@ namespace {
 // per SM); Q = 2 gathers each neighbour's spins once for 256 restarts (two
 // blocks per SM). Both visit rows, lanes and partials in the same order,
 // so their results are identical bit for bit.
-template <int Q, int MODE, bool INT_E, bool VAL_I8>
-__global__ void __launch_bounds__(256, Q == 1 ? (MODE == kModeRelaxed ? 3 : 4) : 2) sparse_step_kernel(
+// LANE: the few-rows-per-warp edge visit (small instances, whose grids are
+// small too: two blocks per SM leave it the registers it needs).
+template <int Q, int MODE, bool INT_E, bool VAL_I8, bool LANE>
+__global__ void __launch_bounds__(256, LANE ? 2 : (Q == 1 ? (MODE == kModeRelaxed ? 3 : 4) : 2))
+    sparse_step_kernel(
     int64_t n, int64_t Bp, int64_t rows_per_block, const int32_t* __restrict__ rowptr,
     const int32_t* __restrict__ col, const void* __restrict__ val,
     const uint32_t* __restrict__ bits_in, uint32_t* __restrict__ bits_out,
@@ -36,8 +39,7 @@ __global__ void __launch_bounds__(256, Q == 1 ? (MODE == kModeRelaxed ? 3 : 4) :
     const float2* __restrict__ bias, const long long* __restrict__ counters,
     long long* __restrict__ qpart, long long* __restrict__ hpart, float* __restrict__ epart,
     float* __restrict__ Gout, const float* __restrict__ xin, float* __restrict__ xout,
-    int64_t B, const int* __restrict__ live32, unsigned long long* __restrict__ work,
-    int lane_edges) {
+    int64_t B, const int* __restrict__ live32, unsigned long long* __restrict__ work) {
   constexpr bool RELAXED = MODE == kModeRelaxed;
   constexpr bool UPDATE = MODE == kModeUpdate || RELAXED;
   constexpr int W = 8;  // warps per block
@@ -114,11 +116,15 @@ __global__ void __launch_bounds__(256, Q == 1 ? (MODE == kModeRelaxed ? 3 : 4) :
         }
       }
     };
-    if (lane_edges) {
+    if constexpr (LANE) {
       // few rows per warp (small instances): the row's edges, up to 32 at a
-      // time, lane k loading edge k (one coalesced load), then visited in
-      // order by broadcast, each neighbour's spin word requested one edge
-      // ahead, so the gathers do not wait on one another
+      // time, lane k loading edge k (one coalesced load); then the spin
+      // words of several edges at once, lane L loading word L % (4 Q) of
+      // edge L / (4 Q) (a row's words for this slice are contiguous), so one
+      // load instruction covers 32 / (4 Q) edges; the edges are then added
+      // in order, each lane taking its words by shuffle
+      constexpr int kWpe = 4 * Q;       // words per edge in this slice
+      constexpr int kEpp = 32 / kWpe;   // edges per load pass
       for (int eb = rb; eb < re; eb += 32) {
         const int cnt = re - eb < 32 ? re - eb : 32;
         int jl = 0;
@@ -128,28 +134,29 @@ __global__ void __launch_bounds__(256, Q == 1 ? (MODE == kModeRelaxed ? 3 : 4) :
           vl = VAL_I8 ? (float)static_cast<const int8_t*>(val)[eb + lane]
                       : static_cast<const float*>(val)[eb + lane];
         }
-        uint32_t w_next[Q];
-        int64_t j_next = __shfl_sync(0xffffffffu, jl, 0);
-#pragma unroll
-        for (int q = 0; q < Q; ++q) w_next[q] = __ldg(&bits_in[j_next * words + wofs + 4 * q]);
 #pragma unroll 1
-        for (int k = 0; k < cnt; ++k) {
-          const int64_t j = j_next;
-          const float Jv = __shfl_sync(0xffffffffu, vl, k);
-          uint32_t w[Q];
+        for (int p0 = 0; p0 < cnt; p0 += kEpp) {
+          const int ke = p0 + lane / kWpe;  // < 32
+          const int64_t jk = __shfl_sync(0xffffffffu, jl, ke);
+          uint32_t wv = 0u;
+          if (ke < cnt) wv = __ldg(&bits_in[jk * words + cb / 32 + lane % kWpe]);
+          const int ne = cnt - p0 < kEpp ? cnt - p0 : kEpp;
+#pragma unroll 1
+          for (int e = 0; e < ne; ++e) {
+            const int64_t j = __shfl_sync(0xffffffffu, jl, p0 + e);
+            const float Jv = __shfl_sync(0xffffffffu, vl, p0 + e);
+            uint32_t w[Q];
 #pragma unroll
-          for (int q = 0; q < Q; ++q) w[q] = w_next[q];
-          if (k + 1 < cnt) {
-            j_next = __shfl_sync(0xffffffffu, jl, k + 1);
-#pragma unroll
-            for (int q = 0; q < Q; ++q) w_next[q] = __ldg(&bits_in[j_next * words + wofs + 4 * q]);
+            for (int q = 0; q < Q; ++q)
+              w[q] = __shfl_sync(0xffffffffu, wv, e * kWpe + 4 * q + (lane >> 3));
+            add_edge(j, Jv, w);
           }
-          add_edge(j, Jv, w);
         }
       }
     } else {
       // many rows per warp: every lane reads each edge (broadcast) and the
       // next row's state is already in flight
+#pragma unroll (RELAXED ? 1 : 4)
       for (int e = rb; e < re; ++e) {
         const int64_t j = col[e];
         const float Jv = VAL_I8 ? (float)static_cast<const int8_t*>(val)[e]
@@ -295,13 +302,17 @@ int sparse_step(ising_ds* ds, int mode, float* Gout) {
   const float* xin = mode == kModeRelaxed ? ds->xbuf[t % 2].as<float>() : nullptr;
   float* xout = mode == kModeRelaxed ? ds->xbuf[(t + 1) % 2].as<float>() : nullptr;
   dim3 grid((unsigned)ds->mtiles, (unsigned)(ds->Bp / (128 * Q)));
-  const int lane_edges = (rpb + 7) / 8 <= 4;  // rows per warp
+  const bool lane_edges = (rpb + 7) / 8 <= 4;  // rows per warp
 #define ISING_SP(U, I, V)                                                                     \
   do {                                                                                        \
-    if (Q == 2)                                                                               \
-      sparse_step_kernel<2, U, I, V><<<grid, 256, 0, ctx->stream>>>(ISING_SP_ARGS);           \
+    if (Q == 2 && lane_edges)                                                                 \
+      sparse_step_kernel<2, U, I, V, true><<<grid, 256, 0, ctx->stream>>>(ISING_SP_ARGS);     \
+    else if (Q == 2)                                                                          \
+      sparse_step_kernel<2, U, I, V, false><<<grid, 256, 0, ctx->stream>>>(ISING_SP_ARGS);    \
+    else if (lane_edges)                                                                      \
+      sparse_step_kernel<1, U, I, V, true><<<grid, 256, 0, ctx->stream>>>(ISING_SP_ARGS);     \
     else                                                                                      \
-      sparse_step_kernel<1, U, I, V><<<grid, 256, 0, ctx->stream>>>(ISING_SP_ARGS);           \
+      sparse_step_kernel<1, U, I, V, false><<<grid, 256, 0, ctx->stream>>>(ISING_SP_ARGS);    \
   } while (0)
 #define ISING_SP_ARGS                                                                         \
       ds->n, ds->Bp, rpb, ds->inst.rowptr.as<int32_t>(), ds->inst.indices.as<int32_t>(),      \
@@ -309,8 +320,7 @@ int sparse_step(ising_ds* ds, int mode, float* Gout) {
       ds->hf.as<float>(), ds->hint.as<int32_t>(), ds->k, ds->bias.as<float2>(),               \
       ds->counters.as<long long>(), ds->qpart[ps].as<long long>(),                            \
       ds->hpart[ps].as<long long>(), ds->epart[ps].as<float>(), Gout, xin, xout, ds->B,          \
-      ds->live.p ? ds->live.as<int>() : nullptr, ds->work.as<unsigned long long>(),          \
-      lane_edges
+      ds->live.p ? ds->live.as<int>() : nullptr, ds->work.as<unsigned long long>()
 #define ISING_SP_V(U, I) \
   do { if (ds->sp_int8) ISING_SP(U, I, true); else ISING_SP(U, I, false); } while (0)
 #define ISING_SP_I(U) \
