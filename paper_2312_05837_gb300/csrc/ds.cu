@@ -151,8 +151,19 @@ __device__ __forceinline__ void track_restart(const TrackArgs& A, long long t, i
       atomicSub(&A.live32[b >> 5], 1);
   }
   if (KIND == kSpinBits) {
-    // bit-packed spins are copied by track_bits_copy_kernel
-    if (lane == 0) A.improved[b] = improved ? 1 : 0;
+    if (A.inline_bits) {
+      // bit b of each spin's word column, one spin per lane and pass
+      if (improved) {
+        const uint32_t* bits = static_cast<const uint32_t*>(A.spins[t % 3]);
+        const int64_t words = A.Bp / 32;
+        int8_t* dst = A.best_s + b * A.bs_ld;
+        for (int64_t i = lane; i < A.n; i += 32)
+          dst[i] = ((bits[i * words + (b >> 5)] >> (b & 31)) & 1u) ? 1 : -1;
+      }
+    } else if (lane == 0) {
+      // bit-packed spins are copied by track_bits_copy_kernel
+      A.improved[b] = improved ? 1 : 0;
+    }
   } else if (improved) {
     copy_spin_row_dense<KIND>(A.best_s + b * A.bs_ld, A.spins[t % 3], A.n, A.ld, b, lane);
   }
@@ -423,8 +434,13 @@ TrackArgs track_args(const ising_ds* ds) {
   A.conv_step = conv ? ds->conv_step() : nullptr;
   A.conv_count = conv ? ds->conv_count() : nullptr;
   A.live32 = conv ? ds->live.as<int>() : nullptr;
+  A.inline_bits = false;
   return A;
 }
+
+// Bit-packed spins up to this many per restart are copied by the tracking
+// warps themselves (one launch less per step for small instances).
+constexpr int64_t kInlineBitsMaxN = 4096;
 
 int track_step(ising_ds* ds) {
   ising_ctx* ctx = ds->ctx;
@@ -437,6 +453,13 @@ int track_step(ising_ds* ds) {
     case kSpinF16: track_kernel<kSpinBF16><<<grid, 256, 0, ctx->stream>>>(A); break;  // sign bits
     case kSpinE4M3: track_kernel<kSpinE4M3><<<grid, 256, 0, ctx->stream>>>(A); break;
     default: {
+      if (ds->n <= kInlineBitsMaxN) {
+        // small instances: each improved restart's spins copied by its warp
+        TrackArgs Ai = A;
+        Ai.inline_bits = true;
+        track_kernel<kSpinBits><<<grid, 256, 0, ctx->stream>>>(Ai);
+        break;
+      }
       track_kernel<kSpinBits><<<grid, 256, 0, ctx->stream>>>(A);
       const int64_t words = ds->Bp / 32;
       const int64_t tasks = (ds->n + 31) / 32 * words;

@@ -167,6 +167,9 @@ struct TrackArgs {
   long long* conv_step;
   unsigned long long* conv_count;
   int* live32;  // live restarts per block of 32 (convergence rule), or null
+  // bit-packed spins: copy an improved restart's spins here (small n)
+  // instead of flagging it for track_bits_copy_kernel
+  bool inline_bits;
 };
 
 // What a step launch does: the full update, only the energies of the input
