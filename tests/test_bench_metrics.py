@@ -57,3 +57,23 @@ def test_traffic_figure_only_for_its_workload_and_source():
         got = bench.traffic_for(kernel, src, e["workload"])
         assert got in (None, e["bytes_per_launch"])
     assert bench.traffic_for("no_such_kernel", "bench.py", "er2000") is None
+
+
+def test_serving_capacity_at_the_roofline():
+    """The serving leg's capacity figure: a dense request takes the longer of
+    its E4M3 flop time and its state + J traffic time, a sparse one its
+    24.25 B per padded update; the capacity is requests over their summed
+    times."""
+    import types
+    import bench
+    pk = {"bf16_tflops_sustained": 1000.0, "hbm_gbs": 5000.0}
+    B, T = 256, 2000
+    dense = types.SimpleNamespace(n=1000, layout="dense")
+    sparse = types.SimpleNamespace(n=3000, layout="csr")
+    t_dense = max(2.0 * 1000 ** 2 * B * T / 2e15, (24.0 * 1000 * B + 1000 ** 2) * T / 5e12)
+    t_sparse = 24.25 * 3000 * 256 * T / 5e12
+    got = bench.serving_capacity([(0.0, dense), (0.1, sparse)], B, T, pk)
+    assert got == pytest.approx(2.0 / (t_dense + t_sparse), rel=1e-12)
+    # restarts pad to 128 on the sparse path
+    got_pad = bench.serving_capacity([(0.0, sparse)], 129, T, pk)
+    assert got_pad == pytest.approx(1.0 / (24.25 * 3000 * 256 * T / 5e12), rel=1e-12)
