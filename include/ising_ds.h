@@ -410,7 +410,11 @@ int ising_ds_destroy(ising_ds* ds);
  * is solved exactly as ising_solve would solve it alone (pruning, domain
  * selection with the state kept in device memory between steps, best of
  * restarts, reconstruction, energy), so its result does not depend on what
- * else is being served. The paper has no counterpart.
+ * else is being served. Requests run the tensor-core path in its streaming
+ * form (no grid barrier shared with other requests' kernels), except
+ * instances of at most 128 spins without ISING_DS_CONVERGE or
+ * ISING_DS_RELAXED, whose small resident form has none either and runs a
+ * whole chunk of steps in one launch. The paper has no counterpart.
  * The requests' streams reach the device through the context's hardware
  * work queues (8 unless the environment variable CUDA_DEVICE_MAX_CONNECTIONS,
  * read when the process creates its CUDA context, says more): with more

@@ -169,7 +169,12 @@ int start_request(ising_server* srv, Request* r, double ms[3]) {
     ising_instance red;
     ising_prune_reduced(r->pr, &red);
     ising_ds_params p = r->p;
-    p.flags |= ISING_DS_STREAMING;  // no grid barrier across concurrent requests
+    // no grid barrier across concurrent requests: the streaming form, except
+    // where the small resident form applies (n <= 128, without the
+    // convergence rule or the relaxed product: each CTA holds all of J and
+    // its restarts, no grid barrier), which runs a whole chunk in one launch
+    const bool small = red.n <= 128 && !(p.flags & (ISING_DS_CONVERGE | ISING_DS_RELAXED));
+    if (!small) p.flags |= ISING_DS_STREAMING;
     ISING_TRY(ds_create_impl(ctx, &red, &p, &r->ds, false));
   }
   ISING_CUDA(ctx, cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming));
