@@ -263,8 +263,8 @@ const char* ising_energy_noalloc_error(void);
  * with ISING_DS_STREAMING, without ISING_DS_RELAXED), all with the same
  * operand type (E4M3 or 16-bit) and energy mode (integer or FP32 partials);
  * every member is switched to one restart-tile width chosen for the pack
- * (the least padding of the members' restarts, then the widest that still
- * gives every SM a tile; the results do not depend on it). Sessions may belong to different contexts
+ * (the least waves of tiles over the SMs times the width, padding of the
+ * members' restarts included; the results do not depend on it). Sessions may belong to different contexts
  * of the same device. Otherwise ISING_ENOTSUP / ISING_EINVAL. The pack borrows the
  * sessions: destroy it before any member. Work is queued on `ctx`'s stream,
  * ordered after work already queued on the members' streams and before work

@@ -38,30 +38,26 @@ namespace {
 
 constexpr int64_t kPackGraphSteps = 25;
 
-// The pack's restart-tile width: the least padding over all members (tiles
-// of bn restarts hold ceil(B / bn) x bn columns of a member's B), then,
-// among the widths that pad least, the widest whose tiles still give every
-// SM one (wider tiles issue fewer, longer MMAs), else the narrowest.
+// The pack's restart-tile width: a persistent CTA per SM takes the tiles in
+// waves, so a step costs about (waves) x (the time of one tile), and a
+// tile's time grows with its width (its epilogue over 128 x bn elements, and
+// its products): the width with the least waves x bn is taken (padding of
+// the members' restart counts included in the tile counts), the wider one
+// on a tie.
 int pack_width(const ising_ctx* ctx, ising_ds* const* s, int count) {
   const int widths[4] = {256, 224, 128, 64};
-  double pad[4];
-  int64_t tiles[4];
-  double least = 1e300;
+  int pick = 0;
+  int64_t best = -1;
   for (int w = 0; w < 4; ++w) {
-    pad[w] = 0.0;
-    tiles[w] = 0;
-    for (int k = 0; k < count; ++k) {
-      const int64_t rt = ceil_div_i(s[k]->n, 128), ct = ceil_div_i(s[k]->B, widths[w]);
-      pad[w] += (double)rt * (double)(ct * widths[w] - s[k]->B);
-      tiles[w] += rt * ct;
+    int64_t tiles = 0;
+    for (int k = 0; k < count; ++k)
+      tiles += (int64_t)ceil_div_i(s[k]->n, 128) * ceil_div_i(s[k]->B, widths[w]);
+    const int64_t cost = (tiles + ctx->sm_count - 1) / ctx->sm_count * widths[w];
+    if (best < 0 || cost < best) {
+      best = cost;
+      pick = w;
     }
-    least = std::min(least, pad[w]);
   }
-  int pick = -1;
-  for (int w = 0; w < 4 && pick < 0; ++w)  // widest first
-    if (pad[w] <= least && tiles[w] >= ctx->sm_count) pick = w;
-  for (int w = 3; w >= 0 && pick < 0; --w)  // narrowest first
-    if (pad[w] <= least) pick = w;
   return widths[pick];
 }
 
