@@ -633,6 +633,11 @@ def roofline(ctx, inst, dinst, name, B, kw, steps, pk, sessions=1):
             roof["operand_planes"] = planes
             roof["executed_frac"] = planes * roof["achieved"] / peak
         kname = {0: "tc_step_kernel", 1: "tc_resident_kernel", 2: "tc_small_kernel"}[st["resident"]]
+        if st["resident"] == 0:
+            # the streaming form's kernel for the chosen tile shape
+            kname = ("tc_step_kernel", "tc_step_pair_kernel",
+                     "tc_step_split_kernel")[st.get("tile_pair", 0)]
+            roof["tile"] = {"restarts": st.get("tile_restarts", 0), "pair": st.get("tile_pair", 0)}
         ksrc = "paper_2312_05837_gb300/csrc/ds_tc.cu"
     else:  # plain FP32 FMA on the CUDA cores
         import torch

@@ -180,6 +180,10 @@ typedef struct ising_ds_stats {
                                all of J and its restarts' spins on chip); 0 otherwise */
   int32_t operand_planes;   /* tensor-core path: operand planes of J per product (1 or 2;
                                the tensor cores execute that many products), else 1 */
+  int32_t tile_restarts;    /* tensor-core streaming form: restarts per tile, else 0 */
+  int32_t tile_pair;        /* tensor-core streaming form: 0 one CTA per tile, 1 CTA pairs
+                               sharing spin tiles by multicast, 2 one MMA per CTA pair
+                               (see ising_ds_set_tiles); else 0 */
 } ising_ds_stats;
 
 /* ------------------------------------------------------------------ context */
@@ -261,7 +265,8 @@ const char* ising_energy_noalloc_error(void);
  * identical to running it by itself.
  * Members: sessions of the tensor-core path in the streaming form (created
  * with ISING_DS_STREAMING, without ISING_DS_RELAXED), all with the same
- * operand type (E4M3 or 16-bit) and energy mode (integer or FP32 partials);
+ * operand type (E4M3 or 16-bit), energy mode (integer or FP32 partials) and
+ * number of J planes (one, or two FP16 planes hi + lo);
  * every member is switched to one restart-tile width chosen for the pack
  * (the least waves of tiles over the SMs times the width, padding of the
  * members' restarts included; the results do not depend on it). Sessions may belong to different contexts

@@ -47,7 +47,8 @@ class DSStats(ctypes.Structure):
                 ("last_best_energy", c_double), ("last_best_restart", c_int64),
                 ("steps_done", c_int64), ("path", c_int32), ("precision", c_int32),
                 ("device_ms", c_double), ("kernel_ms", c_double),
-                ("kernel_launches", c_int64), ("resident", c_int32), ("operand_planes", c_int32)]
+                ("kernel_launches", c_int64), ("resident", c_int32), ("operand_planes", c_int32),
+                ("tile_restarts", c_int32), ("tile_pair", c_int32)]
 
 
 class ServerCfg(ctypes.Structure):

@@ -1363,6 +1363,9 @@ extern "C" int ising_ds_result(ising_ds* ds, int8_t* best_spins, double* best_en
     stats->kernel_launches = ds->kernel_launches;
     stats->resident = ds->path == ISING_PATH_TC ? tc_resident_form(ds) : 0;
     stats->operand_planes = ds->path == ISING_PATH_TC ? ds->planes : 1;
+    const bool streaming = ds->path == ISING_PATH_TC && tc_resident_form(ds) == 0;
+    stats->tile_restarts = streaming ? tc_bn(ds) : 0;
+    stats->tile_pair = streaming ? tc_tile_pair(ds) : 0;
   }
   ISING_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   return ISING_OK;

@@ -291,6 +291,7 @@ int track_pack(ising_ctx* ctx, int spin_kind, const TrackArgs* members, const in
 bool tc_packable(const ising_ds* ds);
 uint64_t tc_pack_key(const ising_ds* ds);
 int tc_bn(const ising_ds* ds);                        // restart-tile width
+int tc_tile_pair(const ising_ds* ds);                 // 0 single CTAs, 1 multicast pairs, 2 pair MMA
 constexpr int kTcPair = 1 << 16;   // flag on a width: clusters of two CTAs share spin tiles
 constexpr int kTcSplit = 1 << 17;  // ... and issue their MMAs as one (with kTcPair)
 int tc_bn_candidates(const ising_ds* ds, int* out);   // widths the autotuner may try (<= 8)

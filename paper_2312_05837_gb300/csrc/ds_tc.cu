@@ -18,7 +18,10 @@
 //
 // Streaming form (tc_step_kernel): one persistent CTA per SM, warp-specialised:
 //   warps 0, 2 TMA producers of the J and the S tiles of a STAGES-deep ring
-//              (stages of two k-blocks for BN <= 128, of one for BN = 256),
+//              (stages of two k-blocks for BN <= 128, of one for BN = 256;
+//              with two J planes a stage is one k-block of both planes and
+//              its spin tile, and the MMAs take the planes k-block by
+//              k-block, the order every form uses),
 //   warp 1     allocates tensor memory and issues the MMAs (one thread) into
 //              one of two accumulator buffers (2 x BN columns of 128 lanes),
 //   warps 4-19 epilogue: each thread owns one spin i (its TMEM lane) and walks
@@ -28,6 +31,11 @@
 //              new spin into S_{t+1}, and the energy of the input spins, summed
 //              over each warp's 32 spins by a butterfly across lanes into
 //              one partial row per warp (summed in fixed order afterwards).
+// The same roles run in clusters of two CTAs (tc_step_pair_kernel: each
+// loads half of the spin tile and multicasts it to both; tc_step_split_kernel:
+// the pair's MMAs issued as one, cta_group::2, M 256, each CTA holding its J
+// rows and half of the spin tile), shapes the autotuner times beside single
+// CTAs.
 // Tiles are numbered row tile by row tile (the restart tiles of one row tile
 // are consecutive), so one wave of persistent CTAs covers whole row tiles: a
 // J row tile is read from HBM about once per step and shared through L2 by
@@ -119,6 +127,9 @@ __device__ __forceinline__ unsigned long long now_ns() {
 // issues one TMA copy per ~250 cycles whatever its size); for BN = 224 and
 // 256 such stages would leave room for two only, so there a stage is one
 // k-block.
+// With two J planes a stage instead holds one k-block of both planes and the
+// spin tile of that k-block, which both planes' MMAs read (a third less to
+// copy and to store per MMA than a stage per plane and k-block).
 template <int BN, bool SPLIT = false>
 struct TcLayout {
   static constexpr int kKps = BN >= 192 ? 1 : 2;
@@ -126,15 +137,15 @@ struct TcLayout {
   // SPLIT (the MMA of a CTA pair): each CTA holds half of the spin tile
   static constexpr uint32_t kB = (SPLIT ? BN / 2 : BN) * kRowBytes;
   static constexpr uint32_t kStage = kKps * (kA + kB);
+  static constexpr uint32_t kStage2 = 2 * kA + kB;  // two planes
   // SPLIT: a spin half's worth of room after the last stage, so that every
   // operand read of a stage stays inside this CTA's shared memory whatever
   // part of the pair's tile it covers
   static constexpr uint32_t kTail = SPLIT ? kB : 0;
-  // as many stages as the 227 KB of shared memory hold (the ring's depth
-  // covers the latency of the operand copies from L2)
-  static constexpr int kStages = (225 * 1024 - kTail) / kStage;
-  static constexpr uint32_t kBars = kStages * kStage + kTail;  // barrier block
-  static constexpr uint32_t kBytes = kBars + 256 + 1024;  // + alignment slack
+  // as many stages as the 225 KB region holds (the ring's depth covers the
+  // latency of the operand copies from L2), then the barrier block
+  static constexpr uint32_t kRegion = 225 * 1024;
+  static constexpr uint32_t kBytes = kRegion + 256 + 1024;  // + alignment slack
   // two accumulator buffers; allocations are powers of two columns
   static constexpr uint32_t kTmemCols = 2 * BN <= 128 ? 128 : (2 * BN <= 256 ? 256 : 512);
 };
@@ -210,6 +221,7 @@ struct OneInstance {
   __device__ int total() const { return P.mtiles * P.ntiles; }
   __device__ int* err() const { return P.err; }
   __device__ unsigned long long* trace() const { return P.trace; }
+  __device__ bool fused() const { return P.planes == 2; }
   __device__ const TcArgs& args(const TileRef&) const { return P; }
   __device__ TileRef tile(int tl) const {
     TileRef r;
@@ -268,9 +280,11 @@ struct PackedInstances {
   const int* start;
   int count;
   int* errp;
+  bool planes2;  // every member has two J planes (members share the count)
   __device__ int total() const { return start[count]; }
   __device__ int* err() const { return errp; }
   __device__ unsigned long long* trace() const { return nullptr; }
+  __device__ bool fused() const { return planes2; }
   __device__ const TcArgs& args(const TileRef& T) const { return *T.P; }
   __device__ TileRef tile(int tl) const {
     int lo = 0, hi = count - 1;
@@ -329,6 +343,7 @@ struct PairInstance {
   __device__ int total() const { return (P.mtiles + 1) / 2 * P.ntiles; }
   __device__ int* err() const { return P.err; }
   __device__ unsigned long long* trace() const { return P.trace; }
+  __device__ bool fused() const { return P.planes == 2; }
   __device__ const TcArgs& args(const TileRef&) const { return P; }
   __device__ TileRef tile(int tl) const {
     TileRef r;
@@ -361,13 +376,17 @@ template <int BN, int MODE, bool INT_E, bool FP8, class Src>
 __device__ __forceinline__ void step_tiles(const Src& src) {
   constexpr bool SPLIT = Src::kSplit;
   using Lay = TcLayout<BN, SPLIT>;
-  constexpr int STAGES = Lay::kStages;
   constexpr int kBK = FP8 ? 128 : 64;  // elements per 128-byte row
   static_assert(!Src::kPair || Lay::kKps == 1, "pair tiles take one k-block per stage");
+  // two J planes (every tile of the launch): stages of one k-block of both
+  // planes and its spin tile, the MMAs taking the planes k-block by k-block
+  const bool fused = !FP8 && src.fused();
+  const uint32_t kSt = fused ? Lay::kStage2 : Lay::kStage;
+  const int STAGES = (int)((Lay::kRegion - Lay::kTail) / kSt);
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + Lay::kBars);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + (uint32_t)STAGES * kSt + Lay::kTail);
   uint64_t* empty = full + STAGES;
   uint64_t* acc_full = empty + STAGES;
   uint64_t* acc_empty = acc_full + 2;
@@ -427,7 +446,9 @@ __device__ __forceinline__ void step_tiles(const Src& src) {
         if (T.skip) continue;
         const TcArgs& P = src.args(T);
         const int nk = P.nk, nfull = P.nfull, planes = P.planes;
-        const int nkt = nk * planes;
+        // k-steps of the ring: k-blocks (fused), else k-blocks of each plane
+        const int nkt = fused ? nk : nk * planes;
+        const int kps = fused ? 1 : Lay::kKps;
         if (Src::kGlobalMaps) {
           if (jside) {
             for (int p = 0; p < planes; ++p) {
@@ -440,21 +461,41 @@ __device__ __forceinline__ void step_tiles(const Src& src) {
           }
         }
         if (issued == 0) tc::prefetch_map(jside ? T.A0 : T.B);
-        for (int kt0 = 0; kt0 < nkt; kt0 += Lay::kKps) {
+        for (int kt0 = 0; kt0 < nkt; kt0 += kps) {
           if (!tc::mbar_wait(&empty[stage], phase ^ 1, abort_flag, kWaitCycles)) {
             ok = false;
             break;
           }
-          uint8_t* sa = smem + stage * Lay::kStage;
-          const int cnt = nkt - kt0 < Lay::kKps ? nkt - kt0 : Lay::kKps;
+          uint8_t* sa = smem + stage * kSt;
+          const int cnt = nkt - kt0 < kps ? nkt - kt0 : kps;
           // split pairs: every copy of the pair lands on the first CTA's
           // barrier, whose producers expect both CTAs' bytes
           if (!SPLIT || lead)
-            tc::mbar_expect_tx(&full[stage], (uint32_t)cnt * (jside ? Lay::kA : Lay::kB) *
-                                                 (SPLIT ? 2u : 1u));
+            tc::mbar_expect_tx(&full[stage], (uint32_t)(fused && jside ? planes : cnt) *
+                                                 (jside ? Lay::kA : Lay::kB) * (SPLIT ? 2u : 1u));
           const uint32_t lead_full = SPLIT ? tc::mapa(tc::smem_u32(&full[stage]), 0) : 0u;
           const int plane0 = kt0 / nk, kb0 = kt0 - plane0 * nk;
-          if (Lay::kKps == 2 && kb0 + 1 < nfull) {
+          if (fused) {
+            // k-block kt0 of every plane (slots 0, 1), its spin tile (slot 2)
+            const int kb = kt0;
+            uint8_t* sb = sa + 2 * Lay::kA;
+            if (jside) {
+              for (int p = 0; p < planes; ++p) {
+                if (SPLIT && !lead)
+                  tc::tma_load_2d_to_pair(sa + p * Lay::kA, T.a(p), lead_full, kb * kBK, T.m0, pol);
+                else
+                  tc::tma_load_2d_hint(sa + p * Lay::kA, T.a(p), &full[stage], kb * kBK, T.m0, pol);
+              }
+            } else if constexpr (SPLIT) {
+              if (lead) tc::tma_load_2d_hint(sb, T.B, &full[stage], kb * kBK, T.n0, pol);
+              else tc::tma_load_2d_to_pair(sb, T.B, lead_full, kb * kBK, T.n0 + BN / 2, pol);
+            } else if constexpr (Src::kPair) {
+              tc::tma_load_2d_mc(sb + src.rank * (BN / 2) * kRowBytes, T.B, &full[stage], kb * kBK,
+                                 T.n0 + (int)src.rank * (BN / 2), 0x3, pol);
+            } else {
+              tc::tma_load_2d_hint(sb, T.B, &full[stage], kb * kBK, T.n0, pol);
+            }
+          } else if (Lay::kKps == 2 && kb0 + 1 < nfull) {
             // two whole k-blocks of one plane: one copy per operand
             if (jside) tc::tma_load_3d_hint(sa, T.j2(plane0), &full[stage], 0, T.m0, kb0, pol);
             else
@@ -529,7 +570,9 @@ __device__ __forceinline__ void step_tiles(const Src& src) {
         const TileRef T = src.tile(tl);
         if (T.skip) continue;
         const TcArgs& P = src.args(T);
-        const int nkt = P.nk * P.planes;
+        const int planes = P.planes;
+        const int nkt = fused ? P.nk : P.nk * planes;
+        const int kps = fused ? 1 : Lay::kKps;
         const uint32_t idesc = op_idesc(BN, FP8, P.f16, SPLIT ? 256 : 128);
         const int buf = it & 1;
         const uint32_t use = (uint32_t)(it >> 1);
@@ -540,16 +583,32 @@ __device__ __forceinline__ void step_tiles(const Src& src) {
         }
         tc::fence_after_sync();
         const uint32_t d = tmem_base + (uint32_t)(buf * BN);
-        for (int kt0 = 0; kt0 < nkt; kt0 += Lay::kKps) {
+        for (int kt0 = 0; kt0 < nkt; kt0 += kps) {
           if (!tc::mbar_wait(&full[stage], phase, abort_flag, kWaitCycles)) {
             ok = false;
             break;
           }
           tc::fence_after_sync();
           if (it == 0 && kt0 == 0) ISING_TRACE(3);
-          const uint32_t sb = tc::smem_u32(smem + stage * Lay::kStage);
+          const uint32_t sb = tc::smem_u32(smem + stage * kSt);
+          if (fused) {
+            // k-block kt0: plane 0, then plane 1, against the one spin tile
+            const uint64_t db = tc::desc_k_sw128(sb + 2 * Lay::kA);
+#pragma unroll
+            for (int p = 0; p < 2; ++p) {
+              if (p >= planes) break;
+              const uint64_t da = tc::desc_k_sw128(sb + p * Lay::kA);
+#pragma unroll
+              for (int k = 0; k < 4; ++k) {
+                const uint32_t acc = (kt0 > 0 || p > 0 || k > 0) ? 1u : 0u;
+                if constexpr (SPLIT) tc::mma_f16_pair(d, da + 2u * k, db + 2u * k, idesc, acc);
+                else tc::mma_f16(d, da + 2u * k, db + 2u * k, idesc, acc);
+              }
+            }
+          }
 #pragma unroll
           for (int u = 0; u < Lay::kKps; ++u) {
+            if (fused) break;
             const int kt = kt0 + u;
             if (kt >= nkt) break;
             // descriptors of the tiles; K step k adds 32 bytes (2 in the >> 4 address field)
@@ -800,8 +859,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
 template <int BN, bool INT_E, bool FP8>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_pack_kernel(const PackEntry* __restrict__ entries, const int* __restrict__ start, int count,
-                   int* err) {
-  const PackedInstances<BN> src{entries, start, count, err};
+                   int* err, bool planes2) {
+  const PackedInstances<BN> src{entries, start, count, err, planes2};
   step_tiles<BN, kModeUpdate, INT_E, FP8>(src);
 }
 
@@ -1247,8 +1306,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       // the resident J tiles, once
       if (jres > 0) {
         tc::mbar_expect_tx(jfull, (uint32_t)jres * Lay::kA);
+        // (unit kt of a step is plane kt % planes of k-block kt / planes: the
+        // planes k-block by k-block, the order of every form)
         for (int kt = 0; kt < jres; ++kt) {
-          const int plane = kt / P.nk, kb = kt - plane * P.nk;
+          const int plane = kt % P.planes, kb = kt / P.planes;
           const CUtensorMap* ma = plane == 0 ? &tmA0 : (plane == 1 ? &tmA1 : &tmA2);
           tc::tma_load_2d(smem + (size_t)kt * Lay::kA, ma, jfull, kb * kBK, (int)m0);
         }
@@ -1286,8 +1347,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (kt < nkt) bytes += kt < jres ? Lay::kB : Lay::kA + Lay::kB;
           }
           tc::mbar_expect_tx(&full[stage], bytes);
-          const int plane0 = kt0 / P.nk, kb0 = kt0 - plane0 * P.nk;
-          if (kb0 + 1 < R.nfull) {
+          const int plane0 = kt0 % P.planes, kb0 = kt0 / P.planes;
+          if (P.planes == 1 && kb0 + 1 < R.nfull) {
             // two whole k-blocks of one plane: one box each for J and S (the
             // issue of a TMA instruction, not its bytes, paces this thread)
             if (kt0 >= jres) {
@@ -1303,7 +1364,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int u = 0; u < Lay::kKps; ++u) {
               const int kt = kt0 + u;
               if (kt >= nkt) break;
-              const int plane = kt / P.nk, kb = kt - plane * P.nk;
+              const int plane = kt % P.planes, kb = kt / P.planes;
               if (kt >= jres) {
                 const CUtensorMap* ma = plane == 0 ? &tmA0 : (plane == 1 ? &tmA1 : &tmA2);
                 tc::tma_load_2d(sa + u * Lay::kA, ma, &full[stage], kb * kBK, (int)m0);
@@ -1632,8 +1693,9 @@ __global__ void __launch_bounds__(kSmallThreads, 1)
   if (threadIdx.x == 0) {
     // all of J (every plane and k-block) and S_{t0+1} of this block of restarts
     tc::mbar_expect_tx(tma_bar, (uint32_t)nkt * Lay::kA + (uint32_t)nk * Lay::kSk);
+    // (tile kt: plane kt % planes of k-block kt / planes, the MMAs' order)
     for (int kt = 0; kt < nkt; ++kt) {
-      const int plane = kt / nk, kb = kt - plane * nk;
+      const int plane = kt % P.planes, kb = kt / P.planes;
       const CUtensorMap* ma = plane == 0 ? &tmA0 : (plane == 1 ? &tmA1 : &tmA2);
       tc::tma_load_2d(Jsm + (size_t)kt * Lay::kA, ma, tma_bar, kb * kBK, 0);
     }
@@ -1738,7 +1800,7 @@ __global__ void __launch_bounds__(kSmallThreads, 1)
     if (warp == 0) {
       if (lane == 0) {
         for (int kt = 0; kt < nkt; ++kt) {
-          const int kb = kt % nk;
+          const int kb = kt / P.planes;
           // descriptors of the tiles; K step k adds 32 bytes (2 in the >> 4 address field)
           const uint64_t da = tc::desc_k_sw128(tc::smem_u32(Jsm + (size_t)kt * Lay::kA));
           const uint64_t db = tc::desc_k_sw128(tc::smem_u32(Scur + (size_t)kb * Lay::kSk));
@@ -2566,10 +2628,17 @@ bool tc_packable(const ising_ds* ds) {
 
 uint64_t tc_pack_key(const ising_ds* ds) {
   auto st = static_cast<const TcState*>(ds->tc);
-  return (st->fp8 ? 1u : 0u) | (ds->int_energy ? 2u : 0u);
+  // members of one launch share the operand type, the energy mode and the
+  // number of J planes (which sets the stage layout of the launch)
+  return (st->fp8 ? 1u : 0u) | (ds->int_energy ? 2u : 0u) | (ds->planes == 2 ? 4u : 0u);
 }
 
 int tc_bn(const ising_ds* ds) { return static_cast<const TcState*>(ds->tc)->BN; }
+
+int tc_tile_pair(const ising_ds* ds) {
+  auto st = static_cast<const TcState*>(ds->tc);
+  return st->pair ? (st->split ? 2 : 1) : 0;
+}
 
 // Restart-tile widths the streaming form can take for this session (tiles at
 // least half used); none for the resident forms.
@@ -2665,7 +2734,7 @@ int tc_pack_entry(ising_ds* ds, void* host_entry) {
 namespace {
 template <int BN, bool INT_E, bool FP8>
 int pack_launch_t(ising_ctx* ctx, const void* entries, const int* start, int count, int tiles,
-                  int* err) {
+                  int* err, bool planes2) {
   auto kern = tc_pack_kernel<BN, INT_E, FP8>;
   const size_t smem = TcLayout<BN>::kBytes;
   static bool attr_set = false;  // per instantiation
@@ -2674,29 +2743,30 @@ int pack_launch_t(ising_ctx* ctx, const void* entries, const int* start, int cou
     attr_set = true;
   }
   const int grid = std::max(1, std::min(tiles, ctx->sm_count));
-  kern<<<grid, kThreads, smem, ctx->stream>>>(static_cast<const PackEntry*>(entries), start, count, err);
+  kern<<<grid, kThreads, smem, ctx->stream>>>(static_cast<const PackEntry*>(entries), start, count, err,
+                                              planes2);
   ISING_CUDA(ctx, cudaGetLastError());
   return ISING_OK;
 }
 
 template <int BN>
-int pack_launch_bn(ising_ctx* ctx, bool ie, bool fp8, const void* entries, const int* start,
-                   int count, int tiles, int* err) {
-  if (ie) return fp8 ? pack_launch_t<BN, true, true>(ctx, entries, start, count, tiles, err)
-                     : pack_launch_t<BN, true, false>(ctx, entries, start, count, tiles, err);
-  return fp8 ? pack_launch_t<BN, false, true>(ctx, entries, start, count, tiles, err)
-             : pack_launch_t<BN, false, false>(ctx, entries, start, count, tiles, err);
+int pack_launch_bn(ising_ctx* ctx, bool ie, bool fp8, bool p2, const void* entries,
+                   const int* start, int count, int tiles, int* err) {
+  if (ie) return fp8 ? pack_launch_t<BN, true, true>(ctx, entries, start, count, tiles, err, p2)
+                     : pack_launch_t<BN, true, false>(ctx, entries, start, count, tiles, err, p2);
+  return fp8 ? pack_launch_t<BN, false, true>(ctx, entries, start, count, tiles, err, p2)
+             : pack_launch_t<BN, false, false>(ctx, entries, start, count, tiles, err, p2);
 }
 }  // namespace
 
 int tc_pack_launch(ising_ctx* ctx, uint64_t key, int bn, const void* entries, const int* start,
                    int count, int tiles, int* err) {
-  const bool fp8 = key & 1u, ie = (key & 2u) != 0;
+  const bool fp8 = key & 1u, ie = (key & 2u) != 0, p2 = (key & 4u) != 0;
   switch (bn) {
-    case 256: return pack_launch_bn<256>(ctx, ie, fp8, entries, start, count, tiles, err);
-    case 224: return pack_launch_bn<224>(ctx, ie, fp8, entries, start, count, tiles, err);
-    case 128: return pack_launch_bn<128>(ctx, ie, fp8, entries, start, count, tiles, err);
-    case 64: return pack_launch_bn<64>(ctx, ie, fp8, entries, start, count, tiles, err);
+    case 256: return pack_launch_bn<256>(ctx, ie, fp8, p2, entries, start, count, tiles, err);
+    case 224: return pack_launch_bn<224>(ctx, ie, fp8, p2, entries, start, count, tiles, err);
+    case 128: return pack_launch_bn<128>(ctx, ie, fp8, p2, entries, start, count, tiles, err);
+    case 64: return pack_launch_bn<64>(ctx, ie, fp8, p2, entries, start, count, tiles, err);
     default: return fail(ctx, ISING_EINVAL, "pack: unknown tile width");
   }
 }

@@ -187,7 +187,7 @@ extern "C" int ising_pack_create(ising_ctx* ctx, ising_ds* const* sessions, int3
     const uint64_t kk = tc_pack_key(ds);
     if (k == 0) key = kk;
     else if (kk != key)
-      return fail(ctx, ISING_EINVAL, "pack: members differ in operand type or energy mode (member %d)", k);
+      return fail(ctx, ISING_EINVAL, "pack: members differ in operand type, energy mode or J planes (member %d)", k);
   }
   auto pk = new ising_pack();
   pk->ctx = ctx;

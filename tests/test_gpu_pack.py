@@ -107,6 +107,21 @@ def test_pack_rejects_mixed_and_unsupported_members(gpu_ctx):
     i = api.Session(gpu_ctx, _e4m3_members()[0][0], restarts=256, steps=5, streaming=True)
     with pytest.raises(api.IsingError):
         api.Pack(gpu_ctx, [f, i])  # E4M3 and 16-bit operands in one launch
+    # integer couplings: |J| <= 100 in one BF16 plane, up to 3000 in two FP16
+    # planes (a launch's stages hold one plane count)
+    one = api.Session(gpu_ctx, synth.random_sparse_instance(200, 44, p=0.1, kind="int", h="int",
+                                                            layout="dense", jmax=100),
+                      restarts=128, steps=5, streaming=True)
+    two = api.Session(gpu_ctx, synth.random_sparse_instance(200, 45, p=0.1, kind="int", h="int",
+                                                            layout="dense", jmax=3000),
+                      restarts=128, steps=5, streaming=True)
+    one.run(1)
+    two.run(1)
+    assert (one.result()["operand_planes"], two.result()["operand_planes"]) == (1, 2)
+    with pytest.raises(api.IsingError):
+        api.Pack(gpu_ctx, [one, two])
+    one.close()
+    two.close()
     r = api.Session(gpu_ctx, _e4m3_members()[1][0], restarts=100, steps=5)  # resident form
     with pytest.raises(api.IsingError):
         api.Pack(gpu_ctx, [r])
