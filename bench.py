@@ -187,11 +187,18 @@ def launches_per_solve(T: int, rounds: int, path: int, resident: bool, rowsum: b
     field 3), session set-up (fills 2, init 1, operand 1, plus the row-sum
     bound when the tensor-core path accumulates integer energies: `rowsum`,
     plus the per-row scales of row-scaled operands: `rowscale`), the steps
-    (one launch when resident, else step + track per step, plus the copy of
-    improved bit-packed spins on the sparse path), finish (energy-only step +
-    track (+ copy) + argmin), reconstruction (1), full-instance energy (2)."""
+    (one launch when resident; on the streaming tensor-core path one launch
+    per step, each also tracking its predecessor, plus one tracking launch
+    for the last step; else step + track per step, plus the copy of improved
+    bit-packed spins on the sparse path), finish (energy-only step + track
+    (+ copy) + argmin), reconstruction (1), full-instance energy (2)."""
     per_step = 3 if path == 2 else 2
-    steps = 1 if resident else per_step * T
+    if resident:
+        steps = 1
+    elif path == 1:
+        steps = T + 1
+    else:
+        steps = per_step * T
     setup = 4 + (1 if rowsum else 0) + (1 if rowscale else 0)
     return 3 + 3 + 7 * (rounds + 1) + 3 + setup + steps + per_step + 1 + 1 + 2
 

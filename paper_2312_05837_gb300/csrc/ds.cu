@@ -103,82 +103,19 @@ __device__ __forceinline__ int8_t spin_at(const void* spins, int64_t n, int64_t 
   return (w >> (b & 31)) & 1u ? 1 : -1;
 }
 
-// Best tracking of restart b at step t, by one warp: E_t(b) from the
-// partials of slot t % 2 (lane l adds rows l, l+32, ... in order, then a
-// fixed xor tree across lanes, so the sum is deterministic), strict <
-// against the best so far, copy of S_t for an improved restart (for
-// bit-packed spins a per-restart flag instead, which track_bits_copy_kernel
-// reads). With the convergence rule (conv_step non-null) a stopped restart
-// is left alone, and steps t <= T feed the rule.
-template <int KIND>
-__device__ __forceinline__ void track_restart(const TrackArgs& A, long long t, int64_t b, int lane) {
-  const int ps = (int)(t % 2);
-  double E;
-  if (A.int_mode) {
-    const long long* qpart = A.qpart[ps];
-    const long long* hpart = A.hpart[ps];
-    long long q = 0, hs = 0;
-#pragma unroll 4
-    for (int r = lane; r < A.mtiles; r += 32) {
-      q += qpart[(int64_t)r * A.Bp + b];
-      hs += hpart[(int64_t)r * A.Bp + b];
-    }
-    for (int o = 16; o; o >>= 1) {
-      q += __shfl_xor_sync(0xffffffffu, q, o);
-      hs += __shfl_xor_sync(0xffffffffu, hs, o);
-    }
-    E = A.cq * (double)q + A.chs * (double)hs;
-  } else {
-    const float* epart = A.epart[ps];
-    double e = 0.0;
-#pragma unroll 4
-    for (int r = lane; r < A.mtiles; r += 32) e += (double)epart[(int64_t)r * A.Bp + b];
-    for (int o = 16; o; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
-    E = e;
-  }
-  // every lane holds the same E (the xor tree is symmetric)
-  const bool active = A.conv_step == nullptr || A.conv_step[b] == 0;
-  const bool improved = active && E < A.best_E[b];
-  __syncwarp();
-  if (lane == 0 && active) {
-    A.last_E[b] = E;
-    if (improved) {
-      A.best_E[b] = E;
-      A.best_t[b] = t;
-    }
-    if (A.conv_step && t <= A.T &&
-        conv_update(A.conv_ring, A.conv_init, A.conv_step, A.conv_count, A.B, b, t, E) && A.live32)
-      atomicSub(&A.live32[b >> 5], 1);
-  }
-  if (KIND == kSpinBits) {
-    if (A.inline_bits) {
-      // bit b of each spin's word column, one spin per lane and pass
-      if (improved) {
-        const uint32_t* bits = static_cast<const uint32_t*>(A.spins[t % 3]);
-        const int64_t words = A.Bp / 32;
-        int8_t* dst = A.best_s + b * A.bs_ld;
-        for (int64_t i = lane; i < A.n; i += 32)
-          dst[i] = ((bits[i * words + (b >> 5)] >> (b & 31)) & 1u) ? 1 : -1;
-      }
-    } else if (lane == 0) {
-      // bit-packed spins are copied by track_bits_copy_kernel
-      A.improved[b] = improved ? 1 : 0;
-    }
-  } else if (improved) {
-    copy_spin_row_dense<KIND>(A.best_s + b * A.bs_ld, A.spins[t % 3], A.n, A.ld, b, lane);
-  }
-}
-
 // Best tracking for step t = counters[0] + 1 of one session, one warp per
-// restart; the last block advances the step counter.
+// restart; the last block advances the step counter. With A.flush, the step
+// the counter names (already advanced by a step launch that tracks its
+// predecessor) is tracked and the counter is left alone.
 template <int KIND>
 __global__ void __launch_bounds__(256) track_kernel(const TrackArgs A) {
-  const long long t = A.counters[0] + 1;
+  const long long t = A.counters[0] + (A.flush ? 0 : 1);
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t b = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); b < A.B;
        b += warps)
     track_restart<KIND>(A, t, b, lane);
+  if (A.flush) return;
   __shared__ bool last;
   __syncthreads();
   __threadfence();
@@ -435,6 +372,7 @@ TrackArgs track_args(const ising_ds* ds) {
   A.conv_count = conv ? ds->conv_count() : nullptr;
   A.live32 = conv ? ds->live.as<int>() : nullptr;
   A.inline_bits = false;
+  A.flush = false;
   return A;
 }
 
@@ -470,6 +408,21 @@ int track_step(ising_ds* ds) {
           ds->best_s.as<int8_t>(), ds->bs_ld);
       break;
     }
+  }
+  ISING_CUDA(ctx, cudaGetLastError());
+  return ISING_OK;
+}
+
+int track_flush(ising_ds* ds) {
+  ising_ctx* ctx = ds->ctx;
+  const int grid = (int)std::min<int64_t>((ds->B + 7) / 8, (int64_t)ctx->sm_count * 4);
+  TrackArgs A = track_args(ds);
+  A.flush = true;
+  switch (ds->spin_kind) {
+    case kSpinE4M3: track_kernel<kSpinE4M3><<<grid, 256, 0, ctx->stream>>>(A); break;
+    case kSpinBF16:
+    case kSpinF16: track_kernel<kSpinBF16><<<grid, 256, 0, ctx->stream>>>(A); break;
+    default: return fail(ctx, ISING_EINVAL, "tracking flush: spin kind %d", ds->spin_kind);
   }
   ISING_CUDA(ctx, cudaGetLastError());
   return ISING_OK;
@@ -826,6 +779,15 @@ namespace {
 
 constexpr int64_t kGraphSteps = 48;  // a multiple of the launch period 6
 
+// Whether the update launches of this session track the step before theirs
+// (the streaming tensor-core form without the convergence rule or the
+// relaxed product): a step then takes one launch instead of two, and the
+// last step of each run is tracked by a flush launch. Tracking a step twice
+// changes nothing (strict < against the best, the same last energy).
+bool fold_ok(ising_ds* ds) {
+  return ds->path == ISING_PATH_TC && !tc_is_resident(ds) && !ds->relaxed() && !ds->conv.p;
+}
+
 // Captures kGraphSteps steps (step kernel + tracking) into a graph on a
 // private stream; the host step counter is restored afterwards because
 // capture does not execute anything.
@@ -839,11 +801,14 @@ int build_graph(ising_ds* ds) {
   ctx->stream = ds->gstream;
   cudaGraph_t g = nullptr;
   int rc = ISING_OK;
+  const bool fold = fold_ok(ds);
   cudaError_t e = cudaStreamBeginCapture(ds->gstream, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
     for (int64_t s = 0; s < kGraphSteps && rc == ISING_OK; ++s) {
+      ds->fold_track = fold;
       rc = path_step_raw(ds, true);
-      if (rc == ISING_OK) rc = track_step(ds);
+      ds->fold_track = false;
+      if (rc == ISING_OK && !fold) rc = track_step(ds);
       ds->t += 1;
     }
     e = cudaStreamEndCapture(ds->gstream, &g);
@@ -1041,6 +1006,7 @@ int ising::ds_advance(ising_ds* ds, int64_t todo) {
   if (ds->path == ISING_PATH_SPARSE && !ds->tuned) ISING_TRY(autotune_sparse(ds, todo, &s0));
   if (ds->path == ISING_PATH_TC && !ds->tuned) ISING_TRY(autotune_dense(ds, todo, &s0));
   const bool use_graph = !(ds->p.flags & ISING_DS_PROFILE) && todo >= 2 * kGraphSteps;
+  const bool fold = fold_ok(ds);
   for (int64_t s = s0; s < todo;) {
     // (t > 0: the kernels have run once outside capture, which sets their attributes)
     if (use_graph && ds->t > 0 && ds->t % 6 == 0 && todo - s >= kGraphSteps) {
@@ -1048,12 +1014,17 @@ int ising::ds_advance(ising_ds* ds, int64_t todo) {
       ISING_TRY(replay_graph(ds));
       s += kGraphSteps;
     } else {
-      ISING_TRY(path_step(ds, true));
-      ISING_TRY(track_step(ds));
+      ds->fold_track = fold;
+      const int rc = path_step(ds, true);
+      ds->fold_track = false;
+      ISING_TRY(rc);
+      if (!fold) ISING_TRY(track_step(ds));
       ds->t += 1;
       s += 1;
     }
   }
+  // the last step's tracking (its launch tracked only its predecessor)
+  if (fold && todo > s0) ISING_TRY(track_flush(ds));
   return ISING_OK;
 }
 

@@ -170,7 +170,76 @@ struct TrackArgs {
   // bit-packed spins: copy an improved restart's spins here (small n)
   // instead of flagging it for track_bits_copy_kernel
   bool inline_bits;
+  // track the step counters[0] names, without advancing the counter (the
+  // last step of a run whose step launches tracked their predecessors)
+  bool flush;
 };
+
+// Best tracking of restart b at step t, by one warp: E_t(b) from the
+// partials of slot t % 2 (lane l adds rows l, l+32, ... in order, then a
+// fixed xor tree across lanes, so the sum is deterministic), strict <
+// against the best so far, copy of S_t for an improved restart (for
+// bit-packed spins a per-restart flag instead, which track_bits_copy_kernel
+// reads). With the convergence rule (conv_step non-null) a stopped restart
+// is left alone, and steps t <= T feed the rule.
+template <int KIND>
+__device__ __forceinline__ void track_restart(const TrackArgs& A, long long t, int64_t b, int lane) {
+  const int ps = (int)(t % 2);
+  double E;
+  if (A.int_mode) {
+    const long long* qpart = A.qpart[ps];
+    const long long* hpart = A.hpart[ps];
+    long long q = 0, hs = 0;
+#pragma unroll 4
+    for (int r = lane; r < A.mtiles; r += 32) {
+      q += qpart[(int64_t)r * A.Bp + b];
+      hs += hpart[(int64_t)r * A.Bp + b];
+    }
+    for (int o = 16; o; o >>= 1) {
+      q += __shfl_xor_sync(0xffffffffu, q, o);
+      hs += __shfl_xor_sync(0xffffffffu, hs, o);
+    }
+    E = A.cq * (double)q + A.chs * (double)hs;
+  } else {
+    const float* epart = A.epart[ps];
+    double e = 0.0;
+#pragma unroll 4
+    for (int r = lane; r < A.mtiles; r += 32) e += (double)epart[(int64_t)r * A.Bp + b];
+    for (int o = 16; o; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+    E = e;
+  }
+  // every lane holds the same E (the xor tree is symmetric)
+  const bool active = A.conv_step == nullptr || A.conv_step[b] == 0;
+  const bool improved = active && E < A.best_E[b];
+  __syncwarp();
+  if (lane == 0 && active) {
+    A.last_E[b] = E;
+    if (improved) {
+      A.best_E[b] = E;
+      A.best_t[b] = t;
+    }
+    if (A.conv_step && t <= A.T &&
+        conv_update(A.conv_ring, A.conv_init, A.conv_step, A.conv_count, A.B, b, t, E) && A.live32)
+      atomicSub(&A.live32[b >> 5], 1);
+  }
+  if (KIND == kSpinBits) {
+    if (A.inline_bits) {
+      // bit b of each spin's word column, one spin per lane and pass
+      if (improved) {
+        const uint32_t* bits = static_cast<const uint32_t*>(A.spins[t % 3]);
+        const int64_t words = A.Bp / 32;
+        int8_t* dst = A.best_s + b * A.bs_ld;
+        for (int64_t i = lane; i < A.n; i += 32)
+          dst[i] = ((bits[i * words + (b >> 5)] >> (b & 31)) & 1u) ? 1 : -1;
+      }
+    } else if (lane == 0) {
+      // bit-packed spins are copied by track_bits_copy_kernel
+      A.improved[b] = improved ? 1 : 0;
+    }
+  } else if (improved) {
+    copy_spin_row_dense<KIND>(A.best_s + b * A.bs_ld, A.spins[t % 3], A.n, A.ld, b, lane);
+  }
+}
 
 // What a step launch does: the full update, only the energies of the input
 // spins (the final evaluation), or only the coupling product G = J s.
@@ -219,6 +288,9 @@ struct ising_ds {
   // out like the state (FP32; the 16-bit operand type on the tensor-core path)
   ising::DevMem xbuf[2];
   bool relaxed() const { return (p.flags & ISING_DS_RELAXED) != 0; }
+  // the update launches being queued also track the step before theirs and
+  // advance the step counter (streaming tensor-core form; see ds_advance)
+  bool fold_track = false;
   double* conv_ring() const { return conv.as<double>(); }
   double* conv_init() const { return conv.as<double>() + 5 * B; }
   long long* conv_step() const { return reinterpret_cast<long long*>(conv.as<double>() + 6 * B); }
@@ -279,6 +351,7 @@ int ds_advance(ising_ds* ds, int64_t todo);  // queue steps without waiting
 int ds_create_impl(ising_ctx* ctx, const ising_instance* inst, const ising_ds_params* p,
                    ising_ds** out, bool validate);
 int track_step(ising_ds* ds);  // reduce partials of step t+1, best tracking, t += 1
+int track_flush(ising_ds* ds);  // best tracking of step t (counter already advanced)
 TrackArgs track_args(const ising_ds* ds);
 // Best tracking of every member of a pack (device arrays: members[count],
 // rstart[count + 1] restart offsets, `done` a zeroed block counter).

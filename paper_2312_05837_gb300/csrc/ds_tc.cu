@@ -92,6 +92,11 @@ struct TcArgs {
   int nfull;   // streaming kernel: whole k-blocks loadable in pairs (0: never pair)
   const int* live32;          // convergence rule: live restarts per 32 (tiles retire), or null
   unsigned long long* work;   // restart-steps computed (update launches), or null
+  // update launches of one instance: track the step before this one (the
+  // epilogue warps, while the first tile's products run) and advance the
+  // step counter at the end, instead of a tracking launch after each step
+  int fold = 0;
+  TrackArgs trk;
 };
 
 // +1 / -1 in the 16-bit operand type (FP16 0x3C00, BF16 0x3F80; bit 15 is the
@@ -212,6 +217,7 @@ struct OneInstance {
   static constexpr bool kGlobalMaps = false;  // kernel parameters
   static constexpr bool kPair = false;
   static constexpr bool kSplit = false;
+  static constexpr bool kFold = true;  // may track the previous step (TcArgs::fold)
   const TcArgs& P;  // the kernel's parameter
   const CUtensorMap *A0, *A1, *A2, *B, *J0, *J1, *J2, *S2;
   __device__ int first() const { return blockIdx.x; }
@@ -266,6 +272,7 @@ struct PackedInstances {
   static constexpr bool kGlobalMaps = true;  // copied to device memory by the host
   static constexpr bool kPair = false;
   static constexpr bool kSplit = false;
+  static constexpr bool kFold = false;  // members are tracked by one launch after the step
   __device__ int first() const { return blockIdx.x; }
   __device__ int stride() const { return gridDim.x; }
   // the CTA's j-th tile: the tiles are taken wave by wave (a wave is one
@@ -332,6 +339,7 @@ struct PairInstance {
   static constexpr bool kGlobalMaps = false;
   static constexpr bool kPair = true;
   static constexpr bool kSplit = SPLIT;
+  static constexpr bool kFold = true;
   const TcArgs& P;
   const CUtensorMap *A0, *A1, *A2, *B, *J0, *J1, *J2, *S2;
   const CUtensorMap* Bh;  // S_t, boxes of one k-block x BN / 2 restarts
@@ -653,6 +661,19 @@ __device__ __forceinline__ void step_tiles(const Src& src) {
     const int q = warp & 3;             // TMEM lane quarter of this warp
     const int part = (warp - 4) >> 2;   // which quarter of the tile's columns
     constexpr int kCols = BN / 4;
+    if constexpr (MODE == kModeUpdate && Src::kFold) {
+      // the previous step's best tracking, a warp per restart over all the
+      // launch's epilogue warps, while the MMAs of the first tile run (it
+      // reads that step's partial and spin slots, which this step does not
+      // write)
+      const TcArgs& P0 = src.P;
+      const long long tp = P0.counters[0];
+      if (P0.fold && tp >= 1) {
+        const int64_t nw = (int64_t)gridDim.x * kEpiWarps;
+        for (int64_t b = (int64_t)blockIdx.x * kEpiWarps + (warp - 4); b < P0.trk.B; b += nw)
+          track_restart<FP8 ? kSpinE4M3 : kSpinBF16>(P0.trk, tp, b, lane);
+      }
+    }
     int it = 0;
     for (int j = 0, tl = src.at(0); tl < total; tl = src.at(++j)) {
       const TileRef T = src.tile(tl);
@@ -801,6 +822,20 @@ __device__ __forceinline__ void step_tiles(const Src& src) {
   // memory or arrive on its barriers
   if (Src::kPair) tc::cluster_sync();
   if (threadIdx.x == 0) ISING_TRACE(7);
+  if constexpr (MODE == kModeUpdate && Src::kFold) {
+    // the last CTA to get here advances the step counter (every CTA has read
+    // it by then)
+    if (src.P.fold && threadIdx.x == 0) {
+      long long* ctr = src.P.trk.counters;
+      __threadfence();
+      const unsigned long long prev = atomicAdd(reinterpret_cast<unsigned long long*>(&ctr[1]), 1ull);
+      if (prev == gridDim.x - 1) {
+        ctr[0] = ctr[0] + 1;
+        ctr[1] = 0;
+        __threadfence();
+      }
+    }
+  }
   if (warp == 1) {
     tc::fence_after_sync();
     if constexpr (SPLIT) tc::tmem_dealloc_pair(tmem_base, Lay::kTmemCols);
@@ -2439,6 +2474,10 @@ int tc_run(ising_ds* ds, int mode, float* Gout) {
   a.trace = nullptr;
   a.live32 = ds->live.p ? ds->live.as<int>() : nullptr;
   a.work = ds->work.as<unsigned long long>();
+  if (mode == kModeUpdate && ds->fold_track) {
+    a.fold = 1;
+    a.trk = track_args(ds);
+  }
   if (ds->p.flags & ISING_DS_PROFILE) {
     if (!st->trace.p) ISING_TRY(dev_alloc(ds->ctx, st->trace, (size_t)st->grid * 8 * 8));
     a.trace = st->trace.as<unsigned long long>();
