@@ -134,11 +134,13 @@ __global__ void __launch_bounds__(256) track_kernel(const TrackArgs A) {
 // Best tracking of every member of a pack, each at its own step t =
 // counters[0] + 1: member e owns the restarts [rstart[e], rstart[e + 1]) of
 // the launch, one warp per restart; the last block advances every member's
-// step counter (`done` counts finished blocks and is reset).
+// step counter (`done` counts finished blocks and is reset). With `flush`,
+// each member at t = counters[0], the counters left alone.
 template <int KIND>
 __global__ void __launch_bounds__(256) track_pack_kernel(const TrackArgs* __restrict__ M,
                                                          const int64_t* __restrict__ rstart,
-                                                         int count, unsigned long long* done) {
+                                                         int count, unsigned long long* done,
+                                                         bool flush) {
   const int lane = threadIdx.x & 31;
   const int64_t total = rstart[count];
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -150,8 +152,10 @@ __global__ void __launch_bounds__(256) track_pack_kernel(const TrackArgs* __rest
       if (rstart[mid] <= g) lo = mid; else hi = mid - 1;
     }
     const TrackArgs& A = M[lo];
-    track_restart<KIND>(A, A.counters[0] + 1, g - rstart[lo], lane);
+    const long long t = A.counters[0] + (flush ? 0 : 1);
+    if (t >= 1) track_restart<KIND>(A, t, g - rstart[lo], lane);
   }
+  if (flush) return;
   __shared__ bool last;
   __syncthreads();
   __threadfence();
@@ -429,16 +433,16 @@ int track_flush(ising_ds* ds) {
 }
 
 int track_pack(ising_ctx* ctx, int spin_kind, const TrackArgs* members, const int64_t* rstart,
-               int count, int64_t total_restarts, unsigned long long* done) {
+               int count, int64_t total_restarts, unsigned long long* done, bool flush) {
   const int grid = (int)std::max<int64_t>(
       1, std::min<int64_t>((total_restarts + 7) / 8, (int64_t)ctx->sm_count * 4));
   switch (spin_kind) {
     case kSpinE4M3:
-      track_pack_kernel<kSpinE4M3><<<grid, 256, 0, ctx->stream>>>(members, rstart, count, done);
+      track_pack_kernel<kSpinE4M3><<<grid, 256, 0, ctx->stream>>>(members, rstart, count, done, flush);
       break;
     case kSpinBF16:
     case kSpinF16:
-      track_pack_kernel<kSpinBF16><<<grid, 256, 0, ctx->stream>>>(members, rstart, count, done);
+      track_pack_kernel<kSpinBF16><<<grid, 256, 0, ctx->stream>>>(members, rstart, count, done, flush);
       break;
     default: return fail(ctx, ISING_ENOTSUP, "packed tracking: dense spin slots only");
   }

@@ -355,8 +355,11 @@ int track_flush(ising_ds* ds);  // best tracking of step t (counter already adva
 TrackArgs track_args(const ising_ds* ds);
 // Best tracking of every member of a pack (device arrays: members[count],
 // rstart[count + 1] restart offsets, `done` a zeroed block counter).
+// Best tracking of every pack member at counters[0] + 1, advancing the
+// counters; with `flush`, at counters[0] (already advanced by packed update
+// launches that tracked their predecessors), counters left alone.
 int track_pack(ising_ctx* ctx, int spin_kind, const TrackArgs* members, const int64_t* rstart,
-               int count, int64_t total_restarts, unsigned long long* done);
+               int count, int64_t total_restarts, unsigned long long* done, bool flush = false);
 // Pack hooks of the tensor-core path (ds_tc.cu): whether the session can be
 // a pack member (streaming form, update-only), its pack key (members of one
 // launch share it), the bytes and contents of its device entry, and one
@@ -371,8 +374,15 @@ int tc_bn_candidates(const ising_ds* ds, int* out);   // widths the autotuner ma
 int tc_set_bn(ising_ds* ds, int code);                // a width, with kTcPair or not
 size_t tc_pack_entry_bytes();
 int tc_pack_entry(ising_ds* ds, void* host_entry);
+// What a packed update launch needs to track every member's previous step
+// itself (trk null: a tracking launch follows each step instead).
+struct PackFold {
+  const TrackArgs* trk = nullptr;  // the members' tracking arguments (device)
+  const int64_t* rstart = nullptr;  // their restart offsets (device)
+  unsigned long long* done = nullptr;  // the pack's CTA counter
+};
 int tc_pack_launch(ising_ctx* ctx, uint64_t key, int bn, const void* entries, const int* start,
-                   int count, int tiles, int* err);
+                   int count, int tiles, int* err, const PackFold& f);
 int export_spins_int8(ising_ds* ds, int slot, int8_t* out);  // spins[slot] -> int8 [B][n]
 
 }  // namespace ising

@@ -210,6 +210,24 @@ struct TileRef {
   __device__ const CUtensorMap* j2(int plane) const { return plane == 0 ? J0 : (plane == 1 ? J1 : J2); }
 };
 
+// Called by every CTA of a launch at its end: `done` counts the CTAs that
+// got here, and the last one (every CTA has read the step counters by then)
+// resets it and adds one to the step counter of the session (`ctr`) or of
+// each of `count` pack members (trk[e].counters).
+__device__ __forceinline__ void advance_counters(unsigned long long* done, long long* ctr,
+                                                 const TrackArgs* trk, int count) {
+  if (threadIdx.x != 0) return;
+  __threadfence();
+  if (atomicAdd(done, 1ull) != gridDim.x - 1) return;
+  if (trk) {
+    for (int e = 0; e < count; ++e) trk[e].counters[0] += 1;
+  } else {
+    ctr[0] += 1;
+  }
+  *done = 0;
+  __threadfence();
+}
+
 // Tiles of one instance: everything comes from the kernel's parameters (the
 // host chose the slots of step t), tiles numbered row tile by row tile.
 template <int BN>
@@ -228,6 +246,19 @@ struct OneInstance {
   __device__ int* err() const { return P.err; }
   __device__ unsigned long long* trace() const { return P.trace; }
   __device__ bool fused() const { return P.planes == 2; }
+  // (update launches with P.fold) the previous step's tracking, by warp gw
+  // of nw, and the counter advance by the last CTA
+  template <int KIND>
+  __device__ void track_prev(int64_t gw, int64_t nw, int lane) const {
+    const long long tp = P.counters[0];
+    if (!P.fold || tp < 1) return;
+    for (int64_t b = gw; b < P.trk.B; b += nw) track_restart<KIND>(P.trk, tp, b, lane);
+  }
+  __device__ void advance_step() const {
+    if (P.fold)
+      advance_counters(reinterpret_cast<unsigned long long*>(&P.trk.counters[1]), P.trk.counters,
+                       nullptr, 0);
+  }
   __device__ const TcArgs& args(const TileRef&) const { return P; }
   __device__ TileRef tile(int tl) const {
     TileRef r;
@@ -272,7 +303,7 @@ struct PackedInstances {
   static constexpr bool kGlobalMaps = true;  // copied to device memory by the host
   static constexpr bool kPair = false;
   static constexpr bool kSplit = false;
-  static constexpr bool kFold = false;  // members are tracked by one launch after the step
+  static constexpr bool kFold = true;  // may track every member's previous step (trk)
   __device__ int first() const { return blockIdx.x; }
   __device__ int stride() const { return gridDim.x; }
   // the CTA's j-th tile: the tiles are taken wave by wave (a wave is one
@@ -288,10 +319,32 @@ struct PackedInstances {
   int count;
   int* errp;
   bool planes2;  // every member has two J planes (members share the count)
+  // the members' tracking arguments and restart offsets when the launch
+  // tracks every member's previous step (else null)
+  const TrackArgs* trk;
+  const int64_t* rstart;
+  unsigned long long* done;  // the pack's CTA counter
   __device__ int total() const { return start[count]; }
   __device__ int* err() const { return errp; }
   __device__ unsigned long long* trace() const { return nullptr; }
   __device__ bool fused() const { return planes2; }
+  template <int KIND>
+  __device__ void track_prev(int64_t gw, int64_t nw, int lane) const {
+    if (!trk) return;
+    for (int64_t g = gw; g < rstart[count]; g += nw) {
+      int lo = 0, hi = count - 1;
+      while (lo < hi) {  // last member whose first restart is <= g
+        const int mid = (lo + hi + 1) >> 1;
+        if (rstart[mid] <= g) lo = mid; else hi = mid - 1;
+      }
+      const TrackArgs& A = trk[lo];
+      const long long tp = A.counters[0];
+      if (tp >= 1) track_restart<KIND>(A, tp, g - rstart[lo], lane);
+    }
+  }
+  __device__ void advance_step() const {
+    if (trk) advance_counters(done, nullptr, trk, count);
+  }
   __device__ const TcArgs& args(const TileRef& T) const { return *T.P; }
   __device__ TileRef tile(int tl) const {
     int lo = 0, hi = count - 1;
@@ -352,6 +405,17 @@ struct PairInstance {
   __device__ int* err() const { return P.err; }
   __device__ unsigned long long* trace() const { return P.trace; }
   __device__ bool fused() const { return P.planes == 2; }
+  template <int KIND>
+  __device__ void track_prev(int64_t gw, int64_t nw, int lane) const {
+    const long long tp = P.counters[0];
+    if (!P.fold || tp < 1) return;
+    for (int64_t b = gw; b < P.trk.B; b += nw) track_restart<KIND>(P.trk, tp, b, lane);
+  }
+  __device__ void advance_step() const {
+    if (P.fold)
+      advance_counters(reinterpret_cast<unsigned long long*>(&P.trk.counters[1]), P.trk.counters,
+                       nullptr, 0);
+  }
   __device__ const TcArgs& args(const TileRef&) const { return P; }
   __device__ TileRef tile(int tl) const {
     TileRef r;
@@ -666,13 +730,8 @@ __device__ __forceinline__ void step_tiles(const Src& src) {
       // launch's epilogue warps, while the MMAs of the first tile run (it
       // reads that step's partial and spin slots, which this step does not
       // write)
-      const TcArgs& P0 = src.P;
-      const long long tp = P0.counters[0];
-      if (P0.fold && tp >= 1) {
-        const int64_t nw = (int64_t)gridDim.x * kEpiWarps;
-        for (int64_t b = (int64_t)blockIdx.x * kEpiWarps + (warp - 4); b < P0.trk.B; b += nw)
-          track_restart<FP8 ? kSpinE4M3 : kSpinBF16>(P0.trk, tp, b, lane);
-      }
+      src.template track_prev<FP8 ? kSpinE4M3 : kSpinBF16>(
+          (int64_t)blockIdx.x * kEpiWarps + (warp - 4), (int64_t)gridDim.x * kEpiWarps, lane);
     }
     int it = 0;
     for (int j = 0, tl = src.at(0); tl < total; tl = src.at(++j)) {
@@ -822,20 +881,7 @@ __device__ __forceinline__ void step_tiles(const Src& src) {
   // memory or arrive on its barriers
   if (Src::kPair) tc::cluster_sync();
   if (threadIdx.x == 0) ISING_TRACE(7);
-  if constexpr (MODE == kModeUpdate && Src::kFold) {
-    // the last CTA to get here advances the step counter (every CTA has read
-    // it by then)
-    if (src.P.fold && threadIdx.x == 0) {
-      long long* ctr = src.P.trk.counters;
-      __threadfence();
-      const unsigned long long prev = atomicAdd(reinterpret_cast<unsigned long long*>(&ctr[1]), 1ull);
-      if (prev == gridDim.x - 1) {
-        ctr[0] = ctr[0] + 1;
-        ctr[1] = 0;
-        __threadfence();
-      }
-    }
-  }
+  if constexpr (MODE == kModeUpdate && Src::kFold) src.advance_step();
   if (warp == 1) {
     tc::fence_after_sync();
     if constexpr (SPLIT) tc::tmem_dealloc_pair(tmem_base, Lay::kTmemCols);
@@ -894,8 +940,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
 template <int BN, bool INT_E, bool FP8>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_pack_kernel(const PackEntry* __restrict__ entries, const int* __restrict__ start, int count,
-                   int* err, bool planes2) {
-  const PackedInstances<BN> src{entries, start, count, err, planes2};
+                   int* err, bool planes2, const TrackArgs* __restrict__ trk,
+                   const int64_t* __restrict__ rstart, unsigned long long* done) {
+  const PackedInstances<BN> src{entries, start, count, err, planes2, trk, rstart, done};
   step_tiles<BN, kModeUpdate, INT_E, FP8>(src);
 }
 
@@ -2773,7 +2820,7 @@ int tc_pack_entry(ising_ds* ds, void* host_entry) {
 namespace {
 template <int BN, bool INT_E, bool FP8>
 int pack_launch_t(ising_ctx* ctx, const void* entries, const int* start, int count, int tiles,
-                  int* err, bool planes2) {
+                  int* err, bool planes2, const PackFold& f) {
   auto kern = tc_pack_kernel<BN, INT_E, FP8>;
   const size_t smem = TcLayout<BN>::kBytes;
   static bool attr_set = false;  // per instantiation
@@ -2783,29 +2830,29 @@ int pack_launch_t(ising_ctx* ctx, const void* entries, const int* start, int cou
   }
   const int grid = std::max(1, std::min(tiles, ctx->sm_count));
   kern<<<grid, kThreads, smem, ctx->stream>>>(static_cast<const PackEntry*>(entries), start, count, err,
-                                              planes2);
+                                              planes2, f.trk, f.rstart, f.done);
   ISING_CUDA(ctx, cudaGetLastError());
   return ISING_OK;
 }
 
 template <int BN>
 int pack_launch_bn(ising_ctx* ctx, bool ie, bool fp8, bool p2, const void* entries,
-                   const int* start, int count, int tiles, int* err) {
-  if (ie) return fp8 ? pack_launch_t<BN, true, true>(ctx, entries, start, count, tiles, err, p2)
-                     : pack_launch_t<BN, true, false>(ctx, entries, start, count, tiles, err, p2);
-  return fp8 ? pack_launch_t<BN, false, true>(ctx, entries, start, count, tiles, err, p2)
-             : pack_launch_t<BN, false, false>(ctx, entries, start, count, tiles, err, p2);
+                   const int* start, int count, int tiles, int* err, const PackFold& f) {
+  if (ie) return fp8 ? pack_launch_t<BN, true, true>(ctx, entries, start, count, tiles, err, p2, f)
+                     : pack_launch_t<BN, true, false>(ctx, entries, start, count, tiles, err, p2, f);
+  return fp8 ? pack_launch_t<BN, false, true>(ctx, entries, start, count, tiles, err, p2, f)
+             : pack_launch_t<BN, false, false>(ctx, entries, start, count, tiles, err, p2, f);
 }
 }  // namespace
 
 int tc_pack_launch(ising_ctx* ctx, uint64_t key, int bn, const void* entries, const int* start,
-                   int count, int tiles, int* err) {
+                   int count, int tiles, int* err, const PackFold& f) {
   const bool fp8 = key & 1u, ie = (key & 2u) != 0, p2 = (key & 4u) != 0;
   switch (bn) {
-    case 256: return pack_launch_bn<256>(ctx, ie, fp8, p2, entries, start, count, tiles, err);
-    case 224: return pack_launch_bn<224>(ctx, ie, fp8, p2, entries, start, count, tiles, err);
-    case 128: return pack_launch_bn<128>(ctx, ie, fp8, p2, entries, start, count, tiles, err);
-    case 64: return pack_launch_bn<64>(ctx, ie, fp8, p2, entries, start, count, tiles, err);
+    case 256: return pack_launch_bn<256>(ctx, ie, fp8, p2, entries, start, count, tiles, err, f);
+    case 224: return pack_launch_bn<224>(ctx, ie, fp8, p2, entries, start, count, tiles, err, f);
+    case 128: return pack_launch_bn<128>(ctx, ie, fp8, p2, entries, start, count, tiles, err, f);
+    case 64: return pack_launch_bn<64>(ctx, ie, fp8, p2, entries, start, count, tiles, err, f);
     default: return fail(ctx, ISING_EINVAL, "pack: unknown tile width");
   }
 }

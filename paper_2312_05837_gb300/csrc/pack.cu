@@ -1,10 +1,12 @@
 // Batching: several domain-selection sessions (Sec. III-B), of different
 // sizes and restart counts, advanced together. One step of every member is
 // one persistent tensor-core launch over the concatenation of the members'
-// tiles plus one tracking launch over all their restarts; each member keeps
-// its own device step counter, from which the launches pick its spin and
-// partial slots, so the two launches are the same for every step whatever
-// the members' progress and the step loop is replayed from a CUDA graph.
+// tiles, whose epilogue warps also track every member's previous step (with
+// the convergence rule: a tracking launch over all their restarts after each
+// step instead); each member keeps its own device step counter, from which
+// the launches pick its spin and partial slots, so the launches are the same
+// for every step whatever the members' progress and the step loop is
+// replayed from a CUDA graph.
 // A small instance that would leave most SMs idle alone shares the SMs with
 // the other members instead (the restarts of Sec. IV-C, across instances).
 #include "ds_internal.cuh"
@@ -32,6 +34,10 @@ struct ising_pack {
   cudaEvent_t ev = nullptr;
   bool launched = false;  // the kernels have run once outside capture
   int64_t advances = 0;   // pack_advance calls so far
+  // the step launches track every member's previous step (no member uses
+  // the convergence rule); each pack_advance then ends with one tracking
+  // launch for the last step
+  bool fold = false;
 };
 
 namespace {
@@ -64,8 +70,15 @@ int pack_width(const ising_ctx* ctx, ising_ds* const* s, int count) {
 int pack_step(ising_pack* pk) {
   ising_ctx* ctx = pk->ctx;
   int* err = reinterpret_cast<int*>(pk->words.as<unsigned long long>() + 1);
+  PackFold f;
+  if (pk->fold) {
+    f.trk = pk->targs.as<TrackArgs>();
+    f.rstart = pk->rstart.as<int64_t>();
+    f.done = pk->words.as<unsigned long long>();
+  }
   ISING_TRY(tc_pack_launch(ctx, pk->key, pk->bn, pk->entries.p, pk->start.as<int>(),
-                           (int)pk->members.size(), pk->tiles, err));
+                           (int)pk->members.size(), pk->tiles, err, f));
+  if (pk->fold) return ISING_OK;
   return track_pack(ctx, pk->spin_kind, pk->targs.as<TrackArgs>(), pk->rstart.as<int64_t>(),
                     (int)pk->members.size(), pk->restarts, pk->words.as<unsigned long long>());
 }
@@ -151,6 +164,11 @@ int pack_advance(ising_pack* pk, int64_t steps) {
       pk->launched = true;
     }
   }
+  // the last step's tracking (its launch tracked only its predecessor)
+  if (pk->fold && steps > 0)
+    ISING_TRY(track_pack(ctx, pk->spin_kind, pk->targs.as<TrackArgs>(), pk->rstart.as<int64_t>(),
+                         (int)pk->members.size(), pk->restarts, pk->words.as<unsigned long long>(),
+                         true));
   for (ising_ds* ds : pk->members) ds->t += steps;
   pk->advances += 1;
   return members_wait(pk);
@@ -199,6 +217,9 @@ extern "C" int ising_pack_create(ising_ctx* ctx, ising_ds* const* sessions, int3
   pk->key = key;
   pk->bn = pack_width(ctx, sessions, count);
   pk->spin_kind = sessions[0]->spin_kind;
+  pk->fold = true;
+  for (int k = 0; k < count; ++k)
+    if (sessions[k]->conv.p) pk->fold = false;  // retired tiles read the tracked counts
   int rc = [&]() -> int {
     ISING_CUDA(ctx, cudaEventCreateWithFlags(&pk->ev, cudaEventDisableTiming));
     const size_t eb = tc_pack_entry_bytes();
