@@ -256,9 +256,11 @@ const char* ising_energy_noalloc_error(void);
 
 /* Several domain-selection sessions of different sizes advanced together:
  * each step of every member runs as one persistent tensor-core launch over
- * the concatenated tiles of all members plus one tracking launch over all
- * their restarts (the restarts, or "sweeps", of Sec. IV-C batched across
- * instances); from the pack's second ising_pack_run on, the step loop is
+ * the concatenated tiles of all members, which also tracks every member's
+ * previous step (a tracking launch over all their restarts follows each
+ * step instead when a member uses ISING_DS_CONVERGE, and one follows the
+ * last step of each ising_pack_run) (the restarts, or "sweeps", of Sec. IV-C
+ * batched across instances); from the pack's second ising_pack_run on, the step loop is
  * replayed from a CUDA graph captured then. Each member keeps its own step
  * counter on the device and computes exactly what it computes alone (the
  * same products in the same order): a member's state, bests and result are
