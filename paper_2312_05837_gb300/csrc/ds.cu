@@ -104,18 +104,19 @@ __device__ __forceinline__ int8_t spin_at(const void* spins, int64_t n, int64_t 
 }
 
 // Best tracking for step t = counters[0] + 1 of one session, one warp per
-// restart; the last block advances the step counter. With A.flush, the step
-// the counter names (already advanced by a step launch that tracks its
-// predecessor) is tracked and the counter is left alone.
+// restart; the last block advances the step counter and records t as
+// tracked (counters[2]). With A.flush, the step the counter names (already
+// advanced by a step launch that tracks its predecessor) is tracked unless
+// counters[2] says it has been, and only counters[2] changes.
 template <int KIND>
 __global__ void __launch_bounds__(256) track_kernel(const TrackArgs A) {
   const long long t = A.counters[0] + (A.flush ? 0 : 1);
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t b = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); b < A.B;
-       b += warps)
-    track_restart<KIND>(A, t, b, lane);
-  if (A.flush) return;
+  if (t >= 1 && t > A.counters[2])
+    for (int64_t b = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); b < A.B;
+         b += warps)
+      track_restart<KIND>(A, t, b, lane);
   __shared__ bool last;
   __syncthreads();
   __threadfence();
@@ -125,7 +126,9 @@ __global__ void __launch_bounds__(256) track_kernel(const TrackArgs A) {
   }
   __syncthreads();
   if (last && threadIdx.x == 0) {
+    // (every block has read counters[0] and [2] by now)
     A.counters[0] = t;
+    if (t > A.counters[2]) A.counters[2] = t;
     A.counters[1] = 0;
     __threadfence();
   }
@@ -153,16 +156,21 @@ __global__ void __launch_bounds__(256) track_pack_kernel(const TrackArgs* __rest
     }
     const TrackArgs& A = M[lo];
     const long long t = A.counters[0] + (flush ? 0 : 1);
-    if (t >= 1) track_restart<KIND>(A, t, g - rstart[lo], lane);
+    if (t >= 1 && t > A.counters[2]) track_restart<KIND>(A, t, g - rstart[lo], lane);
   }
-  if (flush) return;
   __shared__ bool last;
   __syncthreads();
   __threadfence();
   if (threadIdx.x == 0) last = atomicAdd(done, 1ull) == gridDim.x - 1;
   __syncthreads();
   if (last) {
-    for (int e = threadIdx.x; e < count; e += blockDim.x) M[e].counters[0] += 1;
+    // (every block has read the counters by now) each member's tracked step
+    for (int e = threadIdx.x; e < count; e += blockDim.x) {
+      long long* c = M[e].counters;
+      const long long t = c[0] + (flush ? 0 : 1);
+      c[0] = t;
+      if (t > c[2]) c[2] = t;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
       *done = 0;
@@ -555,14 +563,14 @@ int common_alloc(ising_ds* ds) {
   }
   ISING_TRY(dev_alloc(ctx, ds->work, 8));
   ISING_CUDA(ctx, cudaMemsetAsync(ds->work.p, 0, 8, ctx->stream));
-  ISING_TRY(dev_alloc(ctx, ds->counters, 16));
+  ISING_TRY(dev_alloc(ctx, ds->counters, 32));
   ISING_TRY(dev_alloc(ctx, ds->scratch, 64));
   fill_double<<<grid1d(ctx, B), 256, 0, ctx->stream>>>(ds->best_E.as<double>(), B, INFINITY);
   fill_double<<<grid1d(ctx, B), 256, 0, ctx->stream>>>(ds->last_E.as<double>(), B, INFINITY);
   ISING_CUDA(ctx, cudaGetLastError());
   ISING_CUDA(ctx, cudaMemsetAsync(ds->best_t.p, 0, B * 8, ctx->stream));
   ISING_CUDA(ctx, cudaMemsetAsync(ds->best_s.p, 0, (size_t)B * ds->bs_ld, ctx->stream));
-  ISING_CUDA(ctx, cudaMemsetAsync(ds->counters.p, 0, 16, ctx->stream));
+  ISING_CUDA(ctx, cudaMemsetAsync(ds->counters.p, 0, 32, ctx->stream));
   // Adam bias corrections for t = 0 .. T + 1 (entry 0 unused)
   std::vector<float> bias((size_t)(ds->T + 2) * 2);
   for (int64_t t = 1; t <= ds->T + 1; ++t) {
@@ -786,8 +794,9 @@ constexpr int64_t kGraphSteps = 48;  // a multiple of the launch period 6
 // Whether the update launches of this session track the step before theirs
 // (the streaming tensor-core form without the convergence rule or the
 // relaxed product): a step then takes one launch instead of two, and the
-// last step of each run is tracked by a flush launch. Tracking a step twice
-// changes nothing (strict < against the best, the same last energy).
+// last step of each run is tracked by a flush launch. The session's
+// counters[2] names the latest tracked step, so no launch tracks a step
+// twice, nor a step whose energies were never computed (an imported one).
 bool fold_ok(ising_ds* ds) {
   return ds->path == ISING_PATH_TC && !tc_is_resident(ds) && !ds->relaxed() && !ds->conv.p;
 }
@@ -1182,8 +1191,9 @@ extern "C" int ising_ds_import_state(ising_ds* ds, const float* theta, const flo
     }
   }
   ds->t = t;
-  long long cnt[2] = {(long long)t, 0};
-  ISING_CUDA(ctx, cudaMemcpyAsync(ds->counters.p, cnt, 16, cudaMemcpyHostToDevice, ctx->stream));
+  // (step t has no energies in this session: it counts as tracked)
+  long long cnt[4] = {(long long)t, 0, (long long)t, 0};
+  ISING_CUDA(ctx, cudaMemcpyAsync(ds->counters.p, cnt, 32, cudaMemcpyHostToDevice, ctx->stream));
   const int slot = (int)((t + 1) % 3);
   if (ds->path == ISING_PATH_SPARSE) {
     spins_from_theta_bits<<<grid1d(ctx, n * ds->Bp / 32), 256, 0, ctx->stream>>>(

@@ -296,7 +296,9 @@ struct ising_ds {
   long long* conv_step() const { return reinterpret_cast<long long*>(conv.as<double>() + 6 * B); }
   unsigned long long* conv_count() const { return reinterpret_cast<unsigned long long*>(conv.as<double>() + 7 * B); }
   int64_t bs_ld = 0;       // row pitch of best_s (n rounded up to 16)
-  ising::DevMem counters;  // int64 [0] = steps done, [1] = done-block counter
+  // int64 [0] = steps done, [1] = done-block counter, [2] = the latest step
+  // whose energies have been tracked (0: none), [3] unused
+  ising::DevMem counters;
   ising::DevMem bias;      // float2 [T + 2]: 1/(1-b1^t), 1/(1-b2^t)
   // dense operands
   ising::DevMem Jf;        // plain path: float n x n

@@ -212,17 +212,18 @@ struct TileRef {
 
 // Called by every CTA of a launch at its end: `done` counts the CTAs that
 // got here, and the last one (every CTA has read the step counters by then)
-// resets it and adds one to the step counter of the session (`ctr`) or of
-// each of `count` pack members (trk[e].counters).
+// resets it and, for the session (`ctr`) or each of `count` pack members
+// (trk[e].counters), records the step before this launch's as tracked
+// ([2]) and adds one to the step counter ([0]).
 __device__ __forceinline__ void advance_counters(unsigned long long* done, long long* ctr,
                                                  const TrackArgs* trk, int count) {
   if (threadIdx.x != 0) return;
   __threadfence();
   if (atomicAdd(done, 1ull) != gridDim.x - 1) return;
-  if (trk) {
-    for (int e = 0; e < count; ++e) trk[e].counters[0] += 1;
-  } else {
-    ctr[0] += 1;
+  for (int e = 0; e < (trk ? count : 1); ++e) {
+    long long* c = trk ? trk[e].counters : ctr;
+    if (c[0] > c[2]) c[2] = c[0];
+    c[0] += 1;
   }
   *done = 0;
   __threadfence();
@@ -251,7 +252,7 @@ struct OneInstance {
   template <int KIND>
   __device__ void track_prev(int64_t gw, int64_t nw, int lane) const {
     const long long tp = P.counters[0];
-    if (!P.fold || tp < 1) return;
+    if (!P.fold || tp < 1 || tp <= P.counters[2]) return;  // none, or already tracked
     for (int64_t b = gw; b < P.trk.B; b += nw) track_restart<KIND>(P.trk, tp, b, lane);
   }
   __device__ void advance_step() const {
@@ -339,7 +340,7 @@ struct PackedInstances {
       }
       const TrackArgs& A = trk[lo];
       const long long tp = A.counters[0];
-      if (tp >= 1) track_restart<KIND>(A, tp, g - rstart[lo], lane);
+      if (tp >= 1 && tp > A.counters[2]) track_restart<KIND>(A, tp, g - rstart[lo], lane);
     }
   }
   __device__ void advance_step() const {
@@ -408,7 +409,7 @@ struct PairInstance {
   template <int KIND>
   __device__ void track_prev(int64_t gw, int64_t nw, int lane) const {
     const long long tp = P.counters[0];
-    if (!P.fold || tp < 1) return;
+    if (!P.fold || tp < 1 || tp <= P.counters[2]) return;  // none, or already tracked
     for (int64_t b = gw; b < P.trk.B; b += nw) track_restart<KIND>(P.trk, tp, b, lane);
   }
   __device__ void advance_step() const {

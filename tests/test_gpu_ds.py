@@ -109,6 +109,39 @@ def test_one_step_parity_from_an_imported_state(gpu_ctx, name, prec):
 
 
 @pytest.mark.parametrize("name,prec", CASES)
+def test_bests_after_an_imported_state_cover_the_steps_run(gpu_ctx, name, prec):
+    """A state imported at step t0 has no energies of its own, so the bests
+    of a fresh session afterwards are those of the steps it then runs: per
+    restart the earliest minimum of their energies (strict <), whether the
+    steps run one call at a time or in one call with graph replays, on every
+    path (the streaming tensor-core update launches track the step before
+    theirs, and must not track the imported one)."""
+    inst = INSTANCES[name]
+    B, n, t0, K = 24, inst.n, 7, 100
+    r = np.random.default_rng(12)
+    th = r.uniform(-math.pi, math.pi, (B, n)).astype(np.float32)
+    m = (r.standard_normal((B, n)) * 0.3).astype(np.float32)
+    v = (r.random((B, n)) * 0.5).astype(np.float32)
+    kw = dict(restarts=B, steps=t0 + K + 5, lr=0.5, mu=0.2, seed=1, **_kw(prec))
+    a = api.Session(gpu_ctx, inst, **kw)
+    a.import_state(th, m, v, t0)
+    trace = np.empty((K, B))
+    for k in range(K):
+        a.run(1)
+        trace[k] = a.last_energies()
+    b = api.Session(gpu_ctx, inst, **kw)
+    b.import_state(th, m, v, t0)
+    b.run(K)
+    for s_ in (a, b):
+        E, step, _ = s_.restart_best()
+        np.testing.assert_array_equal(E, trace.min(axis=0))
+        np.testing.assert_array_equal(step, t0 + 1 + trace.argmin(axis=0))
+    np.testing.assert_array_equal(b.last_energies(), trace[-1])
+    a.close()
+    b.close()
+
+
+@pytest.mark.parametrize("name,prec", CASES)
 def test_best_tracking_and_result(gpu_ctx, name, prec):
     inst = INSTANCES[name]
     B, T = 24, 30
