@@ -77,3 +77,24 @@ def test_serving_capacity_at_the_roofline():
     # restarts pad to 128 on the sparse path
     got_pad = bench.serving_capacity([(0.0, sparse)], 129, T, pk)
     assert got_pad == pytest.approx(1.0 / (24.25 * 3000 * 256 * T / 5e12), rel=1e-12)
+
+
+def test_launch_count_model_of_a_solve():
+    """bench.py's count of the library's kernel launches in one solve: the
+    streaming tensor-core path takes one launch per step (each tracks the
+    step before it) plus one tracking launch after the last; the other
+    non-resident paths a step and a tracking launch per step (the sparse path
+    also a spin copy); a resident form one launch for all steps."""
+    import bench
+    T, rounds = 50, 2
+    base = bench.launches_per_solve(0, rounds, 0, False, False, False)
+    assert bench.launches_per_solve(T, rounds, 1, False, False, False) - \
+        bench.launches_per_solve(0, rounds, 1, False, False, False) == T
+    assert bench.launches_per_solve(T, rounds, 0, False, False, False) - base == 2 * T
+    assert bench.launches_per_solve(T, rounds, 2, False, False, False) - \
+        bench.launches_per_solve(0, rounds, 2, False, False, False) == 3 * T
+    assert bench.launches_per_solve(T, rounds, 1, True, False, False) == \
+        bench.launches_per_solve(2 * T, rounds, 1, True, False, False)
+    # set-up: the integer row-sum bound and the per-row scales add a launch each
+    assert bench.launches_per_solve(T, rounds, 1, False, True, True) == \
+        bench.launches_per_solve(T, rounds, 1, False, False, False) + 2
